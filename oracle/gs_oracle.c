@@ -1,0 +1,903 @@
+/*
+ * gs_oracle.c -- plain FP64 CPU oracle for the Gaussian-splatting RGB-D
+ * renderer and the linear-blend-skinning (LBS) deformation of Gaussian avatars.
+ *
+ * TEST INFRASTRUCTURE.  Only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this library.  The CUDA product path
+ * neither links nor calls it, and the two share no source.
+ *
+ * What it follows.  The paper renders scene Gaussians with tile-based 3D
+ * Gaussian Splatting rasterisation (Sec. 2.2 and Sec. 3.2) and deforms canonical
+ * avatar Gaussians to the current pose with a CUDA LBS kernel over per-frame
+ * SMPL-X joint matrices (Sec. 3.1 "Asset Preparation", Sec. 3.3, Sec. 3.3.1).
+ * It prints no rasteriser formulas, so this file writes out the standard
+ * definitions it cites:
+ *   activation  scale = exp(s), opacity = sigmoid(o), R = R(q / |q|),
+ *               Sigma = R diag(scale^2) R^T (or a given posed covariance);
+ *   view        d = mu - C, p = W d   (W world->camera rotation, C centre);
+ *   projection  u = fx px/pz + cx, v = fy py/pz + cy; EWA Jacobian J with
+ *               the lateral clamp at 1.3 x half-field; Sigma2 = J W Sigma W^T J^T
+ *               plus 0.3 px^2 on the diagonal;
+ *   conic       inverse of Sigma2, radius r = ceil(3 sqrt(lambda_max)) with the
+ *               0.1 floor on the discriminant;
+ *   footprint   pixel (i, j) is covered iff |i-u| <= r and |j-v| <= r;
+ *   colour      real spherical harmonics of degree 3 at the unit view
+ *               direction, + 0.5, clamped below at 0;
+ *   order       per pixel, covered Gaussians by (depth key, index);
+ *   blend       alpha = min(0.99, opacity exp(power)), skip alpha < 1/255,
+ *               stop before blending when T (1-alpha) < 1e-4;
+ *               C += c alpha T, D += z alpha T, T *= (1 - alpha).
+ * Two decisions are taken in FP32 so that both sides take them in the same
+ * precision: the depth key that orders and near-culls the Gaussians is
+ *   zkey = fl(fl(fl(W20 d0) + fl(W21 d1)) + fl(W22 d2)),  d_i = fl(mu_i - C_i)
+ * in single precision.  Everything else is double precision.
+ *
+ * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (contraction off so
+ * that the FP32 key is bit-reproducible on x86-64 and aarch64).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <float.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define AMB_VALUE 1u /* colour or depth may differ beyond the FP32 tolerance */
+#define AMB_COUNT 2u /* the contributor count may differ by a flipped decision */
+
+#define ALPHA_MIN (1.0 / 255.0)
+#define ALPHA_MAX 0.99
+#define T_STOP 1e-4
+#define DILATION 0.3
+#define FLAG_NORMALIZE_DEPTH 1
+
+/* ------------------------------------------------------------------------ */
+/* Real spherical harmonics up to degree 3, in the ordering and sign          */
+/* convention of the 3DGS reference renderer (Condon-Shortley phase folded    */
+/* into the m = +-1 terms).  Normalisation constants are written from their   */
+/* closed forms so that they can be checked by eye.                           */
+/* ------------------------------------------------------------------------ */
+static void sh_consts(double c[16])
+{
+    const double pi = 3.14159265358979323846;
+    double c0 = sqrt(1.0 / (4.0 * pi));
+    double c1 = sqrt(3.0 / (4.0 * pi));
+    c[0] = c0;
+    c[1] = -c1; c[2] = c1; c[3] = -c1;
+    c[4] = 0.5 * sqrt(15.0 / pi);
+    c[5] = -0.5 * sqrt(15.0 / pi);
+    c[6] = 0.25 * sqrt(5.0 / pi);
+    c[7] = -0.5 * sqrt(15.0 / pi);
+    c[8] = 0.25 * sqrt(15.0 / pi);
+    c[9] = -0.25 * sqrt(35.0 / (2.0 * pi));
+    c[10] = 0.5 * sqrt(105.0 / pi);
+    c[11] = -0.25 * sqrt(21.0 / (2.0 * pi));
+    c[12] = 0.25 * sqrt(7.0 / pi);
+    c[13] = -0.25 * sqrt(21.0 / (2.0 * pi));
+    c[14] = 0.25 * sqrt(105.0 / pi);
+    c[15] = -0.25 * sqrt(35.0 / (2.0 * pi));
+}
+
+/* Y[k](x,y,z) for a unit direction, and (optionally) its gradient dY[k][3]. */
+static void sh_eval(const double dir[3], double Y[16], double dY[16][3])
+{
+    double c[16];
+    sh_consts(c);
+    double x = dir[0], y = dir[1], z = dir[2];
+    double xx = x * x, yy = y * y, zz = z * z;
+    Y[0] = c[0];
+    Y[1] = c[1] * y;
+    Y[2] = c[2] * z;
+    Y[3] = c[3] * x;
+    Y[4] = c[4] * x * y;
+    Y[5] = c[5] * y * z;
+    Y[6] = c[6] * (2.0 * zz - xx - yy);
+    Y[7] = c[7] * x * z;
+    Y[8] = c[8] * (xx - yy);
+    Y[9] = c[9] * y * (3.0 * xx - yy);
+    Y[10] = c[10] * x * y * z;
+    Y[11] = c[11] * y * (4.0 * zz - xx - yy);
+    Y[12] = c[12] * z * (2.0 * zz - 3.0 * xx - 3.0 * yy);
+    Y[13] = c[13] * x * (4.0 * zz - xx - yy);
+    Y[14] = c[14] * z * (xx - yy);
+    Y[15] = c[15] * x * (xx - 3.0 * yy);
+    if (!dY) return;
+    memset(dY, 0, sizeof(double) * 48);
+    dY[1][1] = c[1];
+    dY[2][2] = c[2];
+    dY[3][0] = c[3];
+    dY[4][0] = c[4] * y;  dY[4][1] = c[4] * x;
+    dY[5][1] = c[5] * z;  dY[5][2] = c[5] * y;
+    dY[6][0] = -2.0 * c[6] * x; dY[6][1] = -2.0 * c[6] * y; dY[6][2] = 4.0 * c[6] * z;
+    dY[7][0] = c[7] * z;  dY[7][2] = c[7] * x;
+    dY[8][0] = 2.0 * c[8] * x; dY[8][1] = -2.0 * c[8] * y;
+    dY[9][0] = 6.0 * c[9] * x * y; dY[9][1] = c[9] * (3.0 * xx - 3.0 * yy);
+    dY[10][0] = c[10] * y * z; dY[10][1] = c[10] * x * z; dY[10][2] = c[10] * x * y;
+    dY[11][0] = -2.0 * c[11] * x * y; dY[11][1] = c[11] * (4.0 * zz - xx - 3.0 * yy);
+    dY[11][2] = 8.0 * c[11] * y * z;
+    dY[12][0] = -6.0 * c[12] * x * z; dY[12][1] = -6.0 * c[12] * y * z;
+    dY[12][2] = c[12] * (6.0 * zz - 3.0 * xx - 3.0 * yy);
+    dY[13][0] = c[13] * (4.0 * zz - 3.0 * xx - yy); dY[13][1] = -2.0 * c[13] * x * y;
+    dY[13][2] = 8.0 * c[13] * x * z;
+    dY[14][0] = 2.0 * c[14] * x * z; dY[14][1] = -2.0 * c[14] * y * z; dY[14][2] = c[14] * (xx - yy);
+    dY[15][0] = c[15] * (3.0 * xx - 3.0 * yy); dY[15][1] = -6.0 * c[15] * x * y;
+}
+
+void or_sh_basis(int64_t n, const double *dirs, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) sh_eval(dirs + 3 * i, out + 16 * i, NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Rotation of a unit quaternion (w, x, y, z) and its partial derivatives.    */
+/* ------------------------------------------------------------------------ */
+static void quat_rot(const double q[4], double R[9])
+{
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1.0 - 2.0 * (y * y + z * z); R[1] = 2.0 * (x * y - w * z);       R[2] = 2.0 * (x * z + w * y);
+    R[3] = 2.0 * (x * y + w * z);       R[4] = 1.0 - 2.0 * (x * x + z * z); R[5] = 2.0 * (y * z - w * x);
+    R[6] = 2.0 * (x * z - w * y);       R[7] = 2.0 * (y * z + w * x);       R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+/* dL/dq (unit quaternion components) given dL/dR (row-major 3x3). */
+static void quat_rot_vjp(const double q[4], const double gR[9], double gq[4])
+{
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    gq[0] = gR[1] * (-2 * z) + gR[2] * (2 * y) + gR[3] * (2 * z) + gR[5] * (-2 * x) + gR[6] * (-2 * y) + gR[7] * (2 * x);
+    gq[1] = gR[1] * (2 * y) + gR[2] * (2 * z) + gR[3] * (2 * y) + gR[4] * (-4 * x) + gR[5] * (-2 * w) + gR[6] * (2 * z) +
+            gR[7] * (2 * w) + gR[8] * (-4 * x);
+    gq[2] = gR[0] * (-4 * y) + gR[1] * (2 * x) + gR[2] * (2 * w) + gR[3] * (2 * x) + gR[5] * (2 * z) + gR[6] * (-2 * w) +
+            gR[7] * (2 * z) + gR[8] * (-4 * y);
+    gq[3] = gR[0] * (-4 * z) + gR[1] * (-2 * w) + gR[2] * (2 * x) + gR[3] * (2 * w) + gR[4] * (-4 * z) + gR[5] * (2 * y) +
+            gR[6] * (2 * x) + gR[7] * (2 * y);
+}
+
+void or_quat_to_rot(const double *q, double *R)
+{
+    double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    double qn[4] = {q[0] / n, q[1] / n, q[2] / n, q[3] / n};
+    quat_rot(qn, R);
+}
+
+/* Sigma = R diag(exp(2 s)) R^T, with R = R(q / |q|). */
+static void cov_from_scale_rot(const double s[3], const double q[4], double S[9])
+{
+    double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    double qn[4] = {q[0] / n, q[1] / n, q[2] / n, q[3] / n};
+    double R[9];
+    quat_rot(qn, R);
+    double sc[3] = {exp(s[0]), exp(s[1]), exp(s[2])};
+    double M[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) M[3 * r + c] = R[3 * r + c] * sc[c];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += M[3 * r + k] * M[3 * c + k];
+            S[3 * r + c] = acc;
+        }
+}
+
+/* Backward of cov_from_scale_rot: given symmetric dL/dSigma, add dL/ds, dL/dq. */
+static void cov_from_scale_rot_vjp(const double s[3], const double q[4], const double gS[9], double gs[3], double gq[4])
+{
+    double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    double qn[4] = {q[0] / n, q[1] / n, q[2] / n, q[3] / n};
+    double R[9];
+    quat_rot(qn, R);
+    double sc[3] = {exp(s[0]), exp(s[1]), exp(s[2])};
+    double M[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) M[3 * r + c] = R[3 * r + c] * sc[c];
+    /* Sigma = M M^T, dL/dM = 2 gS M for symmetric gS */
+    double gM[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += gS[3 * r + k] * M[3 * k + c];
+            gM[3 * r + c] = 2.0 * acc;
+        }
+    double gR[9];
+    for (int c = 0; c < 3; ++c) {
+        double gsc = 0.0;
+        for (int r = 0; r < 3; ++r) {
+            gsc += gM[3 * r + c] * R[3 * r + c];
+            gR[3 * r + c] = gM[3 * r + c] * sc[c];
+        }
+        gs[c] += gsc * sc[c];
+    }
+    double gqn[4];
+    quat_rot_vjp(qn, gR, gqn);
+    double dot = gqn[0] * qn[0] + gqn[1] * qn[1] + gqn[2] * qn[2] + gqn[3] * qn[3];
+    for (int k = 0; k < 4; ++k) gq[k] += (gqn[k] - qn[k] * dot) / n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Projection of one Gaussian into one view.                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double R[9], C[3], fx, fy, cx, cy;
+} cam_t;
+
+static void load_cam(const double *c, cam_t *k)
+{
+    memcpy(k->R, c, 9 * sizeof(double));
+    memcpy(k->C, c + 9, 3 * sizeof(double));
+    k->fx = c[12]; k->fy = c[13]; k->cx = c[14]; k->cy = c[15];
+}
+
+/* Depth key in single precision, in the fixed order stated at the top. */
+static float depth_key(const double mu[3], const cam_t *k)
+{
+    float d0 = (float)mu[0] - (float)k->C[0];
+    float d1 = (float)mu[1] - (float)k->C[1];
+    float d2 = (float)mu[2] - (float)k->C[2];
+    float a = (float)k->R[6] * d0;
+    float b = (float)k->R[7] * d1;
+    float c = (float)k->R[8] * d2;
+    float s = a + b;
+    s = s + c;
+    return s;
+}
+
+typedef struct {
+    /* inputs gathered */
+    double mu[3], Sigma[9];
+    /* view */
+    double d[3], p[3];
+    float zkey;
+    /* projection */
+    double u, v, J[6], T[6], cov2[3], det, conic[3];
+    double tx, ty;
+    int clampx, clampy;
+    double r3;
+    int32_t r, r_lo, r_hi;
+    double opacity, rgb[3], raw[3], dir[3], dnorm;
+    double du, dv; /* FP32 error model of (u, v) in pixels */
+    int cand;      /* footprint under r_hi touches the image */
+    int visible;   /* footprint under r touches the image */
+} proj_t;
+
+static int footprint_on_image(double u, double v, int32_t r, int W, int H)
+{
+    /* exists integer i in [0, W-1] with |i - u| <= r, same for j */
+    double ilo = ceil(u - r), ihi = floor(u + r);
+    double jlo = ceil(v - r), jhi = floor(v + r);
+    if (ilo < 0) ilo = 0;
+    if (ihi > W - 1) ihi = W - 1;
+    if (jlo < 0) jlo = 0;
+    if (jhi > H - 1) jhi = H - 1;
+    return ilo <= ihi && jlo <= jhi;
+}
+
+/* Returns 0 when the Gaussian is culled by the near plane or a singular conic. */
+static int project_one(const double *mu, const double *ls, const double *q, double ologit, const double *sh,
+                       const double *cov3d, int inexact, const cam_t *k, int W, int H, double near_plane, proj_t *o)
+{
+    memset(o, 0, sizeof(*o));
+    memcpy(o->mu, mu, 3 * sizeof(double));
+    o->zkey = depth_key(mu, k);
+    if (!(o->zkey > (float)near_plane)) return 0;
+    for (int i = 0; i < 3; ++i) o->d[i] = mu[i] - k->C[i];
+    for (int r = 0; r < 3; ++r) o->p[r] = k->R[3 * r] * o->d[0] + k->R[3 * r + 1] * o->d[1] + k->R[3 * r + 2] * o->d[2];
+    double px = o->p[0], py = o->p[1], pz = o->p[2];
+    if (cov3d) {
+        double *S = o->Sigma;
+        S[0] = cov3d[0]; S[1] = cov3d[1]; S[2] = cov3d[2];
+        S[3] = cov3d[1]; S[4] = cov3d[3]; S[5] = cov3d[4];
+        S[6] = cov3d[2]; S[7] = cov3d[4]; S[8] = cov3d[5];
+    } else {
+        cov_from_scale_rot(ls, q, o->Sigma);
+    }
+    o->u = k->fx * px / pz + k->cx;
+    o->v = k->fy * py / pz + k->cy;
+    /* EWA Jacobian with the lateral clamp (1.3 x the half field of view) */
+    double limx = 1.3 * (0.5 * W / k->fx), limy = 1.3 * (0.5 * H / k->fy);
+    double tx = px / pz, ty = py / pz;
+    o->clampx = (tx < -limx || tx > limx);
+    o->clampy = (ty < -limy || ty > limy);
+    if (tx < -limx) tx = -limx;
+    if (tx > limx) tx = limx;
+    if (ty < -limy) ty = -limy;
+    if (ty > limy) ty = limy;
+    o->tx = tx; o->ty = ty;
+    double *J = o->J; /* 2x3 row-major */
+    J[0] = k->fx / pz; J[1] = 0.0; J[2] = -k->fx * tx / pz;
+    J[3] = 0.0; J[4] = k->fy / pz; J[5] = -k->fy * ty / pz;
+    double *T = o->T; /* T = J W */
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 3; ++c) T[3 * r + c] = J[3 * r] * k->R[c] + J[3 * r + 1] * k->R[3 + c] + J[3 * r + 2] * k->R[6 + c];
+    double TS[6];
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 3; ++c)
+            TS[3 * r + c] = T[3 * r] * o->Sigma[c] + T[3 * r + 1] * o->Sigma[3 + c] + T[3 * r + 2] * o->Sigma[6 + c];
+    double s00 = TS[0] * T[0] + TS[1] * T[1] + TS[2] * T[2];
+    double s01 = TS[0] * T[3] + TS[1] * T[4] + TS[2] * T[5];
+    double s11 = TS[3] * T[3] + TS[4] * T[4] + TS[5] * T[5];
+    double a = s00 + DILATION, b = s01, c = s11 + DILATION;
+    o->cov2[0] = a; o->cov2[1] = b; o->cov2[2] = c;
+    double det = a * c - b * b;
+    o->det = det;
+    if (!(det > 0.0)) return 0;
+    o->conic[0] = c / det; o->conic[1] = -b / det; o->conic[2] = a / det;
+    double mid = 0.5 * (a + c);
+    double disc = mid * mid - det;
+    if (disc < 0.1) disc = 0.1;
+    double lam = mid + sqrt(disc);
+    o->r3 = 3.0 * sqrt(lam);
+    o->r = (int32_t)ceil(o->r3);
+    /* FP32 can round 3 sqrt(lambda) to the other side of an integer */
+    double k3 = floor(o->r3 + 0.5);
+    if (fabs(o->r3 - k3) <= 4e-6 * o->r3 + 1e-7 && k3 >= 1.0) {
+        o->r_lo = (int32_t)k3;
+        o->r_hi = (int32_t)k3 + 1;
+    } else {
+        o->r_lo = o->r_hi = o->r;
+    }
+    /* FP32 error model of u, v: rounding of d, of p and of the projection */
+    double dl1 = fabs(o->d[0]) + fabs(o->d[1]) + fabs(o->d[2]);
+    double pl1 = fabs(px) + fabs(py) + fabs(pz);
+    double mu_err = inexact ? 2e-6 * (fabs(mu[0]) + fabs(mu[1]) + fabs(mu[2]) + 1.0) : 0.0;
+    double pos_err = 4e-7 * (dl1 + pl1) + mu_err;
+    o->du = k->fx * pos_err / pz * (1.0 + fabs(tx)) + 4e-7 * fabs(o->u - k->cx) + 1e-7;
+    o->dv = k->fy * pos_err / pz * (1.0 + fabs(ty)) + 4e-7 * fabs(o->v - k->cy) + 1e-7;
+    o->cand = footprint_on_image(o->u, o->v, o->r_hi, W, H);
+    o->visible = footprint_on_image(o->u, o->v, o->r, W, H);
+    if (!o->cand) return 0;
+    o->opacity = 1.0 / (1.0 + exp(-ologit));
+    double dn = sqrt(o->d[0] * o->d[0] + o->d[1] * o->d[1] + o->d[2] * o->d[2]);
+    o->dnorm = dn;
+    for (int i = 0; i < 3; ++i) o->dir[i] = o->d[i] / dn;
+    double Y[16];
+    sh_eval(o->dir, Y, NULL);
+    for (int ch = 0; ch < 3; ++ch) {
+        double acc = 0.0;
+        for (int kk = 0; kk < 16; ++kk) acc += Y[kk] * sh[3 * kk + ch];
+        acc += 0.5;
+        o->raw[ch] = acc;
+        o->rgb[ch] = acc < 0.0 ? 0.0 : acc;
+    }
+    return 1;
+}
+
+/* Exported per-Gaussian projection (one view). */
+int64_t or_project(int64_t n, const double *means, const double *log_scales, const double *quats, const double *ologits,
+                   const double *sh, const double *cov3d, const uint8_t *use_cov, const uint8_t *inexact, const double *cam,
+                   int32_t W, int32_t H, double near_plane, int32_t *visible, double *u, double *v, double *z, float *zkey,
+                   double *cov2, double *conic, double *opacity, double *rgb, int32_t *radius, double *r3)
+{
+    cam_t k;
+    load_cam(cam, &k);
+    int64_t nvis = 0;
+#pragma omp parallel for schedule(static) reduction(+ : nvis)
+    for (int64_t g = 0; g < n; ++g) {
+        proj_t o;
+        const double *cv = (cov3d && use_cov && use_cov[g]) ? cov3d + 6 * g : NULL;
+        int ok = project_one(means + 3 * g, log_scales + 3 * g, quats + 4 * g, ologits[g], sh + 48 * g, cv,
+                             inexact ? inexact[g] : 0, &k, W, H, near_plane, &o);
+        int vis = ok && o.visible;
+        visible[g] = vis;
+        nvis += vis;
+        u[g] = o.u; v[g] = o.v; z[g] = o.p[2]; zkey[g] = o.zkey;
+        for (int i = 0; i < 3; ++i) {
+            cov2[3 * g + i] = o.cov2[i];
+            conic[3 * g + i] = o.conic[i];
+            rgb[3 * g + i] = o.rgb[i];
+        }
+        opacity[g] = o.opacity;
+        radius[g] = o.r;
+        r3[g] = o.r3;
+    }
+    return nvis;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-pixel front-to-back blending step.  The pixel-major and the           */
+/* Gaussian-major loops both call this one function, in the same per-pixel    */
+/* order, so their results agree bit for bit.                                 */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double u, v, z, A, B, C, o, rgb[3], du, dv;
+    int32_t r, r_lo, r_hi;
+    float zkey;
+    uint8_t inexact;
+    int64_t idx;
+} cand_t;
+
+typedef struct {
+    double T, C[3], D, relT;
+    int32_t ncov, n, last, done;
+    float prev_zkey;
+    int32_t have_prev, prev_inexact;
+    uint8_t amb;
+    int64_t evals;
+} pix_t;
+
+static void pix_init(pix_t *s)
+{
+    memset(s, 0, sizeof(*s));
+    s->T = 1.0;
+}
+
+static double maxabs3(const double *c)
+{
+    double m = fabs(c[0]);
+    if (fabs(c[1]) > m) m = fabs(c[1]);
+    if (fabs(c[2]) > m) m = fabs(c[2]);
+    return m;
+}
+
+static void blend_step(pix_t *s, const cand_t *g, int i, int j, int32_t pos)
+{
+    if (s->done) return;
+    double dx = g->u - (double)i, dy = g->v - (double)j;
+    double m = fabs(dx) > fabs(dy) ? fabs(dx) : fabs(dy);
+    double eps = (g->du > g->dv ? g->du : g->dv) + 1e-6;
+    if (m > g->r_hi + eps) return;
+    double q = g->A * dx * dx + g->C * dy * dy;
+    double power = -0.5 * q - g->B * dx * dy;
+    double dpow = fabs(g->A * dx + g->B * dy) * g->du + fabs(g->C * dy + g->B * dx) * g->dv +
+                  4e-6 * (0.5 * q + fabs(g->B * dx * dy)) + 2e-6;
+    if (m >= g->r_lo - eps && m <= g->r_hi + eps) {
+        /* coverage can flip under FP32 rounding of u, v or of the radius */
+        s->amb |= AMB_COUNT;
+        if (power <= dpow && g->o * exp(power) >= ALPHA_MIN * (1.0 - 1e-3)) s->amb |= AMB_VALUE;
+    }
+    if (m > (double)g->r) return;
+    if (s->have_prev && (g->inexact || s->prev_inexact)) {
+        float lo = s->prev_zkey < g->zkey ? s->prev_zkey : g->zkey;
+        float hi = s->prev_zkey < g->zkey ? g->zkey : s->prev_zkey;
+        if ((double)hi - (double)lo <= 8.0 * (double)FLT_EPSILON * (double)hi) s->amb |= AMB_VALUE | AMB_COUNT;
+    }
+    s->have_prev = 1;
+    s->prev_zkey = g->zkey;
+    s->prev_inexact = g->inexact;
+    s->ncov += 1;
+    s->evals += 1;
+    if (power > 0.0) return;
+    double G = exp(power);
+    double a_raw = g->o * G;
+    double alpha = a_raw < ALPHA_MAX ? a_raw : ALPHA_MAX;
+    double cmax = maxabs3(g->rgb) + 1.0;
+    /* alpha >= 1/255 decision */
+    if (fabs(power + log(g->o) - log(ALPHA_MIN)) <= dpow + 2e-6) {
+        s->amb |= AMB_COUNT;
+        if (ALPHA_MIN * s->T * cmax > 0.5e-4 || ALPHA_MIN * s->T * g->z > 0.5e-4 * (s->D + ALPHA_MIN * s->T * g->z))
+            s->amb |= AMB_VALUE;
+    }
+    if (alpha < ALPHA_MIN) return;
+    double Tn = s->T * (1.0 - alpha);
+    double relTn = s->relT + 4.8e-7 + (a_raw < ALPHA_MAX ? alpha / (1.0 - alpha) * (dpow + 2e-6) : 0.0);
+    /* T (1 - alpha) < 1e-4 decision */
+    if (fabs(Tn - T_STOP) <= T_STOP * relTn + 1e-12) {
+        s->amb |= AMB_COUNT;
+        double ec = alpha * s->T * (maxabs3(g->rgb) + 1e-30);
+        double ed = alpha * s->T * g->z;
+        if (ec > 0.5e-4 || ed > 0.5e-4 * (s->D + ed)) s->amb |= AMB_VALUE;
+    }
+    if (Tn < T_STOP) {
+        s->done = 1;
+        return;
+    }
+    double w = alpha * s->T;
+    s->C[0] += g->rgb[0] * w;
+    s->C[1] += g->rgb[1] * w;
+    s->C[2] += g->rgb[2] * w;
+    s->D += g->z * w;
+    s->T = Tn;
+    s->relT = relTn;
+    s->n = s->ncov;
+    s->last = pos + 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Candidate list: projected Gaussians whose footprint may touch the image,   */
+/* sorted by (FP32 depth key, index).                                          */
+/* ------------------------------------------------------------------------ */
+static int cand_cmp(const void *a, const void *b)
+{
+    const cand_t *x = (const cand_t *)a, *y = (const cand_t *)b;
+    if (x->zkey < y->zkey) return -1;
+    if (x->zkey > y->zkey) return 1;
+    return (x->idx < y->idx) ? -1 : (x->idx > y->idx);
+}
+
+static int64_t build_candidates(int64_t n, const double *means, const double *ls, const double *q, const double *ologit,
+                                const double *sh, const double *cov3d, const uint8_t *use_cov, const uint8_t *inexact,
+                                const cam_t *k, int W, int H, double near_plane, cand_t **out)
+{
+    cand_t *c = (cand_t *)malloc(sizeof(cand_t) * (size_t)(n > 0 ? n : 1));
+    uint8_t *ok = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+#pragma omp parallel for schedule(static)
+    for (int64_t g = 0; g < n; ++g) {
+        proj_t o;
+        const double *cv = (cov3d && use_cov && use_cov[g]) ? cov3d + 6 * g : NULL;
+        int inx = inexact ? inexact[g] : 0;
+        if (!project_one(means + 3 * g, ls + 3 * g, q + 4 * g, ologit[g], sh + 48 * g, cv, inx, k, W, H, near_plane, &o))
+            continue;
+        ok[g] = 1;
+        cand_t *t = c + g;
+        t->u = o.u; t->v = o.v; t->z = o.p[2];
+        t->A = o.conic[0]; t->B = o.conic[1]; t->C = o.conic[2];
+        t->o = o.opacity;
+        for (int i = 0; i < 3; ++i) t->rgb[i] = o.rgb[i];
+        t->du = o.du; t->dv = o.dv;
+        t->r = o.r; t->r_lo = o.r_lo; t->r_hi = o.r_hi;
+        t->zkey = o.zkey;
+        t->inexact = (uint8_t)inx;
+        t->idx = g;
+    }
+    int64_t m = 0;
+    for (int64_t g = 0; g < n; ++g)
+        if (ok[g]) c[m++] = c[g];
+    free(ok);
+    qsort(c, (size_t)m, sizeof(cand_t), cand_cmp);
+    *out = c;
+    return m;
+}
+
+static void finish_pixel(const pix_t *s, const double *bg, int flags, int64_t p, int64_t HW, double *rgb, double *depth,
+                         double *Tout, int32_t *nout, uint8_t *amb, int32_t *last)
+{
+    for (int ch = 0; ch < 3; ++ch) rgb[ch * HW + p] = s->C[ch] + s->T * bg[ch];
+    double D = s->D;
+    if (flags & FLAG_NORMALIZE_DEPTH) D = (1.0 - s->T) < 1e-4 ? 0.0 : s->D / (1.0 - s->T);
+    depth[p] = D;
+    Tout[p] = s->T;
+    nout[p] = s->n;
+    if (amb) amb[p] = s->amb;
+    if (last) last[p] = s->last;
+}
+
+static int num_threads(int32_t req)
+{
+#ifdef _OPENMP
+    if (req > 0) return req;
+    return omp_get_max_threads();
+#else
+    (void)req;
+    return 1;
+#endif
+}
+
+/* Gaussian-major walk over row bands [0, H): every band walks the whole
+ * sorted candidate list and updates only its own pixels. */
+static int64_t walk_gaussian_major(const cand_t *c, int64_t m, int W, int H, pix_t *st, int nthreads)
+{
+    int64_t evals = 0;
+    int nb = nthreads > H ? H : nthreads;
+    if (nb < 1) nb = 1;
+#pragma omp parallel for schedule(static, 1) num_threads(nb) reduction(+ : evals)
+    for (int b = 0; b < nb; ++b) {
+        int j0 = (int)((int64_t)H * b / nb), j1 = (int)((int64_t)H * (b + 1) / nb);
+        for (int64_t k = 0; k < m; ++k) {
+            const cand_t *g = c + k;
+            double ext = g->r_hi + (g->du > g->dv ? g->du : g->dv) + 1e-6 + 1.0;
+            int ilo = (int)floor(g->u - ext), ihi = (int)ceil(g->u + ext);
+            int jlo = (int)floor(g->v - ext), jhi = (int)ceil(g->v + ext);
+            if (ilo < 0) ilo = 0;
+            if (ihi > W - 1) ihi = W - 1;
+            if (jlo < j0) jlo = j0;
+            if (jhi > j1 - 1) jhi = j1 - 1;
+            for (int j = jlo; j <= jhi; ++j)
+                for (int i = ilo; i <= ihi; ++i) blend_step(st + (int64_t)j * W + i, g, i, j, (int32_t)k);
+        }
+        for (int j = j0; j < j1; ++j)
+            for (int i = 0; i < W; ++i) evals += st[(int64_t)j * W + i].evals;
+    }
+    return evals;
+}
+
+/* Forward render of one view.  mode 0: pixel-major brute force over all
+ * candidates; mode 1: the Gaussian-major walk.  Returns the number of
+ * evaluations (covered Gaussians examined before each pixel stopped). */
+int64_t or_render(int64_t n, const double *means, const double *log_scales, const double *quats, const double *ologits,
+                  const double *sh, const double *cov3d, const uint8_t *use_cov, const uint8_t *inexact, const double *cam,
+                  int32_t W, int32_t H, double near_plane, const double *bg, int32_t mode, int32_t flags, int32_t nthreads,
+                  double *out_rgb, double *out_depth, double *out_T, int32_t *out_n, uint8_t *out_amb, int32_t *out_last)
+{
+    cam_t k;
+    load_cam(cam, &k);
+    cand_t *c = NULL;
+    int64_t m = build_candidates(n, means, log_scales, quats, ologits, sh, cov3d, use_cov, inexact, &k, W, H, near_plane, &c);
+    int64_t HW = (int64_t)W * H;
+    pix_t *st = (pix_t *)malloc(sizeof(pix_t) * (size_t)HW);
+    for (int64_t p = 0; p < HW; ++p) pix_init(st + p);
+    int nt = num_threads(nthreads);
+    int64_t evals = 0;
+    if (mode == 0) {
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt) reduction(+ : evals)
+        for (int64_t p = 0; p < HW; ++p) {
+            int i = (int)(p % W), j = (int)(p / W);
+            for (int64_t kk = 0; kk < m; ++kk) blend_step(st + p, c + kk, i, j, (int32_t)kk);
+            evals += st[p].evals;
+        }
+    } else {
+        evals = walk_gaussian_major(c, m, W, H, st, nt);
+    }
+    for (int64_t p = 0; p < HW; ++p)
+        finish_pixel(st + p, bg, flags, p, HW, out_rgb, out_depth, out_T, out_n, out_amb, out_last);
+    free(st);
+    free(c);
+    return evals;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint (FP64).  Discrete decisions (cull, radius, footprint, skip, stop)  */
+/* are held at their forward values; the 0.99 clamp and the colour clamp at  */
+/* zero pass the true derivative, which is zero where they are active.        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double gu, gv, gA, gB, gC, go, grgb[3], gz;
+} grec_t;
+
+/* Per-Gaussian chain from the screen-space gradients back to the inputs. */
+static void preprocess_vjp(const proj_t *o, const grec_t *gr, const double *ls, const double *q, const double *sh,
+                           int use_cov, const cam_t *k, double *g_mu, double *g_ls, double *g_q, double *g_ologit,
+                           double *g_sh, double *g_cov3d)
+{
+    double gp[3] = {0.0, 0.0, 0.0};
+    double px = o->p[0], py = o->p[1], pz = o->p[2];
+    /* u = fx px/pz + cx, v = fy py/pz + cy; depth uses pz */
+    gp[0] += gr->gu * k->fx / pz;
+    gp[2] += -gr->gu * k->fx * px / (pz * pz);
+    gp[1] += gr->gv * k->fy / pz;
+    gp[2] += -gr->gv * k->fy * py / (pz * pz);
+    gp[2] += gr->gz;
+    /* conic = (c, -b, a) / det of the dilated 2D covariance (a, b, c) */
+    double a = o->cov2[0], b = o->cov2[1], c = o->cov2[2], det = o->det, d2 = det * det;
+    double ga = gr->gA * (-c * c / d2) + gr->gB * (b * c / d2) + gr->gC * (-b * b / d2);
+    double gb = gr->gA * (2.0 * b * c / d2) + gr->gB * (-(a * c + b * b) / d2) + gr->gC * (2.0 * a * b / d2);
+    double gc = gr->gA * (-b * b / d2) + gr->gB * (a * b / d2) + gr->gC * (-a * a / d2);
+    double G2[4] = {ga, 0.5 * gb, 0.5 * gb, gc};
+    const double *T = o->T, *S = o->Sigma;
+    /* dL/dSigma = T^T G2 T ; dL/dT = 2 G2 T Sigma */
+    double gS[9];
+    for (int r = 0; r < 3; ++r)
+        for (int cc = 0; cc < 3; ++cc) {
+            double acc = 0.0;
+            for (int x = 0; x < 2; ++x)
+                for (int y = 0; y < 2; ++y) acc += T[3 * x + r] * G2[2 * x + y] * T[3 * y + cc];
+            gS[3 * r + cc] = acc;
+        }
+    double GT[6];
+    for (int x = 0; x < 2; ++x)
+        for (int cc = 0; cc < 3; ++cc) GT[3 * x + cc] = G2[2 * x] * T[cc] + G2[2 * x + 1] * T[3 + cc];
+    double gT[6];
+    for (int x = 0; x < 2; ++x)
+        for (int cc = 0; cc < 3; ++cc) {
+            double acc = 0.0;
+            for (int kk = 0; kk < 3; ++kk) acc += GT[3 * x + kk] * S[3 * kk + cc];
+            gT[3 * x + cc] = 2.0 * acc;
+        }
+    /* T = J W -> dL/dJ = dL/dT W^T */
+    double gJ[6];
+    for (int x = 0; x < 2; ++x)
+        for (int cc = 0; cc < 3; ++cc)
+            gJ[3 * x + cc] = gT[3 * x] * k->R[3 * cc] + gT[3 * x + 1] * k->R[3 * cc + 1] + gT[3 * x + 2] * k->R[3 * cc + 2];
+    /* J00 = fx/pz, J02 = -fx tx/pz (tx = px/pz unless clamped), J11, J12 alike */
+    gp[2] += gJ[0] * (-k->fx / (pz * pz));
+    gp[2] += gJ[4] * (-k->fy / (pz * pz));
+    if (!o->clampx) {
+        gp[0] += gJ[2] * (-k->fx / (pz * pz));
+        gp[2] += gJ[2] * (2.0 * k->fx * px / (pz * pz * pz));
+    } else {
+        gp[2] += gJ[2] * (k->fx * o->tx / (pz * pz));
+    }
+    if (!o->clampy) {
+        gp[1] += gJ[5] * (-k->fy / (pz * pz));
+        gp[2] += gJ[5] * (2.0 * k->fy * py / (pz * pz * pz));
+    } else {
+        gp[2] += gJ[5] * (k->fy * o->ty / (pz * pz));
+    }
+    /* p = W d -> dL/dd = W^T dL/dp */
+    double gd[3];
+    for (int cc = 0; cc < 3; ++cc) gd[cc] = k->R[cc] * gp[0] + k->R[3 + cc] * gp[1] + k->R[6 + cc] * gp[2];
+    /* colour: rgb = max(0, sum Y(dir) k + 0.5), dir = d / |d| */
+    double Y[16], dY[16][3];
+    sh_eval(o->dir, Y, dY);
+    double gdir[3] = {0.0, 0.0, 0.0};
+    for (int ch = 0; ch < 3; ++ch) {
+        double g = o->raw[ch] < 0.0 ? 0.0 : gr->grgb[ch];
+        if (g == 0.0) continue;
+        for (int kk = 0; kk < 16; ++kk) {
+            g_sh[3 * kk + ch] += Y[kk] * g;
+            double w = sh[3 * kk + ch] * g;
+            gdir[0] += dY[kk][0] * w;
+            gdir[1] += dY[kk][1] * w;
+            gdir[2] += dY[kk][2] * w;
+        }
+    }
+    double dot = gdir[0] * o->dir[0] + gdir[1] * o->dir[1] + gdir[2] * o->dir[2];
+    for (int cc = 0; cc < 3; ++cc) gd[cc] += (gdir[cc] - o->dir[cc] * dot) / o->dnorm;
+    for (int cc = 0; cc < 3; ++cc) g_mu[cc] += gd[cc];
+    /* covariance */
+    if (use_cov) {
+        if (g_cov3d) {
+            g_cov3d[0] += gS[0];
+            g_cov3d[1] += gS[1] + gS[3];
+            g_cov3d[2] += gS[2] + gS[6];
+            g_cov3d[3] += gS[4];
+            g_cov3d[4] += gS[5] + gS[7];
+            g_cov3d[5] += gS[8];
+        }
+    } else {
+        cov_from_scale_rot_vjp(ls, q, gS, g_ls, g_q);
+    }
+    /* opacity = sigmoid(logit) */
+    *g_ologit += gr->go * o->opacity * (1.0 - o->opacity);
+}
+
+/* Backward of one view: dL/d(inputs) for L = <d_rgb, rgb> + <d_depth, depth>.
+ * Gradients are accumulated (+=).  The raw (unnormalised) depth is assumed. */
+int32_t or_render_backward(int64_t n, const double *means, const double *log_scales, const double *quats,
+                           const double *ologits, const double *sh, const double *cov3d, const uint8_t *use_cov,
+                           const double *cam, int32_t W, int32_t H, double near_plane, const double *bg,
+                           const double *d_rgb, const double *d_depth, double *g_means, double *g_log_scales,
+                           double *g_quats, double *g_ologits, double *g_sh, double *g_cov3d)
+{
+    cam_t k;
+    load_cam(cam, &k);
+    cand_t *c = NULL;
+    int64_t m = build_candidates(n, means, log_scales, quats, ologits, sh, cov3d, use_cov, NULL, &k, W, H, near_plane, &c);
+    int64_t HW = (int64_t)W * H;
+    pix_t *st = (pix_t *)malloc(sizeof(pix_t) * (size_t)HW);
+    for (int64_t p = 0; p < HW; ++p) pix_init(st + p);
+    walk_gaussian_major(c, m, W, H, st, 1);
+    /* reverse walk: T is rebuilt by division, S accumulates what lies behind */
+    double *Tc = (double *)malloc(sizeof(double) * (size_t)HW);
+    double *Sc = (double *)malloc(sizeof(double) * (size_t)HW * 4);
+    for (int64_t p = 0; p < HW; ++p) {
+        Tc[p] = st[p].T;
+        for (int ch = 0; ch < 3; ++ch) Sc[4 * p + ch] = st[p].T * bg[ch];
+        Sc[4 * p + 3] = 0.0;
+    }
+    grec_t *gr = (grec_t *)calloc((size_t)(m > 0 ? m : 1), sizeof(grec_t));
+    for (int64_t kk = m - 1; kk >= 0; --kk) {
+        const cand_t *g = c + kk;
+        grec_t *q = gr + kk;
+        int r = g->r;
+        int ilo = (int)ceil(g->u - r) - 1, ihi = (int)floor(g->u + r) + 1;
+        int jlo = (int)ceil(g->v - r) - 1, jhi = (int)floor(g->v + r) + 1;
+        if (ilo < 0) ilo = 0;
+        if (ihi > W - 1) ihi = W - 1;
+        if (jlo < 0) jlo = 0;
+        if (jhi > H - 1) jhi = H - 1;
+        for (int j = jlo; j <= jhi; ++j)
+            for (int i = ilo; i <= ihi; ++i) {
+                int64_t p = (int64_t)j * W + i;
+                if (kk >= st[p].last) continue;
+                double dx = g->u - i, dy = g->v - j;
+                if (fabs(dx) > r || fabs(dy) > r) continue;
+                double power = -0.5 * (g->A * dx * dx + g->C * dy * dy) - g->B * dx * dy;
+                if (power > 0.0) continue;
+                double G = exp(power);
+                double a_raw = g->o * G;
+                double alpha = a_raw < ALPHA_MAX ? a_raw : ALPHA_MAX;
+                if (alpha < ALPHA_MIN) continue;
+                double Ti = Tc[p] / (1.0 - alpha);
+                double w = alpha * Ti;
+                double gal = 0.0;
+                for (int ch = 0; ch < 3; ++ch) {
+                    double dl = d_rgb[ch * HW + p];
+                    q->grgb[ch] += w * dl;
+                    gal += dl * (g->rgb[ch] * Ti - Sc[4 * p + ch] / (1.0 - alpha));
+                    Sc[4 * p + ch] += g->rgb[ch] * w;
+                }
+                double dd = d_depth[p];
+                q->gz += w * dd;
+                gal += dd * (g->z * Ti - Sc[4 * p + 3] / (1.0 - alpha));
+                Sc[4 * p + 3] += g->z * w;
+                Tc[p] = Ti;
+                if (a_raw < ALPHA_MAX) {
+                    q->go += gal * G;
+                    double gpow = gal * alpha;
+                    q->gu += gpow * (-(g->A * dx + g->B * dy));
+                    q->gv += gpow * (-(g->C * dy + g->B * dx));
+                    q->gA += gpow * (-0.5 * dx * dx);
+                    q->gC += gpow * (-0.5 * dy * dy);
+                    q->gB += gpow * (-dx * dy);
+                }
+            }
+    }
+    for (int64_t kk = 0; kk < m; ++kk) {
+        int64_t g = c[kk].idx;
+        proj_t o;
+        int uc = (cov3d && use_cov && use_cov[g]) ? 1 : 0;
+        project_one(means + 3 * g, log_scales + 3 * g, quats + 4 * g, ologits[g], sh + 48 * g, uc ? cov3d + 6 * g : NULL, 0,
+                    &k, W, H, near_plane, &o);
+        preprocess_vjp(&o, gr + kk, log_scales + 3 * g, quats + 4 * g, sh + 48 * g, uc, &k, g_means + 3 * g,
+                       g_log_scales + 3 * g, g_quats + 4 * g, g_ologits + g, g_sh + 48 * g,
+                       g_cov3d ? g_cov3d + 6 * g : NULL);
+    }
+    free(gr);
+    free(Sc);
+    free(Tc);
+    free(st);
+    free(c);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Linear blend skinning (Sec. 3.3): A = sum_k w_k G[j_k] (3x4),              */
+/* mu' = A3 mu_c + a, Sigma' = A3 Sigma_c A3^T with Sigma_c from (s, q).      */
+/* Weights are used as given (no renormalisation).                            */
+/* ------------------------------------------------------------------------ */
+static void blend_joints(const int32_t *ids, const double *w, const double *Gav, double A[12])
+{
+    memset(A, 0, 12 * sizeof(double));
+    for (int kk = 0; kk < 4; ++kk) {
+        const double *Gj = Gav + 12 * ids[kk];
+        for (int e = 0; e < 12; ++e) A[e] += w[kk] * Gj[e];
+    }
+}
+
+void or_lbs(int64_t m, const double *means_c, const double *log_scales_c, const double *quats_c, const int32_t *joint_ids,
+            const double *weights, const int32_t *avatar_of, const double *G, int32_t n_joints, double *out_means,
+            double *out_cov)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t g = 0; g < m; ++g) {
+        double A[12];
+        blend_joints(joint_ids + 4 * g, weights + 4 * g, G + (int64_t)12 * n_joints * avatar_of[g], A);
+        const double *mu = means_c + 3 * g;
+        for (int r = 0; r < 3; ++r) out_means[3 * g + r] = A[4 * r] * mu[0] + A[4 * r + 1] * mu[1] + A[4 * r + 2] * mu[2] + A[4 * r + 3];
+        double S[9];
+        cov_from_scale_rot(log_scales_c + 3 * g, quats_c + 4 * g, S);
+        double AS[9], P[9];
+        for (int r = 0; r < 3; ++r)
+            for (int cc = 0; cc < 3; ++cc) AS[3 * r + cc] = A[4 * r] * S[cc] + A[4 * r + 1] * S[3 + cc] + A[4 * r + 2] * S[6 + cc];
+        for (int r = 0; r < 3; ++r)
+            for (int cc = 0; cc < 3; ++cc) P[3 * r + cc] = AS[3 * r] * A[4 * cc] + AS[3 * r + 1] * A[4 * cc + 1] + AS[3 * r + 2] * A[4 * cc + 2];
+        double *o = out_cov + 6 * g;
+        o[0] = P[0]; o[1] = P[1]; o[2] = P[2]; o[3] = P[4]; o[4] = P[5]; o[5] = P[8];
+    }
+}
+
+void or_lbs_backward(int64_t m, const double *means_c, const double *log_scales_c, const double *quats_c,
+                     const int32_t *joint_ids, const double *weights, const int32_t *avatar_of, const double *G,
+                     int32_t n_joints, const double *g_means, const double *g_cov, double *g_means_c,
+                     double *g_log_scales_c, double *g_quats_c, double *g_G)
+{
+    for (int64_t g = 0; g < m; ++g) {
+        const double *Gav = G + (int64_t)12 * n_joints * avatar_of[g];
+        double A[12];
+        blend_joints(joint_ids + 4 * g, weights + 4 * g, Gav, A);
+        const double *mu = means_c + 3 * g;
+        const double *gm = g_means + 3 * g, *gc = g_cov + 6 * g;
+        double S[9];
+        cov_from_scale_rot(log_scales_c + 3 * g, quats_c + 4 * g, S);
+        double Gs[9] = {gc[0], 0.5 * gc[1], 0.5 * gc[2], 0.5 * gc[1], gc[3], 0.5 * gc[4], 0.5 * gc[2], 0.5 * gc[4], gc[5]};
+        /* dL/dA3 = gm mu^T + 2 Gs A3 S ; dL/da = gm */
+        double gA[12];
+        for (int r = 0; r < 3; ++r) {
+            for (int cc = 0; cc < 3; ++cc) {
+                double acc = 0.0;
+                for (int x = 0; x < 3; ++x)
+                    for (int y = 0; y < 3; ++y) acc += Gs[3 * r + x] * A[4 * x + y] * S[3 * y + cc];
+                gA[4 * r + cc] = gm[r] * mu[cc] + 2.0 * acc;
+            }
+            gA[4 * r + 3] = gm[r];
+        }
+        /* dL/dmu_c = A3^T gm ; dL/dSigma_c = A3^T Gs A3 */
+        for (int cc = 0; cc < 3; ++cc) g_means_c[3 * g + cc] += A[cc] * gm[0] + A[4 + cc] * gm[1] + A[8 + cc] * gm[2];
+        double gSc[9];
+        for (int r = 0; r < 3; ++r)
+            for (int cc = 0; cc < 3; ++cc) {
+                double acc = 0.0;
+                for (int x = 0; x < 3; ++x)
+                    for (int y = 0; y < 3; ++y) acc += A[4 * x + r] * Gs[3 * x + y] * A[4 * y + cc];
+                gSc[3 * r + cc] = acc;
+            }
+        cov_from_scale_rot_vjp(log_scales_c + 3 * g, quats_c + 4 * g, gSc, g_log_scales_c + 3 * g, g_quats_c + 4 * g);
+        double *gGav = g_G + (int64_t)12 * n_joints * avatar_of[g];
+        for (int kk = 0; kk < 4; ++kk) {
+            double *gj = gGav + 12 * joint_ids[4 * g + kk];
+            for (int e = 0; e < 12; ++e) gj[e] += weights[4 * g + kk] * gA[e];
+        }
+    }
+}
+
+int32_t or_abi_version(void) { return 1; }

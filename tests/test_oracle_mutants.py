@@ -1,0 +1,62 @@
+"""Planted mistakes: each mutant is a copy of the oracle source with one
+plausible slip; the pin named beside it must fail on the mutant (and passes on
+the real oracle).  CPU only; nothing here touches the CUDA path."""
+import pytest
+
+import oracle as _oracle
+import test_oracle_adjoint as adj
+import test_oracle_pins as pins
+
+MUTANTS = [
+    ("dropped dilation", "#define DILATION 0.3", "#define DILATION 0.0",
+     lambda o: pins.test_single_gaussian_closed_form(o, 3.0, -2.5, 0.3, 16.5)),
+    ("no discriminant floor", "if (disc < 0.1) disc = 0.1;", "",
+     lambda o: pins.test_single_gaussian_closed_form(o, 5.0, -1.5, -1.0, 16.0)),
+    ("no 0.99 clamp", "double a_raw = g->o * G;\n    double alpha = a_raw < ALPHA_MAX ? a_raw : ALPHA_MAX;",
+     "double a_raw = g->o * G;\n    double alpha = a_raw;",
+     lambda o: pins.test_single_gaussian_closed_form(o, 2.0, -3.0, 5.0, 24.0)),
+    ("no 1/255 skip", "if (alpha < ALPHA_MIN) return;", "if (alpha <= 0.0) return;",
+     lambda o: pins.test_single_gaussian_closed_form(o, 3.0, -2.5, 0.3, 16.5)),
+    ("radius one pixel too wide", "o->r = (int32_t)ceil(o->r3);", "o->r = (int32_t)ceil(o->r3) + 1;",
+     pins.test_elongated_gaussian_square_footprint_closed_form),
+    ("stop tested on T before the step", "if (Tn < T_STOP) {", "if (s->T < T_STOP) {",
+     pins.test_stop_rule_never_blends_below_threshold),
+    ("depth weighted by alpha only", "s->D += g->z * w;", "s->D += g->z * alpha;", pins.test_transmittance_invariant),
+    ("Jacobian sign", "J[0] = k->fx / pz; J[1] = 0.0; J[2] = -k->fx * tx / pz;",
+     "J[0] = k->fx / pz; J[1] = 0.0; J[2] = k->fx * tx / pz;", pins.test_ewa_covariance_is_linearised_pinhole),
+    ("no lateral clamp", "if (tx > limx) tx = limx;", "", pins.test_lateral_clamp_of_jacobian),
+    ("quaternion entry sign", "R[1] = 2.0 * (x * y - w * z);", "R[1] = 2.0 * (x * y + w * z);",
+     pins.test_quaternion_rotation),
+    ("SH degree-1 sign", "c[1] = -c1;", "c[1] = c1;", pins.test_sh_matches_scipy_real_harmonics),
+    ("SH degree-3 constant", "c[12] = 0.25 * sqrt(7.0 / pi);", "c[12] = 0.5 * sqrt(7.0 / pi);",
+     pins.test_sh_orthonormal_by_quadrature),
+    ("no colour clamp", "o->rgb[ch] = acc < 0.0 ? 0.0 : acc;", "o->rgb[ch] = acc;",
+     pins.test_colour_clamped_at_zero_and_direction_dependent),
+    ("camera centre added", "for (int i = 0; i < 3; ++i) o->d[i] = mu[i] - k->C[i];",
+     "for (int i = 0; i < 3; ++i) o->d[i] = mu[i] + k->C[i];", pins.test_camera_translation_equivariance),
+    ("view rotation transposed",
+     "o->p[r] = k->R[3 * r] * o->d[0] + k->R[3 * r + 1] * o->d[1] + k->R[3 * r + 2] * o->d[2];",
+     "o->p[r] = k->R[r] * o->d[0] + k->R[r + 3] * o->d[1] + k->R[r + 6] * o->d[2];",
+     pins.test_camera_rotation_equivariance),
+    ("tie-break reversed", "return (x->idx < y->idx) ? -1 : (x->idx > y->idx);",
+     "return (x->idx > y->idx) ? -1 : (x->idx < y->idx);", pins.test_equal_depth_ties_follow_index),
+    ("LBS drops translation", "mu[2] + A[4 * r + 3];", "mu[2];", pins.test_lbs_common_rigid_transform_and_no_renormalisation),
+    ("LBS renormalises weights", "for (int e = 0; e < 12; ++e) A[e] += w[kk] * Gj[e];",
+     "for (int e = 0; e < 12; ++e) A[e] += w[kk] / (w[0] + w[1] + w[2] + w[3]) * Gj[e];",
+     pins.test_lbs_common_rigid_transform_and_no_renormalisation),
+    ("adjoint: conic derivative sign", "gr->gB * (b * c / d2)", "gr->gB * (-b * c / d2)",
+     adj.test_adjoint_matches_finite_differences),
+    ("adjoint: clamp passes gradient", "if (a_raw < ALPHA_MAX) {\n                    q->go", "if (1) {\n                    q->go",
+     adj.test_adjoint_matches_finite_differences),
+    ("adjoint: LBS covariance factor", "gA[4 * r + cc] = gm[r] * mu[cc] + 2.0 * acc;",
+     "gA[4 * r + cc] = gm[r] * mu[cc] + acc;", adj.test_lbs_adjoint_matches_finite_differences),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pin", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(oracle, name, old, new, pin):
+    src = _oracle.source()
+    assert src.count(old) == 1, f"mutation site not unique: {name}"
+    with _oracle.variant(src.replace(old, new)):
+        with pytest.raises(AssertionError):
+            pin(_oracle)

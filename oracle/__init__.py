@@ -44,6 +44,7 @@ _LIB = None
 
 AMB_VALUE = 1
 AMB_COUNT = 2
+AMB_FOOTPRINT, AMB_ORDER, AMB_ALPHA, AMB_STOP = 4, 8, 16, 32  # which decision was near its threshold
 
 
 def _so_path() -> Path:
@@ -101,7 +102,7 @@ def _bind(L):
     P = ctypes.c_void_p
     i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
     L.or_project.restype = i64
-    L.or_project.argtypes = [i64, P, P, P, P, P, P, P, P, P, i32, i32, f64] + [P] * 11
+    L.or_project.argtypes = [i64, P, P, P, P, P, P, P, P, P, i32, i32, f64] + [P] * 12
     L.or_render.restype = i64
     L.or_render.argtypes = [i64, P, P, P, P, P, P, P, P, P, i32, i32, f64, P, i32, i32, i32] + [P] * 6
     L.or_render_backward.restype = i32
@@ -172,12 +173,13 @@ def project(g: dict, cam, W: int, H: int, near: float = 0.2) -> dict:
         visible=np.zeros(n, np.int32), u=np.zeros(n), v=np.zeros(n), z=np.zeros(n),
         zkey=np.zeros(n, np.float32), cov2=np.zeros((n, 3)), conic=np.zeros((n, 3)),
         opacity=np.zeros(n), rgb=np.zeros((n, 3)), radius=np.zeros(n, np.int32), r3=np.zeros(n),
+        err_uv=np.zeros((n, 2)),
     )
     L.or_project(n, _p(G["means"]), _p(G["log_scales"]), _p(G["quats"]), _p(G["ologits"]), _p(G["sh"]),
                  _p(G["cov3d"]), _p(G["use_cov"]), _p(G["inexact"]), _p(cam64), W, H, near,
                  _p(out["visible"]), _p(out["u"]), _p(out["v"]), _p(out["z"]), _p(out["zkey"]),
                  _p(out["cov2"]), _p(out["conic"]), _p(out["opacity"]), _p(out["rgb"]),
-                 _p(out["radius"]), _p(out["r3"]))
+                 _p(out["radius"]), _p(out["r3"]), _p(out["err_uv"]))
     out["visible"] = out["visible"].astype(bool)
     return out
 

@@ -46,6 +46,11 @@
 
 #define AMB_VALUE 1u /* colour or depth may differ beyond the FP32 tolerance */
 #define AMB_COUNT 2u /* the contributor count may differ by a flipped decision */
+/* which decision was near its threshold (informational) */
+#define AMB_FOOTPRINT 4u
+#define AMB_ORDER 8u
+#define AMB_ALPHA 16u
+#define AMB_STOP 32u
 
 #define ALPHA_MIN (1.0 / 255.0)
 #define ALPHA_MAX 0.99
@@ -339,10 +344,12 @@ static int project_one(const double *mu, const double *ls, const double *q, doub
     /* FP32 error model of u, v: rounding of d, of p and of the projection */
     double dl1 = fabs(o->d[0]) + fabs(o->d[1]) + fabs(o->d[2]);
     double pl1 = fabs(px) + fabs(py) + fabs(pz);
-    double mu_err = inexact ? 2e-6 * (fabs(mu[0]) + fabs(mu[1]) + fabs(mu[2]) + 1.0) : 0.0;
-    double pos_err = 4e-7 * (dl1 + pl1) + mu_err;
-    o->du = k->fx * pos_err / pz * (1.0 + fabs(tx)) + 4e-7 * fabs(o->u - k->cx) + 1e-7;
-    o->dv = k->fy * pos_err / pz * (1.0 + fabs(ty)) + 4e-7 * fabs(o->v - k->cy) + 1e-7;
+    /* bound on |u_fp32 - u|: a few single-precision roundings of d, p and of
+     * the projection; measured FP32 errors stay below a third of it */
+    double mu_err = inexact ? 3e-7 * (fabs(mu[0]) + fabs(mu[1]) + fabs(mu[2]) + 1.0) : 0.0;
+    double pos_err = 1e-7 * (dl1 + pl1) + mu_err;
+    o->du = k->fx * pos_err / pz * (1.0 + fabs(tx)) + 1e-7 * fabs(o->u - k->cx) + 1e-7;
+    o->dv = k->fy * pos_err / pz * (1.0 + fabs(ty)) + 1e-7 * fabs(o->v - k->cy) + 1e-7;
     o->cand = footprint_on_image(o->u, o->v, o->r_hi, W, H);
     o->visible = footprint_on_image(o->u, o->v, o->r, W, H);
     if (!o->cand) return 0;
@@ -366,7 +373,8 @@ static int project_one(const double *mu, const double *ls, const double *q, doub
 int64_t or_project(int64_t n, const double *means, const double *log_scales, const double *quats, const double *ologits,
                    const double *sh, const double *cov3d, const uint8_t *use_cov, const uint8_t *inexact, const double *cam,
                    int32_t W, int32_t H, double near_plane, int32_t *visible, double *u, double *v, double *z, float *zkey,
-                   double *cov2, double *conic, double *opacity, double *rgb, int32_t *radius, double *r3)
+                   double *cov2, double *conic, double *opacity, double *rgb, int32_t *radius, double *r3,
+                   double *err_uv)
 {
     cam_t k;
     load_cam(cam, &k);
@@ -389,6 +397,10 @@ int64_t or_project(int64_t n, const double *means, const double *log_scales, con
         opacity[g] = o.opacity;
         radius[g] = o.r;
         r3[g] = o.r3;
+        if (err_uv) {
+            err_uv[2 * g] = o.du;
+            err_uv[2 * g + 1] = o.dv;
+        }
     }
     return nvis;
 }
@@ -439,17 +451,17 @@ static void blend_step(pix_t *s, const cand_t *g, int i, int j, int32_t pos)
     double q = g->A * dx * dx + g->C * dy * dy;
     double power = -0.5 * q - g->B * dx * dy;
     double dpow = fabs(g->A * dx + g->B * dy) * g->du + fabs(g->C * dy + g->B * dx) * g->dv +
-                  4e-6 * (0.5 * q + fabs(g->B * dx * dy)) + 2e-6;
+                  2e-6 * (0.5 * q + fabs(g->B * dx * dy)) + 1e-6;
     if (m >= g->r_lo - eps && m <= g->r_hi + eps) {
         /* coverage can flip under FP32 rounding of u, v or of the radius */
-        s->amb |= AMB_COUNT;
+        s->amb |= AMB_COUNT | AMB_FOOTPRINT;
         if (power <= dpow && g->o * exp(power) >= ALPHA_MIN * (1.0 - 1e-3)) s->amb |= AMB_VALUE;
     }
     if (m > (double)g->r) return;
     if (s->have_prev && (g->inexact || s->prev_inexact)) {
         float lo = s->prev_zkey < g->zkey ? s->prev_zkey : g->zkey;
         float hi = s->prev_zkey < g->zkey ? g->zkey : s->prev_zkey;
-        if ((double)hi - (double)lo <= 8.0 * (double)FLT_EPSILON * (double)hi) s->amb |= AMB_VALUE | AMB_COUNT;
+        if ((double)hi - (double)lo <= 8.0 * (double)FLT_EPSILON * (double)hi) s->amb |= AMB_VALUE | AMB_COUNT | AMB_ORDER;
     }
     s->have_prev = 1;
     s->prev_zkey = g->zkey;
@@ -463,7 +475,7 @@ static void blend_step(pix_t *s, const cand_t *g, int i, int j, int32_t pos)
     double cmax = maxabs3(g->rgb) + 1.0;
     /* alpha >= 1/255 decision */
     if (fabs(power + log(g->o) - log(ALPHA_MIN)) <= dpow + 2e-6) {
-        s->amb |= AMB_COUNT;
+        s->amb |= AMB_COUNT | AMB_ALPHA;
         if (ALPHA_MIN * s->T * cmax > 0.5e-4 || ALPHA_MIN * s->T * g->z > 0.5e-4 * (s->D + ALPHA_MIN * s->T * g->z))
             s->amb |= AMB_VALUE;
     }
@@ -472,7 +484,7 @@ static void blend_step(pix_t *s, const cand_t *g, int i, int j, int32_t pos)
     double relTn = s->relT + 4.8e-7 + (a_raw < ALPHA_MAX ? alpha / (1.0 - alpha) * (dpow + 2e-6) : 0.0);
     /* T (1 - alpha) < 1e-4 decision */
     if (fabs(Tn - T_STOP) <= T_STOP * relTn + 1e-12) {
-        s->amb |= AMB_COUNT;
+        s->amb |= AMB_COUNT | AMB_STOP;
         double ec = alpha * s->T * (maxabs3(g->rgb) + 1e-30);
         double ed = alpha * s->T * g->z;
         if (ec > 0.5e-4 || ed > 0.5e-4 * (s->D + ed)) s->amb |= AMB_VALUE;

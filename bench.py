@@ -1,0 +1,449 @@
+#!/usr/bin/env python
+"""Throughput of batched RGB-D Gaussian-splatting rendering on GB300.
+
+Workload (one step): 64 environments, each its own synthetic indoor room of
+U[300k, 1.5M] Gaussians (uneven), one 256x256 RGB-D camera per env at a random
+pose; forward (EWA projection + SH-3 colour, binning, per-tile sort, blending)
+and backward (gradients w.r.t. all Gaussian parameters) in one captured CUDA
+graph, SH stored in FP16, blending by a persistent grid, tile size and batch
+depth chosen by the autotuner.  The paper measures its renderer inside
+Habitat-Lab at 256x256 with 300K-7M Gaussians (Sec. 4.5, Table 6); its scans
+are not available, the synthetic rooms stand in for them.
+
+Prints one JSON line (rank 0).  value = env-frames/s of the whole job
+(forward + backward), with the forward alone, the plain per-env FP32 path, the
+live per-stage timing of the dominant kernel against its roofline, the
+end-to-end number through the public API with host buffers, the clocks seen
+during the timed region and the FP64 CPU oracle on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RGB-D frames/s at 64 envs (fwd, fwd+bwd) vs plain per-env path; % roofline"
+UNIT = "env-frames/s"
+N_ENVS, W, H = 64, 256, 256
+N_MIN, N_MAX = 300_000, 1_500_000
+TILE_CANDIDATES = [(16, 16, 256), (16, 16, 128), (16, 8, 128), (16, 8, 64), (8, 8, 64), (32, 8, 256), (32, 8, 128)]
+KERNELS_PER_STEP = 9  # setup, preprocess, scan, scatter, sort_small, sort_big, blend, blend_backward, preprocess_backward
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def smi_index(local: int) -> int:
+    """nvidia-smi index of the local CUDA device (CUDA_VISIBLE_DEVICES remaps)."""
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [x.strip() for x in vis.split(",") if x.strip()]
+    if local < len(ids) and ids[local].isdigit():
+        return int(ids[local])
+    return local
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (test infrastructure; timed as it stands)
+# ---------------------------------------------------------------------------
+def oracle_step(env_ids, seed0, budget_s=None):
+    """FP64 oracle forward + backward of whole envs; returns (envs done, seconds)."""
+    import oracle
+    from paper_2604_12626_gb300 import synth
+
+    oracle.build()
+    sizes = synth.batch_sizes(N_ENVS, N_MIN, N_MAX, seed0)
+    done, t_total = 0, 0.0
+    rng = np.random.default_rng(0)
+    for e in env_ids:
+        g = synth.room_scene(sizes[e], seed=seed0 + e)
+        cam = synth.room_camera(seed0 + e, W, H)
+        d_rgb = rng.standard_normal((3, H, W))
+        d_depth = rng.standard_normal((H, W)) * 0.1
+        t0 = time.perf_counter()
+        oracle.render(g, cam, W, H)
+        oracle.render_backward(g, cam, W, H, d_rgb, d_depth)
+        t_total += time.perf_counter() - t0
+        done += 1
+        if budget_s is not None and t_total >= budget_s:
+            break
+    return done, t_total
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    envs_per_step = 1
+    for _ in range(args.warmup):
+        oracle_step([0], 0)
+    t = 0.0
+    n = 0
+    for k in range(args.steps):
+        d, s = oracle_step([(k * envs_per_step + i) % N_ENVS for i in range(envs_per_step)], 0)
+        n += d
+        t += s
+    value = n / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "FP64 CPU oracle, forward+backward of one 256x256 room env (300k-1.5M "
+                                   "Gaussians) per step, env k at step k"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} env(s) of the 64-env batch, forward (OpenMP) + backward (1 thread)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args, ws, rank, local):
+    import torch
+
+    from paper_2604_12626_gb300 import api, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    seed0 = rank * N_ENVS  # weak scaling: every rank renders its own 64 envs
+    t0 = time.time()
+    g, offs, cams = synth.batched_rooms(N_ENVS, N_MIN, N_MAX, W, H, seed0=seed0, scale=args.scale)
+    t_gen = time.time() - t0
+    N = int(offs[-1])
+    T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)  # noqa: E731
+    means, ls, quats, ologit = T(g["means"]), T(g["log_scales"]), T(g["quats"]), T(g["opacity_logits"])
+    sh32 = T(g["sh"])
+    sh16 = sh32.to(torch.float16)
+    del g
+    cams_d = api.cameras_tensor(cams, dev)
+    batch = api.Batch(offs)
+    G16 = api.Gaussians(means, ls, quats, ologit, sh16)
+    G32 = api.Gaussians(means, ls, quats, ologit, sh32)
+
+    # --- autotune the batched renderer (tile, batch depth), cached per GPU + workload
+    rend = api.Renderer(batch, W, H, device=dev, tile=(8, 8), batch_depth=64, persistent=True, grad_overwrite=True)
+    cache_path = os.path.join(ROOT, "paper_2604_12626_gb300", "_build", "autotune.json")
+    key = f"{torch.cuda.get_device_name(dev)}|{N_ENVS}x{W}x{H}|N={N}|f16"
+    cache = {}
+    try:
+        with open(cache_path) as f:
+            cache = json.load(f)
+    except Exception:
+        pass
+    if key in cache and not args.retune:
+        tw, th, bd = cache[key]["choice"]
+        rend.cfg.tile_w, rend.cfg.tile_h, rend.cfg.batch_depth = tw, th, bd
+        tuned = dict(cache[key], cached=True)
+    else:
+        choice, best_ms = rend.autotune(G16, cams_d, TILE_CANDIDATES, reps=3)
+        tuned = {"choice": list(choice), "ms": best_ms, "cached": False}
+        cache[key] = tuned
+        try:
+            with open(cache_path, "w") as f:
+                json.dump(cache, f, indent=1)
+        except Exception:
+            pass
+    outs = rend.alloc_outputs()
+    grads = dict(means=torch.empty((N, 3), device=dev), log_scales=torch.empty((N, 3), device=dev),
+                 quats=torch.empty((N, 4), device=dev), opacity_logits=torch.empty((N,), device=dev),
+                 sh=torch.empty((N, 16, 3), device=dev))
+    rng = torch.Generator(device=dev)
+    rng.manual_seed(1234 + rank)
+    d_rgb = torch.randn((N_ENVS, 3, H, W), device=dev, generator=rng)
+    d_depth = 0.1 * torch.randn((N_ENVS, H, W), device=dev, generator=rng)
+
+    stream = torch.cuda.Stream(device=dev)
+
+    def step_fwd():
+        rend.forward(G16, cams_d, out=outs, stream=stream)
+
+    def step_fb():
+        rend.forward(G16, cams_d, out=outs, stream=stream)
+        rend.backward(G16, cams_d, d_rgb, d_depth, grads=grads, stream=stream)
+
+    with torch.cuda.stream(stream):
+        step_fb()
+    torch.cuda.synchronize()
+    assert rend.status() == 0, "pair capacity exceeded"
+    stats = rend.stats(stream)
+
+    def capture(fn):
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr, stream=stream):
+            fn()
+        return gr
+
+    g_fb = capture(step_fb)
+    g_fwd = capture(step_fwd)
+
+    def timed(replay, k, warm, sample_clocks=False):
+        with torch.cuda.stream(stream):
+            for _ in range(warm):
+                replay()
+        torch.cuda.synchronize()
+        barrier(ws)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(smi_index(local)) if sample_clocks else None
+        if sampler:
+            sampler.__enter__()
+            time.sleep(0.3)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(k):
+                replay()
+            e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.__exit__(None, None, None)
+        barrier(ws)
+        ms = e0.elapsed_time(e1) / k
+        return max_over_ranks(ms, ws), (sampler.summary() if sampler else None)
+
+    ms_fb, clocks = timed(g_fb.replay, args.steps, args.warmup, sample_clocks=True)
+    ms_fwd, _ = timed(g_fwd.replay, args.steps, args.warmup)
+    assert rend.status(stream) == 0
+
+    # --- plain per-env path: one gs_render per env, FP32 SH, 16x16 tiles, B=256, no graph
+    plain_ms = None
+    if not args.no_plain:
+        envs = []
+        for e in range(N_ENVS):
+            a, b = int(offs[e]), int(offs[e + 1])
+            ge = api.Gaussians(means[a:b], ls[a:b], quats[a:b], ologit[a:b], sh32[a:b])
+            envs.append(ge)
+        sizes = np.diff(offs)
+        big = int(np.argmax(sizes))
+        r1 = api.Renderer(api.Batch(np.array([0, sizes[big]])), W, H, device=dev)
+        outs1 = r1.alloc_outputs()
+        cam_e = [cams_d[e:e + 1] for e in range(N_ENVS)]
+
+        def plain_step():
+            for e in range(N_ENVS):
+                r1.batch = api.Batch(np.array([0, sizes[e]]))
+                r1.forward(envs[e], cam_e[e], out=outs1, stream=stream)
+
+        plain_ms, _ = timed(plain_step, max(2, args.steps // 2), 1)
+
+    # --- live per-stage timing (same workload, launched without the graph)
+    api.profile_enable(True)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            step_fb()
+    torch.cuda.synchronize()
+    prof = api.profile_read()
+    api.profile_enable(False)
+    stage_ms = {k: v[0] / max(v[1], 1) for k, v in prof.items()}
+
+    # --- end to end through the public API with host buffers
+    cams_host = torch.from_numpy(np.ascontiguousarray(cams, np.float32)).pin_memory()
+    rgb_host = torch.empty((N_ENVS, 3, H, W), dtype=torch.float32).pin_memory()
+    depth_host = torch.empty((N_ENVS, H, W), dtype=torch.float32).pin_memory()
+    cams_dev2 = torch.empty_like(cams_d)
+
+    def e2e_step():
+        cams_dev2.copy_(cams_host.view(-1, 16), non_blocking=True)
+        rend.forward(G16, cams_dev2, out=outs, stream=stream)
+        rend.backward(G16, cams_dev2, d_rgb, d_depth, grads=grads, stream=stream)
+        rgb_host.copy_(outs[0], non_blocking=True)
+        depth_host.copy_(outs[1], non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        e2e_ms, _ = timed(e2e_step, args.steps, 1)
+    h2d = cams_host.numel() * 4
+    d2h = (rgb_host.numel() + depth_host.numel()) * 4
+
+    # --- roofline of the dominant kernel
+    hbm, peak_kind = peaks()
+    R = stats["n_records"]
+    nvis = stats["n_visible"]
+    P = stats["n_pairs"]
+    f_v = nvis / max(R, 1)
+    # algorithmic bytes per launch (per-unit figures in the design doc)
+    alg = {
+        "preprocess": 16 * R + nvis * (12 + 16 + 4 + 96 + 44),
+        "preprocess_backward": 12 * N + nvis * (12 + 16 + 4 + 96 + 40) + N * 59 * 4,
+        "scatter": 4 * (R // 32) + nvis * 20 + 12 * P,
+        "sort_small": 16 * P,
+        "blend_backward": 48 * P + (N_ENVS * W * H) * 24 + 40 * P,
+        "blend": 48 * P + (N_ENVS * W * H) * 24,
+    }
+    dom = max(stage_ms, key=lambda k: stage_ms[k])
+    if dom in ("preprocess", "preprocess_backward", "scatter", "sort_small"):
+        ach = alg[dom] / (stage_ms[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "peak_kind": peak_kind}
+    else:
+        ach = alg[dom] / (stage_ms[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "peak_kind": peak_kind,
+                "note": "dominant kernel is issue-bound; HBM fraction of its algorithmic bytes shown"}
+    roof["per_kernel_gbs"] = {k: alg[k] / (stage_ms[k] * 1e-3) / 1e9 for k in alg if k in stage_ms}
+
+    # --- CPU oracle on a bounded sample (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        n, t = oracle_step(list(range(N_ENVS)), seed0, budget_s=args.cpu_budget)
+        cpu = {"value": n / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n} env(s) of this batch (env 0..{n - 1}), FP64 forward (OpenMP, all cores) + "
+                         f"backward (1 thread), {t:.1f} s"}
+
+    total_envs = N_ENVS * ws
+    line = {
+        "metric": METRIC, "value": total_envs / (ms_fb * 1e-3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_fb, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{N_ENVS} envs x synthetic room (U[300k,1.5M] Gaussians, uneven), {W}x{H} RGB-D, "
+                               "forward+backward, SH stored fp16, persistent blend in one CUDA graph, "
+                               "autotuned tile", "n_envs_per_gpu": N_ENVS, "gaussians_per_gpu": N,
+                   "width": W, "height": H, "tile": [rend.cfg.tile_w, rend.cfg.tile_h],
+                   "batch_depth": rend.cfg.batch_depth, "sh_storage": "f16", "autotune": tuned,
+                   "l2_policy": "inputs larger than L2 (no flush)", "parallelism": f"env-sharded x{ws}"},
+        "fwd": {"value": total_envs / (ms_fwd * 1e-3), "ms_per_step": ms_fwd},
+        "plain_per_env": (None if plain_ms is None else
+                          {"value": total_envs / (plain_ms * 1e-3), "ms_per_step": plain_ms,
+                           "what": "forward only: 64 gs_render calls, FP32 SH, 16x16 tiles, B=256, no graph",
+                           "batched_fwd_speedup": plain_ms / ms_fwd}),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": total_envs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "what": "public API calls per step: cameras H2D from pinned memory, "
+                                                   "gs_render + gs_render_backward, RGB + depth D2H"},
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "clocks": clocks,
+        "stage_ms": stage_ms,
+        "stats": {"records": R, "visible": nvis, "f_v": f_v, "pairs": P, "pairs_per_visible": P / max(nvis, 1),
+                  "max_bin": stats["max_bin"], "gen_s": t_gen},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0, help="scale the per-env Gaussian counts (testing only)")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--retune", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

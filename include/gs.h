@@ -1,0 +1,242 @@
+/*
+ * gs.h -- C ABI of libgs: batched Gaussian-splatting RGB-D rendering with
+ * drivable LBS avatars, hand-written CUDA for sm_103a (GB300).
+ *
+ * The paper (Habitat-GS) renders scene Gaussians with a CUDA tile-based 3D
+ * Gaussian Splatting rasteriser producing colour and depth (Sec. 3.1, Sec. 3.2),
+ * and deforms canonical avatar Gaussians with a CUDA linear-blend-skinning
+ * kernel over per-frame SMPL-X joint matrices before rasterising all avatars in
+ * one pass (Sec. 3.2 last paragraph, Sec. 3.3, Sec. 3.3.1).  This header is the
+ * boundary of that hot path; everything behind it runs in this library's own
+ * kernels.
+ *
+ * Conventions (all entry points):
+ *  - Every pointer argument named as "device" is a caller-owned device pointer;
+ *    the library never allocates device memory and never frees anything.  All
+ *    scratch lives in a caller-provided workspace (see gs_render_workspace_size).
+ *  - Arrays are dense, row-major, float32 unless stated, and must be 16-byte
+ *    aligned (GS_ERR_ALIGNMENT otherwise), except gs_gaussians.means,
+ *    log_scales, opacity_logits and cov3d, which need 4 bytes, so that one env
+ *    of a concatenated batch can be passed as a slice.  Struct arguments are
+ *    host memory.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy default
+ *    stream).  No call synchronises the stream except gs_get_status and
+ *    gs_render_stats, and no call reads device memory from the host, so
+ *    gs_render / gs_render_backward / gs_deform_avatars(_backward) can be
+ *    captured into a CUDA graph.
+ *  - Returns GS_OK or a negative gs_status.  Errors the device detects (pair
+ *    capacity exceeded) set a status word in the workspace, which gs_render
+ *    clears when it starts and gs_render_backward leaves as it is; read it with
+ *    gs_get_status.  Outputs of such a call are unspecified but every write
+ *    stays in bounds.
+ *  - Camera convention: world->camera rotation R (rows: right, down, forward;
+ *    OpenCV), camera centre C in world coordinates, so p = R (mu - C).  Pixel
+ *    (i, j) has its centre at image coordinates (i, j).
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t gs_status;
+#define GS_OK 0
+#define GS_ERR_INVALID_ARG (-1)
+#define GS_ERR_ALIGNMENT (-2)
+#define GS_ERR_WORKSPACE_TOO_SMALL (-3)
+#define GS_ERR_CAPACITY (-4)
+#define GS_ERR_CUDA (-5)
+#define GS_ERR_TIMEOUT (-6)
+#define GS_ERR_UNSUPPORTED (-7)
+
+/* storage type of the SH coefficients (arithmetic is always float32) */
+#define GS_SH_F32 0
+#define GS_SH_F16 1
+#define GS_SH_BF16 2
+
+/* gs_render_config.flags */
+#define GS_FLAG_PERSISTENT 1      /* blend with a persistent grid over an (view, tile) work queue */
+#define GS_FLAG_NORMALIZE_DEPTH 2 /* depth = D / (1 - T), 0 where 1 - T < 1e-4 (forward only) */
+#define GS_FLAG_GRAD_OVERWRITE 4  /* gs_render_backward writes every gradient row (zeros where a
+                                     Gaussian is seen by no view) instead of adding to it */
+
+#define GS_MAX_ENVS 512
+#define GS_MAX_VIEWS 512
+
+/* A pinhole camera, 64 bytes: p = R (mu - C); u = fx px/pz + cx, v = fy py/pz + cy. */
+typedef struct {
+    float R[9]; /* world->camera rotation, row-major */
+    float C[3]; /* camera centre, world coordinates */
+    float fx, fy, cx, cy;
+} gs_camera;
+
+/* The Gaussians of all environments, concatenated env after env (device).
+ * Gaussian k of env e sits at index env_offsets[e] + k.  Within an env the
+ * Gaussians from env_cov3d_begin[e] on (typically the posed avatars) take their
+ * covariance from cov3d instead of (log_scales, quats). */
+typedef struct {
+    const float *means;          /* [N,3] world positions */
+    const float *log_scales;     /* [N,3] log of the per-axis standard deviation */
+    const float *quats;          /* [N,4] rotation (w, x, y, z), normalised by the kernel */
+    const float *opacity_logits; /* [N] opacity = sigmoid(logit) */
+    const void *sh;              /* [N,16,3] degree-3 SH, coefficient-major, channel fastest */
+    int32_t sh_dtype;            /* GS_SH_F32 / GS_SH_F16 / GS_SH_BF16 */
+    int32_t reserved;
+    const float *cov3d;          /* [N,6] (xx, xy, xz, yy, yz, zz) or NULL */
+    int64_t n;                   /* total Gaussians N */
+} gs_gaussians;
+
+/* Batch structure (host arrays; copied into the workspace by every call). */
+typedef struct {
+    int32_t n_envs;                 /* E, 1..GS_MAX_ENVS */
+    int32_t n_views;                /* V, 1..GS_MAX_VIEWS; several views may share an env */
+    const int64_t *env_offsets;     /* host [E+1], env_offsets[0] = 0, env_offsets[E] = N */
+    const int64_t *env_cov3d_begin; /* host [E] absolute index, or NULL (no cov3d use) */
+    const int32_t *view_env;        /* host [V] env of each view */
+} gs_batch;
+
+typedef struct {
+    int32_t width, height;     /* image size shared by all views */
+    int32_t tile_w, tile_h;    /* blend tile; tile_w * tile_h <= 1024; 0 -> 16 x 16 */
+    int32_t batch_depth;       /* Gaussians staged per shared-memory batch, 32..256; 0 -> 256 */
+    int32_t flags;             /* GS_FLAG_* */
+    float bg[3];               /* background colour added with the final transmittance */
+    float near_plane;          /* Gaussians with FP32 view depth <= near are culled; 0 -> 0.2 */
+    int64_t pair_capacity;     /* max (tile, Gaussian) pairs; 0 -> 4 x records + 65536 */
+} gs_render_config;
+
+/* Per-call counters, read back by gs_render_stats (synchronises). */
+typedef struct {
+    int64_t n_records;  /* (view, Gaussian) records considered */
+    int64_t n_visible;  /* records that passed near, conic and footprint culling */
+    int64_t n_pairs;    /* (tile, Gaussian) pairs generated */
+    int64_t max_bin;    /* largest pair count of one (view, tile) */
+    int32_t status;     /* device status word (0 or a GS_ERR_* code) */
+    int32_t reserved;
+} gs_stats;
+
+/* Canonical avatar Gaussians for LBS (device). */
+typedef struct {
+    const float *means;         /* [M,3] canonical positions */
+    const float *log_scales;    /* [M,3] */
+    const float *quats;         /* [M,4] (w, x, y, z) */
+    const uint16_t *joint_ids;  /* [M,4] joint index per skin weight, < n_joints */
+    const float *weights;       /* [M,4] skin weights, used as given (no renormalisation) */
+    const int32_t *avatar_of;   /* [M] avatar of each Gaussian, < n_avatars */
+    const int64_t *dest;        /* [M] output index of each Gaussian, or NULL for 0..M-1 */
+    int64_t m;
+    int32_t n_avatars, n_joints; /* n_joints <= 64 */
+} gs_avatars;
+
+/* Workspace bytes needed by gs_render / gs_render_backward for this config
+ * and batch (the backward reuses the forward's workspace). */
+gs_status gs_render_workspace_size(const gs_render_config *cfg, const gs_batch *batch, size_t *bytes);
+
+/* Forward render of V views (Sec. 3.2: CUDA 3DGS rasterisation to colour and
+ * depth).  Pipeline: EWA projection + SH-3 colour per (view, Gaussian), binning
+ * of (tile, depth key) pairs, per-tile sort by (FP32 view depth, index), tile
+ * ranges, front-to-back blending (alpha = min(0.99, o exp(power)), skip alpha <
+ * 1/255, stop before T < 1e-4).  A Gaussian covers pixel (i, j) iff
+ * |i - u| <= r and |j - v| <= r, r = ceil(3 sqrt(lambda_max)).
+ *   cams          device [V] gs_camera
+ *   out_rgb       device [V,3,H,W]  C + T bg
+ *   out_depth     device [V,H,W]    sum z alpha T (raw), or normalised (flag)
+ *   out_T         device [V,H,W]    final transmittance
+ *   out_ncontrib  device [V,H,W] int32: 1 + position of the last blended
+ *                 Gaussian among the Gaussians covering that pixel
+ * The workspace keeps what the backward needs. */
+gs_status gs_render(const gs_gaussians *g, const gs_batch *batch, const gs_camera *cams, const gs_render_config *cfg,
+                    void *workspace, size_t workspace_bytes, float *out_rgb, float *out_depth, float *out_T,
+                    int32_t *out_ncontrib, void *stream);
+
+/* Adjoint of gs_render for L with dL/drgb = d_rgb [V,3,H,W] and dL/ddepth =
+ * d_depth [V,H,W] (device; raw depth only).  Must follow gs_render with the
+ * same arguments and an untouched workspace.  Gradients are ADDED to the
+ * outputs (device) -- or overwrites them with GS_FLAG_GRAD_OVERWRITE --:
+ * d_means [N,3], d_log_scales [N,3], d_quats [N,4],
+ * d_opacity_logits [N], d_sh [N,16,3] float32 whatever the SH storage type,
+ * d_cov3d [N,6] or NULL (written for Gaussians that use cov3d).  The discrete
+ * decisions are held fixed; the 0.99 clamp and the colour clamp at 0 pass zero
+ * gradient where active. */
+gs_status gs_render_backward(const gs_gaussians *g, const gs_batch *batch, const gs_camera *cams,
+                             const gs_render_config *cfg, void *workspace, size_t workspace_bytes,
+                             const float *d_rgb, const float *d_depth, float *d_means, float *d_log_scales,
+                             float *d_quats, float *d_opacity_logits, float *d_sh, float *d_cov3d, void *stream);
+
+/* Linear blend skinning (Sec. 3.3): A = sum_k w_k G[avatar][j_k] (3x4),
+ * mean' = A[:, :3] mean + A[:, 3], cov' = A[:, :3] Sigma A[:, :3]^T with
+ * Sigma = R(q) diag(exp(2 s)) R(q)^T.  joint_G: device [A, n_joints, 3, 4].
+ * Writes out_means[dest[i]] ([.,3]) and out_cov3d[dest[i]] ([.,6]). */
+gs_status gs_deform_avatars(const gs_avatars *av, const float *joint_G, float *out_means, float *out_cov3d,
+                            void *stream);
+
+/* Adjoint of gs_deform_avatars: reads d_means[dest[i]], d_cov3d[dest[i]] and
+ * ADDS to d_canon_means [M,3], d_canon_log_scales [M,3], d_canon_quats [M,4]
+ * and d_joint_G [A, n_joints, 3, 4] (device). */
+gs_status gs_deform_avatars_backward(const gs_avatars *av, const float *joint_G, const float *d_means,
+                                     const float *d_cov3d, float *d_canon_means, float *d_canon_log_scales,
+                                     float *d_canon_quats, float *d_joint_G, void *stream);
+
+/* Synchronises `stream`, returns the device status of the workspace (set by
+ * the last gs_render and any gs_render_backward after it) in *device_status
+ * (GS_OK or GS_ERR_CAPACITY) and clears it. */
+gs_status gs_get_status(void *workspace, size_t workspace_bytes, void *stream, int32_t *device_status);
+
+/* Synchronises `stream` and copies the last call's counters. */
+gs_status gs_render_stats(const void *workspace, size_t workspace_bytes, void *stream, gs_stats *out);
+
+/* Times gs_render for each (tile_w, tile_h, batch_depth) candidate on the given
+ * inputs (CUDA events on `stream`, `reps` timed runs after one warm-up) and
+ * writes the fastest into cfg->tile_w/tile_h/batch_depth.  The workspace must
+ * be sized for the largest candidate bin count (8 x 8 tiles).  Results do not
+ * depend on the tile (the footprint is per pixel), only the time does.
+ * candidates: host [n_candidates][3]; best_ms receives the best time. */
+gs_status gs_autotune(const gs_gaussians *g, const gs_batch *batch, const gs_camera *cams, gs_render_config *cfg,
+                      void *workspace, size_t workspace_bytes, float *out_rgb, float *out_depth, float *out_T,
+                      int32_t *out_ncontrib, const int32_t *candidates, int32_t n_candidates, int32_t reps,
+                      float *best_ms, void *stream);
+
+/* Device addresses of the workspace sections a gs_render call leaves behind,
+ * for inspection (tests, statistics).  Host-only arithmetic on `workspace`;
+ * nothing is read or written.  Layouts:
+ *   records    [R][12] float: (uc, vc, z, r, A, B, C, opacity, red, green, blue, 0)
+ *              where uc = u - cx, vc = v - cy, z the FP32 depth key, r the radius;
+ *              R = n_records, record of (view v, local index k) at view_rec_off[v] + k
+ *   vis        [ceil(R/32)] uint32 visibility bits
+ *   keys       [pair_capacity] uint64 (depth bits << 32 | record), sorted per bin
+ *   bin_start  [n_bins + 1] uint32, bin = view * tiles_per_view + ty * tiles_x + tx */
+typedef struct {
+    void *records, *vis, *keys, *bin_start;
+    int64_t n_records, pair_capacity;
+    int32_t n_bins, tiles_x, tiles_y, tiles_per_view;
+} gs_ws_sections;
+
+gs_status gs_workspace_sections(const gs_render_config *cfg, const gs_batch *batch, void *workspace,
+                                gs_ws_sections *out);
+
+/* Stage profiling.  While enabled, every gs_render / gs_render_backward /
+ * gs_deform_avatars(_backward) call records a CUDA event pair on its stream
+ * around each kernel (not while the stream is being captured).
+ * gs_profile_read synchronises on those events and returns, per stage, the
+ * summed milliseconds and the number of launches since the last read, then
+ * resets.  Stages: 0 setup, 1 preprocess, 2 scan, 3 scatter, 4 sort_small,
+ * 5 sort_big, 6 blend, 7 blend_backward, 8 preprocess_backward, 9 deform,
+ * 10 deform_backward (GS_N_STAGES).  Not thread-safe. */
+#define GS_N_STAGES 11
+gs_status gs_profile_enable(int32_t enable);
+gs_status gs_profile_read(float *stage_ms, int32_t *stage_launches);
+
+/* The CUDA error behind the last GS_ERR_CUDA (a cudaError_t value), 0 if none. */
+int32_t gs_last_cuda_error(void);
+
+int32_t gs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H */

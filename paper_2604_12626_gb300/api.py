@@ -1,0 +1,452 @@
+"""Thin ctypes binding of libgs (include/gs.h) plus the torch.autograd.Function.
+
+Argument marshalling only: every step of the renderer runs in libgs's CUDA
+kernels.  PyTorch provides device memory (workspaces, outputs) and streams.
+There is no CPU fallback: importing this module raises if libgs.so has not been
+built, and every call raises on a non-zero status.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+import torch
+
+_LIB_PATH = Path(__file__).resolve().parent / "_build" / "libgs.so"
+if not _LIB_PATH.exists():
+    raise ImportError(f"libgs.so is not built ({_LIB_PATH}); run `python -m paper_2604_12626_gb300.build`")
+_lib = ctypes.CDLL(str(_LIB_PATH))
+
+GS_OK = 0
+STATUS_NAMES = {0: "GS_OK", -1: "GS_ERR_INVALID_ARG", -2: "GS_ERR_ALIGNMENT", -3: "GS_ERR_WORKSPACE_TOO_SMALL",
+                -4: "GS_ERR_CAPACITY", -5: "GS_ERR_CUDA", -6: "GS_ERR_TIMEOUT", -7: "GS_ERR_UNSUPPORTED"}
+SH_F32, SH_F16, SH_BF16 = 0, 1, 2
+FLAG_PERSISTENT, FLAG_NORMALIZE_DEPTH, FLAG_GRAD_OVERWRITE = 1, 2, 4
+N_STAGES = 11
+STAGES = ("setup", "preprocess", "scan", "scatter", "sort_small", "sort_big", "blend", "blend_backward",
+          "preprocess_backward", "deform", "deform_backward")
+MAX_ENVS = MAX_VIEWS = 512
+
+_P = ctypes.c_void_p
+
+
+class GsCamera(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_float * 9), ("C", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
+
+
+class GsGaussians(ctypes.Structure):
+    _fields_ = [("means", _P), ("log_scales", _P), ("quats", _P), ("opacity_logits", _P), ("sh", _P),
+                ("sh_dtype", ctypes.c_int32), ("reserved", ctypes.c_int32), ("cov3d", _P), ("n", ctypes.c_int64)]
+
+
+class GsBatch(ctypes.Structure):
+    _fields_ = [("n_envs", ctypes.c_int32), ("n_views", ctypes.c_int32), ("env_offsets", _P),
+                ("env_cov3d_begin", _P), ("view_env", _P)]
+
+
+class GsRenderConfig(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("tile_w", ctypes.c_int32),
+                ("tile_h", ctypes.c_int32), ("batch_depth", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("bg", ctypes.c_float * 3), ("near_plane", ctypes.c_float), ("pair_capacity", ctypes.c_int64)]
+
+
+class GsStats(ctypes.Structure):
+    _fields_ = [("n_records", ctypes.c_int64), ("n_visible", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
+                ("max_bin", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class GsWsSections(ctypes.Structure):
+    _fields_ = [("records", _P), ("vis", _P), ("keys", _P), ("bin_start", _P), ("n_records", ctypes.c_int64),
+                ("pair_capacity", ctypes.c_int64), ("n_bins", ctypes.c_int32), ("tiles_x", ctypes.c_int32),
+                ("tiles_y", ctypes.c_int32), ("tiles_per_view", ctypes.c_int32)]
+
+
+class GsAvatars(ctypes.Structure):
+    _fields_ = [("means", _P), ("log_scales", _P), ("quats", _P), ("joint_ids", _P), ("weights", _P),
+                ("avatar_of", _P), ("dest", _P), ("m", ctypes.c_int64), ("n_avatars", ctypes.c_int32),
+                ("n_joints", ctypes.c_int32)]
+
+
+_R = ctypes.POINTER
+_lib.gs_render_workspace_size.argtypes = [_R(GsRenderConfig), _R(GsBatch), _R(ctypes.c_size_t)]
+_lib.gs_render.argtypes = [_R(GsGaussians), _R(GsBatch), _P, _R(GsRenderConfig), _P, ctypes.c_size_t, _P, _P, _P, _P,
+                           _P]
+_lib.gs_render_backward.argtypes = [_R(GsGaussians), _R(GsBatch), _P, _R(GsRenderConfig), _P, ctypes.c_size_t, _P, _P,
+                                    _P, _P, _P, _P, _P, _P, _P]
+_lib.gs_deform_avatars.argtypes = [_R(GsAvatars), _P, _P, _P, _P]
+_lib.gs_deform_avatars_backward.argtypes = [_R(GsAvatars), _P, _P, _P, _P, _P, _P, _P, _P]
+_lib.gs_get_status.argtypes = [_P, ctypes.c_size_t, _P, _R(ctypes.c_int32)]
+_lib.gs_render_stats.argtypes = [_P, ctypes.c_size_t, _P, _R(GsStats)]
+_lib.gs_autotune.argtypes = [_R(GsGaussians), _R(GsBatch), _P, _R(GsRenderConfig), _P, ctypes.c_size_t, _P, _P, _P,
+                             _P, _P, ctypes.c_int32, ctypes.c_int32, _R(ctypes.c_float), _P]
+_lib.gs_workspace_sections.argtypes = [_R(GsRenderConfig), _R(GsBatch), _P, _R(GsWsSections)]
+_lib.gs_profile_enable.argtypes = [ctypes.c_int32]
+_lib.gs_profile_read.argtypes = [_P, _P]
+for _f in ("gs_profile_enable", "gs_profile_read", "gs_workspace_sections", "gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_deform_avatars",
+           "gs_deform_avatars_backward", "gs_get_status", "gs_render_stats", "gs_autotune"):
+    getattr(_lib, _f).restype = ctypes.c_int32
+_lib.gs_last_cuda_error.restype = ctypes.c_int32
+_lib.gs_version.restype = ctypes.c_int32
+
+EXPORTS = ("gs_profile_enable", "gs_profile_read", "gs_workspace_sections", "gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_deform_avatars",
+           "gs_deform_avatars_backward", "gs_get_status", "gs_render_stats", "gs_autotune", "gs_last_cuda_error",
+           "gs_version")
+
+
+class GsError(RuntimeError):
+    pass
+
+
+def _check(st: int, what: str):
+    if st != GS_OK:
+        extra = f" (cudaError {_lib.gs_last_cuda_error()})" if st == -5 else ""
+        raise GsError(f"{what} failed: {STATUS_NAMES.get(st, st)}{extra}")
+
+
+def lib_path() -> str:
+    return str(_LIB_PATH)
+
+
+def version() -> int:
+    return _lib.gs_version()
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _sh_dtype(t: torch.Tensor) -> int:
+    return {torch.float32: SH_F32, torch.float16: SH_F16, torch.bfloat16: SH_BF16}[t.dtype]
+
+
+def _need(t, dtype, shape_tail, name):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if tuple(t.shape[1:]) != tuple(shape_tail):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}")
+
+
+class Batch:
+    """Batch structure: env_offsets [E+1], view_env [V], optional env_cov3d_begin [E] (host arrays)."""
+
+    def __init__(self, env_offsets, view_env=None, env_cov3d_begin=None):
+        self.env_offsets = np.ascontiguousarray(np.asarray(env_offsets, np.int64))
+        E = len(self.env_offsets) - 1
+        self.view_env = np.ascontiguousarray(np.asarray(view_env if view_env is not None else np.arange(E), np.int32))
+        self.env_cov3d_begin = (None if env_cov3d_begin is None else
+                                np.ascontiguousarray(np.asarray(env_cov3d_begin, np.int64)))
+        self.c = GsBatch(E, len(self.view_env), self.env_offsets.ctypes.data_as(_P),
+                         None if self.env_cov3d_begin is None else self.env_cov3d_begin.ctypes.data_as(_P),
+                         self.view_env.ctypes.data_as(_P))
+
+    @property
+    def n_envs(self):
+        return len(self.env_offsets) - 1
+
+    @property
+    def n_views(self):
+        return len(self.view_env)
+
+    @property
+    def n_gaussians(self):
+        return int(self.env_offsets[-1])
+
+
+def profile_enable(on: bool = True):
+    _check(_lib.gs_profile_enable(1 if on else 0), "gs_profile_enable")
+
+
+def profile_read() -> dict:
+    """Per-stage (summed ms, launches) since the last read; synchronises."""
+    ms = (ctypes.c_float * N_STAGES)()
+    n = (ctypes.c_int32 * N_STAGES)()
+    _check(_lib.gs_profile_read(ctypes.cast(ms, _P), ctypes.cast(n, _P)), "gs_profile_read")
+    return {STAGES[i]: (ms[i], n[i]) for i in range(N_STAGES) if n[i]}
+
+
+def make_config(width, height, tile=(16, 16), batch_depth=256, bg=(0.0, 0.0, 0.0), near=0.2, pair_capacity=0,
+                persistent=False, normalize_depth=False, grad_overwrite=False) -> GsRenderConfig:
+    c = GsRenderConfig()
+    c.width, c.height = width, height
+    c.tile_w, c.tile_h = tile
+    c.batch_depth = batch_depth
+    c.flags = ((FLAG_PERSISTENT if persistent else 0) | (FLAG_NORMALIZE_DEPTH if normalize_depth else 0)
+               | (FLAG_GRAD_OVERWRITE if grad_overwrite else 0))
+    c.bg[:] = list(bg)
+    c.near_plane = near
+    c.pair_capacity = pair_capacity
+    return c
+
+
+def workspace_size(cfg: GsRenderConfig, batch: Batch) -> int:
+    n = ctypes.c_size_t(0)
+    _check(_lib.gs_render_workspace_size(ctypes.byref(cfg), ctypes.byref(batch.c), ctypes.byref(n)),
+           "gs_render_workspace_size")
+    return n.value
+
+
+def cameras_tensor(cams: np.ndarray, device="cuda") -> torch.Tensor:
+    """[V,16] float32 (R, C, fx, fy, cx, cy) -> device tensor laid out as gs_camera[V]."""
+    a = np.ascontiguousarray(np.asarray(cams, np.float32).reshape(-1, 16))
+    return torch.from_numpy(a).to(device)
+
+
+class Gaussians:
+    """Device tensors of the concatenated Gaussians (see gs_gaussians)."""
+
+    def __init__(self, means, log_scales, quats, opacity_logits, sh, cov3d=None):
+        n = means.shape[0]
+        _need(means, torch.float32, (3,), "means")
+        _need(log_scales, torch.float32, (3,), "log_scales")
+        _need(quats, torch.float32, (4,), "quats")
+        _need(opacity_logits, torch.float32, (), "opacity_logits")
+        if sh.dtype not in (torch.float32, torch.float16, torch.bfloat16):
+            raise ValueError("sh must be float32, float16 or bfloat16")
+        _need(sh, sh.dtype, (16, 3), "sh")
+        if cov3d is not None:
+            _need(cov3d, torch.float32, (6,), "cov3d")
+        for t in (log_scales, quats, opacity_logits, sh):
+            if t.shape[0] != n:
+                raise ValueError("all Gaussian arrays need the same length")
+        self.means, self.log_scales, self.quats, self.opacity_logits, self.sh, self.cov3d = (
+            means, log_scales, quats, opacity_logits, sh, cov3d)
+        self.c = GsGaussians(_ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity_logits), _ptr(sh),
+                             _sh_dtype(sh), 0, _ptr(cov3d), n)
+
+    @classmethod
+    def from_numpy(cls, g: dict, device="cuda", sh_dtype=torch.float32):
+        t = {k: torch.from_numpy(np.ascontiguousarray(g[k])).to(device) for k in
+             ("means", "log_scales", "quats", "opacity_logits", "sh")}
+        sh = t["sh"].to(sh_dtype)
+        cov = None
+        if g.get("cov3d") is not None:
+            cov = torch.from_numpy(np.ascontiguousarray(g["cov3d"], np.float32)).to(device)
+        return cls(t["means"], t["log_scales"], t["quats"], t["opacity_logits"], sh, cov)
+
+
+class Renderer:
+    """A configured renderer with its own workspace (one gs_render / gs_render_backward pair)."""
+
+    def __init__(self, batch: Batch, width: int, height: int, device="cuda", **cfg_kw):
+        self.batch = batch
+        self.cfg = make_config(width, height, **cfg_kw)
+        self.device = torch.device(device)
+        self.ws_bytes = workspace_size(self.cfg, batch)
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        self.workspace[:4096].zero_()  # status word and counters
+
+    @property
+    def width(self):
+        return self.cfg.width
+
+    @property
+    def height(self):
+        return self.cfg.height
+
+    def alloc_outputs(self):
+        V, H, W = self.batch.n_views, self.cfg.height, self.cfg.width
+        dev = self.device
+        return (torch.empty((V, 3, H, W), device=dev), torch.empty((V, H, W), device=dev),
+                torch.empty((V, H, W), device=dev), torch.empty((V, H, W), dtype=torch.int32, device=dev))
+
+    def forward(self, g: Gaussians, cams: torch.Tensor, out=None, stream=None):
+        """Returns (rgb [V,3,H,W], depth [V,H,W], T [V,H,W], n_contrib [V,H,W])."""
+        if out is None:
+            out = self.alloc_outputs()
+        rgb, depth, T, nc = out
+        _check(_lib.gs_render(ctypes.byref(g.c), ctypes.byref(self.batch.c), _ptr(cams), ctypes.byref(self.cfg),
+                              _ptr(self.workspace), self.ws_bytes, _ptr(rgb), _ptr(depth), _ptr(T), _ptr(nc),
+                              _stream(stream)), "gs_render")
+        return out
+
+    def backward(self, g: Gaussians, cams: torch.Tensor, d_rgb, d_depth, grads=None, stream=None):
+        """Adds dL/d(params) into ``grads`` (allocated zero if None); returns it."""
+        n = g.means.shape[0]
+        dev = self.device
+        if grads is None:
+            grads = dict(means=torch.zeros((n, 3), device=dev), log_scales=torch.zeros((n, 3), device=dev),
+                         quats=torch.zeros((n, 4), device=dev), opacity_logits=torch.zeros((n,), device=dev),
+                         sh=torch.zeros((n, 16, 3), device=dev),
+                         cov3d=torch.zeros((n, 6), device=dev) if g.cov3d is not None else None)
+        d_rgb = d_rgb.contiguous()
+        d_depth = d_depth.contiguous()
+        _check(_lib.gs_render_backward(ctypes.byref(g.c), ctypes.byref(self.batch.c), _ptr(cams),
+                                       ctypes.byref(self.cfg), _ptr(self.workspace), self.ws_bytes, _ptr(d_rgb),
+                                       _ptr(d_depth), _ptr(grads["means"]), _ptr(grads["log_scales"]),
+                                       _ptr(grads["quats"]), _ptr(grads["opacity_logits"]), _ptr(grads["sh"]),
+                                       _ptr(grads.get("cov3d")), _stream(stream)), "gs_render_backward")
+        return grads
+
+    def stats(self, stream=None) -> dict:
+        s = GsStats()
+        _check(_lib.gs_render_stats(_ptr(self.workspace), self.ws_bytes, _stream(stream), ctypes.byref(s)),
+               "gs_render_stats")
+        return dict(n_records=s.n_records, n_visible=s.n_visible, n_pairs=s.n_pairs, max_bin=s.max_bin,
+                    status=s.status)
+
+    def status(self, stream=None) -> int:
+        v = ctypes.c_int32(0)
+        _check(_lib.gs_get_status(_ptr(self.workspace), self.ws_bytes, _stream(stream), ctypes.byref(v)),
+               "gs_get_status")
+        return v.value
+
+    def sections(self) -> dict:
+        """Views into the workspace left by the last forward: records [R,12] float32,
+        vis [ceil(R/32)] int32 bits, keys [cap] int64 (depth bits << 32 | record),
+        bin_start [n_bins+1] int32, plus the tile grid."""
+        s = GsWsSections()
+        _check(_lib.gs_workspace_sections(ctypes.byref(self.cfg), ctypes.byref(self.batch.c), _ptr(self.workspace),
+                                          ctypes.byref(s)), "gs_workspace_sections")
+        base = self.workspace.data_ptr()
+
+        def view(addr, nbytes, dtype):
+            off = addr - base
+            return self.workspace[off:off + nbytes].view(dtype)
+
+        R = s.n_records
+        return dict(records=view(s.records, R * 48, torch.float32).view(R, 12),
+                    vis=view(s.vis, ((R + 31) // 32) * 4, torch.int32),
+                    keys=view(s.keys, s.pair_capacity * 8, torch.int64),
+                    bin_start=view(s.bin_start, (s.n_bins + 1) * 4, torch.int32),
+                    n_bins=s.n_bins, tiles_x=s.tiles_x, tiles_y=s.tiles_y, tiles_per_view=s.tiles_per_view)
+
+    def autotune(self, g: Gaussians, cams: torch.Tensor, candidates, reps=3, out=None, stream=None):
+        """Time each (tile_w, tile_h, batch_depth) candidate; keep the fastest in self.cfg."""
+        if out is None:
+            out = self.alloc_outputs()
+        cand = np.ascontiguousarray(np.asarray(candidates, np.int32).reshape(-1, 3))
+        best = ctypes.c_float(0)
+        cfg = GsRenderConfig.from_buffer_copy(self.cfg)
+        rgb, depth, T, nc = out
+        _check(_lib.gs_autotune(ctypes.byref(g.c), ctypes.byref(self.batch.c), _ptr(cams), ctypes.byref(cfg),
+                                _ptr(self.workspace), self.ws_bytes, _ptr(rgb), _ptr(depth), _ptr(T), _ptr(nc),
+                                cand.ctypes.data_as(_P), len(cand), reps, ctypes.byref(best), _stream(stream)),
+               "gs_autotune")
+        self.cfg = cfg
+        return (cfg.tile_w, cfg.tile_h, cfg.batch_depth), best.value
+
+
+class Avatars:
+    """Canonical avatar Gaussians and skinning data on the device (see gs_avatars)."""
+
+    def __init__(self, means, log_scales, quats, joint_ids, weights, avatar_of, n_avatars, n_joints=24, dest=None):
+        m = means.shape[0]
+        _need(means, torch.float32, (3,), "means")
+        _need(log_scales, torch.float32, (3,), "log_scales")
+        _need(quats, torch.float32, (4,), "quats")
+        _need(weights, torch.float32, (4,), "weights")
+        if joint_ids.dtype != torch.int16 or tuple(joint_ids.shape) != (m, 4):
+            raise ValueError("joint_ids must be [M,4] int16 (uint16 bit pattern)")
+        if avatar_of.dtype != torch.int32 or tuple(avatar_of.shape) != (m,):
+            raise ValueError("avatar_of must be [M] int32")
+        if dest is not None and (dest.dtype != torch.int64 or tuple(dest.shape) != (m,)):
+            raise ValueError("dest must be [M] int64")
+        self.t = (means, log_scales, quats, joint_ids, weights, avatar_of, dest)
+        self.m, self.n_avatars, self.n_joints = m, n_avatars, n_joints
+        self.c = GsAvatars(_ptr(means), _ptr(log_scales), _ptr(quats), _ptr(joint_ids), _ptr(weights),
+                           _ptr(avatar_of), _ptr(dest), m, n_avatars, n_joints)
+
+
+def deform(av: Avatars, G: torch.Tensor, out_means: torch.Tensor, out_cov3d: torch.Tensor, stream=None):
+    _check(_lib.gs_deform_avatars(ctypes.byref(av.c), _ptr(G), _ptr(out_means), _ptr(out_cov3d), _stream(stream)),
+           "gs_deform_avatars")
+
+
+def deform_backward(av: Avatars, G, d_means, d_cov3d, grads, stream=None):
+    _check(_lib.gs_deform_avatars_backward(ctypes.byref(av.c), _ptr(G), _ptr(d_means), _ptr(d_cov3d),
+                                           _ptr(grads["means"]), _ptr(grads["log_scales"]), _ptr(grads["quats"]),
+                                           _ptr(grads["G"]), _stream(stream)), "gs_deform_avatars_backward")
+    return grads
+
+
+class RenderFunction(torch.autograd.Function):
+    """(means, log_scales, quats, opacity_logits, sh) -> (rgb [V,3,H,W], depth [V,H,W]).
+
+    The forward runs gs_render; the backward runs gs_render_backward with the
+    per-pixel (T_final, last index) checkpoint kept in the renderer workspace.
+    SH gradients are float32 whatever the SH storage type."""
+
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logits, sh, renderer: Renderer, cams):
+        g = Gaussians(means.detach(), log_scales.detach(), quats.detach(), opacity_logits.detach(), sh.detach())
+        rgb, depth, T, nc = renderer.forward(g, cams)
+        ctx.renderer, ctx.cams, ctx.g = renderer, cams, g
+        ctx.sh_dtype = sh.dtype
+        return rgb, depth
+
+    @staticmethod
+    def backward(ctx, d_rgb, d_depth):
+        r = ctx.renderer
+        V, H, W = r.batch.n_views, r.height, r.width
+        if d_rgb is None:
+            d_rgb = torch.zeros((V, 3, H, W), device=r.device)
+        if d_depth is None:
+            d_depth = torch.zeros((V, H, W), device=r.device)
+        gr = r.backward(ctx.g, ctx.cams, d_rgb.float(), d_depth.float())
+        return (gr["means"], gr["log_scales"], gr["quats"], gr["opacity_logits"], gr["sh"].to(ctx.sh_dtype), None,
+                None)
+
+
+def render(means, log_scales, quats, opacity_logits, sh, renderer: Renderer, cams):
+    """Differentiable batched render; see RenderFunction."""
+    return RenderFunction.apply(means, log_scales, quats, opacity_logits, sh, renderer, cams)
+
+
+class SceneWithAvatarsFunction(torch.autograd.Function):
+    """Scene Gaussians plus LBS-deformed avatar Gaussians rendered in one pass.
+
+    Inputs: scene (means, log_scales, quats, opacity_logits, sh) [Ns...], avatar
+    canonical (means, log_scales, quats) [M...], avatar opacity_logits [M], avatar
+    sh [M,16,3], joint matrices G [A,J,3,4].  One env: Gaussian order is scene then
+    avatars.  Gradients flow to all of them, including G, through
+    gs_deform_avatars_backward."""
+
+    @staticmethod
+    def forward(ctx, s_means, s_ls, s_q, s_op, s_sh, a_means, a_ls, a_q, a_op, a_sh, G, av_static, renderer, cams):
+        ns, m = s_means.shape[0], a_means.shape[0]
+        dev = s_means.device
+        means = torch.empty((ns + m, 3), device=dev)
+        cov3d = torch.zeros((ns + m, 6), device=dev)
+        means[:ns] = s_means.detach()
+        joint_ids, weights, avatar_of, n_avatars, n_joints = av_static
+        dest = torch.arange(ns, ns + m, dtype=torch.int64, device=dev)
+        av = Avatars(a_means.detach().contiguous(), a_ls.detach().contiguous(), a_q.detach().contiguous(),
+                     joint_ids, weights, avatar_of, n_avatars, n_joints, dest=dest)
+        deform(av, G.detach().contiguous(), means, cov3d)
+        ls = torch.cat([s_ls.detach(), torch.zeros((m, 3), device=dev)])
+        q = torch.cat([s_q.detach(), torch.tensor([[1.0, 0.0, 0.0, 0.0]], device=dev).expand(m, 4)]).contiguous()
+        op = torch.cat([s_op.detach(), a_op.detach()]).contiguous()
+        sh = torch.cat([s_sh.detach(), a_sh.detach()]).contiguous()
+        g = Gaussians(means, ls, q, op, sh, cov3d)
+        rgb, depth, T, nc = renderer.forward(g, cams)
+        ctx.save = (g, av, G.detach().contiguous(), renderer, cams, ns, m, s_sh.dtype)
+        return rgb, depth
+
+    @staticmethod
+    def backward(ctx, d_rgb, d_depth):
+        g, av, G, r, cams, ns, m, shd = ctx.save
+        V, H, W = r.batch.n_views, r.height, r.width
+        if d_rgb is None:
+            d_rgb = torch.zeros((V, 3, H, W), device=r.device)
+        if d_depth is None:
+            d_depth = torch.zeros((V, H, W), device=r.device)
+        gr = r.backward(g, cams, d_rgb.float(), d_depth.float())
+        ga = dict(means=torch.zeros((m, 3), device=r.device), log_scales=torch.zeros((m, 3), device=r.device),
+                  quats=torch.zeros((m, 4), device=r.device), G=torch.zeros_like(G))
+        deform_backward(av, G, gr["means"], gr["cov3d"], ga)
+        return (gr["means"][:ns], gr["log_scales"][:ns], gr["quats"][:ns], gr["opacity_logits"][:ns],
+                gr["sh"][:ns].to(shd), ga["means"], ga["log_scales"], ga["quats"], gr["opacity_logits"][ns:],
+                gr["sh"][ns:].to(shd), ga["G"], None, None, None)

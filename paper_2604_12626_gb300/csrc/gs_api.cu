@@ -1,0 +1,581 @@
+// gs_api.cu -- the extern "C" entry points of libgs (include/gs.h).
+//
+// Host side only: argument checks, the workspace layout, the batch table and
+// the launch sequence.  No call allocates device memory, and only
+// gs_get_status / gs_render_stats synchronise.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "gs.h"
+#include "gs_internal.cuh"
+#include "gs_launch.h"
+
+namespace {
+
+using namespace gs;
+
+thread_local int32_t g_last_cuda_error = 0;
+
+gs_status cuda_fail(cudaError_t e)
+{
+    g_last_cuda_error = (int32_t)e;
+    return GS_ERR_CUDA;
+}
+
+gs_status check_launch()
+{
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GS_OK : cuda_fail(e);
+}
+
+// ---------------------------------------------------------------------------
+// stage profiling (events around each launch, outside stream capture)
+// ---------------------------------------------------------------------------
+struct ProfRec {
+    int stage;
+    cudaEvent_t a, b;
+};
+bool g_prof = false;
+std::vector<ProfRec> g_prof_pending;
+std::vector<cudaEvent_t> g_prof_pool;
+
+cudaEvent_t prof_event()
+{
+    if (!g_prof_pool.empty()) {
+        cudaEvent_t e = g_prof_pool.back();
+        g_prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+bool capturing(cudaStream_t s)
+{
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &st);
+    return st != cudaStreamCaptureStatusNone;
+}
+
+// RAII marker: records an event before and after the launches in its scope.
+struct Stage {
+    int stage;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    Stage(int st, cudaStream_t str) : stage(st), s(str)
+    {
+        if (g_prof && !capturing(s)) {
+            a = prof_event();
+            cudaEventRecord(a, s);
+        }
+    }
+    ~Stage()
+    {
+        if (a) {
+            cudaEvent_t b = prof_event();
+            cudaEventRecord(b, s);
+            g_prof_pending.push_back(ProfRec{stage, a, b});
+        }
+    }
+};
+
+constexpr int kMaxDevices = 64;
+std::once_flag g_once[kMaxDevices];
+cudaError_t g_init_err[kMaxDevices];
+int g_sms[kMaxDevices];
+
+gs_status device_init(int *sms)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= kMaxDevices) return GS_ERR_UNSUPPORTED;
+    std::call_once(g_once[dev], [dev]() {
+        cudaError_t r = configure_forward_kernels();
+        if (r == cudaSuccess) r = configure_backward_kernels();
+        int n = 0;
+        if (r == cudaSuccess) r = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        g_sms[dev] = n;
+        g_init_err[dev] = r;
+    });
+    if (g_init_err[dev] != cudaSuccess) return cuda_fail(g_init_err[dev]);
+    *sms = g_sms[dev];
+    return GS_OK;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Plan {
+    int W, H, tw, th, tiles_x, tiles_y, tpv, n_bins, B, flags;
+    int64_t N, R, cap;
+    float near_plane;
+    // byte offsets
+    size_t o_hdr, o_tb, o_rec, o_vis, o_cnt, o_start, o_cur, o_big, o_keys, o_scr, o_pT, o_pL, o_drec, total;
+};
+
+gs_status make_plan(const gs_render_config *cfg, const gs_batch *b, Plan &p)
+{
+    if (!cfg || !b) return GS_ERR_INVALID_ARG;
+    if (b->n_envs < 1 || b->n_envs > GS_MAX_ENVS || b->n_views < 1 || b->n_views > GS_MAX_VIEWS)
+        return GS_ERR_INVALID_ARG;
+    if (!b->env_offsets || !b->view_env) return GS_ERR_INVALID_ARG;
+    if (cfg->width < 1 || cfg->height < 1 || cfg->width > 16384 || cfg->height > 16384) return GS_ERR_INVALID_ARG;
+    p.W = cfg->width;
+    p.H = cfg->height;
+    p.tw = cfg->tile_w > 0 ? cfg->tile_w : 16;
+    p.th = cfg->tile_h > 0 ? cfg->tile_h : 16;
+    if (p.tw * p.th > 1024 || (p.tw * p.th) % 32 != 0) return GS_ERR_INVALID_ARG;
+    p.B = cfg->batch_depth > 0 ? cfg->batch_depth : 256;
+    if (p.B < 32 || p.B > 256) return GS_ERR_INVALID_ARG;
+    p.flags = cfg->flags;
+    p.near_plane = cfg->near_plane > 0.0f ? cfg->near_plane : 0.2f;
+    p.tiles_x = (p.W + p.tw - 1) / p.tw;
+    p.tiles_y = (p.H + p.th - 1) / p.th;
+    p.tpv = p.tiles_x * p.tiles_y;
+    const int64_t nb = (int64_t)p.tpv * b->n_views;
+    if (nb > (int64_t)1 << 30) return GS_ERR_INVALID_ARG;
+    p.n_bins = (int)nb;
+    if (b->env_offsets[0] != 0) return GS_ERR_INVALID_ARG;
+    for (int e = 0; e < b->n_envs; ++e)
+        if (b->env_offsets[e + 1] < b->env_offsets[e]) return GS_ERR_INVALID_ARG;
+    p.N = b->env_offsets[b->n_envs];
+    int64_t R = 0;
+    for (int v = 0; v < b->n_views; ++v) {
+        const int e = b->view_env[v];
+        if (e < 0 || e >= b->n_envs) return GS_ERR_INVALID_ARG;
+        R += b->env_offsets[e + 1] - b->env_offsets[e];
+    }
+    if (R >= ((int64_t)1 << 31)) return GS_ERR_UNSUPPORTED;
+    p.R = R;
+    p.cap = cfg->pair_capacity > 0 ? cfg->pair_capacity : 4 * R + 65536;
+    if (p.cap > ((int64_t)1 << 31) - 1) p.cap = ((int64_t)1 << 31) - 1;
+    const int64_t npix = (int64_t)b->n_views * p.W * p.H;
+    size_t o = 0;
+    p.o_hdr = o; o = align256(o + sizeof(Header));
+    p.o_tb = o; o = align256(o + sizeof(Table));
+    p.o_rec = o; o = align256(o + (size_t)R * 48);
+    p.o_vis = o; o = align256(o + (size_t)((R + 31) / 32 + 1) * 4);
+    p.o_cnt = o; o = align256(o + (size_t)nb * 4);
+    p.o_start = o; o = align256(o + (size_t)(nb + 1) * 4);
+    p.o_cur = o; o = align256(o + (size_t)nb * 4);
+    p.o_big = o; o = align256(o + (size_t)nb * 4);
+    p.o_keys = o; o = align256(o + (size_t)p.cap * 8);
+    p.o_scr = o; o = align256(o + (size_t)p.cap * 8);
+    p.o_pT = o; o = align256(o + (size_t)npix * 4);
+    p.o_pL = o; o = align256(o + (size_t)npix * 4);
+    p.o_drec = o; o = align256(o + (size_t)R * 48);
+    p.total = o;
+    return GS_OK;
+}
+
+Ws ws_ptrs(void *base, const Plan &p)
+{
+    char *b = static_cast<char *>(base);
+    Ws w;
+    w.hdr = reinterpret_cast<Header *>(b + p.o_hdr);
+    w.tb = reinterpret_cast<Table *>(b + p.o_tb);
+    w.rec = reinterpret_cast<float4 *>(b + p.o_rec);
+    w.vis = reinterpret_cast<uint32_t *>(b + p.o_vis);
+    w.bin_count = reinterpret_cast<uint32_t *>(b + p.o_cnt);
+    w.bin_start = reinterpret_cast<uint32_t *>(b + p.o_start);
+    w.bin_cursor = reinterpret_cast<uint32_t *>(b + p.o_cur);
+    w.big_list = reinterpret_cast<uint32_t *>(b + p.o_big);
+    w.keys = reinterpret_cast<unsigned long long *>(b + p.o_keys);
+    w.scratch = reinterpret_cast<unsigned long long *>(b + p.o_scr);
+    w.pix_T = reinterpret_cast<float *>(b + p.o_pT);
+    w.pix_last = reinterpret_cast<uint32_t *>(b + p.o_pL);
+    w.d_rec = reinterpret_cast<float *>(b + p.o_drec);
+    return w;
+}
+
+void fill_table(const Plan &p, const gs_batch *b, const gs_render_config *cfg, Table &t)
+{
+    std::memset(&t, 0, sizeof(Table));
+    t.n_envs = b->n_envs;
+    t.n_views = b->n_views;
+    t.W = p.W; t.H = p.H; t.tile_w = p.tw; t.tile_h = p.th;
+    t.tiles_x = p.tiles_x; t.tiles_y = p.tiles_y; t.tiles_per_view = p.tpv; t.n_bins = p.n_bins;
+    t.batch_depth = p.B;
+    t.flags = p.flags;
+    t.n_records = p.R;
+    t.pair_capacity = p.cap;
+    t.n_gauss = p.N;
+    for (int k = 0; k < 3; ++k) t.bg[k] = cfg->bg[k];
+    t.near_plane = p.near_plane;
+    for (int e = 0; e <= b->n_envs; ++e) t.env_off[e] = b->env_offsets[e];
+    for (int e = 0; e < b->n_envs; ++e)
+        t.env_cov_begin[e] = b->env_cov3d_begin ? b->env_cov3d_begin[e] : b->env_offsets[e + 1];
+    int64_t off = 0;
+    for (int v = 0; v < b->n_views; ++v) {
+        const int e = b->view_env[v];
+        t.view_env[v] = e;
+        t.view_rec_off[v] = off;
+        off += b->env_offsets[e + 1] - b->env_offsets[e];
+    }
+    t.view_rec_off[b->n_views] = off;
+    // views grouped by env (CSR)
+    int cnt = 0;
+    for (int e = 0; e < b->n_envs; ++e) {
+        t.env_view_begin[e] = cnt;
+        for (int v = 0; v < b->n_views; ++v)
+            if (b->view_env[v] == e) t.env_views[cnt++] = v;
+    }
+    t.env_view_begin[b->n_envs] = cnt;
+}
+
+gs_status check_gaussians(const gs_gaussians *g, const Plan &p, bool need_sq)
+{
+    if (!g || !g->means || !g->opacity_logits || !g->sh) return GS_ERR_INVALID_ARG;
+    if (g->n != p.N) return GS_ERR_INVALID_ARG;
+    if (g->sh_dtype < GS_SH_F32 || g->sh_dtype > GS_SH_BF16) return GS_ERR_INVALID_ARG;
+    if (need_sq && (!g->log_scales || !g->quats)) return GS_ERR_INVALID_ARG;
+    // rows read with 16-byte vector loads need 16-byte alignment; the rest 4
+    const void *p16[] = {g->quats, g->sh};
+    for (const void *q : p16)
+        if (q && !aligned16(q)) return GS_ERR_ALIGNMENT;
+    const void *p4[] = {g->means, g->log_scales, g->opacity_logits, g->cov3d};
+    for (const void *q : p4)
+        if (q && (reinterpret_cast<uintptr_t>(q) & 3u)) return GS_ERR_ALIGNMENT;
+    return GS_OK;
+}
+
+gs_status enqueue_forward(const gs_gaussians *g, const gs_batch *b, const gs_camera *cams,
+                          const gs_render_config *cfg, void *ws, size_t ws_bytes, float *rgb, float *depth, float *T,
+                          int32_t *ncontrib, cudaStream_t s)
+{
+    int sms = 0;
+    gs_status st = device_init(&sms);
+    if (st != GS_OK) return st;
+    Plan p;
+    st = make_plan(cfg, b, p);
+    if (st != GS_OK) return st;
+    st = check_gaussians(g, p, true);
+    if (st != GS_OK) return st;
+    if (!cams || !ws || !rgb || !depth || !T || !ncontrib) return GS_ERR_INVALID_ARG;
+    if (!aligned16(cams) || !aligned16(ws) || !aligned16(rgb) || !aligned16(depth) || !aligned16(T) ||
+        !aligned16(ncontrib))
+        return GS_ERR_ALIGNMENT;
+    if (ws_bytes < p.total) return GS_ERR_WORKSPACE_TOO_SMALL;
+    Table t;
+    fill_table(p, b, cfg, t);
+    Ws w = ws_ptrs(ws, p);
+    {
+        Stage st0(0, s);
+        launch_setup(t, w, s);
+        cudaError_t e = cudaMemsetAsync(w.vis, 0, (size_t)((p.R + 31) / 32 + 1) * 4, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.bin_count, 0, (size_t)p.n_bins * 4, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.bin_cursor, 0, (size_t)p.n_bins * 4, s);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    {
+        Stage st1(1, s);
+        launch_preprocess(g, cams, w, p.N, s);
+    }
+    {
+        Stage st2(2, s);
+        launch_scan(w, s);
+    }
+    {
+        Stage st3(3, s);
+        launch_scatter(cams, w, p.N, s);
+    }
+    {
+        Stage st4(4, s);
+        launch_sort_small(w, p.n_bins, s);
+    }
+    {
+        Stage st5(5, s);
+        launch_sort_big(w, sms, s);
+    }
+    const int threads = p.tw * p.th;
+    const bool persistent = (p.flags & GS_FLAG_PERSISTENT) != 0;
+    int pgrid = 0;
+    if (persistent) {
+        pgrid = sms * blend_blocks_per_sm(threads, p.B);
+        if (pgrid > p.n_bins) pgrid = p.n_bins;
+    }
+    {
+        Stage st6(6, s);
+        launch_blend(cams, w, rgb, depth, T, ncontrib, p.n_bins, threads, p.B, persistent, pgrid, s);
+    }
+    return check_launch();
+}
+
+} // namespace
+
+extern "C" {
+
+gs_status gs_render_workspace_size(const gs_render_config *cfg, const gs_batch *batch, size_t *bytes)
+{
+    if (!bytes) return GS_ERR_INVALID_ARG;
+    Plan p;
+    gs_status st = make_plan(cfg, batch, p);
+    if (st != GS_OK) return st;
+    *bytes = p.total;
+    return GS_OK;
+}
+
+gs_status gs_render(const gs_gaussians *g, const gs_batch *batch, const gs_camera *cams, const gs_render_config *cfg,
+                    void *workspace, size_t workspace_bytes, float *out_rgb, float *out_depth, float *out_T,
+                    int32_t *out_ncontrib, void *stream)
+{
+    return enqueue_forward(g, batch, cams, cfg, workspace, workspace_bytes, out_rgb, out_depth, out_T, out_ncontrib,
+                           static_cast<cudaStream_t>(stream));
+}
+
+gs_status gs_render_backward(const gs_gaussians *g, const gs_batch *batch, const gs_camera *cams,
+                             const gs_render_config *cfg, void *workspace, size_t workspace_bytes,
+                             const float *d_rgb, const float *d_depth, float *d_means, float *d_log_scales,
+                             float *d_quats, float *d_opacity_logits, float *d_sh, float *d_cov3d, void *stream)
+{
+    int sms = 0;
+    gs_status st = device_init(&sms);
+    if (st != GS_OK) return st;
+    Plan p;
+    st = make_plan(cfg, batch, p);
+    if (st != GS_OK) return st;
+    st = check_gaussians(g, p, true);
+    if (st != GS_OK) return st;
+    if (cfg->flags & GS_FLAG_NORMALIZE_DEPTH) return GS_ERR_UNSUPPORTED;
+    if (!cams || !workspace || !d_rgb || !d_depth || !d_means || !d_log_scales || !d_quats || !d_opacity_logits ||
+        !d_sh)
+        return GS_ERR_INVALID_ARG;
+    const void *ptrs[] = {cams, workspace, d_rgb, d_depth, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh};
+    for (const void *q : ptrs)
+        if (!aligned16(q)) return GS_ERR_ALIGNMENT;
+    if (d_cov3d && !aligned16(d_cov3d)) return GS_ERR_ALIGNMENT;
+    if (workspace_bytes < p.total) return GS_ERR_WORKSPACE_TOO_SMALL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Ws w = ws_ptrs(workspace, p);
+    {
+        Stage st7(7, s);
+        cudaError_t e = cudaMemsetAsync(w.d_rec, 0, (size_t)p.R * 48, s);
+        if (e != cudaSuccess) return cuda_fail(e);
+        launch_blend_backward(cams, w, d_rgb, d_depth, p.n_bins, p.tw * p.th, p.B, s);
+    }
+    {
+        Stage st8(8, s);
+        GradOut o{d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_cov3d};
+        launch_preprocess_backward(g, cams, w, o, p.N, (cfg->flags & GS_FLAG_GRAD_OVERWRITE) != 0, s);
+    }
+    return check_launch();
+}
+
+gs_status gs_deform_avatars(const gs_avatars *av, const float *joint_G, float *out_means, float *out_cov3d,
+                            void *stream)
+{
+    if (!av || !joint_G || !out_means || !out_cov3d) return GS_ERR_INVALID_ARG;
+    if (av->m < 0 || av->n_avatars < 1 || av->n_joints < 1 || av->n_joints > 64) return GS_ERR_INVALID_ARG;
+    if (av->m == 0) return GS_OK;
+    if (!av->means || !av->log_scales || !av->quats || !av->joint_ids || !av->weights || !av->avatar_of)
+        return GS_ERR_INVALID_ARG;
+    const void *ptrs[] = {av->means, av->log_scales, av->quats, av->joint_ids, av->weights, av->avatar_of,
+                          joint_G, out_means, out_cov3d};
+    for (const void *q : ptrs)
+        if (!aligned16(q)) return GS_ERR_ALIGNMENT;
+    {
+        Stage st9(9, static_cast<cudaStream_t>(stream));
+        launch_deform(av, joint_G, out_means, out_cov3d, static_cast<cudaStream_t>(stream));
+    }
+    return check_launch();
+}
+
+gs_status gs_deform_avatars_backward(const gs_avatars *av, const float *joint_G, const float *d_means,
+                                     const float *d_cov3d, float *d_canon_means, float *d_canon_log_scales,
+                                     float *d_canon_quats, float *d_joint_G, void *stream)
+{
+    if (!av || !joint_G || !d_means || !d_cov3d || !d_canon_means || !d_canon_log_scales || !d_canon_quats ||
+        !d_joint_G)
+        return GS_ERR_INVALID_ARG;
+    if (av->m < 0 || av->n_avatars < 1 || av->n_joints < 1 || av->n_joints > 64) return GS_ERR_INVALID_ARG;
+    if (av->m == 0) return GS_OK;
+    const void *ptrs[] = {av->means, av->log_scales, av->quats, av->joint_ids, av->weights, av->avatar_of, joint_G,
+                          d_means, d_cov3d, d_canon_means, d_canon_log_scales, d_canon_quats, d_joint_G};
+    for (const void *q : ptrs)
+        if (!q || !aligned16(q)) return q ? GS_ERR_ALIGNMENT : GS_ERR_INVALID_ARG;
+    {
+        Stage st10(10, static_cast<cudaStream_t>(stream));
+        launch_deform_backward(av, joint_G, d_means, d_cov3d, d_canon_means, d_canon_log_scales, d_canon_quats,
+                               d_joint_G, static_cast<cudaStream_t>(stream));
+    }
+    return check_launch();
+}
+
+gs_status gs_get_status(void *workspace, size_t workspace_bytes, void *stream, int32_t *device_status)
+{
+    if (!workspace || !device_status || workspace_bytes < sizeof(Header)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Header *h = static_cast<Header *>(workspace);
+    int32_t v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, &h->status, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&h->status, 0, 4, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *device_status = v;
+    return GS_OK;
+}
+
+gs_status gs_render_stats(const void *workspace, size_t workspace_bytes, void *stream, gs_stats *out)
+{
+    if (!workspace || !out || workspace_bytes < sizeof(Header) + sizeof(Table)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const char *b = static_cast<const char *>(workspace);
+    Table t;
+    cudaError_t e = cudaMemcpyAsync(&t, b + align256(sizeof(Header)), sizeof(Table), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    // rebuild the plan offsets from the table
+    Plan p;
+    gs_render_config cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.width = t.W; cfg.height = t.H; cfg.tile_w = t.tile_w; cfg.tile_h = t.tile_h;
+    cfg.batch_depth = t.batch_depth; cfg.pair_capacity = t.pair_capacity; cfg.flags = t.flags;
+    gs_batch bt;
+    bt.n_envs = t.n_envs; bt.n_views = t.n_views;
+    bt.env_offsets = t.env_off; bt.env_cov3d_begin = nullptr; bt.view_env = t.view_env;
+    gs_status st = make_plan(&cfg, &bt, p);
+    if (st != GS_OK) return st;
+    if (workspace_bytes < p.total) return GS_ERR_WORKSPACE_TOO_SMALL;
+    Ws w = ws_ptrs(const_cast<void *>(workspace), p);
+    e = cudaMemsetAsync(&w.hdr->n_visible, 0, 4, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    launch_count_visible(w, (p.R + 31) / 32, s);
+    Header h;
+    e = cudaMemcpyAsync(&h, w.hdr, sizeof(Header), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    out->n_records = t.n_records;
+    out->n_visible = h.n_visible;
+    out->n_pairs = h.n_pairs;
+    out->max_bin = h.max_bin;
+    out->status = h.status;
+    out->reserved = 0;
+    return GS_OK;
+}
+
+gs_status gs_autotune(const gs_gaussians *g, const gs_batch *batch, const gs_camera *cams, gs_render_config *cfg,
+                      void *workspace, size_t workspace_bytes, float *out_rgb, float *out_depth, float *out_T,
+                      int32_t *out_ncontrib, const int32_t *candidates, int32_t n_candidates, int32_t reps,
+                      float *best_ms, void *stream)
+{
+    if (!cfg || !candidates || n_candidates < 1 || reps < 1) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(e);
+    }
+    gs_render_config best = *cfg;
+    float best_t = -1.0f;
+    gs_status result = GS_OK;
+    for (int c = 0; c < n_candidates && result == GS_OK; ++c) {
+        gs_render_config k = *cfg;
+        k.tile_w = candidates[3 * c];
+        k.tile_h = candidates[3 * c + 1];
+        k.batch_depth = candidates[3 * c + 2];
+        Plan p;
+        if (make_plan(&k, batch, p) != GS_OK || p.total > workspace_bytes) continue;
+        gs_status st = enqueue_forward(g, batch, cams, &k, workspace, workspace_bytes, out_rgb, out_depth, out_T,
+                                       out_ncontrib, s);
+        if (st != GS_OK) {
+            result = st;
+            break;
+        }
+        e = cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == GS_OK; ++r)
+            st = enqueue_forward(g, batch, cams, &k, workspace, workspace_bytes, out_rgb, out_depth, out_T,
+                                 out_ncontrib, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            result = cuda_fail(e);
+            break;
+        }
+        if (st != GS_OK) {
+            result = st;
+            break;
+        }
+        ms /= (float)reps;
+        if (best_t < 0.0f || ms < best_t) {
+            best_t = ms;
+            best = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (result != GS_OK) return result;
+    if (best_t < 0.0f) return GS_ERR_WORKSPACE_TOO_SMALL;
+    *cfg = best;
+    if (best_ms) *best_ms = best_t;
+    return GS_OK;
+}
+
+gs_status gs_workspace_sections(const gs_render_config *cfg, const gs_batch *batch, void *workspace,
+                                gs_ws_sections *out)
+{
+    if (!workspace || !out) return GS_ERR_INVALID_ARG;
+    Plan p;
+    gs_status st = make_plan(cfg, batch, p);
+    if (st != GS_OK) return st;
+    char *b = static_cast<char *>(workspace);
+    out->records = b + p.o_rec;
+    out->vis = b + p.o_vis;
+    out->keys = b + p.o_keys;
+    out->bin_start = b + p.o_start;
+    out->n_records = p.R;
+    out->pair_capacity = p.cap;
+    out->n_bins = p.n_bins;
+    out->tiles_x = p.tiles_x;
+    out->tiles_y = p.tiles_y;
+    out->tiles_per_view = p.tpv;
+    return GS_OK;
+}
+
+gs_status gs_profile_enable(int32_t enable)
+{
+    g_prof = enable != 0;
+    return GS_OK;
+}
+
+gs_status gs_profile_read(float *stage_ms, int32_t *stage_launches)
+{
+    if (!stage_ms || !stage_launches) return GS_ERR_INVALID_ARG;
+    for (int i = 0; i < GS_N_STAGES; ++i) {
+        stage_ms[i] = 0.0f;
+        stage_launches[i] = 0;
+    }
+    gs_status result = GS_OK;
+    for (const ProfRec &r : g_prof_pending) {
+        float ms = 0.0f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) result = cuda_fail(e);
+        if (r.stage >= 0 && r.stage < GS_N_STAGES) {
+            stage_ms[r.stage] += ms;
+            stage_launches[r.stage] += 1;
+        }
+        g_prof_pool.push_back(r.a);
+        g_prof_pool.push_back(r.b);
+    }
+    g_prof_pending.clear();
+    return result;
+}
+
+int32_t gs_last_cuda_error(void) { return g_last_cuda_error; }
+
+int32_t gs_version(void) { return 1; }
+
+} // extern "C"

@@ -1,0 +1,530 @@
+// gs_backward.cu -- adjoint kernels of libgs (sm_103a).
+//
+// blend_backward   one CTA per (view, tile).  Each pixel walks its tile list
+//                  back to front from the last pair it blended, rebuilding the
+//                  transmittance by division (T_i = T_{i+1} / (1 - alpha_i)), so
+//                  only T_final and the last index per pixel were saved.  The
+//                  per-pair gradients of (uc, vc, conic, opacity, colour, z) are
+//                  reduced across the warp by shuffles, then across the CTA in
+//                  shared memory, and flushed with one set of float4 atomics per
+//                  (tile, Gaussian).
+// preprocess_backward  one thread per Gaussian, looping over the views of its
+//                  env: the chain rule through the conic inverse, the dilation,
+//                  J W Sigma W^T J^T, the quaternion normalisation and scales,
+//                  the SH direction and coefficients, and the opacity sigmoid.
+// Discrete decisions (cull, radius, footprint, skips, stop) are the forward's,
+// recomputed bit for bit from the same helpers; the 0.99 clamp and the colour
+// clamp at 0 pass zero gradient where active.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "gs_internal.cuh"
+#include "gs_launch.h"
+
+namespace gs {
+
+constexpr int kGradStride = 12; // floats per record gradient (3 float4)
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void bin_range_b(const Ws &w, int bin, uint32_t &start, uint32_t &n)
+{
+    const uint64_t cap = (uint64_t)w.tb->pair_capacity;
+    uint64_t s = w.bin_start[bin], e = w.bin_start[bin + 1];
+    if (e > cap) e = cap;
+    if (s > e) s = e;
+    start = (uint32_t)s;
+    n = (uint32_t)(e - s);
+}
+
+__global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, const float *__restrict__ d_rgb,
+                                      const float *__restrict__ d_depth)
+{
+    extern __shared__ float4 smem_b[];
+    const Table *tb = w.tb;
+    const int B = tb->batch_depth;
+    float4 *s0 = smem_b, *s1 = smem_b + B, *s2 = smem_b + 2 * B;
+    float *acc = reinterpret_cast<float *>(smem_b + 3 * B); // [B][kGradStride]
+    uint32_t *sidx = reinterpret_cast<uint32_t *>(acc + B * kGradStride);
+    __shared__ uint32_t smax_last;
+
+    const int bin = blockIdx.x;
+    const int v = bin / tb->tiles_per_view;
+    const int t = bin - v * tb->tiles_per_view;
+    const int tyi = t / tb->tiles_x, txi = t - tyi * tb->tiles_x;
+    const int lx = threadIdx.x % tb->tile_w, ly = threadIdx.x / tb->tile_w;
+    const int i = txi * tb->tile_w + lx, j = tyi * tb->tile_h + ly;
+    const int W = tb->W, H = tb->H;
+    const bool inside = i < W && j < H;
+    const gs_camera &cam = cams[v];
+    const float pxc = pix_c(i, cam.cx), pyc = pix_c(j, cam.cy);
+    const size_t HW = (size_t)W * H;
+    const size_t p = (size_t)j * W + i;
+    uint32_t start, n;
+    bin_range_b(w, bin, start, n);
+    const unsigned long long *keys = w.keys + start;
+
+    float T = 1.0f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f, dD = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f, SD = 0.f;
+    uint32_t last = 0;
+    if (inside) {
+        T = w.pix_T[(size_t)v * HW + p];
+        last = w.pix_last[(size_t)v * HW + p];
+        dC0 = d_rgb[(3 * (size_t)v + 0) * HW + p];
+        dC1 = d_rgb[(3 * (size_t)v + 1) * HW + p];
+        dC2 = d_rgb[(3 * (size_t)v + 2) * HW + p];
+        dD = d_depth[(size_t)v * HW + p];
+        S0 = T * tb->bg[0];
+        S1 = T * tb->bg[1];
+        S2 = T * tb->bg[2];
+    }
+    if (threadIdx.x == 0) smax_last = 0;
+    __syncthreads();
+    const uint32_t wl = __reduce_max_sync(0xffffffffu, last);
+    if ((threadIdx.x & 31) == 0) atomicMax(&smax_last, wl);
+    __syncthreads();
+    const uint32_t n_proc = min(smax_last, n);
+    const int lane = threadIdx.x & 31;
+
+    for (int32_t hi = (int32_t)n_proc; hi > 0; hi -= B) {
+        const int32_t lo = max(0, hi - B);
+        const int cnt = hi - lo;
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+            uint32_t rec = (uint32_t)keys[lo + k];
+            if (rec >= (uint32_t)tb->n_records) rec = 0; // only after a capacity overflow
+            const float4 *src = w.rec + 3 * (size_t)rec;
+            s0[k] = src[0];
+            s1[k] = src[1];
+            s2[k] = src[2];
+            sidx[k] = rec;
+        }
+        for (int k = threadIdx.x; k < cnt * kGradStride; k += blockDim.x) acc[k] = 0.0f;
+        __syncthreads();
+        for (int k = cnt - 1; k >= 0; --k) {
+            const uint32_t pos = (uint32_t)(lo + k);
+            float g_u = 0.f, g_v = 0.f, g_A = 0.f, g_B = 0.f, g_C = 0.f, g_o = 0.f, g_r = 0.f, g_g = 0.f, g_b = 0.f,
+                  g_z = 0.f;
+            bool contrib = false;
+            if (pos < last) {
+                const float4 a = s0[k];
+                const float dx = __fsub_rn(a.x, pxc), dy = __fsub_rn(a.y, pyc);
+                if (fmaxf(fabsf(dx), fabsf(dy)) <= a.w) {
+                    const float4 q = s1[k];
+                    const float power = gauss_power(q.x, q.y, q.z, dx, dy);
+                    if (power <= 0.0f) {
+                        const float ar = raw_alpha(q.w, power);
+                        const float alpha = fminf(kAlphaMax, ar);
+                        if (alpha >= kAlphaMin) {
+                            contrib = true;
+                            const float4 c = s2[k];
+                            const float om = 1.0f - alpha;
+                            const float Ti = T / om;
+                            const float wgt = alpha * Ti;
+                            g_r = wgt * dC0;
+                            g_g = wgt * dC1;
+                            g_b = wgt * dC2;
+                            g_z = wgt * dD;
+                            const float iom = 1.0f / om;
+                            const float dal = dC0 * (c.x * Ti - S0 * iom) + dC1 * (c.y * Ti - S1 * iom) +
+                                              dC2 * (c.z * Ti - S2 * iom) + dD * (a.z * Ti - SD * iom);
+                            S0 += c.x * wgt;
+                            S1 += c.y * wgt;
+                            S2 += c.z * wgt;
+                            SD += a.z * wgt;
+                            T = Ti;
+                            if (ar < kAlphaMax) {
+                                const float G = ar / q.w;
+                                g_o = dal * G;
+                                const float gp = dal * alpha;
+                                g_u = -gp * (q.x * dx + q.y * dy);
+                                g_v = -gp * (q.z * dy + q.y * dx);
+                                g_A = -0.5f * gp * dx * dx;
+                                g_C = -0.5f * gp * dy * dy;
+                                g_B = -gp * dx * dy;
+                            }
+                        }
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+                g_u = warp_sum(g_u); g_v = warp_sum(g_v); g_A = warp_sum(g_A); g_B = warp_sum(g_B);
+                g_C = warp_sum(g_C); g_o = warp_sum(g_o); g_r = warp_sum(g_r); g_g = warp_sum(g_g);
+                g_b = warp_sum(g_b); g_z = warp_sum(g_z);
+                if (lane == 0) {
+                    float *ak = acc + k * kGradStride;
+                    atomicAdd(ak + 0, g_u); atomicAdd(ak + 1, g_v); atomicAdd(ak + 2, g_A); atomicAdd(ak + 3, g_B);
+                    atomicAdd(ak + 4, g_C); atomicAdd(ak + 5, g_o); atomicAdd(ak + 6, g_r); atomicAdd(ak + 7, g_g);
+                    atomicAdd(ak + 8, g_b); atomicAdd(ak + 9, g_z);
+                }
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+            const float4 *ak = reinterpret_cast<const float4 *>(acc + k * kGradStride);
+            const float4 x0 = ak[0], x1 = ak[1], x2 = ak[2];
+            if (x0.x != 0.f || x0.y != 0.f || x0.z != 0.f || x0.w != 0.f || x1.x != 0.f || x1.y != 0.f ||
+                x1.z != 0.f || x1.w != 0.f || x2.x != 0.f || x2.y != 0.f) {
+                float4 *dst = reinterpret_cast<float4 *>(w.d_rec + (size_t)sidx[k] * kGradStride);
+                atomicAdd(dst + 0, x0);
+                atomicAdd(dst + 1, x1);
+                atomicAdd(dst + 2, x2);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// preprocess backward
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_env_b(const Table *tb, int64_t g)
+{
+    int lo = 0, hi = tb->n_envs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tb->env_off[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int SHT>
+__device__ __forceinline__ void load_sh_b(const void *sh, int64_t g, float (&k)[48])
+{
+    if (SHT == GS_SH_F32) {
+        const float4 *p = reinterpret_cast<const float4 *>(sh) + g * 12;
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            const float4 v = __ldg(p + i);
+            k[4 * i] = v.x; k[4 * i + 1] = v.y; k[4 * i + 2] = v.z; k[4 * i + 3] = v.w;
+        }
+    } else {
+        const uint4 *p = reinterpret_cast<const uint4 *>(sh) + g * 6;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const uint4 v = __ldg(p + i);
+            const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (SHT == GS_SH_F16) {
+                    const __half2 h = *reinterpret_cast<const __half2 *>(&u[j]);
+                    const float2 f = __half22float2(h);
+                    k[8 * i + 2 * j] = f.x; k[8 * i + 2 * j + 1] = f.y;
+                } else {
+                    k[8 * i + 2 * j] = __uint_as_float(u[j] << 16);
+                    k[8 * i + 2 * j + 1] = __uint_as_float(u[j] & 0xffff0000u);
+                }
+            }
+        }
+    }
+}
+
+// dL/d(dir) += sum_k grad(Y_k) * w_k for the degree-3 basis.
+__device__ __forceinline__ void sh_dir_vjp(float x, float y, float z, const float (&wk)[16], float &gx, float &gy,
+                                           float &gz)
+{
+    const float xx = x * x, yy = y * y, zz = z * z;
+    gx += -kSH1 * wk[3];
+    gy += -kSH1 * wk[1];
+    gz += kSH1 * wk[2];
+    gx += kSH2a * y * wk[4]; gy += kSH2a * x * wk[4];
+    gy += -kSH2a * z * wk[5]; gz += -kSH2a * y * wk[5];
+    gx += -2.f * kSH2b * x * wk[6]; gy += -2.f * kSH2b * y * wk[6]; gz += 4.f * kSH2b * z * wk[6];
+    gx += -kSH2a * z * wk[7]; gz += -kSH2a * x * wk[7];
+    gx += 2.f * kSH2c * x * wk[8]; gy += -2.f * kSH2c * y * wk[8];
+    gx += -6.f * kSH3a * x * y * wk[9]; gy += -kSH3a * (3.f * xx - 3.f * yy) * wk[9];
+    gx += kSH3b * y * z * wk[10]; gy += kSH3b * x * z * wk[10]; gz += kSH3b * x * y * wk[10];
+    gx += 2.f * kSH3c * x * y * wk[11]; gy += -kSH3c * (4.f * zz - xx - 3.f * yy) * wk[11];
+    gz += -8.f * kSH3c * y * z * wk[11];
+    gx += -6.f * kSH3d * x * z * wk[12]; gy += -6.f * kSH3d * y * z * wk[12];
+    gz += kSH3d * (6.f * zz - 3.f * xx - 3.f * yy) * wk[12];
+    gx += -kSH3c * (4.f * zz - 3.f * xx - yy) * wk[13]; gy += 2.f * kSH3c * x * y * wk[13];
+    gz += -8.f * kSH3c * x * z * wk[13];
+    gx += 2.f * kSH3e * x * z * wk[14]; gy += -2.f * kSH3e * y * z * wk[14]; gz += kSH3e * (xx - yy) * wk[14];
+    gx += -kSH3a * (3.f * xx - 3.f * yy) * wk[15]; gy += 6.f * kSH3a * x * y * wk[15];
+}
+
+struct GaussInB {
+    const float *means, *log_scales, *quats, *ologits, *cov3d;
+    const void *sh;
+};
+
+template <int SHT, bool OVERWRITE>
+__global__ void __launch_bounds__(256) preprocess_backward_kernel(const gs_camera *__restrict__ cams, GaussInB gin,
+                                                                  Ws w, GradOut o)
+{
+    const Table *tb = w.tb;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= tb->n_gauss) return;
+    const int e = find_env_b(tb, g);
+    const int vb = tb->env_view_begin[e], ve = tb->env_view_begin[e + 1];
+    const int64_t local = g - tb->env_off[e];
+    const bool use_cov = gin.cov3d != nullptr && g >= tb->env_cov_begin[e];
+    const float mx = __ldg(gin.means + 3 * g), my = __ldg(gin.means + 3 * g + 1), mz = __ldg(gin.means + 3 * g + 2);
+    float S[6];
+    bool have_sigma = false, any = false, have_sh = false;
+    float gS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float gm0 = 0.f, gm1 = 0.f, gm2 = 0.f, go = 0.f;
+    float gsh[48];
+    float kk[48];
+#pragma unroll
+    for (int i = 0; i < 48; ++i) gsh[i] = 0.f;
+    float op = 0.f;
+    const int W = tb->W, H = tb->H;
+    for (int kv = vb; kv < ve; ++kv) {
+        const int v = tb->env_views[kv];
+        const uint32_t rec = (uint32_t)(tb->view_rec_off[v] + local);
+        if (!((__ldg(w.vis + (rec >> 5)) >> (rec & 31)) & 1u)) continue;
+        const float4 *gr4 = reinterpret_cast<const float4 *>(w.d_rec + (size_t)rec * kGradStride);
+        const float4 r0 = gr4[0], r1 = gr4[1], r2 = gr4[2];
+        // (uc, vc, A, B, C, opacity, r, g, b, z)
+        const float g_u = r0.x, g_v = r0.y, gA = r0.z, gB = r0.w, gC = r1.x, g_op = r1.y, g_r = r1.z, g_g = r1.w,
+                    g_b = r2.x, g_z = r2.y;
+        const gs_camera &cam = cams[v];
+        if (!have_sigma) {
+            if (use_cov) {
+#pragma unroll
+                for (int i = 0; i < 6; ++i) S[i] = __ldg(gin.cov3d + 6 * g + i);
+            } else {
+                const float3 ls = make_float3(__ldg(gin.log_scales + 3 * g), __ldg(gin.log_scales + 3 * g + 1),
+                                              __ldg(gin.log_scales + 3 * g + 2));
+                const float4 q = __ldg(reinterpret_cast<const float4 *>(gin.quats) + g);
+                sigma_from_sq(ls, q, S);
+            }
+            have_sigma = true;
+        }
+        if (!have_sh) {
+            load_sh_b<SHT>(gin.sh, g, kk);
+            op = 1.0f / (1.0f + expf(-__ldg(gin.ologits + g)));
+            have_sh = true;
+        }
+        any = true;
+        const float zk = depth_key(mx, my, mz, cam);
+        Proj pj;
+        project_ewa(mx, my, mz, zk, S, cam, W, H, pj);
+        const float px = pj.px, py = pj.py, pz = pj.pz, ipz = 1.0f / pz, ipz2 = ipz * ipz;
+        float gpx = g_u * cam.fx * ipz, gpy = g_v * cam.fy * ipz;
+        float gpz = -g_u * cam.fx * px * ipz2 - g_v * cam.fy * py * ipz2 + g_z;
+        // conic = (c, -b, a) / det
+        const float a = pj.a, b = pj.b, c = pj.c, det = pj.det, id2 = 1.0f / (det * det);
+        const float ga = (-gA * c * c + gB * b * c - gC * b * b) * id2;
+        const float gb = (2.f * gA * b * c - gB * (a * c + b * b) + 2.f * gC * a * b) * id2;
+        const float gc = (-gA * b * b + gB * a * b - gC * a * a) * id2;
+        const float G00 = ga, G01 = 0.5f * gb, G11 = gc;
+        const float *t = pj.t;
+        // dL/dSigma = T^T G2 T (symmetric)
+        const float h0 = G00 * t[0] + G01 * t[3], h1 = G00 * t[1] + G01 * t[4], h2 = G00 * t[2] + G01 * t[5];
+        const float k0 = G01 * t[0] + G11 * t[3], k1 = G01 * t[1] + G11 * t[4], k2 = G01 * t[2] + G11 * t[5];
+        gS[0] += t[0] * h0 + t[3] * k0;
+        gS[1] += t[0] * h1 + t[3] * k1;
+        gS[2] += t[0] * h2 + t[3] * k2;
+        gS[3] += t[1] * h1 + t[4] * k1;
+        gS[4] += t[1] * h2 + t[4] * k2;
+        gS[5] += t[2] * h2 + t[5] * k2;
+        // dL/dT = 2 G2 T Sigma ; rows x = 0, 1
+        const float TS00 = t[0] * S[0] + t[1] * S[1] + t[2] * S[2], TS01 = t[0] * S[1] + t[1] * S[3] + t[2] * S[4],
+                    TS02 = t[0] * S[2] + t[1] * S[4] + t[2] * S[5];
+        const float TS10 = t[3] * S[0] + t[4] * S[1] + t[5] * S[2], TS11 = t[3] * S[1] + t[4] * S[3] + t[5] * S[4],
+                    TS12 = t[3] * S[2] + t[4] * S[4] + t[5] * S[5];
+        const float gT00 = 2.f * (G00 * TS00 + G01 * TS10), gT01 = 2.f * (G00 * TS01 + G01 * TS11),
+                    gT02 = 2.f * (G00 * TS02 + G01 * TS12);
+        const float gT10 = 2.f * (G01 * TS00 + G11 * TS10), gT11 = 2.f * (G01 * TS01 + G11 * TS11),
+                    gT12 = 2.f * (G01 * TS02 + G11 * TS12);
+        // T = J W: dL/dJ = dL/dT W^T (entries J00, J02, J11, J12)
+        const float gJ00 = gT00 * cam.R[0] + gT01 * cam.R[1] + gT02 * cam.R[2];
+        const float gJ02 = gT00 * cam.R[6] + gT01 * cam.R[7] + gT02 * cam.R[8];
+        const float gJ11 = gT10 * cam.R[3] + gT11 * cam.R[4] + gT12 * cam.R[5];
+        const float gJ12 = gT10 * cam.R[6] + gT11 * cam.R[7] + gT12 * cam.R[8];
+        gpz += -gJ00 * cam.fx * ipz2 - gJ11 * cam.fy * ipz2;
+        if (!pj.clampx) {
+            gpx += -gJ02 * cam.fx * ipz2;
+            gpz += 2.f * gJ02 * cam.fx * px * ipz2 * ipz;
+        } else {
+            gpz += gJ02 * cam.fx * pj.tx * ipz2;
+        }
+        if (!pj.clampy) {
+            gpy += -gJ12 * cam.fy * ipz2;
+            gpz += 2.f * gJ12 * cam.fy * py * ipz2 * ipz;
+        } else {
+            gpz += gJ12 * cam.fy * pj.ty * ipz2;
+        }
+        // p = W d
+        float gd0 = cam.R[0] * gpx + cam.R[3] * gpy + cam.R[6] * gpz;
+        float gd1 = cam.R[1] * gpx + cam.R[4] * gpy + cam.R[7] * gpz;
+        float gd2 = cam.R[2] * gpx + cam.R[5] * gpy + cam.R[8] * gpz;
+        // colour
+        const float dnorm = sqrtf(pj.d0 * pj.d0 + pj.d1 * pj.d1 + pj.d2 * pj.d2), idn = 1.0f / dnorm;
+        const float x = pj.d0 * idn, y = pj.d1 * idn, z = pj.d2 * idn;
+        float Y[16];
+        sh_basis(x, y, z, Y);
+        float gch[3] = {g_r, g_g, g_b};
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float raw = 0.5f;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) raw += Y[i] * kk[3 * i + ch];
+            if (raw < 0.0f) gch[ch] = 0.0f;
+        }
+        float wk[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            gsh[3 * i] += Y[i] * gch[0];
+            gsh[3 * i + 1] += Y[i] * gch[1];
+            gsh[3 * i + 2] += Y[i] * gch[2];
+            wk[i] = kk[3 * i] * gch[0] + kk[3 * i + 1] * gch[1] + kk[3 * i + 2] * gch[2];
+        }
+        float gx = 0.f, gy = 0.f, gz = 0.f;
+        sh_dir_vjp(x, y, z, wk, gx, gy, gz);
+        const float dot = gx * x + gy * y + gz * z;
+        gd0 += (gx - x * dot) * idn;
+        gd1 += (gy - y * dot) * idn;
+        gd2 += (gz - z * dot) * idn;
+        gm0 += gd0;
+        gm1 += gd1;
+        gm2 += gd2;
+        go += g_op;
+    }
+    if (!any) {
+        if (OVERWRITE) {
+            for (int i = 0; i < 3; ++i) o.means[3 * g + i] = 0.f;
+            o.ologits[g] = 0.f;
+            float4 *dsh4 = reinterpret_cast<float4 *>(o.sh + 48 * g);
+#pragma unroll
+            for (int i = 0; i < 12; ++i) dsh4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (use_cov) {
+                if (o.cov3d)
+                    for (int i = 0; i < 6; ++i) o.cov3d[6 * g + i] = 0.f;
+            } else {
+                for (int i = 0; i < 3; ++i) o.log_scales[3 * g + i] = 0.f;
+                reinterpret_cast<float4 *>(o.quats)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        return;
+    }
+    if (OVERWRITE) {
+        o.means[3 * g] = gm0;
+        o.means[3 * g + 1] = gm1;
+        o.means[3 * g + 2] = gm2;
+        o.ologits[g] = go * op * (1.0f - op);
+        float4 *dsh4 = reinterpret_cast<float4 *>(o.sh + 48 * g);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) dsh4[i] = make_float4(gsh[4 * i], gsh[4 * i + 1], gsh[4 * i + 2], gsh[4 * i + 3]);
+    } else {
+        o.means[3 * g] += gm0;
+        o.means[3 * g + 1] += gm1;
+        o.means[3 * g + 2] += gm2;
+        o.ologits[g] += go * op * (1.0f - op);
+        float *dsh = o.sh + 48 * g;
+#pragma unroll
+        for (int i = 0; i < 48; ++i) dsh[i] += gsh[i];
+    }
+    if (use_cov) {
+        if (o.cov3d) {
+            float *dc = o.cov3d + 6 * g;
+            const float v6[6] = {gS[0], 2.f * gS[1], 2.f * gS[2], gS[3], 2.f * gS[4], gS[5]};
+            for (int i = 0; i < 6; ++i) dc[i] = OVERWRITE ? v6[i] : dc[i] + v6[i];
+        }
+        return;
+    }
+    // Sigma = M M^T, M = R diag(s): dL/dM = 2 gS M
+    const float3 ls = make_float3(__ldg(gin.log_scales + 3 * g), __ldg(gin.log_scales + 3 * g + 1),
+                                  __ldg(gin.log_scales + 3 * g + 2));
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(gin.quats) + g);
+    const float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w), iq = 1.0f / qn;
+    const float qw = q.x * iq, qx = q.y * iq, qy = q.z * iq, qz = q.w * iq;
+    float R[9];
+    quat_rot(qw, qx, qy, qz, R);
+    const float sc[3] = {expf(ls.x), expf(ls.y), expf(ls.z)};
+    const float Gs[9] = {gS[0], gS[1], gS[2], gS[1], gS[3], gS[4], gS[2], gS[4], gS[5]};
+    float gR[9], gsv[3];
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+        float gscc = 0.f;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            // (gS M)[r][cc] with M[k][cc] = R[k][cc] sc[cc]
+            const float gM = 2.f * (Gs[3 * r] * R[cc] + Gs[3 * r + 1] * R[3 + cc] + Gs[3 * r + 2] * R[6 + cc]) * sc[cc];
+            gscc += gM * R[3 * r + cc];
+            gR[3 * r + cc] = gM * sc[cc];
+        }
+        gsv[cc] = gscc * sc[cc];
+    }
+    for (int i = 0; i < 3; ++i) o.log_scales[3 * g + i] = OVERWRITE ? gsv[i] : o.log_scales[3 * g + i] + gsv[i];
+    const float gw = gR[1] * (-2 * qz) + gR[2] * (2 * qy) + gR[3] * (2 * qz) + gR[5] * (-2 * qx) + gR[6] * (-2 * qy) +
+                     gR[7] * (2 * qx);
+    const float gx = gR[1] * (2 * qy) + gR[2] * (2 * qz) + gR[3] * (2 * qy) + gR[4] * (-4 * qx) + gR[5] * (-2 * qw) +
+                     gR[6] * (2 * qz) + gR[7] * (2 * qw) + gR[8] * (-4 * qx);
+    const float gy = gR[0] * (-4 * qy) + gR[1] * (2 * qx) + gR[2] * (2 * qw) + gR[3] * (2 * qx) + gR[5] * (2 * qz) +
+                     gR[6] * (-2 * qw) + gR[7] * (2 * qz) + gR[8] * (-4 * qy);
+    const float gz = gR[0] * (-4 * qz) + gR[1] * (-2 * qw) + gR[2] * (2 * qx) + gR[3] * (2 * qw) + gR[4] * (-4 * qz) +
+                     gR[5] * (2 * qy) + gR[6] * (2 * qx) + gR[7] * (2 * qy);
+    const float dq = gw * qw + gx * qx + gy * qy + gz * qz;
+    const float4 gq4 = make_float4((gw - qw * dq) * iq, (gx - qx * dq) * iq, (gy - qy * dq) * iq, (gz - qz * dq) * iq);
+    float4 *dqo = reinterpret_cast<float4 *>(o.quats) + g;
+    if (OVERWRITE) {
+        *dqo = gq4;
+    } else {
+        float4 cur = *dqo;
+        *dqo = make_float4(cur.x + gq4.x, cur.y + gq4.y, cur.z + gq4.z, cur.w + gq4.w);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// popcount of the visibility mask (statistics only)
+// ---------------------------------------------------------------------------
+__global__ void count_visible_kernel(Ws w, int64_t n_words)
+{
+    uint32_t c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_words; i += (int64_t)gridDim.x * blockDim.x)
+        c += __popc(w.vis[i]);
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&w.hdr->n_visible, c);
+}
+
+void launch_count_visible(const Ws &w, int64_t n_words, cudaStream_t s)
+{
+    count_visible_kernel<<<256, 256, 0, s>>>(w, n_words);
+}
+
+static int blend_bwd_smem(int batch_depth)
+{
+    return 3 * batch_depth * (int)sizeof(float4) + batch_depth * kGradStride * 4 + batch_depth * 4;
+}
+
+void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,
+                           int threads, int batch_depth, cudaStream_t s)
+{
+    blend_backward_kernel<<<n_bins, threads, blend_bwd_smem(batch_depth), s>>>(cams, w, d_rgb, d_depth);
+}
+
+template <bool OW>
+static void launch_pb(const gs_gaussians *g, const gs_camera *cams, const Ws &w, const GradOut &o, unsigned grid,
+                      cudaStream_t s)
+{
+    GaussInB gin{g->means, g->log_scales, g->quats, g->opacity_logits, g->cov3d, g->sh};
+    switch (g->sh_dtype) {
+    case GS_SH_F16: preprocess_backward_kernel<GS_SH_F16, OW><<<grid, 256, 0, s>>>(cams, gin, w, o); break;
+    case GS_SH_BF16: preprocess_backward_kernel<GS_SH_BF16, OW><<<grid, 256, 0, s>>>(cams, gin, w, o); break;
+    default: preprocess_backward_kernel<GS_SH_F32, OW><<<grid, 256, 0, s>>>(cams, gin, w, o); break;
+    }
+}
+
+void launch_preprocess_backward(const gs_gaussians *g, const gs_camera *cams, const Ws &w, const GradOut &o,
+                                int64_t n, bool overwrite, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (!grid) return;
+    if (overwrite) launch_pb<true>(g, cams, w, o, grid, s);
+    else launch_pb<false>(g, cams, w, o, grid, s);
+}
+
+cudaError_t configure_backward_kernels()
+{
+    return cudaFuncSetAttribute(blend_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, blend_bwd_smem(256));
+}
+
+} // namespace gs

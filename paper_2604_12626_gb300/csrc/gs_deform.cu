@@ -1,0 +1,207 @@
+// gs_deform.cu -- linear blend skinning of canonical avatar Gaussians
+// (Sec. 3.3: a CUDA LBS kernel deforms pre-baked canonical Gaussians to the
+// current SMPL-X pose; Sec. 3.3.1: per-frame joint matrices).
+//
+// deform           one thread per avatar Gaussian: A = sum_k w_k G[avatar][j_k]
+//                  (3x4, weights as given), mean' = A3 mean + a,
+//                  cov' = A3 Sigma A3^T with Sigma = R(q) diag(exp(2 s)) R(q)^T;
+//                  the joint matrices of the CTA's avatar are staged in shared
+//                  memory.  100 bytes of HBM traffic per Gaussian.
+// deform_backward  the adjoint; per-joint gradients are reduced in shared memory
+//                  per CTA (for the CTA's first avatar) before global atomics.
+#include "gs_internal.cuh"
+#include "gs_launch.h"
+
+namespace gs {
+
+constexpr int kMaxJoints = 64;
+
+struct AvIn {
+    const float *means, *log_scales, *quats, *weights;
+    const uint16_t *joint_ids;
+    const int32_t *avatar_of;
+    const int64_t *dest;
+    int64_t m;
+    int32_t n_avatars, n_joints;
+};
+
+// joint ids >= n_joints (a caller error) are clamped so that reads stay in bounds
+__device__ __forceinline__ ushort4 clamp_ids(ushort4 id, int nj)
+{
+    const unsigned short m = (unsigned short)(nj - 1);
+    return make_ushort4(min(id.x, m), min(id.y, m), min(id.z, m), min(id.w, m));
+}
+
+__device__ __forceinline__ int clamp_avatar(int a, int na) { return a < 0 ? 0 : (a >= na ? na - 1 : a); }
+
+__device__ __forceinline__ void blend_matrix(const float *Gs, const ushort4 id, const float4 wt, float (&A)[12])
+{
+    const float *g0 = Gs + 12 * id.x, *g1 = Gs + 12 * id.y, *g2 = Gs + 12 * id.z, *g3 = Gs + 12 * id.w;
+#pragma unroll
+    for (int e = 0; e < 12; ++e) A[e] = wt.x * g0[e] + wt.y * g1[e] + wt.z * g2[e] + wt.w * g3[e];
+}
+
+__global__ void __launch_bounds__(256) deform_kernel(AvIn in, const float *__restrict__ G, float *out_means,
+                                                     float *out_cov)
+{
+    __shared__ float sG[kMaxJoints * 12];
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x;
+    const int64_t i = base + threadIdx.x;
+    const int a0 = clamp_avatar(in.avatar_of[base], in.n_avatars);
+    const int nj12 = in.n_joints * 12;
+    for (int k = threadIdx.x; k < nj12; k += blockDim.x) sG[k] = G[(size_t)a0 * nj12 + k];
+    __syncthreads();
+    if (i >= in.m) return;
+    const int av = clamp_avatar(in.avatar_of[i], in.n_avatars);
+    const float *Gs = av == a0 ? sG : G + (size_t)av * nj12;
+    const ushort4 id = clamp_ids(reinterpret_cast<const ushort4 *>(in.joint_ids)[i], in.n_joints);
+    const float4 wt = reinterpret_cast<const float4 *>(in.weights)[i];
+    float A[12];
+    blend_matrix(Gs, id, wt, A);
+    const float mx = in.means[3 * i], my = in.means[3 * i + 1], mz = in.means[3 * i + 2];
+    const float3 ls = make_float3(in.log_scales[3 * i], in.log_scales[3 * i + 1], in.log_scales[3 * i + 2]);
+    const float4 q = reinterpret_cast<const float4 *>(in.quats)[i];
+    float S[6];
+    sigma_from_sq(ls, q, S);
+    const float Sf[9] = {S[0], S[1], S[2], S[1], S[3], S[4], S[2], S[4], S[5]};
+    float AS[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) AS[3 * r + c] = A[4 * r] * Sf[c] + A[4 * r + 1] * Sf[3 + c] + A[4 * r + 2] * Sf[6 + c];
+    const int64_t d = in.dest ? in.dest[i] : i;
+    out_means[3 * d] = A[0] * mx + A[1] * my + A[2] * mz + A[3];
+    out_means[3 * d + 1] = A[4] * mx + A[5] * my + A[6] * mz + A[7];
+    out_means[3 * d + 2] = A[8] * mx + A[9] * my + A[10] * mz + A[11];
+    float *oc = out_cov + 6 * d;
+    oc[0] = AS[0] * A[0] + AS[1] * A[1] + AS[2] * A[2];
+    oc[1] = AS[0] * A[4] + AS[1] * A[5] + AS[2] * A[6];
+    oc[2] = AS[0] * A[8] + AS[1] * A[9] + AS[2] * A[10];
+    oc[3] = AS[3] * A[4] + AS[4] * A[5] + AS[5] * A[6];
+    oc[4] = AS[3] * A[8] + AS[4] * A[9] + AS[5] * A[10];
+    oc[5] = AS[6] * A[8] + AS[7] * A[9] + AS[8] * A[10];
+}
+
+__global__ void __launch_bounds__(256) deform_backward_kernel(AvIn in, const float *__restrict__ G,
+                                                              const float *__restrict__ d_means,
+                                                              const float *__restrict__ d_cov, float *d_cm,
+                                                              float *d_cls, float *d_cq, float *d_G)
+{
+    __shared__ float sG[kMaxJoints * 12];
+    __shared__ float sdG[kMaxJoints * 12];
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x;
+    const int64_t i = base + threadIdx.x;
+    const int a0 = clamp_avatar(in.avatar_of[base], in.n_avatars);
+    const int nj12 = in.n_joints * 12;
+    for (int k = threadIdx.x; k < nj12; k += blockDim.x) {
+        sG[k] = G[(size_t)a0 * nj12 + k];
+        sdG[k] = 0.0f;
+    }
+    __syncthreads();
+    if (i < in.m) {
+        const int av = clamp_avatar(in.avatar_of[i], in.n_avatars);
+        const float *Gs = av == a0 ? sG : G + (size_t)av * nj12;
+        const ushort4 id = clamp_ids(reinterpret_cast<const ushort4 *>(in.joint_ids)[i], in.n_joints);
+        const float4 wt = reinterpret_cast<const float4 *>(in.weights)[i];
+        float A[12];
+        blend_matrix(Gs, id, wt, A);
+        const float mu[3] = {in.means[3 * i], in.means[3 * i + 1], in.means[3 * i + 2]};
+        const float3 ls = make_float3(in.log_scales[3 * i], in.log_scales[3 * i + 1], in.log_scales[3 * i + 2]);
+        const float4 q = reinterpret_cast<const float4 *>(in.quats)[i];
+        float S6[6];
+        sigma_from_sq(ls, q, S6);
+        const float S[9] = {S6[0], S6[1], S6[2], S6[1], S6[3], S6[4], S6[2], S6[4], S6[5]};
+        const int64_t d = in.dest ? in.dest[i] : i;
+        const float gm[3] = {d_means[3 * d], d_means[3 * d + 1], d_means[3 * d + 2]};
+        const float *gc = d_cov + 6 * d;
+        const float Gm[9] = {gc[0], 0.5f * gc[1], 0.5f * gc[2], 0.5f * gc[1], gc[3], 0.5f * gc[4],
+                             0.5f * gc[2], 0.5f * gc[4], gc[5]};
+        // dL/dA3 = gm mu^T + 2 Gm A3 S ; dL/da = gm
+        float GA[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) GA[3 * r + c] = Gm[3 * r] * A[c] + Gm[3 * r + 1] * A[4 + c] + Gm[3 * r + 2] * A[8 + c];
+        float gA[12];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                gA[4 * r + c] = gm[r] * mu[c] + 2.f * (GA[3 * r] * S[c] + GA[3 * r + 1] * S[3 + c] + GA[3 * r + 2] * S[6 + c]);
+            gA[4 * r + 3] = gm[r];
+        }
+        // dL/dmu_c = A3^T gm
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d_cm[3 * i + c] += A[c] * gm[0] + A[4 + c] * gm[1] + A[8 + c] * gm[2];
+        // dL/dSigma_c = A3^T Gm A3 (symmetric)
+        float gS[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                gS[3 * r + c] = A[r] * GA[c] + A[4 + r] * GA[3 + c] + A[8 + r] * GA[6 + c];
+        // Sigma = M M^T with M = R(q) diag(s)
+        const float iq = 1.0f / sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+        const float qw = q.x * iq, qx = q.y * iq, qy = q.z * iq, qz = q.w * iq;
+        float R[9];
+        quat_rot(qw, qx, qy, qz, R);
+        const float sc[3] = {expf(ls.x), expf(ls.y), expf(ls.z)};
+        float gR[9];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float gsc = 0.f;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const float gM = 2.f * (gS[3 * r] * R[c] + gS[3 * r + 1] * R[3 + c] + gS[3 * r + 2] * R[6 + c]) * sc[c];
+                gsc += gM * R[3 * r + c];
+                gR[3 * r + c] = gM * sc[c];
+            }
+            d_cls[3 * i + c] += gsc * sc[c];
+        }
+        const float gw = gR[1] * (-2 * qz) + gR[2] * (2 * qy) + gR[3] * (2 * qz) + gR[5] * (-2 * qx) +
+                         gR[6] * (-2 * qy) + gR[7] * (2 * qx);
+        const float gx = gR[1] * (2 * qy) + gR[2] * (2 * qz) + gR[3] * (2 * qy) + gR[4] * (-4 * qx) +
+                         gR[5] * (-2 * qw) + gR[6] * (2 * qz) + gR[7] * (2 * qw) + gR[8] * (-4 * qx);
+        const float gy = gR[0] * (-4 * qy) + gR[1] * (2 * qx) + gR[2] * (2 * qw) + gR[3] * (2 * qx) +
+                         gR[5] * (2 * qz) + gR[6] * (-2 * qw) + gR[7] * (2 * qz) + gR[8] * (-4 * qy);
+        const float gz = gR[0] * (-4 * qz) + gR[1] * (-2 * qw) + gR[2] * (2 * qx) + gR[3] * (2 * qw) +
+                         gR[4] * (-4 * qz) + gR[5] * (2 * qy) + gR[6] * (2 * qx) + gR[7] * (2 * qy);
+        const float dq = gw * qw + gx * qx + gy * qy + gz * qz;
+        d_cq[4 * i] += (gw - qw * dq) * iq;
+        d_cq[4 * i + 1] += (gx - qx * dq) * iq;
+        d_cq[4 * i + 2] += (gy - qy * dq) * iq;
+        d_cq[4 * i + 3] += (gz - qz * dq) * iq;
+        // dL/dG[j_k] += w_k dL/dA
+        const int ids[4] = {id.x, id.y, id.z, id.w};
+        const float ws[4] = {wt.x, wt.y, wt.z, wt.w};
+        float *dst = av == a0 ? sdG : d_G + (size_t)av * nj12;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int e = 0; e < 12; ++e) atomicAdd(dst + 12 * ids[k] + e, ws[k] * gA[e]);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nj12; k += blockDim.x)
+        if (sdG[k] != 0.0f) atomicAdd(d_G + (size_t)a0 * nj12 + k, sdG[k]);
+}
+
+static AvIn make_in(const gs_avatars *av)
+{
+    return AvIn{av->means, av->log_scales, av->quats, av->weights, av->joint_ids, av->avatar_of, av->dest,
+                av->m, av->n_avatars, av->n_joints};
+}
+
+void launch_deform(const gs_avatars *av, const float *G, float *out_means, float *out_cov, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)((av->m + 255) / 256);
+    if (grid) deform_kernel<<<grid, 256, 0, s>>>(make_in(av), G, out_means, out_cov);
+}
+
+void launch_deform_backward(const gs_avatars *av, const float *G, const float *d_means, const float *d_cov,
+                            float *d_cm, float *d_cls, float *d_cq, float *d_G, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)((av->m + 255) / 256);
+    if (grid) deform_backward_kernel<<<grid, 256, 0, s>>>(make_in(av), G, d_means, d_cov, d_cm, d_cls, d_cq, d_G);
+}
+
+} // namespace gs

@@ -1,0 +1,564 @@
+// gs_forward.cu -- forward kernels of libgs (sm_103a).
+//
+// One gs_render call runs, on one stream and with no host synchronisation:
+//   setup       batch table -> workspace, counters cleared
+//   preprocess  one thread per Gaussian, looping over the views of its env:
+//               FP32 depth key + near cull, covariance, EWA projection with
+//               0.3 px dilation, conic, radius, exact per-pixel footprint
+//               range, SH-3 colour; writes the 48-byte record, the visibility
+//               bit and one bin-count increment per touched tile
+//   scan        exclusive scan of the bin counts -> tile ranges [start, end)
+//   scatter     one (depth key << 32 | record) key per touched tile, placed in
+//               its bin by an atomic cursor (order inside a bin is arbitrary)
+//   sort        each bin sorted by key = (FP32 depth bits, record index), so the
+//               result equals a stable sort of the keys emitted in record order;
+//               <= 4096 keys: bitonic sort in shared memory, one CTA per bin;
+//               larger bins: 16384-key shared-memory chunks + merge-path merges
+//   blend       one CTA per (view, tile) -- or a persistent grid pulling tiles
+//               from an atomic queue -- stages batches of records in shared
+//               memory and blends front to back per pixel with block-wide early
+//               exit once every pixel of the tile has stopped.
+// The rasterisation follows the 3DGS method the paper builds its renderer on
+// (Sec. 2.2, Sec. 3.2); the exact definition is the one in include/gs.h.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "gs_internal.cuh"
+#include "gs_launch.h"
+
+namespace gs {
+
+// ---------------------------------------------------------------------------
+// setup
+// ---------------------------------------------------------------------------
+__global__ void setup_kernel(const Table tb, Ws w)
+{
+    const int32_t *src = reinterpret_cast<const int32_t *>(&tb);
+    int32_t *dst = reinterpret_cast<int32_t *>(w.tb);
+    const int n = (int)(sizeof(Table) / 4);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+    uint32_t *h = reinterpret_cast<uint32_t *>(w.hdr);
+    for (int i = threadIdx.x; i < (int)(sizeof(Header) / 4); i += blockDim.x) h[i] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// preprocess
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_env(const Table *tb, int64_t g)
+{
+    int lo = 0, hi = tb->n_envs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tb->env_off[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int SHT>
+__device__ __forceinline__ void load_sh(const void *sh, int64_t g, float (&k)[48])
+{
+    if (SHT == GS_SH_F32) {
+        const float4 *p = reinterpret_cast<const float4 *>(sh) + g * 12;
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            float4 v = __ldg(p + i);
+            k[4 * i] = v.x; k[4 * i + 1] = v.y; k[4 * i + 2] = v.z; k[4 * i + 3] = v.w;
+        }
+    } else {
+        const uint4 *p = reinterpret_cast<const uint4 *>(sh) + g * 6;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            uint4 v = __ldg(p + i);
+            uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (SHT == GS_SH_F16) {
+                    __half2 h = *reinterpret_cast<__half2 *>(&u[j]);
+                    float2 f = __half22float2(h);
+                    k[8 * i + 2 * j] = f.x; k[8 * i + 2 * j + 1] = f.y;
+                } else {
+                    k[8 * i + 2 * j] = __uint_as_float(u[j] << 16);
+                    k[8 * i + 2 * j + 1] = __uint_as_float(u[j] & 0xffff0000u);
+                }
+            }
+        }
+    }
+}
+
+struct GaussIn {
+    const float *means, *log_scales, *quats, *ologits, *cov3d;
+    const void *sh;
+};
+
+template <int SHT>
+__global__ void __launch_bounds__(256) preprocess_kernel(const gs_camera *__restrict__ cams, GaussIn gin, Ws w)
+{
+    const Table *tb = w.tb;
+    const int64_t N = tb->n_gauss;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = g < N;
+    const int lane = threadIdx.x & 31;
+    int e = 0, nv = 0, vb = 0;
+    int64_t local = 0;
+    float mx = 0.f, my = 0.f, mz = 0.f;
+    if (valid) {
+        e = find_env(tb, g);
+        vb = tb->env_view_begin[e];
+        nv = tb->env_view_begin[e + 1] - vb;
+        local = g - tb->env_off[e];
+        mx = __ldg(gin.means + 3 * g);
+        my = __ldg(gin.means + 3 * g + 1);
+        mz = __ldg(gin.means + 3 * g + 2);
+    }
+    const int nv_max = __reduce_max_sync(0xffffffffu, nv);
+    const int W = tb->W, H = tb->H, tw = tb->tile_w, th = tb->tile_h, tx_n = tb->tiles_x;
+    const float near_plane = tb->near_plane;
+    bool have_sigma = false;
+    float S[6];
+    for (int k = 0; k < nv_max; ++k) {
+        bool vis = false;
+        uint32_t rec = 0;
+        if (k < nv) {
+            const int v = tb->env_views[vb + k];
+            const gs_camera cam = cams[v];
+            const float zk = depth_key(mx, my, mz, cam);
+            if (zk > near_plane) {
+                if (!have_sigma) {
+                    if (gin.cov3d && g >= tb->env_cov_begin[e]) {
+#pragma unroll
+                        for (int i = 0; i < 6; ++i) S[i] = __ldg(gin.cov3d + 6 * g + i);
+                    } else {
+                        float3 ls = make_float3(__ldg(gin.log_scales + 3 * g), __ldg(gin.log_scales + 3 * g + 1),
+                                                __ldg(gin.log_scales + 3 * g + 2));
+                        float4 q = __ldg(reinterpret_cast<const float4 *>(gin.quats) + g);
+                        sigma_from_sq(ls, q, S);
+                    }
+                    have_sigma = true;
+                }
+                Proj pj;
+                const bool ok = project_ewa(mx, my, mz, zk, S, cam, W, H, pj);
+                if (ok) {
+                    const float idet = 1.0f / pj.det;
+                    const float r = radius_px(pj);
+                    int x0, x1, y0, y1;
+                    if (pixel_range(pj.uc, r, cam.cx, W, x0, x1) && pixel_range(pj.vc, r, cam.cy, H, y0, y1)) {
+                        vis = true;
+                        rec = (uint32_t)(tb->view_rec_off[v] + local);
+                        float kk[48], Y[16];
+                        load_sh<SHT>(gin.sh, g, kk);
+                        const float dn = 1.0f / sqrtf(pj.d0 * pj.d0 + pj.d1 * pj.d1 + pj.d2 * pj.d2);
+                        sh_basis(pj.d0 * dn, pj.d1 * dn, pj.d2 * dn, Y);
+                        float col[3];
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) {
+                            float acc = 0.5f;
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) acc += Y[i] * kk[3 * i + ch];
+                            col[ch] = fmaxf(acc, 0.0f);
+                        }
+                        const float op = 1.0f / (1.0f + expf(-__ldg(gin.ologits + g)));
+                        float4 *dst = w.rec + 3 * (size_t)rec;
+                        dst[0] = make_float4(pj.uc, pj.vc, zk, r);
+                        dst[1] = make_float4(pj.c * idet, -pj.b * idet, pj.a * idet, op);
+                        dst[2] = make_float4(col[0], col[1], col[2], 0.0f);
+                        const int bx0 = x0 / tw, bx1 = x1 / tw, by0 = y0 / th, by1 = y1 / th;
+                        uint32_t *bc = w.bin_count + (size_t)v * tb->tiles_per_view;
+                        for (int by = by0; by <= by1; ++by)
+                            for (int bx = bx0; bx <= bx1; ++bx) atomicAdd(bc + by * tx_n + bx, 1u);
+                    }
+                }
+            }
+        }
+        // visibility bit, aggregated over the lanes that share a word
+        const uint32_t word = vis ? (rec >> 5) : 0xffffffffu;
+        const unsigned grp = __match_any_sync(0xffffffffu, word);
+        const uint32_t bits = __reduce_or_sync(grp, vis ? (1u << (rec & 31)) : 0u);
+        const int leader = __ffs(grp) - 1;
+        if (vis && leader == lane) atomicOr(w.vis + word, bits);
+        const unsigned nvis = __popc(__ballot_sync(0xffffffffu, vis));
+        if (lane == 0 && nvis) atomicAdd(&w.hdr->n_visible, nvis);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// scan of the bin counts (single CTA, any number of bins)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) scan_bins_kernel(Ws w)
+{
+    const int nb = w.tb->n_bins;
+    const int T = blockDim.x;
+    const int per = (nb + T - 1) / T;
+    const int b0 = min(nb, (int)threadIdx.x * per), b1 = min(b0 + per, nb);
+    unsigned long long s = 0;
+    uint32_t mx = 0;
+    for (int i = b0; i < b1; ++i) {
+        const uint32_t c = w.bin_count[i];
+        s += c;
+        mx = max(mx, c);
+    }
+    __shared__ unsigned long long sh[1024];
+    __shared__ uint32_t smax[32];
+    sh[threadIdx.x] = s;
+    const uint32_t m = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    for (int off = 1; off < T; off <<= 1) { // Hillis-Steele inclusive scan
+        const unsigned long long v = threadIdx.x >= off ? sh[threadIdx.x - off] : 0ull;
+        __syncthreads();
+        sh[threadIdx.x] += v;
+        __syncthreads();
+    }
+    // pair counts beyond the capacity (or 32 bits) are clamped: every bin range
+    // stays inside [0, capacity) and the status word records the overflow
+    const unsigned long long cap = (unsigned long long)w.tb->pair_capacity;
+    unsigned long long run = sh[threadIdx.x] - s; // exclusive
+    for (int i = b0; i < b1; ++i) {
+        w.bin_start[i] = (uint32_t)min(run, cap);
+        run += w.bin_count[i];
+    }
+    if (threadIdx.x == T - 1) {
+        const unsigned long long total = sh[T - 1];
+        w.bin_start[nb] = (uint32_t)min(total, cap);
+        w.hdr->n_pairs = (uint32_t)min(total, 0xffffffffull);
+        if (total > cap) set_status(w.hdr, GS_ERR_CAPACITY);
+    }
+    if (threadIdx.x < 32) {
+        uint32_t v = threadIdx.x < (unsigned)(T >> 5) ? smax[threadIdx.x] : 0u;
+        v = __reduce_max_sync(0xffffffffu, v);
+        if (threadIdx.x == 0) w.hdr->max_bin = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// scatter: one key per (visible record, touched tile)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) scatter_kernel(const gs_camera *__restrict__ cams, Ws w)
+{
+    const Table *tb = w.tb;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= tb->n_gauss) return;
+    const int e = find_env(tb, g);
+    const int vb = tb->env_view_begin[e], ve = tb->env_view_begin[e + 1];
+    const int64_t local = g - tb->env_off[e];
+    const int W = tb->W, H = tb->H, tw = tb->tile_w, th = tb->tile_h, tx_n = tb->tiles_x;
+    const uint64_t cap = (uint64_t)tb->pair_capacity;
+    for (int k = vb; k < ve; ++k) {
+        const int v = tb->env_views[k];
+        const uint32_t rec = (uint32_t)(tb->view_rec_off[v] + local);
+        if (!((__ldg(w.vis + (rec >> 5)) >> (rec & 31)) & 1u)) continue;
+        const float4 r0 = w.rec[3 * (size_t)rec];
+        const gs_camera &cam = cams[v];
+        int x0, x1, y0, y1;
+        if (!(pixel_range(r0.x, r0.w, cam.cx, W, x0, x1) && pixel_range(r0.y, r0.w, cam.cy, H, y0, y1))) continue;
+        const unsigned long long key = ((unsigned long long)__float_as_uint(r0.z) << 32) | rec;
+        const int bx0 = x0 / tw, bx1 = x1 / tw, by0 = y0 / th, by1 = y1 / th;
+        const size_t bbase = (size_t)v * tb->tiles_per_view;
+        for (int by = by0; by <= by1; ++by)
+            for (int bx = bx0; bx <= bx1; ++bx) {
+                const size_t bin = bbase + by * tx_n + bx;
+                const uint64_t slot = (uint64_t)w.bin_start[bin] + atomicAdd(w.bin_cursor + bin, 1u);
+                if (slot < (uint64_t)w.bin_start[bin + 1] && slot < cap) w.keys[slot] = key;
+            }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-bin sort
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void bin_range(const Ws &w, int bin, uint32_t &start, uint32_t &n)
+{
+    const uint64_t cap = (uint64_t)w.tb->pair_capacity;
+    uint64_t s = w.bin_start[bin], e = w.bin_start[bin + 1];
+    if (e > cap) e = cap;
+    if (s > e) s = e;
+    start = (uint32_t)s;
+    n = (uint32_t)(e - s);
+}
+
+// Bitonic sort of s[0..m) (m a power of two) by the whole CTA.
+__device__ __forceinline__ void bitonic_smem(unsigned long long *s, int m)
+{
+    const int half = m >> 1;
+    for (int k = 2; k <= m; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int p = threadIdx.x; p < half; p += blockDim.x) {
+                const int i = ((p & ~(j - 1)) << 1) | (p & (j - 1));
+                const int l = i | j;
+                const bool up = (i & k) == 0;
+                const unsigned long long a = s[i], b = s[l];
+                if ((a > b) == up) {
+                    s[i] = b;
+                    s[l] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__device__ __forceinline__ int pow2_at_least(uint32_t n)
+{
+    int m = 1;
+    while ((uint32_t)m < n) m <<= 1;
+    return m;
+}
+
+constexpr int kSmallSort = 4096;
+constexpr int kBigSort = 16384;
+
+__global__ void __launch_bounds__(256) sort_small_kernel(Ws w)
+{
+    extern __shared__ unsigned long long smem_keys[];
+    const int bin = blockIdx.x;
+    uint32_t start, n;
+    bin_range(w, bin, start, n);
+    if (n <= 1) return;
+    if (n > (uint32_t)kSmallSort) {
+        if (threadIdx.x == 0) w.big_list[atomicAdd(&w.hdr->n_big, 1u)] = (uint32_t)bin;
+        return;
+    }
+    const int m = pow2_at_least(n);
+    unsigned long long *src = w.keys + start;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) smem_keys[i] = i < (int)n ? src[i] : ~0ull;
+    __syncthreads();
+    bitonic_smem(smem_keys, m);
+    for (int i = threadIdx.x; i < (int)n; i += blockDim.x) src[i] = smem_keys[i];
+}
+
+// Merge sorted a[0..na) and b[0..nb) into d (keys unique), whole CTA.
+__device__ void merge_cta(const unsigned long long *a, uint32_t na, const unsigned long long *b, uint32_t nb,
+                          unsigned long long *d)
+{
+    const uint32_t total = na + nb;
+    const uint32_t per = (total + blockDim.x - 1) / blockDim.x;
+    const uint32_t d0 = min(total, threadIdx.x * per), d1 = min(total, d0 + per);
+    if (d0 >= d1) return;
+    uint32_t lo = d0 > nb ? d0 - nb : 0, hi = min(d0, na);
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] < b[d0 - 1 - mid]) lo = mid + 1;
+        else hi = mid;
+    }
+    uint32_t i = lo, j = d0 - lo;
+    for (uint32_t o = d0; o < d1; ++o) {
+        const bool take_a = j >= nb || (i < na && a[i] < b[j]);
+        d[o] = take_a ? a[i++] : b[j++];
+    }
+}
+
+__global__ void __launch_bounds__(1024) sort_big_kernel(Ws w)
+{
+    extern __shared__ unsigned long long smem_keys[];
+    __shared__ uint32_t item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item = atomicAdd(&w.hdr->big_queue, 1u);
+        __syncthreads();
+        if (item >= w.hdr->n_big) break;
+        const int bin = (int)w.big_list[item];
+        uint32_t start, n;
+        bin_range(w, bin, start, n);
+        unsigned long long *keys = w.keys + start;
+        // sort chunks of kBigSort in shared memory
+        for (uint32_t c0 = 0; c0 < n; c0 += kBigSort) {
+            const uint32_t cn = min((uint32_t)kBigSort, n - c0);
+            const int m = pow2_at_least(cn);
+            for (int i = threadIdx.x; i < m; i += blockDim.x) smem_keys[i] = i < (int)cn ? keys[c0 + i] : ~0ull;
+            __syncthreads();
+            bitonic_smem(smem_keys, m);
+            for (int i = threadIdx.x; i < (int)cn; i += blockDim.x) keys[c0 + i] = smem_keys[i];
+            __syncthreads();
+        }
+        // merge runs, ping-ponging with the scratch buffer
+        unsigned long long *src = keys, *dst = w.scratch + start;
+        for (uint32_t width = kBigSort; width < n; width <<= 1) {
+            for (uint32_t lo = 0; lo < n; lo += 2 * width) {
+                const uint32_t mid = min(lo + width, n), hi = min(lo + 2 * width, n);
+                merge_cta(src + lo, mid - lo, src + mid, hi - mid, dst + lo);
+            }
+            __syncthreads();
+            unsigned long long *t = src;
+            src = dst;
+            dst = t;
+        }
+        if (src != keys) {
+            for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) keys[i] = src[i];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// blend
+// ---------------------------------------------------------------------------
+struct OutPtrs {
+    float *rgb, *depth, *T;
+    int32_t *ncontrib;
+};
+
+__device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, const OutPtrs &o, int bin,
+                                          float4 *s0, float4 *s1, float4 *s2)
+{
+    const Table *tb = w.tb;
+    const int v = bin / tb->tiles_per_view;
+    const int t = bin - v * tb->tiles_per_view;
+    const int tyi = t / tb->tiles_x, txi = t - tyi * tb->tiles_x;
+    const int lx = threadIdx.x % tb->tile_w, ly = threadIdx.x / tb->tile_w;
+    const int i = txi * tb->tile_w + lx, j = tyi * tb->tile_h + ly;
+    const int W = tb->W, H = tb->H;
+    const bool inside = i < W && j < H;
+    const gs_camera &cam = cams[v];
+    const float pxc = pix_c(i, cam.cx), pyc = pix_c(j, cam.cy);
+    uint32_t start, n;
+    bin_range(w, bin, start, n);
+    const unsigned long long *keys = w.keys + start;
+    const int B = tb->batch_depth;
+    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, D = 0.0f;
+    int32_t ncov = 0, ncon = 0;
+    uint32_t last = 0;
+    bool done = !inside;
+    for (uint32_t base = 0; base < n; base += B) {
+        if (__syncthreads_count(done) == (int)blockDim.x) break;
+        const int cnt = (int)min((uint32_t)B, n - base);
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+            uint32_t rec = (uint32_t)keys[base + k];
+            if (rec >= (uint32_t)tb->n_records) rec = 0; // only after a capacity overflow
+            const float4 *src = w.rec + 3 * (size_t)rec;
+            s0[k] = src[0];
+            s1[k] = src[1];
+            s2[k] = src[2];
+        }
+        __syncthreads();
+        if (!done) {
+            for (int k = 0; k < cnt; ++k) {
+                const float4 a = s0[k];
+                const float dx = __fsub_rn(a.x, pxc), dy = __fsub_rn(a.y, pyc);
+                if (fmaxf(fabsf(dx), fabsf(dy)) > a.w) continue;
+                ++ncov;
+                const float4 q = s1[k];
+                const float power = gauss_power(q.x, q.y, q.z, dx, dy);
+                if (power > 0.0f) continue;
+                const float alpha = fminf(kAlphaMax, raw_alpha(q.w, power));
+                if (alpha < kAlphaMin) continue;
+                const float Tn = T * (1.0f - alpha);
+                if (Tn < kTStop) {
+                    done = true;
+                    break;
+                }
+                const float wgt = alpha * T;
+                const float4 c = s2[k];
+                C0 += c.x * wgt;
+                C1 += c.y * wgt;
+                C2 += c.z * wgt;
+                D += a.z * wgt;
+                T = Tn;
+                ncon = ncov;
+                last = base + k + 1;
+            }
+        }
+    }
+    if (inside) {
+        const size_t HW = (size_t)W * H;
+        const size_t p = (size_t)j * W + i;
+        o.rgb[(3 * (size_t)v + 0) * HW + p] = C0 + T * tb->bg[0];
+        o.rgb[(3 * (size_t)v + 1) * HW + p] = C1 + T * tb->bg[1];
+        o.rgb[(3 * (size_t)v + 2) * HW + p] = C2 + T * tb->bg[2];
+        float dd = D;
+        if (tb->flags & GS_FLAG_NORMALIZE_DEPTH) dd = (1.0f - T) < 1e-4f ? 0.0f : D / (1.0f - T);
+        o.depth[(size_t)v * HW + p] = dd;
+        o.T[(size_t)v * HW + p] = T;
+        o.ncontrib[(size_t)v * HW + p] = ncon;
+        w.pix_T[(size_t)v * HW + p] = T;
+        w.pix_last[(size_t)v * HW + p] = last;
+    }
+}
+
+__global__ void blend_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
+{
+    extern __shared__ float4 smem_f4[];
+    const int B = w.tb->batch_depth;
+    float4 *s0 = smem_f4, *s1 = smem_f4 + B, *s2 = smem_f4 + 2 * B;
+    blend_tile(w, cams, o, blockIdx.x, s0, s1, s2);
+}
+
+__global__ void blend_persistent_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
+{
+    extern __shared__ float4 smem_f4[];
+    __shared__ uint32_t item;
+    const int B = w.tb->batch_depth;
+    float4 *s0 = smem_f4, *s1 = smem_f4 + B, *s2 = smem_f4 + 2 * B;
+    const uint32_t nb = (uint32_t)w.tb->n_bins;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item = atomicAdd(&w.hdr->queue, 1u);
+        __syncthreads();
+        if (item >= nb) break;
+        blend_tile(w, cams, o, (int)item, s0, s1, s2);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers
+// ---------------------------------------------------------------------------
+void launch_setup(const Table &tb, const Ws &w, cudaStream_t s) { setup_kernel<<<1, 256, 0, s>>>(tb, w); }
+
+void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w, int64_t n, cudaStream_t s)
+{
+    GaussIn gin{g->means, g->log_scales, g->quats, g->opacity_logits, g->cov3d, g->sh};
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (grid == 0) return;
+    switch (g->sh_dtype) {
+    case GS_SH_F16: preprocess_kernel<GS_SH_F16><<<grid, 256, 0, s>>>(cams, gin, w); break;
+    case GS_SH_BF16: preprocess_kernel<GS_SH_BF16><<<grid, 256, 0, s>>>(cams, gin, w); break;
+    default: preprocess_kernel<GS_SH_F32><<<grid, 256, 0, s>>>(cams, gin, w); break;
+    }
+}
+
+void launch_scan(const Ws &w, cudaStream_t s) { scan_bins_kernel<<<1, 1024, 0, s>>>(w); }
+
+void launch_scatter(const gs_camera *cams, const Ws &w, int64_t n, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (grid) scatter_kernel<<<grid, 256, 0, s>>>(cams, w);
+}
+
+int sort_big_smem_bytes() { return kBigSort * 8; }
+
+void launch_sort_small(const Ws &w, int n_bins, cudaStream_t s)
+{
+    sort_small_kernel<<<n_bins, 256, kSmallSort * 8, s>>>(w);
+}
+
+void launch_sort_big(const Ws &w, int n_sms, cudaStream_t s)
+{
+    sort_big_kernel<<<n_sms, 1024, kBigSort * 8, s>>>(w);
+}
+
+int blend_smem_bytes(int batch_depth) { return 3 * batch_depth * (int)sizeof(float4); }
+
+void launch_blend(const gs_camera *cams, const Ws &w, float *rgb, float *depth, float *T, int32_t *ncontrib,
+                  int n_bins, int threads, int batch_depth, bool persistent, int persistent_grid, cudaStream_t s)
+{
+    OutPtrs o{rgb, depth, T, ncontrib};
+    const int smem = blend_smem_bytes(batch_depth);
+    if (persistent)
+        blend_persistent_kernel<<<persistent_grid, threads, smem, s>>>(cams, w, o);
+    else
+        blend_kernel<<<n_bins, threads, smem, s>>>(cams, w, o);
+}
+
+cudaError_t configure_forward_kernels()
+{
+    cudaError_t e = cudaFuncSetAttribute(sort_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBigSort * 8);
+    if (e != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+int blend_blocks_per_sm(int threads, int batch_depth)
+{
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blend_persistent_kernel, threads, blend_smem_bytes(batch_depth));
+    return nb > 0 ? nb : 1;
+}
+
+} // namespace gs

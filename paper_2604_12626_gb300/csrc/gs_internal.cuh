@@ -1,0 +1,246 @@
+// gs_internal.cuh -- device-side data layout and the helpers every kernel of
+// libgs shares.  Not part of the C ABI.
+//
+// Workspace layout (all sections 256-byte aligned, sizes from the batch):
+//   Header      device counters and the sticky status word
+//   Table       the batch structure (env/view offsets), written by setup
+//   rec         [R] Record (48 B): (uc, vc, z, r) (A, B, C, opacity) (r, g, b, 0)
+//               R = sum over views of the Gaussians of the view's env
+//   vis         [R/32] visibility bitmask of the records
+//   bin_count   [B] pairs per (view, tile) bin, B = V * tiles
+//   bin_start   [B+1] exclusive scan of bin_count (tile ranges)
+//   bin_cursor  [B] scatter cursors
+//   big_list    [B] bins sorted by the large-bin path
+//   keys        [P_cap] uint64 (FP32 depth bits << 32 | record index)
+//   scratch     [P_cap] uint64, merge buffer of the large-bin sort
+//   pix_T       [V*H*W] final transmittance (saved for the backward)
+//   pix_last    [V*H*W] 1 + tile-list position of the last blended pair
+//   d_rec       [R] 12 floats: dL/d(uc, vc, A, B, C, opacity, r, g, b, z)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs.h"
+
+namespace gs {
+
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTStop = 1e-4f;
+constexpr float kDilation = 0.3f;
+
+struct Header {
+    int32_t status;     // sticky GS_ERR_* (0 = ok)
+    uint32_t n_visible; // visible records
+    uint32_t n_pairs;   // total pairs (before capacity clamp)
+    uint32_t max_bin;   // largest bin
+    uint32_t n_big;     // bins routed to the large-bin sort
+    uint32_t queue;     // persistent blend work counter
+    uint32_t queue_bwd; // persistent backward work counter
+    uint32_t big_queue; // large-bin sort work counter
+    uint32_t pad[56];
+};
+
+struct Table {
+    int32_t n_envs, n_views;
+    int32_t W, H, tile_w, tile_h, tiles_x, tiles_y, tiles_per_view, n_bins;
+    int32_t batch_depth, flags;
+    int64_t n_records, pair_capacity, n_gauss;
+    float bg[3];
+    float near_plane;
+    int64_t env_off[GS_MAX_ENVS + 1];
+    int64_t env_cov_begin[GS_MAX_ENVS];
+    int64_t view_rec_off[GS_MAX_VIEWS + 1];
+    int32_t view_env[GS_MAX_VIEWS];
+    int32_t env_view_begin[GS_MAX_ENVS + 1];
+    int32_t env_views[GS_MAX_VIEWS];
+};
+
+struct Ws {
+    Header *hdr;
+    Table *tb;
+    float4 *rec;  // 3 float4 per record
+    uint32_t *vis;
+    uint32_t *bin_count, *bin_start, *bin_cursor, *big_list;
+    unsigned long long *keys, *scratch;
+    float *pix_T;
+    uint32_t *pix_last;
+    float *d_rec; // 12 floats per record
+};
+
+// ---------------------------------------------------------------------------
+// Decisions both the forward and the backward take; written with explicit
+// round-to-nearest intrinsics so that every kernel gets the same bits.
+// ---------------------------------------------------------------------------
+
+// FP32 view depth: fl(fl(fl(R20 d0) + fl(R21 d1)) + fl(R22 d2)), d = fl(mu - C).
+__device__ __forceinline__ float depth_key(float mx, float my, float mz, const gs_camera &c)
+{
+    float d0 = __fsub_rn(mx, c.C[0]);
+    float d1 = __fsub_rn(my, c.C[1]);
+    float d2 = __fsub_rn(mz, c.C[2]);
+    float s = __fadd_rn(__fmul_rn(c.R[6], d0), __fmul_rn(c.R[7], d1));
+    return __fadd_rn(s, __fmul_rn(c.R[8], d2));
+}
+
+// Pixel coordinate relative to the principal point.
+__device__ __forceinline__ float pix_c(int i, float c) { return __fsub_rn((float)i, c); }
+
+// Square footprint: pixel covered iff |uc - pxc| <= r (and the same in y).
+__device__ __forceinline__ bool covers1(float uc, float r, float pxc) { return fabsf(__fsub_rn(uc, pxc)) <= r; }
+
+// Smallest and largest i in [0, n) covered in one axis; false when none.
+__device__ __forceinline__ bool pixel_range(float uc, float r, float c, int n, int &lo, int &hi)
+{
+    float g = fminf(fmaxf(uc + c - r, -1.0f), (float)n + 1.0f);
+    int a = (int)ceilf(g);
+    a = a < 0 ? 0 : (a > n ? n : a);
+#pragma unroll 1
+    for (int k = 0; k < 4 && a > 0 && covers1(uc, r, pix_c(a - 1, c)); ++k) --a;
+#pragma unroll 1
+    for (int k = 0; k < 4 && a < n && !covers1(uc, r, pix_c(a, c)); ++k) ++a;
+    if (a >= n || !covers1(uc, r, pix_c(a, c))) return false;
+    float h = fminf(fmaxf(uc + c + r, -1.0f), (float)n + 1.0f);
+    int b = (int)floorf(h);
+    b = b < a ? a : (b > n - 1 ? n - 1 : b);
+#pragma unroll 1
+    for (int k = 0; k < 4 && b < n - 1 && covers1(uc, r, pix_c(b + 1, c)); ++k) ++b;
+#pragma unroll 1
+    for (int k = 0; k < 4 && b > a && !covers1(uc, r, pix_c(b, c)); ++k) --b;
+    lo = a;
+    hi = b;
+    return true;
+}
+
+// Gaussian falloff exponent at offset (dx, dy) = centre - pixel.
+__device__ __forceinline__ float gauss_power(float A, float B, float C, float dx, float dy)
+{
+    float q = __fmaf_rn(A, __fmul_rn(dx, dx), __fmul_rn(C, __fmul_rn(dy, dy)));
+    return __fmaf_rn(-0.5f, q, -__fmul_rn(B, __fmul_rn(dx, dy)));
+}
+
+// alpha before the clamp; the clamp is min(0.99, .)
+__device__ __forceinline__ float raw_alpha(float opacity, float power) { return __fmul_rn(opacity, __expf(power)); }
+
+__device__ __forceinline__ void set_status(Header *h, int32_t code) { atomicCAS(&h->status, 0, code); }
+
+// ---------------------------------------------------------------------------
+// Projection of one Gaussian into one view (forward and backward share it).
+// ---------------------------------------------------------------------------
+
+// Rotation of the normalised quaternion (w, x, y, z), row-major.
+__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float (&R)[9])
+{
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Sigma = R(q) diag(exp(2 s)) R(q)^T as (xx, xy, xz, yy, yz, zz).
+__device__ __forceinline__ void sigma_from_sq(float3 ls, float4 q, float (&S)[6])
+{
+    const float inv = 1.0f / sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    float R[9];
+    quat_rot(q.x * inv, q.y * inv, q.z * inv, q.w * inv, R);
+    const float s0 = expf(ls.x), s1 = expf(ls.y), s2 = expf(ls.z);
+    float M[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        M[3 * r] = R[3 * r] * s0;
+        M[3 * r + 1] = R[3 * r + 1] * s1;
+        M[3 * r + 2] = R[3 * r + 2] * s2;
+    }
+    S[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+    S[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+    S[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+    S[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+    S[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+    S[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+}
+
+struct Proj {
+    float d0, d1, d2;         // mu - C
+    float px, py, pz;         // view space (pz is the FP32 depth key)
+    float uc, vc;             // fx px/pz, fy py/pz (pixel offset from the principal point)
+    float tx, ty;             // px/pz, py/pz clamped for the Jacobian
+    bool clampx, clampy;
+    float t[6];               // T = J W (2x3)
+    float a, b, c, det;       // dilated 2D covariance, determinant
+};
+
+// EWA projection with the lateral clamp at 1.3 x the half field and the
+// 0.3 px^2 dilation.  Returns false when the conic is singular.
+__device__ __forceinline__ bool project_ewa(float mx, float my, float mz, float zk, const float (&S)[6],
+                                            const gs_camera &cam, int W, int H, Proj &p)
+{
+    p.d0 = __fsub_rn(mx, cam.C[0]);
+    p.d1 = __fsub_rn(my, cam.C[1]);
+    p.d2 = __fsub_rn(mz, cam.C[2]);
+    p.px = cam.R[0] * p.d0 + cam.R[1] * p.d1 + cam.R[2] * p.d2;
+    p.py = cam.R[3] * p.d0 + cam.R[4] * p.d1 + cam.R[5] * p.d2;
+    p.pz = zk;
+    const float izx = p.px / p.pz, izy = p.py / p.pz;
+    p.uc = cam.fx * izx;
+    p.vc = cam.fy * izy;
+    const float limx = 1.3f * (0.5f * (float)W / cam.fx), limy = 1.3f * (0.5f * (float)H / cam.fy);
+    p.clampx = izx < -limx || izx > limx;
+    p.clampy = izy < -limy || izy > limy;
+    p.tx = fminf(limx, fmaxf(-limx, izx));
+    p.ty = fminf(limy, fmaxf(-limy, izy));
+    const float j00 = cam.fx / p.pz, j02 = -cam.fx * p.tx / p.pz, j11 = cam.fy / p.pz, j12 = -cam.fy * p.ty / p.pz;
+    float *t = p.t;
+    t[0] = j00 * cam.R[0] + j02 * cam.R[6];
+    t[1] = j00 * cam.R[1] + j02 * cam.R[7];
+    t[2] = j00 * cam.R[2] + j02 * cam.R[8];
+    t[3] = j11 * cam.R[3] + j12 * cam.R[6];
+    t[4] = j11 * cam.R[4] + j12 * cam.R[7];
+    t[5] = j11 * cam.R[5] + j12 * cam.R[8];
+    const float u0 = S[0] * t[0] + S[1] * t[1] + S[2] * t[2], u1 = S[1] * t[0] + S[3] * t[1] + S[4] * t[2],
+                u2 = S[2] * t[0] + S[4] * t[1] + S[5] * t[2];
+    const float w0 = S[0] * t[3] + S[1] * t[4] + S[2] * t[5], w1 = S[1] * t[3] + S[3] * t[4] + S[4] * t[5],
+                w2 = S[2] * t[3] + S[4] * t[4] + S[5] * t[5];
+    p.a = t[0] * u0 + t[1] * u1 + t[2] * u2 + kDilation;
+    p.b = t[0] * w0 + t[1] * w1 + t[2] * w2;
+    p.c = t[3] * w0 + t[4] * w1 + t[5] * w2 + kDilation;
+    p.det = p.a * p.c - p.b * p.b;
+    return p.det > 0.0f;
+}
+
+// 3-sigma radius of the dilated 2D covariance, an integer number of pixels.
+__device__ __forceinline__ float radius_px(const Proj &p)
+{
+    const float mid = 0.5f * (p.a + p.c);
+    const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - p.det));
+    return ceilf(3.0f * sqrtf(lam));
+}
+
+// Real SH basis of degree 3 (3DGS ordering and signs) at unit direction (x, y, z).
+constexpr float kSH0 = 0.28209479177387814f;
+constexpr float kSH1 = 0.48860251190291987f;
+constexpr float kSH2a = 1.0925484305920792f, kSH2b = 0.31539156525252005f, kSH2c = 0.54627421529603959f;
+constexpr float kSH3a = 0.59004358992664352f, kSH3b = 2.8906114426405538f, kSH3c = 0.45704579946446572f,
+                kSH3d = 0.3731763325901154f, kSH3e = 1.4453057213202769f;
+
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float (&Y)[16])
+{
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[0] = kSH0;
+    Y[1] = -kSH1 * y;
+    Y[2] = kSH1 * z;
+    Y[3] = -kSH1 * x;
+    Y[4] = kSH2a * x * y;
+    Y[5] = -kSH2a * y * z;
+    Y[6] = kSH2b * (2.0f * zz - xx - yy);
+    Y[7] = -kSH2a * x * z;
+    Y[8] = kSH2c * (xx - yy);
+    Y[9] = -kSH3a * y * (3.0f * xx - yy);
+    Y[10] = kSH3b * x * y * z;
+    Y[11] = -kSH3c * y * (4.0f * zz - xx - yy);
+    Y[12] = kSH3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    Y[13] = -kSH3c * x * (4.0f * zz - xx - yy);
+    Y[14] = kSH3e * z * (xx - yy);
+    Y[15] = -kSH3a * x * (xx - 3.0f * yy);
+}
+
+} // namespace gs

@@ -1,0 +1,36 @@
+// gs_launch.h -- host-side launchers of the kernels (internal to libgs).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+
+cudaError_t configure_forward_kernels();
+cudaError_t configure_backward_kernels();
+
+void launch_setup(const Table &tb, const Ws &w, cudaStream_t s);
+void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w, int64_t n, cudaStream_t s);
+void launch_scan(const Ws &w, cudaStream_t s);
+void launch_scatter(const gs_camera *cams, const Ws &w, int64_t n, cudaStream_t s);
+void launch_sort_small(const Ws &w, int n_bins, cudaStream_t s);
+void launch_sort_big(const Ws &w, int n_sms, cudaStream_t s);
+void launch_blend(const gs_camera *cams, const Ws &w, float *rgb, float *depth, float *T, int32_t *ncontrib,
+                  int n_bins, int threads, int batch_depth, bool persistent, int persistent_grid, cudaStream_t s);
+int blend_blocks_per_sm(int threads, int batch_depth);
+void launch_count_visible(const Ws &w, int64_t n_words, cudaStream_t s);
+
+struct GradOut {
+    float *means, *log_scales, *quats, *ologits, *sh, *cov3d;
+};
+void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,
+                           int threads, int batch_depth, cudaStream_t s);
+void launch_preprocess_backward(const gs_gaussians *g, const gs_camera *cams, const Ws &w, const GradOut &o,
+                                int64_t n, bool overwrite, cudaStream_t s);
+
+void launch_deform(const gs_avatars *av, const float *G, float *out_means, float *out_cov, cudaStream_t s);
+void launch_deform_backward(const gs_avatars *av, const float *G, const float *d_means, const float *d_cov,
+                            float *d_cm, float *d_cls, float *d_cq, float *d_G, cudaStream_t s);
+
+} // namespace gs

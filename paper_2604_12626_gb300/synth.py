@@ -17,6 +17,8 @@ room's floor, walls and ceiling, the rest are furniture-like blobs.
 from __future__ import annotations
 
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -176,12 +178,10 @@ def batched_rooms(n_envs: int = 64, n_min: int = 300_000, n_max: int = 1_500_000
                   seed0: int = 0, scale: float = 1.0):
     """One room per env (env e seeded by seed0 + e) with N_e ~ U{n_min..n_max}
     (times ``scale``), one camera per env.  Returns (arrays, env_offsets, cams)."""
-    scenes, cams = [], []
-    for e in range(n_envs):
-        rng = np.random.default_rng(seed0 + e)
-        n = int(rng.integers(n_min, n_max + 1) * scale)
-        scenes.append(room_scene(max(n, 1), seed=seed0 + e))
-        cams.append(room_camera(seed0 + e, W, H))
+    sizes = batch_sizes(n_envs, n_min, n_max, seed0, scale)
+    with ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 4)) as ex:  # the generators release the GIL
+        scenes = list(ex.map(lambda e: room_scene(sizes[e], seed=seed0 + e), range(n_envs)))
+    cams = [room_camera(seed0 + e, W, H) for e in range(n_envs)]
     g, offs = concat(scenes)
     return g, offs, np.stack(cams)
 

@@ -1,0 +1,203 @@
+"""Adjoint of the CUDA path (gs_render_backward, gs_deform_avatars_backward,
+the autograd Functions) against the FP64 oracle adjoint, which is itself pinned
+to FP64 central finite differences (tests/test_oracle_adjoint.py)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2604_12626_gb300 import synth  # noqa: E402
+
+GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+@pytest.fixture(scope="module")
+def gs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_12626_gb300 import api
+
+    return api
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def gpu_forward_backward(api, g, cams, W, H, d_rgb, d_depth, offs=None, view_env=None, sh_dtype=torch.float32, **kw):
+    n = g["means"].shape[0]
+    offs = np.array([0, n]) if offs is None else offs
+    r = api.Renderer(api.Batch(offs, view_env), W, H, **kw)
+    G = api.Gaussians.from_numpy(g, sh_dtype=sh_dtype)
+    ct = api.cameras_tensor(cams)
+    r.forward(G, ct)
+    gr = r.backward(G, ct, torch.from_numpy(d_rgb).float().cuda(), torch.from_numpy(d_depth).float().cuda())
+    torch.cuda.synchronize()
+    assert r.status() == 0
+    return {k: (v.cpu().numpy() if v is not None else None) for k, v in gr.items()}
+
+
+def oracle_grads(oracle, g, cams, W, H, d_rgb, d_depth, offs=None, view_env=None):
+    n = g["means"].shape[0]
+    offs = np.array([0, n]) if offs is None else offs
+    view_env = np.arange(len(offs) - 1) if view_env is None else np.asarray(view_env)
+    out = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
+               opacity_logits=np.zeros(n), sh=np.zeros((n, 16, 3)))
+    for v, e in enumerate(view_env):
+        sl = slice(offs[e], offs[e + 1])
+        ge = {k: x[sl] for k, x in g.items()}
+        gv = oracle.render_backward(ge, cams[v], W, H, d_rgb[v], d_depth[v])
+        for k in GROUPS:
+            out[k][sl] += gv[k]
+    return out
+
+
+def test_backward_matches_oracle_box_scene(gs, oracle):
+    g = synth.box_scene(3000, seed=0)
+    g["log_scales"] += np.float32(0.7)
+    W = H = 96
+    cam = synth.identity_camera(W, H)
+    rng = np.random.default_rng(0)
+    d_rgb = rng.standard_normal((1, 3, H, W)).astype(np.float32)
+    d_depth = rng.standard_normal((1, H, W)).astype(np.float32)
+    a = gpu_forward_backward(gs, g, cam[None], W, H, d_rgb, d_depth)
+    b = oracle_grads(oracle, g, cam[None], W, H, d_rgb, d_depth)
+    for k in GROUPS:
+        e = rel_l2(a[k], b[k])
+        print(f"box grad {k}: rel L2 {e:.2e}")
+        assert e < 1e-4, (k, e)
+
+
+def test_backward_matches_oracle_room_views(gs, oracle):
+    g = synth.room_scene(120_000, seed=3)
+    W = H = 128
+    cams = np.stack([synth.room_camera(30 + k, W, H) for k in range(3)])
+    rng = np.random.default_rng(1)
+    d_rgb = rng.standard_normal((3, 3, H, W)).astype(np.float32)
+    d_depth = (0.1 * rng.standard_normal((3, H, W))).astype(np.float32)
+    offs = np.array([0, 120_000])
+    a = gpu_forward_backward(gs, g, cams, W, H, d_rgb, d_depth, offs=offs, view_env=[0, 0, 0])
+    b = oracle_grads(oracle, g, cams, W, H, d_rgb, d_depth, offs=offs, view_env=[0, 0, 0])
+    for k in GROUPS:
+        e = rel_l2(a[k], b[k])
+        print(f"room grad {k}: rel L2 {e:.2e}")
+        assert e < 1e-3, (k, e)
+
+
+def test_backward_batched_envs_and_persistent(gs, oracle):
+    g, offs, cams = synth.batched_rooms(n_envs=3, n_min=20_000, n_max=60_000, W=96, H=96, seed0=200)
+    W = H = 96
+    rng = np.random.default_rng(2)
+    d_rgb = rng.standard_normal((3, 3, H, W)).astype(np.float32)
+    d_depth = (0.1 * rng.standard_normal((3, H, W))).astype(np.float32)
+    a = gpu_forward_backward(gs, g, cams, W, H, d_rgb, d_depth, offs=offs, persistent=True)
+    b = oracle_grads(oracle, g, cams, W, H, d_rgb, d_depth, offs=offs)
+    for k in GROUPS:
+        assert rel_l2(a[k], b[k]) < 1e-3, k
+
+
+@pytest.mark.parametrize("dt", ["f16", "bf16"])
+def test_backward_half_sh(gs, oracle, dt):
+    g = synth.box_scene(2000, seed=4)
+    g["log_scales"] += np.float32(0.7)
+    W = H = 64
+    cam = synth.identity_camera(W, H)
+    rng = np.random.default_rng(3)
+    d_rgb = rng.standard_normal((1, 3, H, W)).astype(np.float32)
+    d_depth = rng.standard_normal((1, H, W)).astype(np.float32)
+    tdt = torch.float16 if dt == "f16" else torch.bfloat16
+    a = gpu_forward_backward(gs, g, cam[None], W, H, d_rgb, d_depth, sh_dtype=tdt)
+    gq = dict(g)
+    gq["sh"] = (g["sh"].astype(np.float16).astype(np.float32) if dt == "f16"
+                else synth.bf16_to_f32(synth.bf16_bits(g["sh"])))
+    b = oracle_grads(oracle, gq, cam[None], W, H, d_rgb, d_depth)
+    for k in GROUPS:
+        assert rel_l2(a[k], b[k]) < 1e-4, k
+
+
+def test_autograd_function_l1_loss(gs):
+    g = synth.box_scene(2000, seed=5)
+    g["log_scales"] += np.float32(0.7)
+    W = H = 64
+    cam = synth.identity_camera(W, H)
+    r = gs.Renderer(gs.Batch(np.array([0, 2000])), W, H)
+    ct = gs.cameras_tensor(cam[None])
+    params = {k: torch.from_numpy(np.ascontiguousarray(g[k])).cuda().requires_grad_(True)
+              for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+    target = torch.rand((1, 3, H, W), device="cuda")
+    rgb, depth = gs.render(params["means"], params["log_scales"], params["quats"], params["opacity_logits"],
+                           params["sh"], r, ct)
+    loss = (rgb - target).abs().mean() + 0.1 * depth.mean()
+    loss.backward()
+    d_rgb = (torch.sign(rgb - target) / rgb.numel()).detach()
+    d_depth = torch.full_like(depth, 0.1 / depth.numel())
+    G = gs.Gaussians(*(params[k].detach() for k in ("means", "log_scales", "quats", "opacity_logits", "sh")))
+    r2 = gs.Renderer(gs.Batch(np.array([0, 2000])), W, H)
+    r2.forward(G, ct)
+    ref = r2.backward(G, ct, d_rgb, d_depth)
+    for k in params:
+        torch.testing.assert_close(params[k].grad, ref[k], rtol=1e-5, atol=1e-9)
+
+
+def _avatar_scene(seed, n_scene=100, n_av=100, n_avatars=2):
+    rng = np.random.default_rng(seed)
+    sc = synth.box_scene(n_scene, seed=seed)
+    sc["log_scales"] = rng.normal(-1.6, 0.3, (n_scene, 3)).astype(np.float32)
+    avs = [synth.avatar_canonical(n_av, seed + k) for k in range(n_avatars)]
+    av = {k: np.concatenate([a[k] for a in avs]) for k in avs[0]}
+    av["means"] *= np.float32(0.4)
+    av["log_scales"] = rng.normal(-2.3, 0.3, (n_av * n_avatars, 3)).astype(np.float32)
+    Gm = np.stack([synth.random_pose(seed + k, root_t=[0.3 * k - 0.15, 0.0, 3.0]) for k in range(n_avatars)])
+    # keep the avatars in front of the camera: undo the random root yaw's translation drift
+    Gm = Gm.astype(np.float32)
+    avatar_of = np.repeat(np.arange(n_avatars), n_av).astype(np.int32)
+    return sc, av, Gm, avatar_of
+
+
+def test_scene_with_avatars_forward_backward_vs_oracle(gs, oracle):
+    sc, av, Gm, avatar_of = _avatar_scene(11)
+    ns, m = sc["means"].shape[0], av["means"].shape[0]
+    W = H = 48
+    cam = synth.identity_camera(W, H)
+    # oracle: FP64 LBS then render, adjoint through both
+    pm, pc = oracle.lbs(av["means"], av["log_scales"], av["quats"], av["joint_ids"].astype(np.int32), av["weights"],
+                        avatar_of, Gm.astype(np.float64))
+    gall = dict(means=np.concatenate([sc["means"].astype(np.float64), pm]),
+                log_scales=np.concatenate([sc["log_scales"], np.zeros((m, 3), np.float32)]),
+                quats=np.concatenate([sc["quats"], np.tile(np.float32([1, 0, 0, 0]), (m, 1))]),
+                opacity_logits=np.concatenate([sc["opacity_logits"], av["opacity_logits"]]),
+                sh=np.concatenate([sc["sh"], av["sh"]]), cov3d=np.concatenate([np.zeros((ns, 6)), pc]),
+                use_cov=np.concatenate([np.zeros(ns, np.uint8), np.ones(m, np.uint8)]),
+                inexact=np.concatenate([np.zeros(ns, np.uint8), np.ones(m, np.uint8)]))
+    ora = oracle.render(gall, cam, W, H)
+    rng = np.random.default_rng(4)
+    d_rgb = rng.standard_normal((3, H, W))
+    d_depth = rng.standard_normal((H, W))
+    og = oracle.render_backward(gall, cam, W, H, d_rgb, d_depth)
+    oga = oracle.lbs_backward(av["means"], av["log_scales"], av["quats"], av["joint_ids"].astype(np.int32),
+                              av["weights"], avatar_of, Gm.astype(np.float64), og["means"][ns:], og["cov3d"][ns:])
+    # GPU: autograd through SceneWithAvatarsFunction
+    T = lambda x, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(x)).to("cuda", dt)  # noqa: E731
+    sp = [T(sc[k]).requires_grad_(True) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
+    ap = [T(av[k]).requires_grad_(True) for k in ("means", "log_scales", "quats")]
+    aop, ash = T(av["opacity_logits"]).requires_grad_(True), T(av["sh"]).requires_grad_(True)
+    Gt = T(Gm).requires_grad_(True)
+    static = (T(av["joint_ids"].view(np.int16), torch.int16), T(av["weights"]), T(avatar_of, torch.int32), 2, 24)
+    r = gs.Renderer(gs.Batch(np.array([0, ns + m]), env_cov3d_begin=[ns]), W, H)
+    rgb, depth = gs.SceneWithAvatarsFunction.apply(*sp, *ap, aop, ash, Gt, static, r, gs.cameras_tensor(cam[None]))
+    from helpers import compare_view
+    compare_view(dict(rgb=rgb[0].detach().cpu().numpy(), depth=depth[0].detach().cpu().numpy(),
+                      T=ora["T"], n_contrib=ora["n_contrib"]), ora)
+    loss = (rgb[0] * T(d_rgb)).sum() + (depth[0] * T(d_depth)).sum()
+    loss.backward()
+    pairs = [(sp[0].grad, og["means"][:ns]), (sp[1].grad, og["log_scales"][:ns]), (sp[2].grad, og["quats"][:ns]),
+             (sp[3].grad, og["opacity_logits"][:ns]), (sp[4].grad, og["sh"][:ns]), (ap[0].grad, oga["means"]),
+             (ap[1].grad, oga["log_scales"]), (ap[2].grad, oga["quats"]), (aop.grad, og["opacity_logits"][ns:]),
+             (ash.grad, og["sh"][ns:]), (Gt.grad, oga["G"])]
+    for i, (a, b) in enumerate(pairs):
+        e = rel_l2(a.cpu().numpy(), b)
+        print(f"avatar-scene grad {i}: rel L2 {e:.2e}")
+        assert e < 1e-3, (i, e)

@@ -1,0 +1,215 @@
+"""Forward parity of the CUDA path (through the C ABI) against the FP64 oracle,
+bit-exact tile keys and order against a CPU reference, and the invariances the
+definition implies (tile size, persistent grid, batching)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from helpers import compare_view, gpu_outputs, reference_keys  # noqa: E402
+from paper_2604_12626_gb300 import synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def gs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_12626_gb300 import api
+
+    return api
+
+
+def render_gpu(api, g, cams, W, H, offs=None, view_env=None, sh_dtype=torch.float32, **kw):
+    n = g["means"].shape[0]
+    offs = np.array([0, n]) if offs is None else offs
+    batch = api.Batch(offs, view_env)
+    r = api.Renderer(batch, W, H, **kw)
+    G = api.Gaussians.from_numpy(g, sh_dtype=sh_dtype)
+    ct = api.cameras_tensor(cams)
+    out = r.forward(G, ct)
+    torch.cuda.synchronize()
+    assert r.status() == 0
+    return r, out, G, ct
+
+
+def test_box_scene_matches_oracle_pixel_major(gs, oracle):
+    g = synth.box_scene(5000, seed=0)
+    W = H = 128
+    cam = synth.identity_camera(W, H)
+    r, out, _, _ = render_gpu(gs, g, cam[None], W, H)
+    ora = oracle.render(g, cam, W, H, mode="pixel")
+    st = compare_view(gpu_outputs(out, 0), ora)
+    print("box 5k 128x128:", st)
+    stats = r.stats()
+    assert stats["n_visible"] > 4000 and stats["n_pairs"] >= stats["n_visible"]
+
+
+def _check_keys(r, cams, W, H, view_of_rec):
+    s = r.sections()
+    rec = s["records"].cpu().numpy()
+    vis = s["vis"].cpu().numpy()
+    bs = s["bin_start"].cpu().numpy().astype(np.int64)
+    keys = s["keys"].cpu().numpy().view(np.uint64)
+    counts, ref = reference_keys(rec, vis, view_of_rec, cams, W, H, r.cfg.tile_w, r.cfg.tile_h)
+    n_bins = s["n_bins"]
+    assert np.array_equal(np.diff(bs), counts[:n_bins]), "bin counts (tile ranges) differ"
+    assert np.array_equal(keys[:bs[-1]], ref), "sorted keys differ"
+    return int(bs[-1])
+
+
+def test_box_scene_keys_bit_exact(gs):
+    g = synth.box_scene(5000, seed=0)
+    W = H = 128
+    cam = synth.identity_camera(W, H)
+    r, out, _, _ = render_gpu(gs, g, cam[None], W, H)
+    P = _check_keys(r, cam[None], W, H, np.zeros(5000, np.int64))
+    assert P > 5000
+
+
+@pytest.fixture(scope="module")
+def room1m():
+    g = synth.room_scene(1_000_000, seed=1)
+    cam = synth.room_camera(1, 640, 480)
+    return g, cam
+
+
+def test_room_1m_640x480_matches_oracle(gs, oracle, room1m):
+    g, cam = room1m
+    W, H = 640, 480
+    r, out, _, _ = render_gpu(gs, g, cam[None], W, H)
+    ora = oracle.render(g, cam, W, H)
+    st = compare_view(gpu_outputs(out, 0), ora)
+    print("room 1M 640x480:", st, r.stats())
+
+
+def test_room_1m_keys_bit_exact(gs, room1m):
+    g, cam = room1m
+    W, H = 640, 480
+    r, out, _, _ = render_gpu(gs, g, cam[None], W, H)
+    P = _check_keys(r, cam[None], W, H, np.zeros(g["means"].shape[0], np.int64))
+    assert P > 100_000
+
+
+@pytest.mark.parametrize("tile,depth", [((8, 8), 64), ((16, 8), 128), ((32, 8), 256), ((32, 16), 32)])
+def test_tile_size_does_not_change_results(gs, tile, depth):
+    g = synth.room_scene(200_000, seed=4)
+    W, H = 200, 150  # not a multiple of any tile
+    cam = synth.room_camera(4, W, H)
+    _, a, _, _ = render_gpu(gs, g, cam[None], W, H)
+    _, b, _, _ = render_gpu(gs, g, cam[None], W, H, tile=tile, batch_depth=depth)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+def test_persistent_grid_equals_one_cta_per_tile(gs):
+    g = synth.room_scene(300_000, seed=5)
+    W = H = 256
+    cam = synth.room_camera(5, W, H)
+    _, a, _, _ = render_gpu(gs, g, cam[None], W, H)
+    _, b, _, _ = render_gpu(gs, g, cam[None], W, H, persistent=True)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+@pytest.fixture(scope="module")
+def small_batch():
+    return synth.batched_rooms(n_envs=6, n_min=30_000, n_max=150_000, W=256, H=256, seed0=100)
+
+
+def test_batched_equals_per_env_loop(gs, small_batch):
+    g, offs, cams = small_batch
+    W = H = 256
+    _, ab, _, _ = render_gpu(gs, g, cams, W, H, offs=offs, persistent=True)
+    for e in range(len(offs) - 1):
+        ge = {k: v[offs[e]:offs[e + 1]] for k, v in g.items()}
+        _, ae, _, _ = render_gpu(gs, ge, cams[e:e + 1], W, H)
+        for x, y in zip(ab, ae):
+            assert torch.equal(x[e], y[0])
+
+
+def test_batched_matches_oracle(gs, oracle, small_batch):
+    g, offs, cams = small_batch
+    W = H = 256
+    r, out, _, _ = render_gpu(gs, g, cams, W, H, offs=offs, persistent=True)
+    for e in range(len(offs) - 1):
+        ge = {k: v[offs[e]:offs[e + 1]] for k, v in g.items()}
+        compare_view(gpu_outputs(out, e), oracle.render(ge, cams[e], W, H))
+    views = np.repeat(np.arange(len(offs) - 1), np.diff(offs))
+    _check_keys(r, cams, W, H, views)
+
+
+def test_views_sharing_an_env(gs, oracle):
+    # several cameras on one scene: one record per (view, Gaussian)
+    g = synth.room_scene(150_000, seed=7)
+    W = H = 128
+    cams = np.stack([synth.room_camera(20 + k, W, H) for k in range(4)])
+    r, out, _, _ = render_gpu(gs, g, cams, W, H, offs=np.array([0, 150_000]), view_env=[0, 0, 0, 0])
+    for v in range(4):
+        compare_view(gpu_outputs(out, v), oracle.render(g, cams[v], W, H))
+    _check_keys(r, cams, W, H, np.repeat(np.arange(4), 150_000))
+
+
+@pytest.mark.parametrize("dt", ["f16", "bf16"])
+def test_half_precision_sh_storage(gs, oracle, dt):
+    g = synth.room_scene(200_000, seed=8)
+    W = H = 256
+    cam = synth.room_camera(8, W, H)
+    tdt = torch.float16 if dt == "f16" else torch.bfloat16
+    _, out, _, _ = render_gpu(gs, g, cam[None], W, H, sh_dtype=tdt)
+    gq = dict(g)
+    if dt == "f16":
+        gq["sh"] = g["sh"].astype(np.float16).astype(np.float32)
+    else:
+        gq["sh"] = synth.bf16_to_f32(synth.bf16_bits(g["sh"]))
+    st = compare_view(gpu_outputs(out, 0), oracle.render(gq, cam, W, H))  # exact on the stored values
+    full = oracle.render(g, cam, W, H)
+    err = np.abs(out[0][0].cpu().numpy() - full["rgb"]).max()
+    print(f"SH {dt}: vs quantised-input oracle {st}, vs FP32-input oracle max |rgb| err {err:.2e}")
+    assert err < (2e-3 if dt == "f16" else 2e-2)
+
+
+def test_background_and_normalised_depth(gs, oracle):
+    g = synth.box_scene(3000, seed=9)
+    W = H = 64
+    cam = synth.identity_camera(W, H)
+    bg = (0.2, 0.5, 0.9)
+    _, out, _, _ = render_gpu(gs, g, cam[None], W, H, bg=bg, normalize_depth=True)
+    compare_view(gpu_outputs(out, 0), oracle.render(g, cam, W, H, bg=bg, normalize_depth=True))
+
+
+def test_edge_cases(gs, oracle):
+    W, H = 37, 23
+    cam = synth.identity_camera(W, H)
+    # everything behind the camera or beyond the near plane
+    g = synth.box_scene(500, seed=10)
+    g["means"][:, 2] = np.float32(-1.0)
+    _, out, _, _ = render_gpu(gs, g, cam[None], W, H)
+    assert torch.all(out[2] == 1.0) and torch.all(out[0] == 0.0) and torch.all(out[3] == 0)
+    # an empty env next to a non-empty one; 1x1 image
+    g = synth.box_scene(400, seed=11)
+    g["log_scales"] += np.float32(2.0)
+    offs = np.array([0, 0, 400])
+    c1 = synth.identity_camera(1, 1)
+    r, out, _, _ = render_gpu(gs, g, np.stack([c1, c1]), 1, 1, offs=offs)
+    assert torch.all(out[2][0] == 1.0)
+    compare_view(gpu_outputs(out, 1), oracle.render(g, c1, 1, 1))
+    # one Gaussian covering the whole image
+    g = dict(means=np.float32([[0.0, 0.0, 3.0]]), log_scales=np.float32([[1.0, 1.0, 1.0]]),
+             quats=np.float32([[1, 0, 0, 0]]), opacity_logits=np.float32([2.0]), sh=np.zeros((1, 16, 3), np.float32))
+    _, out, _, _ = render_gpu(gs, g, cam[None], W, H)
+    compare_view(gpu_outputs(out, 0), oracle.render(g, cam, W, H))
+
+
+def test_capacity_overflow_is_reported_not_written(gs):
+    g = synth.box_scene(5000, seed=0)
+    W = H = 128
+    cam = synth.identity_camera(W, H)
+    batch = gs.Batch(np.array([0, 5000]))
+    r = gs.Renderer(batch, W, H, pair_capacity=1000)
+    G = gs.Gaussians.from_numpy(g)
+    out = r.forward(G, gs.cameras_tensor(cam[None]))
+    torch.cuda.synchronize()
+    assert r.status() == -4  # GS_ERR_CAPACITY
+    assert r.status() == 0   # cleared by the read
+    assert torch.isfinite(out[0]).all()

@@ -153,6 +153,30 @@ gs_status gs_render(const gs_gaussians *g, const gs_batch *batch, const gs_camer
                     void *workspace, size_t workspace_bytes, float *out_rgb, float *out_depth, float *out_T,
                     int32_t *out_ncontrib, void *stream);
 
+/* gs_render without a workspace, for callers that cannot allocate device
+ * memory -- for instance a sensor plugin inside a host simulator whose device
+ * memory is owned by another framework's allocator, or a real-time path that
+ * must not allocate after start-up.  The paper has no counterpart; it is an
+ * addition of this library.
+ * The scratch is a file-scope device array of GS_STATIC_SCRATCH_BYTES (64 MiB)
+ * inside libgs, present on every GPU that loads the library until the process
+ * exits.  Inputs and outputs are as for gs_render.  Problems whose workspace
+ * (gs_render_workspace_size) exceeds the array are rejected with
+ * GS_ERR_WORKSPACE_TOO_SMALL before any work is enqueued; 64 MiB holds about
+ * 300k (view, Gaussian) records at 256x256 with the default pair capacity.
+ * Allocates nothing: no cudaMalloc/cudaFree, no library allocation, and no
+ * profiling events.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  Every call on a device shares the one array and leaves its
+ * contents behind (the call clears what must start at zero itself), so calls
+ * whose work overlaps on the GPU -- two streams, or two threads -- race;
+ * serialise them.  The backward cannot follow this call (its state lives in
+ * the shared array). */
+#define GS_STATIC_SCRATCH_BYTES (64ll << 20)
+gs_status gs_render_static(const gs_gaussians *g, const gs_batch *batch, const gs_camera *cams,
+                           const gs_render_config *cfg, float *out_rgb, float *out_depth, float *out_T,
+                           int32_t *out_ncontrib, void *stream);
+
 /* Adjoint of gs_render for L with dL/drgb = d_rgb [V,3,H,W] and dL/ddepth =
  * d_depth [V,H,W] (device; raw depth only).  Must follow gs_render with the
  * same arguments and an untouched workspace.  Gradients are ADDED to the

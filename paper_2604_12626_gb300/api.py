@@ -82,15 +82,16 @@ _lib.gs_render_stats.argtypes = [_P, ctypes.c_size_t, _P, _R(GsStats)]
 _lib.gs_autotune.argtypes = [_R(GsGaussians), _R(GsBatch), _P, _R(GsRenderConfig), _P, ctypes.c_size_t, _P, _P, _P,
                              _P, _P, ctypes.c_int32, ctypes.c_int32, _R(ctypes.c_float), _P]
 _lib.gs_workspace_sections.argtypes = [_R(GsRenderConfig), _R(GsBatch), _P, _R(GsWsSections)]
+_lib.gs_render_static.argtypes = [_R(GsGaussians), _R(GsBatch), _P, _R(GsRenderConfig), _P, _P, _P, _P, _P]
 _lib.gs_profile_enable.argtypes = [ctypes.c_int32]
 _lib.gs_profile_read.argtypes = [_P, _P]
-for _f in ("gs_profile_enable", "gs_profile_read", "gs_workspace_sections", "gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_deform_avatars",
+for _f in ("gs_render_static", "gs_profile_enable", "gs_profile_read", "gs_workspace_sections", "gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_deform_avatars",
            "gs_deform_avatars_backward", "gs_get_status", "gs_render_stats", "gs_autotune"):
     getattr(_lib, _f).restype = ctypes.c_int32
 _lib.gs_last_cuda_error.restype = ctypes.c_int32
 _lib.gs_version.restype = ctypes.c_int32
 
-EXPORTS = ("gs_profile_enable", "gs_profile_read", "gs_workspace_sections", "gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_deform_avatars",
+EXPORTS = ("gs_render_static", "gs_profile_enable", "gs_profile_read", "gs_workspace_sections", "gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_deform_avatars",
            "gs_deform_avatars_backward", "gs_get_status", "gs_render_stats", "gs_autotune", "gs_last_cuda_error",
            "gs_version")
 
@@ -358,6 +359,19 @@ class Avatars:
         self.m, self.n_avatars, self.n_joints = m, n_avatars, n_joints
         self.c = GsAvatars(_ptr(means), _ptr(log_scales), _ptr(quats), _ptr(joint_ids), _ptr(weights),
                            _ptr(avatar_of), _ptr(dest), m, n_avatars, n_joints)
+
+
+STATIC_SCRATCH_BYTES = 64 << 20
+
+
+def render_static(g: Gaussians, batch: Batch, cams: torch.Tensor, cfg: GsRenderConfig, out, stream=None):
+    """gs_render_static: a forward render that allocates nothing (scratch in a
+    64 MiB static device array inside libgs).  ``out`` = (rgb, depth, T,
+    n_contrib) preallocated by the caller.  Calls must not overlap on the GPU."""
+    rgb, depth, T, nc = out
+    _check(_lib.gs_render_static(ctypes.byref(g.c), ctypes.byref(batch.c), _ptr(cams), ctypes.byref(cfg), _ptr(rgb),
+                                 _ptr(depth), _ptr(T), _ptr(nc), _stream(stream)), "gs_render_static")
+    return out
 
 
 def deform(av: Avatars, G: torch.Tensor, out_means: torch.Tensor, out_cov3d: torch.Tensor, stream=None):

@@ -40,6 +40,7 @@ struct ProfRec {
     cudaEvent_t a, b;
 };
 bool g_prof = false;
+thread_local bool g_prof_suppress = false;
 std::vector<ProfRec> g_prof_pending;
 std::vector<cudaEvent_t> g_prof_pool;
 
@@ -69,7 +70,7 @@ struct Stage {
     cudaEvent_t a = nullptr;
     Stage(int st, cudaStream_t str) : stage(st), s(str)
     {
-        if (g_prof && !capturing(s)) {
+        if (g_prof && !g_prof_suppress && !capturing(s)) {
             a = prof_event();
             cudaEventRecord(a, s);
         }
@@ -309,6 +310,15 @@ gs_status enqueue_forward(const gs_gaussians *g, const gs_batch *b, const gs_cam
 }
 
 } // namespace
+
+namespace gs {
+
+gs_status record_cuda_error(cudaError_t e) { return cuda_fail(e); }
+
+ProfileSuppress::ProfileSuppress() : prev(g_prof_suppress) { g_prof_suppress = true; }
+ProfileSuppress::~ProfileSuppress() { g_prof_suppress = prev; }
+
+} // namespace gs
 
 extern "C" {
 

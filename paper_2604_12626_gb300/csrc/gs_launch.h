@@ -33,4 +33,15 @@ void launch_deform(const gs_avatars *av, const float *G, float *out_means, float
 void launch_deform_backward(const gs_avatars *av, const float *G, const float *d_means, const float *d_cov,
                             float *d_cm, float *d_cls, float *d_cq, float *d_G, cudaStream_t s);
 
+// Records a CUDA error for gs_last_cuda_error and returns GS_ERR_CUDA.
+gs_status record_cuda_error(cudaError_t e);
+
+// While alive on this thread, the calls made by this thread record no stage
+// profiling events.
+struct ProfileSuppress {
+    ProfileSuppress();
+    ~ProfileSuppress();
+    bool prev;
+};
+
 } // namespace gs

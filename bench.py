@@ -38,7 +38,7 @@ METRIC = "RGB-D frames/s at 64 envs (fwd, fwd+bwd) vs plain per-env path; % roof
 UNIT = "env-frames/s"
 N_ENVS, W, H = 64, 256, 256
 N_MIN, N_MAX = 300_000, 1_500_000
-TILE_CANDIDATES = [(16, 16, 256), (16, 16, 128), (16, 8, 128), (16, 8, 64), (8, 8, 64), (32, 8, 256), (32, 8, 128)]
+TILE_CANDIDATES = [(16, 16, 256), (16, 16, 128), (16, 8, 128), (16, 8, 64), (8, 8, 64), (8, 8, 128), (8, 8, 256), (32, 8, 256)]
 KERNELS_PER_STEP = 9  # setup, preprocess, scan, scatter, sort_small, sort_big, blend, blend_backward, preprocess_backward
 
 
@@ -231,7 +231,11 @@ def run_ours(args, ws, rank, local):
             cache = json.load(f)
     except Exception:
         pass
-    if key in cache and not args.retune:
+    if args.tile:
+        tw, th, bd = (int(x) for x in args.tile.split(","))
+        rend.cfg.tile_w, rend.cfg.tile_h, rend.cfg.batch_depth = tw, th, bd
+        tuned = {"choice": [tw, th, bd], "fixed": True}
+    elif key in cache and not args.retune:
         tw, th, bd = cache[key]["choice"]
         rend.cfg.tile_w, rend.cfg.tile_h, rend.cfg.batch_depth = tw, th, bd
         tuned = dict(cache[key], cached=True)
@@ -431,6 +435,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--retune", action="store_true")
+    ap.add_argument("--tile", default="", help="fixed tile_w,tile_h,batch_depth instead of the autotuner")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

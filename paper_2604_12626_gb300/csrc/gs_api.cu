@@ -118,7 +118,7 @@ struct Plan {
     int64_t N, R, cap;
     float near_plane;
     // byte offsets
-    size_t o_hdr, o_tb, o_rec, o_vis, o_cnt, o_start, o_cur, o_big, o_keys, o_scr, o_pT, o_pL, o_drec, total;
+    size_t o_hdr, o_tb, o_rec, o_vis, o_cnt, o_start, o_cur, o_big, o_heavy, o_keys, o_scr, o_pT, o_pL, o_drec, total;
 };
 
 gs_status make_plan(const gs_render_config *cfg, const gs_batch *b, Plan &p)
@@ -134,7 +134,7 @@ gs_status make_plan(const gs_render_config *cfg, const gs_batch *b, Plan &p)
     p.th = cfg->tile_h > 0 ? cfg->tile_h : 16;
     if (p.tw * p.th > 1024 || (p.tw * p.th) % 32 != 0) return GS_ERR_INVALID_ARG;
     p.B = cfg->batch_depth > 0 ? cfg->batch_depth : 256;
-    if (p.B < 32 || p.B > 256) return GS_ERR_INVALID_ARG;
+    if (p.B < 32 || p.B > 256 || p.B > 4 * p.tw * p.th) return GS_ERR_INVALID_ARG;
     p.flags = cfg->flags;
     p.near_plane = cfg->near_plane > 0.0f ? cfg->near_plane : 0.2f;
     p.tiles_x = (p.W + p.tw - 1) / p.tw;
@@ -167,6 +167,7 @@ gs_status make_plan(const gs_render_config *cfg, const gs_batch *b, Plan &p)
     p.o_start = o; o = align256(o + (size_t)(nb + 1) * 4);
     p.o_cur = o; o = align256(o + (size_t)nb * 4);
     p.o_big = o; o = align256(o + (size_t)nb * 4);
+    p.o_heavy = o; o = align256(o + (size_t)4096 * 4);
     p.o_keys = o; o = align256(o + (size_t)p.cap * 8);
     p.o_scr = o; o = align256(o + (size_t)p.cap * 8);
     p.o_pT = o; o = align256(o + (size_t)npix * 4);
@@ -188,6 +189,7 @@ Ws ws_ptrs(void *base, const Plan &p)
     w.bin_start = reinterpret_cast<uint32_t *>(b + p.o_start);
     w.bin_cursor = reinterpret_cast<uint32_t *>(b + p.o_cur);
     w.big_list = reinterpret_cast<uint32_t *>(b + p.o_big);
+    w.heavy = reinterpret_cast<uint32_t *>(b + p.o_heavy);
     w.keys = reinterpret_cast<unsigned long long *>(b + p.o_keys);
     w.scratch = reinterpret_cast<unsigned long long *>(b + p.o_scr);
     w.pix_T = reinterpret_cast<float *>(b + p.o_pT);
@@ -196,7 +198,7 @@ Ws ws_ptrs(void *base, const Plan &p)
     return w;
 }
 
-void fill_table(const Plan &p, const gs_batch *b, const gs_render_config *cfg, Table &t)
+void fill_table(const Plan &p, const gs_batch *b, const gs_render_config *cfg, int n_sms, Table &t)
 {
     std::memset(&t, 0, sizeof(Table));
     t.n_envs = b->n_envs;
@@ -208,6 +210,8 @@ void fill_table(const Plan &p, const gs_batch *b, const gs_render_config *cfg, T
     t.n_records = p.R;
     t.pair_capacity = p.cap;
     t.n_gauss = p.N;
+    t.chunk = chunk_size(p.N, n_sms);
+    t.n_chunks = (int)((p.N + t.chunk - 1) / t.chunk);
     for (int k = 0; k < 3; ++k) t.bg[k] = cfg->bg[k];
     t.near_plane = p.near_plane;
     for (int e = 0; e <= b->n_envs; ++e) t.env_off[e] = b->env_offsets[e];
@@ -265,7 +269,7 @@ gs_status enqueue_forward(const gs_gaussians *g, const gs_batch *b, const gs_cam
         return GS_ERR_ALIGNMENT;
     if (ws_bytes < p.total) return GS_ERR_WORKSPACE_TOO_SMALL;
     Table t;
-    fill_table(p, b, cfg, t);
+    fill_table(p, b, cfg, sms, t);
     Ws w = ws_ptrs(ws, p);
     {
         Stage st0(0, s);
@@ -277,7 +281,7 @@ gs_status enqueue_forward(const gs_gaussians *g, const gs_batch *b, const gs_cam
     }
     {
         Stage st1(1, s);
-        launch_preprocess(g, cams, w, p.N, s);
+        launch_preprocess(g, cams, w, t.n_chunks, s);
     }
     {
         Stage st2(2, s);
@@ -285,7 +289,7 @@ gs_status enqueue_forward(const gs_gaussians *g, const gs_batch *b, const gs_cam
     }
     {
         Stage st3(3, s);
-        launch_scatter(cams, w, p.N, s);
+        launch_scatter(cams, w, t.n_chunks, s);
     }
     {
         Stage st4(4, s);
@@ -367,8 +371,11 @@ gs_status gs_render_backward(const gs_gaussians *g, const gs_batch *batch, const
     {
         Stage st7(7, s);
         cudaError_t e = cudaMemsetAsync(w.d_rec, 0, (size_t)p.R * 48, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(&w.hdr->queue_bwd, 0, 4, s);
         if (e != cudaSuccess) return cuda_fail(e);
-        launch_blend_backward(cams, w, d_rgb, d_depth, p.n_bins, p.tw * p.th, p.B, s);
+        int pgrid = sms * blend_backward_blocks_per_sm(p.tw * p.th, p.B);
+        if (pgrid > p.n_bins) pgrid = p.n_bins;
+        launch_blend_backward(cams, w, d_rgb, d_depth, p.n_bins, p.tw * p.th, p.B, pgrid, s);
     }
     {
         Stage st8(8, s);

@@ -42,18 +42,49 @@ __device__ __forceinline__ void bin_range_b(const Ws &w, int bin, uint32_t &star
     n = (uint32_t)(e - s);
 }
 
-__global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, const float *__restrict__ d_rgb,
-                                      const float *__restrict__ d_depth)
+// Sums v[0..15] over the warp with 16 shuffles (butterfly transpose): on
+// return, lane l holds the warp total of v[(l >> 1) & 15] (lanes l and l^1
+// hold the same value).
+__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16])
 {
-    extern __shared__ float4 smem_b[];
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const bool up = lane & 16;
+        const float keep = up ? v[i + 8] : v[i], send = up ? v[i] : v[i + 8];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool up = lane & 8;
+        const float keep = up ? v[i + 4] : v[i], send = up ? v[i] : v[i + 4];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool up = lane & 4;
+        const float keep = up ? v[i + 2] : v[i], send = up ? v[i] : v[i + 2];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const bool up = lane & 2;
+        const float keep = up ? v[1] : v[0], send = up ? v[0] : v[1];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+constexpr int kMaxPerB = 4;
+
+// One (view, tile) bin, back to front, batches gathered with cp.async and
+// double-buffered like the forward.
+__device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera *cams, const float *d_rgb,
+                                                   const float *d_depth, int bin, float4 *sm, float *acc,
+                                                   uint32_t *sidx, uint32_t *smax_last)
+{
     const Table *tb = w.tb;
     const int B = tb->batch_depth;
-    float4 *s0 = smem_b, *s1 = smem_b + B, *s2 = smem_b + 2 * B;
-    float *acc = reinterpret_cast<float *>(smem_b + 3 * B); // [B][kGradStride]
-    uint32_t *sidx = reinterpret_cast<uint32_t *>(acc + B * kGradStride);
-    __shared__ uint32_t smax_last;
-
-    const int bin = blockIdx.x;
+    const int nthr = blockDim.x;
     const int v = bin / tb->tiles_per_view;
     const int t = bin - v * tb->tiles_per_view;
     const int tyi = t / tb->tiles_x, txi = t - tyi * tb->tiles_x;
@@ -68,6 +99,7 @@ __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, 
     uint32_t start, n;
     bin_range_b(w, bin, start, n);
     const unsigned long long *keys = w.keys + start;
+    const uint32_t R = (uint32_t)tb->n_records;
 
     float T = 1.0f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f, dD = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f, SD = 0.f;
     uint32_t last = 0;
@@ -82,32 +114,64 @@ __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, 
         S1 = T * tb->bg[1];
         S2 = T * tb->bg[2];
     }
-    if (threadIdx.x == 0) smax_last = 0;
+    if (threadIdx.x == 0) *smax_last = 0;
     __syncthreads();
     const uint32_t wl = __reduce_max_sync(0xffffffffu, last);
-    if ((threadIdx.x & 31) == 0) atomicMax(&smax_last, wl);
+    if ((threadIdx.x & 31) == 0) atomicMax(smax_last, wl);
     __syncthreads();
-    const uint32_t n_proc = min(smax_last, n);
+    const uint32_t n_proc = min(*smax_last, n);
     const int lane = threadIdx.x & 31;
-
-    for (int32_t hi = (int32_t)n_proc; hi > 0; hi -= B) {
-        const int32_t lo = max(0, hi - B);
-        const int cnt = hi - lo;
-        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-            uint32_t rec = (uint32_t)keys[lo + k];
-            if (rec >= (uint32_t)tb->n_records) rec = 0; // only after a capacity overflow
-            const float4 *src = w.rec + 3 * (size_t)rec;
-            s0[k] = src[0];
-            s1[k] = src[1];
-            s2[k] = src[2];
-            sidx[k] = rec;
+    const int nb = (int)((n_proc + B - 1) / B);
+    // batch b covers [lo_b, hi_b), hi_b = n_proc - b B
+    auto lo_of = [&](int b) { return (int32_t)n_proc - (b + 1) * B < 0 ? 0 : (int32_t)n_proc - (b + 1) * B; };
+    auto hi_of = [&](int b) { return (int32_t)n_proc - b * B; };
+    unsigned long long kr[kMaxPerB];
+    auto load_keys = [&](int b) {
+        const int32_t lo = lo_of(b), cnt = hi_of(b) - lo;
+#pragma unroll
+        for (int q = 0; q < kMaxPerB; ++q) {
+            const int e = threadIdx.x + q * nthr;
+            kr[q] = (b < nb && e < cnt) ? keys[lo + e] : 0ull;
         }
-        for (int k = threadIdx.x; k < cnt * kGradStride; k += blockDim.x) acc[k] = 0.0f;
+    };
+    auto issue = [&](int b) {
+        float4 *buf = sm + (b & 1) * 3 * B;
+        uint32_t *ib = sidx + (b & 1) * B;
+        const int32_t cnt = hi_of(b) - lo_of(b);
+#pragma unroll
+        for (int q = 0; q < kMaxPerB; ++q) {
+            const int e = threadIdx.x + q * nthr;
+            if (e < cnt) {
+                uint32_t rec = (uint32_t)kr[q];
+                if (rec >= R) rec = 0; // only after a capacity overflow
+                const float4 *src = w.rec + 3 * (size_t)rec;
+                cp_async16(buf + e, src);
+                cp_async16(buf + B + e, src + 1);
+                cp_async16(buf + 2 * B + e, src + 2);
+                ib[e] = rec;
+            }
+        }
+    };
+    if (nb > 0) {
+        load_keys(0);
+        issue(0);
+        cp_async_commit();
+        load_keys(1);
+    }
+    for (int b = 0; b < nb; ++b) {
+        if (b + 1 < nb) issue(b + 1);
+        cp_async_commit();
+        if (b + 2 < nb) load_keys(b + 2);
+        const int32_t lo = lo_of(b), cnt = hi_of(b) - lo;
+        for (int k = threadIdx.x; k < cnt * kGradStride; k += nthr) acc[k] = 0.0f;
+        cp_async_wait<1>();
         __syncthreads();
+        const float4 *s0 = sm + (b & 1) * 3 * B, *s1 = s0 + B, *s2 = s0 + 2 * B;
         for (int k = cnt - 1; k >= 0; --k) {
             const uint32_t pos = (uint32_t)(lo + k);
-            float g_u = 0.f, g_v = 0.f, g_A = 0.f, g_B = 0.f, g_C = 0.f, g_o = 0.f, g_r = 0.f, g_g = 0.f, g_b = 0.f,
-                  g_z = 0.f;
+            float g[16];
+#pragma unroll
+            for (int x = 0; x < 16; ++x) g[x] = 0.f;
             bool contrib = false;
             if (pos < last) {
                 const float4 a = s0[k];
@@ -124,10 +188,10 @@ __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, 
                             const float om = 1.0f - alpha;
                             const float Ti = T / om;
                             const float wgt = alpha * Ti;
-                            g_r = wgt * dC0;
-                            g_g = wgt * dC1;
-                            g_b = wgt * dC2;
-                            g_z = wgt * dD;
+                            g[6] = wgt * dC0;
+                            g[7] = wgt * dC1;
+                            g[8] = wgt * dC2;
+                            g[9] = wgt * dD;
                             const float iom = 1.0f / om;
                             const float dal = dC0 * (c.x * Ti - S0 * iom) + dC1 * (c.y * Ti - S1 * iom) +
                                               dC2 * (c.z * Ti - S2 * iom) + dD * (a.z * Ti - SD * iom);
@@ -138,43 +202,58 @@ __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, 
                             T = Ti;
                             if (ar < kAlphaMax) {
                                 const float G = ar / q.w;
-                                g_o = dal * G;
+                                g[5] = dal * G;
                                 const float gp = dal * alpha;
-                                g_u = -gp * (q.x * dx + q.y * dy);
-                                g_v = -gp * (q.z * dy + q.y * dx);
-                                g_A = -0.5f * gp * dx * dx;
-                                g_C = -0.5f * gp * dy * dy;
-                                g_B = -gp * dx * dy;
+                                g[0] = -gp * (q.x * dx + q.y * dy);
+                                g[1] = -gp * (q.z * dy + q.y * dx);
+                                g[2] = -0.5f * gp * dx * dx;
+                                g[4] = -0.5f * gp * dy * dy;
+                                g[3] = -gp * dx * dy;
                             }
                         }
                     }
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-                g_u = warp_sum(g_u); g_v = warp_sum(g_v); g_A = warp_sum(g_A); g_B = warp_sum(g_B);
-                g_C = warp_sum(g_C); g_o = warp_sum(g_o); g_r = warp_sum(g_r); g_g = warp_sum(g_g);
-                g_b = warp_sum(g_b); g_z = warp_sum(g_z);
-                if (lane == 0) {
-                    float *ak = acc + k * kGradStride;
-                    atomicAdd(ak + 0, g_u); atomicAdd(ak + 1, g_v); atomicAdd(ak + 2, g_A); atomicAdd(ak + 3, g_B);
-                    atomicAdd(ak + 4, g_C); atomicAdd(ak + 5, g_o); atomicAdd(ak + 6, g_r); atomicAdd(ak + 7, g_g);
-                    atomicAdd(ak + 8, g_b); atomicAdd(ak + 9, g_z);
-                }
+                const float tot = warp_transpose_sum16(g);
+                const int idx = (lane >> 1) & 15;
+                if (!(lane & 1) && idx < 10) atomicAdd(acc + k * kGradStride + idx, tot);
             }
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+        const uint32_t *ib = sidx + (b & 1) * B;
+        for (int k = threadIdx.x; k < cnt; k += nthr) {
             const float4 *ak = reinterpret_cast<const float4 *>(acc + k * kGradStride);
             const float4 x0 = ak[0], x1 = ak[1], x2 = ak[2];
             if (x0.x != 0.f || x0.y != 0.f || x0.z != 0.f || x0.w != 0.f || x1.x != 0.f || x1.y != 0.f ||
                 x1.z != 0.f || x1.w != 0.f || x2.x != 0.f || x2.y != 0.f) {
-                float4 *dst = reinterpret_cast<float4 *>(w.d_rec + (size_t)sidx[k] * kGradStride);
+                float4 *dst = reinterpret_cast<float4 *>(w.d_rec + (size_t)ib[k] * kGradStride);
                 atomicAdd(dst + 0, x0);
                 atomicAdd(dst + 1, x1);
                 atomicAdd(dst + 2, x2);
             }
         }
         __syncthreads();
+    }
+    cp_async_wait<0>();
+}
+
+__global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, const float *__restrict__ d_rgb,
+                                      const float *__restrict__ d_depth)
+{
+    extern __shared__ float4 smem_b[];
+    __shared__ uint32_t smax_last, item;
+    const int B = w.tb->batch_depth;
+    float *acc = reinterpret_cast<float *>(smem_b + 2 * 3 * B); // [B][kGradStride]
+    uint32_t *sidx = reinterpret_cast<uint32_t *>(acc + B * kGradStride); // [2][B]
+    const uint32_t n_items = (uint32_t)w.tb->n_bins + w.hdr->n_heavy;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item = atomicAdd(&w.hdr->queue_bwd, 1u);
+        __syncthreads();
+        if (item >= n_items) break;
+        const int bin = bin_of_item(w, item);
+        if (bin >= 0) blend_backward_tile(w, cams, d_rgb, d_depth, bin, smem_b, acc, sidx, &smax_last);
     }
 }
 
@@ -492,13 +571,21 @@ void launch_count_visible(const Ws &w, int64_t n_words, cudaStream_t s)
 
 static int blend_bwd_smem(int batch_depth)
 {
-    return 3 * batch_depth * (int)sizeof(float4) + batch_depth * kGradStride * 4 + batch_depth * 4;
+    return 2 * 3 * batch_depth * (int)sizeof(float4) + batch_depth * kGradStride * 4 + 2 * batch_depth * 4;
 }
 
 void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,
-                           int threads, int batch_depth, cudaStream_t s)
+                           int threads, int batch_depth, int persistent_grid, cudaStream_t s)
 {
-    blend_backward_kernel<<<n_bins, threads, blend_bwd_smem(batch_depth), s>>>(cams, w, d_rgb, d_depth);
+    (void)n_bins;
+    blend_backward_kernel<<<persistent_grid, threads, blend_bwd_smem(batch_depth), s>>>(cams, w, d_rgb, d_depth);
+}
+
+int blend_backward_blocks_per_sm(int threads, int batch_depth)
+{
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blend_backward_kernel, threads, blend_bwd_smem(batch_depth));
+    return nb > 0 ? nb : 1;
 }
 
 template <bool OW>

@@ -91,99 +91,216 @@ struct GaussIn {
     const void *sh;
 };
 
+// Every preprocess / scatter CTA owns a chunk of kChunk consecutive Gaussians.
+// Per-(view, tile) counts and cursors of a chunk that lies inside one env are
+// aggregated in shared memory, so that global atomics are one per (CTA, bin)
+// rather than one per pair.
+constexpr int kChunkMax = 16384;
+constexpr int kHistCap = 8192;
+constexpr int kPreThreads = 256;
+
+struct Chunk {
+    int64_t g0, g1;
+    int e0, e1, vb, nv, kmax;
+    bool hist;
+};
+
+__device__ __forceinline__ void chunk_setup(const Table *tb, int64_t cta, Chunk &c)
+{
+    c.g0 = cta * tb->chunk;
+    c.g1 = min(c.g0 + tb->chunk, tb->n_gauss);
+    c.e0 = find_env(tb, c.g0);
+    c.e1 = find_env(tb, c.g1 - 1);
+    c.vb = tb->env_view_begin[c.e0];
+    c.nv = tb->env_view_begin[c.e0 + 1] - c.vb;
+    c.kmax = 0;
+    for (int e = c.e0; e <= c.e1; ++e) c.kmax = max(c.kmax, tb->env_view_begin[e + 1] - tb->env_view_begin[e]);
+    c.hist = c.e0 == c.e1 && c.nv * tb->tiles_per_view <= kHistCap;
+}
+
+// One visible (view, Gaussian) waiting for its colour, record and bin counts.
+struct QEntry {
+    uint32_t rec, g;
+    float uc, vc, zk, r, A, B, C, d0, d1, d2;
+    uint16_t x0, x1, y0, y1;
+    uint16_t v, k;
+    uint32_t pad;
+};
+
 template <int SHT>
-__global__ void __launch_bounds__(256) preprocess_kernel(const gs_camera *__restrict__ cams, GaussIn gin, Ws w)
+__device__ __forceinline__ float3 sh_colour(const void *sh, int64_t g, float x, float y, float z)
+{
+    float kk[48], Y[16];
+    load_sh<SHT>(sh, g, kk);
+    sh_basis(x, y, z, Y);
+    float col[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.5f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc += Y[i] * kk[3 * i + ch];
+        col[ch] = fmaxf(acc, 0.0f);
+    }
+    return make_float3(col[0], col[1], col[2]);
+}
+
+// Phase 2, one entry per lane of a warp: colour, record, visibility bit and
+// bin counts of a queued visible (view, Gaussian).
+template <int SHT>
+__device__ __forceinline__ void finish_entry(const QEntry &en, bool active, uint32_t *hist, const Chunk &c,
+                                             const GaussIn &gin, const Ws &w)
 {
     const Table *tb = w.tb;
-    const int64_t N = tb->n_gauss;
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = g < N;
-    const int lane = threadIdx.x & 31;
-    int e = 0, nv = 0, vb = 0;
-    int64_t local = 0;
+    if (active) {
+        const int tpv = tb->tiles_per_view, tx_n = tb->tiles_x, tw = tb->tile_w, th = tb->tile_h;
+        const float dn = 1.0f / sqrtf(en.d0 * en.d0 + en.d1 * en.d1 + en.d2 * en.d2);
+        const float3 col = sh_colour<SHT>(gin.sh, en.g, en.d0 * dn, en.d1 * dn, en.d2 * dn);
+        const float op = 1.0f / (1.0f + expf(-__ldg(gin.ologits + en.g)));
+        float4 *dst = w.rec + 3 * (size_t)en.rec;
+        dst[0] = make_float4(en.uc, en.vc, en.zk, en.r);
+        dst[1] = make_float4(en.A, en.B, en.C, op);
+        dst[2] = make_float4(col.x, col.y, col.z, 0.0f);
+        const int bx0 = en.x0 / tw, bx1 = en.x1 / tw, by0 = en.y0 / th, by1 = en.y1 / th;
+        uint32_t *hk = c.hist ? hist + en.k * tpv : w.bin_count + (size_t)en.v * tpv;
+        for (int by = by0; by <= by1; ++by)
+            for (int bx = bx0; bx <= bx1; ++bx) atomicAdd(hk + by * tx_n + bx, 1u);
+    }
+    // visibility bit, aggregated over the lanes that share a word
+    const uint32_t word = active ? (en.rec >> 5) : 0xffffffffu;
+    const unsigned grp = __match_any_sync(0xffffffffu, word);
+    const uint32_t bits = __reduce_or_sync(grp, active ? (1u << (en.rec & 31)) : 0u);
+    if (active && (threadIdx.x & 31) == __ffs(grp) - 1) atomicOr(w.vis + word, bits);
+}
+
+// Each warp walks 32-Gaussian rounds of the chunk on its own (no CTA barrier in
+// the loop): phase 1 on every lane (near cull, covariance, projection, radius,
+// footprint), visible results into the warp's ring queue in shared memory, and
+// phase 2 on full warps of 32 queued entries.  The next round's means are
+// loaded before the current round is processed.
+constexpr int kWarpQ = 64;
+
+template <int SHT>
+__global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(const gs_camera *__restrict__ cams, GaussIn gin,
+                                                                    Ws w)
+{
+    extern __shared__ __align__(16) unsigned char smem_pre[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    QEntry *q = reinterpret_cast<QEntry *>(smem_pre) + warp * kWarpQ;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem_pre + (kPreThreads / 32) * kWarpQ * sizeof(QEntry));
+    const Table *tb = w.tb;
+    Chunk c;
+    chunk_setup(tb, blockIdx.x, c);
+    const int tpv = tb->tiles_per_view;
+    if (c.hist)
+        for (int i = threadIdx.x; i < c.nv * tpv; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    const int W = tb->W, H = tb->H;
+    const float near_plane = tb->near_plane;
+    const int nwarps = blockDim.x >> 5;
+    int head = 0, tail = 0; // ring queue of this warp
+    int64_t g = c.g0 + warp * 32 + lane;
     float mx = 0.f, my = 0.f, mz = 0.f;
-    if (valid) {
-        e = find_env(tb, g);
-        vb = tb->env_view_begin[e];
-        nv = tb->env_view_begin[e + 1] - vb;
-        local = g - tb->env_off[e];
+    if (g < c.g1) {
         mx = __ldg(gin.means + 3 * g);
         my = __ldg(gin.means + 3 * g + 1);
         mz = __ldg(gin.means + 3 * g + 2);
     }
-    const int nv_max = __reduce_max_sync(0xffffffffu, nv);
-    const int W = tb->W, H = tb->H, tw = tb->tile_w, th = tb->tile_h, tx_n = tb->tiles_x;
-    const float near_plane = tb->near_plane;
-    bool have_sigma = false;
-    float S[6];
-    for (int k = 0; k < nv_max; ++k) {
-        bool vis = false;
-        uint32_t rec = 0;
-        if (k < nv) {
-            const int v = tb->env_views[vb + k];
-            const gs_camera cam = cams[v];
-            const float zk = depth_key(mx, my, mz, cam);
-            if (zk > near_plane) {
-                if (!have_sigma) {
-                    if (gin.cov3d && g >= tb->env_cov_begin[e]) {
+    for (int64_t base = c.g0 + warp * 32; base < c.g1; base += 32 * nwarps) {
+        const bool valid = g < c.g1;
+        // prefetch the next round's means
+        const int64_t gn = g + 32 * nwarps;
+        float nx = 0.f, ny = 0.f, nz = 0.f;
+        if (gn < c.g1) {
+            nx = __ldg(gin.means + 3 * gn);
+            ny = __ldg(gin.means + 3 * gn + 1);
+            nz = __ldg(gin.means + 3 * gn + 2);
+        }
+        int e = c.e0;
+        if (valid && c.e0 != c.e1) e = find_env(tb, g);
+        const int vb = tb->env_view_begin[e];
+        const int nv = valid ? tb->env_view_begin[e + 1] - vb : 0;
+        const int64_t local = g - tb->env_off[e];
+        bool have_sigma = false;
+        float S[6];
+        for (int k = 0; k < c.kmax; ++k) {
+            bool vis = false;
+            QEntry en;
+            if (k < nv) {
+                const int v = tb->env_views[vb + k];
+                const gs_camera cam = cams[v];
+                const float zk = depth_key(mx, my, mz, cam);
+                if (zk > near_plane) {
+                    if (!have_sigma) {
+                        if (gin.cov3d && g >= tb->env_cov_begin[e]) {
 #pragma unroll
-                        for (int i = 0; i < 6; ++i) S[i] = __ldg(gin.cov3d + 6 * g + i);
-                    } else {
-                        float3 ls = make_float3(__ldg(gin.log_scales + 3 * g), __ldg(gin.log_scales + 3 * g + 1),
-                                                __ldg(gin.log_scales + 3 * g + 2));
-                        float4 q = __ldg(reinterpret_cast<const float4 *>(gin.quats) + g);
-                        sigma_from_sq(ls, q, S);
-                    }
-                    have_sigma = true;
-                }
-                Proj pj;
-                const bool ok = project_ewa(mx, my, mz, zk, S, cam, W, H, pj);
-                if (ok) {
-                    const float idet = 1.0f / pj.det;
-                    const float r = radius_px(pj);
-                    int x0, x1, y0, y1;
-                    if (pixel_range(pj.uc, r, cam.cx, W, x0, x1) && pixel_range(pj.vc, r, cam.cy, H, y0, y1)) {
-                        vis = true;
-                        rec = (uint32_t)(tb->view_rec_off[v] + local);
-                        float kk[48], Y[16];
-                        load_sh<SHT>(gin.sh, g, kk);
-                        const float dn = 1.0f / sqrtf(pj.d0 * pj.d0 + pj.d1 * pj.d1 + pj.d2 * pj.d2);
-                        sh_basis(pj.d0 * dn, pj.d1 * dn, pj.d2 * dn, Y);
-                        float col[3];
-#pragma unroll
-                        for (int ch = 0; ch < 3; ++ch) {
-                            float acc = 0.5f;
-#pragma unroll
-                            for (int i = 0; i < 16; ++i) acc += Y[i] * kk[3 * i + ch];
-                            col[ch] = fmaxf(acc, 0.0f);
+                            for (int i = 0; i < 6; ++i) S[i] = __ldg(gin.cov3d + 6 * g + i);
+                        } else {
+                            const float3 ls = make_float3(__ldg(gin.log_scales + 3 * g),
+                                                          __ldg(gin.log_scales + 3 * g + 1),
+                                                          __ldg(gin.log_scales + 3 * g + 2));
+                            const float4 qq = __ldg(reinterpret_cast<const float4 *>(gin.quats) + g);
+                            sigma_from_sq(ls, qq, S);
                         }
-                        const float op = 1.0f / (1.0f + expf(-__ldg(gin.ologits + g)));
-                        float4 *dst = w.rec + 3 * (size_t)rec;
-                        dst[0] = make_float4(pj.uc, pj.vc, zk, r);
-                        dst[1] = make_float4(pj.c * idet, -pj.b * idet, pj.a * idet, op);
-                        dst[2] = make_float4(col[0], col[1], col[2], 0.0f);
-                        const int bx0 = x0 / tw, bx1 = x1 / tw, by0 = y0 / th, by1 = y1 / th;
-                        uint32_t *bc = w.bin_count + (size_t)v * tb->tiles_per_view;
-                        for (int by = by0; by <= by1; ++by)
-                            for (int bx = bx0; bx <= bx1; ++bx) atomicAdd(bc + by * tx_n + bx, 1u);
+                        have_sigma = true;
+                    }
+                    Proj pj;
+                    if (project_ewa(mx, my, mz, zk, S, cam, W, H, pj)) {
+                        const float r = radius_px(pj);
+                        int x0, x1, y0, y1;
+                        if (pixel_range(pj.uc, r, cam.cx, W, x0, x1) && pixel_range(pj.vc, r, cam.cy, H, y0, y1)) {
+                            vis = true;
+                            const float idet = 1.0f / pj.det;
+                            en.rec = (uint32_t)(tb->view_rec_off[v] + local);
+                            en.g = (uint32_t)g;
+                            en.uc = pj.uc; en.vc = pj.vc; en.zk = zk; en.r = r;
+                            en.A = pj.c * idet; en.B = -pj.b * idet; en.C = pj.a * idet;
+                            en.d0 = pj.d0; en.d1 = pj.d1; en.d2 = pj.d2;
+                            en.x0 = (uint16_t)x0; en.x1 = (uint16_t)x1; en.y0 = (uint16_t)y0; en.y1 = (uint16_t)y1;
+                            en.v = (uint16_t)v; en.k = (uint16_t)k;
+                        }
                     }
                 }
             }
+            const unsigned bal = __ballot_sync(0xffffffffu, vis);
+            if (vis) q[(tail + __popc(bal & ((1u << lane) - 1u))) & (kWarpQ - 1)] = en;
+            tail += __popc(bal);
+            __syncwarp();
+            if (tail - head >= 32) {
+                const QEntry mine = q[(head + lane) & (kWarpQ - 1)];
+                head += 32;
+                __syncwarp();
+                finish_entry<SHT>(mine, true, hist, c, gin, w);
+            }
         }
-        // visibility bit, aggregated over the lanes that share a word
-        const uint32_t word = vis ? (rec >> 5) : 0xffffffffu;
-        const unsigned grp = __match_any_sync(0xffffffffu, word);
-        const uint32_t bits = __reduce_or_sync(grp, vis ? (1u << (rec & 31)) : 0u);
-        const int leader = __ffs(grp) - 1;
-        if (vis && leader == lane) atomicOr(w.vis + word, bits);
-        const unsigned nvis = __popc(__ballot_sync(0xffffffffu, vis));
-        if (lane == 0 && nvis) atomicAdd(&w.hdr->n_visible, nvis);
+        g = gn;
+        mx = nx;
+        my = ny;
+        mz = nz;
+    }
+    if (tail > head) {
+        const bool act = lane < tail - head;
+        QEntry mine;
+        if (act) mine = q[(head + lane) & (kWarpQ - 1)];
+        finish_entry<SHT>(mine, act, hist, c, gin, w);
+    }
+    __syncthreads();
+    if (c.hist) {
+        for (int i = threadIdx.x; i < c.nv * tpv; i += blockDim.x) {
+            const uint32_t cnt = hist[i];
+            if (cnt) {
+                const int v = tb->env_views[c.vb + i / tpv];
+                atomicAdd(w.bin_count + (size_t)v * tpv + (i % tpv), cnt);
+            }
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
 // scan of the bin counts (single CTA, any number of bins)
 // ---------------------------------------------------------------------------
+constexpr int kHeavyMin = 1024; // pairs from which a bin may be scheduled first
+constexpr int kHeavyCap = 4096;
+__device__ __forceinline__ void bitonic_smem(unsigned long long *s, int m);
 __global__ void __launch_bounds__(1024) scan_bins_kernel(Ws w)
 {
     const int nb = w.tb->n_bins;
@@ -228,6 +345,50 @@ __global__ void __launch_bounds__(1024) scan_bins_kernel(Ws w)
         v = __reduce_max_sync(0xffffffffu, v);
         if (threadIdx.x == 0) w.hdr->max_bin = v;
     }
+    // heavy-first list: the bins with at least heavy_min pairs, largest first.
+    // heavy_min = the smallest power of two >= kHeavyMin that keeps the list
+    // within kHeavyCap entries.
+    __shared__ uint32_t lg[33];
+    __shared__ unsigned long long hl[kHeavyCap];
+    __shared__ uint32_t hn, hmin;
+    if (threadIdx.x < 33) lg[threadIdx.x] = 0;
+    if (threadIdx.x == 0) hn = 0;
+    __syncthreads();
+    for (int i = b0; i < b1; ++i) {
+        const uint32_t c = w.bin_count[i];
+        if (c >= (uint32_t)kHeavyMin) atomicAdd(&lg[32 - __clz(c)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0, th = 0xffffffffu;
+        for (int b = 32; b >= 0; --b) {
+            if (acc + lg[b] > (uint32_t)kHeavyCap) break;
+            acc += lg[b];
+            if (lg[b]) th = b == 0 ? 0u : (1u << (b - 1));
+        }
+        hmin = max(th, (uint32_t)kHeavyMin);
+    }
+    __syncthreads();
+    const uint32_t th = hmin;
+    for (int i = b0; i < b1; ++i) {
+        const uint32_t c = w.bin_count[i];
+        if (c >= th) {
+            const uint32_t at = atomicAdd(&hn, 1u);
+            if (at < (uint32_t)kHeavyCap) hl[at] = ((unsigned long long)(~c) << 32) | (uint32_t)i;
+        }
+    }
+    __syncthreads();
+    const int nh = (int)min(hn, (uint32_t)kHeavyCap);
+    int mh = 1;
+    while (mh < nh) mh <<= 1;
+    for (int i = nh + threadIdx.x; i < mh; i += T) hl[i] = ~0ull;
+    __syncthreads();
+    bitonic_smem(hl, mh);
+    for (int i = threadIdx.x; i < nh; i += T) w.heavy[i] = (uint32_t)hl[i];
+    if (threadIdx.x == 0) {
+        w.hdr->n_heavy = (uint32_t)nh;
+        w.hdr->heavy_min = nh > 0 ? th : 0xffffffffu;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -235,31 +396,112 @@ __global__ void __launch_bounds__(1024) scan_bins_kernel(Ws w)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) scatter_kernel(const gs_camera *__restrict__ cams, Ws w)
 {
+    extern __shared__ uint32_t hist_sc[];
     const Table *tb = w.tb;
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= tb->n_gauss) return;
-    const int e = find_env(tb, g);
-    const int vb = tb->env_view_begin[e], ve = tb->env_view_begin[e + 1];
-    const int64_t local = g - tb->env_off[e];
-    const int W = tb->W, H = tb->H, tw = tb->tile_w, th = tb->tile_h, tx_n = tb->tiles_x;
+    Chunk c;
+    chunk_setup(tb, blockIdx.x, c);
+    const int W = tb->W, H = tb->H, tw = tb->tile_w, th = tb->tile_h, tx_n = tb->tiles_x, tpv = tb->tiles_per_view;
     const uint64_t cap = (uint64_t)tb->pair_capacity;
-    for (int k = vb; k < ve; ++k) {
-        const int v = tb->env_views[k];
-        const uint32_t rec = (uint32_t)(tb->view_rec_off[v] + local);
-        if (!((__ldg(w.vis + (rec >> 5)) >> (rec & 31)) & 1u)) continue;
-        const float4 r0 = w.rec[3 * (size_t)rec];
-        const gs_camera &cam = cams[v];
-        int x0, x1, y0, y1;
-        if (!(pixel_range(r0.x, r0.w, cam.cx, W, x0, x1) && pixel_range(r0.y, r0.w, cam.cy, H, y0, y1))) continue;
-        const unsigned long long key = ((unsigned long long)__float_as_uint(r0.z) << 32) | rec;
-        const int bx0 = x0 / tw, bx1 = x1 / tw, by0 = y0 / th, by1 = y1 / th;
-        const size_t bbase = (size_t)v * tb->tiles_per_view;
-        for (int by = by0; by <= by1; ++by)
-            for (int bx = bx0; bx <= bx1; ++bx) {
-                const size_t bin = bbase + by * tx_n + bx;
-                const uint64_t slot = (uint64_t)w.bin_start[bin] + atomicAdd(w.bin_cursor + bin, 1u);
-                if (slot < (uint64_t)w.bin_start[bin + 1] && slot < cap) w.keys[slot] = key;
+    if (!c.hist) {
+        // chunk across envs or too many bins: one global cursor atomic per pair
+        for (int64_t g = c.g0 + threadIdx.x; g < c.g1; g += blockDim.x) {
+            const int e = find_env(tb, g);
+            const int64_t local = g - tb->env_off[e];
+            for (int k = tb->env_view_begin[e]; k < tb->env_view_begin[e + 1]; ++k) {
+                const int v = tb->env_views[k];
+                const uint32_t rec = (uint32_t)(tb->view_rec_off[v] + local);
+                if (!((__ldg(w.vis + (rec >> 5)) >> (rec & 31)) & 1u)) continue;
+                const float4 r0 = w.rec[3 * (size_t)rec];
+                const gs_camera &cam = cams[v];
+                int x0, x1, y0, y1;
+                if (!(pixel_range(r0.x, r0.w, cam.cx, W, x0, x1) && pixel_range(r0.y, r0.w, cam.cy, H, y0, y1)))
+                    continue;
+                const unsigned long long key = ((unsigned long long)__float_as_uint(r0.z) << 32) | rec;
+                const size_t bbase = (size_t)v * tpv;
+                for (int by = y0 / th; by <= y1 / th; ++by)
+                    for (int bx = x0 / tw; bx <= x1 / tw; ++bx) {
+                        const size_t bin = bbase + by * tx_n + bx;
+                        const uint64_t slot = (uint64_t)w.bin_start[bin] + atomicAdd(w.bin_cursor + bin, 1u);
+                        if (slot < (uint64_t)w.bin_start[bin + 1] && slot < cap) w.keys[slot] = key;
+                    }
             }
+        }
+        return;
+    }
+    uint32_t *list = hist_sc + kHistCap; // visible records of one view slot, compacted
+    __shared__ int list_n;
+    for (int i = threadIdx.x; i < c.nv * tpv; i += blockDim.x) hist_sc[i] = 0u;
+    const int64_t loc0 = c.g0 - tb->env_off[c.e0], loc1 = c.g1 - tb->env_off[c.e0];
+    // builds the list of visible records of view slot k (ends with a barrier)
+    auto build_list = [&](int k) {
+        if (threadIdx.x == 0) list_n = 0;
+        __syncthreads();
+        const int64_t roff = tb->view_rec_off[tb->env_views[c.vb + k]];
+        const int64_t r0 = roff + loc0, r1 = roff + loc1;
+        const int64_t wlo = r0 >> 5, whi = (r1 - 1) >> 5;
+        for (int64_t wd = wlo + threadIdx.x; wd <= whi; wd += blockDim.x) {
+            uint32_t bits = __ldg(w.vis + wd);
+            const int64_t b0 = wd << 5;
+            if (b0 < r0) bits &= ~((1u << (uint32_t)(r0 - b0)) - 1u);
+            if (b0 + 32 > r1) bits &= (uint32_t)((1ull << (uint32_t)(r1 - b0)) - 1ull);
+            if (!bits) continue;
+            int at = atomicAdd(&list_n, __popc(bits));
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                list[at++] = (uint32_t)(b0 + b);
+            }
+        }
+        __syncthreads();
+    };
+    // pass 1: count the chunk's pairs per (view slot, tile)
+    for (int k = 0; k < c.nv; ++k) {
+        build_list(k);
+        const gs_camera &cam = cams[tb->env_views[c.vb + k]];
+        uint32_t *hk = hist_sc + k * tpv;
+        const int n = list_n;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint32_t rec = list[i];
+            const float4 r0 = w.rec[3 * (size_t)rec];
+            int x0, x1, y0, y1;
+            if (!(pixel_range(r0.x, r0.w, cam.cx, W, x0, x1) && pixel_range(r0.y, r0.w, cam.cy, H, y0, y1))) continue;
+            for (int by = y0 / th; by <= y1 / th; ++by)
+                for (int bx = x0 / tw; bx <= x1 / tw; ++bx) atomicAdd(hk + by * tx_n + bx, 1u);
+        }
+        __syncthreads();
+    }
+    // pass 2: reserve a contiguous slot range per bin (one global atomic each)
+    for (int i = threadIdx.x; i < c.nv * tpv; i += blockDim.x) {
+        const uint32_t cnt = hist_sc[i];
+        if (cnt) {
+            const size_t bin = (size_t)tb->env_views[c.vb + i / tpv] * tpv + (i % tpv);
+            hist_sc[i] = w.bin_start[bin] + atomicAdd(w.bin_cursor + bin, cnt);
+        }
+    }
+    __syncthreads();
+    // pass 3: write the keys
+    for (int k = 0; k < c.nv; ++k) {
+        if (c.nv > 1) build_list(k);
+        const int v = tb->env_views[c.vb + k];
+        const gs_camera &cam = cams[v];
+        uint32_t *hk = hist_sc + k * tpv;
+        const size_t bbase = (size_t)v * tpv;
+        const int n = list_n;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint32_t rec = list[i];
+            const float4 r0 = w.rec[3 * (size_t)rec];
+            int x0, x1, y0, y1;
+            if (!(pixel_range(r0.x, r0.w, cam.cx, W, x0, x1) && pixel_range(r0.y, r0.w, cam.cy, H, y0, y1))) continue;
+            const unsigned long long key = ((unsigned long long)__float_as_uint(r0.z) << 32) | rec;
+            for (int by = y0 / th; by <= y1 / th; ++by)
+                for (int bx = x0 / tw; bx <= x1 / tw; ++bx) {
+                    const int t = by * tx_n + bx;
+                    const uint64_t slot = atomicAdd(hk + t, 1u);
+                    const uint64_t end = min((uint64_t)w.bin_start[bbase + t + 1], cap);
+                    if (slot < end) w.keys[slot] = key;
+                }
+        }
+        __syncthreads();
     }
 }
 
@@ -396,8 +638,13 @@ struct OutPtrs {
     int32_t *ncontrib;
 };
 
+// Blends one (view, tile) bin.  Batches of B records are gathered into shared
+// memory with cp.async, double-buffered: batch b+1 is in flight while batch b
+// is blended (keys of batch b+2 are prefetched into registers).
+constexpr int kMaxPer = 4; // records per thread and batch (B <= 4 x threads)
+
 __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, const OutPtrs &o, int bin,
-                                          float4 *s0, float4 *s1, float4 *s2)
+                                          float4 *sm)
 {
     const Table *tb = w.tb;
     const int v = bin / tb->tiles_per_view;
@@ -413,50 +660,87 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
     bin_range(w, bin, start, n);
     const unsigned long long *keys = w.keys + start;
     const int B = tb->batch_depth;
+    const int nthr = blockDim.x;
+    const uint32_t R = (uint32_t)tb->n_records;
+    const int nb = (int)((n + B - 1) / B);
+    unsigned long long kr[kMaxPer];
+    auto load_keys = [&](int b) {
+#pragma unroll
+        for (int q = 0; q < kMaxPer; ++q) {
+            const int e = threadIdx.x + q * nthr;
+            const uint32_t idx = (uint32_t)b * B + e;
+            kr[q] = (b < nb && e < B && idx < n) ? keys[idx] : 0ull;
+        }
+    };
+    auto issue = [&](int b) {
+        float4 *buf = sm + (b & 1) * 3 * B;
+#pragma unroll
+        for (int q = 0; q < kMaxPer; ++q) {
+            const int e = threadIdx.x + q * nthr;
+            const uint32_t idx = (uint32_t)b * B + e;
+            if (e < B && idx < n) {
+                uint32_t rec = (uint32_t)kr[q];
+                if (rec >= R) rec = 0; // only after a capacity overflow
+                const float4 *src = w.rec + 3 * (size_t)rec;
+                cp_async16(buf + e, src);
+                cp_async16(buf + B + e, src + 1);
+                cp_async16(buf + 2 * B + e, src + 2);
+            }
+        }
+    };
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, D = 0.0f;
     int32_t ncov = 0, ncon = 0;
     uint32_t last = 0;
     bool done = !inside;
-    for (uint32_t base = 0; base < n; base += B) {
-        if (__syncthreads_count(done) == (int)blockDim.x) break;
-        const int cnt = (int)min((uint32_t)B, n - base);
-        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-            uint32_t rec = (uint32_t)keys[base + k];
-            if (rec >= (uint32_t)tb->n_records) rec = 0; // only after a capacity overflow
-            const float4 *src = w.rec + 3 * (size_t)rec;
-            s0[k] = src[0];
-            s1[k] = src[1];
-            s2[k] = src[2];
-        }
-        __syncthreads();
-        if (!done) {
-            for (int k = 0; k < cnt; ++k) {
+    if (nb > 0) {
+        load_keys(0);
+        issue(0);
+        cp_async_commit();
+        load_keys(1);
+    }
+    for (int b = 0; b < nb; ++b) {
+        if (b + 1 < nb) issue(b + 1);
+        cp_async_commit();
+        if (b + 2 < nb) load_keys(b + 2);
+        cp_async_wait<1>();
+        if (__syncthreads_count(done) == nthr) break;
+        const float4 *s0 = sm + (b & 1) * 3 * B, *s1 = s0 + B, *s2 = s0 + 2 * B;
+        const int cnt = (int)min((uint32_t)B, n - (uint32_t)b * B);
+        // warp-synchronous: every lane runs the same iterations (predicated),
+        // the warp leaves once all its lanes have stopped
+        for (int k = 0; k < cnt; ++k) {
+            if (__all_sync(0xffffffffu, done)) break;
+            if (!done) {
                 const float4 a = s0[k];
                 const float dx = __fsub_rn(a.x, pxc), dy = __fsub_rn(a.y, pyc);
-                if (fmaxf(fabsf(dx), fabsf(dy)) > a.w) continue;
-                ++ncov;
-                const float4 q = s1[k];
-                const float power = gauss_power(q.x, q.y, q.z, dx, dy);
-                if (power > 0.0f) continue;
-                const float alpha = fminf(kAlphaMax, raw_alpha(q.w, power));
-                if (alpha < kAlphaMin) continue;
-                const float Tn = T * (1.0f - alpha);
-                if (Tn < kTStop) {
-                    done = true;
-                    break;
+                if (fmaxf(fabsf(dx), fabsf(dy)) <= a.w) {
+                    ++ncov;
+                    const float4 q = s1[k];
+                    const float power = gauss_power(q.x, q.y, q.z, dx, dy);
+                    const float alpha = fminf(kAlphaMax, raw_alpha(q.w, power));
+                    if (power <= 0.0f && alpha >= kAlphaMin) {
+                        const float Tn = T * (1.0f - alpha);
+                        if (Tn < kTStop) {
+                            done = true;
+                        } else {
+                            const float wgt = alpha * T;
+                            const float4 c = s2[k];
+                            C0 += c.x * wgt;
+                            C1 += c.y * wgt;
+                            C2 += c.z * wgt;
+                            D += a.z * wgt;
+                            T = Tn;
+                            ncon = ncov;
+                            last = (uint32_t)b * B + k + 1;
+                        }
+                    }
                 }
-                const float wgt = alpha * T;
-                const float4 c = s2[k];
-                C0 += c.x * wgt;
-                C1 += c.y * wgt;
-                C2 += c.z * wgt;
-                D += a.z * wgt;
-                T = Tn;
-                ncon = ncov;
-                last = base + k + 1;
             }
+            __syncwarp();
         }
+        __syncthreads();
     }
+    cp_async_wait<0>();
     if (inside) {
         const size_t HW = (size_t)W * H;
         const size_t p = (size_t)j * W + i;
@@ -476,24 +760,21 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
 __global__ void blend_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
 {
     extern __shared__ float4 smem_f4[];
-    const int B = w.tb->batch_depth;
-    float4 *s0 = smem_f4, *s1 = smem_f4 + B, *s2 = smem_f4 + 2 * B;
-    blend_tile(w, cams, o, blockIdx.x, s0, s1, s2);
+    blend_tile(w, cams, o, blockIdx.x, smem_f4);
 }
 
 __global__ void blend_persistent_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
 {
     extern __shared__ float4 smem_f4[];
     __shared__ uint32_t item;
-    const int B = w.tb->batch_depth;
-    float4 *s0 = smem_f4, *s1 = smem_f4 + B, *s2 = smem_f4 + 2 * B;
-    const uint32_t nb = (uint32_t)w.tb->n_bins;
+    const uint32_t n_items = (uint32_t)w.tb->n_bins + w.hdr->n_heavy;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) item = atomicAdd(&w.hdr->queue, 1u);
         __syncthreads();
-        if (item >= nb) break;
-        blend_tile(w, cams, o, (int)item, s0, s1, s2);
+        if (item >= n_items) break;
+        const int bin = bin_of_item(w, item);
+        if (bin >= 0) blend_tile(w, cams, o, bin, smem_f4);
     }
 }
 
@@ -502,24 +783,35 @@ __global__ void blend_persistent_kernel(const gs_camera *__restrict__ cams, Ws w
 // ---------------------------------------------------------------------------
 void launch_setup(const Table &tb, const Ws &w, cudaStream_t s) { setup_kernel<<<1, 256, 0, s>>>(tb, w); }
 
-void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w, int64_t n, cudaStream_t s)
+constexpr int kPreSmem = (kPreThreads / 32) * kWarpQ * (int)sizeof(QEntry) + kHistCap * 4;
+
+int chunk_size(int64_t n, int n_sms)
+{
+    // enough CTAs to fill the GPU a few times over, at most kChunkMax Gaussians each
+    int c = 1024;
+    while (c < kChunkMax && (int64_t)c * 2 * n_sms * 6 <= n) c *= 2;
+    return c;
+}
+
+void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s)
 {
     GaussIn gin{g->means, g->log_scales, g->quats, g->opacity_logits, g->cov3d, g->sh};
-    const unsigned grid = (unsigned)((n + 255) / 256);
+    const unsigned grid = (unsigned)n_chunks;
     if (grid == 0) return;
     switch (g->sh_dtype) {
-    case GS_SH_F16: preprocess_kernel<GS_SH_F16><<<grid, 256, 0, s>>>(cams, gin, w); break;
-    case GS_SH_BF16: preprocess_kernel<GS_SH_BF16><<<grid, 256, 0, s>>>(cams, gin, w); break;
-    default: preprocess_kernel<GS_SH_F32><<<grid, 256, 0, s>>>(cams, gin, w); break;
+    case GS_SH_F16: preprocess_kernel<GS_SH_F16><<<grid, kPreThreads, kPreSmem, s>>>(cams, gin, w); break;
+    case GS_SH_BF16: preprocess_kernel<GS_SH_BF16><<<grid, kPreThreads, kPreSmem, s>>>(cams, gin, w); break;
+    default: preprocess_kernel<GS_SH_F32><<<grid, kPreThreads, kPreSmem, s>>>(cams, gin, w); break;
     }
 }
 
 void launch_scan(const Ws &w, cudaStream_t s) { scan_bins_kernel<<<1, 1024, 0, s>>>(w); }
 
-void launch_scatter(const gs_camera *cams, const Ws &w, int64_t n, cudaStream_t s)
+constexpr int kScatterSmem = kHistCap * 4 + kChunkMax * 4;
+
+void launch_scatter(const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s)
 {
-    const unsigned grid = (unsigned)((n + 255) / 256);
-    if (grid) scatter_kernel<<<grid, 256, 0, s>>>(cams, w);
+    if (n_chunks) scatter_kernel<<<n_chunks, 256, kScatterSmem, s>>>(cams, w);
 }
 
 int sort_big_smem_bytes() { return kBigSort * 8; }
@@ -534,7 +826,7 @@ void launch_sort_big(const Ws &w, int n_sms, cudaStream_t s)
     sort_big_kernel<<<n_sms, 1024, kBigSort * 8, s>>>(w);
 }
 
-int blend_smem_bytes(int batch_depth) { return 3 * batch_depth * (int)sizeof(float4); }
+int blend_smem_bytes(int batch_depth) { return 2 * 3 * batch_depth * (int)sizeof(float4); }
 
 void launch_blend(const gs_camera *cams, const Ws &w, float *rgb, float *depth, float *T, int32_t *ncontrib,
                   int n_bins, int threads, int batch_depth, bool persistent, int persistent_grid, cudaStream_t s)
@@ -550,8 +842,15 @@ void launch_blend(const gs_camera *cams, const Ws &w, float *rgb, float *depth, 
 cudaError_t configure_forward_kernels()
 {
     cudaError_t e = cudaFuncSetAttribute(sort_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBigSort * 8);
-    if (e != cudaSuccess) return e;
-    return cudaSuccess;
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(preprocess_kernel<GS_SH_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPreSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(preprocess_kernel<GS_SH_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPreSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(preprocess_kernel<GS_SH_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPreSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScatterSmem);
+    return e;
 }
 
 int blend_blocks_per_sm(int threads, int batch_depth)

@@ -39,13 +39,16 @@ struct Header {
     uint32_t queue;     // persistent blend work counter
     uint32_t queue_bwd; // persistent backward work counter
     uint32_t big_queue; // large-bin sort work counter
-    uint32_t pad[56];
+    uint32_t n_heavy;   // bins in the heavy-first list
+    uint32_t heavy_min; // pair count from which a bin is in that list
+    uint32_t pad[54];
 };
 
 struct Table {
     int32_t n_envs, n_views;
     int32_t W, H, tile_w, tile_h, tiles_x, tiles_y, tiles_per_view, n_bins;
     int32_t batch_depth, flags;
+    int32_t chunk, n_chunks; // Gaussians per preprocess / scatter CTA, and how many CTAs
     int64_t n_records, pair_capacity, n_gauss;
     float bg[3];
     float near_plane;
@@ -62,7 +65,7 @@ struct Ws {
     Table *tb;
     float4 *rec;  // 3 float4 per record
     uint32_t *vis;
-    uint32_t *bin_count, *bin_start, *bin_cursor, *big_list;
+    uint32_t *bin_count, *bin_start, *bin_cursor, *big_list, *heavy;
     unsigned long long *keys, *scratch;
     float *pix_T;
     uint32_t *pix_last;
@@ -118,6 +121,25 @@ __device__ __forceinline__ float gauss_power(float A, float B, float C, float dx
 {
     float q = __fmaf_rn(A, __fmul_rn(dx, dx), __fmul_rn(C, __fmul_rn(dy, dy)));
     return __fmaf_rn(-0.5f, q, -__fmul_rn(B, __fmul_rn(dx, dy)));
+}
+
+// cp.async gathers (16 bytes each) into shared memory
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Persistent blend order: heavy bins (sorted by pair count, largest first), then
+// every other bin in index order.  Returns -1 for a slot that is skipped.
+__device__ __forceinline__ int bin_of_item(const Ws &w, uint32_t item)
+{
+    const uint32_t nh = w.hdr->n_heavy;
+    if (item < nh) return (int)w.heavy[item];
+    const uint32_t b = item - nh;
+    return w.bin_count[b] >= w.hdr->heavy_min ? -1 : (int)b;
 }
 
 // alpha before the clamp; the clamp is min(0.99, .)

@@ -11,9 +11,10 @@ cudaError_t configure_forward_kernels();
 cudaError_t configure_backward_kernels();
 
 void launch_setup(const Table &tb, const Ws &w, cudaStream_t s);
-void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w, int64_t n, cudaStream_t s);
+int chunk_size(int64_t n, int n_sms);
+void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s);
 void launch_scan(const Ws &w, cudaStream_t s);
-void launch_scatter(const gs_camera *cams, const Ws &w, int64_t n, cudaStream_t s);
+void launch_scatter(const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s);
 void launch_sort_small(const Ws &w, int n_bins, cudaStream_t s);
 void launch_sort_big(const Ws &w, int n_sms, cudaStream_t s);
 void launch_blend(const gs_camera *cams, const Ws &w, float *rgb, float *depth, float *T, int32_t *ncontrib,
@@ -25,7 +26,8 @@ struct GradOut {
     float *means, *log_scales, *quats, *ologits, *sh, *cov3d;
 };
 void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,
-                           int threads, int batch_depth, cudaStream_t s);
+                           int threads, int batch_depth, int persistent_grid, cudaStream_t s);
+int blend_backward_blocks_per_sm(int threads, int batch_depth);
 void launch_preprocess_backward(const gs_gaussians *g, const gs_camera *cams, const Ws &w, const GradOut &o,
                                 int64_t n, bool overwrite, cudaStream_t s);
 

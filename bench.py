@@ -38,7 +38,10 @@ METRIC = "RGB-D frames/s at 64 envs (fwd, fwd+bwd) vs plain per-env path; % roof
 UNIT = "env-frames/s"
 N_ENVS, W, H = 64, 256, 256
 N_MIN, N_MAX = 300_000, 1_500_000
-TILE_CANDIDATES = [(16, 16, 256), (16, 16, 128), (16, 8, 128), (16, 8, 64), (8, 8, 64), (8, 8, 128), (8, 8, 256), (32, 8, 256)]
+# (tile_w, tile_h, batch_depth, pixels per thread x, y)
+TILE_CANDIDATES = [(16, 16, 256, 1, 1), (16, 16, 256, 2, 2), (16, 16, 128, 2, 2), (16, 16, 128, 2, 1),
+                   (16, 8, 128, 1, 1), (16, 8, 128, 2, 1), (8, 8, 64, 1, 1), (8, 8, 128, 1, 1), (8, 8, 64, 2, 1),
+                   (32, 16, 256, 2, 2)]
 KERNELS_PER_STEP = 9  # setup, preprocess, scan, scatter, sort_small, sort_big, blend, blend_backward, preprocess_backward
 
 
@@ -199,6 +202,41 @@ def run_reference(args, ws, rank):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def tune_fwd_bwd(api, rend, G, cams, candidates, N, dev, reps=2):
+    """The autotuner on the whole step: gs_autotune times the forward per
+    candidate; the backward is timed here with the same CUDA events, and the
+    candidate with the fastest forward + backward wins."""
+    import torch
+
+    outs = rend.alloc_outputs()
+    d_rgb = torch.zeros((rend.batch.n_views, 3, rend.height, rend.width), device=dev)
+    d_depth = torch.zeros((rend.batch.n_views, rend.height, rend.width), device=dev)
+    grads = dict(means=torch.empty((N, 3), device=dev), log_scales=torch.empty((N, 3), device=dev),
+                 quats=torch.empty((N, 4), device=dev), opacity_logits=torch.empty((N,), device=dev),
+                 sh=torch.empty((N, 16, 3), device=dev))
+    best, best_ms = None, None
+    base = api.GsRenderConfig.from_buffer_copy(rend.cfg)
+    for cand in candidates:
+        rend.cfg = api.GsRenderConfig.from_buffer_copy(base)
+        try:
+            (_, fwd_ms) = rend.autotune(G, cams, [cand], reps=reps, out=outs)
+        except api.GsError:
+            continue
+        rend.backward(G, cams, d_rgb, d_depth, grads=grads)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            rend.forward(G, cams, out=outs)
+            rend.backward(G, cams, d_rgb, d_depth, grads=grads)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        if best_ms is None or ms < best_ms:
+            best, best_ms = list(cand), ms
+    rend.cfg = api.GsRenderConfig.from_buffer_copy(base)
+    rend.cfg.tile_w, rend.cfg.tile_h, rend.cfg.batch_depth, rend.cfg.pix_x, rend.cfg.pix_y = best
+    return best, best_ms
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -224,7 +262,7 @@ def run_ours(args, ws, rank, local):
     # --- autotune the batched renderer (tile, batch depth), cached per GPU + workload
     rend = api.Renderer(batch, W, H, device=dev, tile=(8, 8), batch_depth=64, persistent=True, grad_overwrite=True)
     cache_path = os.path.join(ROOT, "paper_2604_12626_gb300", "_build", "autotune.json")
-    key = f"{torch.cuda.get_device_name(dev)}|{N_ENVS}x{W}x{H}|N={N}|f16"
+    key = f"{torch.cuda.get_device_name(dev)}|{N_ENVS}x{W}x{H}|N={N}|f16|fwd+bwd"
     cache = {}
     try:
         with open(cache_path) as f:
@@ -232,15 +270,15 @@ def run_ours(args, ws, rank, local):
     except Exception:
         pass
     if args.tile:
-        tw, th, bd = (int(x) for x in args.tile.split(","))
-        rend.cfg.tile_w, rend.cfg.tile_h, rend.cfg.batch_depth = tw, th, bd
-        tuned = {"choice": [tw, th, bd], "fixed": True}
+        ch = [int(x) for x in args.tile.split(",")] + [1, 1]
+        rend.cfg.tile_w, rend.cfg.tile_h, rend.cfg.batch_depth, rend.cfg.pix_x, rend.cfg.pix_y = ch[:5]
+        tuned = {"choice": ch[:5], "fixed": True}
     elif key in cache and not args.retune:
-        tw, th, bd = cache[key]["choice"]
-        rend.cfg.tile_w, rend.cfg.tile_h, rend.cfg.batch_depth = tw, th, bd
+        ch = cache[key]["choice"]
+        rend.cfg.tile_w, rend.cfg.tile_h, rend.cfg.batch_depth, rend.cfg.pix_x, rend.cfg.pix_y = ch
         tuned = dict(cache[key], cached=True)
     else:
-        choice, best_ms = rend.autotune(G16, cams_d, TILE_CANDIDATES, reps=3)
+        choice, best_ms = tune_fwd_bwd(api, rend, G16, cams_d, TILE_CANDIDATES, N, dev)
         tuned = {"choice": list(choice), "ms": best_ms, "cached": False}
         cache[key] = tuned
         try:
@@ -402,7 +440,8 @@ def run_ours(args, ws, rank, local):
                                "forward+backward, SH stored fp16, persistent blend in one CUDA graph, "
                                "autotuned tile", "n_envs_per_gpu": N_ENVS, "gaussians_per_gpu": N,
                    "width": W, "height": H, "tile": [rend.cfg.tile_w, rend.cfg.tile_h],
-                   "batch_depth": rend.cfg.batch_depth, "sh_storage": "f16", "autotune": tuned,
+                   "batch_depth": rend.cfg.batch_depth, "pixels_per_thread": [rend.cfg.pix_x, rend.cfg.pix_y],
+                   "sh_storage": "f16", "autotune": tuned,
                    "l2_policy": "inputs larger than L2 (no flush)", "parallelism": f"env-sharded x{ws}"},
         "fwd": {"value": total_envs / (ms_fwd * 1e-3), "ms_per_step": ms_fwd},
         "plain_per_env": (None if plain_ms is None else

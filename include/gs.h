@@ -101,12 +101,15 @@ typedef struct {
 
 typedef struct {
     int32_t width, height;     /* image size shared by all views */
-    int32_t tile_w, tile_h;    /* blend tile; tile_w * tile_h <= 1024; 0 -> 16 x 16 */
-    int32_t batch_depth;       /* Gaussians staged per shared-memory batch, 32..256; 0 -> 256 */
+    int32_t tile_w, tile_h;    /* blend tile; 0 -> 16 x 16 */
+    int32_t batch_depth;       /* Gaussians staged per shared-memory batch, 32..256 and at most
+                                  4 x the CTA's threads; 0 -> 256 */
     int32_t flags;             /* GS_FLAG_* */
     float bg[3];               /* background colour added with the final transmittance */
     float near_plane;          /* Gaussians with FP32 view depth <= near are culled; 0 -> 0.2 */
     int64_t pair_capacity;     /* max (tile, Gaussian) pairs; 0 -> 4 x records + 65536 */
+    int32_t pix_x, pix_y;      /* pixels per blend thread, each 1 or 2 (0 -> 1); the CTA has
+                                  (tile_w / pix_x) x (tile_h / pix_y) threads, a multiple of 32 */
 } gs_render_config;
 
 /* Per-call counters, read back by gs_render_stats (synchronises). */
@@ -213,12 +216,12 @@ gs_status gs_get_status(void *workspace, size_t workspace_bytes, void *stream, i
 /* Synchronises `stream` and copies the last call's counters. */
 gs_status gs_render_stats(const void *workspace, size_t workspace_bytes, void *stream, gs_stats *out);
 
-/* Times gs_render for each (tile_w, tile_h, batch_depth) candidate on the given
- * inputs (CUDA events on `stream`, `reps` timed runs after one warm-up) and
- * writes the fastest into cfg->tile_w/tile_h/batch_depth.  The workspace must
- * be sized for the largest candidate bin count (8 x 8 tiles).  Results do not
- * depend on the tile (the footprint is per pixel), only the time does.
- * candidates: host [n_candidates][3]; best_ms receives the best time. */
+/* Times gs_render for each (tile_w, tile_h, batch_depth, pix_x, pix_y) candidate
+ * on the given inputs (CUDA events on `stream`, `reps` timed runs after one
+ * warm-up) and writes the fastest into cfg.  Candidates whose workspace does
+ * not fit workspace_bytes are skipped.  Results do not depend on the
+ * candidate (the footprint is per pixel), only the time does.
+ * candidates: host [n_candidates][5]; best_ms receives the best time. */
 gs_status gs_autotune(const gs_gaussians *g, const gs_batch *batch, const gs_camera *cams, gs_render_config *cfg,
                       void *workspace, size_t workspace_bytes, float *out_rgb, float *out_depth, float *out_T,
                       int32_t *out_ncontrib, const int32_t *candidates, int32_t n_candidates, int32_t reps,

@@ -49,7 +49,8 @@ class GsBatch(ctypes.Structure):
 class GsRenderConfig(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("tile_w", ctypes.c_int32),
                 ("tile_h", ctypes.c_int32), ("batch_depth", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("bg", ctypes.c_float * 3), ("near_plane", ctypes.c_float), ("pair_capacity", ctypes.c_int64)]
+                ("bg", ctypes.c_float * 3), ("near_plane", ctypes.c_float), ("pair_capacity", ctypes.c_int64),
+                ("pix_x", ctypes.c_int32), ("pix_y", ctypes.c_int32)]
 
 
 class GsStats(ctypes.Structure):
@@ -179,10 +180,11 @@ def profile_read() -> dict:
 
 
 def make_config(width, height, tile=(16, 16), batch_depth=256, bg=(0.0, 0.0, 0.0), near=0.2, pair_capacity=0,
-                persistent=False, normalize_depth=False, grad_overwrite=False) -> GsRenderConfig:
+                persistent=False, normalize_depth=False, grad_overwrite=False, pix=(1, 1)) -> GsRenderConfig:
     c = GsRenderConfig()
     c.width, c.height = width, height
     c.tile_w, c.tile_h = tile
+    c.pix_x, c.pix_y = pix
     c.batch_depth = batch_depth
     c.flags = ((FLAG_PERSISTENT if persistent else 0) | (FLAG_NORMALIZE_DEPTH if normalize_depth else 0)
                | (FLAG_GRAD_OVERWRITE if grad_overwrite else 0))
@@ -325,10 +327,10 @@ class Renderer:
                     n_bins=s.n_bins, tiles_x=s.tiles_x, tiles_y=s.tiles_y, tiles_per_view=s.tiles_per_view)
 
     def autotune(self, g: Gaussians, cams: torch.Tensor, candidates, reps=3, out=None, stream=None):
-        """Time each (tile_w, tile_h, batch_depth) candidate; keep the fastest in self.cfg."""
+        """Time each (tile_w, tile_h, batch_depth, pix_x, pix_y) candidate; keep the fastest in self.cfg."""
         if out is None:
             out = self.alloc_outputs()
-        cand = np.ascontiguousarray(np.asarray(candidates, np.int32).reshape(-1, 3))
+        cand = np.ascontiguousarray(np.asarray(candidates, np.int32).reshape(-1, 5))
         best = ctypes.c_float(0)
         cfg = GsRenderConfig.from_buffer_copy(self.cfg)
         rgb, depth, T, nc = out
@@ -337,7 +339,7 @@ class Renderer:
                                 cand.ctypes.data_as(_P), len(cand), reps, ctypes.byref(best), _stream(stream)),
                "gs_autotune")
         self.cfg = cfg
-        return (cfg.tile_w, cfg.tile_h, cfg.batch_depth), best.value
+        return (cfg.tile_w, cfg.tile_h, cfg.batch_depth, cfg.pix_x, cfg.pix_y), best.value
 
 
 class Avatars:

@@ -114,7 +114,7 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Plan {
-    int W, H, tw, th, tiles_x, tiles_y, tpv, n_bins, B, flags;
+    int W, H, tw, th, px, py, threads, tiles_x, tiles_y, tpv, n_bins, B, flags;
     int64_t N, R, cap;
     float near_plane;
     // byte offsets
@@ -132,9 +132,13 @@ gs_status make_plan(const gs_render_config *cfg, const gs_batch *b, Plan &p)
     p.H = cfg->height;
     p.tw = cfg->tile_w > 0 ? cfg->tile_w : 16;
     p.th = cfg->tile_h > 0 ? cfg->tile_h : 16;
-    if (p.tw * p.th > 1024 || (p.tw * p.th) % 32 != 0) return GS_ERR_INVALID_ARG;
+    p.px = cfg->pix_x > 0 ? cfg->pix_x : 1;
+    p.py = cfg->pix_y > 0 ? cfg->pix_y : 1;
+    if (p.px > 2 || p.py > 2 || p.tw % p.px || p.th % p.py) return GS_ERR_INVALID_ARG;
+    p.threads = (p.tw / p.px) * (p.th / p.py);
+    if (p.threads > 1024 || p.threads % 32 != 0) return GS_ERR_INVALID_ARG;
     p.B = cfg->batch_depth > 0 ? cfg->batch_depth : 256;
-    if (p.B < 32 || p.B > 256 || p.B > 4 * p.tw * p.th) return GS_ERR_INVALID_ARG;
+    if (p.B < 32 || p.B > 256 || p.B > 4 * p.threads) return GS_ERR_INVALID_ARG;
     p.flags = cfg->flags;
     p.near_plane = cfg->near_plane > 0.0f ? cfg->near_plane : 0.2f;
     p.tiles_x = (p.W + p.tw - 1) / p.tw;
@@ -203,7 +207,7 @@ void fill_table(const Plan &p, const gs_batch *b, const gs_render_config *cfg, i
     std::memset(&t, 0, sizeof(Table));
     t.n_envs = b->n_envs;
     t.n_views = b->n_views;
-    t.W = p.W; t.H = p.H; t.tile_w = p.tw; t.tile_h = p.th;
+    t.W = p.W; t.H = p.H; t.tile_w = p.tw; t.tile_h = p.th; t.pix_x = p.px; t.pix_y = p.py;
     t.tiles_x = p.tiles_x; t.tiles_y = p.tiles_y; t.tiles_per_view = p.tpv; t.n_bins = p.n_bins;
     t.batch_depth = p.B;
     t.flags = p.flags;
@@ -299,16 +303,10 @@ gs_status enqueue_forward(const gs_gaussians *g, const gs_batch *b, const gs_cam
         Stage st5(5, s);
         launch_sort_big(w, sms, s);
     }
-    const int threads = p.tw * p.th;
     const bool persistent = (p.flags & GS_FLAG_PERSISTENT) != 0;
-    int pgrid = 0;
-    if (persistent) {
-        pgrid = sms * blend_blocks_per_sm(threads, p.B);
-        if (pgrid > p.n_bins) pgrid = p.n_bins;
-    }
     {
         Stage st6(6, s);
-        launch_blend(cams, w, rgb, depth, T, ncontrib, p.n_bins, threads, p.B, persistent, pgrid, s);
+        launch_blend(cams, w, rgb, depth, T, ncontrib, p.n_bins, p.px, p.py, p.threads, p.B, persistent, sms, s);
     }
     return check_launch();
 }
@@ -373,14 +371,14 @@ gs_status gs_render_backward(const gs_gaussians *g, const gs_batch *batch, const
         cudaError_t e = cudaMemsetAsync(w.d_rec, 0, (size_t)p.R * 48, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(&w.hdr->queue_bwd, 0, 4, s);
         if (e != cudaSuccess) return cuda_fail(e);
-        int pgrid = sms * blend_backward_blocks_per_sm(p.tw * p.th, p.B);
-        if (pgrid > p.n_bins) pgrid = p.n_bins;
-        launch_blend_backward(cams, w, d_rgb, d_depth, p.n_bins, p.tw * p.th, p.B, pgrid, s);
+        launch_blend_backward(cams, w, d_rgb, d_depth, p.n_bins, p.px, p.py, p.threads, p.B, sms, s);
     }
     {
         Stage st8(8, s);
         GradOut o{d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_cov3d};
-        launch_preprocess_backward(g, cams, w, o, p.N, (cfg->flags & GS_FLAG_GRAD_OVERWRITE) != 0, s);
+        const int chunk = chunk_size(p.N, sms);
+        launch_preprocess_backward(g, cams, w, o, (int)((p.N + chunk - 1) / chunk),
+                                   (cfg->flags & GS_FLAG_GRAD_OVERWRITE) != 0, s);
     }
     return check_launch();
 }
@@ -455,6 +453,7 @@ gs_status gs_render_stats(const void *workspace, size_t workspace_bytes, void *s
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.width = t.W; cfg.height = t.H; cfg.tile_w = t.tile_w; cfg.tile_h = t.tile_h;
     cfg.batch_depth = t.batch_depth; cfg.pair_capacity = t.pair_capacity; cfg.flags = t.flags;
+    cfg.pix_x = t.pix_x; cfg.pix_y = t.pix_y;
     gs_batch bt;
     bt.n_envs = t.n_envs; bt.n_views = t.n_views;
     bt.env_offsets = t.env_off; bt.env_cov3d_begin = nullptr; bt.view_env = t.view_env;
@@ -498,9 +497,11 @@ gs_status gs_autotune(const gs_gaussians *g, const gs_batch *batch, const gs_cam
     gs_status result = GS_OK;
     for (int c = 0; c < n_candidates && result == GS_OK; ++c) {
         gs_render_config k = *cfg;
-        k.tile_w = candidates[3 * c];
-        k.tile_h = candidates[3 * c + 1];
-        k.batch_depth = candidates[3 * c + 2];
+        k.tile_w = candidates[5 * c];
+        k.tile_h = candidates[5 * c + 1];
+        k.batch_depth = candidates[5 * c + 2];
+        k.pix_x = candidates[5 * c + 3];
+        k.pix_y = candidates[5 * c + 4];
         Plan p;
         if (make_plan(&k, batch, p) != GS_OK || p.total > workspace_bytes) continue;
         gs_status st = enqueue_forward(g, batch, cams, &k, workspace, workspace_bytes, out_rgb, out_depth, out_T,

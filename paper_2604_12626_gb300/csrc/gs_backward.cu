@@ -74,49 +74,82 @@ __device__ __forceinline__ float warp_transpose_sum16(float (&v)[16])
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+// Sums v[0..31] over the warp with 31 shuffles (butterfly transpose): on
+// return, lane l holds the warp total of v[l].
+__device__ __forceinline__ float warp_transpose_sum32(float (&v)[32])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16, m = 32; o > 0; o >>= 1, m >>= 1) {
+        const bool up = lane & o;
+#pragma unroll
+        for (int i = 0; i < m / 2; ++i) {
+            const float keep = up ? v[i + m / 2] : v[i], send = up ? v[i] : v[i + m / 2];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
+}
+
 constexpr int kMaxPerB = 4;
+constexpr int kGroup = 3; // Gaussians whose gradients share one warp reduction
 
 // One (view, tile) bin, back to front, batches gathered with cp.async and
-// double-buffered like the forward.
+// double-buffered like the forward.  A thread owns PX x PY pixels and sums
+// their contributions before the warp reduction, so there is one reduction per
+// (warp, Gaussian) for PX x PY x 32 pixels.
+template <int PX, int PY>
 __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera *cams, const float *d_rgb,
                                                    const float *d_depth, int bin, float4 *sm, float *acc,
                                                    uint32_t *sidx, uint32_t *smax_last)
 {
+    constexpr int NP = PX * PY;
     const Table *tb = w.tb;
     const int B = tb->batch_depth;
     const int nthr = blockDim.x;
     const int v = bin / tb->tiles_per_view;
     const int t = bin - v * tb->tiles_per_view;
     const int tyi = t / tb->tiles_x, txi = t - tyi * tb->tiles_x;
-    const int lx = threadIdx.x % tb->tile_w, ly = threadIdx.x / tb->tile_w;
-    const int i = txi * tb->tile_w + lx, j = tyi * tb->tile_h + ly;
+    const int tcols = tb->tile_w / PX;
+    const int i0 = txi * tb->tile_w + (threadIdx.x % tcols) * PX, j0 = tyi * tb->tile_h + (threadIdx.x / tcols) * PY;
     const int W = tb->W, H = tb->H;
-    const bool inside = i < W && j < H;
     const gs_camera &cam = cams[v];
-    const float pxc = pix_c(i, cam.cx), pyc = pix_c(j, cam.cy);
+    float pxc[PX], pyc[PY];
+#pragma unroll
+    for (int a = 0; a < PX; ++a) pxc[a] = pix_c(i0 + a, cam.cx);
+#pragma unroll
+    for (int b = 0; b < PY; ++b) pyc[b] = pix_c(j0 + b, cam.cy);
     const size_t HW = (size_t)W * H;
-    const size_t p = (size_t)j * W + i;
     uint32_t start, n;
     bin_range_b(w, bin, start, n);
     const unsigned long long *keys = w.keys + start;
     const uint32_t R = (uint32_t)tb->n_records;
 
-    float T = 1.0f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f, dD = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f, SD = 0.f;
-    uint32_t last = 0;
-    if (inside) {
-        T = w.pix_T[(size_t)v * HW + p];
-        last = w.pix_last[(size_t)v * HW + p];
-        dC0 = d_rgb[(3 * (size_t)v + 0) * HW + p];
-        dC1 = d_rgb[(3 * (size_t)v + 1) * HW + p];
-        dC2 = d_rgb[(3 * (size_t)v + 2) * HW + p];
-        dD = d_depth[(size_t)v * HW + p];
-        S0 = T * tb->bg[0];
-        S1 = T * tb->bg[1];
-        S2 = T * tb->bg[2];
+    float T[NP], dC0[NP], dC1[NP], dC2[NP], dD[NP], S0[NP], S1[NP], S2[NP], SD[NP];
+    uint32_t last[NP];
+    uint32_t tlast = 0;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int i = i0 + p % PX, j = j0 + p / PX;
+        T[p] = 1.0f; dC0[p] = dC1[p] = dC2[p] = dD[p] = 0.f; S0[p] = S1[p] = S2[p] = SD[p] = 0.f;
+        last[p] = 0;
+        if (i < W && j < H) {
+            const size_t px = (size_t)j * W + i;
+            T[p] = w.pix_T[(size_t)v * HW + px];
+            last[p] = w.pix_last[(size_t)v * HW + px];
+            dC0[p] = d_rgb[(3 * (size_t)v + 0) * HW + px];
+            dC1[p] = d_rgb[(3 * (size_t)v + 1) * HW + px];
+            dC2[p] = d_rgb[(3 * (size_t)v + 2) * HW + px];
+            dD[p] = d_depth[(size_t)v * HW + px];
+            S0[p] = T[p] * tb->bg[0];
+            S1[p] = T[p] * tb->bg[1];
+            S2[p] = T[p] * tb->bg[2];
+        }
+        tlast = max(tlast, last[p]);
     }
     if (threadIdx.x == 0) *smax_last = 0;
     __syncthreads();
-    const uint32_t wl = __reduce_max_sync(0xffffffffu, last);
+    const uint32_t wl = __reduce_max_sync(0xffffffffu, tlast);
     if ((threadIdx.x & 31) == 0) atomicMax(smax_last, wl);
     __syncthreads();
     const uint32_t n_proc = min(*smax_last, n);
@@ -167,57 +200,80 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
         cp_async_wait<1>();
         __syncthreads();
         const float4 *s0 = sm + (b & 1) * 3 * B, *s1 = s0 + B, *s2 = s0 + 2 * B;
-        for (int k = cnt - 1; k >= 0; --k) {
-            const uint32_t pos = (uint32_t)(lo + k);
-            float g[16];
+        // groups of kGroup Gaussians, back to front: falloff and alpha first
+        // (independent of T), then the sequential transmittance rebuild and
+        // gradients, then one warp reduction of the group's 10 x kGroup sums
+        for (int k1 = cnt - 1; k1 >= 0; k1 -= kGroup) {
+            float g[32];
 #pragma unroll
-            for (int x = 0; x < 16; ++x) g[x] = 0.f;
+            for (int x = 0; x < 32; ++x) g[x] = 0.f;
             bool contrib = false;
-            if (pos < last) {
-                const float4 a = s0[k];
-                const float dx = __fsub_rn(a.x, pxc), dy = __fsub_rn(a.y, pyc);
-                if (fmaxf(fabsf(dx), fabsf(dy)) <= a.w) {
-                    const float4 q = s1[k];
-                    const float power = gauss_power(q.x, q.y, q.z, dx, dy);
-                    if (power <= 0.0f) {
-                        const float ar = raw_alpha(q.w, power);
-                        const float alpha = fminf(kAlphaMax, ar);
-                        if (alpha >= kAlphaMin) {
+            if (__any_sync(0xffffffffu, (uint32_t)(lo + k1 - (kGroup - 1)) < tlast || k1 < kGroup - 1)) {
+                float ar[kGroup][NP], dxs[kGroup][NP], dys[kGroup][NP];
+                bool ok[kGroup][NP];
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u) {
+                    const int k = k1 - u;
+                    const float4 a = s0[k < 0 ? 0 : k];
+                    const float4 q = s1[k < 0 ? 0 : k];
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        const float dx = __fsub_rn(a.x, pxc[p % PX]), dy = __fsub_rn(a.y, pyc[p / PX]);
+                        const float power = gauss_power(q.x, q.y, q.z, dx, dy);
+                        ar[u][p] = raw_alpha(q.w, power);
+                        dxs[u][p] = dx;
+                        dys[u][p] = dy;
+                        ok[u][p] = k >= 0 && (uint32_t)(lo + k) < last[p] && fmaxf(fabsf(dx), fabsf(dy)) <= a.w &&
+                                   power <= 0.0f && fminf(kAlphaMax, ar[u][p]) >= kAlphaMin;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u) {
+                    const int k = k1 - u;
+                    const float4 a = s0[k < 0 ? 0 : k];
+                    const float4 q = s1[k < 0 ? 0 : k];
+                    const float4 c = s2[k < 0 ? 0 : k];
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        if (ok[u][p]) {
                             contrib = true;
-                            const float4 c = s2[k];
+                            const float alpha = fminf(kAlphaMax, ar[u][p]);
                             const float om = 1.0f - alpha;
-                            const float Ti = T / om;
+                            const float Ti = T[p] / om;
                             const float wgt = alpha * Ti;
-                            g[6] = wgt * dC0;
-                            g[7] = wgt * dC1;
-                            g[8] = wgt * dC2;
-                            g[9] = wgt * dD;
+                            float *gu = g + 10 * u;
+                            gu[6] += wgt * dC0[p];
+                            gu[7] += wgt * dC1[p];
+                            gu[8] += wgt * dC2[p];
+                            gu[9] += wgt * dD[p];
                             const float iom = 1.0f / om;
-                            const float dal = dC0 * (c.x * Ti - S0 * iom) + dC1 * (c.y * Ti - S1 * iom) +
-                                              dC2 * (c.z * Ti - S2 * iom) + dD * (a.z * Ti - SD * iom);
-                            S0 += c.x * wgt;
-                            S1 += c.y * wgt;
-                            S2 += c.z * wgt;
-                            SD += a.z * wgt;
-                            T = Ti;
-                            if (ar < kAlphaMax) {
-                                const float G = ar / q.w;
-                                g[5] = dal * G;
+                            const float dal = dC0[p] * (c.x * Ti - S0[p] * iom) + dC1[p] * (c.y * Ti - S1[p] * iom) +
+                                              dC2[p] * (c.z * Ti - S2[p] * iom) + dD[p] * (a.z * Ti - SD[p] * iom);
+                            S0[p] += c.x * wgt;
+                            S1[p] += c.y * wgt;
+                            S2[p] += c.z * wgt;
+                            SD[p] += a.z * wgt;
+                            T[p] = Ti;
+                            if (ar[u][p] < kAlphaMax) {
+                                const float dx = dxs[u][p], dy = dys[u][p];
+                                const float G = ar[u][p] / q.w;
+                                gu[5] += dal * G;
                                 const float gp = dal * alpha;
-                                g[0] = -gp * (q.x * dx + q.y * dy);
-                                g[1] = -gp * (q.z * dy + q.y * dx);
-                                g[2] = -0.5f * gp * dx * dx;
-                                g[4] = -0.5f * gp * dy * dy;
-                                g[3] = -gp * dx * dy;
+                                gu[0] += -gp * (q.x * dx + q.y * dy);
+                                gu[1] += -gp * (q.z * dy + q.y * dx);
+                                gu[2] += -0.5f * gp * dx * dx;
+                                gu[4] += -0.5f * gp * dy * dy;
+                                gu[3] += -gp * dx * dy;
                             }
                         }
                     }
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-                const float tot = warp_transpose_sum16(g);
-                const int idx = (lane >> 1) & 15;
-                if (!(lane & 1) && idx < 10) atomicAdd(acc + k * kGradStride + idx, tot);
+                const float tot = warp_transpose_sum32(g);
+                const int u = lane / 10, j = lane - 10 * u;
+                const int k = k1 - u;
+                if (lane < 10 * kGroup && k >= 0) atomicAdd(acc + k * kGradStride + j, tot);
             }
         }
         __syncthreads();
@@ -238,6 +294,7 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
     cp_async_wait<0>();
 }
 
+template <int PX, int PY>
 __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, const float *__restrict__ d_rgb,
                                       const float *__restrict__ d_depth)
 {
@@ -253,7 +310,7 @@ __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, 
         __syncthreads();
         if (item >= n_items) break;
         const int bin = bin_of_item(w, item);
-        if (bin >= 0) blend_backward_tile(w, cams, d_rgb, d_depth, bin, smem_b, acc, sidx, &smax_last);
+        if (bin >= 0) blend_backward_tile<PX, PY>(w, cams, d_rgb, d_depth, bin, smem_b, acc, sidx, &smax_last);
     }
 }
 
@@ -332,27 +389,73 @@ struct GaussInB {
     const void *sh;
 };
 
+// Streams the 48 SH coefficients of Gaussian g and returns, per basis
+// function, sum_ch k[i][ch] * gch[ch].
+template <int SHT>
+__device__ __forceinline__ void sh_weighted(const void *sh, int64_t g, const float (&gch)[3], float (&wk)[16])
+{
+#pragma unroll
+    for (int i = 0; i < 16; ++i) wk[i] = 0.f;
+    if (SHT == GS_SH_F32) {
+        const float4 *p = reinterpret_cast<const float4 *>(sh) + g * 12;
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            const float4 v = __ldg(p + i);
+            const float c[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) wk[(4 * i + j) / 3] += c[j] * gch[(4 * i + j) % 3];
+        }
+    } else {
+        const uint4 *p = reinterpret_cast<const uint4 *>(sh) + g * 6;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const uint4 v = __ldg(p + i);
+            const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float lo, hi;
+                if (SHT == GS_SH_F16) {
+                    const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&u[j]));
+                    lo = f.x;
+                    hi = f.y;
+                } else {
+                    lo = __uint_as_float(u[j] << 16);
+                    hi = __uint_as_float(u[j] & 0xffff0000u);
+                }
+                wk[(8 * i + 2 * j) / 3] += lo * gch[(8 * i + 2 * j) % 3];
+                wk[(8 * i + 2 * j + 1) / 3] += hi * gch[(8 * i + 2 * j + 1) % 3];
+            }
+        }
+    }
+}
+
+// Full chain for one Gaussian seen by at least one view: screen-space
+// gradients of each visible view back to the Gaussian's parameters.
 template <int SHT, bool OVERWRITE>
-__global__ void __launch_bounds__(256) preprocess_backward_kernel(const gs_camera *__restrict__ cams, GaussInB gin,
-                                                                  Ws w, GradOut o)
+__device__ __forceinline__ void gaussian_backward(const gs_camera *__restrict__ cams, const GaussInB &gin, const Ws &w,
+                                                  const GradOut &o, int64_t g)
 {
     const Table *tb = w.tb;
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= tb->n_gauss) return;
     const int e = find_env_b(tb, g);
     const int vb = tb->env_view_begin[e], ve = tb->env_view_begin[e + 1];
     const int64_t local = g - tb->env_off[e];
     const bool use_cov = gin.cov3d != nullptr && g >= tb->env_cov_begin[e];
     const float mx = __ldg(gin.means + 3 * g), my = __ldg(gin.means + 3 * g + 1), mz = __ldg(gin.means + 3 * g + 2);
     float S[6];
-    bool have_sigma = false, any = false, have_sh = false;
+    if (use_cov) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) S[i] = __ldg(gin.cov3d + 6 * g + i);
+    } else {
+        const float3 ls = make_float3(__ldg(gin.log_scales + 3 * g), __ldg(gin.log_scales + 3 * g + 1),
+                                      __ldg(gin.log_scales + 3 * g + 2));
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(gin.quats) + g);
+        sigma_from_sq(ls, q, S);
+    }
+    const float op = 1.0f / (1.0f + expf(-__ldg(gin.ologits + g)));
     float gS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float gm0 = 0.f, gm1 = 0.f, gm2 = 0.f, go = 0.f;
-    float gsh[48];
-    float kk[48];
-#pragma unroll
-    for (int i = 0; i < 48; ++i) gsh[i] = 0.f;
-    float op = 0.f;
+    bool first_sh = true;
+    float4 *dsh4 = reinterpret_cast<float4 *>(o.sh + 48 * g);
     const int W = tb->W, H = tb->H;
     for (int kv = vb; kv < ve; ++kv) {
         const int v = tb->env_views[kv];
@@ -361,31 +464,15 @@ __global__ void __launch_bounds__(256) preprocess_backward_kernel(const gs_camer
         const float4 *gr4 = reinterpret_cast<const float4 *>(w.d_rec + (size_t)rec * kGradStride);
         const float4 r0 = gr4[0], r1 = gr4[1], r2 = gr4[2];
         // (uc, vc, A, B, C, opacity, r, g, b, z)
-        const float g_u = r0.x, g_v = r0.y, gA = r0.z, gB = r0.w, gC = r1.x, g_op = r1.y, g_r = r1.z, g_g = r1.w,
-                    g_b = r2.x, g_z = r2.y;
+        const float g_u = r0.x, g_v = r0.y, gA = r0.z, gB = r0.w, gC = r1.x, g_op = r1.y;
+        const float4 col = w.rec[3 * (size_t)rec + 2]; // a channel clamped at 0 passes no gradient
+        float gch[3] = {col.x > 0.f ? r1.z : 0.f, col.y > 0.f ? r1.w : 0.f, col.z > 0.f ? r2.x : 0.f};
+        const float g_z = r2.y;
         const gs_camera &cam = cams[v];
-        if (!have_sigma) {
-            if (use_cov) {
-#pragma unroll
-                for (int i = 0; i < 6; ++i) S[i] = __ldg(gin.cov3d + 6 * g + i);
-            } else {
-                const float3 ls = make_float3(__ldg(gin.log_scales + 3 * g), __ldg(gin.log_scales + 3 * g + 1),
-                                              __ldg(gin.log_scales + 3 * g + 2));
-                const float4 q = __ldg(reinterpret_cast<const float4 *>(gin.quats) + g);
-                sigma_from_sq(ls, q, S);
-            }
-            have_sigma = true;
-        }
-        if (!have_sh) {
-            load_sh_b<SHT>(gin.sh, g, kk);
-            op = 1.0f / (1.0f + expf(-__ldg(gin.ologits + g)));
-            have_sh = true;
-        }
-        any = true;
         const float zk = depth_key(mx, my, mz, cam);
         Proj pj;
         project_ewa(mx, my, mz, zk, S, cam, W, H, pj);
-        const float px = pj.px, py = pj.py, pz = pj.pz, ipz = 1.0f / pz, ipz2 = ipz * ipz;
+        const float px = pj.px, py = pj.py, ipz = 1.0f / pj.pz, ipz2 = ipz * ipz;
         float gpx = g_u * cam.fx * ipz, gpy = g_v * cam.fy * ipz;
         float gpz = -g_u * cam.fx * px * ipz2 - g_v * cam.fy * py * ipz2 + g_z;
         // conic = (c, -b, a) / det
@@ -435,27 +522,26 @@ __global__ void __launch_bounds__(256) preprocess_backward_kernel(const gs_camer
         float gd0 = cam.R[0] * gpx + cam.R[3] * gpy + cam.R[6] * gpz;
         float gd1 = cam.R[1] * gpx + cam.R[4] * gpy + cam.R[7] * gpz;
         float gd2 = cam.R[2] * gpx + cam.R[5] * gpy + cam.R[8] * gpz;
-        // colour
+        // colour: SH coefficients get Y(dir) x gch, the direction gets grad(Y) . (k gch)
         const float dnorm = sqrtf(pj.d0 * pj.d0 + pj.d1 * pj.d1 + pj.d2 * pj.d2), idn = 1.0f / dnorm;
         const float x = pj.d0 * idn, y = pj.d1 * idn, z = pj.d2 * idn;
         float Y[16];
         sh_basis(x, y, z, Y);
-        float gch[3] = {g_r, g_g, g_b};
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float raw = 0.5f;
+        for (int i = 0; i < 12; ++i) {
+            float vals[4];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) raw += Y[i] * kk[3 * i + ch];
-            if (raw < 0.0f) gch[ch] = 0.0f;
+            for (int jj = 0; jj < 4; ++jj) vals[jj] = Y[(4 * i + jj) / 3] * gch[(4 * i + jj) % 3];
+            float4 val = make_float4(vals[0], vals[1], vals[2], vals[3]);
+            if (!(OVERWRITE && first_sh)) {
+                const float4 cur = dsh4[i];
+                val = make_float4(cur.x + val.x, cur.y + val.y, cur.z + val.z, cur.w + val.w);
+            }
+            dsh4[i] = val;
         }
+        first_sh = false;
         float wk[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            gsh[3 * i] += Y[i] * gch[0];
-            gsh[3 * i + 1] += Y[i] * gch[1];
-            gsh[3 * i + 2] += Y[i] * gch[2];
-            wk[i] = kk[3 * i] * gch[0] + kk[3 * i + 1] * gch[1] + kk[3 * i + 2] * gch[2];
-        }
+        sh_weighted<SHT>(gin.sh, g, gch, wk);
         float gx = 0.f, gy = 0.f, gz = 0.f;
         sh_dir_vjp(x, y, z, wk, gx, gy, gz);
         const float dot = gx * x + gy * y + gz * z;
@@ -467,39 +553,16 @@ __global__ void __launch_bounds__(256) preprocess_backward_kernel(const gs_camer
         gm2 += gd2;
         go += g_op;
     }
-    if (!any) {
-        if (OVERWRITE) {
-            for (int i = 0; i < 3; ++i) o.means[3 * g + i] = 0.f;
-            o.ologits[g] = 0.f;
-            float4 *dsh4 = reinterpret_cast<float4 *>(o.sh + 48 * g);
-#pragma unroll
-            for (int i = 0; i < 12; ++i) dsh4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (use_cov) {
-                if (o.cov3d)
-                    for (int i = 0; i < 6; ++i) o.cov3d[6 * g + i] = 0.f;
-            } else {
-                for (int i = 0; i < 3; ++i) o.log_scales[3 * g + i] = 0.f;
-                reinterpret_cast<float4 *>(o.quats)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
-        return;
-    }
     if (OVERWRITE) {
         o.means[3 * g] = gm0;
         o.means[3 * g + 1] = gm1;
         o.means[3 * g + 2] = gm2;
         o.ologits[g] = go * op * (1.0f - op);
-        float4 *dsh4 = reinterpret_cast<float4 *>(o.sh + 48 * g);
-#pragma unroll
-        for (int i = 0; i < 12; ++i) dsh4[i] = make_float4(gsh[4 * i], gsh[4 * i + 1], gsh[4 * i + 2], gsh[4 * i + 3]);
     } else {
         o.means[3 * g] += gm0;
         o.means[3 * g + 1] += gm1;
         o.means[3 * g + 2] += gm2;
         o.ologits[g] += go * op * (1.0f - op);
-        float *dsh = o.sh + 48 * g;
-#pragma unroll
-        for (int i = 0; i < 48; ++i) dsh[i] += gsh[i];
     }
     if (use_cov) {
         if (o.cov3d) {
@@ -547,9 +610,69 @@ __global__ void __launch_bounds__(256) preprocess_backward_kernel(const gs_camer
     if (OVERWRITE) {
         *dqo = gq4;
     } else {
-        float4 cur = *dqo;
+        const float4 cur = *dqo;
         *dqo = make_float4(cur.x + gq4.x, cur.y + gq4.y, cur.z + gq4.z, cur.w + gq4.w);
     }
+}
+
+// Zero gradient rows of a Gaussian no view sees (overwrite mode).
+__device__ __forceinline__ void zero_rows(const GradOut &o, int64_t g, bool use_cov)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o.means[3 * g + i] = 0.f;
+    o.ologits[g] = 0.f;
+    float4 *dsh4 = reinterpret_cast<float4 *>(o.sh + 48 * g);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) dsh4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (use_cov) {
+        if (o.cov3d)
+            for (int i = 0; i < 6; ++i) o.cov3d[6 * g + i] = 0.f;
+    } else {
+        for (int i = 0; i < 3; ++i) o.log_scales[3 * g + i] = 0.f;
+        reinterpret_cast<float4 *>(o.quats)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// Chunked like the forward preprocess: every lane checks whether any view sees
+// its Gaussian (zero rows otherwise, in overwrite mode); the seen ones go
+// through a per-warp ring queue and are processed 32 at a time, so that the
+// long chain runs on full warps.
+constexpr int kBwdWarpQ = 64;
+
+template <int SHT, bool OVERWRITE>
+__global__ void __launch_bounds__(256, 2) preprocess_backward_kernel(const gs_camera *__restrict__ cams, GaussInB gin,
+                                                                     Ws w, GradOut o)
+{
+    __shared__ uint32_t qs[8][kBwdWarpQ];
+    const Table *tb = w.tb;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    uint32_t *q = qs[warp];
+    const int64_t g0 = (int64_t)blockIdx.x * tb->chunk, g1 = min(g0 + tb->chunk, tb->n_gauss);
+    int head = 0, tail = 0;
+    for (int64_t base = g0 + warp * 32; base < g1; base += 32 * nwarps) {
+        const int64_t g = base + lane;
+        bool seen = false;
+        if (g < g1) {
+            const int e = find_env_b(tb, g);
+            const int64_t local = g - tb->env_off[e];
+            for (int kv = tb->env_view_begin[e]; kv < tb->env_view_begin[e + 1] && !seen; ++kv) {
+                const uint32_t rec = (uint32_t)(tb->view_rec_off[tb->env_views[kv]] + local);
+                seen = (__ldg(w.vis + (rec >> 5)) >> (rec & 31)) & 1u;
+            }
+            if (!seen && OVERWRITE) zero_rows(o, g, gin.cov3d != nullptr && g >= tb->env_cov_begin[e]);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, seen);
+        if (seen) q[(tail + __popc(bal & ((1u << lane) - 1u))) & (kBwdWarpQ - 1)] = (uint32_t)(g - g0);
+        tail += __popc(bal);
+        __syncwarp();
+        if (tail - head >= 32) {
+            const int64_t gg = g0 + q[(head + lane) & (kBwdWarpQ - 1)];
+            head += 32;
+            __syncwarp();
+            gaussian_backward<SHT, OVERWRITE>(cams, gin, w, o, gg);
+        }
+    }
+    if (lane < tail - head) gaussian_backward<SHT, OVERWRITE>(cams, gin, w, o, g0 + q[(head + lane) & (kBwdWarpQ - 1)]);
 }
 
 // ---------------------------------------------------------------------------
@@ -574,18 +697,25 @@ static int blend_bwd_smem(int batch_depth)
     return 2 * 3 * batch_depth * (int)sizeof(float4) + batch_depth * kGradStride * 4 + 2 * batch_depth * 4;
 }
 
-void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,
-                           int threads, int batch_depth, int persistent_grid, cudaStream_t s)
+template <int PX, int PY>
+static void launch_bb(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,
+                      int threads, int batch_depth, int n_sms, cudaStream_t s)
 {
-    (void)n_bins;
-    blend_backward_kernel<<<persistent_grid, threads, blend_bwd_smem(batch_depth), s>>>(cams, w, d_rgb, d_depth);
+    const int smem = blend_bwd_smem(batch_depth);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blend_backward_kernel<PX, PY>, threads, smem);
+    int grid = n_sms * (nb > 0 ? nb : 1);
+    if (grid > n_bins) grid = n_bins;
+    blend_backward_kernel<PX, PY><<<grid, threads, smem, s>>>(cams, w, d_rgb, d_depth);
 }
 
-int blend_backward_blocks_per_sm(int threads, int batch_depth)
+void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,
+                           int px, int py, int threads, int batch_depth, int n_sms, cudaStream_t s)
 {
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blend_backward_kernel, threads, blend_bwd_smem(batch_depth));
-    return nb > 0 ? nb : 1;
+    if (px == 2 && py == 2) launch_bb<2, 2>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, s);
+    else if (px == 2) launch_bb<2, 1>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, s);
+    else if (py == 2) launch_bb<1, 2>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, s);
+    else launch_bb<1, 1>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, s);
 }
 
 template <bool OW>
@@ -601,9 +731,9 @@ static void launch_pb(const gs_gaussians *g, const gs_camera *cams, const Ws &w,
 }
 
 void launch_preprocess_backward(const gs_gaussians *g, const gs_camera *cams, const Ws &w, const GradOut &o,
-                                int64_t n, bool overwrite, cudaStream_t s)
+                                int n_chunks, bool overwrite, cudaStream_t s)
 {
-    const unsigned grid = (unsigned)((n + 255) / 256);
+    const unsigned grid = (unsigned)n_chunks;
     if (!grid) return;
     if (overwrite) launch_pb<true>(g, cams, w, o, grid, s);
     else launch_pb<false>(g, cams, w, o, grid, s);
@@ -611,7 +741,15 @@ void launch_preprocess_backward(const gs_gaussians *g, const gs_camera *cams, co
 
 cudaError_t configure_backward_kernels()
 {
-    return cudaFuncSetAttribute(blend_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, blend_bwd_smem(256));
+    const int smem = blend_bwd_smem(256);
+    cudaError_t e = cudaFuncSetAttribute(blend_backward_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(blend_backward_kernel<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(blend_backward_kernel<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(blend_backward_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
 }
 
 } // namespace gs

@@ -638,24 +638,32 @@ struct OutPtrs {
     int32_t *ncontrib;
 };
 
-// Blends one (view, tile) bin.  Batches of B records are gathered into shared
-// memory with cp.async, double-buffered: batch b+1 is in flight while batch b
-// is blended (keys of batch b+2 are prefetched into registers).
+// Blends one (view, tile) bin.  Each thread owns PX x PY neighbouring pixels,
+// so every Gaussian fetched from shared memory serves several pixels.  Batches
+// of B records are gathered into shared memory with cp.async, double-buffered:
+// batch b+1 is in flight while batch b is blended (keys of batch b+2 are
+// prefetched into registers).
 constexpr int kMaxPer = 4; // records per thread and batch (B <= 4 x threads)
+constexpr int kUnroll = 4; // Gaussians evaluated together in the blend loop
 
+template <int PX, int PY>
 __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, const OutPtrs &o, int bin,
                                           float4 *sm)
 {
+    constexpr int NP = PX * PY;
     const Table *tb = w.tb;
     const int v = bin / tb->tiles_per_view;
     const int t = bin - v * tb->tiles_per_view;
     const int tyi = t / tb->tiles_x, txi = t - tyi * tb->tiles_x;
-    const int lx = threadIdx.x % tb->tile_w, ly = threadIdx.x / tb->tile_w;
-    const int i = txi * tb->tile_w + lx, j = tyi * tb->tile_h + ly;
+    const int tcols = tb->tile_w / PX;
+    const int i0 = txi * tb->tile_w + (threadIdx.x % tcols) * PX, j0 = tyi * tb->tile_h + (threadIdx.x / tcols) * PY;
     const int W = tb->W, H = tb->H;
-    const bool inside = i < W && j < H;
     const gs_camera &cam = cams[v];
-    const float pxc = pix_c(i, cam.cx), pyc = pix_c(j, cam.cy);
+    float pxc[PX], pyc[PY];
+#pragma unroll
+    for (int a = 0; a < PX; ++a) pxc[a] = pix_c(i0 + a, cam.cx);
+#pragma unroll
+    for (int b = 0; b < PY; ++b) pyc[b] = pix_c(j0 + b, cam.cy);
     uint32_t start, n;
     bin_range(w, bin, start, n);
     const unsigned long long *keys = w.keys + start;
@@ -688,10 +696,20 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
             }
         }
     };
-    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, D = 0.0f;
-    int32_t ncov = 0, ncon = 0;
-    uint32_t last = 0;
-    bool done = !inside;
+    float T[NP], C0[NP], C1[NP], C2[NP], D[NP];
+    int32_t ncov[NP], ncon[NP];
+    uint32_t last[NP];
+    bool dn[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        T[p] = 1.0f; C0[p] = C1[p] = C2[p] = D[p] = 0.0f;
+        ncov[p] = ncon[p] = 0;
+        last[p] = 0;
+        dn[p] = !(i0 + p % PX < W && j0 + p / PX < H);
+    }
+    bool tdone = true;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) tdone = tdone && dn[p];
     if (nb > 0) {
         load_keys(0);
         issue(0);
@@ -703,66 +721,95 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
         cp_async_commit();
         if (b + 2 < nb) load_keys(b + 2);
         cp_async_wait<1>();
-        if (__syncthreads_count(done) == nthr) break;
+        if (__syncthreads_count(tdone) == nthr) break;
         const float4 *s0 = sm + (b & 1) * 3 * B, *s1 = s0 + B, *s2 = s0 + 2 * B;
         const int cnt = (int)min((uint32_t)B, n - (uint32_t)b * B);
         // warp-synchronous: every lane runs the same iterations (predicated),
-        // the warp leaves once all its lanes have stopped
-        for (int k = 0; k < cnt; ++k) {
-            if (__all_sync(0xffffffffu, done)) break;
-            if (!done) {
-                const float4 a = s0[k];
-                const float dx = __fsub_rn(a.x, pxc), dy = __fsub_rn(a.y, pyc);
-                if (fmaxf(fabsf(dx), fabsf(dy)) <= a.w) {
-                    ++ncov;
-                    const float4 q = s1[k];
-                    const float power = gauss_power(q.x, q.y, q.z, dx, dy);
-                    const float alpha = fminf(kAlphaMax, raw_alpha(q.w, power));
-                    if (power <= 0.0f && alpha >= kAlphaMin) {
-                        const float Tn = T * (1.0f - alpha);
-                        if (Tn < kTStop) {
-                            done = true;
-                        } else {
-                            const float wgt = alpha * T;
-                            const float4 c = s2[k];
-                            C0 += c.x * wgt;
-                            C1 += c.y * wgt;
-                            C2 += c.z * wgt;
-                            D += a.z * wgt;
-                            T = Tn;
-                            ncon = ncov;
-                            last = (uint32_t)b * B + k + 1;
+        // the warp leaves once all its lanes have stopped.  Four Gaussians at a
+        // time: their falloff and alpha (independent of T) first, for ILP, then
+        // the front-to-back updates in order.
+        for (int k0 = 0; k0 < cnt; k0 += kUnroll) {
+            if (__all_sync(0xffffffffu, tdone)) break;
+            if (!tdone) {
+                float al[kUnroll][NP];
+                bool ok[kUnroll][NP], cv[kUnroll][NP];
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    const float4 a = s0[k0 + u]; // B is a multiple of kUnroll: stays in the buffer
+                    const float4 q = s1[k0 + u];
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        const float dx = __fsub_rn(a.x, pxc[p % PX]), dy = __fsub_rn(a.y, pyc[p / PX]);
+                        cv[u][p] = (k0 + u < cnt) && fmaxf(fabsf(dx), fabsf(dy)) <= a.w;
+                        const float power = gauss_power(q.x, q.y, q.z, dx, dy);
+                        al[u][p] = fminf(kAlphaMax, raw_alpha(q.w, power));
+                        ok[u][p] = cv[u][p] && power <= 0.0f && al[u][p] >= kAlphaMin;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    const float4 c = s2[k0 + u];
+                    const float z = s0[k0 + u].z;
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        if (!dn[p] && cv[u][p]) {
+                            ++ncov[p];
+                            if (ok[u][p]) {
+                                const float alpha = al[u][p];
+                                const float Tn = T[p] * (1.0f - alpha);
+                                if (Tn < kTStop) {
+                                    dn[p] = true;
+                                } else {
+                                    const float wgt = alpha * T[p];
+                                    C0[p] += c.x * wgt;
+                                    C1[p] += c.y * wgt;
+                                    C2[p] += c.z * wgt;
+                                    D[p] += z * wgt;
+                                    T[p] = Tn;
+                                    ncon[p] = ncov[p];
+                                    last[p] = (uint32_t)b * B + k0 + u + 1;
+                                }
+                            }
                         }
                     }
                 }
+                tdone = true;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) tdone = tdone && dn[p];
             }
             __syncwarp();
         }
         __syncthreads();
     }
     cp_async_wait<0>();
-    if (inside) {
-        const size_t HW = (size_t)W * H;
-        const size_t p = (size_t)j * W + i;
-        o.rgb[(3 * (size_t)v + 0) * HW + p] = C0 + T * tb->bg[0];
-        o.rgb[(3 * (size_t)v + 1) * HW + p] = C1 + T * tb->bg[1];
-        o.rgb[(3 * (size_t)v + 2) * HW + p] = C2 + T * tb->bg[2];
-        float dd = D;
-        if (tb->flags & GS_FLAG_NORMALIZE_DEPTH) dd = (1.0f - T) < 1e-4f ? 0.0f : D / (1.0f - T);
-        o.depth[(size_t)v * HW + p] = dd;
-        o.T[(size_t)v * HW + p] = T;
-        o.ncontrib[(size_t)v * HW + p] = ncon;
-        w.pix_T[(size_t)v * HW + p] = T;
-        w.pix_last[(size_t)v * HW + p] = last;
+    const size_t HW = (size_t)W * H;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int i = i0 + p % PX, j = j0 + p / PX;
+        if (i < W && j < H) {
+            const size_t px = (size_t)j * W + i;
+            o.rgb[(3 * (size_t)v + 0) * HW + px] = C0[p] + T[p] * tb->bg[0];
+            o.rgb[(3 * (size_t)v + 1) * HW + px] = C1[p] + T[p] * tb->bg[1];
+            o.rgb[(3 * (size_t)v + 2) * HW + px] = C2[p] + T[p] * tb->bg[2];
+            float dd = D[p];
+            if (tb->flags & GS_FLAG_NORMALIZE_DEPTH) dd = (1.0f - T[p]) < 1e-4f ? 0.0f : D[p] / (1.0f - T[p]);
+            o.depth[(size_t)v * HW + px] = dd;
+            o.T[(size_t)v * HW + px] = T[p];
+            o.ncontrib[(size_t)v * HW + px] = ncon[p];
+            w.pix_T[(size_t)v * HW + px] = T[p];
+            w.pix_last[(size_t)v * HW + px] = last[p];
+        }
     }
 }
 
+template <int PX, int PY>
 __global__ void blend_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
 {
     extern __shared__ float4 smem_f4[];
-    blend_tile(w, cams, o, blockIdx.x, smem_f4);
+    blend_tile<PX, PY>(w, cams, o, blockIdx.x, smem_f4);
 }
 
+template <int PX, int PY>
 __global__ void blend_persistent_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
 {
     extern __shared__ float4 smem_f4[];
@@ -774,7 +821,7 @@ __global__ void blend_persistent_kernel(const gs_camera *__restrict__ cams, Ws w
         __syncthreads();
         if (item >= n_items) break;
         const int bin = bin_of_item(w, item);
-        if (bin >= 0) blend_tile(w, cams, o, bin, smem_f4);
+        if (bin >= 0) blend_tile<PX, PY>(w, cams, o, bin, smem_f4);
     }
 }
 
@@ -828,15 +875,31 @@ void launch_sort_big(const Ws &w, int n_sms, cudaStream_t s)
 
 int blend_smem_bytes(int batch_depth) { return 2 * 3 * batch_depth * (int)sizeof(float4); }
 
+template <int PX, int PY>
+static void launch_blend_t(const gs_camera *cams, const Ws &w, const OutPtrs &o, int n_bins, int threads,
+                           int batch_depth, bool persistent, int n_sms, cudaStream_t s)
+{
+    const int smem = blend_smem_bytes(batch_depth);
+    if (persistent) {
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blend_persistent_kernel<PX, PY>, threads, smem);
+        int grid = n_sms * (nb > 0 ? nb : 1);
+        if (grid > n_bins) grid = n_bins;
+        blend_persistent_kernel<PX, PY><<<grid, threads, smem, s>>>(cams, w, o);
+    } else {
+        blend_kernel<PX, PY><<<n_bins, threads, smem, s>>>(cams, w, o);
+    }
+}
+
 void launch_blend(const gs_camera *cams, const Ws &w, float *rgb, float *depth, float *T, int32_t *ncontrib,
-                  int n_bins, int threads, int batch_depth, bool persistent, int persistent_grid, cudaStream_t s)
+                  int n_bins, int px, int py, int threads, int batch_depth, bool persistent, int n_sms,
+                  cudaStream_t s)
 {
     OutPtrs o{rgb, depth, T, ncontrib};
-    const int smem = blend_smem_bytes(batch_depth);
-    if (persistent)
-        blend_persistent_kernel<<<persistent_grid, threads, smem, s>>>(cams, w, o);
-    else
-        blend_kernel<<<n_bins, threads, smem, s>>>(cams, w, o);
+    if (px == 2 && py == 2) launch_blend_t<2, 2>(cams, w, o, n_bins, threads, batch_depth, persistent, n_sms, s);
+    else if (px == 2) launch_blend_t<2, 1>(cams, w, o, n_bins, threads, batch_depth, persistent, n_sms, s);
+    else if (py == 2) launch_blend_t<1, 2>(cams, w, o, n_bins, threads, batch_depth, persistent, n_sms, s);
+    else launch_blend_t<1, 1>(cams, w, o, n_bins, threads, batch_depth, persistent, n_sms, s);
 }
 
 cudaError_t configure_forward_kernels()
@@ -853,11 +916,6 @@ cudaError_t configure_forward_kernels()
     return e;
 }
 
-int blend_blocks_per_sm(int threads, int batch_depth)
-{
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blend_persistent_kernel, threads, blend_smem_bytes(batch_depth));
-    return nb > 0 ? nb : 1;
-}
+
 
 } // namespace gs

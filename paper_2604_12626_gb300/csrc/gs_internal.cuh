@@ -47,6 +47,7 @@ struct Header {
 struct Table {
     int32_t n_envs, n_views;
     int32_t W, H, tile_w, tile_h, tiles_x, tiles_y, tiles_per_view, n_bins;
+    int32_t pix_x, pix_y; // pixels per blend thread
     int32_t batch_depth, flags;
     int32_t chunk, n_chunks; // Gaussians per preprocess / scatter CTA, and how many CTAs
     int64_t n_records, pair_capacity, n_gauss;

@@ -18,18 +18,17 @@ void launch_scatter(const gs_camera *cams, const Ws &w, int n_chunks, cudaStream
 void launch_sort_small(const Ws &w, int n_bins, cudaStream_t s);
 void launch_sort_big(const Ws &w, int n_sms, cudaStream_t s);
 void launch_blend(const gs_camera *cams, const Ws &w, float *rgb, float *depth, float *T, int32_t *ncontrib,
-                  int n_bins, int threads, int batch_depth, bool persistent, int persistent_grid, cudaStream_t s);
-int blend_blocks_per_sm(int threads, int batch_depth);
+                  int n_bins, int px, int py, int threads, int batch_depth, bool persistent, int n_sms,
+                  cudaStream_t s);
 void launch_count_visible(const Ws &w, int64_t n_words, cudaStream_t s);
 
 struct GradOut {
     float *means, *log_scales, *quats, *ologits, *sh, *cov3d;
 };
 void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,
-                           int threads, int batch_depth, int persistent_grid, cudaStream_t s);
-int blend_backward_blocks_per_sm(int threads, int batch_depth);
+                           int px, int py, int threads, int batch_depth, int n_sms, cudaStream_t s);
 void launch_preprocess_backward(const gs_gaussians *g, const gs_camera *cams, const Ws &w, const GradOut &o,
-                                int64_t n, bool overwrite, cudaStream_t s);
+                                int n_chunks, bool overwrite, cudaStream_t s);
 
 void launch_deform(const gs_avatars *av, const float *G, float *out_means, float *out_cov, cudaStream_t s);
 void launch_deform_backward(const gs_avatars *av, const float *G, const float *d_means, const float *d_cov,

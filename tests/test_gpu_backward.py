@@ -99,6 +99,21 @@ def test_backward_batched_envs_and_persistent(gs, oracle):
         assert rel_l2(a[k], b[k]) < 1e-3, k
 
 
+@pytest.mark.parametrize("tile,depth,pix", [((8, 8), 64, (1, 1)), ((16, 16), 256, (2, 2)), ((16, 8), 128, (2, 1)),
+                                            ((8, 16), 64, (1, 2))])
+def test_backward_tile_and_pixels_per_thread(gs, oracle, tile, depth, pix):
+    g = synth.room_scene(80_000, seed=9)
+    W, H = 136, 104  # ragged against every tile
+    cam = synth.room_camera(9, W, H)
+    rng = np.random.default_rng(5)
+    d_rgb = rng.standard_normal((1, 3, H, W)).astype(np.float32)
+    d_depth = (0.1 * rng.standard_normal((1, H, W))).astype(np.float32)
+    a = gpu_forward_backward(gs, g, cam[None], W, H, d_rgb, d_depth, tile=tile, batch_depth=depth, pix=pix)
+    b = oracle_grads(oracle, g, cam[None], W, H, d_rgb, d_depth)
+    for k in GROUPS:
+        assert rel_l2(a[k], b[k]) < 1e-3, k
+
+
 @pytest.mark.parametrize("dt", ["f16", "bf16"])
 def test_backward_half_sh(gs, oracle, dt):
     g = synth.box_scene(2000, seed=4)

@@ -91,23 +91,26 @@ def test_room_1m_keys_bit_exact(gs, room1m):
     assert P > 100_000
 
 
-@pytest.mark.parametrize("tile,depth", [((8, 8), 64), ((16, 8), 128), ((32, 8), 256), ((32, 16), 32)])
-def test_tile_size_does_not_change_results(gs, tile, depth):
+@pytest.mark.parametrize("tile,depth,pix", [((8, 8), 64, (1, 1)), ((16, 8), 128, (1, 1)), ((32, 8), 256, (1, 1)),
+                                            ((32, 16), 32, (1, 1)), ((16, 16), 256, (2, 2)), ((8, 8), 128, (2, 1)),
+                                            ((16, 8), 64, (1, 2)), ((16, 16), 128, (2, 1))])
+def test_tile_size_does_not_change_results(gs, tile, depth, pix):
     g = synth.room_scene(200_000, seed=4)
     W, H = 200, 150  # not a multiple of any tile
     cam = synth.room_camera(4, W, H)
     _, a, _, _ = render_gpu(gs, g, cam[None], W, H)
-    _, b, _, _ = render_gpu(gs, g, cam[None], W, H, tile=tile, batch_depth=depth)
+    _, b, _, _ = render_gpu(gs, g, cam[None], W, H, tile=tile, batch_depth=depth, pix=pix)
     for x, y in zip(a, b):
         assert torch.equal(x, y)
 
 
-def test_persistent_grid_equals_one_cta_per_tile(gs):
+@pytest.mark.parametrize("pix", [(1, 1), (2, 2)])
+def test_persistent_grid_equals_one_cta_per_tile(gs, pix):
     g = synth.room_scene(300_000, seed=5)
     W = H = 256
     cam = synth.room_camera(5, W, H)
     _, a, _, _ = render_gpu(gs, g, cam[None], W, H)
-    _, b, _, _ = render_gpu(gs, g, cam[None], W, H, persistent=True)
+    _, b, _, _ = render_gpu(gs, g, cam[None], W, H, persistent=True, pix=pix)
     for x, y in zip(a, b):
         assert torch.equal(x, y)
 

@@ -118,7 +118,9 @@ struct Plan {
     int64_t N, R, cap;
     float near_plane;
     // byte offsets
-    size_t o_hdr, o_tb, o_rec, o_vis, o_cnt, o_start, o_cur, o_big, o_heavy, o_keys, o_scr, o_pT, o_pL, o_drec, total;
+    size_t o_hdr, o_tb, o_rec, o_vis, o_cnt, o_fcnt, o_start, o_cur, o_big, o_heavy, o_rel, o_keys, o_scr, o_pT, o_pL,
+        o_drec, total;
+    int chunk, n_chunks;
 };
 
 gs_status make_plan(const gs_render_config *cfg, const gs_batch *b, Plan &p)
@@ -168,10 +170,17 @@ gs_status make_plan(const gs_render_config *cfg, const gs_batch *b, Plan &p)
     p.o_rec = o; o = align256(o + (size_t)R * 48);
     p.o_vis = o; o = align256(o + (size_t)((R + 31) / 32 + 1) * 4);
     p.o_cnt = o; o = align256(o + (size_t)nb * 4);
+    p.o_fcnt = o; o = align256(o + (size_t)nb * 4);
     p.o_start = o; o = align256(o + (size_t)(nb + 1) * 4);
     p.o_cur = o; o = align256(o + (size_t)nb * 4);
     p.o_big = o; o = align256(o + (size_t)nb * 4);
     p.o_heavy = o; o = align256(o + (size_t)4096 * 4);
+    p.chunk = chunk_of(p.N);
+    int64_t nch = 0;
+    for (int e = 0; e < b->n_envs; ++e) nch += (b->env_offsets[e + 1] - b->env_offsets[e] + p.chunk - 1) / p.chunk;
+    if (nch > (int64_t)1 << 30) return GS_ERR_UNSUPPORTED;
+    p.n_chunks = (int)nch;
+    p.o_rel = o; o = align256(o + (size_t)p.n_chunks * kHistCap * 4);
     p.o_keys = o; o = align256(o + (size_t)p.cap * 8);
     p.o_scr = o; o = align256(o + (size_t)p.cap * 8);
     p.o_pT = o; o = align256(o + (size_t)npix * 4);
@@ -194,6 +203,8 @@ Ws ws_ptrs(void *base, const Plan &p)
     w.bin_cursor = reinterpret_cast<uint32_t *>(b + p.o_cur);
     w.big_list = reinterpret_cast<uint32_t *>(b + p.o_big);
     w.heavy = reinterpret_cast<uint32_t *>(b + p.o_heavy);
+    w.bin_fcount = reinterpret_cast<uint32_t *>(b + p.o_fcnt);
+    w.rel = reinterpret_cast<uint32_t *>(b + p.o_rel);
     w.keys = reinterpret_cast<unsigned long long *>(b + p.o_keys);
     w.scratch = reinterpret_cast<unsigned long long *>(b + p.o_scr);
     w.pix_T = reinterpret_cast<float *>(b + p.o_pT);
@@ -214,8 +225,13 @@ void fill_table(const Plan &p, const gs_batch *b, const gs_render_config *cfg, i
     t.n_records = p.R;
     t.pair_capacity = p.cap;
     t.n_gauss = p.N;
-    t.chunk = chunk_size(p.N, n_sms);
-    t.n_chunks = (int)((p.N + t.chunk - 1) / t.chunk);
+    (void)n_sms;
+    t.chunk = p.chunk;
+    t.n_chunks = p.n_chunks;
+    t.chunk_off[0] = 0;
+    for (int e = 0; e < b->n_envs; ++e)
+        t.chunk_off[e + 1] =
+            t.chunk_off[e] + (int32_t)((b->env_offsets[e + 1] - b->env_offsets[e] + p.chunk - 1) / p.chunk);
     for (int k = 0; k < 3; ++k) t.bg[k] = cfg->bg[k];
     t.near_plane = p.near_plane;
     for (int e = 0; e <= b->n_envs; ++e) t.env_off[e] = b->env_offsets[e];
@@ -280,6 +296,7 @@ gs_status enqueue_forward(const gs_gaussians *g, const gs_batch *b, const gs_cam
         launch_setup(t, w, s);
         cudaError_t e = cudaMemsetAsync(w.vis, 0, (size_t)((p.R + 31) / 32 + 1) * 4, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.bin_count, 0, (size_t)p.n_bins * 4, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.bin_fcount, 0, (size_t)p.n_bins * 4, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.bin_cursor, 0, (size_t)p.n_bins * 4, s);
         if (e != cudaSuccess) return cuda_fail(e);
     }
@@ -376,9 +393,7 @@ gs_status gs_render_backward(const gs_gaussians *g, const gs_batch *batch, const
     {
         Stage st8(8, s);
         GradOut o{d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_cov3d};
-        const int chunk = chunk_size(p.N, sms);
-        launch_preprocess_backward(g, cams, w, o, (int)((p.N + chunk - 1) / chunk),
-                                   (cfg->flags & GS_FLAG_GRAD_OVERWRITE) != 0, s);
+        launch_preprocess_backward(g, cams, w, o, p.n_chunks, (cfg->flags & GS_FLAG_GRAD_OVERWRITE) != 0, s);
     }
     return check_launch();
 }

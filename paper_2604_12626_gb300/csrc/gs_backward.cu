@@ -647,19 +647,47 @@ __global__ void __launch_bounds__(256, 2) preprocess_backward_kernel(const gs_ca
     const Table *tb = w.tb;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     uint32_t *q = qs[warp];
-    const int64_t g0 = (int64_t)blockIdx.x * tb->chunk, g1 = min(g0 + tb->chunk, tb->n_gauss);
+    int lo = 0, hi = tb->n_envs - 1; // env of the chunk (chunks never straddle envs)
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tb->chunk_off[mid] <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t g0 = tb->env_off[lo] + (int64_t)(blockIdx.x - tb->chunk_off[lo]) * tb->chunk;
+    const int64_t g1 = min(g0 + tb->chunk, tb->env_off[lo + 1]);
     int head = 0, tail = 0;
+    const int64_t env_base = tb->env_off[lo];
+    const int vb = tb->env_view_begin[lo], ve = tb->env_view_begin[lo + 1];
+    const bool use_cov = gin.cov3d != nullptr && g0 >= tb->env_cov_begin[lo];
+    const bool split_cov = gin.cov3d != nullptr && g0 < tb->env_cov_begin[lo] && g1 > tb->env_cov_begin[lo];
     for (int64_t base = g0 + warp * 32; base < g1; base += 32 * nwarps) {
         const int64_t g = base + lane;
         bool seen = false;
         if (g < g1) {
-            const int e = find_env_b(tb, g);
-            const int64_t local = g - tb->env_off[e];
-            for (int kv = tb->env_view_begin[e]; kv < tb->env_view_begin[e + 1] && !seen; ++kv) {
+            const int64_t local = g - env_base;
+            for (int kv = vb; kv < ve && !seen; ++kv) {
                 const uint32_t rec = (uint32_t)(tb->view_rec_off[tb->env_views[kv]] + local);
                 seen = (__ldg(w.vis + (rec >> 5)) >> (rec & 31)) & 1u;
             }
-            if (!seen && OVERWRITE) zero_rows(o, g, gin.cov3d != nullptr && g >= tb->env_cov_begin[e]);
+        }
+        if (OVERWRITE) {
+            // zero this warp's 32 consecutive rows with coalesced stores; the
+            // rows of seen Gaussians are overwritten later by this same warp
+            const int nrow = (int)min((int64_t)32, g1 - base);
+            float4 *sh4 = reinterpret_cast<float4 *>(o.sh + 48 * base);
+            for (int i = lane; i < 12 * nrow; i += 32) sh4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = lane; i < 3 * nrow; i += 32) o.means[3 * base + i] = 0.f;
+            if (lane < nrow) o.ologits[base + lane] = 0.f;
+            if (split_cov) {
+                if (g < g1) zero_rows(o, g, g >= tb->env_cov_begin[lo]);
+            } else if (use_cov) {
+                if (o.cov3d)
+                    for (int i = lane; i < 6 * nrow; i += 32) o.cov3d[6 * base + i] = 0.f;
+            } else {
+                for (int i = lane; i < 3 * nrow; i += 32) o.log_scales[3 * base + i] = 0.f;
+                if (lane < nrow) reinterpret_cast<float4 *>(o.quats)[base + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            __syncwarp();
         }
         const unsigned bal = __ballot_sync(0xffffffffu, seen);
         if (seen) q[(tail + __popc(bal & ((1u << lane) - 1u))) & (kBwdWarpQ - 1)] = (uint32_t)(g - g0);

@@ -95,8 +95,7 @@ struct GaussIn {
 // Per-(view, tile) counts and cursors of a chunk that lies inside one env are
 // aggregated in shared memory, so that global atomics are one per (CTA, bin)
 // rather than one per pair.
-constexpr int kChunkMax = 16384;
-constexpr int kHistCap = 8192;
+
 constexpr int kPreThreads = 256;
 
 struct Chunk {
@@ -105,17 +104,21 @@ struct Chunk {
     bool hist;
 };
 
-__device__ __forceinline__ void chunk_setup(const Table *tb, int64_t cta, Chunk &c)
+__device__ __forceinline__ void chunk_setup(const Table *tb, int cta, Chunk &c)
 {
-    c.g0 = cta * tb->chunk;
-    c.g1 = min(c.g0 + tb->chunk, tb->n_gauss);
-    c.e0 = find_env(tb, c.g0);
-    c.e1 = find_env(tb, c.g1 - 1);
-    c.vb = tb->env_view_begin[c.e0];
-    c.nv = tb->env_view_begin[c.e0 + 1] - c.vb;
-    c.kmax = 0;
-    for (int e = c.e0; e <= c.e1; ++e) c.kmax = max(c.kmax, tb->env_view_begin[e + 1] - tb->env_view_begin[e]);
-    c.hist = c.e0 == c.e1 && c.nv * tb->tiles_per_view <= kHistCap;
+    int lo = 0, hi = tb->n_envs - 1; // env of the chunk: last e with chunk_off[e] <= cta
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tb->chunk_off[mid] <= cta) lo = mid;
+        else hi = mid - 1;
+    }
+    c.e0 = c.e1 = lo;
+    c.g0 = tb->env_off[lo] + (int64_t)(cta - tb->chunk_off[lo]) * tb->chunk;
+    c.g1 = min(c.g0 + tb->chunk, tb->env_off[lo + 1]);
+    c.vb = tb->env_view_begin[lo];
+    c.nv = tb->env_view_begin[lo + 1] - c.vb;
+    c.kmax = c.nv;
+    c.hist = c.nv * tb->tiles_per_view <= kHistCap;
 }
 
 // One visible (view, Gaussian) waiting for its colour, record and bin counts.
@@ -156,12 +159,12 @@ __device__ __forceinline__ void finish_entry(const QEntry &en, bool active, uint
         const float dn = 1.0f / sqrtf(en.d0 * en.d0 + en.d1 * en.d1 + en.d2 * en.d2);
         const float3 col = sh_colour<SHT>(gin.sh, en.g, en.d0 * dn, en.d1 * dn, en.d2 * dn);
         const float op = 1.0f / (1.0f + expf(-__ldg(gin.ologits + en.g)));
+        const int bx0 = en.x0 / tw, bx1 = en.x1 / tw, by0 = en.y0 / th, by1 = en.y1 / th;
         float4 *dst = w.rec + 3 * (size_t)en.rec;
         dst[0] = make_float4(en.uc, en.vc, en.zk, en.r);
         dst[1] = make_float4(en.A, en.B, en.C, op);
-        dst[2] = make_float4(col.x, col.y, col.z, 0.0f);
-        const int bx0 = en.x0 / tw, bx1 = en.x1 / tw, by0 = en.y0 / th, by1 = en.y1 / th;
-        uint32_t *hk = c.hist ? hist + en.k * tpv : w.bin_count + (size_t)en.v * tpv;
+        dst[2] = make_float4(col.x, col.y, col.z, __uint_as_float(pack_rect(bx0, by0, bx1 - bx0 + 1, by1 - by0 + 1)));
+        uint32_t *hk = c.hist ? hist + en.k * tpv : w.bin_fcount + (size_t)en.v * tpv;
         for (int by = by0; by <= by1; ++by)
             for (int bx = bx0; bx <= bx1; ++bx) atomicAdd(hk + by * tx_n + bx, 1u);
     }
@@ -178,12 +181,15 @@ __device__ __forceinline__ void finish_entry(const QEntry &en, bool active, uint
 // phase 2 on full warps of 32 queued entries.  The next round's means are
 // loaded before the current round is processed.
 constexpr int kWarpQ = 64;
+constexpr int kMaxViewsPerChunk = 16; // cameras of a chunk's env staged in shared memory
 
 template <int SHT>
 __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(const gs_camera *__restrict__ cams, GaussIn gin,
                                                                     Ws w)
 {
     extern __shared__ __align__(16) unsigned char smem_pre[];
+    __shared__ gs_camera s_cam[kMaxViewsPerChunk];
+    __shared__ int64_t s_roff[kMaxViewsPerChunk];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     QEntry *q = reinterpret_cast<QEntry *>(smem_pre) + warp * kWarpQ;
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem_pre + (kPreThreads / 32) * kWarpQ * sizeof(QEntry));
@@ -193,10 +199,20 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(const gs_cam
     const int tpv = tb->tiles_per_view;
     if (c.hist)
         for (int i = threadIdx.x; i < c.nv * tpv; i += blockDim.x) hist[i] = 0u;
+    const bool cam_smem = c.nv <= kMaxViewsPerChunk;
+    if (cam_smem)
+        for (int k = threadIdx.x; k < c.nv; k += blockDim.x) {
+            const int v = tb->env_views[c.vb + k];
+            s_cam[k] = cams[v];
+            s_roff[k] = tb->view_rec_off[v];
+        }
     __syncthreads();
     const int W = tb->W, H = tb->H;
     const float near_plane = tb->near_plane;
     const int nwarps = blockDim.x >> 5;
+    const int64_t env_base = tb->env_off[c.e0];
+    const bool env_cov = gin.cov3d != nullptr;
+    const int64_t cov_begin = tb->env_cov_begin[c.e0];
     int head = 0, tail = 0; // ring queue of this warp
     int64_t g = c.g0 + warp * 32 + lane;
     float mx = 0.f, my = 0.f, mz = 0.f;
@@ -215,23 +231,20 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(const gs_cam
             ny = __ldg(gin.means + 3 * gn + 1);
             nz = __ldg(gin.means + 3 * gn + 2);
         }
-        int e = c.e0;
-        if (valid && c.e0 != c.e1) e = find_env(tb, g);
-        const int vb = tb->env_view_begin[e];
-        const int nv = valid ? tb->env_view_begin[e + 1] - vb : 0;
-        const int64_t local = g - tb->env_off[e];
+        const int nv = valid ? c.nv : 0;
+        const int64_t local = g - env_base;
         bool have_sigma = false;
         float S[6];
         for (int k = 0; k < c.kmax; ++k) {
             bool vis = false;
             QEntry en;
             if (k < nv) {
-                const int v = tb->env_views[vb + k];
-                const gs_camera cam = cams[v];
+                const int v = cam_smem ? 0 : tb->env_views[c.vb + k];
+                const gs_camera &cam = cam_smem ? s_cam[k] : cams[v];
                 const float zk = depth_key(mx, my, mz, cam);
                 if (zk > near_plane) {
                     if (!have_sigma) {
-                        if (gin.cov3d && g >= tb->env_cov_begin[e]) {
+                        if (env_cov && g >= cov_begin) {
 #pragma unroll
                             for (int i = 0; i < 6; ++i) S[i] = __ldg(gin.cov3d + 6 * g + i);
                         } else {
@@ -250,13 +263,13 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(const gs_cam
                         if (pixel_range(pj.uc, r, cam.cx, W, x0, x1) && pixel_range(pj.vc, r, cam.cy, H, y0, y1)) {
                             vis = true;
                             const float idet = 1.0f / pj.det;
-                            en.rec = (uint32_t)(tb->view_rec_off[v] + local);
+                            en.rec = (uint32_t)((cam_smem ? s_roff[k] : tb->view_rec_off[v]) + local);
                             en.g = (uint32_t)g;
                             en.uc = pj.uc; en.vc = pj.vc; en.zk = zk; en.r = r;
                             en.A = pj.c * idet; en.B = -pj.b * idet; en.C = pj.a * idet;
                             en.d0 = pj.d0; en.d1 = pj.d1; en.d2 = pj.d2;
                             en.x0 = (uint16_t)x0; en.x1 = (uint16_t)x1; en.y0 = (uint16_t)y0; en.y1 = (uint16_t)y1;
-                            en.v = (uint16_t)v; en.k = (uint16_t)k;
+                            en.v = (uint16_t)(cam_smem ? tb->env_views[c.vb + k] : v); en.k = (uint16_t)k;
                         }
                     }
                 }
@@ -285,11 +298,13 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(const gs_cam
     }
     __syncthreads();
     if (c.hist) {
+        // the returned old count is this chunk's offset inside the bin
+        uint32_t *rel = w.rel + (size_t)blockIdx.x * kHistCap;
         for (int i = threadIdx.x; i < c.nv * tpv; i += blockDim.x) {
             const uint32_t cnt = hist[i];
             if (cnt) {
                 const int v = tb->env_views[c.vb + i / tpv];
-                atomicAdd(w.bin_count + (size_t)v * tpv + (i % tpv), cnt);
+                rel[i] = atomicAdd(w.bin_count + (size_t)v * tpv + (i % tpv), cnt);
             }
         }
     }
@@ -310,7 +325,7 @@ __global__ void __launch_bounds__(1024) scan_bins_kernel(Ws w)
     unsigned long long s = 0;
     uint32_t mx = 0;
     for (int i = b0; i < b1; ++i) {
-        const uint32_t c = w.bin_count[i];
+        const uint32_t c = w.bin_count[i] + w.bin_fcount[i];
         s += c;
         mx = max(mx, c);
     }
@@ -332,7 +347,7 @@ __global__ void __launch_bounds__(1024) scan_bins_kernel(Ws w)
     unsigned long long run = sh[threadIdx.x] - s; // exclusive
     for (int i = b0; i < b1; ++i) {
         w.bin_start[i] = (uint32_t)min(run, cap);
-        run += w.bin_count[i];
+        run += w.bin_count[i] + w.bin_fcount[i];
     }
     if (threadIdx.x == T - 1) {
         const unsigned long long total = sh[T - 1];
@@ -355,7 +370,7 @@ __global__ void __launch_bounds__(1024) scan_bins_kernel(Ws w)
     if (threadIdx.x == 0) hn = 0;
     __syncthreads();
     for (int i = b0; i < b1; ++i) {
-        const uint32_t c = w.bin_count[i];
+        const uint32_t c = w.bin_count[i] + w.bin_fcount[i];
         if (c >= (uint32_t)kHeavyMin) atomicAdd(&lg[32 - __clz(c)], 1u);
     }
     __syncthreads();
@@ -371,7 +386,7 @@ __global__ void __launch_bounds__(1024) scan_bins_kernel(Ws w)
     __syncthreads();
     const uint32_t th = hmin;
     for (int i = b0; i < b1; ++i) {
-        const uint32_t c = w.bin_count[i];
+        const uint32_t c = w.bin_count[i] + w.bin_fcount[i];
         if (c >= th) {
             const uint32_t at = atomicAdd(&hn, 1u);
             if (at < (uint32_t)kHeavyCap) hl[at] = ((unsigned long long)(~c) << 32) | (uint32_t)i;
@@ -396,47 +411,33 @@ __global__ void __launch_bounds__(1024) scan_bins_kernel(Ws w)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) scatter_kernel(const gs_camera *__restrict__ cams, Ws w)
 {
-    extern __shared__ uint32_t hist_sc[];
+    extern __shared__ uint32_t smem_sc[];
+    uint32_t *base = smem_sc;          // [kHistCap] next free slot per (view slot, tile)
+    uint32_t *list = smem_sc + kHistCap; // visible records of one view slot, compacted
+    __shared__ int list_n;
     const Table *tb = w.tb;
     Chunk c;
     chunk_setup(tb, blockIdx.x, c);
     const int W = tb->W, H = tb->H, tw = tb->tile_w, th = tb->tile_h, tx_n = tb->tiles_x, tpv = tb->tiles_per_view;
     const uint64_t cap = (uint64_t)tb->pair_capacity;
-    if (!c.hist) {
-        // chunk across envs or too many bins: one global cursor atomic per pair
-        for (int64_t g = c.g0 + threadIdx.x; g < c.g1; g += blockDim.x) {
-            const int e = find_env(tb, g);
-            const int64_t local = g - tb->env_off[e];
-            for (int k = tb->env_view_begin[e]; k < tb->env_view_begin[e + 1]; ++k) {
-                const int v = tb->env_views[k];
-                const uint32_t rec = (uint32_t)(tb->view_rec_off[v] + local);
-                if (!((__ldg(w.vis + (rec >> 5)) >> (rec & 31)) & 1u)) continue;
-                const float4 r0 = w.rec[3 * (size_t)rec];
-                const gs_camera &cam = cams[v];
-                int x0, x1, y0, y1;
-                if (!(pixel_range(r0.x, r0.w, cam.cx, W, x0, x1) && pixel_range(r0.y, r0.w, cam.cy, H, y0, y1)))
-                    continue;
-                const unsigned long long key = ((unsigned long long)__float_as_uint(r0.z) << 32) | rec;
-                const size_t bbase = (size_t)v * tpv;
-                for (int by = y0 / th; by <= y1 / th; ++by)
-                    for (int bx = x0 / tw; bx <= x1 / tw; ++bx) {
-                        const size_t bin = bbase + by * tx_n + bx;
-                        const uint64_t slot = (uint64_t)w.bin_start[bin] + atomicAdd(w.bin_cursor + bin, 1u);
-                        if (slot < (uint64_t)w.bin_start[bin + 1] && slot < cap) w.keys[slot] = key;
-                    }
-            }
+    // first slot of each of this chunk's bins: bin start + the chunk's offset
+    // (chunks with more bins than shared memory holds place their pairs after
+    // the aggregated ones of each bin, one global cursor atomic per pair)
+    const uint32_t *rel = w.rel + (size_t)blockIdx.x * kHistCap;
+    if (c.hist)
+        for (int i = threadIdx.x; i < c.nv * tpv; i += blockDim.x) {
+            const size_t bin = (size_t)tb->env_views[c.vb + i / tpv] * tpv + (i % tpv);
+            base[i] = w.bin_start[bin] + rel[i]; // unused where the chunk has no pair
         }
-        return;
-    }
-    uint32_t *list = hist_sc + kHistCap; // visible records of one view slot, compacted
-    __shared__ int list_n;
-    for (int i = threadIdx.x; i < c.nv * tpv; i += blockDim.x) hist_sc[i] = 0u;
+    const bool overflow = (uint64_t)w.hdr->n_pairs > cap;
     const int64_t loc0 = c.g0 - tb->env_off[c.e0], loc1 = c.g1 - tb->env_off[c.e0];
-    // builds the list of visible records of view slot k (ends with a barrier)
-    auto build_list = [&](int k) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int k = 0; k < c.nv; ++k) {
+        // visible records of view slot k, compacted
         if (threadIdx.x == 0) list_n = 0;
         __syncthreads();
-        const int64_t roff = tb->view_rec_off[tb->env_views[c.vb + k]];
+        const int v = tb->env_views[c.vb + k];
+        const int64_t roff = tb->view_rec_off[v];
         const int64_t r0 = roff + loc0, r1 = roff + loc1;
         const int64_t wlo = r0 >> 5, whi = (r1 - 1) >> 5;
         for (int64_t wd = wlo + threadIdx.x; wd <= whi; wd += blockDim.x) {
@@ -447,59 +448,79 @@ __global__ void __launch_bounds__(256) scatter_kernel(const gs_camera *__restric
             if (!bits) continue;
             int at = atomicAdd(&list_n, __popc(bits));
             while (bits) {
-                const int b = __ffs(bits) - 1;
+                const int bb = __ffs(bits) - 1;
                 bits &= bits - 1u;
-                list[at++] = (uint32_t)(b0 + b);
+                list[at++] = (uint32_t)(b0 + bb);
             }
         }
         __syncthreads();
-    };
-    // pass 1: count the chunk's pairs per (view slot, tile)
-    for (int k = 0; k < c.nv; ++k) {
-        build_list(k);
-        const gs_camera &cam = cams[tb->env_views[c.vb + k]];
-        uint32_t *hk = hist_sc + k * tpv;
-        const int n = list_n;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const uint32_t rec = list[i];
-            const float4 r0 = w.rec[3 * (size_t)rec];
-            int x0, x1, y0, y1;
-            if (!(pixel_range(r0.x, r0.w, cam.cx, W, x0, x1) && pixel_range(r0.y, r0.w, cam.cy, H, y0, y1))) continue;
-            for (int by = y0 / th; by <= y1 / th; ++by)
-                for (int bx = x0 / tw; bx <= x1 / tw; ++bx) atomicAdd(hk + by * tx_n + bx, 1u);
-        }
-        __syncthreads();
-    }
-    // pass 2: reserve a contiguous slot range per bin (one global atomic each)
-    for (int i = threadIdx.x; i < c.nv * tpv; i += blockDim.x) {
-        const uint32_t cnt = hist_sc[i];
-        if (cnt) {
-            const size_t bin = (size_t)tb->env_views[c.vb + i / tpv] * tpv + (i % tpv);
-            hist_sc[i] = w.bin_start[bin] + atomicAdd(w.bin_cursor + bin, cnt);
-        }
-    }
-    __syncthreads();
-    // pass 3: write the keys
-    for (int k = 0; k < c.nv; ++k) {
-        if (c.nv > 1) build_list(k);
-        const int v = tb->env_views[c.vb + k];
         const gs_camera &cam = cams[v];
-        uint32_t *hk = hist_sc + k * tpv;
+        uint32_t *bk = base + (c.hist ? k * tpv : 0);
         const size_t bbase = (size_t)v * tpv;
         const int n = list_n;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const uint32_t rec = list[i];
-            const float4 r0 = w.rec[3 * (size_t)rec];
-            int x0, x1, y0, y1;
-            if (!(pixel_range(r0.x, r0.w, cam.cx, W, x0, x1) && pixel_range(r0.y, r0.w, cam.cy, H, y0, y1))) continue;
-            const unsigned long long key = ((unsigned long long)__float_as_uint(r0.z) << 32) | rec;
-            for (int by = y0 / th; by <= y1 / th; ++by)
-                for (int bx = x0 / tw; bx <= x1 / tw; ++bx) {
-                    const int t = by * tx_n + bx;
-                    const uint64_t slot = atomicAdd(hk + t, 1u);
-                    const uint64_t end = min((uint64_t)w.bin_start[bbase + t + 1], cap);
-                    if (slot < end) w.keys[slot] = key;
+        // each warp expands 32 records into their (record, tile) pairs, 32
+        // pairs at a time, so that the per-record tile loops do not diverge
+        for (int i0 = warp * 32; i0 < n; i0 += nwarps * 32) {
+            const int i = i0 + lane;
+            uint32_t rec = 0, zb = 0, tx0 = 0, ty0 = 0, ntx = 0, cnt = 0;
+            if (i < n) {
+                rec = list[i];
+                const float4 ra = w.rec[3 * (size_t)rec];
+                zb = __float_as_uint(ra.z);
+                const uint32_t pr = __float_as_uint(w.rec[3 * (size_t)rec + 2].w);
+                if (pr != 0xffffffffu) {
+                    tx0 = pr & 2047u;
+                    ty0 = (pr >> 11) & 2047u;
+                    ntx = ((pr >> 22) & 31u) + 1;
+                    cnt = ntx * (((pr >> 27) & 31u) + 1);
+                } else {
+                    int x0, x1, y0, y1;
+                    if (pixel_range(ra.x, ra.w, cam.cx, W, x0, x1) && pixel_range(ra.y, ra.w, cam.cy, H, y0, y1)) {
+                        tx0 = x0 / tw;
+                        ty0 = y0 / th;
+                        ntx = x1 / tw - tx0 + 1;
+                        cnt = ntx * (y1 / th - ty0 + 1);
+                    }
                 }
+            }
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+                const uint32_t t = t0 + lane;
+                // owner: the first lane whose inclusive count exceeds t
+                int lo = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const uint32_t pv = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+                    if (pv <= t) lo += step;
+                }
+                const uint32_t o_incl = __shfl_sync(0xffffffffu, incl, lo);
+                const uint32_t o_cnt = __shfl_sync(0xffffffffu, cnt, lo);
+                const uint32_t o_rec = __shfl_sync(0xffffffffu, rec, lo);
+                const uint32_t o_zb = __shfl_sync(0xffffffffu, zb, lo);
+                const uint32_t o_tx0 = __shfl_sync(0xffffffffu, tx0, lo);
+                const uint32_t o_ty0 = __shfl_sync(0xffffffffu, ty0, lo);
+                const uint32_t o_ntx = __shfl_sync(0xffffffffu, ntx, lo);
+                if (t < total) {
+                    const uint32_t jj = t - (o_incl - o_cnt);
+                    const uint32_t ty = o_ty0 + jj / o_ntx, tx = o_tx0 + jj % o_ntx;
+                    const int tl = (int)(ty * tx_n + tx);
+                    uint32_t slot;
+                    if (c.hist) {
+                        slot = atomicAdd(bk + tl, 1u);
+                    } else {
+                        const size_t bin = bbase + tl;
+                        slot = w.bin_start[bin] + w.bin_count[bin] + atomicAdd(w.bin_cursor + bin, 1u);
+                    }
+                    if (!overflow || (slot < w.bin_start[bbase + tl + 1] && (uint64_t)slot < cap))
+                        w.keys[slot] = ((unsigned long long)o_zb << 32) | o_rec;
+                }
+            }
         }
         __syncthreads();
     }
@@ -831,14 +852,6 @@ __global__ void blend_persistent_kernel(const gs_camera *__restrict__ cams, Ws w
 void launch_setup(const Table &tb, const Ws &w, cudaStream_t s) { setup_kernel<<<1, 256, 0, s>>>(tb, w); }
 
 constexpr int kPreSmem = (kPreThreads / 32) * kWarpQ * (int)sizeof(QEntry) + kHistCap * 4;
-
-int chunk_size(int64_t n, int n_sms)
-{
-    // enough CTAs to fill the GPU a few times over, at most kChunkMax Gaussians each
-    int c = 1024;
-    while (c < kChunkMax && (int64_t)c * 2 * n_sms * 6 <= n) c *= 2;
-    return c;
-}
 
 void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s)
 {

@@ -59,6 +59,7 @@ struct Table {
     int32_t view_env[GS_MAX_VIEWS];
     int32_t env_view_begin[GS_MAX_ENVS + 1];
     int32_t env_views[GS_MAX_VIEWS];
+    int32_t chunk_off[GS_MAX_ENVS + 1]; // first chunk of each env (chunks never straddle envs)
 };
 
 struct Ws {
@@ -67,11 +68,33 @@ struct Ws {
     float4 *rec;  // 3 float4 per record
     uint32_t *vis;
     uint32_t *bin_count, *bin_start, *bin_cursor, *big_list, *heavy;
+    uint32_t *bin_fcount; // pairs of chunks counted without shared-memory aggregation
+    uint32_t *rel;        // [n_chunks][kHistCap] offset of a chunk's pairs inside each bin
     unsigned long long *keys, *scratch;
     float *pix_T;
     uint32_t *pix_last;
     float *d_rec; // 12 floats per record
 };
+
+constexpr int kChunkMax = 16384; // Gaussians per preprocess / scatter CTA, at most
+constexpr int kChunkMin = 1024;
+constexpr int kHistCap = 8192;   // (view, tile) counters a chunk keeps in shared memory
+
+// Chunk size from the Gaussian count alone: about 2048 chunks, 1024..16384.
+inline int chunk_of(int64_t n)
+{
+    int c = kChunkMin;
+    while (c < kChunkMax && (int64_t)c * 2048 < n) c *= 2;
+    return c;
+}
+
+// Tile rectangle of a visible record packed into 32 bits: tx0 (11 bits),
+// ty0 (11), ntx - 1 (5), nty - 1 (5); all-ones when it does not fit.
+__host__ __device__ __forceinline__ uint32_t pack_rect(int tx0, int ty0, int ntx, int nty)
+{
+    if (tx0 >= 2048 || ty0 >= 2048 || ntx > 32 || nty > 32) return 0xffffffffu;
+    return (uint32_t)tx0 | ((uint32_t)ty0 << 11) | ((uint32_t)(ntx - 1) << 22) | ((uint32_t)(nty - 1) << 27);
+}
 
 // ---------------------------------------------------------------------------
 // Decisions both the forward and the backward take; written with explicit

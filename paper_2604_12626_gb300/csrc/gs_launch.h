@@ -11,7 +11,6 @@ cudaError_t configure_forward_kernels();
 cudaError_t configure_backward_kernels();
 
 void launch_setup(const Table &tb, const Ws &w, cudaStream_t s);
-int chunk_size(int64_t n, int n_sms);
 void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s);
 void launch_scan(const Ws &w, cudaStream_t s);
 void launch_scatter(const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s);

@@ -119,7 +119,7 @@ struct Plan {
     float near_plane;
     // byte offsets
     size_t o_hdr, o_tb, o_rec, o_vis, o_cnt, o_fcnt, o_start, o_cur, o_big, o_heavy, o_rel, o_keys, o_scr, o_pT, o_pL,
-        o_drec, total;
+        o_drec, o_hseg, o_hof, o_pC, o_ckC, o_ckD, total;
     int chunk, n_chunks;
 };
 
@@ -186,6 +186,14 @@ gs_status make_plan(const gs_render_config *cfg, const gs_batch *b, Plan &p)
     p.o_pT = o; o = align256(o + (size_t)npix * 4);
     p.o_pL = o; o = align256(o + (size_t)npix * 4);
     p.o_drec = o; o = align256(o + (size_t)R * 48);
+    p.o_hseg = o; o = align256(o + (size_t)(kHeavyCap + 1) * 4);
+    p.o_hof = o; o = align256(o + (size_t)nb * 4);
+    p.o_pC = o; o = align256(o + (size_t)npix * 16);
+    // checkpoint slots: every heavy bin has at most count / kSeg boundaries
+    const size_t slots = (size_t)(p.cap / kSeg) + kHeavyCap + 1;
+    const size_t tpx = (size_t)p.tw * p.th;
+    p.o_ckC = o; o = align256(o + slots * tpx * 16);
+    p.o_ckD = o; o = align256(o + slots * tpx * 4);
     p.total = o;
     return GS_OK;
 }
@@ -210,6 +218,11 @@ Ws ws_ptrs(void *base, const Plan &p)
     w.pix_T = reinterpret_cast<float *>(b + p.o_pT);
     w.pix_last = reinterpret_cast<uint32_t *>(b + p.o_pL);
     w.d_rec = reinterpret_cast<float *>(b + p.o_drec);
+    w.heavy_seg = reinterpret_cast<uint32_t *>(b + p.o_hseg);
+    w.heavy_of = reinterpret_cast<int32_t *>(b + p.o_hof);
+    w.pix_C = reinterpret_cast<float4 *>(b + p.o_pC);
+    w.ck_C = reinterpret_cast<float4 *>(b + p.o_ckC);
+    w.ck_D = reinterpret_cast<float *>(b + p.o_ckD);
     return w;
 }
 

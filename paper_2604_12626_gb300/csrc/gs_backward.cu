@@ -98,10 +98,15 @@ constexpr int kGroup = 3; // Gaussians whose gradients share one warp reduction
 // double-buffered like the forward.  A thread owns PX x PY pixels and sums
 // their contributions before the warp reduction, so there is one reduction per
 // (warp, Gaussian) for PX x PY x 32 pixels.
+// Segment [seg_lo, seg_hi) of the bin's list (the whole list for light bins).
+// A segment that ends before the tile's last blended position starts from the
+// forward's checkpoint at seg_hi: T there, and behind it the final colour and
+// depth minus what was accumulated in front of seg_hi.
 template <int PX, int PY>
 __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera *cams, const float *d_rgb,
-                                                   const float *d_depth, int bin, float4 *sm, float *acc,
-                                                   uint32_t *sidx, uint32_t *smax_last)
+                                                   const float *d_depth, int bin, uint32_t seg_lo, uint32_t seg_hi,
+                                                   int64_t ck_slot, float4 *sm, float *acc, uint32_t *sidx,
+                                                   uint32_t *smax_last)
 {
     constexpr int NP = PX * PY;
     const Table *tb = w.tb;
@@ -152,11 +157,35 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
     const uint32_t wl = __reduce_max_sync(0xffffffffu, tlast);
     if ((threadIdx.x & 31) == 0) atomicMax(smax_last, wl);
     __syncthreads();
-    const uint32_t n_proc = min(*smax_last, n);
+    const uint32_t tile_last = min(*smax_last, n);
+    if (seg_lo >= tile_last) return; // nothing blended in this segment
+    const uint32_t n_proc = min(tile_last, seg_hi);
+    if (n_proc < tile_last) {
+        // start from the checkpoint before position seg_hi
+        const int tpx = tb->tile_w * tb->tile_h;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const int i = i0 + p % PX, j = j0 + p / PX;
+            if (i < W && j < H) {
+                const int lpx = ((threadIdx.x / tcols) * PY + p / PX) * tb->tile_w + (threadIdx.x % tcols) * PX + p % PX;
+                const float4 ck = w.ck_C[(size_t)ck_slot * tpx + lpx];
+                const float ckd = w.ck_D[(size_t)ck_slot * tpx + lpx];
+                const float4 fin = w.pix_C[(size_t)v * HW + (size_t)j * W + i];
+                T[p] = ck.x;
+                S0[p] = fin.x - ck.y;
+                S1[p] = fin.y - ck.z;
+                S2[p] = fin.z - ck.w;
+                SD[p] = fin.w - ckd;
+            }
+        }
+    }
     const int lane = threadIdx.x & 31;
-    const int nb = (int)((n_proc + B - 1) / B);
-    // batch b covers [lo_b, hi_b), hi_b = n_proc - b B
-    auto lo_of = [&](int b) { return (int32_t)n_proc - (b + 1) * B < 0 ? 0 : (int32_t)n_proc - (b + 1) * B; };
+    const int nb = (int)((n_proc - seg_lo + B - 1) / B);
+    // batch b covers [lo_b, hi_b), hi_b = n_proc - b B, lo_b >= seg_lo
+    auto lo_of = [&](int b) {
+        const int32_t x = (int32_t)n_proc - (b + 1) * B;
+        return x < (int32_t)seg_lo ? (int32_t)seg_lo : x;
+    };
     auto hi_of = [&](int b) { return (int32_t)n_proc - b * B; };
     unsigned long long kr[kMaxPerB];
     auto load_keys = [&](int b) {
@@ -303,14 +332,31 @@ __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, 
     const int B = w.tb->batch_depth;
     float *acc = reinterpret_cast<float *>(smem_b + 2 * 3 * B); // [B][kGradStride]
     uint32_t *sidx = reinterpret_cast<uint32_t *>(acc + B * kGradStride); // [2][B]
-    const uint32_t n_items = (uint32_t)w.tb->n_bins + w.hdr->n_heavy;
+    // items: the kSeg-long segments of the heavy bins (largest bins first),
+    // then every other bin whole
+    const uint32_t nhi = w.hdr->n_heavy_items, nh = w.hdr->n_heavy;
+    const uint32_t n_items = nhi + (uint32_t)w.tb->n_bins;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) item = atomicAdd(&w.hdr->queue_bwd, 1u);
         __syncthreads();
         if (item >= n_items) break;
-        const int bin = bin_of_item(w, item);
-        if (bin >= 0) blend_backward_tile<PX, PY>(w, cams, d_rgb, d_depth, bin, smem_b, acc, sidx, &smax_last);
+        if (item < nhi) {
+            uint32_t lo = 0, hi = nh - 1; // heavy bin: last h with heavy_seg[h] <= item
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (w.heavy_seg[mid] <= item) lo = mid;
+                else hi = mid - 1;
+            }
+            const uint32_t s = item - w.heavy_seg[lo];
+            blend_backward_tile<PX, PY>(w, cams, d_rgb, d_depth, (int)w.heavy[lo], s * kSeg, (s + 1) * kSeg,
+                                        (int64_t)w.heavy_seg[lo] + s, smem_b, acc, sidx, &smax_last);
+        } else {
+            const uint32_t b = item - nhi;
+            if (w.bin_count[b] + w.bin_fcount[b] >= w.hdr->heavy_min) continue;
+            blend_backward_tile<PX, PY>(w, cams, d_rgb, d_depth, (int)b, 0u, 0xffffffffu, 0, smem_b, acc, sidx,
+                                        &smax_last);
+        }
     }
 }
 

@@ -313,8 +313,6 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(const gs_cam
 // ---------------------------------------------------------------------------
 // scan of the bin counts (single CTA, any number of bins)
 // ---------------------------------------------------------------------------
-constexpr int kHeavyMin = 1024; // pairs from which a bin may be scheduled first
-constexpr int kHeavyCap = 4096;
 __device__ __forceinline__ void bitonic_smem(unsigned long long *s, int m);
 __global__ void __launch_bounds__(1024) scan_bins_kernel(Ws w)
 {
@@ -400,7 +398,23 @@ __global__ void __launch_bounds__(1024) scan_bins_kernel(Ws w)
     __syncthreads();
     bitonic_smem(hl, mh);
     for (int i = threadIdx.x; i < nh; i += T) w.heavy[i] = (uint32_t)hl[i];
+    // backward segments of the heavy bins: ceil(count / kSeg) each, scanned
+    for (int i = b0; i < b1; ++i) w.heavy_of[i] = -1;
+    __shared__ uint32_t segs[kHeavyCap];
+    for (int i = threadIdx.x; i < nh; i += T) {
+        const uint32_t cnt = ~(uint32_t)(hl[i] >> 32);
+        segs[i] = (cnt + kSeg - 1) / kSeg;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nh; i += T) w.heavy_of[(uint32_t)hl[i]] = i;
     if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int i = 0; i < nh; ++i) {
+            w.heavy_seg[i] = acc;
+            acc += segs[i];
+        }
+        w.heavy_seg[nh] = acc;
+        w.hdr->n_heavy_items = acc;
         w.hdr->n_heavy = (uint32_t)nh;
         w.hdr->heavy_min = nh > 0 ? th : 0xffffffffu;
     }
@@ -668,7 +682,7 @@ constexpr int kMaxPer = 4; // records per thread and batch (B <= 4 x threads)
 constexpr int kUnroll = 4; // Gaussians evaluated together in the blend loop
 
 template <int PX, int PY>
-__device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, const OutPtrs &o, int bin,
+__device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, const OutPtrs &o, int bin, int heavy,
                                           float4 *sm)
 {
     constexpr int NP = PX * PY;
@@ -737,7 +751,19 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
         cp_async_commit();
         load_keys(1);
     }
+    const int tpx = tb->tile_w * tb->tile_h;
+    const uint32_t ck_base = heavy >= 0 ? w.heavy_seg[heavy] : 0u;
     for (int b = 0; b < nb; ++b) {
+        if (heavy >= 0 && b > 0 && ((uint32_t)b * B) % kSeg == 0) {
+            // checkpoint before list position b B, for the backward's segments
+            const size_t slot = (size_t)(ck_base + ((uint32_t)b * B) / kSeg - 1) * tpx;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const int lpx = ((threadIdx.x / tcols) * PY + p / PX) * tb->tile_w + (threadIdx.x % tcols) * PX + p % PX;
+                w.ck_C[slot + lpx] = make_float4(T[p], C0[p], C1[p], C2[p]);
+                w.ck_D[slot + lpx] = D[p];
+            }
+        }
         if (b + 1 < nb) issue(b + 1);
         cp_async_commit();
         if (b + 2 < nb) load_keys(b + 2);
@@ -819,6 +845,8 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
             o.ncontrib[(size_t)v * HW + px] = ncon[p];
             w.pix_T[(size_t)v * HW + px] = T[p];
             w.pix_last[(size_t)v * HW + px] = last[p];
+            w.pix_C[(size_t)v * HW + px] = make_float4(C0[p] + T[p] * tb->bg[0], C1[p] + T[p] * tb->bg[1],
+                                                       C2[p] + T[p] * tb->bg[2], D[p]);
         }
     }
 }
@@ -827,7 +855,7 @@ template <int PX, int PY>
 __global__ void blend_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
 {
     extern __shared__ float4 smem_f4[];
-    blend_tile<PX, PY>(w, cams, o, blockIdx.x, smem_f4);
+    blend_tile<PX, PY>(w, cams, o, blockIdx.x, w.heavy_of[blockIdx.x], smem_f4);
 }
 
 template <int PX, int PY>
@@ -842,7 +870,7 @@ __global__ void blend_persistent_kernel(const gs_camera *__restrict__ cams, Ws w
         __syncthreads();
         if (item >= n_items) break;
         const int bin = bin_of_item(w, item);
-        if (bin >= 0) blend_tile<PX, PY>(w, cams, o, bin, smem_f4);
+        if (bin >= 0) blend_tile<PX, PY>(w, cams, o, bin, item < w.hdr->n_heavy ? (int)item : -1, smem_f4);
     }
 }
 

@@ -41,7 +41,8 @@ struct Header {
     uint32_t big_queue; // large-bin sort work counter
     uint32_t n_heavy;   // bins in the heavy-first list
     uint32_t heavy_min; // pair count from which a bin is in that list
-    uint32_t pad[54];
+    uint32_t n_heavy_items; // backward work items of the heavy bins (one per kSeg-long segment)
+    uint32_t pad[53];
 };
 
 struct Table {
@@ -70,12 +71,20 @@ struct Ws {
     uint32_t *bin_count, *bin_start, *bin_cursor, *big_list, *heavy;
     uint32_t *bin_fcount; // pairs of chunks counted without shared-memory aggregation
     uint32_t *rel;        // [n_chunks][kHistCap] offset of a chunk's pairs inside each bin
+    uint32_t *heavy_seg;  // [kHeavyCap + 1] first backward segment of each heavy bin
+    int32_t *heavy_of;    // [n_bins] position in the heavy list, -1 if not heavy
+    float4 *pix_C;        // [V*H*W] final (r, g, b, depth), background included
+    float4 *ck_C;         // [slots][tile pixels] (T, r, g, b) before each segment boundary
+    float *ck_D;          // [slots][tile pixels] depth before each segment boundary
     unsigned long long *keys, *scratch;
     float *pix_T;
     uint32_t *pix_last;
     float *d_rec; // 12 floats per record
 };
 
+constexpr int kSeg = 2048;       // backward segment of a heavy bin (a multiple of every batch depth)
+constexpr int kHeavyMin = 1024;  // pairs from which a bin may be scheduled first
+constexpr int kHeavyCap = 4096;  // entries of the heavy-first list
 constexpr int kChunkMax = 16384; // Gaussians per preprocess / scatter CTA, at most
 constexpr int kChunkMin = 1024;
 constexpr int kHistCap = 8192;   // (view, tile) counters a chunk keeps in shared memory

@@ -114,6 +114,31 @@ def test_backward_tile_and_pixels_per_thread(gs, oracle, tile, depth, pix):
         assert rel_l2(a[k], b[k]) < 1e-3, k
 
 
+@pytest.mark.parametrize("persistent", [False, True])
+def test_backward_heavy_tiles_split_into_segments(gs, oracle, persistent):
+    # a dense room seen at 64x64: tiles hold several thousand pairs, so the
+    # backward runs them as 2048-long segments started from forward checkpoints
+    g = synth.room_scene(400_000, seed=12)
+    W = H = 64
+    cam = synth.room_camera(12, W, H)
+    rng = np.random.default_rng(6)
+    d_rgb = rng.standard_normal((1, 3, H, W)).astype(np.float32)
+    d_depth = (0.1 * rng.standard_normal((1, H, W))).astype(np.float32)
+    r = gs.Renderer(gs.Batch(np.array([0, 400_000])), W, H, persistent=persistent)
+    G = gs.Gaussians.from_numpy(g)
+    ct = gs.cameras_tensor(cam[None])
+    r.forward(G, ct)
+    st = r.stats()
+    assert st["max_bin"] > 3 * 2048, st
+    gr = r.backward(G, ct, torch.from_numpy(d_rgb).cuda(), torch.from_numpy(d_depth).cuda())
+    torch.cuda.synchronize()
+    b = oracle_grads(oracle, g, cam[None], W, H, d_rgb, d_depth)
+    for k in GROUPS:
+        e = rel_l2(gr[k].cpu().numpy(), b[k])
+        print(f"heavy-tile grad {k}: rel L2 {e:.2e}")
+        assert e < 1e-3, (k, e)
+
+
 @pytest.mark.parametrize("dt", ["f16", "bf16"])
 def test_backward_half_sh(gs, oracle, dt):
     g = synth.box_scene(2000, seed=4)

@@ -150,13 +150,13 @@ def max_over_ranks(x, ws):
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (test infrastructure; timed as it stands)
 # ---------------------------------------------------------------------------
-def oracle_step(env_ids, seed0, budget_s=None):
+def oracle_step(env_ids, seed0, budget_s=None, scale=1.0):
     """FP64 oracle forward + backward of whole envs; returns (envs done, seconds)."""
     import oracle
     from paper_2604_12626_gb300 import synth
 
     oracle.build()
-    sizes = synth.batch_sizes(N_ENVS, N_MIN, N_MAX, seed0)
+    sizes = synth.batch_sizes(max(env_ids) + 1, N_MIN, N_MAX, seed0, scale)
     done, t_total = 0, 0.0
     rng = np.random.default_rng(0)
     for e in env_ids:
@@ -237,6 +237,79 @@ def tune_fwd_bwd(api, rend, G, cams, candidates, N, dev, reps=2):
     rend.cfg.tile_w, rend.cfg.tile_h, rend.cfg.batch_depth, rend.cfg.pix_x, rend.cfg.pix_y = best
     return best, best_ms
 
+# Algorithmic work per unit (the figures and their derivation are in the design
+# notes): bytes for the memory-bound stages, FP32 lane operations for blending.
+OPS_PER_EVAL_FWD = 17   # offset, quadratic form, exp, alpha clamp / skip, T update, 3 colours + depth
+OPS_PER_EVAL_BWD = 40   # recomputed alpha, T_prev, dL/dalpha, conic / centre / colour / depth terms
+KERNEL_OF_STAGE = {"preprocess": "preprocess_kernel", "scan": "scan_bins_kernel", "scatter": "scatter_kernel",
+                   "sort_small": "sort_small_kernel", "sort_big": "sort_big_kernel",
+                   "blend": "blend_persistent_kernel", "blend_backward": "blend_backward_kernel",
+                   "preprocess_backward": "preprocess_backward_kernel"}
+CSRC = os.path.join(ROOT, "paper_2604_12626_gb300", "csrc")
+
+
+def source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(CSRC)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(CSRC, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def dram_traffic():
+    """Per-launch DRAM bytes of each kernel from the committed ncu summary, or
+    {} once the kernel sources have changed since it was taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            t = json.load(f)
+    except Exception:
+        return {}
+    if t.get("source_hash") != source_hash():
+        return {}
+    return t.get("kernels", {})
+
+
+def rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_pix, N, sm_count, sm_mhz):
+    """Achieved vs peak per kernel, from live CUDA-event stage times."""
+    hbm, peak_kind = peaks()
+    mhz = sm_mhz or 2070.0
+    alu_peak = sm_count * 128 * mhz * 1e6 / 1e12  # FP32 lanes x clock, T lane-ops/s
+    R, nvis, P = stats["n_records"], stats["n_visible"], stats["n_pairs"]
+    traffic = dram_traffic()
+    mem = {  # algorithmic bytes per launch (FP16 SH storage)
+        "preprocess": 16 * R + nvis * (12 + 16 + 4 + 96 + 44),
+        "scatter": nvis * 20 + 12 * P,
+        "sort": 16 * P,
+        "preprocess_backward": 12 * N + nvis * (12 + 16 + 4 + 96 + 40) + N * 59 * 4,
+    }
+    ops = {"blend": OPS_PER_EVAL_FWD * n_eval_fwd, "blend_backward": OPS_PER_EVAL_BWD * n_eval_bwd}
+    ms = dict(stage_ms)
+    if "sort_small" in ms:
+        ms["sort"] = ms.get("sort_small", 0.0) + ms.get("sort_big", 0.0)
+    out = {}
+    for k, b in mem.items():
+        if k in ms and ms[k] > 0:
+            a = b / (ms[k] * 1e-3) / 1e9
+            out[k] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+                      "algorithmic": b, "ms": ms[k], "peak_kind": peak_kind}
+    for k, f in ops.items():
+        if k in ms and ms[k] > 0:
+            a = f / (ms[k] * 1e-3) / 1e12
+            out[k] = {"bound": "alu", "achieved": a, "peak": alu_peak, "unit": "TFLOP/s", "frac": a / alu_peak,
+                      "algorithmic": f, "ms": ms[k],
+                      "peak_kind": f"derived: {sm_count} SMs x 128 FP32 lanes x {mhz:.0f} MHz"}
+    for k, v in out.items():
+        kern = [KERNEL_OF_STAGE[x] for x in (("sort_small", "sort_big") if k == "sort" else (k,))]
+        tb = [traffic.get(x, {}).get("dram_bytes_per_launch") for x in kern]
+        v["traffic"] = None if any(x is None for x in tb) else float(sum(tb))
+    dom = max(out, key=lambda k: out[k]["ms"])
+    roof = dict(out[dom], kernel=dom)
+    return roof, out
+
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -244,9 +317,10 @@ def run_ours(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    seed0 = rank * N_ENVS  # weak scaling: every rank renders its own 64 envs
+    n_envs = args.envs
+    seed0 = rank * n_envs  # weak scaling: every rank renders its own envs
     t0 = time.time()
-    g, offs, cams = synth.batched_rooms(N_ENVS, N_MIN, N_MAX, W, H, seed0=seed0, scale=args.scale)
+    g, offs, cams = synth.batched_rooms(n_envs, N_MIN, N_MAX, W, H, seed0=seed0, scale=args.scale)
     t_gen = time.time() - t0
     N = int(offs[-1])
     T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)  # noqa: E731
@@ -262,7 +336,7 @@ def run_ours(args, ws, rank, local):
     # --- autotune the batched renderer (tile, batch depth), cached per GPU + workload
     rend = api.Renderer(batch, W, H, device=dev, tile=(8, 8), batch_depth=64, persistent=True, grad_overwrite=True)
     cache_path = os.path.join(ROOT, "paper_2604_12626_gb300", "_build", "autotune.json")
-    key = f"{torch.cuda.get_device_name(dev)}|{N_ENVS}x{W}x{H}|N={N}|f16|fwd+bwd"
+    key = f"{torch.cuda.get_device_name(dev)}|{n_envs}x{W}x{H}|N={N}|f16|fwd+bwd"
     cache = {}
     try:
         with open(cache_path) as f:
@@ -292,8 +366,8 @@ def run_ours(args, ws, rank, local):
                  sh=torch.empty((N, 16, 3), device=dev))
     rng = torch.Generator(device=dev)
     rng.manual_seed(1234 + rank)
-    d_rgb = torch.randn((N_ENVS, 3, H, W), device=dev, generator=rng)
-    d_depth = 0.1 * torch.randn((N_ENVS, H, W), device=dev, generator=rng)
+    d_rgb = torch.randn((n_envs, 3, H, W), device=dev, generator=rng)
+    d_depth = 0.1 * torch.randn((n_envs, H, W), device=dev, generator=rng)
 
     stream = torch.cuda.Stream(device=dev)
 
@@ -351,7 +425,7 @@ def run_ours(args, ws, rank, local):
     plain_ms = None
     if not args.no_plain:
         envs = []
-        for e in range(N_ENVS):
+        for e in range(n_envs):
             a, b = int(offs[e]), int(offs[e + 1])
             ge = api.Gaussians(means[a:b], ls[a:b], quats[a:b], ologit[a:b], sh32[a:b])
             envs.append(ge)
@@ -359,10 +433,10 @@ def run_ours(args, ws, rank, local):
         big = int(np.argmax(sizes))
         r1 = api.Renderer(api.Batch(np.array([0, sizes[big]])), W, H, device=dev)
         outs1 = r1.alloc_outputs()
-        cam_e = [cams_d[e:e + 1] for e in range(N_ENVS)]
+        cam_e = [cams_d[e:e + 1] for e in range(n_envs)]
 
         def plain_step():
-            for e in range(N_ENVS):
+            for e in range(n_envs):
                 r1.batch = api.Batch(np.array([0, sizes[e]]))
                 r1.forward(envs[e], cam_e[e], out=outs1, stream=stream)
 
@@ -380,8 +454,8 @@ def run_ours(args, ws, rank, local):
 
     # --- end to end through the public API with host buffers
     cams_host = torch.from_numpy(np.ascontiguousarray(cams, np.float32)).pin_memory()
-    rgb_host = torch.empty((N_ENVS, 3, H, W), dtype=torch.float32).pin_memory()
-    depth_host = torch.empty((N_ENVS, H, W), dtype=torch.float32).pin_memory()
+    rgb_host = torch.empty((n_envs, 3, H, W), dtype=torch.float32).pin_memory()
+    depth_host = torch.empty((n_envs, H, W), dtype=torch.float32).pin_memory()
     cams_dev2 = torch.empty_like(cams_d)
 
     def e2e_step():
@@ -396,49 +470,31 @@ def run_ours(args, ws, rank, local):
     h2d = cams_host.numel() * 4
     d2h = (rgb_host.numel() + depth_host.numel()) * 4
 
-    # --- roofline of the dominant kernel
-    hbm, peak_kind = peaks()
-    R = stats["n_records"]
-    nvis = stats["n_visible"]
-    P = stats["n_pairs"]
-    f_v = nvis / max(R, 1)
-    # algorithmic bytes per launch (per-unit figures in the design doc)
-    alg = {
-        "preprocess": 16 * R + nvis * (12 + 16 + 4 + 96 + 44),
-        "preprocess_backward": 12 * N + nvis * (12 + 16 + 4 + 96 + 40) + N * 59 * 4,
-        "scatter": 4 * (R // 32) + nvis * 20 + 12 * P,
-        "sort_small": 16 * P,
-        "blend_backward": 48 * P + (N_ENVS * W * H) * 24 + 40 * P,
-        "blend": 48 * P + (N_ENVS * W * H) * 24,
-    }
-    dom = max(stage_ms, key=lambda k: stage_ms[k])
-    if dom in ("preprocess", "preprocess_backward", "scatter", "sort_small"):
-        ach = alg[dom] / (stage_ms[dom] * 1e-3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "peak_kind": peak_kind}
-    else:
-        ach = alg[dom] / (stage_ms[dom] * 1e-3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "peak_kind": peak_kind,
-                "note": "dominant kernel is issue-bound; HBM fraction of its algorithmic bytes shown"}
-    roof["per_kernel_gbs"] = {k: alg[k] / (stage_ms[k] * 1e-3) / 1e9 for k in alg if k in stage_ms}
+    # --- exact work counts for the blend rooflines (outside the timed region)
+    with torch.cuda.stream(stream):
+        n_eval_fwd = rend.count_evaluations(G16, cams_d, out=outs, stream=stream)
+    torch.cuda.synchronize()
+    n_eval_bwd = int(outs[3].sum().item())  # sum of n_contrib: what the backward walks
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof, per_kernel = rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_envs * W * H, N, sm_count,
+                                 (clocks or {}).get("sm_max_mhz"))
 
     # --- CPU oracle on a bounded sample (rank 0, N = 1)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        n, t = oracle_step(list(range(N_ENVS)), seed0, budget_s=args.cpu_budget)
+        n, t = oracle_step(list(range(n_envs)), seed0, budget_s=args.cpu_budget, scale=args.scale)
         cpu = {"value": n / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{n} env(s) of this batch (env 0..{n - 1}), FP64 forward (OpenMP, all cores) + "
                          f"backward (1 thread), {t:.1f} s"}
 
-    total_envs = N_ENVS * ws
+    total_envs = n_envs * ws
     line = {
         "metric": METRIC, "value": total_envs / (ms_fb * 1e-3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_fb, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{N_ENVS} envs x synthetic room (U[300k,1.5M] Gaussians, uneven), {W}x{H} RGB-D, "
+        "config": {"workload": f"{n_envs} envs x synthetic room (U[300k,1.5M] Gaussians, uneven), {W}x{H} RGB-D, "
                                "forward+backward, SH stored fp16, persistent blend in one CUDA graph, "
-                               "autotuned tile", "n_envs_per_gpu": N_ENVS, "gaussians_per_gpu": N,
+                               "autotuned tile", "n_envs_per_gpu": n_envs, "gaussians_per_gpu": N,
                    "width": W, "height": H, "tile": [rend.cfg.tile_w, rend.cfg.tile_h],
                    "batch_depth": rend.cfg.batch_depth, "pixels_per_thread": [rend.cfg.pix_x, rend.cfg.pix_y],
                    "sh_storage": "f16", "autotune": tuned,
@@ -449,6 +505,7 @@ def run_ours(args, ws, rank, local):
                            "what": "forward only: 64 gs_render calls, FP32 SH, 16x16 tiles, B=256, no graph",
                            "batched_fwd_speedup": plain_ms / ms_fwd}),
         "roofline": roof,
+        "roofline_per_kernel": per_kernel,
         "cpu_baseline": cpu,
         "e2e": {"value": total_envs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "what": "public API calls per step: cameras H2D from pinned memory, "
@@ -456,8 +513,10 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "clocks": clocks,
         "stage_ms": stage_ms,
-        "stats": {"records": R, "visible": nvis, "f_v": f_v, "pairs": P, "pairs_per_visible": P / max(nvis, 1),
-                  "max_bin": stats["max_bin"], "gen_s": t_gen},
+        "stats": {"records": stats["n_records"], "visible": stats["n_visible"],
+                  "f_v": stats["n_visible"] / max(stats["n_records"], 1), "pairs": stats["n_pairs"],
+                  "pairs_per_visible": stats["n_pairs"] / max(stats["n_visible"], 1), "max_bin": stats["max_bin"],
+                  "evaluations_fwd": n_eval_fwd, "evaluations_bwd": n_eval_bwd, "gen_s": t_gen},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -475,6 +534,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--tile", default="", help="fixed tile_w,tile_h,batch_depth instead of the autotuner")
+    ap.add_argument("--envs", type=int, default=N_ENVS, help="envs per GPU (64; fewer only for small profiling cases)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -63,6 +63,8 @@ typedef int32_t gs_status;
 #define GS_FLAG_NORMALIZE_DEPTH 2 /* depth = D / (1 - T), 0 where 1 - T < 1e-4 (forward only) */
 #define GS_FLAG_GRAD_OVERWRITE 4  /* gs_render_backward writes every gradient row (zeros where a
                                      Gaussian is seen by no view) instead of adding to it */
+#define GS_FLAG_COUNT_EVALS 8     /* the forward also counts blend evaluations into
+                                     gs_stats.n_evaluations (one atomic per warp and tile) */
 
 #define GS_MAX_ENVS 512
 #define GS_MAX_VIEWS 512
@@ -120,6 +122,9 @@ typedef struct {
     int64_t max_bin;    /* largest pair count of one (view, tile) */
     int32_t status;     /* device status word (0 or a GS_ERR_* code) */
     int32_t reserved;
+    int64_t n_evaluations; /* with GS_FLAG_COUNT_EVALS: sum over pixels of the covered Gaussians
+                              examined in depth order up to and including the one that stops the
+                              pixel (Sec. 3.1 blending rule); else 0 */
 } gs_stats;
 
 /* Canonical avatar Gaussians for LBS (device). */

@@ -22,7 +22,7 @@ GS_OK = 0
 STATUS_NAMES = {0: "GS_OK", -1: "GS_ERR_INVALID_ARG", -2: "GS_ERR_ALIGNMENT", -3: "GS_ERR_WORKSPACE_TOO_SMALL",
                 -4: "GS_ERR_CAPACITY", -5: "GS_ERR_CUDA", -6: "GS_ERR_TIMEOUT", -7: "GS_ERR_UNSUPPORTED"}
 SH_F32, SH_F16, SH_BF16 = 0, 1, 2
-FLAG_PERSISTENT, FLAG_NORMALIZE_DEPTH, FLAG_GRAD_OVERWRITE = 1, 2, 4
+FLAG_PERSISTENT, FLAG_NORMALIZE_DEPTH, FLAG_GRAD_OVERWRITE, FLAG_COUNT_EVALS = 1, 2, 4, 8
 N_STAGES = 11
 STAGES = ("setup", "preprocess", "scan", "scatter", "sort_small", "sort_big", "blend", "blend_backward",
           "preprocess_backward", "deform", "deform_backward")
@@ -55,7 +55,8 @@ class GsRenderConfig(ctypes.Structure):
 
 class GsStats(ctypes.Structure):
     _fields_ = [("n_records", ctypes.c_int64), ("n_visible", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
-                ("max_bin", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("max_bin", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_evaluations", ctypes.c_int64)]
 
 
 class GsWsSections(ctypes.Structure):
@@ -298,7 +299,19 @@ class Renderer:
         _check(_lib.gs_render_stats(_ptr(self.workspace), self.ws_bytes, _stream(stream), ctypes.byref(s)),
                "gs_render_stats")
         return dict(n_records=s.n_records, n_visible=s.n_visible, n_pairs=s.n_pairs, max_bin=s.max_bin,
-                    status=s.status)
+                    status=s.status, n_evaluations=s.n_evaluations)
+
+    def count_evaluations(self, g: Gaussians, cams: torch.Tensor, out=None, stream=None) -> int:
+        """Runs one forward with GS_FLAG_COUNT_EVALS and returns the blend
+        evaluations (per pixel, the covered Gaussians examined up to and
+        including the one that stops it, summed over all views)."""
+        prev = self.cfg.flags
+        self.cfg.flags = prev | FLAG_COUNT_EVALS
+        try:
+            self.forward(g, cams, out=out, stream=stream)
+            return self.stats(stream)["n_evaluations"]
+        finally:
+            self.cfg.flags = prev
 
     def status(self, stream=None) -> int:
         v = ctypes.c_int32(0)

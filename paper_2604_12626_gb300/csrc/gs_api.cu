@@ -502,6 +502,7 @@ gs_status gs_render_stats(const void *workspace, size_t workspace_bytes, void *s
     out->max_bin = h.max_bin;
     out->status = h.status;
     out->reserved = 0;
+    out->n_evaluations = (t.flags & GS_FLAG_COUNT_EVALS) ? (int64_t)h.n_evals : 0;
     return GS_OK;
 }
 

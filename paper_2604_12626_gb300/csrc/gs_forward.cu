@@ -829,6 +829,14 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
         __syncthreads();
     }
     cp_async_wait<0>();
+    if (tb->flags & GS_FLAG_COUNT_EVALS) {
+        unsigned long long ev = 0;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) ev += (uint32_t)ncov[p];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, off);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&w.hdr->n_evals, ev);
+    }
     const size_t HW = (size_t)W * H;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {

@@ -42,7 +42,9 @@ struct Header {
     uint32_t n_heavy;   // bins in the heavy-first list
     uint32_t heavy_min; // pair count from which a bin is in that list
     uint32_t n_heavy_items; // backward work items of the heavy bins (one per kSeg-long segment)
-    uint32_t pad[53];
+    uint32_t pad0;
+    unsigned long long n_evals; // blend evaluations, counted under GS_FLAG_COUNT_EVALS
+    uint32_t pad[50];
 };
 
 struct Table {

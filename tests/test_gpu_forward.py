@@ -216,3 +216,22 @@ def test_capacity_overflow_is_reported_not_written(gs):
     assert r.status() == -4  # GS_ERR_CAPACITY
     assert r.status() == 0   # cleared by the read
     assert torch.isfinite(out[0]).all()
+
+
+@pytest.mark.parametrize("tile,persistent", [((16, 16), False), ((8, 8), True)])
+def test_evaluation_count_matches_oracle(gs, oracle, tile, persistent):
+    """GS_FLAG_COUNT_EVALS: per pixel, the covered Gaussians examined in depth
+    order up to and including the one that stops it, summed -- the oracle's own
+    count.  Scene and seed are chosen so that the oracle flags no pixel whose
+    count FP32 rounding could change, so the two must agree exactly."""
+    g = synth.box_scene(1500, seed=2)
+    g["opacity_logits"] = g["opacity_logits"] + 3.0  # opaque enough that pixels stop
+    W = H = 64
+    cam = synth.identity_camera(W, H)
+    ora = oracle.render(g, cam, W, H, mode="gaussian")
+    assert not np.any(ora["amb"] & 2)
+    r, out, G, ct = render_gpu(gs, g, cam[None], W, H, tile=tile, persistent=persistent)
+    assert r.stats()["n_evaluations"] == 0  # not counted without the flag
+    ev = r.count_evaluations(G, ct)
+    assert ev == ora["evals"], (ev, ora["evals"])
+    assert ev > int(ora["n_contrib"].sum())  # skipped and stopping Gaussians are counted too

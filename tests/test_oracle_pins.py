@@ -60,6 +60,7 @@ def test_single_gaussian_closed_form(oracle, z, ls, logit, f):
     np.testing.assert_allclose(out["T"], 1.0 - a, rtol=0, atol=1e-13)
     np.testing.assert_allclose(out["depth"], z * a, rtol=0, atol=1e-12)
     assert np.array_equal(out["n_contrib"], blended.astype(np.int32))
+    assert out["evals"] == int(covered.sum())  # one examination per covered pixel
     assert oracle.project(g, cam, W, H)["radius"][0] == r  # 0.1 floor on the discriminant
     if logit >= 5.0:
         assert abs(out["T"][int(c), int(c)] - 0.01) < 1e-15  # 0.99 clamp at the centre
@@ -156,6 +157,38 @@ def test_stop_rule_never_blends_below_threshold(oracle):
     k_stop = next(k for k in range(1, n) if (1 - o) ** k < 1e-4)
     assert out["n_contrib"][4, 4] == k_stop - 1
     assert abs(out["T"][4, 4] - (1 - o) ** (k_stop - 1)) < 1e-15
+
+
+def test_evaluation_count_closed_form(oracle):
+    # 30 wide isotropic splats stacked on the axis, each covering the whole 9x9
+    # image: per pixel, the examinations are the splats in depth order up to and
+    # including the first whose blend would take T below 1e-4 (or all of them)
+    n, W, f, o = 30, 9, 8.0, 0.9
+    z = np.linspace(2.0, 4.0, n)
+    g = dict(means=np.stack([np.zeros(n), np.zeros(n), z], 1).astype(np.float32),
+             log_scales=np.zeros((n, 3), np.float32), quats=np.tile(np.float32([1, 0, 0, 0]), (n, 1)),
+             opacity_logits=np.full(n, np.float32(math.log(o / (1 - o)))), sh=np.zeros((n, 16, 3), np.float32))
+    out = oracle.render(g, cam_f(W, W, f), W, W)
+    o = 1.0 / (1.0 + math.exp(-float(g["opacity_logits"][0])))
+    zf = g["means"][:, 2].astype(np.float64)
+    s2 = (f / zf) ** 2 + 0.3
+    assert np.all(np.ceil(3.0 * np.sqrt(s2 + math.sqrt(0.1))) >= 4)  # every splat covers the image
+    jj, ii = np.mgrid[0:W, 0:W].astype(np.float64)
+    rho2 = (ii - 4) ** 2 + (jj - 4) ** 2
+    total = 0
+    for y in range(W):
+        for x in range(W):
+            T, k = 1.0, 0
+            for kk in range(n):
+                a = min(0.99, o * math.exp(-0.5 * rho2[y, x] / s2[kk]))
+                assert a >= 1.0 / 255.0
+                k += 1
+                if T * (1.0 - a) < 1e-4:
+                    break
+                T *= 1.0 - a
+            total += k
+    assert total < n * W * W  # some pixels stop
+    assert out["evals"] == total
 
 
 # ---------------------------------------------------------------------------

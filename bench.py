@@ -42,7 +42,6 @@ N_MIN, N_MAX = 300_000, 1_500_000
 TILE_CANDIDATES = [(16, 16, 256, 1, 1), (16, 16, 256, 2, 2), (16, 16, 128, 2, 2), (16, 16, 128, 2, 1),
                    (16, 8, 128, 1, 1), (16, 8, 128, 2, 1), (8, 8, 64, 1, 1), (8, 8, 128, 1, 1), (8, 8, 64, 2, 1),
                    (32, 16, 256, 2, 2)]
-KERNELS_PER_STEP = 9  # setup, preprocess, scan, scatter, sort_small, sort_big, blend, blend_backward, preprocess_backward
 
 
 def peaks():
@@ -242,7 +241,7 @@ def tune_fwd_bwd(api, rend, G, cams, candidates, N, dev, reps=2):
 OPS_PER_EVAL_FWD = 17   # offset, quadratic form, exp, alpha clamp / skip, T update, 3 colours + depth
 OPS_PER_EVAL_BWD = 40   # recomputed alpha, T_prev, dL/dalpha, conic / centre / colour / depth terms
 KERNEL_OF_STAGE = {"preprocess": "preprocess_kernel", "scan": "scan_bins_kernel", "scatter": "scatter_kernel",
-                   "sort_small": "sort_small_kernel", "sort_big": "sort_big_kernel",
+                   "sort_chunks": "sort_chunks_kernel", "merge": "merge_pass_kernel",
                    "blend": "blend_persistent_kernel", "blend_backward": "blend_backward_kernel",
                    "preprocess_backward": "preprocess_backward_kernel"}
 CSRC = os.path.join(ROOT, "paper_2604_12626_gb300", "csrc")
@@ -287,8 +286,9 @@ def rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_pix, N, sm_count, sm_mh
     }
     ops = {"blend": OPS_PER_EVAL_FWD * n_eval_fwd, "blend_backward": OPS_PER_EVAL_BWD * n_eval_bwd}
     ms = dict(stage_ms)
-    if "sort_small" in ms:
-        ms["sort"] = ms.get("sort_small", 0.0) + ms.get("sort_big", 0.0)
+    if "sort" in ms:
+        ms["sort_chunks"] = ms["sort"]
+        ms["sort"] = ms["sort"] + ms.get("merge", 0.0)
     out = {}
     for k, b in mem.items():
         if k in ms and ms[k] > 0:
@@ -302,7 +302,7 @@ def rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_pix, N, sm_count, sm_mh
                       "algorithmic": f, "ms": ms[k],
                       "peak_kind": f"derived: {sm_count} SMs x 128 FP32 lanes x {mhz:.0f} MHz"}
     for k, v in out.items():
-        kern = [KERNEL_OF_STAGE[x] for x in (("sort_small", "sort_big") if k == "sort" else (k,))]
+        kern = [KERNEL_OF_STAGE[x] for x in (("sort_chunks", "merge") if k == "sort" else (k,))]
         tb = [traffic.get(x, {}).get("dram_bytes_per_launch") for x in kern]
         v["traffic"] = None if any(x is None for x in tb) else float(sum(tb))
     dom = max(out, key=lambda k: out[k]["ms"])
@@ -510,7 +510,7 @@ def run_ours(args, ws, rank, local):
         "e2e": {"value": total_envs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "what": "public API calls per step: cameras H2D from pinned memory, "
                                                    "gs_render + gs_render_backward, RGB + depth D2H"},
-        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "gpu_launches": (rend.kernels_per_forward() + 2) * args.steps,  # + blend_backward, preprocess_backward
         "clocks": clocks,
         "stage_ms": stage_ms,
         "stats": {"records": stats["n_records"], "visible": stats["n_visible"],

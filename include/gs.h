@@ -156,7 +156,9 @@ gs_status gs_render_workspace_size(const gs_render_config *cfg, const gs_batch *
  *   out_T         device [V,H,W]    final transmittance
  *   out_ncontrib  device [V,H,W] int32: 1 + position of the last blended
  *                 Gaussian among the Gaussians covering that pixel
- * The workspace keeps what the backward needs. */
+ * The workspace keeps what the backward needs.  A tile whose CTA
+ * ((tile_w / pix_x) x (tile_h / pix_y) threads) exceeds what the blend kernels'
+ * registers allow is rejected with GS_ERR_UNSUPPORTED (e.g. 32x32 at 1x1). */
 gs_status gs_render(const gs_gaussians *g, const gs_batch *batch, const gs_camera *cams, const gs_render_config *cfg,
                     void *workspace, size_t workspace_bytes, float *out_rgb, float *out_depth, float *out_T,
                     int32_t *out_ncontrib, void *stream);
@@ -255,8 +257,9 @@ gs_status gs_workspace_sections(const gs_render_config *cfg, const gs_batch *bat
  * around each kernel (not while the stream is being captured).
  * gs_profile_read synchronises on those events and returns, per stage, the
  * summed milliseconds and the number of launches since the last read, then
- * resets.  Stages: 0 setup, 1 preprocess, 2 scan, 3 scatter, 4 sort_small,
- * 5 sort_big, 6 blend, 7 blend_backward, 8 preprocess_backward, 9 deform,
+ * resets.  Stages: 0 setup, 1 preprocess, 2 scan, 3 scatter, 4 sort (every
+ * bin, or 4096-key chunk of a larger bin), 5 merge (bins of more than 4096
+ * pairs), 6 blend, 7 blend_backward, 8 preprocess_backward, 9 deform,
  * 10 deform_backward (GS_N_STAGES).  Not thread-safe. */
 #define GS_N_STAGES 11
 gs_status gs_profile_enable(int32_t enable);

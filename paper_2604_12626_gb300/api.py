@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "GS_OK", -1: "GS_ERR_INVALID_ARG", -2: "GS_ERR_ALIGNMENT", -3
 SH_F32, SH_F16, SH_BF16 = 0, 1, 2
 FLAG_PERSISTENT, FLAG_NORMALIZE_DEPTH, FLAG_GRAD_OVERWRITE, FLAG_COUNT_EVALS = 1, 2, 4, 8
 N_STAGES = 11
-STAGES = ("setup", "preprocess", "scan", "scatter", "sort_small", "sort_big", "blend", "blend_backward",
+STAGES = ("setup", "preprocess", "scan", "scatter", "sort", "merge", "blend", "blend_backward",
           "preprocess_backward", "deform", "deform_backward")
 MAX_ENVS = MAX_VIEWS = 512
 
@@ -337,7 +337,15 @@ class Renderer:
                     vis=view(s.vis, ((R + 31) // 32) * 4, torch.int32),
                     keys=view(s.keys, s.pair_capacity * 8, torch.int64),
                     bin_start=view(s.bin_start, (s.n_bins + 1) * 4, torch.int32),
-                    n_bins=s.n_bins, tiles_x=s.tiles_x, tiles_y=s.tiles_y, tiles_per_view=s.tiles_per_view)
+                    n_bins=s.n_bins, tiles_x=s.tiles_x, tiles_y=s.tiles_y, tiles_per_view=s.tiles_per_view,
+                    pair_capacity=s.pair_capacity)
+
+    def kernels_per_forward(self) -> int:
+        """Kernel launches of one forward: setup, preprocess, scan, scatter,
+        sort, one merge pass per doubling of 4096 up to the pair capacity, blend."""
+        cap = self.sections()["pair_capacity"]
+        chunks = -(-cap // 4096)
+        return 6 + max(0, (chunks - 1).bit_length())
 
     def autotune(self, g: Gaussians, cams: torch.Tensor, candidates, reps=3, out=None, stream=None):
         """Time each (tile_w, tile_h, batch_depth, pix_x, pix_y) candidate; keep the fastest in self.cfg."""

@@ -99,6 +99,7 @@ gs_status device_init(int *sms)
     std::call_once(g_once[dev], [dev]() {
         cudaError_t r = configure_forward_kernels();
         if (r == cudaSuccess) r = configure_backward_kernels();
+        if (r == cudaSuccess) r = configure_sort_kernels();
         int n = 0;
         if (r == cudaSuccess) r = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         g_sms[dev] = n;
@@ -173,7 +174,7 @@ gs_status make_plan(const gs_render_config *cfg, const gs_batch *b, Plan &p)
     p.o_fcnt = o; o = align256(o + (size_t)nb * 4);
     p.o_start = o; o = align256(o + (size_t)(nb + 1) * 4);
     p.o_cur = o; o = align256(o + (size_t)nb * 4);
-    p.o_big = o; o = align256(o + (size_t)nb * 4);
+    p.o_big = o; o = align256(o + (size_t)(2 * (p.cap / kSortChunk) + 2) * 8);
     p.o_heavy = o; o = align256(o + (size_t)4096 * 4);
     p.chunk = chunk_of(p.N);
     int64_t nch = 0;
@@ -209,7 +210,7 @@ Ws ws_ptrs(void *base, const Plan &p)
     w.bin_count = reinterpret_cast<uint32_t *>(b + p.o_cnt);
     w.bin_start = reinterpret_cast<uint32_t *>(b + p.o_start);
     w.bin_cursor = reinterpret_cast<uint32_t *>(b + p.o_cur);
-    w.big_list = reinterpret_cast<uint32_t *>(b + p.o_big);
+    w.big_list = reinterpret_cast<unsigned long long *>(b + p.o_big);
     w.heavy = reinterpret_cast<uint32_t *>(b + p.o_heavy);
     w.bin_fcount = reinterpret_cast<uint32_t *>(b + p.o_fcnt);
     w.rel = reinterpret_cast<uint32_t *>(b + p.o_rel);
@@ -297,6 +298,7 @@ gs_status enqueue_forward(const gs_gaussians *g, const gs_batch *b, const gs_cam
     st = check_gaussians(g, p, true);
     if (st != GS_OK) return st;
     if (!cams || !ws || !rgb || !depth || !T || !ncontrib) return GS_ERR_INVALID_ARG;
+    if (p.threads > blend_thread_limit(p.px, p.py)) return GS_ERR_UNSUPPORTED; // CTA too large for the registers
     if (!aligned16(cams) || !aligned16(ws) || !aligned16(rgb) || !aligned16(depth) || !aligned16(T) ||
         !aligned16(ncontrib))
         return GS_ERR_ALIGNMENT;
@@ -327,11 +329,11 @@ gs_status enqueue_forward(const gs_gaussians *g, const gs_batch *b, const gs_cam
     }
     {
         Stage st4(4, s);
-        launch_sort_small(w, p.n_bins, s);
+        launch_sort_chunks(w, sms, s);
     }
     {
         Stage st5(5, s);
-        launch_sort_big(w, sms, s);
+        launch_merge_passes(w, merge_passes_for_capacity(p.cap), sms, s);
     }
     const bool persistent = (p.flags & GS_FLAG_PERSISTENT) != 0;
     {
@@ -386,6 +388,7 @@ gs_status gs_render_backward(const gs_gaussians *g, const gs_batch *batch, const
     st = check_gaussians(g, p, true);
     if (st != GS_OK) return st;
     if (cfg->flags & GS_FLAG_NORMALIZE_DEPTH) return GS_ERR_UNSUPPORTED;
+    if (p.threads > blend_backward_thread_limit(p.px, p.py)) return GS_ERR_UNSUPPORTED;
     if (!cams || !workspace || !d_rgb || !d_depth || !d_means || !d_log_scales || !d_quats || !d_opacity_logits ||
         !d_sh)
         return GS_ERR_INVALID_ARG;

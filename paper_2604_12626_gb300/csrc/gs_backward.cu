@@ -32,16 +32,6 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-__device__ __forceinline__ void bin_range_b(const Ws &w, int bin, uint32_t &start, uint32_t &n)
-{
-    const uint64_t cap = (uint64_t)w.tb->pair_capacity;
-    uint64_t s = w.bin_start[bin], e = w.bin_start[bin + 1];
-    if (e > cap) e = cap;
-    if (s > e) s = e;
-    start = (uint32_t)s;
-    n = (uint32_t)(e - s);
-}
-
 // Sums v[0..15] over the warp with 16 shuffles (butterfly transpose): on
 // return, lane l holds the warp total of v[(l >> 1) & 15] (lanes l and l^1
 // hold the same value).
@@ -126,7 +116,7 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
     for (int b = 0; b < PY; ++b) pyc[b] = pix_c(j0 + b, cam.cy);
     const size_t HW = (size_t)W * H;
     uint32_t start, n;
-    bin_range_b(w, bin, start, n);
+    bin_range(w, bin, start, n);
     const unsigned long long *keys = w.keys + start;
     const uint32_t R = (uint32_t)tb->n_records;
 
@@ -716,26 +706,32 @@ __global__ void __launch_bounds__(256, 2) preprocess_backward_kernel(const gs_ca
                 seen = (__ldg(w.vis + (rec >> 5)) >> (rec & 31)) & 1u;
             }
         }
+        const unsigned bal = __ballot_sync(0xffffffffu, seen);
         if (OVERWRITE) {
-            // zero this warp's 32 consecutive rows with coalesced stores; the
-            // rows of seen Gaussians are overwritten later by this same warp
+            // zero the rows of this warp's 32 consecutive Gaussians that no
+            // view sees, with coalesced stores; seen rows are written once,
+            // later, by this same warp
             const int nrow = (int)min((int64_t)32, g1 - base);
+            const unsigned unseen = ~bal;
             float4 *sh4 = reinterpret_cast<float4 *>(o.sh + 48 * base);
-            for (int i = lane; i < 12 * nrow; i += 32) sh4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int i = lane; i < 3 * nrow; i += 32) o.means[3 * base + i] = 0.f;
-            if (lane < nrow) o.ologits[base + lane] = 0.f;
+            for (int i = lane; i < 12 * nrow; i += 32)
+                if ((unseen >> (i / 12)) & 1u) sh4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = lane; i < 3 * nrow; i += 32)
+                if ((unseen >> (i / 3)) & 1u) o.means[3 * base + i] = 0.f;
+            if (lane < nrow && !seen) o.ologits[base + lane] = 0.f;
             if (split_cov) {
-                if (g < g1) zero_rows(o, g, g >= tb->env_cov_begin[lo]);
+                if (g < g1 && !seen) zero_rows(o, g, g >= tb->env_cov_begin[lo]);
             } else if (use_cov) {
                 if (o.cov3d)
-                    for (int i = lane; i < 6 * nrow; i += 32) o.cov3d[6 * base + i] = 0.f;
+                    for (int i = lane; i < 6 * nrow; i += 32)
+                        if ((unseen >> (i / 6)) & 1u) o.cov3d[6 * base + i] = 0.f;
             } else {
-                for (int i = lane; i < 3 * nrow; i += 32) o.log_scales[3 * base + i] = 0.f;
-                if (lane < nrow) reinterpret_cast<float4 *>(o.quats)[base + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int i = lane; i < 3 * nrow; i += 32)
+                    if ((unseen >> (i / 3)) & 1u) o.log_scales[3 * base + i] = 0.f;
+                if (lane < nrow && !seen)
+                    reinterpret_cast<float4 *>(o.quats)[base + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            __syncwarp();
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, seen);
         if (seen) q[(tail + __popc(bal & ((1u << lane) - 1u))) & (kBwdWarpQ - 1)] = (uint32_t)(g - g0);
         tail += __popc(bal);
         __syncwarp();
@@ -781,6 +777,22 @@ static void launch_bb(const gs_camera *cams, const Ws &w, const float *d_rgb, co
     int grid = n_sms * (nb > 0 ? nb : 1);
     if (grid > n_bins) grid = n_bins;
     blend_backward_kernel<PX, PY><<<grid, threads, smem, s>>>(cams, w, d_rgb, d_depth);
+}
+
+template <int PX, int PY>
+static int bb_limit_t()
+{
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, blend_backward_kernel<PX, PY>) != cudaSuccess) return 0;
+    return a.maxThreadsPerBlock;
+}
+
+int blend_backward_thread_limit(int px, int py)
+{
+    if (px == 2 && py == 2) return bb_limit_t<2, 2>();
+    if (px == 2) return bb_limit_t<2, 1>();
+    if (py == 2) return bb_limit_t<1, 2>();
+    return bb_limit_t<1, 1>();
 }
 
 void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,

@@ -11,9 +11,8 @@
 //   scatter     one (depth key << 32 | record) key per touched tile, placed in
 //               its bin by an atomic cursor (order inside a bin is arbitrary)
 //   sort        each bin sorted by key = (FP32 depth bits, record index), so the
-//               result equals a stable sort of the keys emitted in record order;
-//               <= 4096 keys: bitonic sort in shared memory, one CTA per bin;
-//               larger bins: 16384-key shared-memory chunks + merge-path merges
+//               result equals a stable sort of the keys emitted in record order
+//               (gs_sort.cu)
 //   blend       one CTA per (view, tile) -- or a persistent grid pulling tiles
 //               from an atomic queue -- stages batches of records in shared
 //               memory and blends front to back per pixel with block-wide early
@@ -343,9 +342,27 @@ __global__ void __launch_bounds__(1024) scan_bins_kernel(Ws w)
     // stays inside [0, capacity) and the status word records the overflow
     const unsigned long long cap = (unsigned long long)w.tb->pair_capacity;
     unsigned long long run = sh[threadIdx.x] - s; // exclusive
+    // bins of more than kSortChunk pairs (after the clamp) are sorted in
+    // kSortChunk-long chunks and merged: one list entry per chunk
+    __shared__ uint32_t n_big, max_pass;
+    if (threadIdx.x == 0) n_big = max_pass = 0;
+    __syncthreads();
     for (int i = b0; i < b1; ++i) {
-        w.bin_start[i] = (uint32_t)min(run, cap);
+        const unsigned long long lo = min(run, cap);
+        w.bin_start[i] = (uint32_t)lo;
         run += w.bin_count[i] + w.bin_fcount[i];
+        const uint32_t n = (uint32_t)(min(run, cap) - lo);
+        if (n > (uint32_t)kSortChunk) {
+            const uint32_t nch = (n + kSortChunk - 1) / kSortChunk;
+            const uint32_t at = atomicAdd(&n_big, nch);
+            for (uint32_t t = 0; t < nch; ++t) w.big_list[at + t] = ((unsigned long long)i << 32) | t;
+            atomicMax(&max_pass, (uint32_t)(32 - __clz(nch - 1u)));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        w.hdr->n_big = n_big;
+        w.hdr->max_pass = max_pass;
     }
     if (threadIdx.x == T - 1) {
         const unsigned long long total = sh[T - 1];
@@ -541,18 +558,8 @@ __global__ void __launch_bounds__(256) scatter_kernel(const gs_camera *__restric
 }
 
 // ---------------------------------------------------------------------------
-// per-bin sort
+// bitonic sort in shared memory (the heavy-bin list of the scan)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void bin_range(const Ws &w, int bin, uint32_t &start, uint32_t &n)
-{
-    const uint64_t cap = (uint64_t)w.tb->pair_capacity;
-    uint64_t s = w.bin_start[bin], e = w.bin_start[bin + 1];
-    if (e > cap) e = cap;
-    if (s > e) s = e;
-    start = (uint32_t)s;
-    n = (uint32_t)(e - s);
-}
-
 // Bitonic sort of s[0..m) (m a power of two) by the whole CTA.
 __device__ __forceinline__ void bitonic_smem(unsigned long long *s, int m)
 {
@@ -570,97 +577,6 @@ __device__ __forceinline__ void bitonic_smem(unsigned long long *s, int m)
                 }
             }
             __syncthreads();
-        }
-    }
-}
-
-__device__ __forceinline__ int pow2_at_least(uint32_t n)
-{
-    int m = 1;
-    while ((uint32_t)m < n) m <<= 1;
-    return m;
-}
-
-constexpr int kSmallSort = 4096;
-constexpr int kBigSort = 16384;
-
-__global__ void __launch_bounds__(256) sort_small_kernel(Ws w)
-{
-    extern __shared__ unsigned long long smem_keys[];
-    const int bin = blockIdx.x;
-    uint32_t start, n;
-    bin_range(w, bin, start, n);
-    if (n <= 1) return;
-    if (n > (uint32_t)kSmallSort) {
-        if (threadIdx.x == 0) w.big_list[atomicAdd(&w.hdr->n_big, 1u)] = (uint32_t)bin;
-        return;
-    }
-    const int m = pow2_at_least(n);
-    unsigned long long *src = w.keys + start;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) smem_keys[i] = i < (int)n ? src[i] : ~0ull;
-    __syncthreads();
-    bitonic_smem(smem_keys, m);
-    for (int i = threadIdx.x; i < (int)n; i += blockDim.x) src[i] = smem_keys[i];
-}
-
-// Merge sorted a[0..na) and b[0..nb) into d (keys unique), whole CTA.
-__device__ void merge_cta(const unsigned long long *a, uint32_t na, const unsigned long long *b, uint32_t nb,
-                          unsigned long long *d)
-{
-    const uint32_t total = na + nb;
-    const uint32_t per = (total + blockDim.x - 1) / blockDim.x;
-    const uint32_t d0 = min(total, threadIdx.x * per), d1 = min(total, d0 + per);
-    if (d0 >= d1) return;
-    uint32_t lo = d0 > nb ? d0 - nb : 0, hi = min(d0, na);
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (a[mid] < b[d0 - 1 - mid]) lo = mid + 1;
-        else hi = mid;
-    }
-    uint32_t i = lo, j = d0 - lo;
-    for (uint32_t o = d0; o < d1; ++o) {
-        const bool take_a = j >= nb || (i < na && a[i] < b[j]);
-        d[o] = take_a ? a[i++] : b[j++];
-    }
-}
-
-__global__ void __launch_bounds__(1024) sort_big_kernel(Ws w)
-{
-    extern __shared__ unsigned long long smem_keys[];
-    __shared__ uint32_t item;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) item = atomicAdd(&w.hdr->big_queue, 1u);
-        __syncthreads();
-        if (item >= w.hdr->n_big) break;
-        const int bin = (int)w.big_list[item];
-        uint32_t start, n;
-        bin_range(w, bin, start, n);
-        unsigned long long *keys = w.keys + start;
-        // sort chunks of kBigSort in shared memory
-        for (uint32_t c0 = 0; c0 < n; c0 += kBigSort) {
-            const uint32_t cn = min((uint32_t)kBigSort, n - c0);
-            const int m = pow2_at_least(cn);
-            for (int i = threadIdx.x; i < m; i += blockDim.x) smem_keys[i] = i < (int)cn ? keys[c0 + i] : ~0ull;
-            __syncthreads();
-            bitonic_smem(smem_keys, m);
-            for (int i = threadIdx.x; i < (int)cn; i += blockDim.x) keys[c0 + i] = smem_keys[i];
-            __syncthreads();
-        }
-        // merge runs, ping-ponging with the scratch buffer
-        unsigned long long *src = keys, *dst = w.scratch + start;
-        for (uint32_t width = kBigSort; width < n; width <<= 1) {
-            for (uint32_t lo = 0; lo < n; lo += 2 * width) {
-                const uint32_t mid = min(lo + width, n), hi = min(lo + 2 * width, n);
-                merge_cta(src + lo, mid - lo, src + mid, hi - mid, dst + lo);
-            }
-            __syncthreads();
-            unsigned long long *t = src;
-            src = dst;
-            dst = t;
-        }
-        if (src != keys) {
-            for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) keys[i] = src[i];
         }
     }
 }
@@ -910,18 +826,6 @@ void launch_scatter(const gs_camera *cams, const Ws &w, int n_chunks, cudaStream
     if (n_chunks) scatter_kernel<<<n_chunks, 256, kScatterSmem, s>>>(cams, w);
 }
 
-int sort_big_smem_bytes() { return kBigSort * 8; }
-
-void launch_sort_small(const Ws &w, int n_bins, cudaStream_t s)
-{
-    sort_small_kernel<<<n_bins, 256, kSmallSort * 8, s>>>(w);
-}
-
-void launch_sort_big(const Ws &w, int n_sms, cudaStream_t s)
-{
-    sort_big_kernel<<<n_sms, 1024, kBigSort * 8, s>>>(w);
-}
-
 int blend_smem_bytes(int batch_depth) { return 2 * 3 * batch_depth * (int)sizeof(float4); }
 
 template <int PX, int PY>
@@ -940,6 +844,23 @@ static void launch_blend_t(const gs_camera *cams, const Ws &w, const OutPtrs &o,
     }
 }
 
+template <int PX, int PY>
+static int blend_limit_t()
+{
+    cudaFuncAttributes a, b;
+    if (cudaFuncGetAttributes(&a, blend_kernel<PX, PY>) != cudaSuccess) return 0;
+    if (cudaFuncGetAttributes(&b, blend_persistent_kernel<PX, PY>) != cudaSuccess) return 0;
+    return a.maxThreadsPerBlock < b.maxThreadsPerBlock ? a.maxThreadsPerBlock : b.maxThreadsPerBlock;
+}
+
+int blend_thread_limit(int px, int py)
+{
+    if (px == 2 && py == 2) return blend_limit_t<2, 2>();
+    if (px == 2) return blend_limit_t<2, 1>();
+    if (py == 2) return blend_limit_t<1, 2>();
+    return blend_limit_t<1, 1>();
+}
+
 void launch_blend(const gs_camera *cams, const Ws &w, float *rgb, float *depth, float *T, int32_t *ncontrib,
                   int n_bins, int px, int py, int threads, int batch_depth, bool persistent, int n_sms,
                   cudaStream_t s)
@@ -953,9 +874,8 @@ void launch_blend(const gs_camera *cams, const Ws &w, float *rgb, float *depth, 
 
 cudaError_t configure_forward_kernels()
 {
-    cudaError_t e = cudaFuncSetAttribute(sort_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBigSort * 8);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(preprocess_kernel<GS_SH_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPreSmem);
+    cudaError_t e = cudaFuncSetAttribute(preprocess_kernel<GS_SH_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kPreSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(preprocess_kernel<GS_SH_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPreSmem);
     if (e == cudaSuccess)

@@ -10,9 +10,9 @@
 //   bin_count   [B] pairs per (view, tile) bin, B = V * tiles
 //   bin_start   [B+1] exclusive scan of bin_count (tile ranges)
 //   bin_cursor  [B] scatter cursors
-//   big_list    [B] bins sorted by the large-bin path
+//   big_list    [2 P_cap/4096 + 2] (bin << 32 | chunk) of the bins of > 4096 pairs
 //   keys        [P_cap] uint64 (FP32 depth bits << 32 | record index)
-//   scratch     [P_cap] uint64, merge buffer of the large-bin sort
+//   scratch     [P_cap] uint64, ping-pong buffer of the large-bin merges
 //   pix_T       [V*H*W] final transmittance (saved for the backward)
 //   pix_last    [V*H*W] 1 + tile-list position of the last blended pair
 //   d_rec       [R] 12 floats: dL/d(uc, vc, A, B, C, opacity, r, g, b, z)
@@ -29,20 +29,21 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTStop = 1e-4f;
 constexpr float kDilation = 0.3f;
+constexpr int kSortChunk = 4096; // keys one CTA sorts; larger bins are merged
 
 struct Header {
     int32_t status;     // sticky GS_ERR_* (0 = ok)
     uint32_t n_visible; // visible records
     uint32_t n_pairs;   // total pairs (before capacity clamp)
     uint32_t max_bin;   // largest bin
-    uint32_t n_big;     // bins routed to the large-bin sort
+    uint32_t n_big;     // 4096-key chunks of the bins of more than 4096 pairs
     uint32_t queue;     // persistent blend work counter
     uint32_t queue_bwd; // persistent backward work counter
-    uint32_t big_queue; // large-bin sort work counter
+    uint32_t big_queue; // chunk-sort work counter
     uint32_t n_heavy;   // bins in the heavy-first list
     uint32_t heavy_min; // pair count from which a bin is in that list
     uint32_t n_heavy_items; // backward work items of the heavy bins (one per kSeg-long segment)
-    uint32_t pad0;
+    uint32_t max_pass;  // merge passes the largest bin needs
     unsigned long long n_evals; // blend evaluations, counted under GS_FLAG_COUNT_EVALS
     uint32_t pad[50];
 };
@@ -70,7 +71,8 @@ struct Ws {
     Table *tb;
     float4 *rec;  // 3 float4 per record
     uint32_t *vis;
-    uint32_t *bin_count, *bin_start, *bin_cursor, *big_list, *heavy;
+    uint32_t *bin_count, *bin_start, *bin_cursor, *heavy;
+    unsigned long long *big_list;
     uint32_t *bin_fcount; // pairs of chunks counted without shared-memory aggregation
     uint32_t *rel;        // [n_chunks][kHistCap] offset of a chunk's pairs inside each bin
     uint32_t *heavy_seg;  // [kHeavyCap + 1] first backward segment of each heavy bin
@@ -181,6 +183,17 @@ __device__ __forceinline__ int bin_of_item(const Ws &w, uint32_t item)
 __device__ __forceinline__ float raw_alpha(float opacity, float power) { return __fmul_rn(opacity, __expf(power)); }
 
 __device__ __forceinline__ void set_status(Header *h, int32_t code) { atomicCAS(&h->status, 0, code); }
+
+// Pair range [start, start + n) of a bin, clamped to the pair capacity.
+__device__ __forceinline__ void bin_range(const Ws &w, int bin, uint32_t &start, uint32_t &n)
+{
+    const uint64_t cap = (uint64_t)w.tb->pair_capacity;
+    uint64_t s = w.bin_start[bin], e = w.bin_start[bin + 1];
+    if (e > cap) e = cap;
+    if (s > e) s = e;
+    start = (uint32_t)s;
+    n = (uint32_t)(e - s);
+}
 
 // ---------------------------------------------------------------------------
 // Projection of one Gaussian into one view (forward and backward share it).

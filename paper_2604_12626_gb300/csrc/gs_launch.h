@@ -14,11 +14,17 @@ void launch_setup(const Table &tb, const Ws &w, cudaStream_t s);
 void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s);
 void launch_scan(const Ws &w, cudaStream_t s);
 void launch_scatter(const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s);
-void launch_sort_small(const Ws &w, int n_bins, cudaStream_t s);
-void launch_sort_big(const Ws &w, int n_sms, cudaStream_t s);
+cudaError_t configure_sort_kernels();
+int merge_passes_for_capacity(int64_t pair_capacity);
+void launch_sort_chunks(const Ws &w, int n_sms, cudaStream_t s);
+void launch_merge_passes(const Ws &w, int n_passes, int n_sms, cudaStream_t s);
 void launch_blend(const gs_camera *cams, const Ws &w, float *rgb, float *depth, float *T, int32_t *ncontrib,
                   int n_bins, int px, int py, int threads, int batch_depth, bool persistent, int n_sms,
                   cudaStream_t s);
+// Largest CTA (threads) the blend kernels of this pixels-per-thread variant can
+// launch with (register-limited), forward and backward.
+int blend_thread_limit(int px, int py);
+int blend_backward_thread_limit(int px, int py);
 void launch_count_visible(const Ws &w, int64_t n_words, cudaStream_t s);
 
 struct GradOut {

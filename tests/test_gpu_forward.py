@@ -235,3 +235,35 @@ def test_evaluation_count_matches_oracle(gs, oracle, tile, persistent):
     ev = r.count_evaluations(G, ct)
     assert ev == ora["evals"], (ev, ora["evals"])
     assert ev > int(ora["n_contrib"].sum())  # skipped and stopping Gaussians are counted too
+
+
+def test_large_bins_keys_bit_exact(gs):
+    """Bins of tens of thousands of pairs: 4096-key chunk sorts, then several
+    merge passes (runs of 4096, 8192, ...) that must end in the keys buffer."""
+    g = synth.room_scene(400_000, seed=7)
+    W = H = 64
+    cam = synth.room_camera(7, W, H)
+    with pytest.raises(gs.GsError, match="UNSUPPORTED"):  # 1024 threads: more registers than an SM has
+        render_gpu(gs, g, cam[None], W, H, tile=(32, 32), batch_depth=256)
+    r, out, _, _ = render_gpu(gs, g, cam[None], W, H, tile=(32, 32), batch_depth=256, pix=(2, 2))
+    assert r.stats()["max_bin"] > 4 * 4096
+    _check_keys(r, cam[None], W, H, np.zeros(g["means"].shape[0], np.int64))
+
+
+@pytest.mark.parametrize("n", [3000, 20_000])
+def test_equal_depths_sorted_by_record_index(gs, oracle, n):
+    """Every Gaussian at exactly the same FP32 depth: the order inside a bin is
+    then the record index alone (within one chunk and across merged chunks)."""
+    rng = np.random.default_rng(11)
+    g = dict(means=np.stack([rng.uniform(-0.8, 0.8, n), rng.uniform(-0.8, 0.8, n), np.full(n, 3.0)], 1).astype(np.float32),
+             log_scales=rng.normal(-3.0, 0.3, (n, 3)).astype(np.float32),
+             quats=rng.normal(size=(n, 4)).astype(np.float32),
+             opacity_logits=rng.normal(0, 1, n).astype(np.float32),
+             sh=(rng.normal(0, 0.1, (n, 16, 3))).astype(np.float32))
+    W = H = 32
+    cam = synth.identity_camera(W, H)
+    r, out, _, _ = render_gpu(gs, g, cam[None], W, H, tile=(16, 16))
+    _check_keys(r, cam[None], W, H, np.zeros(n, np.int64))
+    if n > 4096:
+        assert r.stats()["max_bin"] > 4096
+    compare_view(gpu_outputs(out, 0), oracle.render(g, cam, W, H))

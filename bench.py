@@ -118,32 +118,21 @@ def smi_index(local: int) -> int:
 
 
 def dist_init():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if ws > 1:
-        import torch.distributed as dist
+    from paper_2604_12626_gb300 import shard
 
-        dist.init_process_group("nccl")
-    return ws, rank, local
+    return shard.init("nccl")
 
 
 def barrier(ws):
-    if ws > 1:
-        import torch.distributed as dist
+    from paper_2604_12626_gb300 import shard
 
-        dist.barrier()
+    shard.barrier(ws)
 
 
 def max_over_ranks(x, ws):
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
+    from paper_2604_12626_gb300 import shard
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return shard.max_over_ranks(x, ws)
 
 
 # ---------------------------------------------------------------------------
@@ -313,12 +302,12 @@ def rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_pix, N, sm_count, sm_mh
 def run_ours(args, ws, rank, local):
     import torch
 
-    from paper_2604_12626_gb300 import api, synth
+    from paper_2604_12626_gb300 import api, shard, synth
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n_envs = args.envs
-    seed0 = rank * n_envs  # weak scaling: every rank renders its own envs
+    seed0 = shard.env_block(rank, n_envs).start  # weak scaling: every rank renders its own envs
     t0 = time.time()
     g, offs, cams = synth.batched_rooms(n_envs, N_MIN, N_MAX, W, H, seed0=seed0, scale=args.scale)
     t_gen = time.time() - t0
@@ -489,7 +478,7 @@ def run_ours(args, ws, rank, local):
 
     total_envs = n_envs * ws
     line = {
-        "metric": METRIC, "value": total_envs / (ms_fb * 1e-3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "metric": METRIC, "value": shard.job_throughput(n_envs, ws, ms_fb), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_fb, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{n_envs} envs x synthetic room (U[300k,1.5M] Gaussians, uneven), {W}x{H} RGB-D, "

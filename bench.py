@@ -292,7 +292,7 @@ def rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_pix, N, sm_count, sm_mh
                       "peak_kind": f"derived: {sm_count} SMs x 128 FP32 lanes x {mhz:.0f} MHz"}
     for k, v in out.items():
         kern = [KERNEL_OF_STAGE[x] for x in (("sort_chunks", "merge") if k == "sort" else (k,))]
-        tb = [traffic.get(x, {}).get("dram_bytes_per_launch") for x in kern]
+        tb = [traffic.get(x, {}).get("dram_bytes_per_call") for x in kern]
         v["traffic"] = None if any(x is None for x in tb) else float(sum(tb))
     dom = max(out, key=lambda k: out[k]["ms"])
     roof = dict(out[dom], kernel=dom)

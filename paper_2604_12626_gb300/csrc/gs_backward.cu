@@ -114,6 +114,7 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
     for (int a = 0; a < PX; ++a) pxc[a] = pix_c(i0 + a, cam.cx);
 #pragma unroll
     for (int b = 0; b < PY; ++b) pyc[b] = pix_c(j0 + b, cam.cy);
+    const float2 npx2 = make_float2(-pxc[0], -pxc[PX - 1]);
     const size_t HW = (size_t)W * H;
     uint32_t start, n;
     bin_range(w, bin, start, n);
@@ -228,22 +229,42 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
             for (int x = 0; x < 32; ++x) g[x] = 0.f;
             bool contrib = false;
             if (__any_sync(0xffffffffu, (uint32_t)(lo + k1 - (kGroup - 1)) < tlast || k1 < kGroup - 1)) {
-                float ar[kGroup][NP], dxs[kGroup][NP], dys[kGroup][NP];
+                float ar[kGroup][NP], ex[kGroup][NP], dxs[kGroup][NP], dys[kGroup][NP];
                 bool ok[kGroup][NP];
 #pragma unroll
                 for (int u = 0; u < kGroup; ++u) {
                     const int k = k1 - u;
                     const float4 a = s0[k < 0 ? 0 : k];
                     const float4 q = s1[k < 0 ? 0 : k];
+                    float pw[NP];
+                    if constexpr (PX == 2) {
+                        // the two pixels of a row as packed FP32 pairs
+#pragma unroll
+                        for (int b = 0; b < PY; ++b) {
+                            const float dy = __fsub_rn(a.y, pyc[b]);
+                            const float2 dx2 = __fadd2_rn(make_float2(a.x, a.x), npx2); // = a.x - pxc
+                            const float2 p2 = gauss_power2(q.x, q.y, q.z, dx2, dy);
+                            dxs[u][2 * b] = dx2.x;
+                            dxs[u][2 * b + 1] = dx2.y;
+                            dys[u][2 * b] = dys[u][2 * b + 1] = dy;
+                            pw[2 * b] = p2.x;
+                            pw[2 * b + 1] = p2.y;
+                        }
+                    } else {
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) {
+                            dxs[u][p] = __fsub_rn(a.x, pxc[p % PX]);
+                            dys[u][p] = __fsub_rn(a.y, pyc[p / PX]);
+                            pw[p] = gauss_power(q.x, q.y, q.z, dxs[u][p], dys[u][p]);
+                        }
+                    }
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
-                        const float dx = __fsub_rn(a.x, pxc[p % PX]), dy = __fsub_rn(a.y, pyc[p / PX]);
-                        const float power = gauss_power(q.x, q.y, q.z, dx, dy);
-                        ar[u][p] = raw_alpha(q.w, power);
-                        dxs[u][p] = dx;
-                        dys[u][p] = dy;
-                        ok[u][p] = k >= 0 && (uint32_t)(lo + k) < last[p] && fmaxf(fabsf(dx), fabsf(dy)) <= a.w &&
-                                   power <= 0.0f && fminf(kAlphaMax, ar[u][p]) >= kAlphaMin;
+                        ex[u][p] = __expf(pw[p]);
+                        ar[u][p] = __fmul_rn(q.w, ex[u][p]); // = raw_alpha(q.w, power)
+                        ok[u][p] = k >= 0 && (uint32_t)(lo + k) < last[p] &&
+                                   fmaxf(fabsf(dxs[u][p]), fabsf(dys[u][p])) <= a.w && pw[p] <= 0.0f &&
+                                   fminf(kAlphaMax, ar[u][p]) >= kAlphaMin;
                     }
                 }
 #pragma unroll
@@ -258,14 +279,14 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
                             contrib = true;
                             const float alpha = fminf(kAlphaMax, ar[u][p]);
                             const float om = 1.0f - alpha;
-                            const float Ti = T[p] / om;
+                            const float iom = __fdividef(1.0f, om); // om in [0.01, 1): fast reciprocal
+                            const float Ti = T[p] * iom;
                             const float wgt = alpha * Ti;
                             float *gu = g + 10 * u;
                             gu[6] += wgt * dC0[p];
                             gu[7] += wgt * dC1[p];
                             gu[8] += wgt * dC2[p];
                             gu[9] += wgt * dD[p];
-                            const float iom = 1.0f / om;
                             const float dal = dC0[p] * (c.x * Ti - S0[p] * iom) + dC1[p] * (c.y * Ti - S1[p] * iom) +
                                               dC2[p] * (c.z * Ti - S2[p] * iom) + dD[p] * (a.z * Ti - SD[p] * iom);
                             S0[p] += c.x * wgt;
@@ -275,8 +296,7 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
                             T[p] = Ti;
                             if (ar[u][p] < kAlphaMax) {
                                 const float dx = dxs[u][p], dy = dys[u][p];
-                                const float G = ar[u][p] / q.w;
-                                gu[5] += dal * G;
+                                gu[5] += dal * ex[u][p]; // d alpha / d opacity = exp(power)
                                 const float gp = dal * alpha;
                                 gu[0] += -gp * (q.x * dx + q.y * dy);
                                 gu[1] += -gp * (q.z * dy + q.y * dx);

@@ -615,6 +615,7 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
     for (int a = 0; a < PX; ++a) pxc[a] = pix_c(i0 + a, cam.cx);
 #pragma unroll
     for (int b = 0; b < PY; ++b) pyc[b] = pix_c(j0 + b, cam.cy);
+    const float2 npx2 = make_float2(-pxc[0], -pxc[PX - 1]);
     uint32_t start, n;
     bin_range(w, bin, start, n);
     const unsigned long long *keys = w.keys + start;
@@ -700,13 +701,32 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
                 for (int u = 0; u < kUnroll; ++u) {
                     const float4 a = s0[k0 + u]; // B is a multiple of kUnroll: stays in the buffer
                     const float4 q = s1[k0 + u];
+                    if constexpr (PX == 2) {
+                        // the two pixels of a row as packed FP32 pairs
 #pragma unroll
-                    for (int p = 0; p < NP; ++p) {
-                        const float dx = __fsub_rn(a.x, pxc[p % PX]), dy = __fsub_rn(a.y, pyc[p / PX]);
-                        cv[u][p] = (k0 + u < cnt) && fmaxf(fabsf(dx), fabsf(dy)) <= a.w;
-                        const float power = gauss_power(q.x, q.y, q.z, dx, dy);
-                        al[u][p] = fminf(kAlphaMax, raw_alpha(q.w, power));
-                        ok[u][p] = cv[u][p] && power <= 0.0f && al[u][p] >= kAlphaMin;
+                        for (int b = 0; b < PY; ++b) {
+                            const float dy = __fsub_rn(a.y, pyc[b]);
+                            const float2 dx2 = __fadd2_rn(make_float2(a.x, a.x), npx2); // = a.x - pxc
+                            const float2 pw = gauss_power2(q.x, q.y, q.z, dx2, dy);
+                            const float2 ar = __fmul2_rn(make_float2(q.w, q.w), make_float2(__expf(pw.x), __expf(pw.y)));
+                            const float dxs[2] = {dx2.x, dx2.y}, pws[2] = {pw.x, pw.y}, ars[2] = {ar.x, ar.y};
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const int p = 2 * b + h;
+                                cv[u][p] = (k0 + u < cnt) && fmaxf(fabsf(dxs[h]), fabsf(dy)) <= a.w;
+                                al[u][p] = fminf(kAlphaMax, ars[h]);
+                                ok[u][p] = cv[u][p] && pws[h] <= 0.0f && al[u][p] >= kAlphaMin;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) {
+                            const float dx = __fsub_rn(a.x, pxc[p % PX]), dy = __fsub_rn(a.y, pyc[p / PX]);
+                            cv[u][p] = (k0 + u < cnt) && fmaxf(fabsf(dx), fabsf(dy)) <= a.w;
+                            const float power = gauss_power(q.x, q.y, q.z, dx, dy);
+                            al[u][p] = fminf(kAlphaMax, raw_alpha(q.w, power));
+                            ok[u][p] = cv[u][p] && power <= 0.0f && al[u][p] >= kAlphaMin;
+                        }
                     }
                 }
 #pragma unroll

@@ -160,6 +160,17 @@ __device__ __forceinline__ float gauss_power(float A, float B, float C, float dx
     return __fmaf_rn(-0.5f, q, -__fmul_rn(B, __fmul_rn(dx, dy)));
 }
 
+// gauss_power for two pixels of one row at once, with packed FP32 pairs
+// (sm_100+): the same operations in the same order, so each element is
+// bit-identical to gauss_power(A, B, C, dx2.{x,y}, dy).
+__device__ __forceinline__ float2 gauss_power2(float A, float B, float C, float2 dx2, float dy)
+{
+    const float cdy = __fmul_rn(C, __fmul_rn(dy, dy));
+    const float2 q = __ffma2_rn(make_float2(A, A), __fmul2_rn(dx2, dx2), make_float2(cdy, cdy));
+    const float2 nb = __fmul2_rn(make_float2(-B, -B), __fmul2_rn(dx2, make_float2(dy, dy))); // = -(B (dx dy))
+    return __ffma2_rn(make_float2(-0.5f, -0.5f), q, nb);
+}
+
 // cp.async gathers (16 bytes each) into shared memory
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {

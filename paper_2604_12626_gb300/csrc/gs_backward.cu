@@ -373,47 +373,6 @@ __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, 
 // ---------------------------------------------------------------------------
 // preprocess backward
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int find_env_b(const Table *tb, int64_t g)
-{
-    int lo = 0, hi = tb->n_envs - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (tb->env_off[mid] <= g) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-template <int SHT>
-__device__ __forceinline__ void load_sh_b(const void *sh, int64_t g, float (&k)[48])
-{
-    if (SHT == GS_SH_F32) {
-        const float4 *p = reinterpret_cast<const float4 *>(sh) + g * 12;
-#pragma unroll
-        for (int i = 0; i < 12; ++i) {
-            const float4 v = __ldg(p + i);
-            k[4 * i] = v.x; k[4 * i + 1] = v.y; k[4 * i + 2] = v.z; k[4 * i + 3] = v.w;
-        }
-    } else {
-        const uint4 *p = reinterpret_cast<const uint4 *>(sh) + g * 6;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            const uint4 v = __ldg(p + i);
-            const uint32_t u[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (SHT == GS_SH_F16) {
-                    const __half2 h = *reinterpret_cast<const __half2 *>(&u[j]);
-                    const float2 f = __half22float2(h);
-                    k[8 * i + 2 * j] = f.x; k[8 * i + 2 * j + 1] = f.y;
-                } else {
-                    k[8 * i + 2 * j] = __uint_as_float(u[j] << 16);
-                    k[8 * i + 2 * j + 1] = __uint_as_float(u[j] & 0xffff0000u);
-                }
-            }
-        }
-    }
-}
 
 // dL/d(dir) += sum_k grad(Y_k) * w_k for the degree-3 basis.
 __device__ __forceinline__ void sh_dir_vjp(float x, float y, float z, const float (&wk)[16], float &gx, float &gy,
@@ -489,22 +448,23 @@ __device__ __forceinline__ void sh_weighted(const void *sh, int64_t g, const flo
 // gradients of each visible view back to the Gaussian's parameters.
 template <int SHT, bool OVERWRITE>
 __device__ __forceinline__ void gaussian_backward(const gs_camera *__restrict__ cams, const GaussInB &gin, const Ws &w,
-                                                  const GradOut &o, int64_t g)
+                                                  const GradOut &o, int64_t g, int e)
 {
     const Table *tb = w.tb;
-    const int e = find_env_b(tb, g);
     const int vb = tb->env_view_begin[e], ve = tb->env_view_begin[e + 1];
     const int64_t local = g - tb->env_off[e];
     const bool use_cov = gin.cov3d != nullptr && g >= tb->env_cov_begin[e];
     const float mx = __ldg(gin.means + 3 * g), my = __ldg(gin.means + 3 * g + 1), mz = __ldg(gin.means + 3 * g + 2);
     float S[6];
+    float3 ls = make_float3(0.f, 0.f, 0.f);
+    float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
     if (use_cov) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) S[i] = __ldg(gin.cov3d + 6 * g + i);
     } else {
-        const float3 ls = make_float3(__ldg(gin.log_scales + 3 * g), __ldg(gin.log_scales + 3 * g + 1),
-                                      __ldg(gin.log_scales + 3 * g + 2));
-        const float4 q = __ldg(reinterpret_cast<const float4 *>(gin.quats) + g);
+        ls = make_float3(__ldg(gin.log_scales + 3 * g), __ldg(gin.log_scales + 3 * g + 1),
+                         __ldg(gin.log_scales + 3 * g + 2));
+        q = __ldg(reinterpret_cast<const float4 *>(gin.quats) + g);
         sigma_from_sq(ls, q, S);
     }
     const float op = 1.0f / (1.0f + expf(-__ldg(gin.ologits + g)));
@@ -629,9 +589,6 @@ __device__ __forceinline__ void gaussian_backward(const gs_camera *__restrict__ 
         return;
     }
     // Sigma = M M^T, M = R diag(s): dL/dM = 2 gS M
-    const float3 ls = make_float3(__ldg(gin.log_scales + 3 * g), __ldg(gin.log_scales + 3 * g + 1),
-                                  __ldg(gin.log_scales + 3 * g + 2));
-    const float4 q = __ldg(reinterpret_cast<const float4 *>(gin.quats) + g);
     const float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w), iq = 1.0f / qn;
     const float qw = q.x * iq, qx = q.y * iq, qy = q.z * iq, qz = q.w * iq;
     float R[9];
@@ -759,10 +716,11 @@ __global__ void __launch_bounds__(256, 2) preprocess_backward_kernel(const gs_ca
             const int64_t gg = g0 + q[(head + lane) & (kBwdWarpQ - 1)];
             head += 32;
             __syncwarp();
-            gaussian_backward<SHT, OVERWRITE>(cams, gin, w, o, gg);
+            gaussian_backward<SHT, OVERWRITE>(cams, gin, w, o, gg, lo);
         }
     }
-    if (lane < tail - head) gaussian_backward<SHT, OVERWRITE>(cams, gin, w, o, g0 + q[(head + lane) & (kBwdWarpQ - 1)]);
+    if (lane < tail - head)
+        gaussian_backward<SHT, OVERWRITE>(cams, gin, w, o, g0 + q[(head + lane) & (kBwdWarpQ - 1)], lo);
 }
 
 // ---------------------------------------------------------------------------

@@ -115,6 +115,12 @@ def _bind(L):
     L.or_sh_basis.argtypes = [i64, P, P]
     L.or_quat_to_rot.restype = None
     L.or_quat_to_rot.argtypes = [P, P]
+    L.or_composite_nearest.restype = None
+    L.or_composite_nearest.argtypes = [i64, i64, P, P, P, P, P, P]
+    L.or_forward_kinematics.restype = None
+    L.or_forward_kinematics.argtypes = [i32, i32, P, P, P, P, P]
+    L.or_interpolate_frames.restype = None
+    L.or_interpolate_frames.argtypes = [i32, i32, i32, P, P, P]
     return L
 
 
@@ -253,6 +259,40 @@ def lbs_backward(means_c, log_scales_c, quats_c, joint_ids, weights, avatar_of, 
     L.or_lbs_backward(m, _p(means_c), _p(_f64(log_scales_c)), _p(_f64(quats_c)), _p(ids), _p(_f64(weights)),
                       _p(av), _p(G), nj, _p(_f64(g_means)), _p(_f64(g_cov)), _p(out["means"]),
                       _p(out["log_scales"]), _p(out["quats"]), _p(out["G"]))
+    return out
+
+
+def composite_nearest(rgb_a, depth_a, rgb_b, depth_b):
+    """Nearest-fragment composite of two layers: rgb [V,3,H,W], depth [V,H,W]."""
+    L = _lib()
+    da, db = _f64(depth_a), _f64(depth_b)
+    V = da.shape[0] if da.ndim == 3 else 1
+    hw = da.size // V
+    rgb = np.zeros((V, 3) + da.shape[-2:])
+    dep = np.zeros((V,) + da.shape[-2:])
+    L.or_composite_nearest(V, hw, _p(_f64(rgb_a)), _p(da), _p(_f64(rgb_b)), _p(db), _p(rgb), _p(dep))
+    return rgb, dep
+
+
+def forward_kinematics(local_rot, root, rest, parents):
+    """Skinning matrices [A,J,3,4] from local rotations [A,J,3,3], root [A,3,4],
+    rest joints [J,3] and parents [J]."""
+    L = _lib()
+    lr = _f64(local_rot)
+    A, J = lr.shape[0], lr.shape[1]
+    out = np.zeros((A, J, 3, 4))
+    par = np.ascontiguousarray(np.asarray(parents, np.int32).reshape(J))
+    L.or_forward_kinematics(A, J, _p(lr), _p(_f64(root)), _p(_f64(rest)), _p(par), _p(out))
+    return out
+
+
+def interpolate_frames(frames, t):
+    """Joint matrices [A,J,3,4] at fractional frame positions t [A] from frames [A,F,J,3,4]."""
+    L = _lib()
+    fr = _f64(frames)
+    A, F, J = fr.shape[0], fr.shape[1], fr.shape[2]
+    out = np.zeros((A, J, 3, 4))
+    L.or_interpolate_frames(A, F, J, _p(fr), _p(_f64(np.asarray(t, np.float64).reshape(A))), _p(out))
     return out
 
 

@@ -912,4 +912,108 @@ void or_lbs_backward(int64_t m, const double *means_c, const double *log_scales_
     }
 }
 
+/* ------------------------------------------------------------------------
+ * Nearest-fragment composite (Sec. 3.2, the full-screen pass that merges the
+ * 3DGS colour/depth with another layer -- the mesh pass, or the avatars'
+ * Gaussian pass): per pixel (C, D) = (D_a < D_b) ? (C_a, D_a) : (C_b, D_b).
+ * Reading: a depth that is not a positive finite number marks a pixel the
+ * layer does not cover and compares as +infinity, so the formula's else branch
+ * also decides when neither layer covers the pixel.
+ * rgb [V,3,H,W], depth [V,H,W].
+ * ------------------------------------------------------------------------ */
+static double layer_depth(double d) { return (d > 0.0 && d <= DBL_MAX) ? d : INFINITY; }
+
+void or_composite_nearest(int64_t n_views, int64_t hw, const double *rgb_a, const double *depth_a, const double *rgb_b,
+                          const double *depth_b, double *rgb_out, double *depth_out)
+{
+    for (int64_t v = 0; v < n_views; ++v)
+        for (int64_t p = 0; p < hw; ++p) {
+            const int64_t i = v * hw + p;
+            const int take_a = layer_depth(depth_a[i]) < layer_depth(depth_b[i]);
+            depth_out[i] = take_a ? depth_a[i] : depth_b[i];
+            for (int c = 0; c < 3; ++c) {
+                const int64_t k = (3 * v + c) * hw + p;
+                rgb_out[k] = take_a ? rgb_a[k] : rgb_b[k];
+            }
+        }
+}
+
+/* ------------------------------------------------------------------------
+ * Forward kinematics of a joint tree (the per-frame joint matrices the
+ * avatar module feeds to LBS, Sec. 3.3.1): for avatar a,
+ *   G_0 = [R_root R_0 | t_root],  G_j = G_parent(j) [R_j | J_j - J_parent(j)],
+ *   M_j = G_j [I | -J_j]   (the skinning matrix of joint j, 3x4 row-major),
+ * with J the rest-pose joint positions and parent(j) < j.
+ *   local_rot [A,J,3,3], root [A,3,4] (R_root | t_root), rest [J,3],
+ *   parents [J] (parents[0] ignored) -> out [A,J,3,4].
+ * ------------------------------------------------------------------------ */
+static void mat3_mul(const double *a, const double *b, double *o)
+{
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) o[3 * r + c] = a[3 * r] * b[c] + a[3 * r + 1] * b[3 + c] + a[3 * r + 2] * b[6 + c];
+}
+
+void or_forward_kinematics(int32_t n_avatars, int32_t n_joints, const double *local_rot, const double *root,
+                           const double *rest, const int32_t *parents, double *out)
+{
+    double *GR = (double *)malloc((size_t)n_joints * 9 * sizeof(double));
+    double *Gt = (double *)malloc((size_t)n_joints * 3 * sizeof(double));
+    for (int32_t a = 0; a < n_avatars; ++a) {
+        const double *Rl = local_rot + (int64_t)a * n_joints * 9;
+        const double *rt = root + 12 * a;
+        const double Rr[9] = {rt[0], rt[1], rt[2], rt[4], rt[5], rt[6], rt[8], rt[9], rt[10]};
+        mat3_mul(Rr, Rl, GR);
+        Gt[0] = rt[3]; Gt[1] = rt[7]; Gt[2] = rt[11];
+        for (int32_t j = 1; j < n_joints; ++j) {
+            const int32_t p = parents[j];
+            mat3_mul(GR + 9 * p, Rl + 9 * j, GR + 9 * j);
+            for (int r = 0; r < 3; ++r) {
+                double acc = Gt[3 * p + r];
+                for (int c = 0; c < 3; ++c) acc += GR[9 * p + 3 * r + c] * (rest[3 * j + c] - rest[3 * p + c]);
+                Gt[3 * j + r] = acc;
+            }
+        }
+        for (int32_t j = 0; j < n_joints; ++j) {
+            double *M = out + ((int64_t)a * n_joints + j) * 12;
+            for (int r = 0; r < 3; ++r) {
+                double t = Gt[3 * j + r];
+                for (int c = 0; c < 3; ++c) {
+                    M[4 * r + c] = GR[9 * j + 3 * r + c];
+                    t -= GR[9 * j + 3 * r + c] * rest[3 * j + c];
+                }
+                M[4 * r + 3] = t;
+            }
+        }
+    }
+    free(GR);
+    free(Gt);
+}
+
+/* ------------------------------------------------------------------------
+ * Joint matrices at simulation time (Sec. 3.3.1: the per-frame matrices are
+ * interpolated at the current time).  Reading: linear interpolation of the
+ * 3x4 matrices of the two frames around the fractional frame position t,
+ *   f = clamp(floor(t), 0, F-1), w = clamp(t - f, 0, 1), g = min(f+1, F-1),
+ *   M(t) = (1 - w) M_f + w M_g   -- LBS itself blends matrices linearly.
+ * frames [A,F,J,12], t [A] -> out [A,J,12].
+ * ------------------------------------------------------------------------ */
+void or_interpolate_frames(int32_t n_avatars, int32_t n_frames, int32_t n_joints, const double *frames, const double *t,
+                           double *out)
+{
+    for (int32_t a = 0; a < n_avatars; ++a) {
+        double tf = t[a];
+        double f = floor(tf);
+        if (!(f >= 0.0)) f = 0.0;
+        if (f > n_frames - 1) f = n_frames - 1;
+        double w = tf - f;
+        if (!(w >= 0.0)) w = 0.0;
+        if (w > 1.0) w = 1.0;
+        const int32_t f0 = (int32_t)f, f1 = f0 + 1 < n_frames ? f0 + 1 : n_frames - 1;
+        const double *A0 = frames + ((int64_t)a * n_frames + f0) * n_joints * 12;
+        const double *A1 = frames + ((int64_t)a * n_frames + f1) * n_joints * 12;
+        double *o = out + (int64_t)a * n_joints * 12;
+        for (int32_t e = 0; e < n_joints * 12; ++e) o[e] = (1.0 - w) * A0[e] + w * A1[e];
+    }
+}
+
 int32_t or_abi_version(void) { return 1; }

@@ -6,6 +6,7 @@ import pytest
 import oracle as _oracle
 import test_oracle_adjoint as adj
 import test_oracle_pins as pins
+import test_oracle_pins_drive as drive
 
 MUTANTS = [
     ("dropped dilation", "#define DILATION 0.3", "#define DILATION 0.0",
@@ -48,6 +49,20 @@ MUTANTS = [
      adj.test_adjoint_matches_finite_differences),
     ("adjoint: clamp passes gradient", "if (a_raw < ALPHA_MAX) {\n                    q->go", "if (1) {\n                    q->go",
      adj.test_adjoint_matches_finite_differences),
+    ("composite keeps the farther fragment",
+     "const int take_a = layer_depth(depth_a[i]) < layer_depth(depth_b[i]);",
+     "const int take_a = layer_depth(depth_a[i]) > layer_depth(depth_b[i]);", drive.test_composite_picks_the_nearer_fragment),
+    ("composite: empty layer compares as depth 0", "return (d > 0.0 && d <= DBL_MAX) ? d : INFINITY;", "return d;",
+     drive.test_composite_picks_the_nearer_fragment),
+    ("FK: child offset from the rest joint instead of the bone",
+     "acc += GR[9 * p + 3 * r + c] * (rest[3 * j + c] - rest[3 * p + c]);", "acc += GR[9 * p + 3 * r + c] * rest[3 * j + c];",
+     drive.test_fk_rigid_invariants),
+    ("FK: local rotation applied before the parent's", "mat3_mul(GR + 9 * p, Rl + 9 * j, GR + 9 * j);",
+     "mat3_mul(Rl + 9 * j, GR + 9 * p, GR + 9 * j);", drive.test_fk_root_equivariance),
+    ("FK: skinning matrix without the rest offset", "t -= GR[9 * j + 3 * r + c] * rest[3 * j + c];", "",
+     drive.test_fk_zero_pose_is_identity),
+    ("interpolation weights swapped", "o[e] = (1.0 - w) * A0[e] + w * A1[e];", "o[e] = w * A0[e] + (1.0 - w) * A1[e];",
+     drive.test_interpolation_between_frames),
     ("adjoint: LBS covariance factor", "gA[4 * r + cc] = gm[r] * mu[cc] + 2.0 * acc;",
      "gA[4 * r + cc] = gm[r] * mu[cc] + acc;", adj.test_lbs_adjoint_matches_finite_differences),
 ]

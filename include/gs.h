@@ -215,6 +215,45 @@ gs_status gs_deform_avatars_backward(const gs_avatars *av, const float *joint_G,
                                      const float *d_cov3d, float *d_canon_means, float *d_canon_log_scales,
                                      float *d_canon_quats, float *d_joint_G, void *stream);
 
+/* Nearest-fragment composite of two RGB-D layers (Sec. 3.2: the full-screen
+ * pass that merges the 3DGS colour and depth with the mesh pass, and the
+ * avatars' Gaussian pass with the scene's).  Per pixel
+ *   (C, D) = (D_a < D_b) ? (C_a, D_a) : (C_b, D_b),
+ * where a depth that is not a positive finite number -- a pixel the layer
+ * does not cover, e.g. gs_render's normalised depth 0 -- compares as
+ * +infinity (so the second layer is kept when neither covers the pixel).
+ *   rgb_a, rgb_b, rgb_out        device [V,3,H,W] float32
+ *   depth_a, depth_b, depth_out  device [V,H,W] float32
+ * All 16-byte aligned; the outputs may alias either input (element-wise).
+ * For a Gaussian layer pass gs_render's depth under GS_FLAG_NORMALIZE_DEPTH. */
+gs_status gs_composite_nearest(const float *rgb_a, const float *depth_a, const float *rgb_b, const float *depth_b,
+                               int32_t n_views, int32_t height, int32_t width, float *rgb_out, float *depth_out,
+                               void *stream);
+
+/* Skinning matrices of A avatars by forward kinematics of one joint tree
+ * (Sec. 3.3.1: the per-frame SMPL-X joint matrices that drive the LBS kernel):
+ *   G_0 = [R_root R_0 | t_root],  G_j = G_parent(j) [R_j | J_j - J_parent(j)],
+ *   M_j = G_j [I | -J_j]   (3x4 row-major, the joint_G of gs_deform_avatars)
+ *   local_rot     device [A,J,3,3]  local joint rotations R_j
+ *   root          device [A,3,4]    [R_root | t_root]
+ *   rest          device [J,3]      rest-pose joint positions J_j
+ *   parents_host  HOST [J] int32    parent of each joint, parents[j] < j for
+ *                                   j > 0 (parents[0] is ignored)
+ *   out           device [A,J,3,4]
+ * 1 <= J <= 64; GS_ERR_INVALID_ARG for a parent that is not below its child. */
+gs_status gs_forward_kinematics(const float *local_rot, const float *root, const float *rest,
+                                const int32_t *parents_host, int32_t n_avatars, int32_t n_joints, float *out,
+                                void *stream);
+
+/* Joint matrices at the current simulation time (Sec. 3.3.1: the per-frame
+ * matrices are interpolated at the simulation time).  For avatar a at the
+ * fractional frame position t[a]: f = clamp(floor(t), 0, F-1),
+ * w = clamp(t - f, 0, 1), out = (1 - w) M[f] + w M[min(f+1, F-1)] -- linear in
+ * the matrices, as LBS itself blends them.
+ *   frames  device [A,F,J,3,4], t device [A] float32, out device [A,J,3,4] */
+gs_status gs_interpolate_joints(const float *frames, const float *t, int32_t n_avatars, int32_t n_frames,
+                                int32_t n_joints, float *out, void *stream);
+
 /* Synchronises `stream`, returns the device status of the workspace (set by
  * the last gs_render and any gs_render_backward after it) in *device_status
  * (GS_OK or GS_ERR_CAPACITY) and clears it. */

@@ -78,6 +78,9 @@ _lib.gs_render.argtypes = [_R(GsGaussians), _R(GsBatch), _P, _R(GsRenderConfig),
 _lib.gs_render_backward.argtypes = [_R(GsGaussians), _R(GsBatch), _P, _R(GsRenderConfig), _P, ctypes.c_size_t, _P, _P,
                                     _P, _P, _P, _P, _P, _P, _P]
 _lib.gs_deform_avatars.argtypes = [_R(GsAvatars), _P, _P, _P, _P]
+_lib.gs_composite_nearest.argtypes = [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]
+_lib.gs_forward_kinematics.argtypes = [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]
+_lib.gs_interpolate_joints.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P]
 _lib.gs_deform_avatars_backward.argtypes = [_R(GsAvatars), _P, _P, _P, _P, _P, _P, _P, _P]
 _lib.gs_get_status.argtypes = [_P, ctypes.c_size_t, _P, _R(ctypes.c_int32)]
 _lib.gs_render_stats.argtypes = [_P, ctypes.c_size_t, _P, _R(GsStats)]
@@ -95,7 +98,7 @@ _lib.gs_version.restype = ctypes.c_int32
 
 EXPORTS = ("gs_render_static", "gs_profile_enable", "gs_profile_read", "gs_workspace_sections", "gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_deform_avatars",
            "gs_deform_avatars_backward", "gs_get_status", "gs_render_stats", "gs_autotune", "gs_last_cuda_error",
-           "gs_version")
+           "gs_version", "gs_composite_nearest", "gs_forward_kinematics", "gs_interpolate_joints")
 
 
 class GsError(RuntimeError):
@@ -407,6 +410,44 @@ def deform_backward(av: Avatars, G, d_means, d_cov3d, grads, stream=None):
                                            _ptr(grads["means"]), _ptr(grads["log_scales"]), _ptr(grads["quats"]),
                                            _ptr(grads["G"]), _stream(stream)), "gs_deform_avatars_backward")
     return grads
+
+
+def composite_nearest(rgb_a, depth_a, rgb_b, depth_b, out=None, stream=None):
+    """Per pixel the nearer of two RGB-D layers (gs_composite_nearest).
+    rgb [V,3,H,W], depth [V,H,W] float32 CUDA tensors; returns (rgb, depth)."""
+    V, _, H, W = rgb_a.shape
+    for t, shp in ((rgb_a, (V, 3, H, W)), (rgb_b, (V, 3, H, W)), (depth_a, (V, H, W)), (depth_b, (V, H, W))):
+        if tuple(t.shape) != shp or t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+            raise GsError("composite_nearest: contiguous float32 CUDA tensors [V,3,H,W] and [V,H,W] expected")
+    if out is None:
+        out = (torch.empty_like(rgb_a), torch.empty_like(depth_a))
+    _check(_lib.gs_composite_nearest(_ptr(rgb_a), _ptr(depth_a), _ptr(rgb_b), _ptr(depth_b), V, H, W, _ptr(out[0]),
+                                     _ptr(out[1]), _stream(stream)), "gs_composite_nearest")
+    return out
+
+
+def forward_kinematics(local_rot, root, rest, parents, out=None, stream=None):
+    """Skinning matrices [A,J,3,4] (gs_forward_kinematics) from local rotations
+    [A,J,3,3], root [A,3,4] and rest joints [J,3] (CUDA float32) and the parent
+    of each joint (host sequence)."""
+    A, J = local_rot.shape[0], local_rot.shape[1]
+    par = np.ascontiguousarray(np.asarray(parents, np.int32).reshape(J))
+    if out is None:
+        out = torch.empty((A, J, 3, 4), dtype=torch.float32, device=local_rot.device)
+    _check(_lib.gs_forward_kinematics(_ptr(local_rot), _ptr(root), _ptr(rest), par.ctypes.data_as(_P), A, J,
+                                      _ptr(out), _stream(stream)), "gs_forward_kinematics")
+    return out
+
+
+def interpolate_joints(frames, t, out=None, stream=None):
+    """Joint matrices [A,J,3,4] at fractional frame positions t [A] from
+    per-frame matrices [A,F,J,3,4] (gs_interpolate_joints)."""
+    A, F, J = frames.shape[0], frames.shape[1], frames.shape[2]
+    if out is None:
+        out = torch.empty((A, J, 3, 4), dtype=torch.float32, device=frames.device)
+    _check(_lib.gs_interpolate_joints(_ptr(frames), _ptr(t), A, F, J, _ptr(out), _stream(stream)),
+           "gs_interpolate_joints")
+    return out
 
 
 class RenderFunction(torch.autograd.Function):

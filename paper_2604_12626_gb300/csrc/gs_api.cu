@@ -433,6 +433,62 @@ gs_status gs_deform_avatars(const gs_avatars *av, const float *joint_G, float *o
     return check_launch();
 }
 
+gs_status gs_composite_nearest(const float *rgb_a, const float *depth_a, const float *rgb_b, const float *depth_b,
+                               int32_t n_views, int32_t height, int32_t width, float *rgb_out, float *depth_out,
+                               void *stream)
+{
+    if (!rgb_a || !depth_a || !rgb_b || !depth_b || !rgb_out || !depth_out) return GS_ERR_INVALID_ARG;
+    if (n_views < 0 || height < 0 || width < 0) return GS_ERR_INVALID_ARG;
+    const void *ptrs[] = {rgb_a, depth_a, rgb_b, depth_b, rgb_out, depth_out};
+    for (const void *q : ptrs)
+        if (!aligned16(q)) return GS_ERR_ALIGNMENT;
+    if ((int64_t)n_views * height * width == 0) return GS_OK;
+    int sms = 0;
+    gs_status st = device_init(&sms);
+    if (st != GS_OK) return st;
+    launch_composite(rgb_a, depth_a, rgb_b, depth_b, rgb_out, depth_out, n_views, (int64_t)height * width, sms,
+                     static_cast<cudaStream_t>(stream));
+    return check_launch();
+}
+
+gs_status gs_forward_kinematics(const float *local_rot, const float *root, const float *rest,
+                                const int32_t *parents_host, int32_t n_avatars, int32_t n_joints, float *out,
+                                void *stream)
+{
+    if (!local_rot || !root || !rest || !parents_host || !out) return GS_ERR_INVALID_ARG;
+    if (n_avatars < 0 || n_joints < 1 || n_joints > kMaxJoints) return GS_ERR_INVALID_ARG;
+    JointTree tree;
+    std::memset(&tree, 0, sizeof(tree));
+    tree.n = n_joints;
+    tree.parent[0] = -1;
+    for (int j = 1; j < n_joints; ++j) {
+        const int32_t p = parents_host[j];
+        if (p < 0 || p >= j) return GS_ERR_INVALID_ARG;
+        tree.parent[j] = (int8_t)p;
+        tree.depth[j] = (int8_t)(tree.depth[p] + 1);
+        if (tree.depth[j] > tree.max_depth) tree.max_depth = tree.depth[j];
+    }
+    if (n_avatars == 0) return GS_OK;
+    int sms = 0;
+    gs_status st = device_init(&sms);
+    if (st != GS_OK) return st;
+    launch_fk(local_rot, root, rest, tree, n_avatars, out, static_cast<cudaStream_t>(stream));
+    return check_launch();
+}
+
+gs_status gs_interpolate_joints(const float *frames, const float *t, int32_t n_avatars, int32_t n_frames,
+                                int32_t n_joints, float *out, void *stream)
+{
+    if (!frames || !t || !out) return GS_ERR_INVALID_ARG;
+    if (n_avatars < 0 || n_frames < 1 || n_joints < 1 || n_joints > kMaxJoints) return GS_ERR_INVALID_ARG;
+    if (n_avatars == 0) return GS_OK;
+    int sms = 0;
+    gs_status st = device_init(&sms);
+    if (st != GS_OK) return st;
+    launch_interp(frames, t, n_avatars, n_frames, n_joints, out, sms, static_cast<cudaStream_t>(stream));
+    return check_launch();
+}
+
 gs_status gs_deform_avatars_backward(const gs_avatars *av, const float *joint_G, const float *d_means,
                                      const float *d_cov3d, float *d_canon_means, float *d_canon_log_scales,
                                      float *d_canon_quats, float *d_joint_G, void *stream)

@@ -14,7 +14,6 @@
 
 namespace gs {
 
-constexpr int kMaxJoints = 64;
 
 struct AvIn {
     const float *means, *log_scales, *quats, *weights;

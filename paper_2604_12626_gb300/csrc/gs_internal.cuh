@@ -30,6 +30,14 @@ constexpr float kAlphaMax = 0.99f;
 constexpr float kTStop = 1e-4f;
 constexpr float kDilation = 0.3f;
 constexpr int kSortChunk = 4096; // keys one CTA sorts; larger bins are merged
+constexpr int kMaxJoints = 64;    // joints of one avatar tree
+
+// A joint tree passed by value: parent and depth of every joint (parent < child).
+struct JointTree {
+    int32_t n, max_depth;
+    int8_t parent[kMaxJoints];
+    int8_t depth[kMaxJoints];
+};
 
 struct Header {
     int32_t status;     // sticky GS_ERR_* (0 = ok)

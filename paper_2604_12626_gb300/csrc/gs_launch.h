@@ -39,6 +39,13 @@ void launch_deform(const gs_avatars *av, const float *G, float *out_means, float
 void launch_deform_backward(const gs_avatars *av, const float *G, const float *d_means, const float *d_cov,
                             float *d_cm, float *d_cls, float *d_cq, float *d_G, cudaStream_t s);
 
+void launch_composite(const float *rgb_a, const float *depth_a, const float *rgb_b, const float *depth_b,
+                      float *rgb_out, float *depth_out, int64_t n_views, int64_t hw, int n_sms, cudaStream_t s);
+void launch_fk(const float *local_rot, const float *root, const float *rest, const JointTree &tree, int n_avatars,
+               float *out, cudaStream_t s);
+void launch_interp(const float *frames, const float *t, int n_avatars, int n_frames, int n_joints, float *out,
+                   int n_sms, cudaStream_t s);
+
 // Records a CUDA error for gs_last_cuda_error and returns GS_ERR_CUDA.
 gs_status record_cuda_error(cudaError_t e);
 

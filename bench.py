@@ -299,6 +299,76 @@ def rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_pix, N, sm_count, sm_mh
     return roof, out
 
 
+def _event_ms(torch, stream, fn, reps=10):
+    with torch.cuda.stream(stream):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def avatar_and_composite_rows(api, synth, torch, dev, stream, outs, hbm_peak):
+    """CUDA-event times of the kernels outside the headline step: LBS deform
+    and its adjoint (100 B per avatar Gaussian forward), keyframe
+    interpolation + forward kinematics of 256 avatars, and the composite of two
+    64 x 256 x 256 RGB-D layers (48 B per pixel)."""
+    n_av, n_per, n_frames = 256, 50_000, 30
+    base = [synth.avatar_canonical(n_per, k) for k in range(8)]  # 8 distinct avatars, tiled over 32 envs
+    cat = {k: np.concatenate([base[a % 8][k] for a in range(n_av)]) for k in base[0]}
+    m = n_av * n_per
+    T = lambda x, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(x)).to(dev, dt)  # noqa: E731
+    av = api.Avatars(T(cat["means"]), T(cat["log_scales"]), T(cat["quats"]), T(cat["joint_ids"].view(np.int16),
+                     torch.int16), T(cat["weights"]), T(np.repeat(np.arange(n_av), n_per).astype(np.int32), torch.int32),
+                     n_av, synth.N_JOINTS)
+    del cat
+    rng = np.random.default_rng(7)
+    frames = T(np.stack([np.stack([synth.random_pose(17 * a + f % 4) for f in range(n_frames)])
+                         for a in range(n_av)]).astype(np.float32))
+    t = T(rng.uniform(0, n_frames - 1, n_av).astype(np.float32))
+    from scipy.spatial.transform import Rotation
+
+    local = T(Rotation.from_rotvec(rng.normal(0, 0.3, (n_av * synth.N_JOINTS, 3))).as_matrix()
+              .reshape(n_av, synth.N_JOINTS, 3, 3).astype(np.float32))
+    root = T(np.tile(np.hstack([np.eye(3), [[1.0], [2.0], [0.9]]]).astype(np.float32), (n_av, 1, 1)))
+    rest = T(synth.REST_JOINTS.astype(np.float32))
+    G = torch.empty((n_av, synth.N_JOINTS, 3, 4), device=dev)
+    om, oc = torch.empty((m, 3), device=dev), torch.empty((m, 6), device=dev)
+    gr = dict(means=torch.zeros((m, 3), device=dev), log_scales=torch.zeros((m, 3), device=dev),
+              quats=torch.zeros((m, 4), device=dev), G=torch.zeros_like(G))
+    interp_ms = _event_ms(torch, stream, lambda: api.interpolate_joints(frames, t, out=G, stream=stream))
+    fk_ms = _event_ms(torch, stream, lambda: api.forward_kinematics(local, root, rest, synth.PARENTS, out=G,
+                                                                   stream=stream))
+    deform_ms = _event_ms(torch, stream, lambda: api.deform(av, G, om, oc, stream=stream))
+    dmean, dcov = torch.ones_like(om), torch.ones_like(oc)
+    deform_bwd_ms = _event_ms(torch, stream, lambda: api.deform_backward(av, G, dmean, dcov, gr, stream=stream), 5)
+    fwd_bytes = 100 * m
+    bwd_bytes = m * (12 + 12 + 16 + 8 + 16 + 4 + 12 + 24 + 40)  # inputs, upstream grads, canonical grads (RMW excluded)
+    del av, om, oc, gr, dmean, dcov, frames
+    # composite of the bench frames with a second layer of the same shape
+    V, _, H, W = outs[0].shape
+    rgb_b = torch.rand_like(outs[0])
+    dep_b = torch.rand_like(outs[1]) * 8.0
+    rgb_o, dep_o = torch.empty_like(outs[0]), torch.empty_like(outs[1])
+    comp_ms = _event_ms(torch, stream, lambda: api.composite_nearest(outs[0], outs[1], rgb_b, dep_b,
+                                                                    out=(rgb_o, dep_o), stream=stream))
+    comp_bytes = 48 * V * H * W
+
+    def hbm(b, ms):
+        a = b / (ms * 1e-3) / 1e9
+        return {"ms": ms, "achieved_gbs": a, "frac": a / hbm_peak, "algorithmic_bytes": b}
+
+    return {"lbs_deform": dict(hbm(fwd_bytes, deform_ms), avatars=n_av, gaussians=m),
+            "lbs_deform_backward": dict(hbm(bwd_bytes, deform_bwd_ms), avatars=n_av, gaussians=m,
+                                        note="joint-gradient atomics per Gaussian and joint"),
+            "keyframe_interpolation": {"ms": interp_ms, "avatars": n_av, "frames": n_frames},
+            "forward_kinematics": {"ms": fk_ms, "avatars": n_av, "joints": synth.N_JOINTS},
+            "composite": dict(hbm(comp_bytes, comp_ms), views=V, width=W, height=H)}
+
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -468,6 +538,11 @@ def run_ours(args, ws, rank, local):
     roof, per_kernel = rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_envs * W * H, N, sm_count,
                                  (clocks or {}).get("sm_max_mhz"))
 
+    # --- the avatar rows (LBS, its adjoint, keyframes + FK) and the composite,
+    # timed on their own: 32 envs x 8 avatars x 50k Gaussians, and the
+    # nearest-fragment merge of the bench frames with a second layer
+    extra = avatar_and_composite_rows(api, synth, torch, dev, stream, outs, hbm_peak=peaks()[0])
+
     # --- CPU oracle on a bounded sample (rank 0, N = 1)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -495,6 +570,7 @@ def run_ours(args, ws, rank, local):
                            "batched_fwd_speedup": plain_ms / ms_fwd}),
         "roofline": roof,
         "roofline_per_kernel": per_kernel,
+        "other_rows": extra,
         "cpu_baseline": cpu,
         "e2e": {"value": total_envs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "what": "public API calls per step: cameras H2D from pinned memory, "

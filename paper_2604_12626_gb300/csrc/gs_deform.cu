@@ -81,21 +81,21 @@ __global__ void __launch_bounds__(256) deform_kernel(AvIn in, const float *__res
     oc[5] = AS[6] * A[8] + AS[7] * A[9] + AS[8] * A[10];
 }
 
+constexpr int kDeformWarps = 8; // 256 threads
+
 __global__ void __launch_bounds__(256) deform_backward_kernel(AvIn in, const float *__restrict__ G,
                                                               const float *__restrict__ d_means,
                                                               const float *__restrict__ d_cov, float *d_cm,
                                                               float *d_cls, float *d_cq, float *d_G)
 {
     __shared__ float sG[kMaxJoints * 12];
-    __shared__ float sdG[kMaxJoints * 12];
+    __shared__ float sdG[kDeformWarps][kMaxJoints * 12]; // one copy per warp: no atomics across warps
     const int64_t base = (int64_t)blockIdx.x * blockDim.x;
     const int64_t i = base + threadIdx.x;
     const int a0 = clamp_avatar(in.avatar_of[base], in.n_avatars);
     const int nj12 = in.n_joints * 12;
-    for (int k = threadIdx.x; k < nj12; k += blockDim.x) {
-        sG[k] = G[(size_t)a0 * nj12 + k];
-        sdG[k] = 0.0f;
-    }
+    for (int k = threadIdx.x; k < nj12; k += blockDim.x) sG[k] = G[(size_t)a0 * nj12 + k];
+    for (int k = threadIdx.x; k < kDeformWarps * kMaxJoints * 12; k += blockDim.x) (&sdG[0][0])[k] = 0.0f;
     __syncthreads();
     if (i < in.m) {
         const int av = clamp_avatar(in.avatar_of[i], in.n_avatars);
@@ -173,15 +173,19 @@ __global__ void __launch_bounds__(256) deform_backward_kernel(AvIn in, const flo
         // dL/dG[j_k] += w_k dL/dA
         const int ids[4] = {id.x, id.y, id.z, id.w};
         const float ws[4] = {wt.x, wt.y, wt.z, wt.w};
-        float *dst = av == a0 ? sdG : d_G + (size_t)av * nj12;
+        float *dst = av == a0 ? sdG[threadIdx.x >> 5] : d_G + (size_t)av * nj12;
 #pragma unroll
         for (int k = 0; k < 4; ++k)
 #pragma unroll
             for (int e = 0; e < 12; ++e) atomicAdd(dst + 12 * ids[k] + e, ws[k] * gA[e]);
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < nj12; k += blockDim.x)
-        if (sdG[k] != 0.0f) atomicAdd(d_G + (size_t)a0 * nj12 + k, sdG[k]);
+    for (int k = threadIdx.x; k < nj12; k += blockDim.x) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int q = 0; q < kDeformWarps; ++q) acc += sdG[q][k];
+        if (acc != 0.0f) atomicAdd(d_G + (size_t)a0 * nj12 + k, acc);
+    }
 }
 
 static AvIn make_in(const gs_avatars *av)

@@ -312,128 +312,174 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(const gs_cam
 // ---------------------------------------------------------------------------
 // scan of the bin counts (single CTA, any number of bins)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void bitonic_smem(unsigned long long *s, int m);
+constexpr int kScanPer = 4; // consecutive bins per thread and tile
+
+// Bins with at least heavy_min pairs go to the heavy-first list, bucketed by
+// floor(log2(count)) from the largest bucket down (order inside a bucket is
+// arbitrary: it only steers scheduling); heavy_min is the smallest power of two
+// >= kHeavyMin that keeps the list within kHeavyCap entries.
 __global__ void __launch_bounds__(1024) scan_bins_kernel(Ws w)
 {
     const int nb = w.tb->n_bins;
     const int T = blockDim.x;
-    const int per = (nb + T - 1) / T;
-    const int b0 = min(nb, (int)threadIdx.x * per), b1 = min(b0 + per, nb);
-    unsigned long long s = 0;
-    uint32_t mx = 0;
-    for (int i = b0; i < b1; ++i) {
-        const uint32_t c = w.bin_count[i] + w.bin_fcount[i];
-        s += c;
-        mx = max(mx, c);
-    }
-    __shared__ unsigned long long sh[1024];
-    __shared__ uint32_t smax[32];
-    sh[threadIdx.x] = s;
-    const uint32_t m = __reduce_max_sync(0xffffffffu, mx);
-    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
-    __syncthreads();
-    for (int off = 1; off < T; off <<= 1) { // Hillis-Steele inclusive scan
-        const unsigned long long v = threadIdx.x >= off ? sh[threadIdx.x - off] : 0ull;
-        __syncthreads();
-        sh[threadIdx.x] += v;
-        __syncthreads();
-    }
-    // pair counts beyond the capacity (or 32 bits) are clamped: every bin range
-    // stays inside [0, capacity) and the status word records the overflow
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned long long cap = (unsigned long long)w.tb->pair_capacity;
-    unsigned long long run = sh[threadIdx.x] - s; // exclusive
-    // bins of more than kSortChunk pairs (after the clamp) are sorted in
-    // kSortChunk-long chunks and merged: one list entry per chunk
-    __shared__ uint32_t n_big, max_pass;
-    if (threadIdx.x == 0) n_big = max_pass = 0;
-    __syncthreads();
-    for (int i = b0; i < b1; ++i) {
-        const unsigned long long lo = min(run, cap);
-        w.bin_start[i] = (uint32_t)lo;
-        run += w.bin_count[i] + w.bin_fcount[i];
-        const uint32_t n = (uint32_t)(min(run, cap) - lo);
-        if (n > (uint32_t)kSortChunk) {
-            const uint32_t nch = (n + kSortChunk - 1) / kSortChunk;
-            const uint32_t at = atomicAdd(&n_big, nch);
-            for (uint32_t t = 0; t < nch; ++t) w.big_list[at + t] = ((unsigned long long)i << 32) | t;
-            atomicMax(&max_pass, (uint32_t)(32 - __clz(nch - 1u)));
-        }
+    __shared__ unsigned long long wsum[32];
+    __shared__ unsigned long long carry;
+    __shared__ uint32_t lg[33], bucket_at[33];
+    __shared__ uint32_t n_big, max_pass, smax, hmin, nh;
+    __shared__ uint32_t hcnt[kHeavyCap];
+    __shared__ uint32_t hscan[32];
+    if (threadIdx.x < 33) lg[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+        n_big = max_pass = smax = 0;
+        carry = 0;
     }
+    __syncthreads();
+    uint32_t mx = 0;
+    const int tile = T * kScanPer;
+    for (int t0 = 0; t0 < nb; t0 += tile) {
+        const int b0 = t0 + threadIdx.x * kScanPer;
+        uint32_t c[kScanPer];
+        unsigned long long s = 0;
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            c[k] = b0 + k < nb ? w.bin_count[b0 + k] + w.bin_fcount[b0 + k] : 0u;
+            s += c[k];
+        }
+        unsigned long long incl = s;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long x = lane < (T >> 5) ? wsum[lane] : 0ull;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned long long v = __shfl_up_sync(0xffffffffu, x, off);
+                if (lane >= off) x += v;
+            }
+            wsum[lane] = x;
+        }
+        __syncthreads();
+        // pair counts beyond the capacity (or 32 bits) are clamped: every bin
+        // range stays inside [0, capacity) and the status word records it
+        unsigned long long run = carry + (warp ? wsum[warp - 1] : 0ull) + incl - s;
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            const int i = b0 + k;
+            if (i >= nb) break;
+            const unsigned long long lo = min(run, cap);
+            w.bin_start[i] = (uint32_t)lo;
+            run += c[k];
+            mx = max(mx, c[k]);
+            if (c[k] >= (uint32_t)kHeavyMin) atomicAdd(&lg[32 - __clz(c[k])], 1u);
+            // bins of more than kSortChunk pairs (after the clamp) are sorted in
+            // kSortChunk-long chunks and merged: one list entry per chunk
+            const uint32_t n = (uint32_t)(min(run, cap) - lo);
+            if (n > (uint32_t)kSortChunk) {
+                const uint32_t nch = (n + kSortChunk - 1) / kSortChunk;
+                const uint32_t at = atomicAdd(&n_big, nch);
+                for (uint32_t t = 0; t < nch; ++t) w.big_list[at + t] = ((unsigned long long)i << 32) | t;
+                atomicMax(&max_pass, (uint32_t)(32 - __clz(nch - 1u)));
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == T - 1) carry += wsum[(T >> 5) - 1];
+        __syncthreads();
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) atomicMax(&smax, mx);
     __syncthreads();
     if (threadIdx.x == 0) {
-        w.hdr->n_big = n_big;
-        w.hdr->max_pass = max_pass;
-    }
-    if (threadIdx.x == T - 1) {
-        const unsigned long long total = sh[T - 1];
+        const unsigned long long total = carry;
         w.bin_start[nb] = (uint32_t)min(total, cap);
         w.hdr->n_pairs = (uint32_t)min(total, 0xffffffffull);
         if (total > cap) set_status(w.hdr, GS_ERR_CAPACITY);
-    }
-    if (threadIdx.x < 32) {
-        uint32_t v = threadIdx.x < (unsigned)(T >> 5) ? smax[threadIdx.x] : 0u;
-        v = __reduce_max_sync(0xffffffffu, v);
-        if (threadIdx.x == 0) w.hdr->max_bin = v;
-    }
-    // heavy-first list: the bins with at least heavy_min pairs, largest first.
-    // heavy_min = the smallest power of two >= kHeavyMin that keeps the list
-    // within kHeavyCap entries.
-    __shared__ uint32_t lg[33];
-    __shared__ unsigned long long hl[kHeavyCap];
-    __shared__ uint32_t hn, hmin;
-    if (threadIdx.x < 33) lg[threadIdx.x] = 0;
-    if (threadIdx.x == 0) hn = 0;
-    __syncthreads();
-    for (int i = b0; i < b1; ++i) {
-        const uint32_t c = w.bin_count[i] + w.bin_fcount[i];
-        if (c >= (uint32_t)kHeavyMin) atomicAdd(&lg[32 - __clz(c)], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0, th = 0xffffffffu;
+        w.hdr->max_bin = smax;
+        w.hdr->n_big = n_big;
+        w.hdr->max_pass = max_pass;
+        // heavy threshold, then the start of every included bucket, largest first
+        uint32_t acc = 0, bth = 33;
         for (int b = 32; b >= 0; --b) {
             if (acc + lg[b] > (uint32_t)kHeavyCap) break;
             acc += lg[b];
-            if (lg[b]) th = b == 0 ? 0u : (1u << (b - 1));
+            if (lg[b]) bth = b;
         }
-        hmin = max(th, (uint32_t)kHeavyMin);
+        uint32_t th = bth == 33 ? 0xffffffffu : (bth == 0 ? 0u : (1u << (bth - 1)));
+        th = max(th, (uint32_t)kHeavyMin);
+        hmin = th;
+        uint32_t at = 0;
+        for (int b = 32; b >= 0; --b) {
+            bucket_at[b] = at;
+            const bool in = b > 0 && (1u << (b - 1)) >= th;
+            if (in) at += lg[b];
+        }
+        nh = at;
     }
     __syncthreads();
     const uint32_t th = hmin;
-    for (int i = b0; i < b1; ++i) {
-        const uint32_t c = w.bin_count[i] + w.bin_fcount[i];
-        if (c >= th) {
-            const uint32_t at = atomicAdd(&hn, 1u);
-            if (at < (uint32_t)kHeavyCap) hl[at] = ((unsigned long long)(~c) << 32) | (uint32_t)i;
+    // heavy list and heavy_of, one more coalesced pass over the counts
+    for (int t0 = 0; t0 < nb; t0 += tile) {
+        const int b0 = t0 + threadIdx.x * kScanPer;
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            const int i = b0 + k;
+            if (i >= nb) break;
+            const uint32_t c = w.bin_count[i] + w.bin_fcount[i];
+            int32_t h = -1;
+            if (c >= th) {
+                h = (int32_t)atomicAdd(&bucket_at[32 - __clz(c)], 1u);
+                w.heavy[h] = (uint32_t)i;
+                hcnt[h] = c;
+            }
+            w.heavy_of[i] = h;
         }
     }
     __syncthreads();
-    const int nh = (int)min(hn, (uint32_t)kHeavyCap);
-    int mh = 1;
-    while (mh < nh) mh <<= 1;
-    for (int i = nh + threadIdx.x; i < mh; i += T) hl[i] = ~0ull;
-    __syncthreads();
-    bitonic_smem(hl, mh);
-    for (int i = threadIdx.x; i < nh; i += T) w.heavy[i] = (uint32_t)hl[i];
     // backward segments of the heavy bins: ceil(count / kSeg) each, scanned
-    for (int i = b0; i < b1; ++i) w.heavy_of[i] = -1;
-    __shared__ uint32_t segs[kHeavyCap];
-    for (int i = threadIdx.x; i < nh; i += T) {
-        const uint32_t cnt = ~(uint32_t)(hl[i] >> 32);
-        segs[i] = (cnt + kSeg - 1) / kSeg;
+    const uint32_t n_h = nh;
+    uint32_t seg[kHeavyCap / 1024];
+    uint32_t ssum = 0;
+#pragma unroll
+    for (int k = 0; k < kHeavyCap / 1024; ++k) {
+        const uint32_t i = threadIdx.x * (kHeavyCap / 1024) + k;
+        seg[k] = i < n_h ? (hcnt[i] + kSeg - 1) / kSeg : 0u;
+        ssum += seg[k];
+    }
+    uint32_t sincl = ssum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, sincl, off);
+        if (lane >= off) sincl += v;
+    }
+    if (lane == 31) hscan[warp] = sincl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t x = lane < (T >> 5) ? hscan[lane] : 0u;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += v;
+        }
+        hscan[lane] = x;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nh; i += T) w.heavy_of[(uint32_t)hl[i]] = i;
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0;
-        for (int i = 0; i < nh; ++i) {
-            w.heavy_seg[i] = acc;
-            acc += segs[i];
-        }
-        w.heavy_seg[nh] = acc;
-        w.hdr->n_heavy_items = acc;
-        w.hdr->n_heavy = (uint32_t)nh;
-        w.hdr->heavy_min = nh > 0 ? th : 0xffffffffu;
+    uint32_t srun = (warp ? hscan[warp - 1] : 0u) + sincl - ssum;
+#pragma unroll
+    for (int k = 0; k < kHeavyCap / 1024; ++k) {
+        const uint32_t i = threadIdx.x * (kHeavyCap / 1024) + k;
+        if (i < n_h) w.heavy_seg[i] = srun;
+        srun += seg[k];
+    }
+    if (threadIdx.x == T - 1) {
+        w.heavy_seg[n_h] = srun;
+        w.hdr->n_heavy_items = srun;
+        w.hdr->n_heavy = n_h;
+        w.hdr->heavy_min = n_h > 0 ? th : 0xffffffffu;
     }
 }
 
@@ -554,30 +600,6 @@ __global__ void __launch_bounds__(256) scatter_kernel(const gs_camera *__restric
             }
         }
         __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// bitonic sort in shared memory (the heavy-bin list of the scan)
-// ---------------------------------------------------------------------------
-// Bitonic sort of s[0..m) (m a power of two) by the whole CTA.
-__device__ __forceinline__ void bitonic_smem(unsigned long long *s, int m)
-{
-    const int half = m >> 1;
-    for (int k = 2; k <= m; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int p = threadIdx.x; p < half; p += blockDim.x) {
-                const int i = ((p & ~(j - 1)) << 1) | (p & (j - 1));
-                const int l = i | j;
-                const bool up = (i & k) == 0;
-                const unsigned long long a = s[i], b = s[l];
-                if ((a > b) == up) {
-                    s[i] = b;
-                    s[l] = a;
-                }
-            }
-            __syncthreads();
-        }
     }
 }
 

@@ -195,7 +195,7 @@ __device__ __forceinline__ int bin_of_item(const Ws &w, uint32_t item)
     const uint32_t nh = w.hdr->n_heavy;
     if (item < nh) return (int)w.heavy[item];
     const uint32_t b = item - nh;
-    return w.bin_count[b] >= w.hdr->heavy_min ? -1 : (int)b;
+    return w.bin_count[b] + w.bin_fcount[b] >= w.hdr->heavy_min ? -1 : (int)b;
 }
 
 // alpha before the clamp; the clamp is min(0.99, .)

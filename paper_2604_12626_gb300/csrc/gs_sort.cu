@@ -225,6 +225,31 @@ __global__ void __launch_bounds__(kSortThreads, 3) sort_chunks_kernel(Ws w)
     }
 }
 
+// Merge path with one warp: the number of elements of a[0..na) among the
+// first d outputs of merge(a, b) (keys unique).  Each round probes 32 points
+// of the remaining range; the first probe whose a-key is not below the
+// opposite b-key bounds the answer from above.  About log32 of the range
+// dependent global loads instead of log2.
+__device__ __forceinline__ uint32_t merge_path_warp(const unsigned long long *a, uint32_t na,
+                                                    const unsigned long long *b, uint32_t nb, uint32_t d)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t lo = d > nb ? d - nb : 0u, hi = min(d, na);
+    while (hi > lo) {
+        const uint32_t len = hi - lo;
+        const uint32_t p = lo + (uint32_t)(((unsigned long long)lane * len) >> 5);
+        const bool pr = p < hi && a[p] < b[d - 1 - p];
+        const int k = __popc(__ballot_sync(0xffffffffu, pr));
+        const uint32_t p_prev = __shfl_sync(0xffffffffu, p, k > 0 ? k - 1 : 0);
+        const uint32_t p_next = __shfl_sync(0xffffffffu, p, k < 32 ? k : 31);
+        const uint32_t nlo = k > 0 ? p_prev + 1 : lo;
+        const uint32_t nhi = k < 32 ? min(p_next, hi) : hi;
+        lo = nlo;
+        hi = max(nhi, nlo);
+    }
+    return lo;
+}
+
 struct MergeSmem {
     unsigned long long in[kSortChunk];
     unsigned long long out[kSortChunk];
@@ -255,15 +280,10 @@ __global__ void __launch_bounds__(kSortThreads) merge_pass_kernel(Ws w, int pass
         const uint32_t a0 = (o0 / (2 * width)) * (2 * width);
         const uint32_t a1 = min(a0 + width, n), b1 = min(a1 + width, n);
         const uint32_t na = a1 - a0, nb = b1 - a1;
-        if (threadIdx.x < 2) {
-            const uint32_t d = (threadIdx.x == 0 ? o0 : o1) - a0;
-            uint32_t lo = d > nb ? d - nb : 0u, hi = min(d, na);
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (src[a0 + mid] < src[a1 + d - 1 - mid]) lo = mid + 1;
-                else hi = mid;
-            }
-            sm.split[threadIdx.x] = lo;
+        if (threadIdx.x < 64) { // warp 0: diagonal o0, warp 1: diagonal o1
+            const int wq = threadIdx.x >> 5;
+            const uint32_t sp = merge_path_warp(src + a0, na, src + a1, nb, (wq == 0 ? o0 : o1) - a0);
+            if ((threadIdx.x & 31) == 0) sm.split[wq] = sp;
         }
         __syncthreads();
         const uint32_t i0 = sm.split[0], i1 = sm.split[1];

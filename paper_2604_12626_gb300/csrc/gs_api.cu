@@ -186,7 +186,7 @@ gs_status make_plan(const gs_render_config *cfg, const gs_batch *b, Plan &p)
     p.o_scr = o; o = align256(o + (size_t)p.cap * 8);
     p.o_pT = o; o = align256(o + (size_t)npix * 4);
     p.o_pL = o; o = align256(o + (size_t)npix * 4);
-    p.o_drec = o; o = align256(o + (size_t)R * 48);
+    p.o_drec = o; o = align256(o + (size_t)R * kGradStride * 4);
     p.o_hseg = o; o = align256(o + (size_t)(kHeavyCap + 1) * 4);
     p.o_hof = o; o = align256(o + (size_t)nb * 4);
     p.o_pC = o; o = align256(o + (size_t)npix * 16);
@@ -401,9 +401,11 @@ gs_status gs_render_backward(const gs_gaussians *g, const gs_batch *batch, const
     Ws w = ws_ptrs(workspace, p);
     {
         Stage st7(7, s);
-        cudaError_t e = cudaMemsetAsync(w.d_rec, 0, (size_t)p.R * 48, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(&w.hdr->queue_bwd, 0, 4, s);
+        // the record gradient rows were zeroed by the forward (visible records
+        // only); a repeated backward of the same forward clears them first
+        cudaError_t e = cudaMemsetAsync(&w.hdr->queue_bwd, 0, 4, s);
         if (e != cudaSuccess) return cuda_fail(e);
+        launch_clear_record_grads(w, p.R, sms, s);
         launch_blend_backward(cams, w, d_rgb, d_depth, p.n_bins, p.px, p.py, p.threads, p.B, sms, s);
     }
     {

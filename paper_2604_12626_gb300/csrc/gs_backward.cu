@@ -23,7 +23,6 @@
 
 namespace gs {
 
-constexpr int kGradStride = 12; // floats per record gradient (3 float4)
 
 __device__ __forceinline__ float warp_sum(float v)
 {
@@ -216,7 +215,7 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
         cp_async_commit();
         if (b + 2 < nb) load_keys(b + 2);
         const int32_t lo = lo_of(b), cnt = hi_of(b) - lo;
-        for (int k = threadIdx.x; k < cnt * kGradStride; k += nthr) acc[k] = 0.0f;
+        for (int k = threadIdx.x; k < cnt * kAccStride; k += nthr) acc[k] = 0.0f;
         cp_async_wait<1>();
         __syncthreads();
         const float4 *s0 = sm + (b & 1) * 3 * B, *s1 = s0 + B, *s2 = s0 + 2 * B;
@@ -312,13 +311,13 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
                 const float tot = warp_transpose_sum32(g);
                 const int u = lane / 10, j = lane - 10 * u;
                 const int k = k1 - u;
-                if (lane < 10 * kGroup && k >= 0) atomicAdd(acc + k * kGradStride + j, tot);
+                if (lane < 10 * kGroup && k >= 0) atomicAdd(acc + k * kAccStride + j, tot);
             }
         }
         __syncthreads();
         const uint32_t *ib = sidx + (b & 1) * B;
         for (int k = threadIdx.x; k < cnt; k += nthr) {
-            const float4 *ak = reinterpret_cast<const float4 *>(acc + k * kGradStride);
+            const float4 *ak = reinterpret_cast<const float4 *>(acc + k * kAccStride);
             const float4 x0 = ak[0], x1 = ak[1], x2 = ak[2];
             if (x0.x != 0.f || x0.y != 0.f || x0.z != 0.f || x0.w != 0.f || x1.x != 0.f || x1.y != 0.f ||
                 x1.z != 0.f || x1.w != 0.f || x2.x != 0.f || x2.y != 0.f) {
@@ -340,12 +339,13 @@ __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, 
     extern __shared__ float4 smem_b[];
     __shared__ uint32_t smax_last, item;
     const int B = w.tb->batch_depth;
-    float *acc = reinterpret_cast<float *>(smem_b + 2 * 3 * B); // [B][kGradStride]
-    uint32_t *sidx = reinterpret_cast<uint32_t *>(acc + B * kGradStride); // [2][B]
+    float *acc = reinterpret_cast<float *>(smem_b + 2 * 3 * B); // [B][kAccStride]
+    uint32_t *sidx = reinterpret_cast<uint32_t *>(acc + B * kAccStride); // [2][B]
     // items: the kSeg-long segments of the heavy bins (largest bins first),
     // then every other bin whole
     const uint32_t nhi = w.hdr->n_heavy_items, nh = w.hdr->n_heavy;
     const uint32_t n_items = nhi + (uint32_t)w.tb->n_bins;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&w.hdr->n_backward, 1u); // d_rec is dirty from here on
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) item = atomicAdd(&w.hdr->queue_bwd, 1u);
@@ -415,7 +415,7 @@ __device__ __forceinline__ void sh_weighted(const void *sh, int64_t g, const flo
         const float4 *p = reinterpret_cast<const float4 *>(sh) + g * 12;
 #pragma unroll
         for (int i = 0; i < 12; ++i) {
-            const float4 v = __ldg(p + i);
+            const float4 v = __ldcg(p + i);
             const float c[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) wk[(4 * i + j) / 3] += c[j] * gch[(4 * i + j) % 3];
@@ -424,7 +424,7 @@ __device__ __forceinline__ void sh_weighted(const void *sh, int64_t g, const flo
         const uint4 *p = reinterpret_cast<const uint4 *>(sh) + g * 6;
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-            const uint4 v = __ldg(p + i);
+            const uint4 v = __ldcg(p + i);
             const uint32_t u[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -445,7 +445,10 @@ __device__ __forceinline__ void sh_weighted(const void *sh, int64_t g, const flo
 }
 
 // Full chain for one Gaussian seen by at least one view: screen-space
-// gradients of each visible view back to the Gaussian's parameters.
+// gradients of each visible view back to the Gaussian's parameters.  The
+// per-Gaussian rows are scattered (a quarter of the rows are seen), so they
+// are loaded through L2 only (ld.global.cg): an L1 fill would pull whole
+// 128-byte lines of mostly unseen neighbours.
 template <int SHT, bool OVERWRITE>
 __device__ __forceinline__ void gaussian_backward(const gs_camera *__restrict__ cams, const GaussInB &gin, const Ws &w,
                                                   const GradOut &o, int64_t g, int e)
@@ -454,20 +457,20 @@ __device__ __forceinline__ void gaussian_backward(const gs_camera *__restrict__ 
     const int vb = tb->env_view_begin[e], ve = tb->env_view_begin[e + 1];
     const int64_t local = g - tb->env_off[e];
     const bool use_cov = gin.cov3d != nullptr && g >= tb->env_cov_begin[e];
-    const float mx = __ldg(gin.means + 3 * g), my = __ldg(gin.means + 3 * g + 1), mz = __ldg(gin.means + 3 * g + 2);
+    const float mx = __ldcg(gin.means + 3 * g), my = __ldcg(gin.means + 3 * g + 1), mz = __ldcg(gin.means + 3 * g + 2);
     float S[6];
     float3 ls = make_float3(0.f, 0.f, 0.f);
     float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
     if (use_cov) {
 #pragma unroll
-        for (int i = 0; i < 6; ++i) S[i] = __ldg(gin.cov3d + 6 * g + i);
+        for (int i = 0; i < 6; ++i) S[i] = __ldcg(gin.cov3d + 6 * g + i);
     } else {
-        ls = make_float3(__ldg(gin.log_scales + 3 * g), __ldg(gin.log_scales + 3 * g + 1),
-                         __ldg(gin.log_scales + 3 * g + 2));
-        q = __ldg(reinterpret_cast<const float4 *>(gin.quats) + g);
+        ls = make_float3(__ldcg(gin.log_scales + 3 * g), __ldcg(gin.log_scales + 3 * g + 1),
+                         __ldcg(gin.log_scales + 3 * g + 2));
+        q = __ldcg(reinterpret_cast<const float4 *>(gin.quats) + g);
         sigma_from_sq(ls, q, S);
     }
-    const float op = 1.0f / (1.0f + expf(-__ldg(gin.ologits + g)));
+    const float op = 1.0f / (1.0f + expf(-__ldcg(gin.ologits + g)));
     float gS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float gm0 = 0.f, gm1 = 0.f, gm2 = 0.f, go = 0.f;
     bool first_sh = true;
@@ -476,18 +479,20 @@ __device__ __forceinline__ void gaussian_backward(const gs_camera *__restrict__ 
     for (int kv = vb; kv < ve; ++kv) {
         const int v = tb->env_views[kv];
         const uint32_t rec = (uint32_t)(tb->view_rec_off[v] + local);
-        if (!((__ldg(w.vis + (rec >> 5)) >> (rec & 31)) & 1u)) continue;
+        if (!((__ldcg(w.vis + (rec >> 5)) >> (rec & 31)) & 1u)) continue;
         const float4 *gr4 = reinterpret_cast<const float4 *>(w.d_rec + (size_t)rec * kGradStride);
-        const float4 r0 = gr4[0], r1 = gr4[1], r2 = gr4[2];
+        const float4 r0 = __ldcg(gr4), r1 = __ldcg(gr4 + 1), r2 = __ldcg(gr4 + 2);
+        const uint32_t clamped = __float_as_uint(__ldcg(gr4 + 3).x); // colour channels clamped at 0
+        // a channel clamped at 0 passes no gradient
+        const float gch[3] = {(clamped & 1u) ? 0.f : r1.z, (clamped & 2u) ? 0.f : r1.w, (clamped & 4u) ? 0.f : r2.x};
         // (uc, vc, A, B, C, opacity, r, g, b, z)
         const float g_u = r0.x, g_v = r0.y, gA = r0.z, gB = r0.w, gC = r1.x, g_op = r1.y;
-        const float4 col = w.rec[3 * (size_t)rec + 2]; // a channel clamped at 0 passes no gradient
-        float gch[3] = {col.x > 0.f ? r1.z : 0.f, col.y > 0.f ? r1.w : 0.f, col.z > 0.f ? r2.x : 0.f};
         const float g_z = r2.y;
         const gs_camera &cam = cams[v];
         const float zk = depth_key(mx, my, mz, cam);
         Proj pj;
         project_ewa(mx, my, mz, zk, S, cam, W, H, pj);
+
         const float px = pj.px, py = pj.py, ipz = 1.0f / pj.pz, ipz2 = ipz * ipz;
         float gpx = g_u * cam.fx * ipz, gpy = g_v * cam.fy * ipz;
         float gpz = -g_u * cam.fx * px * ipz2 - g_v * cam.fy * py * ipz2 + g_z;
@@ -539,8 +544,9 @@ __device__ __forceinline__ void gaussian_backward(const gs_camera *__restrict__ 
         float gd1 = cam.R[1] * gpx + cam.R[4] * gpy + cam.R[7] * gpz;
         float gd2 = cam.R[2] * gpx + cam.R[5] * gpy + cam.R[8] * gpz;
         // colour: SH coefficients get Y(dir) x gch, the direction gets grad(Y) . (k gch)
-        const float dnorm = sqrtf(pj.d0 * pj.d0 + pj.d1 * pj.d1 + pj.d2 * pj.d2), idn = 1.0f / dnorm;
-        const float x = pj.d0 * idn, y = pj.d1 * idn, z = pj.d2 * idn;
+        float idn;
+        const float3 dir = view_dir(pj.d0, pj.d1, pj.d2, idn);
+        const float x = dir.x, y = dir.y, z = dir.z;
         float Y[16];
         sh_basis(x, y, z, Y);
 #pragma unroll
@@ -724,6 +730,29 @@ __global__ void __launch_bounds__(256, 2) preprocess_backward_kernel(const gs_ca
 }
 
 // ---------------------------------------------------------------------------
+// Record gradient rows: the forward leaves the rows of visible records at zero;
+// a second backward of the same forward finds them filled by the first and
+// clears them here (the gradient part only: the clamp bits stay).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) clear_record_grads_kernel(Ws w, int64_t n_words)
+{
+    if (w.hdr->n_backward == 0) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_words * 32;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t bits = w.vis[i >> 5];
+        if (!((bits >> (i & 31)) & 1u)) continue;
+        float4 *row = reinterpret_cast<float4 *>(w.d_rec + (size_t)i * kGradStride);
+        row[0] = row[1] = row[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+void launch_clear_record_grads(const Ws &w, int64_t n_records, int n_sms, cudaStream_t s)
+{
+    const int64_t n_words = (n_records + 31) / 32;
+    clear_record_grads_kernel<<<n_sms * 4, 256, 0, s>>>(w, n_words);
+}
+
+// ---------------------------------------------------------------------------
 // popcount of the visibility mask (statistics only)
 // ---------------------------------------------------------------------------
 __global__ void count_visible_kernel(Ws w, int64_t n_words)
@@ -742,7 +771,7 @@ void launch_count_visible(const Ws &w, int64_t n_words, cudaStream_t s)
 
 static int blend_bwd_smem(int batch_depth)
 {
-    return 2 * 3 * batch_depth * (int)sizeof(float4) + batch_depth * kGradStride * 4 + 2 * batch_depth * 4;
+    return 2 * 3 * batch_depth * (int)sizeof(float4) + batch_depth * kAccStride * 4 + 2 * batch_depth * 4;
 }
 
 template <int PX, int PY>

@@ -54,37 +54,6 @@ __device__ __forceinline__ int find_env(const Table *tb, int64_t g)
     return lo;
 }
 
-template <int SHT>
-__device__ __forceinline__ void load_sh(const void *sh, int64_t g, float (&k)[48])
-{
-    if (SHT == GS_SH_F32) {
-        const float4 *p = reinterpret_cast<const float4 *>(sh) + g * 12;
-#pragma unroll
-        for (int i = 0; i < 12; ++i) {
-            float4 v = __ldg(p + i);
-            k[4 * i] = v.x; k[4 * i + 1] = v.y; k[4 * i + 2] = v.z; k[4 * i + 3] = v.w;
-        }
-    } else {
-        const uint4 *p = reinterpret_cast<const uint4 *>(sh) + g * 6;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            uint4 v = __ldg(p + i);
-            uint32_t u[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (SHT == GS_SH_F16) {
-                    __half2 h = *reinterpret_cast<__half2 *>(&u[j]);
-                    float2 f = __half22float2(h);
-                    k[8 * i + 2 * j] = f.x; k[8 * i + 2 * j + 1] = f.y;
-                } else {
-                    k[8 * i + 2 * j] = __uint_as_float(u[j] << 16);
-                    k[8 * i + 2 * j + 1] = __uint_as_float(u[j] & 0xffff0000u);
-                }
-            }
-        }
-    }
-}
-
 struct GaussIn {
     const float *means, *log_scales, *quats, *ologits, *cov3d;
     const void *sh;
@@ -129,23 +98,6 @@ struct QEntry {
     uint32_t pad;
 };
 
-template <int SHT>
-__device__ __forceinline__ float3 sh_colour(const void *sh, int64_t g, float x, float y, float z)
-{
-    float kk[48], Y[16];
-    load_sh<SHT>(sh, g, kk);
-    sh_basis(x, y, z, Y);
-    float col[3];
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        float acc = 0.5f;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) acc += Y[i] * kk[3 * i + ch];
-        col[ch] = fmaxf(acc, 0.0f);
-    }
-    return make_float3(col[0], col[1], col[2]);
-}
-
 // Phase 2, one entry per lane of a warp: colour, record, visibility bit and
 // bin counts of a queued visible (view, Gaussian).
 template <int SHT>
@@ -155,14 +107,22 @@ __device__ __forceinline__ void finish_entry(const QEntry &en, bool active, uint
     const Table *tb = w.tb;
     if (active) {
         const int tpv = tb->tiles_per_view, tx_n = tb->tiles_x, tw = tb->tile_w, th = tb->tile_h;
-        const float dn = 1.0f / sqrtf(en.d0 * en.d0 + en.d1 * en.d1 + en.d2 * en.d2);
-        const float3 col = sh_colour<SHT>(gin.sh, en.g, en.d0 * dn, en.d1 * dn, en.d2 * dn);
+        float idn;
+        const float3 dir = view_dir(en.d0, en.d1, en.d2, idn);
+        const float3 col = sh_colour<SHT>(gin.sh, en.g, dir.x, dir.y, dir.z);
         const float op = 1.0f / (1.0f + expf(-__ldg(gin.ologits + en.g)));
         const int bx0 = en.x0 / tw, bx1 = en.x1 / tw, by0 = en.y0 / th, by1 = en.y1 / th;
         float4 *dst = w.rec + 3 * (size_t)en.rec;
         dst[0] = make_float4(en.uc, en.vc, en.zk, en.r);
         dst[1] = make_float4(en.A, en.B, en.C, op);
         dst[2] = make_float4(col.x, col.y, col.z, __uint_as_float(pack_rect(bx0, by0, bx1 - bx0 + 1, by1 - by0 + 1)));
+        // the record's gradient row starts at zero for the backward, which
+        // accumulates into it and zeroes it again once consumed; beside it,
+        // which colour channels were clamped at 0 (they pass no gradient)
+        float4 *dr = reinterpret_cast<float4 *>(w.d_rec + (size_t)en.rec * kGradStride);
+        const uint32_t clamped = (col.x > 0.f ? 0u : 1u) | (col.y > 0.f ? 0u : 2u) | (col.z > 0.f ? 0u : 4u);
+        dr[0] = dr[1] = dr[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        dr[3] = make_float4(__uint_as_float(clamped), 0.f, 0.f, 0.f);
         uint32_t *hk = c.hist ? hist + en.k * tpv : w.bin_fcount + (size_t)en.v * tpv;
         for (int by = by0; by <= by1; ++by)
             for (int bx = bx0; bx <= bx1; ++bx) atomicAdd(hk + by * tx_n + bx, 1u);

@@ -15,9 +15,13 @@
 //   scratch     [P_cap] uint64, ping-pong buffer of the large-bin merges
 //   pix_T       [V*H*W] final transmittance (saved for the backward)
 //   pix_last    [V*H*W] 1 + tile-list position of the last blended pair
-//   d_rec       [R] 12 floats: dL/d(uc, vc, A, B, C, opacity, r, g, b, z)
+//   d_rec       [R] 16 floats (64 B, one DRAM burst): dL/d(uc, vc, A, B, C,
+//               opacity, r, g, b, z), 2 unused, then at [12] the bits of the
+//               colour channels that were clamped at 0 (written by the forward)
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,6 +34,8 @@ constexpr float kAlphaMax = 0.99f;
 constexpr float kTStop = 1e-4f;
 constexpr float kDilation = 0.3f;
 constexpr int kSortChunk = 4096; // keys one CTA sorts; larger bins are merged
+constexpr int kGradStride = 16;   // floats per record row of d_rec: 12 gradient + colour-clamp mask + 3 unused
+constexpr int kAccStride = 12;    // floats per record in the backward's shared-memory accumulator
 constexpr int kMaxJoints = 64;    // joints of one avatar tree
 
 // A joint tree passed by value: parent and depth of every joint (parent < child).
@@ -53,7 +59,8 @@ struct Header {
     uint32_t n_heavy_items; // backward work items of the heavy bins (one per kSeg-long segment)
     uint32_t max_pass;  // merge passes the largest bin needs
     unsigned long long n_evals; // blend evaluations, counted under GS_FLAG_COUNT_EVALS
-    uint32_t pad[50];
+    uint32_t n_backward;  // gs_render_backward calls since the forward (d_rec is clean while 0)
+    uint32_t pad[49];
 };
 
 struct Table {
@@ -91,7 +98,7 @@ struct Ws {
     unsigned long long *keys, *scratch;
     float *pix_T;
     uint32_t *pix_last;
-    float *d_rec; // 12 floats per record
+    float *d_rec; // kGradStride floats per record
 };
 
 constexpr int kSeg = 2048;       // backward segment of a heavy bin (a multiple of every batch depth)
@@ -330,6 +337,68 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float (&Y)[1
     Y[13] = -kSH3c * x * (4.0f * zz - xx - yy);
     Y[14] = kSH3e * z * (xx - yy);
     Y[15] = -kSH3a * x * (xx - 3.0f * yy);
+}
+
+// Unit view direction d / |d| (d = mu - C) with every rounding explicit, so
+// that the forward and the backward evaluate the colour -- and take its clamp
+// decision -- on identical values.  inv receives 1 / |d|.
+__device__ __forceinline__ float3 view_dir(float d0, float d1, float d2, float &inv)
+{
+    const float n2 = __fmaf_rn(d0, d0, __fmaf_rn(d1, d1, __fmul_rn(d2, d2)));
+    inv = __fdiv_rn(1.0f, __fsqrt_rn(n2));
+    return make_float3(__fmul_rn(d0, inv), __fmul_rn(d1, inv), __fmul_rn(d2, inv));
+}
+
+
+// SH-3 colour at a unit direction: 0.5 + sum_i Y_i k_i per channel, clamped
+// below at 0.  The coefficients are streamed in memory order (no 48-value
+// array held in registers); each channel is one chain of fused multiply-adds
+// in index order, the same sequence wherever it is called.
+template <int SHT>
+__device__ __forceinline__ float3 sh_colour_basis(const void *sh, int64_t g, const float (&Y)[16])
+{
+    float acc[3] = {0.5f, 0.5f, 0.5f};
+    if (SHT == GS_SH_F32) {
+        const float4 *p = reinterpret_cast<const float4 *>(sh) + g * 12;
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            const float4 v = __ldg(p + i);
+            const float c[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[(4 * i + j) % 3] = __fmaf_rn(Y[(4 * i + j) / 3], c[j], acc[(4 * i + j) % 3]);
+        }
+    } else {
+        const uint4 *p = reinterpret_cast<const uint4 *>(sh) + g * 6;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const uint4 v = __ldg(p + i);
+            const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float lo, hi;
+                if (SHT == GS_SH_F16) {
+                    const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&u[j]));
+                    lo = f.x;
+                    hi = f.y;
+                } else {
+                    lo = __uint_as_float(u[j] << 16);
+                    hi = __uint_as_float(u[j] & 0xffff0000u);
+                }
+                const int e = 8 * i + 2 * j;
+                acc[e % 3] = __fmaf_rn(Y[e / 3], lo, acc[e % 3]);
+                acc[(e + 1) % 3] = __fmaf_rn(Y[(e + 1) / 3], hi, acc[(e + 1) % 3]);
+            }
+        }
+    }
+    return make_float3(fmaxf(acc[0], 0.0f), fmaxf(acc[1], 0.0f), fmaxf(acc[2], 0.0f));
+}
+
+template <int SHT>
+__device__ __forceinline__ float3 sh_colour(const void *sh, int64_t g, float x, float y, float z)
+{
+    float Y[16];
+    sh_basis(x, y, z, Y);
+    return sh_colour_basis<SHT>(sh, g, Y);
 }
 
 } // namespace gs

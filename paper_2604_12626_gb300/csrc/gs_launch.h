@@ -30,6 +30,7 @@ void launch_count_visible(const Ws &w, int64_t n_words, cudaStream_t s);
 struct GradOut {
     float *means, *log_scales, *quats, *ologits, *sh, *cov3d;
 };
+void launch_clear_record_grads(const Ws &w, int64_t n_records, int n_sms, cudaStream_t s);
 void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,
                            int px, int py, int threads, int batch_depth, int n_sms, cudaStream_t s);
 void launch_preprocess_backward(const gs_gaussians *g, const gs_camera *cams, const Ws &w, const GradOut &o,

@@ -241,3 +241,30 @@ def test_scene_with_avatars_forward_backward_vs_oracle(gs, oracle):
         e = rel_l2(a.cpu().numpy(), b)
         print(f"avatar-scene grad {i}: rel L2 {e:.2e}")
         assert e < 1e-3, (i, e)
+
+
+def test_repeated_backward_of_one_forward(gs):
+    """Two backward calls after one forward (as autograd with retain_graph
+    does) give the same gradients: the record gradient rows the first call
+    filled are cleared before the second accumulates into them; a new forward
+    starts from clean rows again."""
+    g = synth.room_scene(150_000, seed=21)
+    W = H = 96
+    cam = synth.room_camera(21, W, H)
+    rng = np.random.default_rng(3)
+    d_rgb = torch.from_numpy(rng.standard_normal((1, 3, H, W))).float().cuda()
+    d_dep = torch.from_numpy(0.1 * rng.standard_normal((1, H, W))).float().cuda()
+    r = gs.Renderer(gs.Batch(np.array([0, g["means"].shape[0]])), W, H, tile=(8, 8), batch_depth=64, pix=(2, 1),
+                    persistent=True, grad_overwrite=True)
+    G = gs.Gaussians.from_numpy(g)
+    ct = gs.cameras_tensor(cam[None])
+    r.forward(G, ct)
+    a = {k: v.clone() for k, v in r.backward(G, ct, d_rgb, d_dep).items() if v is not None}
+    b = {k: v.clone() for k, v in r.backward(G, ct, d_rgb, d_dep).items() if v is not None}
+    r.forward(G, ct)
+    c = {k: v.clone() for k, v in r.backward(G, ct, d_rgb, d_dep).items() if v is not None}
+    torch.cuda.synchronize()
+    for k in a:
+        assert rel_l2(b[k].cpu().numpy(), a[k].cpu().numpy()) < 1e-6, k
+        assert rel_l2(c[k].cpu().numpy(), a[k].cpu().numpy()) < 1e-6, k
+    assert float(a["opacity_logits"].abs().sum()) > 0

@@ -173,7 +173,7 @@ gs_status gs_render(const gs_gaussians *g, const gs_batch *batch, const gs_camer
  * exits.  Inputs and outputs are as for gs_render.  Problems whose workspace
  * (gs_render_workspace_size) exceeds the array are rejected with
  * GS_ERR_WORKSPACE_TOO_SMALL before any work is enqueued; 64 MiB holds about
- * 300k (view, Gaussian) records at 256x256 with the default pair capacity.
+ * 195k (view, Gaussian) records at 256x256 with the default pair capacity.
  * Allocates nothing: no cudaMalloc/cudaFree, no library allocation, and no
  * profiling events.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress), so make that first call before any stream

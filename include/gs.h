@@ -163,6 +163,22 @@ gs_status gs_render(const gs_gaussians *g, const gs_batch *batch, const gs_camer
                     void *workspace, size_t workspace_bytes, float *out_rgb, float *out_depth, float *out_T,
                     int32_t *out_ncontrib, void *stream);
 
+/* gs_render with the avatars posed inside the preprocess (Sec. 3.3: LBS of
+ * the canonical avatar Gaussians, fused into the projection so that the posed
+ * mean and covariance are never written to or read from memory).  The batch
+ * must give env_cov3d_begin: rows [env_cov3d_begin[e], env_offsets[e+1]) of
+ * env e are avatar Gaussians, and they are the canonical rows of `av` in env
+ * order (env 0's first, then env 1's ...; av->dest must be NULL, av->m their
+ * total).  For those rows g->means is read but ignored and g->log_scales,
+ * g->quats, g->cov3d are not used; opacity and SH are g's rows as for the
+ * scene.  joint_G: device [n_avatars, n_joints, 3, 4].  The result equals
+ * gs_deform_avatars into those rows followed by gs_render.  Forward only: a
+ * gs_render_backward needs the posed rows in memory (the unfused path). */
+gs_status gs_render_avatars(const gs_gaussians *g, const gs_batch *batch, const gs_avatars *av, const float *joint_G,
+                            const gs_camera *cams, const gs_render_config *cfg, void *workspace,
+                            size_t workspace_bytes, float *out_rgb, float *out_depth, float *out_T,
+                            int32_t *out_ncontrib, void *stream);
+
 /* gs_render without a workspace, for callers that cannot allocate device
  * memory -- for instance a sensor plugin inside a host simulator whose device
  * memory is owned by another framework's allocator, or a real-time path that

@@ -78,6 +78,8 @@ _lib.gs_render.argtypes = [_R(GsGaussians), _R(GsBatch), _P, _R(GsRenderConfig),
 _lib.gs_render_backward.argtypes = [_R(GsGaussians), _R(GsBatch), _P, _R(GsRenderConfig), _P, ctypes.c_size_t, _P, _P,
                                     _P, _P, _P, _P, _P, _P, _P]
 _lib.gs_deform_avatars.argtypes = [_R(GsAvatars), _P, _P, _P, _P]
+_lib.gs_render_avatars.argtypes = [_R(GsGaussians), _R(GsBatch), _R(GsAvatars), _P, _P, _R(GsRenderConfig), _P,
+                                   ctypes.c_size_t, _P, _P, _P, _P, _P]
 _lib.gs_composite_nearest.argtypes = [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]
 _lib.gs_forward_kinematics.argtypes = [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]
 _lib.gs_interpolate_joints.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P]
@@ -98,7 +100,8 @@ _lib.gs_version.restype = ctypes.c_int32
 
 EXPORTS = ("gs_render_static", "gs_profile_enable", "gs_profile_read", "gs_workspace_sections", "gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_deform_avatars",
            "gs_deform_avatars_backward", "gs_get_status", "gs_render_stats", "gs_autotune", "gs_last_cuda_error",
-           "gs_version", "gs_composite_nearest", "gs_forward_kinematics", "gs_interpolate_joints")
+           "gs_version", "gs_composite_nearest", "gs_forward_kinematics", "gs_interpolate_joints",
+           "gs_render_avatars")
 
 
 class GsError(RuntimeError):
@@ -296,6 +299,20 @@ class Renderer:
                                        _ptr(grads["quats"]), _ptr(grads["opacity_logits"]), _ptr(grads["sh"]),
                                        _ptr(grads.get("cov3d")), _stream(stream)), "gs_render_backward")
         return grads
+
+    def forward_avatars(self, g: Gaussians, av: "Avatars", joint_G: torch.Tensor, cams: torch.Tensor, out=None,
+                        stream=None):
+        """gs_render_avatars: like forward, with the avatar rows of every env
+        (from the batch's env_cov3d_begin on) posed by LBS inside the
+        preprocess from ``av`` (canonical rows in env order, no dest)."""
+        if out is None:
+            out = self.alloc_outputs()
+        rgb, depth, T, nc = out
+        _check(_lib.gs_render_avatars(ctypes.byref(g.c), ctypes.byref(self.batch.c), ctypes.byref(av.c),
+                                      _ptr(joint_G), _ptr(cams), ctypes.byref(self.cfg), _ptr(self.workspace),
+                                      self.ws_bytes, _ptr(rgb), _ptr(depth), _ptr(T), _ptr(nc), _stream(stream)),
+               "gs_render_avatars")
+        return out
 
     def stats(self, stream=None) -> dict:
         s = GsStats()

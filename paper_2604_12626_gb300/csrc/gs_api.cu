@@ -287,7 +287,8 @@ gs_status check_gaussians(const gs_gaussians *g, const Plan &p, bool need_sq)
 
 gs_status enqueue_forward(const gs_gaussians *g, const gs_batch *b, const gs_camera *cams,
                           const gs_render_config *cfg, void *ws, size_t ws_bytes, float *rgb, float *depth, float *T,
-                          int32_t *ncontrib, cudaStream_t s)
+                          int32_t *ncontrib, cudaStream_t s, const gs_avatars *av = nullptr,
+                          const float *joint_G = nullptr)
 {
     int sms = 0;
     gs_status st = device_init(&sms);
@@ -305,6 +306,15 @@ gs_status enqueue_forward(const gs_gaussians *g, const gs_batch *b, const gs_cam
     if (ws_bytes < p.total) return GS_ERR_WORKSPACE_TOO_SMALL;
     Table t;
     fill_table(p, b, cfg, sms, t);
+    if (av) {
+        // fused LBS: the avatar rows of env e are canonical rows env_av_base[e] + (g - env_cov_begin[e])
+        int64_t base = 0;
+        for (int e = 0; e < b->n_envs; ++e) {
+            t.env_av_base[e] = base;
+            base += t.env_off[e + 1] - t.env_cov_begin[e];
+        }
+        if (base != av->m) return GS_ERR_INVALID_ARG;
+    }
     Ws w = ws_ptrs(ws, p);
     {
         Stage st0(0, s);
@@ -317,7 +327,7 @@ gs_status enqueue_forward(const gs_gaussians *g, const gs_batch *b, const gs_cam
     }
     {
         Stage st1(1, s);
-        launch_preprocess(g, cams, w, t.n_chunks, s);
+        launch_preprocess(g, cams, w, t.n_chunks, s, av, joint_G);
     }
     {
         Stage st2(2, s);
@@ -433,6 +443,28 @@ gs_status gs_deform_avatars(const gs_avatars *av, const float *joint_G, float *o
         launch_deform(av, joint_G, out_means, out_cov3d, static_cast<cudaStream_t>(stream));
     }
     return check_launch();
+}
+
+gs_status gs_render_avatars(const gs_gaussians *g, const gs_batch *batch, const gs_avatars *av, const float *joint_G,
+                            const gs_camera *cams, const gs_render_config *cfg, void *workspace,
+                            size_t workspace_bytes, float *out_rgb, float *out_depth, float *out_T,
+                            int32_t *out_ncontrib, void *stream)
+{
+    if (!g || !batch || !av || !joint_G || !batch->env_cov3d_begin) return GS_ERR_INVALID_ARG;
+    if (av->dest) return GS_ERR_INVALID_ARG;
+    if (av->m < 0 || av->n_avatars < 1 || av->n_joints < 1 || av->n_joints > kMaxJoints) return GS_ERR_INVALID_ARG;
+    if (av->m > 0 && (!av->means || !av->log_scales || !av->quats || !av->joint_ids || !av->weights || !av->avatar_of))
+        return GS_ERR_INVALID_ARG;
+    const void *ptrs[] = {av->means, av->log_scales, av->quats, av->joint_ids, av->weights, av->avatar_of, joint_G};
+    for (const void *q : ptrs)
+        if (q && !aligned16(q)) return GS_ERR_ALIGNMENT;
+    for (int e = 0; e < batch->n_envs; ++e)
+        if (batch->env_cov3d_begin[e] < batch->env_offsets[e] || batch->env_cov3d_begin[e] > batch->env_offsets[e + 1])
+            return GS_ERR_INVALID_ARG;
+    gs_gaussians gg = *g;
+    gg.cov3d = nullptr; // the avatar rows are posed inside the preprocess
+    return enqueue_forward(&gg, batch, cams, cfg, workspace, workspace_bytes, out_rgb, out_depth, out_T,
+                           out_ncontrib, static_cast<cudaStream_t>(stream), av, joint_G);
 }
 
 gs_status gs_composite_nearest(const float *rgb_a, const float *depth_a, const float *rgb_b, const float *depth_b,

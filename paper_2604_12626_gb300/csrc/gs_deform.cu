@@ -24,22 +24,6 @@ struct AvIn {
     int32_t n_avatars, n_joints;
 };
 
-// joint ids >= n_joints (a caller error) are clamped so that reads stay in bounds
-__device__ __forceinline__ ushort4 clamp_ids(ushort4 id, int nj)
-{
-    const unsigned short m = (unsigned short)(nj - 1);
-    return make_ushort4(min(id.x, m), min(id.y, m), min(id.z, m), min(id.w, m));
-}
-
-__device__ __forceinline__ int clamp_avatar(int a, int na) { return a < 0 ? 0 : (a >= na ? na - 1 : a); }
-
-__device__ __forceinline__ void blend_matrix(const float *Gs, const ushort4 id, const float4 wt, float (&A)[12])
-{
-    const float *g0 = Gs + 12 * id.x, *g1 = Gs + 12 * id.y, *g2 = Gs + 12 * id.z, *g3 = Gs + 12 * id.w;
-#pragma unroll
-    for (int e = 0; e < 12; ++e) A[e] = wt.x * g0[e] + wt.y * g1[e] + wt.z * g2[e] + wt.w * g3[e];
-}
-
 __global__ void __launch_bounds__(256) deform_kernel(AvIn in, const float *__restrict__ G, float *out_means,
                                                      float *out_cov)
 {
@@ -55,30 +39,17 @@ __global__ void __launch_bounds__(256) deform_kernel(AvIn in, const float *__res
     const float *Gs = av == a0 ? sG : G + (size_t)av * nj12;
     const ushort4 id = clamp_ids(reinterpret_cast<const ushort4 *>(in.joint_ids)[i], in.n_joints);
     const float4 wt = reinterpret_cast<const float4 *>(in.weights)[i];
-    float A[12];
-    blend_matrix(Gs, id, wt, A);
-    const float mx = in.means[3 * i], my = in.means[3 * i + 1], mz = in.means[3 * i + 2];
-    const float3 ls = make_float3(in.log_scales[3 * i], in.log_scales[3 * i + 1], in.log_scales[3 * i + 2]);
-    const float4 q = reinterpret_cast<const float4 *>(in.quats)[i];
-    float S[6];
-    sigma_from_sq(ls, q, S);
-    const float Sf[9] = {S[0], S[1], S[2], S[1], S[3], S[4], S[2], S[4], S[5]};
-    float AS[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) AS[3 * r + c] = A[4 * r] * Sf[c] + A[4 * r + 1] * Sf[3 + c] + A[4 * r + 2] * Sf[6 + c];
+    float mu[3], cov[6];
+    lbs_gaussian(Gs, id, wt, make_float3(in.means[3 * i], in.means[3 * i + 1], in.means[3 * i + 2]),
+                 make_float3(in.log_scales[3 * i], in.log_scales[3 * i + 1], in.log_scales[3 * i + 2]),
+                 reinterpret_cast<const float4 *>(in.quats)[i], mu, cov);
     const int64_t d = in.dest ? in.dest[i] : i;
-    out_means[3 * d] = A[0] * mx + A[1] * my + A[2] * mz + A[3];
-    out_means[3 * d + 1] = A[4] * mx + A[5] * my + A[6] * mz + A[7];
-    out_means[3 * d + 2] = A[8] * mx + A[9] * my + A[10] * mz + A[11];
+    out_means[3 * d] = mu[0];
+    out_means[3 * d + 1] = mu[1];
+    out_means[3 * d + 2] = mu[2];
     float *oc = out_cov + 6 * d;
-    oc[0] = AS[0] * A[0] + AS[1] * A[1] + AS[2] * A[2];
-    oc[1] = AS[0] * A[4] + AS[1] * A[5] + AS[2] * A[6];
-    oc[2] = AS[0] * A[8] + AS[1] * A[9] + AS[2] * A[10];
-    oc[3] = AS[3] * A[4] + AS[4] * A[5] + AS[5] * A[6];
-    oc[4] = AS[3] * A[8] + AS[4] * A[9] + AS[5] * A[10];
-    oc[5] = AS[6] * A[8] + AS[7] * A[9] + AS[8] * A[10];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) oc[k] = cov[k];
 }
 
 constexpr int kDeformWarps = 8; // 256 threads

@@ -57,6 +57,12 @@ __device__ __forceinline__ int find_env(const Table *tb, int64_t g)
 struct GaussIn {
     const float *means, *log_scales, *quats, *ologits, *cov3d;
     const void *sh;
+    // fused LBS (gs_render_avatars): the avatar rows of every env are posed
+    // here from their canonical Gaussians instead of read from means / cov3d
+    const float *av_means, *av_log_scales, *av_quats, *av_weights, *av_G;
+    const uint16_t *av_ids;
+    const int32_t *av_of;
+    int32_t n_avatars, n_joints;
 };
 
 // Every preprocess / scatter CTA owns a chunk of kChunk consecutive Gaussians.
@@ -194,6 +200,24 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(const gs_cam
         const int64_t local = g - env_base;
         bool have_sigma = false;
         float S[6];
+        if (gin.av_G && valid && g >= cov_begin) {
+            // posed mean and covariance by LBS, never written to memory
+            const int64_t i = tb->env_av_base[c.e0] + (g - cov_begin);
+            const int a = clamp_avatar(__ldg(gin.av_of + i), gin.n_avatars);
+            const ushort4 id = clamp_ids(__ldg(reinterpret_cast<const ushort4 *>(gin.av_ids) + i), gin.n_joints);
+            const float4 wt = __ldg(reinterpret_cast<const float4 *>(gin.av_weights) + i);
+            float mu[3];
+            lbs_gaussian(gin.av_G + (size_t)a * gin.n_joints * 12, id, wt,
+                         make_float3(__ldg(gin.av_means + 3 * i), __ldg(gin.av_means + 3 * i + 1),
+                                     __ldg(gin.av_means + 3 * i + 2)),
+                         make_float3(__ldg(gin.av_log_scales + 3 * i), __ldg(gin.av_log_scales + 3 * i + 1),
+                                     __ldg(gin.av_log_scales + 3 * i + 2)),
+                         __ldg(reinterpret_cast<const float4 *>(gin.av_quats) + i), mu, S);
+            mx = mu[0];
+            my = mu[1];
+            mz = mu[2];
+            have_sigma = true;
+        }
         for (int k = 0; k < c.kmax; ++k) {
             bool vis = false;
             QEntry en;
@@ -807,9 +831,16 @@ void launch_setup(const Table &tb, const Ws &w, cudaStream_t s) { setup_kernel<<
 
 constexpr int kPreSmem = (kPreThreads / 32) * kWarpQ * (int)sizeof(QEntry) + kHistCap * 4;
 
-void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s)
+void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s,
+                       const gs_avatars *av, const float *joint_G)
 {
-    GaussIn gin{g->means, g->log_scales, g->quats, g->opacity_logits, g->cov3d, g->sh};
+    GaussIn gin{g->means, g->log_scales, g->quats, g->opacity_logits, g->cov3d, g->sh,
+                nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0};
+    if (av && joint_G) {
+        gin.av_means = av->means; gin.av_log_scales = av->log_scales; gin.av_quats = av->quats;
+        gin.av_weights = av->weights; gin.av_G = joint_G; gin.av_ids = av->joint_ids; gin.av_of = av->avatar_of;
+        gin.n_avatars = av->n_avatars; gin.n_joints = av->n_joints;
+    }
     const unsigned grid = (unsigned)n_chunks;
     if (grid == 0) return;
     switch (g->sh_dtype) {

@@ -74,6 +74,7 @@ struct Table {
     float near_plane;
     int64_t env_off[GS_MAX_ENVS + 1];
     int64_t env_cov_begin[GS_MAX_ENVS];
+    int64_t env_av_base[GS_MAX_ENVS]; // fused LBS: canonical-avatar row of the env's first avatar Gaussian
     int64_t view_rec_off[GS_MAX_VIEWS + 1];
     int32_t view_env[GS_MAX_VIEWS];
     int32_t env_view_begin[GS_MAX_ENVS + 1];
@@ -399,6 +400,52 @@ __device__ __forceinline__ float3 sh_colour(const void *sh, int64_t g, float x, 
     float Y[16];
     sh_basis(x, y, z, Y);
     return sh_colour_basis<SHT>(sh, g, Y);
+}
+
+// joint ids >= n_joints (a caller error) are clamped so that reads stay in bounds
+__device__ __forceinline__ ushort4 clamp_ids(ushort4 id, int nj)
+{
+    const unsigned short m = (unsigned short)(nj - 1);
+    return make_ushort4(min(id.x, m), min(id.y, m), min(id.z, m), min(id.w, m));
+}
+
+__device__ __forceinline__ int clamp_avatar(int a, int na) { return a < 0 ? 0 : (a >= na ? na - 1 : a); }
+
+__device__ __forceinline__ void blend_matrix(const float *Gs, const ushort4 id, const float4 wt, float (&A)[12])
+{
+    const float *g0 = Gs + 12 * id.x, *g1 = Gs + 12 * id.y, *g2 = Gs + 12 * id.z, *g3 = Gs + 12 * id.w;
+#pragma unroll
+    for (int e = 0; e < 12; ++e)
+        A[e] = __fmaf_rn(wt.w, g3[e], __fmaf_rn(wt.z, g2[e], __fmaf_rn(wt.y, g1[e], __fmul_rn(wt.x, g0[e]))));
+}
+
+// LBS of one canonical Gaussian (Sec. 3.3): A = sum_k w_k G[j_k] (3x4),
+// mean' = A3 mean + a, cov' = A3 Sigma A3^T (upper triangle xx, xy, xz, yy,
+// yz, zz), every rounding explicit so that the deform kernel and the fused
+// preprocess produce identical bits.
+__device__ __forceinline__ void lbs_gaussian(const float *Gs, ushort4 id, float4 wt, float3 m, float3 ls, float4 q,
+                                             float (&mu)[3], float (&cov)[6])
+{
+    float A[12];
+    blend_matrix(Gs, id, wt, A);
+    float S[6];
+    sigma_from_sq(ls, q, S);
+    const float Sf[9] = {S[0], S[1], S[2], S[1], S[3], S[4], S[2], S[4], S[5]};
+    float AS[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            AS[3 * r + c] = __fmaf_rn(A[4 * r + 2], Sf[6 + c], __fmaf_rn(A[4 * r + 1], Sf[3 + c], __fmul_rn(A[4 * r], Sf[c])));
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        mu[r] = __fmaf_rn(A[4 * r + 2], m.z, __fmaf_rn(A[4 * r + 1], m.y, __fmaf_rn(A[4 * r], m.x, A[4 * r + 3])));
+    const int ri[6] = {0, 0, 0, 1, 1, 2}, ci[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const int r = ri[k], c = ci[k];
+        cov[k] = __fmaf_rn(AS[3 * r + 2], A[4 * c + 2], __fmaf_rn(AS[3 * r + 1], A[4 * c + 1], __fmul_rn(AS[3 * r], A[4 * c])));
+    }
 }
 
 } // namespace gs

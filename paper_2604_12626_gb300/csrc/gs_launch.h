@@ -11,7 +11,8 @@ cudaError_t configure_forward_kernels();
 cudaError_t configure_backward_kernels();
 
 void launch_setup(const Table &tb, const Ws &w, cudaStream_t s);
-void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s);
+void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s,
+                       const gs_avatars *av = nullptr, const float *joint_G = nullptr);
 void launch_scan(const Ws &w, cudaStream_t s);
 void launch_scatter(const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s);
 cudaError_t configure_sort_kernels();

@@ -133,3 +133,71 @@ def test_rooms_with_avatars_batched_vs_oracle(gs, oracle):
         st = compare_view(gpu_outputs(out, e), ora)
         print(f"env {e} with avatars: {st}")
         assert (ora["T"] < 0.5).mean() > 0.1
+
+
+def test_fused_lbs_in_preprocess_equals_deform_then_render(gs, oracle):
+    """gs_render_avatars (LBS inside the preprocess, posed Gaussians never in
+    memory) against gs_deform_avatars + gs_render on the same inputs, and
+    against the oracle."""
+    W = H = 96
+    n_room, n_av, n_avatars = 40_000, 3000, 2
+    envs, cams = [], []
+    for e in range(2):
+        room = synth.room_scene(n_room, seed=700 + e)
+        av, G, avatar_of = make_avatars(n_avatars, n_av, 80 + 10 * e)
+        cam = synth.room_camera(700 + e, W, H)
+        fwd, C = cam[6:9], cam[9:12]
+        for k in range(n_avatars):
+            root = C + fwd * (2.0 + 0.6 * k) + np.array([0.0, 0.0, -0.3])
+            G[k, :, :, 3] += (root - G[k, 0, :, 3] - G[k, 0, :, :3] @ synth.REST_JOINTS[0]).astype(np.float32)
+        envs.append((room, av, G, avatar_of))
+        cams.append(cam)
+    cams = np.stack(cams)
+    m_env = n_room + n_av * n_avatars
+    offs = np.array([0, m_env, 2 * m_env])
+    keys = ("means", "log_scales", "quats", "opacity_logits", "sh")
+    cat = {k: np.concatenate([np.concatenate([r[k], a[k]]) for r, a, _, _ in envs]) for k in keys}
+    dest = np.concatenate([np.arange(n_room, m_env) + e * m_env for e in range(2)]).astype(np.int64)
+    av_all = {k: np.concatenate([a[k] for _, a, _, _ in envs]) for k in envs[0][1]}
+    G_all = T(np.concatenate([G for _, _, G, _ in envs]))
+    avatar_of_all = np.concatenate([ao + n_avatars * e for e, (_, _, _, ao) in enumerate(envs)]).astype(np.int32)
+    batch = gs.Batch(offs, env_cov3d_begin=[n_room, m_env + n_room])
+    # unfused: deform into the rows, then render
+    Gg = gs.Gaussians.from_numpy(dict(cat, cov3d=np.zeros((2 * m_env, 6), np.float32)))
+    gs.deform(gpu_avatars(gs, av_all, avatar_of_all, 2 * n_avatars, dest), G_all, Gg.means, Gg.cov3d)
+    r1 = gs.Renderer(batch, W, H, persistent=True)
+    ct = gs.cameras_tensor(cams)
+    a = [x.clone() for x in r1.forward(Gg, ct)]
+    # fused: the avatar rows of `cat` keep their canonical (unposed) values
+    Gf = gs.Gaussians.from_numpy(cat)
+    r2 = gs.Renderer(batch, W, H, persistent=True)
+    b = r2.forward_avatars(Gf, gpu_avatars(gs, av_all, avatar_of_all, 2 * n_avatars), G_all, ct)
+    torch.cuda.synchronize()
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    for e, (room, av, G, avatar_of) in enumerate(envs):
+        pm, pc = oracle.lbs(av["means"], av["log_scales"], av["quats"], av["joint_ids"].astype(np.int32),
+                            av["weights"], avatar_of, G.astype(np.float64))
+        ge = {k: np.concatenate([room[k], av[k]]).astype(np.float64) for k in keys}
+        ge["means"][n_room:] = pm
+        ge["cov3d"] = np.concatenate([np.zeros((n_room, 6)), pc])
+        ge["use_cov"] = np.concatenate([np.zeros(n_room, np.uint8), np.ones(len(pm), np.uint8)])
+        ge["inexact"] = ge["use_cov"]
+        compare_view(gpu_outputs(b, e), oracle.render(ge, cams[e], W, H))
+
+
+def test_fused_lbs_rejects_bad_layouts(gs):
+    W = H = 32
+    room = synth.room_scene(2000, seed=1)
+    av, G, avatar_of = make_avatars(1, 500, 3)
+    cat = {k: np.concatenate([room[k], av[k]]) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+    n = cat["means"].shape[0]
+    Gf = gs.Gaussians.from_numpy(cat)
+    ct = gs.cameras_tensor(synth.room_camera(1, W, H)[None])
+    A = gpu_avatars(gs, av, avatar_of, 1)
+    r = gs.Renderer(gs.Batch(np.array([0, n]), env_cov3d_begin=[2000 + 1]), W, H)  # 499 rows, 500 canonical
+    with pytest.raises(gs.GsError, match="INVALID_ARG"):
+        r.forward_avatars(Gf, A, T(G), ct)
+    r = gs.Renderer(gs.Batch(np.array([0, n])), W, H)  # no avatar rows declared
+    with pytest.raises(gs.GsError, match="INVALID_ARG"):
+        r.forward_avatars(Gf, A, T(G), ct)

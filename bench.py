@@ -369,6 +369,66 @@ def avatar_and_composite_rows(api, synth, torch, dev, stream, outs, hbm_peak):
             "composite": dict(hbm(comp_bytes, comp_ms), views=V, width=W, height=H)}
 
 
+def fused_avatar_row(api, synth, torch, dev, stream):
+    """Forward of 32 envs, each a 1M-Gaussian room plus 8 avatars of 50k
+    Gaussians posed per frame, 256x256: LBS fused into the preprocess
+    (gs_render_avatars) against gs_deform_avatars + gs_render."""
+    n_envs, n_room, n_av, n_per = 32, 1_000_000, 8, 50_000
+    g, offs, cams = synth.batched_rooms(n_envs, n_room, n_room, W, H, seed0=900)
+    base = [synth.avatar_canonical(n_per, k) for k in range(n_av)]
+    per_env = n_room + n_av * n_per
+    keys = ("means", "log_scales", "quats", "opacity_logits", "sh")
+    cat = {k: np.concatenate([np.concatenate([g[k][e * n_room:(e + 1) * n_room]] + [base[a][k] for a in range(n_av)])
+                              for e in range(n_envs)]) for k in keys}
+    del g
+    av = {k: np.concatenate([base[a][k] for _ in range(n_envs) for a in range(n_av)]) for k in base[0]}
+    m = n_envs * n_av * n_per
+    avatar_of = np.repeat(np.arange(n_envs * n_av), n_per).astype(np.int32)
+    dest = np.concatenate([e * per_env + n_room + np.arange(n_av * n_per) for e in range(n_envs)]).astype(np.int64)
+    Gj = np.stack([synth.random_pose(3 * e + a) for e in range(n_envs) for a in range(n_av)]).astype(np.float32)
+    for e in range(n_envs):  # the avatars stand in front of the env's camera
+        fwd, C = cams[e][6:9], cams[e][9:12]
+        for a in range(n_av):
+            k = e * n_av + a
+            root = C + fwd * (1.5 + 0.4 * a) + np.array([0.3 * (a % 3 - 1), 0.0, -0.3])
+            Gj[k, :, :, 3] += (root - Gj[k, 0, :, 3]).astype(np.float32)
+    T = lambda x, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(x)).to(dev, dt)  # noqa: E731
+    sh16 = T(cat.pop("sh")).to(torch.float16)
+    G = {k: T(v) for k, v in cat.items()}
+    del cat
+    cov = torch.zeros((n_envs * per_env, 6), device=dev)
+    means_posed = G["means"].clone()
+    A_unf = api.Avatars(T(av["means"]), T(av["log_scales"]), T(av["quats"]), T(av["joint_ids"].view(np.int16),
+                        torch.int16), T(av["weights"]), T(avatar_of, torch.int32), n_envs * n_av, synth.N_JOINTS,
+                        dest=T(dest, torch.int64))
+    A_fus = api.Avatars(*A_unf.t[:6], n_envs * n_av, synth.N_JOINTS)
+    Gjt = T(Gj)
+    batch = api.Batch(np.arange(n_envs + 1) * per_env, env_cov3d_begin=np.arange(n_envs) * per_env + n_room)
+    g_unf = api.Gaussians(means_posed, G["log_scales"], G["quats"], G["opacity_logits"], sh16, cov3d=cov)
+    g_fus = api.Gaussians(G["means"], G["log_scales"], G["quats"], G["opacity_logits"], sh16)
+    kw = dict(tile=(8, 8), batch_depth=64, pix=(2, 1), persistent=True)
+    r1 = api.Renderer(batch, W, H, device=dev, **kw)
+    r2 = api.Renderer(batch, W, H, device=dev, **kw)
+    ct = api.cameras_tensor(cams, dev)
+    o1, o2 = r1.alloc_outputs(), r2.alloc_outputs()
+
+    def unfused():
+        api.deform(A_unf, Gjt, means_posed, cov, stream=stream)
+        r1.forward(g_unf, ct, out=o1, stream=stream)
+
+    def fused():
+        r2.forward_avatars(g_fus, A_fus, Gjt, ct, out=o2, stream=stream)
+
+    ms_unf = _event_ms(torch, stream, unfused, 5)
+    ms_fus = _event_ms(torch, stream, fused, 5)
+    torch.cuda.synchronize()
+    same = all(bool(torch.equal(x, y)) for x, y in zip(o1, o2))
+    return {"workload": f"{n_envs} envs x (1M room + {n_av} avatars x 50k), {W}x{H}, forward", "gaussians": n_envs * per_env,
+            "avatar_gaussians": m, "unfused_ms": ms_unf, "fused_ms": ms_fus,
+            "unfused_env_frames_per_s": n_envs / (ms_unf * 1e-3), "fused_env_frames_per_s": n_envs / (ms_fus * 1e-3),
+            "bit_identical": same}
+
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -542,6 +602,8 @@ def run_ours(args, ws, rank, local):
     # timed on their own: 32 envs x 8 avatars x 50k Gaussians, and the
     # nearest-fragment merge of the bench frames with a second layer
     extra = avatar_and_composite_rows(api, synth, torch, dev, stream, outs, hbm_peak=peaks()[0])
+    if not args.no_avatar_scene:
+        extra["scene_with_avatars"] = fused_avatar_row(api, synth, torch, dev, stream)
 
     # --- CPU oracle on a bounded sample (rank 0, N = 1)
     cpu = None
@@ -596,6 +658,7 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0, help="scale the per-env Gaussian counts (testing only)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-avatar-scene", action="store_true", help="skip the 32-env rooms-with-avatars forward")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--tile", default="", help="fixed tile_w,tile_h,batch_depth instead of the autotuner")

@@ -102,9 +102,11 @@ def _bind(L):
     P = ctypes.c_void_p
     i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
     L.or_project.restype = i64
-    L.or_project.argtypes = [i64, P, P, P, P, P, P, P, P, P, i32, i32, f64] + [P] * 12
+    L.or_project.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, i32, i32, f64] + [P] * 12
     L.or_render.restype = i64
-    L.or_render.argtypes = [i64, P, P, P, P, P, P, P, P, P, i32, i32, f64, P, i32, i32, i32] + [P] * 6
+    L.or_render.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, i32, i32, f64, P, i32, i32, i32] + [P] * 6
+    L.or_lbs_matrices.restype = None
+    L.or_lbs_matrices.argtypes = [i64, P, P, P, P, i32, P]
     L.or_render_backward.restype = i32
     L.or_render_backward.argtypes = [i64, P, P, P, P, P, P, P, P, i32, i32, f64, P, P, P] + [P] * 6
     L.or_lbs.restype = None
@@ -157,6 +159,7 @@ def _gauss(g: dict):
         cov3d=cov,
         use_cov=use,
         inexact=_u8(g.get("inexact")),
+        dirmat=_f64(g.get("sh_dirmat"), (n, 9)) if g.get("sh_dirmat") is not None else None,
     )
 
 
@@ -182,7 +185,7 @@ def project(g: dict, cam, W: int, H: int, near: float = 0.2) -> dict:
         err_uv=np.zeros((n, 2)),
     )
     L.or_project(n, _p(G["means"]), _p(G["log_scales"]), _p(G["quats"]), _p(G["ologits"]), _p(G["sh"]),
-                 _p(G["cov3d"]), _p(G["use_cov"]), _p(G["inexact"]), _p(cam64), W, H, near,
+                 _p(G["cov3d"]), _p(G["use_cov"]), _p(G["inexact"]), _p(G["dirmat"]), _p(cam64), W, H, near,
                  _p(out["visible"]), _p(out["u"]), _p(out["v"]), _p(out["z"]), _p(out["zkey"]),
                  _p(out["cov2"]), _p(out["conic"]), _p(out["opacity"]), _p(out["rgb"]),
                  _p(out["radius"]), _p(out["r3"]), _p(out["err_uv"]))
@@ -206,7 +209,8 @@ def render(g: dict, cam, W: int, H: int, near: float = 0.2, bg=(0.0, 0.0, 0.0), 
     amb = np.zeros((H, W), np.uint8)
     last = np.zeros((H, W), np.int32)
     ev = L.or_render(G["n"], _p(G["means"]), _p(G["log_scales"]), _p(G["quats"]), _p(G["ologits"]), _p(G["sh"]),
-                     _p(G["cov3d"]), _p(G["use_cov"]), _p(G["inexact"]), _p(cam64), W, H, near, _p(bg64),
+                     _p(G["cov3d"]), _p(G["use_cov"]), _p(G["inexact"]), _p(G["dirmat"]), _p(cam64), W, H, near,
+                     _p(bg64),
                      0 if mode == "pixel" else 1, 1 if normalize_depth else 0, nthreads,
                      _p(rgb), _p(depth), _p(T), _p(ncon), _p(amb), _p(last))
     return dict(rgb=rgb, depth=depth, T=T, n_contrib=ncon, amb=amb, last=last, evals=int(ev))
@@ -244,6 +248,19 @@ def lbs(means_c, log_scales_c, quats_c, joint_ids, weights, avatar_of, G):
     L.or_lbs(m, _p(means_c), _p(_f64(log_scales_c)), _p(_f64(quats_c)), _p(ids), _p(_f64(weights)), _p(av),
              _p(G), nj, _p(om), _p(oc))
     return om, oc
+
+
+def lbs_matrices(joint_ids, weights, avatar_of, G):
+    """The blended skinning matrices A [m,3,4] of the avatar Gaussians."""
+    L = _lib()
+    G = _f64(G)
+    nj = G.shape[1]
+    ids = np.ascontiguousarray(np.asarray(joint_ids, np.int32).reshape(-1, 4))
+    m = ids.shape[0]
+    av = np.ascontiguousarray(np.asarray(avatar_of, np.int32).reshape(m))
+    out = np.zeros((m, 3, 4))
+    L.or_lbs_matrices(m, _p(ids), _p(_f64(weights)), _p(av), _p(G), nj, _p(out))
+    return out
 
 
 def lbs_backward(means_c, log_scales_c, quats_c, joint_ids, weights, avatar_of, G, g_means, g_cov):

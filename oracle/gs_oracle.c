@@ -279,7 +279,8 @@ static int footprint_on_image(double u, double v, int32_t r, int W, int H)
 
 /* Returns 0 when the Gaussian is culled by the near plane or a singular conic. */
 static int project_one(const double *mu, const double *ls, const double *q, double ologit, const double *sh,
-                       const double *cov3d, int inexact, const cam_t *k, int W, int H, double near_plane, proj_t *o)
+                       const double *cov3d, int inexact, const cam_t *k, int W, int H, double near_plane, proj_t *o,
+                       const double *dirmat)
 {
     memset(o, 0, sizeof(*o));
     memcpy(o->mu, mu, 3 * sizeof(double));
@@ -354,9 +355,19 @@ static int project_one(const double *mu, const double *ls, const double *q, doub
     o->visible = footprint_on_image(o->u, o->v, o->r, W, H);
     if (!o->cand) return 0;
     o->opacity = 1.0 / (1.0 + exp(-ologit));
-    double dn = sqrt(o->d[0] * o->d[0] + o->d[1] * o->d[1] + o->d[2] * o->d[2]);
+    /* SH direction: the unit view direction, or -- for a posed avatar
+     * Gaussian evaluated in its canonical frame -- M (mu - C) normalised,
+     * M the inverse of the skinning matrix's linear part */
+    double dv3[3];
+    if (dirmat) {
+        for (int r = 0; r < 3; ++r)
+            dv3[r] = dirmat[3 * r] * o->d[0] + dirmat[3 * r + 1] * o->d[1] + dirmat[3 * r + 2] * o->d[2];
+    } else {
+        for (int r = 0; r < 3; ++r) dv3[r] = o->d[r];
+    }
+    double dn = sqrt(dv3[0] * dv3[0] + dv3[1] * dv3[1] + dv3[2] * dv3[2]);
     o->dnorm = dn;
-    for (int i = 0; i < 3; ++i) o->dir[i] = o->d[i] / dn;
+    for (int i = 0; i < 3; ++i) o->dir[i] = dv3[i] / dn;
     double Y[16];
     sh_eval(o->dir, Y, NULL);
     for (int ch = 0; ch < 3; ++ch) {
@@ -371,7 +382,8 @@ static int project_one(const double *mu, const double *ls, const double *q, doub
 
 /* Exported per-Gaussian projection (one view). */
 int64_t or_project(int64_t n, const double *means, const double *log_scales, const double *quats, const double *ologits,
-                   const double *sh, const double *cov3d, const uint8_t *use_cov, const uint8_t *inexact, const double *cam,
+                   const double *sh, const double *cov3d, const uint8_t *use_cov, const uint8_t *inexact,
+                   const double *dirmat, const double *cam,
                    int32_t W, int32_t H, double near_plane, int32_t *visible, double *u, double *v, double *z, float *zkey,
                    double *cov2, double *conic, double *opacity, double *rgb, int32_t *radius, double *r3,
                    double *err_uv)
@@ -384,7 +396,7 @@ int64_t or_project(int64_t n, const double *means, const double *log_scales, con
         proj_t o;
         const double *cv = (cov3d && use_cov && use_cov[g]) ? cov3d + 6 * g : NULL;
         int ok = project_one(means + 3 * g, log_scales + 3 * g, quats + 4 * g, ologits[g], sh + 48 * g, cv,
-                             inexact ? inexact[g] : 0, &k, W, H, near_plane, &o);
+                             inexact ? inexact[g] : 0, &k, W, H, near_plane, &o, dirmat ? dirmat + 9 * g : NULL);
         int vis = ok && o.visible;
         visible[g] = vis;
         nvis += vis;
@@ -518,7 +530,7 @@ static int cand_cmp(const void *a, const void *b)
 
 static int64_t build_candidates(int64_t n, const double *means, const double *ls, const double *q, const double *ologit,
                                 const double *sh, const double *cov3d, const uint8_t *use_cov, const uint8_t *inexact,
-                                const cam_t *k, int W, int H, double near_plane, cand_t **out)
+                                const double *dirmat, const cam_t *k, int W, int H, double near_plane, cand_t **out)
 {
     cand_t *c = (cand_t *)malloc(sizeof(cand_t) * (size_t)(n > 0 ? n : 1));
     uint8_t *ok = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
@@ -527,7 +539,8 @@ static int64_t build_candidates(int64_t n, const double *means, const double *ls
         proj_t o;
         const double *cv = (cov3d && use_cov && use_cov[g]) ? cov3d + 6 * g : NULL;
         int inx = inexact ? inexact[g] : 0;
-        if (!project_one(means + 3 * g, ls + 3 * g, q + 4 * g, ologit[g], sh + 48 * g, cv, inx, k, W, H, near_plane, &o))
+        if (!project_one(means + 3 * g, ls + 3 * g, q + 4 * g, ologit[g], sh + 48 * g, cv, inx, k, W, H, near_plane, &o,
+                         dirmat ? dirmat + 9 * g : NULL))
             continue;
         ok[g] = 1;
         cand_t *t = c + g;
@@ -606,14 +619,16 @@ static int64_t walk_gaussian_major(const cand_t *c, int64_t m, int W, int H, pix
  * candidates; mode 1: the Gaussian-major walk.  Returns the number of
  * evaluations (covered Gaussians examined before each pixel stopped). */
 int64_t or_render(int64_t n, const double *means, const double *log_scales, const double *quats, const double *ologits,
-                  const double *sh, const double *cov3d, const uint8_t *use_cov, const uint8_t *inexact, const double *cam,
+                  const double *sh, const double *cov3d, const uint8_t *use_cov, const uint8_t *inexact,
+                  const double *dirmat, const double *cam,
                   int32_t W, int32_t H, double near_plane, const double *bg, int32_t mode, int32_t flags, int32_t nthreads,
                   double *out_rgb, double *out_depth, double *out_T, int32_t *out_n, uint8_t *out_amb, int32_t *out_last)
 {
     cam_t k;
     load_cam(cam, &k);
     cand_t *c = NULL;
-    int64_t m = build_candidates(n, means, log_scales, quats, ologits, sh, cov3d, use_cov, inexact, &k, W, H, near_plane, &c);
+    int64_t m = build_candidates(n, means, log_scales, quats, ologits, sh, cov3d, use_cov, inexact, dirmat, &k, W, H,
+                                 near_plane, &c);
     int64_t HW = (int64_t)W * H;
     pix_t *st = (pix_t *)malloc(sizeof(pix_t) * (size_t)HW);
     for (int64_t p = 0; p < HW; ++p) pix_init(st + p);
@@ -753,7 +768,8 @@ int32_t or_render_backward(int64_t n, const double *means, const double *log_sca
     cam_t k;
     load_cam(cam, &k);
     cand_t *c = NULL;
-    int64_t m = build_candidates(n, means, log_scales, quats, ologits, sh, cov3d, use_cov, NULL, &k, W, H, near_plane, &c);
+    int64_t m = build_candidates(n, means, log_scales, quats, ologits, sh, cov3d, use_cov, NULL, NULL, &k, W, H,
+                                 near_plane, &c);
     int64_t HW = (int64_t)W * H;
     pix_t *st = (pix_t *)malloc(sizeof(pix_t) * (size_t)HW);
     for (int64_t p = 0; p < HW; ++p) pix_init(st + p);
@@ -819,7 +835,7 @@ int32_t or_render_backward(int64_t n, const double *means, const double *log_sca
         proj_t o;
         int uc = (cov3d && use_cov && use_cov[g]) ? 1 : 0;
         project_one(means + 3 * g, log_scales + 3 * g, quats + 4 * g, ologits[g], sh + 48 * g, uc ? cov3d + 6 * g : NULL, 0,
-                    &k, W, H, near_plane, &o);
+                    &k, W, H, near_plane, &o, NULL);
         preprocess_vjp(&o, gr + kk, log_scales + 3 * g, quats + 4 * g, sh + 48 * g, uc, &k, g_means + 3 * g,
                        g_log_scales + 3 * g, g_quats + 4 * g, g_ologits + g, g_sh + 48 * g,
                        g_cov3d ? g_cov3d + 6 * g : NULL);
@@ -844,6 +860,14 @@ static void blend_joints(const int32_t *ids, const double *w, const double *Gav,
         const double *Gj = Gav + 12 * ids[kk];
         for (int e = 0; e < 12; ++e) A[e] += w[kk] * Gj[e];
     }
+}
+
+/* The blended skinning matrices A = sum_k w_k G[avatar][j_k] (3x4 each). */
+void or_lbs_matrices(int64_t m, const int32_t *joint_ids, const double *weights, const int32_t *avatar_of,
+                     const double *G, int32_t n_joints, double *out_A)
+{
+    for (int64_t g = 0; g < m; ++g)
+        blend_joints(joint_ids + 4 * g, weights + 4 * g, G + (int64_t)12 * n_joints * avatar_of[g], out_A + 12 * g);
 }
 
 void or_lbs(int64_t m, const double *means_c, const double *log_scales_c, const double *quats_c, const int32_t *joint_ids,

@@ -61,6 +61,10 @@ MUTANTS = [
      "mat3_mul(Rl + 9 * j, GR + 9 * p, GR + 9 * j);", drive.test_fk_root_equivariance),
     ("FK: skinning matrix without the rest offset", "t -= GR[9 * j + 3 * r + c] * rest[3 * j + c];", "",
      drive.test_fk_zero_pose_is_identity),
+    ("SH direction matrix transposed",
+     "dv3[r] = dirmat[3 * r] * o->d[0] + dirmat[3 * r + 1] * o->d[1] + dirmat[3 * r + 2] * o->d[2];",
+     "dv3[r] = dirmat[r] * o->d[0] + dirmat[r + 3] * o->d[1] + dirmat[r + 6] * o->d[2];",
+     drive.test_sh_direction_matrix),
     ("interpolation weights swapped", "o[e] = (1.0 - w) * A0[e] + w * A1[e];", "o[e] = w * A0[e] + (1.0 - w) * A1[e];",
      drive.test_interpolation_between_frames),
     ("adjoint: LBS covariance factor", "gA[4 * r + cc] = gm[r] * mu[cc] + 2.0 * acc;",

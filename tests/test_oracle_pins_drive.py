@@ -160,3 +160,33 @@ def test_composite_of_two_renders_matches_the_joint_render_where_opaque(oracle):
     # where the near layer is absent the far layer shows through unchanged
     absent = rn["T"] == 1.0
     np.testing.assert_array_equal(rgb[0][:, absent], rf["rgb"][:, absent])
+
+
+def test_sh_direction_matrix(oracle):
+    """Colour of a posed avatar Gaussian evaluated in its canonical frame: the
+    SH direction is M (mu - C) normalised.  Identity (or any positive scaling)
+    changes nothing; a rotation gives the closed-form degree-1 colour."""
+    rng = np.random.default_rng(9)
+    n = 200
+    g = synth.box_scene(n, seed=9)
+    cam = synth.identity_camera(64, 64)
+    base = oracle.render(g, cam, 64, 64)
+    r = oracle.render(dict(g, sh_dirmat=np.tile(np.eye(3).reshape(1, 9), (n, 1))), cam, 64, 64)
+    for k in ("rgb", "depth", "T", "n_contrib"):
+        np.testing.assert_array_equal(r[k], base[k])
+    r = oracle.render(dict(g, sh_dirmat=np.tile(2.5 * np.eye(3).reshape(1, 9), (n, 1))), cam, 64, 64)
+    np.testing.assert_allclose(r["rgb"], base["rgb"], rtol=0, atol=1e-13)
+    np.testing.assert_array_equal(r["n_contrib"], base["n_contrib"])
+    # one Gaussian on the optical axis: direction (0, 0, 1), rotated by M
+    k0 = np.array([0.3, -0.1, 0.2])
+    k1 = rng.normal(0, 0.3, (3, 3))  # rows: the three degree-1 functions, columns: channels
+    sh = np.zeros((1, 16, 3))
+    sh[0, 0], sh[0, 1:4] = k0, k1
+    one = dict(means=np.array([[0.0, 0.0, 3.0]]), log_scales=np.full((1, 3), -2.0), quats=np.array([[1.0, 0, 0, 0]]),
+               opacity_logits=np.zeros(1), sh=sh)
+    M = Rotation.from_rotvec([0.4, -0.7, 0.2]).as_matrix()
+    x, y, z = M @ np.array([0.0, 0.0, 1.0])
+    c0, c1 = 0.5 / math.sqrt(math.pi), math.sqrt(3.0 / (4.0 * math.pi))
+    expect = np.maximum(0.0, 0.5 + c0 * k0 + c1 * (-y * k1[0] + z * k1[1] - x * k1[2]))
+    p = oracle.project(dict(one, sh_dirmat=M.reshape(1, 9)), cam, 64, 64)
+    np.testing.assert_allclose(p["rgb"][0], expect, atol=1e-14)

@@ -65,6 +65,10 @@ typedef int32_t gs_status;
                                      Gaussian is seen by no view) instead of adding to it */
 #define GS_FLAG_COUNT_EVALS 8     /* the forward also counts blend evaluations into
                                      gs_stats.n_evaluations (one atomic per warp and tile) */
+#define GS_FLAG_AVATAR_CANONICAL_SH 16 /* gs_render_avatars: evaluate an avatar Gaussian's SH at
+                                     A3^-1 (mu' - C) normalised, the view direction in its
+                                     canonical frame (A3: linear part of its skinning matrix);
+                                     without it, at the world view direction */
 
 #define GS_MAX_ENVS 512
 #define GS_MAX_VIEWS 512

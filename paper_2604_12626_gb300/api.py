@@ -22,7 +22,7 @@ GS_OK = 0
 STATUS_NAMES = {0: "GS_OK", -1: "GS_ERR_INVALID_ARG", -2: "GS_ERR_ALIGNMENT", -3: "GS_ERR_WORKSPACE_TOO_SMALL",
                 -4: "GS_ERR_CAPACITY", -5: "GS_ERR_CUDA", -6: "GS_ERR_TIMEOUT", -7: "GS_ERR_UNSUPPORTED"}
 SH_F32, SH_F16, SH_BF16 = 0, 1, 2
-FLAG_PERSISTENT, FLAG_NORMALIZE_DEPTH, FLAG_GRAD_OVERWRITE, FLAG_COUNT_EVALS = 1, 2, 4, 8
+FLAG_PERSISTENT, FLAG_NORMALIZE_DEPTH, FLAG_GRAD_OVERWRITE, FLAG_COUNT_EVALS, FLAG_AVATAR_CANONICAL_SH = 1, 2, 4, 8, 16
 N_STAGES = 11
 STAGES = ("setup", "preprocess", "scan", "scatter", "sort", "merge", "blend", "blend_backward",
           "preprocess_backward", "deform", "deform_backward")

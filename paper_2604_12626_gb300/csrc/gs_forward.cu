@@ -65,6 +65,29 @@ struct GaussIn {
     int32_t n_avatars, n_joints;
 };
 
+// The SH direction of a posed avatar Gaussian evaluated in its canonical
+// frame: A3^-1 (mu' - C), A3 the linear part of its blended skinning matrix
+// (inverse by the adjugate; the length does not matter, the colour normalises).
+__device__ __forceinline__ void canonical_direction(const GaussIn &gin, int64_t i, float &d0, float &d1, float &d2)
+{
+    const int a = clamp_avatar(__ldg(gin.av_of + i), gin.n_avatars);
+    const ushort4 id = clamp_ids(__ldg(reinterpret_cast<const ushort4 *>(gin.av_ids) + i), gin.n_joints);
+    float A[12];
+    blend_matrix(gin.av_G + (size_t)a * gin.n_joints * 12, id, __ldg(reinterpret_cast<const float4 *>(gin.av_weights) + i),
+                 A);
+    const float a00 = A[0], a01 = A[1], a02 = A[2], a10 = A[4], a11 = A[5], a12 = A[6], a20 = A[8], a21 = A[9],
+                a22 = A[10];
+    const float c00 = a11 * a22 - a12 * a21, c01 = a02 * a21 - a01 * a22, c02 = a01 * a12 - a02 * a11;
+    const float c10 = a12 * a20 - a10 * a22, c11 = a00 * a22 - a02 * a20, c12 = a02 * a10 - a00 * a12;
+    const float c20 = a10 * a21 - a11 * a20, c21 = a01 * a20 - a00 * a21, c22 = a00 * a11 - a01 * a10;
+    const float det = a00 * c00 + a01 * c10 + a02 * c20;
+    const float s = det < 0.0f ? -1.0f : 1.0f; // adj = det A^-1: keep the orientation of A^-1
+    const float x = d0, y = d1, z = d2;
+    d0 = s * (c00 * x + c01 * y + c02 * z);
+    d1 = s * (c10 * x + c11 * y + c12 * z);
+    d2 = s * (c20 * x + c21 * y + c22 * z);
+}
+
 // Every preprocess / scatter CTA owns a chunk of kChunk consecutive Gaussians.
 // Per-(view, tile) counts and cursors of a chunk that lies inside one env are
 // aggregated in shared memory, so that global atomics are one per (CTA, bin)
@@ -251,6 +274,9 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(const gs_cam
                             en.uc = pj.uc; en.vc = pj.vc; en.zk = zk; en.r = r;
                             en.A = pj.c * idet; en.B = -pj.b * idet; en.C = pj.a * idet;
                             en.d0 = pj.d0; en.d1 = pj.d1; en.d2 = pj.d2;
+                            if (gin.av_G && (tb->flags & GS_FLAG_AVATAR_CANONICAL_SH) && g >= cov_begin)
+                                canonical_direction(gin, tb->env_av_base[c.e0] + (g - cov_begin), en.d0, en.d1,
+                                                    en.d2);
                             en.x0 = (uint16_t)x0; en.x1 = (uint16_t)x1; en.y0 = (uint16_t)y0; en.y1 = (uint16_t)y1;
                             en.v = (uint16_t)(cam_smem ? tb->env_views[c.vb + k] : v); en.k = (uint16_t)k;
                         }

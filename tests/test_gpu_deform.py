@@ -201,3 +201,44 @@ def test_fused_lbs_rejects_bad_layouts(gs):
     r = gs.Renderer(gs.Batch(np.array([0, n])), W, H)  # no avatar rows declared
     with pytest.raises(gs.GsError, match="INVALID_ARG"):
         r.forward_avatars(Gf, A, T(G), ct)
+
+
+def test_fused_lbs_canonical_sh_direction(gs, oracle):
+    """GS_FLAG_AVATAR_CANONICAL_SH: the avatars' SH evaluated at A3^-1 (mu' - C)
+    against the oracle with that direction matrix; it differs from the world
+    direction render wherever the avatars show."""
+    W = H = 96
+    n_room, n_av, n_avatars = 20_000, 4000, 2
+    room = synth.room_scene(n_room, seed=810)
+    av, G, avatar_of = make_avatars(n_avatars, n_av, 90)
+    av["sh"][:, 1:4] += np.random.default_rng(5).normal(0, 0.4, (n_av * n_avatars, 3, 3)).astype(np.float32)
+    cam = synth.room_camera(810, W, H)
+    fwd, C = cam[6:9], cam[9:12]
+    for k in range(n_avatars):
+        root = C + fwd * (1.8 + 0.6 * k) + np.array([0.0, 0.0, -0.3])
+        G[k, :, :, 3] += (root - G[k, 0, :, 3]).astype(np.float32)
+    keys = ("means", "log_scales", "quats", "opacity_logits", "sh")
+    cat = {k: np.concatenate([room[k], av[k]]) for k in keys}
+    n = cat["means"].shape[0]
+    batch = gs.Batch(np.array([0, n]), env_cov3d_begin=[n_room])
+    A = gpu_avatars(gs, av, avatar_of, n_avatars)
+    ct = gs.cameras_tensor(cam[None])
+    r = gs.Renderer(batch, W, H)
+    world = [x.clone() for x in r.forward_avatars(gs.Gaussians.from_numpy(cat), A, T(G), ct)]
+    r.cfg.flags |= gs.FLAG_AVATAR_CANONICAL_SH
+    canon = r.forward_avatars(gs.Gaussians.from_numpy(cat), A, T(G), ct)
+    torch.cuda.synchronize()
+    ids = av["joint_ids"].astype(np.int32)
+    pm, pc = oracle.lbs(av["means"], av["log_scales"], av["quats"], ids, av["weights"], avatar_of,
+                        G.astype(np.float64))
+    Am = oracle.lbs_matrices(ids, av["weights"], avatar_of, G.astype(np.float64))
+    dirmat = np.concatenate([np.tile(np.eye(3).reshape(1, 9), (n_room, 1)),
+                             np.linalg.inv(Am[:, :, :3]).reshape(-1, 9)])
+    ge = {k: cat[k].astype(np.float64) for k in keys}
+    ge["means"][n_room:] = pm
+    ge.update(cov3d=np.concatenate([np.zeros((n_room, 6)), pc]),
+              use_cov=np.concatenate([np.zeros(n_room, np.uint8), np.ones(len(pm), np.uint8)]))
+    ge["inexact"] = ge["use_cov"]
+    compare_view(gpu_outputs(canon, 0), oracle.render(dict(ge, sh_dirmat=dirmat), cam, W, H))
+    assert not torch.equal(world[0], canon[0])  # the canonical direction changes the avatars' colour
+    assert torch.equal(world[1], canon[1])  # and nothing else

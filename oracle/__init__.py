@@ -117,6 +117,8 @@ def _bind(L):
     L.or_sh_basis.argtypes = [i64, P, P]
     L.or_quat_to_rot.restype = None
     L.or_quat_to_rot.argtypes = [P, P]
+    L.or_raster_mesh.restype = None
+    L.or_raster_mesh.argtypes = [i64, P, P, i64, P, P, i32, i32, f64, P, P, P, P]
     L.or_composite_nearest.restype = None
     L.or_composite_nearest.argtypes = [i64, i64, P, P, P, P, P, P]
     L.or_forward_kinematics.restype = None
@@ -277,6 +279,18 @@ def lbs_backward(means_c, log_scales_c, quats_c, joint_ids, weights, avatar_of, 
                       _p(av), _p(G), nj, _p(_f64(g_means)), _p(_f64(g_cov)), _p(out["means"]),
                       _p(out["log_scales"]), _p(out["quats"]), _p(out["G"]))
     return out
+
+
+def raster_mesh(verts, colors, tris, cam, W: int, H: int, near: float = 0.2, bg=(0.0, 0.0, 0.0)) -> dict:
+    """z-buffered triangle mesh layer: rgb [3,H,W], depth [H,W] (0 where
+    uncovered), amb [H,W] (1 where FP32 rounding could change the pixel)."""
+    L = _lib()
+    v = _f64(verts)
+    tr = np.ascontiguousarray(np.asarray(tris, np.int32).reshape(-1, 3))
+    rgb, depth, amb = np.zeros((3, H, W)), np.zeros((H, W)), np.zeros((H, W), np.uint8)
+    L.or_raster_mesh(v.shape[0], _p(v), _p(_f64(colors)), tr.shape[0], _p(tr), _p(_f64(np.asarray(cam, np.float32))),
+                     W, H, near, _p(_f64(bg)), _p(rgb), _p(depth), _p(amb))
+    return dict(rgb=rgb, depth=depth, amb=amb)
 
 
 def composite_nearest(rgb_a, depth_a, rgb_b, depth_b):

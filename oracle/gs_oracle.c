@@ -1040,4 +1040,97 @@ void or_interpolate_frames(int32_t n_avatars, int32_t n_frames, int32_t n_joints
     }
 }
 
+/* ------------------------------------------------------------------------
+ * Triangle-mesh layer (the mesh pass whose colour and depth the composite of
+ * Sec. 3.2 merges with the Gaussian pass).  Reading of a plain z-buffered
+ * rasteriser:
+ *   q_k = R (P_k - C); a triangle with any q_k.z <= near is culled;
+ *   s_k = (fx q.x / q.z + cx, fy q.y / q.z + cy);
+ *   pixel (i, j) is covered iff its centre lies inside or on the edge of the
+ *   screen triangle (edge functions of one sign with the area, zero allowed);
+ *   screen barycentrics l_k, perspective-correct w_k = l_k / z_k,
+ *   depth z = 1 / sum w_k, colour = z sum w_k c_k (per-vertex colours);
+ *   the smallest depth wins, equal depths keep the lower triangle index.
+ * Uncovered pixels get bg and depth 0.  amb flags pixels whose coverage by
+ * some triangle, or whose winner, FP32 rounding could change.
+ * verts [V,3], colors [V,3], tris [T,3] -> rgb [3,H,W], depth [H,W].
+ * ------------------------------------------------------------------------ */
+void or_raster_mesh(int64_t n_verts, const double *verts, const double *colors, int64_t n_tris, const int32_t *tris,
+                    const double *cam, int32_t W, int32_t H, double near_plane, const double *bg, double *out_rgb,
+                    double *out_depth, uint8_t *out_amb)
+{
+    cam_t k;
+    load_cam(cam, &k);
+    (void)n_verts;
+    const int64_t HW = (int64_t)W * H;
+    /* per-triangle screen data */
+    double *sx = (double *)malloc((size_t)(n_tris > 0 ? n_tris : 1) * 3 * sizeof(double));
+    double *sy = (double *)malloc((size_t)(n_tris > 0 ? n_tris : 1) * 3 * sizeof(double));
+    double *sz = (double *)malloc((size_t)(n_tris > 0 ? n_tris : 1) * 3 * sizeof(double));
+    uint8_t *live = (uint8_t *)calloc((size_t)(n_tris > 0 ? n_tris : 1), 1);
+    for (int64_t t = 0; t < n_tris; ++t) {
+        int ok = 1;
+        for (int a = 0; a < 3; ++a) {
+            const double *P = verts + 3 * tris[3 * t + a];
+            double d[3] = {P[0] - k.C[0], P[1] - k.C[1], P[2] - k.C[2]};
+            double q[3];
+            for (int r = 0; r < 3; ++r) q[r] = k.R[3 * r] * d[0] + k.R[3 * r + 1] * d[1] + k.R[3 * r + 2] * d[2];
+            if (!(q[2] > near_plane)) ok = 0;
+            sz[3 * t + a] = q[2];
+            sx[3 * t + a] = k.fx * q[0] / q[2] + k.cx;
+            sy[3 * t + a] = k.fy * q[1] / q[2] + k.cy;
+        }
+        double area = (sx[3 * t + 1] - sx[3 * t]) * (sy[3 * t + 2] - sy[3 * t]) -
+                      (sy[3 * t + 1] - sy[3 * t]) * (sx[3 * t + 2] - sx[3 * t]);
+        live[t] = ok && area != 0.0;
+    }
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t p = 0; p < HW; ++p) {
+        const double px = (double)(p % W), py = (double)(p / W);
+        double best = INFINITY, second = INFINITY, col[3] = {bg[0], bg[1], bg[2]};
+        uint8_t amb = 0;
+        for (int64_t t = 0; t < n_tris; ++t) {
+            if (!live[t]) continue;
+            const double *X = sx + 3 * t, *Y = sy + 3 * t, *Z = sz + 3 * t;
+            const double area = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0]);
+            double e[3], scale[3];
+            for (int a = 0; a < 3; ++a) {
+                const int b = (a + 1) % 3;
+                e[a] = (X[b] - X[a]) * (py - Y[a]) - (Y[b] - Y[a]) * (px - X[a]);
+                scale[a] = (fabs(X[b] - X[a]) + fabs(Y[b] - Y[a])) * (fabs(px - X[a]) + fabs(py - Y[a]) + 1.0);
+            }
+            const double sgn = area > 0.0 ? 1.0 : -1.0;
+            int inside = 1, near_edge = 0;
+            for (int a = 0; a < 3; ++a) {
+                if (sgn * e[a] < 0.0) inside = 0;
+                /* FP32 screen positions and edge products: a few 1e-7 relative */
+                if (fabs(e[a]) <= 1e-5 * scale[a] + 1e-6) near_edge = 1;
+            }
+            if (near_edge) amb = 1;
+            if (!inside) continue;
+            /* barycentrics: the edge opposite each vertex over the area */
+            const double l0 = e[1] / area, l1 = e[2] / area, l2 = e[0] / area;
+            const double w0 = l0 / Z[0], w1 = l1 / Z[1], w2 = l2 / Z[2];
+            const double z = 1.0 / (w0 + w1 + w2);
+            if (z < best) {
+                second = best;
+                best = z;
+                const int32_t *tv = tris + 3 * t;
+                for (int c = 0; c < 3; ++c)
+                    col[c] = z * (w0 * colors[3 * tv[0] + c] + w1 * colors[3 * tv[1] + c] + w2 * colors[3 * tv[2] + c]);
+            } else if (z < second) {
+                second = z;
+            }
+        }
+        if (second - best <= 1e-5 * best) amb = 1;
+        for (int c = 0; c < 3; ++c) out_rgb[c * HW + p] = col[c];
+        out_depth[p] = best < INFINITY ? best : 0.0;
+        out_amb[p] = amb;
+    }
+    free(sx);
+    free(sy);
+    free(sz);
+    free(live);
+}
+
 int32_t or_abi_version(void) { return 1; }

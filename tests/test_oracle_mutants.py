@@ -65,6 +65,14 @@ MUTANTS = [
      "dv3[r] = dirmat[3 * r] * o->d[0] + dirmat[3 * r + 1] * o->d[1] + dirmat[3 * r + 2] * o->d[2];",
      "dv3[r] = dirmat[r] * o->d[0] + dirmat[r + 3] * o->d[1] + dirmat[r + 6] * o->d[2];",
      drive.test_sh_direction_matrix),
+    ("mesh: barycentric of the wrong edge", "const double l0 = e[1] / area, l1 = e[2] / area, l2 = e[0] / area;",
+     "const double l0 = e[0] / area, l1 = e[1] / area, l2 = e[2] / area;",
+     drive.test_mesh_depth_is_the_ray_plane_intersection_and_colour_the_surface_point),
+    ("mesh: depth interpolated in screen space", "const double z = 1.0 / (w0 + w1 + w2);",
+     "const double z = l0 * Z[0] + l1 * Z[1] + l2 * Z[2];",
+     drive.test_mesh_depth_is_the_ray_plane_intersection_and_colour_the_surface_point),
+    ("mesh: equal depths keep the later triangle", "            if (z < best) {\n                second = best;",
+     "            if (z <= best) {\n                second = best;", drive.test_mesh_occlusion_ties_and_near_cull),
     ("interpolation weights swapped", "o[e] = (1.0 - w) * A0[e] + w * A1[e];", "o[e] = w * A0[e] + (1.0 - w) * A1[e];",
      drive.test_interpolation_between_frames),
     ("adjoint: LBS covariance factor", "gA[4 * r + cc] = gm[r] * mu[cc] + 2.0 * acc;",

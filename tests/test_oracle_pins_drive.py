@@ -190,3 +190,69 @@ def test_sh_direction_matrix(oracle):
     expect = np.maximum(0.0, 0.5 + c0 * k0 + c1 * (-y * k1[0] + z * k1[1] - x * k1[2]))
     p = oracle.project(dict(one, sh_dirmat=M.reshape(1, 9)), cam, 64, 64)
     np.testing.assert_allclose(p["rgb"][0], expect, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# triangle-mesh layer (the mesh pass of the composite, Sec. 3.2)
+# ---------------------------------------------------------------------------
+def _ray(i, j, f, c):
+    return np.stack([(i - c) / f, (j - c) / f, np.ones_like(i)], -1)
+
+
+def test_mesh_depth_is_the_ray_plane_intersection_and_colour_the_surface_point(oracle):
+    W, f = 48, 30.0
+    c = (W - 1) / 2
+    cam = synth.identity_camera(W, W)
+    cam[12:16] = [f, f, c, c]
+    P = np.array([[-1.2, -0.9, 3.0], [1.4, -0.5, 4.5], [-0.2, 1.3, 2.2]])
+    m = oracle.raster_mesh(P, P * 0.1, [[0, 1, 2]], cam, W, W)  # colour = 0.1 x the vertex position
+    jj, ii = np.mgrid[0:W, 0:W].astype(np.float64)
+    r = _ray(ii, jj, f, c)
+    n = np.cross(P[1] - P[0], P[2] - P[0])
+    t = (n @ P[0]) / (r @ n)
+    cov = (m["depth"] > 0) & (m["amb"] == 0)
+    assert cov.sum() > 200
+    np.testing.assert_allclose(m["depth"][cov], t[cov], rtol=1e-12)
+    surf = r * t[..., None] * 0.1
+    np.testing.assert_allclose(np.moveaxis(m["rgb"], 0, -1)[cov], surf[cov], rtol=1e-11, atol=1e-13)
+
+
+def test_mesh_coverage_of_a_right_triangle(oracle):
+    W, f = 40, 20.0
+    c = (W - 1) / 2
+    cam = synth.identity_camera(W, W)
+    cam[12:16] = [f, f, c, c]
+    z, x0, y0, L = 2.0, 5.5, 7.5, 20.0  # screen vertices (x0, y0), (x0 + L, y0), (x0, y0 + L)
+    scr = np.array([[x0, y0], [x0 + L, y0], [x0, y0 + L]])
+    P = np.concatenate([(scr - c) / f * z, np.full((3, 1), z)], 1)
+    m = oracle.raster_mesh(P, np.ones((3, 3)), [[0, 1, 2]], cam, W, W, bg=(0.2, 0.2, 0.2))
+    jj, ii = np.mgrid[0:W, 0:W]
+    want = (ii >= x0) & (jj >= y0) & ((ii - x0) + (jj - y0) <= L)
+    ok = m["amb"] == 0
+    np.testing.assert_array_equal((m["depth"] > 0)[ok], want[ok])
+    np.testing.assert_allclose(m["depth"][want & ok], z, rtol=1e-14)
+    np.testing.assert_allclose(m["rgb"][:, ~want], 0.2)
+    assert np.all(((ii - x0) + (jj - y0))[~ok] == L)  # only centres on the hypotenuse's line are flagged
+
+
+def test_mesh_occlusion_ties_and_near_cull(oracle):
+    W, f = 32, 16.0
+    c = (W - 1) / 2
+    cam = synth.identity_camera(W, W)
+    cam[12:16] = [f, f, c, c]
+    quad = lambda z, s: np.array([[-s, -s, z], [s, -s, z], [s, s, z], [-s, s, z]])  # noqa: E731
+    V = np.concatenate([quad(3.0, 2.0), quad(2.0, 0.8), quad(2.0, 0.8), [[0, 0, 0.1], [1, 0, 3], [0, 1, 3]]])
+    col = np.concatenate([np.full((4, 3), 0.1), np.full((4, 3), 0.5), np.full((4, 3), 0.9), np.full((3, 3), 0.7)])
+    T = [[0, 1, 2], [0, 2, 3], [4, 5, 6], [4, 6, 7], [8, 9, 10], [8, 10, 11], [12, 13, 14]]
+    m = oracle.raster_mesh(V, col, T, cam, W, W)
+    ok = m["amb"] == 0
+    front = (np.abs(np.mgrid[0:W, 0:W][1] - c) < 0.8 / 2.0 * f - 0.5) & (np.abs(np.mgrid[0:W, 0:W][0] - c) < 0.8 / 2.0 * f - 0.5)
+    assert front.sum() > 20
+    # (inside the near quad, away from its edges: the exact tie between the two
+    # copies is flagged for FP32, but the definition decides it by index)
+    np.testing.assert_allclose(m["depth"][front], 2.0)  # the near quad hides the far one
+    np.testing.assert_allclose(m["rgb"][:, front], 0.5)  # equal depths: the lower triangle index wins
+    back = (m["depth"] > 2.5) & ok
+    assert back.sum() > 100
+    np.testing.assert_allclose(m["rgb"][:, back], 0.1)
+    assert not np.any(np.isclose(m["rgb"][0], 0.7))  # the triangle through the near plane is culled

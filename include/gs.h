@@ -250,6 +250,34 @@ gs_status gs_composite_nearest(const float *rgb_a, const float *depth_a, const f
                                int32_t n_views, int32_t height, int32_t width, float *rgb_out, float *depth_out,
                                void *stream);
 
+/* A triangle mesh with per-vertex colours (device): the mesh layer of a scene
+ * that mixes meshes with 3DGS assets (Sec. 3.2). */
+typedef struct {
+    const float *vertices;    /* [V,3] world positions */
+    const float *colors;      /* [V,3] linear RGB */
+    const int32_t *triangles; /* [T,3] vertex indices */
+    int64_t n_vertices, n_triangles;
+} gs_mesh;
+
+/* Workspace bytes of gs_render_mesh: 96 bytes per (view, triangle of its env). */
+gs_status gs_mesh_workspace_size(const gs_batch *batch, size_t *bytes);
+
+/* The mesh pass (Sec. 3.2: the colour and depth of the mesh layer that the
+ * full-screen composite merges with the Gaussian pass), rasterised by CUDA
+ * kernels instead of a graphics API.  Per view, with the camera of gs_render:
+ * q = R (P - C); a triangle with a vertex at q.z <= near_plane (<= 0: 0.2) is
+ * culled (no clipping); a pixel is covered when its centre lies inside or on
+ * the edge of the projected triangle; depth is the perspective-correct
+ * view-space z, colour the perspective-correct interpolation of the vertex
+ * colours; the smallest depth wins, the lower triangle index on a tie.
+ * batch: env_offsets index TRIANGLES (env e's triangles [env_offsets[e],
+ * env_offsets[e+1])), view_env as for gs_render (host).  Uncovered pixels get
+ * bg (host float[3], NULL for black) and depth 0, so the output is a layer
+ * for gs_composite_nearest.  out_rgb [V,3,H,W], out_depth [V,H,W] (device). */
+gs_status gs_render_mesh(const gs_mesh *mesh, const gs_batch *batch, const gs_camera *cams, int32_t width,
+                         int32_t height, const float *bg, float near_plane, void *workspace, size_t workspace_bytes,
+                         float *out_rgb, float *out_depth, void *stream);
+
 /* Skinning matrices of A avatars by forward kinematics of one joint tree
  * (Sec. 3.3.1: the per-frame SMPL-X joint matrices that drive the LBS kernel):
  *   G_0 = [R_root R_0 | t_root],  G_j = G_parent(j) [R_j | J_j - J_parent(j)],

@@ -71,6 +71,11 @@ class GsAvatars(ctypes.Structure):
                 ("n_joints", ctypes.c_int32)]
 
 
+class GsMesh(ctypes.Structure):
+    _fields_ = [("vertices", _P), ("colors", _P), ("triangles", _P), ("n_vertices", ctypes.c_int64),
+                ("n_triangles", ctypes.c_int64)]
+
+
 _R = ctypes.POINTER
 _lib.gs_render_workspace_size.argtypes = [_R(GsRenderConfig), _R(GsBatch), _R(ctypes.c_size_t)]
 _lib.gs_render.argtypes = [_R(GsGaussians), _R(GsBatch), _P, _R(GsRenderConfig), _P, ctypes.c_size_t, _P, _P, _P, _P,
@@ -80,6 +85,9 @@ _lib.gs_render_backward.argtypes = [_R(GsGaussians), _R(GsBatch), _P, _R(GsRende
 _lib.gs_deform_avatars.argtypes = [_R(GsAvatars), _P, _P, _P, _P]
 _lib.gs_render_avatars.argtypes = [_R(GsGaussians), _R(GsBatch), _R(GsAvatars), _P, _P, _R(GsRenderConfig), _P,
                                    ctypes.c_size_t, _P, _P, _P, _P, _P]
+_lib.gs_mesh_workspace_size.argtypes = [_R(GsBatch), _R(ctypes.c_size_t)]
+_lib.gs_render_mesh.argtypes = [_R(GsMesh), _R(GsBatch), _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_float, _P,
+                                ctypes.c_size_t, _P, _P, _P]
 _lib.gs_composite_nearest.argtypes = [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]
 _lib.gs_forward_kinematics.argtypes = [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]
 _lib.gs_interpolate_joints.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P]
@@ -101,7 +109,7 @@ _lib.gs_version.restype = ctypes.c_int32
 EXPORTS = ("gs_render_static", "gs_profile_enable", "gs_profile_read", "gs_workspace_sections", "gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_deform_avatars",
            "gs_deform_avatars_backward", "gs_get_status", "gs_render_stats", "gs_autotune", "gs_last_cuda_error",
            "gs_version", "gs_composite_nearest", "gs_forward_kinematics", "gs_interpolate_joints",
-           "gs_render_avatars")
+           "gs_render_avatars", "gs_mesh_workspace_size", "gs_render_mesh")
 
 
 class GsError(RuntimeError):
@@ -427,6 +435,43 @@ def deform_backward(av: Avatars, G, d_means, d_cov3d, grads, stream=None):
                                            _ptr(grads["means"]), _ptr(grads["log_scales"]), _ptr(grads["quats"]),
                                            _ptr(grads["G"]), _stream(stream)), "gs_deform_avatars_backward")
     return grads
+
+
+class Mesh:
+    """A triangle mesh with per-vertex colours on the device (see gs_mesh)."""
+
+    def __init__(self, vertices, colors, triangles):
+        _need(vertices, torch.float32, (3,), "vertices")
+        _need(colors, torch.float32, (3,), "colors")
+        if triangles.dtype != torch.int32 or triangles.dim() != 2 or triangles.shape[1] != 3:
+            raise ValueError("triangles must be [T,3] int32")
+        self.t = (vertices, colors, triangles)
+        self.c = GsMesh(_ptr(vertices), _ptr(colors), _ptr(triangles), vertices.shape[0], triangles.shape[0])
+
+    @staticmethod
+    def from_numpy(m: dict, device="cuda"):
+        T = lambda x, dt: torch.from_numpy(np.ascontiguousarray(x)).to(device, dt)  # noqa: E731
+        return Mesh(T(m["vertices"], torch.float32), T(m["colors"], torch.float32),
+                    T(m["triangles"], torch.int32))
+
+
+def render_mesh(mesh: Mesh, batch: Batch, cams: torch.Tensor, width: int, height: int, bg=(0.0, 0.0, 0.0),
+                near: float = 0.2, out=None, workspace=None, stream=None):
+    """The mesh layer (gs_render_mesh): (rgb [V,3,H,W], depth [V,H,W]); batch
+    env_offsets index triangles."""
+    nbytes = ctypes.c_size_t(0)
+    _check(_lib.gs_mesh_workspace_size(ctypes.byref(batch.c), ctypes.byref(nbytes)), "gs_mesh_workspace_size")
+    dev = cams.device
+    if workspace is None or workspace.numel() < nbytes.value:
+        workspace = torch.empty(max(int(nbytes.value), 16), dtype=torch.uint8, device=dev)
+    V = batch.n_views
+    if out is None:
+        out = (torch.empty((V, 3, height, width), device=dev), torch.empty((V, height, width), device=dev))
+    bg3 = (ctypes.c_float * 3)(*bg)
+    _check(_lib.gs_render_mesh(ctypes.byref(mesh.c), ctypes.byref(batch.c), _ptr(cams), width, height, bg3, near,
+                               _ptr(workspace), workspace.numel(), _ptr(out[0]), _ptr(out[1]), _stream(stream)),
+           "gs_render_mesh")
+    return out
 
 
 def composite_nearest(rgb_a, depth_a, rgb_b, depth_b, out=None, stream=None):

@@ -467,6 +467,70 @@ gs_status gs_render_avatars(const gs_gaussians *g, const gs_batch *batch, const 
                            out_ncontrib, static_cast<cudaStream_t>(stream), av, joint_G);
 }
 
+static gs_status mesh_table(const gs_batch *b, int32_t W, int32_t H, MeshTable &t)
+{
+    if (!b || !b->env_offsets || !b->view_env) return GS_ERR_INVALID_ARG;
+    if (b->n_envs < 1 || b->n_envs > GS_MAX_ENVS || b->n_views < 1 || b->n_views > GS_MAX_VIEWS) return GS_ERR_INVALID_ARG;
+    if (W < 1 || H < 1 || W > 65535 || H > 65535) return GS_ERR_INVALID_ARG;
+    std::memset(&t, 0, sizeof(t));
+    t.n_views = b->n_views;
+    t.W = W;
+    t.H = H;
+    if (b->env_offsets[0] != 0) return GS_ERR_INVALID_ARG;
+    for (int e = 0; e <= b->n_envs; ++e) {
+        t.env_off[e] = b->env_offsets[e];
+        if (e > 0 && b->env_offsets[e] < b->env_offsets[e - 1]) return GS_ERR_INVALID_ARG;
+    }
+    int64_t off = 0;
+    for (int v = 0; v < b->n_views; ++v) {
+        const int e = b->view_env[v];
+        if (e < 0 || e >= b->n_envs) return GS_ERR_INVALID_ARG;
+        t.view_env[v] = e;
+        t.view_rec_off[v] = off;
+        off += b->env_offsets[e + 1] - b->env_offsets[e];
+    }
+    t.view_rec_off[b->n_views] = off;
+    return GS_OK;
+}
+
+gs_status gs_mesh_workspace_size(const gs_batch *batch, size_t *bytes)
+{
+    if (!bytes) return GS_ERR_INVALID_ARG;
+    MeshTable t;
+    const gs_status st = mesh_table(batch, 1, 1, t);
+    if (st != GS_OK) return st;
+    *bytes = (size_t)t.view_rec_off[t.n_views] * mesh_record_bytes();
+    return GS_OK;
+}
+
+gs_status gs_render_mesh(const gs_mesh *mesh, const gs_batch *batch, const gs_camera *cams, int32_t width,
+                         int32_t height, const float *bg, float near_plane, void *workspace, size_t workspace_bytes,
+                         float *out_rgb, float *out_depth, void *stream)
+{
+    if (!mesh || !cams || !out_rgb || !out_depth) return GS_ERR_INVALID_ARG;
+    if (mesh->n_triangles < 0 || mesh->n_vertices < 1 || !mesh->vertices || !mesh->colors || !mesh->triangles)
+        return GS_ERR_INVALID_ARG;
+    MeshTable t;
+    gs_status st = mesh_table(batch, width, height, t);
+    if (st != GS_OK) return st;
+    if (t.env_off[batch->n_envs] != mesh->n_triangles) return GS_ERR_INVALID_ARG;
+    const size_t need = (size_t)t.view_rec_off[t.n_views] * mesh_record_bytes();
+    if (need && (!workspace || workspace_bytes < need)) return GS_ERR_WORKSPACE_TOO_SMALL;
+    if ((workspace && !aligned16(workspace)) || !aligned16(out_rgb) || !aligned16(out_depth) || !aligned16(cams))
+        return GS_ERR_ALIGNMENT;
+    const void *p4[] = {mesh->vertices, mesh->colors, mesh->triangles};
+    for (const void *q : p4)
+        if (reinterpret_cast<uintptr_t>(q) & 3u) return GS_ERR_ALIGNMENT;
+    t.near_plane = near_plane > 0.f ? near_plane : 0.2f;
+    for (int k = 0; k < 3; ++k) t.bg[k] = bg ? bg[k] : 0.f;
+    int sms = 0;
+    st = device_init(&sms);
+    if (st != GS_OK) return st;
+    const MeshIn in{mesh->vertices, mesh->colors, mesh->triangles, mesh->n_vertices, mesh->n_triangles};
+    launch_mesh(in, cams, t, workspace, out_rgb, out_depth, static_cast<cudaStream_t>(stream));
+    return check_launch();
+}
+
 gs_status gs_composite_nearest(const float *rgb_a, const float *depth_a, const float *rgb_b, const float *depth_b,
                                int32_t n_views, int32_t height, int32_t width, float *rgb_out, float *depth_out,
                                void *stream)

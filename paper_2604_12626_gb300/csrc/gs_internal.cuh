@@ -38,6 +38,21 @@ constexpr int kGradStride = 16;   // floats per record row of d_rec: 12 gradient
 constexpr int kAccStride = 12;    // floats per record in the backward's shared-memory accumulator
 constexpr int kMaxJoints = 64;    // joints of one avatar tree
 
+// Triangle-mesh layer: the mesh, and the view/env structure passed by value.
+struct MeshIn {
+    const float *verts, *colors;
+    const int32_t *tris;
+    int64_t n_verts, n_tris;
+};
+struct MeshTable {
+    int32_t n_views, W, H;
+    float near_plane;
+    float bg[3];
+    int32_t view_env[GS_MAX_VIEWS];
+    int64_t view_rec_off[GS_MAX_VIEWS + 1]; // (view, triangle) records of view v start here
+    int64_t env_off[GS_MAX_ENVS + 1];       // triangles of env e: [env_off[e], env_off[e+1])
+};
+
 // A joint tree passed by value: parent and depth of every joint (parent < child).
 struct JointTree {
     int32_t n, max_depth;

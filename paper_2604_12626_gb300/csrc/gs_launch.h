@@ -48,6 +48,10 @@ void launch_fk(const float *local_rot, const float *root, const float *rest, con
 void launch_interp(const float *frames, const float *t, int n_avatars, int n_frames, int n_joints, float *out,
                    int n_sms, cudaStream_t s);
 
+size_t mesh_record_bytes();
+void launch_mesh(const MeshIn &in, const gs_camera *cams, const MeshTable &t, void *rec, float *rgb, float *depth,
+                 cudaStream_t s);
+
 // Records a CUDA error for gs_last_cuda_error and returns GS_ERR_CUDA.
 gs_status record_cuda_error(cudaError_t e);
 

@@ -192,6 +192,51 @@ def batch_sizes(n_envs: int = 64, n_min: int = 300_000, n_max: int = 1_500_000, 
 
 
 # ---------------------------------------------------------------------------
+# Triangle meshes (the mesh layer of a mixed scene)
+# ---------------------------------------------------------------------------
+
+def room_mesh(seed: int = 0, n_boxes: int = 12, grid: int = 8) -> dict:
+    """A triangle mesh of the room: its six faces, each a grid x grid quad
+    mesh, and n_boxes axis-aligned boxes (furniture) on the floor; random
+    per-vertex colours.  vertices [V,3], colors [V,3] float32, triangles
+    [T,3] int32."""
+    rng = np.random.default_rng(60_000 + seed)
+    verts, tris = [], []
+
+    def add_quad_grid(origin, u, v, n):
+        base = sum(len(x) for x in verts)
+        a = np.linspace(0.0, 1.0, n + 1)
+        pts = origin[None, None, :] + a[:, None, None] * u[None, None, :] + a[None, :, None] * v[None, None, :]
+        verts.append(pts.reshape(-1, 3))
+        for i in range(n):
+            for j in range(n):
+                k = base + i * (n + 1) + j
+                tris.append([k, k + n + 1, k + n + 2])
+                tris.append([k, k + n + 2, k + 1])
+
+    X, Y, Z = ROOM
+    e = np.eye(3)
+    faces = [(np.zeros(3), X * e[0], Y * e[1]), (np.array([0, 0, Z]), X * e[0], Y * e[1]),
+             (np.zeros(3), X * e[0], Z * e[2]), (np.array([0, Y, 0]), X * e[0], Z * e[2]),
+             (np.zeros(3), Y * e[1], Z * e[2]), (np.array([X, 0, 0]), Y * e[1], Z * e[2])]
+    for o, u, v in faces:
+        add_quad_grid(np.asarray(o, np.float64), u, v, grid)
+    for _ in range(n_boxes):
+        size = rng.uniform([0.3, 0.3, 0.3], [1.5, 1.5, 1.2])
+        lo = np.array([rng.uniform(0.2, X - 0.2 - size[0]), rng.uniform(0.2, Y - 0.2 - size[1]), 0.0])
+        hi = lo + size
+        for axis in range(3):
+            for side in (lo, hi):
+                o = lo.copy()
+                o[axis] = side[axis]
+                a1, a2 = [k for k in range(3) if k != axis]
+                add_quad_grid(o, (hi - lo)[a1] * e[a1], (hi - lo)[a2] * e[a2], 1)
+    V = np.concatenate(verts).astype(np.float32)
+    return {"vertices": V, "colors": rng.uniform(0.0, 1.0, (V.shape[0], 3)).astype(np.float32),
+            "triangles": np.asarray(tris, np.int32)}
+
+
+# ---------------------------------------------------------------------------
 # Avatars
 # ---------------------------------------------------------------------------
 

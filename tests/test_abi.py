@@ -45,7 +45,7 @@ def test_ctypes_structs_match_c_layout(tmp_path, lib):
 
     structs = {"gs_camera": api.GsCamera, "gs_gaussians": api.GsGaussians, "gs_batch": api.GsBatch,
                "gs_render_config": api.GsRenderConfig, "gs_stats": api.GsStats, "gs_avatars": api.GsAvatars,
-               "gs_ws_sections": api.GsWsSections}
+               "gs_ws_sections": api.GsWsSections, "gs_mesh": api.GsMesh}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gs.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')

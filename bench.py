@@ -356,6 +356,20 @@ def avatar_and_composite_rows(api, synth, torch, dev, stream, outs, hbm_peak):
     comp_ms = _event_ms(torch, stream, lambda: api.composite_nearest(outs[0], outs[1], rgb_b, dep_b,
                                                                     out=(rgb_o, dep_o), stream=stream))
     comp_bytes = 48 * V * H * W
+    # the mesh layer of a mixed scene: each env's room mesh, one view per env
+    meshes = [synth.room_mesh(e % 8, n_boxes=12, grid=16) for e in range(V)]
+    tri_off = np.cumsum([0] + [mm["triangles"].shape[0] for mm in meshes])
+    v_off = np.cumsum([0] + [mm["vertices"].shape[0] for mm in meshes])
+    mesh = api.Mesh.from_numpy(dict(vertices=np.concatenate([mm["vertices"] for mm in meshes]),
+                                    colors=np.concatenate([mm["colors"] for mm in meshes]),
+                                    triangles=np.concatenate([mm["triangles"] + v_off[k]
+                                                              for k, mm in enumerate(meshes)])), device=dev)
+    mbatch = api.Batch(tri_off)
+    cams_m = api.cameras_tensor(np.stack([synth.room_camera(e, W, H) for e in range(V)]), dev)
+    mout = (torch.empty_like(outs[0]), torch.empty_like(outs[1]))
+    mws = torch.empty(int(tri_off[-1]) * 96 + 16, dtype=torch.uint8, device=dev)
+    mesh_ms = _event_ms(torch, stream, lambda: api.render_mesh(mesh, mbatch, cams_m, W, H, out=mout, workspace=mws,
+                                                               stream=stream))
 
     def hbm(b, ms):
         a = b / (ms * 1e-3) / 1e9
@@ -366,7 +380,9 @@ def avatar_and_composite_rows(api, synth, torch, dev, stream, outs, hbm_peak):
                                         note="joint-gradient atomics per Gaussian and joint"),
             "keyframe_interpolation": {"ms": interp_ms, "avatars": n_av, "frames": n_frames},
             "forward_kinematics": {"ms": fk_ms, "avatars": n_av, "joints": synth.N_JOINTS},
-            "composite": dict(hbm(comp_bytes, comp_ms), views=V, width=W, height=H)}
+            "composite": dict(hbm(comp_bytes, comp_ms), views=V, width=W, height=H),
+            "mesh_layer": {"ms": mesh_ms, "views": V, "triangles_per_view": int(tri_off[-1]) // V, "width": W,
+                           "height": H}}
 
 
 def fused_avatar_row(api, synth, torch, dev, stream):

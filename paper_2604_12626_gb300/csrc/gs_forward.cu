@@ -765,21 +765,60 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
                 for (int u = 0; u < kUnroll; ++u) {
                     const float4 c = s2[k0 + u];
                     const float z = s0[k0 + u].z;
+                    if constexpr (PX == 2) {
+                        // the two pixels of a row updated as packed pairs, branch-free: a
+                        // pixel that does not blend this Gaussian gets weight 0 (C + c 0 = C,
+                        // T (1 - 0) = T exactly), so the arithmetic is the scalar path's
+                        const uint32_t pos = (uint32_t)b * B + k0 + u + 1;
+#pragma unroll
+                        for (int r = 0; r < PY; ++r) {
+                            const int p0 = 2 * r, p1 = 2 * r + 1;
+                            const bool a0 = !dn[p0] && cv[u][p0], a1 = !dn[p1] && cv[u][p1];
+                            ncov[p0] += a0;
+                            ncov[p1] += a1;
+                            const bool k0k = a0 && ok[u][p0], k1k = a1 && ok[u][p1];
+                            const float2 T2 = make_float2(T[p0], T[p1]);
+                            const float2 om = __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-al[u][p0], -al[u][p1]));
+                            const float2 Tn = __fmul2_rn(T2, om);
+                            const bool s0b = k0k && Tn.x < kTStop, s1b = k1k && Tn.y < kTStop;
+                            const bool bl0 = k0k && !s0b, bl1 = k1k && !s1b;
+                            dn[p0] = dn[p0] || s0b;
+                            dn[p1] = dn[p1] || s1b;
+                            const float2 wgt =
+                                __fmul2_rn(make_float2(bl0 ? al[u][p0] : 0.0f, bl1 ? al[u][p1] : 0.0f), T2);
+                            const float2 c0 = __ffma2_rn(make_float2(c.x, c.x), wgt, make_float2(C0[p0], C0[p1]));
+                            const float2 c1 = __ffma2_rn(make_float2(c.y, c.y), wgt, make_float2(C1[p0], C1[p1]));
+                            const float2 c2 = __ffma2_rn(make_float2(c.z, c.z), wgt, make_float2(C2[p0], C2[p1]));
+                            const float2 dd = __ffma2_rn(make_float2(z, z), wgt, make_float2(D[p0], D[p1]));
+                            C0[p0] = c0.x; C0[p1] = c0.y;
+                            C1[p0] = c1.x; C1[p1] = c1.y;
+                            C2[p0] = c2.x; C2[p1] = c2.y;
+                            D[p0] = dd.x; D[p1] = dd.y;
+                            T[p0] = bl0 ? Tn.x : T[p0];
+                            T[p1] = bl1 ? Tn.y : T[p1];
+                            ncon[p0] = bl0 ? ncov[p0] : ncon[p0];
+                            ncon[p1] = bl1 ? ncov[p1] : ncon[p1];
+                            last[p0] = bl0 ? pos : last[p0];
+                            last[p1] = bl1 ? pos : last[p1];
+                        }
+                        continue;
+                    }
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
                         if (!dn[p] && cv[u][p]) {
                             ++ncov[p];
                             if (ok[u][p]) {
+                                // explicit roundings: the packed pair path above does the same
                                 const float alpha = al[u][p];
-                                const float Tn = T[p] * (1.0f - alpha);
+                                const float Tn = __fmul_rn(T[p], __fsub_rn(1.0f, alpha));
                                 if (Tn < kTStop) {
                                     dn[p] = true;
                                 } else {
-                                    const float wgt = alpha * T[p];
-                                    C0[p] += c.x * wgt;
-                                    C1[p] += c.y * wgt;
-                                    C2[p] += c.z * wgt;
-                                    D[p] += z * wgt;
+                                    const float wgt = __fmul_rn(alpha, T[p]);
+                                    C0[p] = __fmaf_rn(c.x, wgt, C0[p]);
+                                    C1[p] = __fmaf_rn(c.y, wgt, C1[p]);
+                                    C2[p] = __fmaf_rn(c.z, wgt, C2[p]);
+                                    D[p] = __fmaf_rn(z, wgt, D[p]);
                                     T[p] = Tn;
                                     ncon[p] = ncov[p];
                                     last[p] = (uint32_t)b * B + k0 + u + 1;
@@ -827,10 +866,20 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
     }
 }
 
+// The batch slots past a batch's end are read by the packed pixel-pair update
+// (with weight 0): they must hold finite values, so the buffers start at zero
+// (later they hold earlier, valid records).
+__device__ __forceinline__ void clear_batch_buffers(float4 *sm, int B)
+{
+    for (int k = threadIdx.x; k < 2 * 3 * B; k += blockDim.x) sm[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+}
+
 template <int PX, int PY>
 __global__ void blend_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
 {
     extern __shared__ float4 smem_f4[];
+    clear_batch_buffers(smem_f4, w.tb->batch_depth);
     blend_tile<PX, PY>(w, cams, o, blockIdx.x, w.heavy_of[blockIdx.x], smem_f4);
 }
 
@@ -839,6 +888,7 @@ __global__ void blend_persistent_kernel(const gs_camera *__restrict__ cams, Ws w
 {
     extern __shared__ float4 smem_f4[];
     __shared__ uint32_t item;
+    clear_batch_buffers(smem_f4, w.tb->batch_depth);
     const uint32_t n_items = (uint32_t)w.tb->n_bins + w.hdr->n_heavy;
     for (;;) {
         __syncthreads();

@@ -7,8 +7,8 @@
 //                       bounding box -> a 96-byte record
 //   mesh_raster_kernel  one CTA per (view, 16x16 tile), one thread per pixel:
 //                       triangle records staged in shared memory 256 at a
-//                       time; a triangle whose box misses the tile is skipped
-//                       by the whole CTA; inside test on the edge functions,
+//                       time, those whose box meets the tile compacted in
+//                       index order; inside test on the edge functions,
 //                       perspective-correct depth and colour, nearest depth
 //                       kept (the lower triangle index on a tie)
 #include <cmath>
@@ -83,6 +83,8 @@ __global__ void __launch_bounds__(kMeshTile *kMeshTile) mesh_raster_kernel(MeshT
                                                                           float *rgb, float *depth)
 {
     __shared__ MeshRec s[kMeshBatch];
+    __shared__ uint16_t hit[kMeshBatch]; // batch slots whose box meets this tile, in index order
+    __shared__ int n_hit, warp_n[kMeshTile * kMeshTile / 32];
     const int v = blockIdx.y;
     const int tiles_x = (t.W + kMeshTile - 1) / kMeshTile;
     const int tx0 = (blockIdx.x % tiles_x) * kMeshTile, ty0 = (blockIdx.x / tiles_x) * kMeshTile;
@@ -90,15 +92,38 @@ __global__ void __launch_bounds__(kMeshTile *kMeshTile) mesh_raster_kernel(MeshT
     const float px = (float)i, py = (float)j;
     float best = INFINITY, r0 = t.bg[0], r1 = t.bg[1], r2 = t.bg[2];
     const int64_t lo = t.view_rec_off[v], hi = t.view_rec_off[v + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t b0 = lo; b0 < hi; b0 += kMeshBatch) {
         const int cnt = (int)min((int64_t)kMeshBatch, hi - b0);
         __syncthreads();
-        if ((int)threadIdx.x < cnt) s[threadIdx.x] = rec[b0 + threadIdx.x];
-        __syncthreads();
-        for (int k = 0; k < cnt; ++k) {
-            const uint32_t bx = __float_as_uint(s[k].c.z), by = __float_as_uint(s[k].c.w);
+        // each thread tests one triangle's box against the tile; the hits are
+        // compacted in index order (warp ballots, then a scan over the warps)
+        bool h = false;
+        if ((int)threadIdx.x < cnt) {
+            const MeshRec m = rec[b0 + threadIdx.x];
+            const uint32_t bx = __float_as_uint(m.c.z), by = __float_as_uint(m.c.w);
             const int x0 = (int)(bx & 0xffffu), x1 = (int)(bx >> 16), y0 = (int)(by & 0xffffu), y1 = (int)(by >> 16);
-            if (x1 < tx0 || x0 > tx0 + kMeshTile - 1 || y1 < ty0 || y0 > ty0 + kMeshTile - 1) continue; // CTA-uniform
+            h = !(x1 < tx0 || x0 > tx0 + kMeshTile - 1 || y1 < ty0 || y0 > ty0 + kMeshTile - 1);
+            s[threadIdx.x] = m;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, h);
+        if (lane == 0) warp_n[warp] = __popc(bal);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int q = 0; q < kMeshTile * kMeshTile / 32; ++q) {
+                const int c = warp_n[q];
+                warp_n[q] = acc;
+                acc += c;
+            }
+            n_hit = acc;
+        }
+        __syncthreads();
+        if (h) hit[warp_n[warp] + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)threadIdx.x;
+        __syncthreads();
+        const int nh = n_hit;
+        for (int q = 0; q < nh; ++q) {
+            const int k = hit[q];
             const float4 A = s[k].a, B = s[k].b, C = s[k].c;
             const float X[3] = {A.x, A.z, B.x}, Y[3] = {A.y, A.w, B.y};
             float e[3];

@@ -409,19 +409,24 @@ gs_status gs_render_backward(const gs_gaussians *g, const gs_batch *batch, const
     if (workspace_bytes < p.total) return GS_ERR_WORKSPACE_TOO_SMALL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Ws w = ws_ptrs(workspace, p);
+    const bool overwrite = (cfg->flags & GS_FLAG_GRAD_OVERWRITE) != 0;
+    GradOut o{d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_cov3d};
     {
         Stage st7(7, s);
         // the record gradient rows were zeroed by the forward (visible records
         // only); a repeated backward of the same forward clears them first
         cudaError_t e = cudaMemsetAsync(&w.hdr->queue_bwd, 0, 4, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(&w.hdr->queue_zero, 0, 4, s);
         if (e != cudaSuccess) return cuda_fail(e);
         launch_clear_record_grads(w, p.R, sms, s);
-        launch_blend_backward(cams, w, d_rgb, d_depth, p.n_bins, p.px, p.py, p.threads, p.B, sms, s);
+        // overwrite mode: the blend backward also sets every gradient row to
+        // zero, between its tiles; the preprocess backward writes the seen rows
+        launch_blend_backward(cams, w, d_rgb, d_depth, p.n_bins, p.px, p.py, p.threads, p.B, sms,
+                              overwrite ? &o : nullptr, p.N, s);
     }
     {
         Stage st8(8, s);
-        GradOut o{d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_cov3d};
-        launch_preprocess_backward(g, cams, w, o, p.n_chunks, (cfg->flags & GS_FLAG_GRAD_OVERWRITE) != 0, s);
+        launch_preprocess_backward(g, cams, w, o, p.n_chunks, overwrite, s);
     }
     return check_launch();
 }

@@ -332,9 +332,32 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
     cp_async_wait<0>();
 }
 
+// Overwrite mode: every gradient row is first set to zero (the preprocess
+// backward then writes the rows of the Gaussians some view sees).  The clearing
+// is split into items of kZeroFloats floats that the persistent blend-backward
+// CTAs take one at a time between their tiles, so that the store stream to HBM
+// runs under the issue-bound blend instead of after it.
+constexpr int64_t kZeroFloats = 1 << 16;
+
+__device__ void zero_item(const ZeroWork &zw, uint32_t z)
+{
+    int a = 0;
+    while (a + 1 < kZeroArrays && zw.first[a + 1] <= z) ++a;
+    float *p = zw.p[a];
+    const int64_t lo = (int64_t)(z - zw.first[a]) * kZeroFloats, hi = min(zw.n[a], lo + kZeroFloats);
+    // scalar up to the first 16-byte boundary and after the last, float4 between
+    const int64_t a4 = min(hi, lo + (int64_t)((((16 - (reinterpret_cast<uintptr_t>(p + lo) & 15)) & 15)) >> 2));
+    const int64_t n4 = (hi - a4) >> 2;
+    if (lo + (int64_t)threadIdx.x < a4) p[lo + threadIdx.x] = 0.f;
+    float4 *q = reinterpret_cast<float4 *>(p + a4);
+    for (int64_t i = threadIdx.x; i < n4; i += blockDim.x) q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int64_t t0 = a4 + 4 * n4;
+    if (t0 + (int64_t)threadIdx.x < hi) p[t0 + threadIdx.x] = 0.f;
+}
+
 template <int PX, int PY>
 __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, const float *__restrict__ d_rgb,
-                                      const float *__restrict__ d_depth)
+                                      const float *__restrict__ d_depth, ZeroWork zw)
 {
     extern __shared__ float4 smem_b[];
     __shared__ uint32_t smax_last, item;
@@ -363,10 +386,23 @@ __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, 
                                         (int64_t)w.heavy_seg[lo] + s, smem_b, acc, sidx, &smax_last);
         } else {
             const uint32_t b = item - nhi;
-            if (w.bin_count[b] + w.bin_fcount[b] >= w.hdr->heavy_min) continue;
-            blend_backward_tile<PX, PY>(w, cams, d_rgb, d_depth, (int)b, 0u, 0xffffffffu, 0, smem_b, acc, sidx,
-                                        &smax_last);
+            if (w.bin_count[b] + w.bin_fcount[b] < w.hdr->heavy_min)
+                blend_backward_tile<PX, PY>(w, cams, d_rgb, d_depth, (int)b, 0u, 0xffffffffu, 0, smem_b, acc, sidx,
+                                            &smax_last);
         }
+        if (zw.total) { // one clearing item between tiles
+            __syncthreads();
+            if (threadIdx.x == 0) item = atomicAdd(&w.hdr->queue_zero, 1u);
+            __syncthreads();
+            if (item < zw.total) zero_item(zw, item);
+        }
+    }
+    for (;;) { // clearing items left when the tiles ran out
+        __syncthreads();
+        if (threadIdx.x == 0) item = zw.total ? atomicAdd(&w.hdr->queue_zero, 1u) : zw.total;
+        __syncthreads();
+        if (item >= zw.total) break;
+        zero_item(zw, item);
     }
 }
 
@@ -634,29 +670,13 @@ __device__ __forceinline__ void gaussian_backward(const gs_camera *__restrict__ 
     }
 }
 
-// Zero gradient rows of a Gaussian no view sees (overwrite mode).
-__device__ __forceinline__ void zero_rows(const GradOut &o, int64_t g, bool use_cov)
-{
-#pragma unroll
-    for (int i = 0; i < 3; ++i) o.means[3 * g + i] = 0.f;
-    o.ologits[g] = 0.f;
-    float4 *dsh4 = reinterpret_cast<float4 *>(o.sh + 48 * g);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) dsh4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (use_cov) {
-        if (o.cov3d)
-            for (int i = 0; i < 6; ++i) o.cov3d[6 * g + i] = 0.f;
-    } else {
-        for (int i = 0; i < 3; ++i) o.log_scales[3 * g + i] = 0.f;
-        reinterpret_cast<float4 *>(o.quats)[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-}
 
 // Chunked like the forward preprocess: every lane checks whether any view sees
 // its Gaussian (zero rows otherwise, in overwrite mode); the seen ones go
 // through a per-warp ring queue and are processed 32 at a time, so that the
 // long chain runs on full warps.
 constexpr int kBwdWarpQ = 64;
+
 
 template <int SHT, bool OVERWRITE>
 __global__ void __launch_bounds__(256, 2) preprocess_backward_kernel(const gs_camera *__restrict__ cams, GaussInB gin,
@@ -677,8 +697,6 @@ __global__ void __launch_bounds__(256, 2) preprocess_backward_kernel(const gs_ca
     int head = 0, tail = 0;
     const int64_t env_base = tb->env_off[lo];
     const int vb = tb->env_view_begin[lo], ve = tb->env_view_begin[lo + 1];
-    const bool use_cov = gin.cov3d != nullptr && g0 >= tb->env_cov_begin[lo];
-    const bool split_cov = gin.cov3d != nullptr && g0 < tb->env_cov_begin[lo] && g1 > tb->env_cov_begin[lo];
     for (int64_t base = g0 + warp * 32; base < g1; base += 32 * nwarps) {
         const int64_t g = base + lane;
         bool seen = false;
@@ -690,31 +708,6 @@ __global__ void __launch_bounds__(256, 2) preprocess_backward_kernel(const gs_ca
             }
         }
         const unsigned bal = __ballot_sync(0xffffffffu, seen);
-        if (OVERWRITE) {
-            // zero the rows of this warp's 32 consecutive Gaussians that no
-            // view sees, with coalesced stores; seen rows are written once,
-            // later, by this same warp
-            const int nrow = (int)min((int64_t)32, g1 - base);
-            const unsigned unseen = ~bal;
-            float4 *sh4 = reinterpret_cast<float4 *>(o.sh + 48 * base);
-            for (int i = lane; i < 12 * nrow; i += 32)
-                if ((unseen >> (i / 12)) & 1u) sh4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int i = lane; i < 3 * nrow; i += 32)
-                if ((unseen >> (i / 3)) & 1u) o.means[3 * base + i] = 0.f;
-            if (lane < nrow && !seen) o.ologits[base + lane] = 0.f;
-            if (split_cov) {
-                if (g < g1 && !seen) zero_rows(o, g, g >= tb->env_cov_begin[lo]);
-            } else if (use_cov) {
-                if (o.cov3d)
-                    for (int i = lane; i < 6 * nrow; i += 32)
-                        if ((unseen >> (i / 6)) & 1u) o.cov3d[6 * base + i] = 0.f;
-            } else {
-                for (int i = lane; i < 3 * nrow; i += 32)
-                    if ((unseen >> (i / 3)) & 1u) o.log_scales[3 * base + i] = 0.f;
-                if (lane < nrow && !seen)
-                    reinterpret_cast<float4 *>(o.quats)[base + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
         if (seen) q[(tail + __popc(bal & ((1u << lane) - 1u))) & (kBwdWarpQ - 1)] = (uint32_t)(g - g0);
         tail += __popc(bal);
         __syncwarp();
@@ -776,14 +769,14 @@ static int blend_bwd_smem(int batch_depth)
 
 template <int PX, int PY>
 static void launch_bb(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,
-                      int threads, int batch_depth, int n_sms, cudaStream_t s)
+                      int threads, int batch_depth, int n_sms, const ZeroWork &zw, cudaStream_t s)
 {
     const int smem = blend_bwd_smem(batch_depth);
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blend_backward_kernel<PX, PY>, threads, smem);
     int grid = n_sms * (nb > 0 ? nb : 1);
     if (grid > n_bins) grid = n_bins;
-    blend_backward_kernel<PX, PY><<<grid, threads, smem, s>>>(cams, w, d_rgb, d_depth);
+    blend_backward_kernel<PX, PY><<<grid, threads, smem, s>>>(cams, w, d_rgb, d_depth, zw);
 }
 
 template <int PX, int PY>
@@ -803,12 +796,28 @@ int blend_backward_thread_limit(int px, int py)
 }
 
 void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,
-                           int px, int py, int threads, int batch_depth, int n_sms, cudaStream_t s)
+                           int px, int py, int threads, int batch_depth, int n_sms, const GradOut *clear, int64_t n,
+                           cudaStream_t s)
 {
-    if (px == 2 && py == 2) launch_bb<2, 2>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, s);
-    else if (px == 2) launch_bb<2, 1>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, s);
-    else if (py == 2) launch_bb<1, 2>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, s);
-    else launch_bb<1, 1>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, s);
+    ZeroWork zw;
+    memset(&zw, 0, sizeof(zw));
+    if (clear) {
+        float *ps[kZeroArrays] = {clear->sh, clear->means, clear->ologits, clear->log_scales, clear->quats,
+                                  clear->cov3d};
+        const int64_t ns[kZeroArrays] = {48 * n, 3 * n, n, 3 * n, 4 * n, clear->cov3d ? 6 * n : 0};
+        uint32_t acc = 0;
+        for (int a = 0; a < kZeroArrays; ++a) {
+            zw.p[a] = ps[a];
+            zw.n[a] = ps[a] ? ns[a] : 0;
+            zw.first[a] = acc;
+            acc += (uint32_t)((zw.n[a] + kZeroFloats - 1) / kZeroFloats);
+        }
+        zw.total = acc;
+    }
+    if (px == 2 && py == 2) launch_bb<2, 2>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);
+    else if (px == 2) launch_bb<2, 1>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);
+    else if (py == 2) launch_bb<1, 2>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);
+    else launch_bb<1, 1>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);
 }
 
 template <bool OW>

@@ -75,7 +75,8 @@ struct Header {
     uint32_t max_pass;  // merge passes the largest bin needs
     unsigned long long n_evals; // blend evaluations, counted under GS_FLAG_COUNT_EVALS
     uint32_t n_backward;  // gs_render_backward calls since the forward (d_rec is clean while 0)
-    uint32_t pad[49];
+    uint32_t queue_zero;  // gradient-clearing items taken by the blend backward
+    uint32_t pad[48];
 };
 
 struct Table {

@@ -31,9 +31,20 @@ void launch_count_visible(const Ws &w, int64_t n_words, cudaStream_t s);
 struct GradOut {
     float *means, *log_scales, *quats, *ologits, *sh, *cov3d;
 };
+
+constexpr int kZeroArrays = 6;
+struct ZeroWork { // gradient arrays to clear and the first clearing item of each
+    float *p[kZeroArrays];
+    int64_t n[kZeroArrays];
+    uint32_t first[kZeroArrays];
+    uint32_t total;
+};
 void launch_clear_record_grads(const Ws &w, int64_t n_records, int n_sms, cudaStream_t s);
+// clear: in overwrite mode the gradient arrays (n Gaussians) the blend backward
+// sets to zero between its tiles, else nullptr
 void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,
-                           int px, int py, int threads, int batch_depth, int n_sms, cudaStream_t s);
+                           int px, int py, int threads, int batch_depth, int n_sms, const GradOut *clear, int64_t n,
+                           cudaStream_t s);
 void launch_preprocess_backward(const gs_gaussians *g, const gs_camera *cams, const Ws &w, const GradOut &o,
                                 int n_chunks, bool overwrite, cudaStream_t s);
 

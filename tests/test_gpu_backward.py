@@ -264,7 +264,7 @@ def test_repeated_backward_of_one_forward(gs):
     r.forward(G, ct)
     c = {k: v.clone() for k, v in r.backward(G, ct, d_rgb, d_dep).items() if v is not None}
     torch.cuda.synchronize()
-    for k in a:
-        assert rel_l2(b[k].cpu().numpy(), a[k].cpu().numpy()) < 1e-6, k
-        assert rel_l2(c[k].cpu().numpy(), a[k].cpu().numpy()) < 1e-6, k
+    for k in a:  # equal up to the order of the float atomics (a stale row would double a gradient)
+        assert rel_l2(b[k].cpu().numpy(), a[k].cpu().numpy()) < 2e-5, k
+        assert rel_l2(c[k].cpu().numpy(), a[k].cpu().numpy()) < 2e-5, k
     assert float(a["opacity_logits"].abs().sum()) > 0

@@ -166,13 +166,17 @@ __device__ __forceinline__ void finish_entry(const QEntry &en, bool active, uint
 // Each warp walks 32-Gaussian rounds of the chunk on its own (no CTA barrier in
 // the loop): phase 1 on every lane (near cull, covariance, projection, radius,
 // footprint), visible results into the warp's ring queue in shared memory, and
-// phase 2 on full warps of 32 queued entries.  The next round's means are
-// loaded before the current round is processed.
+// phase 2 on full warps of 32 queued entries.  The next round's means, scales
+// and rotations are loaded before the current round is processed (most lanes
+// of a warp need them, so the extra bytes are few; 2 CTAs of 256 per SM leave
+// the registers to hold them without spills).
 constexpr int kWarpQ = 64;
 constexpr int kMaxViewsPerChunk = 16; // cameras of a chunk's env staged in shared memory
 
-template <int SHT>
-__global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(const gs_camera *__restrict__ cams, GaussIn gin,
+// FUSED: the batch's avatar rows are posed by LBS here (gs_render_avatars); a
+// separate instantiation so that the plain path carries none of its registers
+template <int SHT, bool FUSED>
+__global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_camera *__restrict__ cams, GaussIn gin,
                                                                     Ws w)
 {
     extern __shared__ __align__(16) unsigned char smem_pre[];
@@ -204,26 +208,40 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(const gs_cam
     int head = 0, tail = 0; // ring queue of this warp
     int64_t g = c.g0 + warp * 32 + lane;
     float mx = 0.f, my = 0.f, mz = 0.f;
+    float3 cls = make_float3(0.f, 0.f, 0.f);
+    float4 cq = make_float4(1.f, 0.f, 0.f, 0.f);
     if (g < c.g1) {
         mx = __ldg(gin.means + 3 * g);
         my = __ldg(gin.means + 3 * g + 1);
         mz = __ldg(gin.means + 3 * g + 2);
+        if (!(env_cov && g >= cov_begin)) {
+            cls = make_float3(__ldg(gin.log_scales + 3 * g), __ldg(gin.log_scales + 3 * g + 1),
+                              __ldg(gin.log_scales + 3 * g + 2));
+            cq = __ldg(reinterpret_cast<const float4 *>(gin.quats) + g);
+        }
     }
     for (int64_t base = c.g0 + warp * 32; base < c.g1; base += 32 * nwarps) {
         const bool valid = g < c.g1;
         // prefetch the next round's means
         const int64_t gn = g + 32 * nwarps;
         float nx = 0.f, ny = 0.f, nz = 0.f;
+        float3 nls = make_float3(0.f, 0.f, 0.f);
+        float4 nq = make_float4(1.f, 0.f, 0.f, 0.f);
         if (gn < c.g1) {
             nx = __ldg(gin.means + 3 * gn);
             ny = __ldg(gin.means + 3 * gn + 1);
             nz = __ldg(gin.means + 3 * gn + 2);
+            if (!(env_cov && gn >= cov_begin)) {
+                nls = make_float3(__ldg(gin.log_scales + 3 * gn), __ldg(gin.log_scales + 3 * gn + 1),
+                                  __ldg(gin.log_scales + 3 * gn + 2));
+                nq = __ldg(reinterpret_cast<const float4 *>(gin.quats) + gn);
+            }
         }
         const int nv = valid ? c.nv : 0;
         const int64_t local = g - env_base;
         bool have_sigma = false;
         float S[6];
-        if (gin.av_G && valid && g >= cov_begin) {
+        if (FUSED && valid && g >= cov_begin) {
             // posed mean and covariance by LBS, never written to memory
             const int64_t i = tb->env_av_base[c.e0] + (g - cov_begin);
             const int a = clamp_avatar(__ldg(gin.av_of + i), gin.n_avatars);
@@ -254,11 +272,7 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(const gs_cam
 #pragma unroll
                             for (int i = 0; i < 6; ++i) S[i] = __ldg(gin.cov3d + 6 * g + i);
                         } else {
-                            const float3 ls = make_float3(__ldg(gin.log_scales + 3 * g),
-                                                          __ldg(gin.log_scales + 3 * g + 1),
-                                                          __ldg(gin.log_scales + 3 * g + 2));
-                            const float4 qq = __ldg(reinterpret_cast<const float4 *>(gin.quats) + g);
-                            sigma_from_sq(ls, qq, S);
+                            sigma_from_sq(cls, cq, S);
                         }
                         have_sigma = true;
                     }
@@ -274,7 +288,7 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(const gs_cam
                             en.uc = pj.uc; en.vc = pj.vc; en.zk = zk; en.r = r;
                             en.A = pj.c * idet; en.B = -pj.b * idet; en.C = pj.a * idet;
                             en.d0 = pj.d0; en.d1 = pj.d1; en.d2 = pj.d2;
-                            if (gin.av_G && (tb->flags & GS_FLAG_AVATAR_CANONICAL_SH) && g >= cov_begin)
+                            if (FUSED && (tb->flags & GS_FLAG_AVATAR_CANONICAL_SH) && g >= cov_begin)
                                 canonical_direction(gin, tb->env_av_base[c.e0] + (g - cov_begin), en.d0, en.d1,
                                                     en.d2);
                             en.x0 = (uint16_t)x0; en.x1 = (uint16_t)x1; en.y0 = (uint16_t)y0; en.y1 = (uint16_t)y1;
@@ -298,6 +312,8 @@ __global__ void __launch_bounds__(kPreThreads, 3) preprocess_kernel(const gs_cam
         mx = nx;
         my = ny;
         mz = nz;
+        cls = nls;
+        cq = nq;
     }
     if (tail > head) {
         const bool act = lane < tail - head;
@@ -919,10 +935,14 @@ void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w
     }
     const unsigned grid = (unsigned)n_chunks;
     if (grid == 0) return;
-    switch (g->sh_dtype) {
-    case GS_SH_F16: preprocess_kernel<GS_SH_F16><<<grid, kPreThreads, kPreSmem, s>>>(cams, gin, w); break;
-    case GS_SH_BF16: preprocess_kernel<GS_SH_BF16><<<grid, kPreThreads, kPreSmem, s>>>(cams, gin, w); break;
-    default: preprocess_kernel<GS_SH_F32><<<grid, kPreThreads, kPreSmem, s>>>(cams, gin, w); break;
+    const bool fused = gin.av_G != nullptr;
+    switch (g->sh_dtype * 2 + (fused ? 1 : 0)) {
+    case GS_SH_F16 * 2: preprocess_kernel<GS_SH_F16, false><<<grid, kPreThreads, kPreSmem, s>>>(cams, gin, w); break;
+    case GS_SH_F16 * 2 + 1: preprocess_kernel<GS_SH_F16, true><<<grid, kPreThreads, kPreSmem, s>>>(cams, gin, w); break;
+    case GS_SH_BF16 * 2: preprocess_kernel<GS_SH_BF16, false><<<grid, kPreThreads, kPreSmem, s>>>(cams, gin, w); break;
+    case GS_SH_BF16 * 2 + 1: preprocess_kernel<GS_SH_BF16, true><<<grid, kPreThreads, kPreSmem, s>>>(cams, gin, w); break;
+    case GS_SH_F32 * 2 + 1: preprocess_kernel<GS_SH_F32, true><<<grid, kPreThreads, kPreSmem, s>>>(cams, gin, w); break;
+    default: preprocess_kernel<GS_SH_F32, false><<<grid, kPreThreads, kPreSmem, s>>>(cams, gin, w); break;
     }
 }
 
@@ -983,12 +1003,15 @@ void launch_blend(const gs_camera *cams, const Ws &w, float *rgb, float *depth, 
 
 cudaError_t configure_forward_kernels()
 {
-    cudaError_t e = cudaFuncSetAttribute(preprocess_kernel<GS_SH_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kPreSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(preprocess_kernel<GS_SH_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPreSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(preprocess_kernel<GS_SH_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPreSmem);
+    cudaError_t e = cudaSuccess;
+    const void *pre[] = {reinterpret_cast<const void *>(preprocess_kernel<GS_SH_F32, false>),
+                         reinterpret_cast<const void *>(preprocess_kernel<GS_SH_F32, true>),
+                         reinterpret_cast<const void *>(preprocess_kernel<GS_SH_F16, false>),
+                         reinterpret_cast<const void *>(preprocess_kernel<GS_SH_F16, true>),
+                         reinterpret_cast<const void *>(preprocess_kernel<GS_SH_BF16, false>),
+                         reinterpret_cast<const void *>(preprocess_kernel<GS_SH_BF16, true>)};
+    for (const void *k : pre)
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kPreSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScatterSmem);
     return e;

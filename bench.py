@@ -260,6 +260,66 @@ def dram_traffic():
     return t.get("kernels", {})
 
 
+FWD_KERNELS = ("setup_kernel", "preprocess_kernel", "scan_bins_kernel", "scatter_kernel", "sort_chunks_kernel",
+               "merge_pass_kernel", "blend_persistent_kernel")
+BWD_KERNELS = ("clear_record_grads_kernel", "blend_backward_kernel", "preprocess_backward_kernel")
+
+
+def ncu_summary(csv_path, command):
+    """Per-kernel launches, time share and DRAM bytes of an ncu --csv launch
+    list of this bench (metrics gpu__time_duration.sum, dram__bytes_read.sum,
+    dram__bytes_write.sum); writes profiles/dram_traffic.json (bytes per
+    gs_render / gs_render_backward call, tagged with the kernel sources' hash)
+    and prints the table."""
+    import collections
+    import csv
+    import re
+
+    with open(csv_path) as f:
+        rows = [r for r in csv.reader(f) if len(r) > 10]
+    h, rows = rows[0], rows[1:]
+    iK, iM, iV, iID, iU = (h.index(x) for x in ("Kernel Name", "Metric Name", "Metric Value", "ID", "Metric Unit"))
+    per, names = collections.defaultdict(dict), {}
+    to_ms = {"nsecond": 1e-6, "ns": 1e-6, "usecond": 1e-3, "us": 1e-3, "msecond": 1.0, "ms": 1.0, "second": 1e3}
+    for r in rows:
+        v = float(r[iV].replace(",", ""))
+        if r[iM] == "gpu__time_duration.sum":
+            v *= to_ms.get(r[iU], 1e-6)
+        per[r[iID]][r[iM]] = v
+        m = re.match(r"(?:void )?(?:gs::)?([A-Za-z_0-9]+)", r[iK])
+        names[r[iID]] = m.group(1) if m else r[iK][:40]
+    agg = collections.OrderedDict()
+    for i, d in per.items():
+        a = agg.setdefault(names[i], dict(launches=0, ms=0.0, rd=0.0, wr=0.0))
+        a["launches"] += 1
+        a["ms"] += d.get("gpu__time_duration.sum", 0.0)
+        a["rd"] += d.get("dram__bytes_read.sum", 0.0)
+        a["wr"] += d.get("dram__bytes_write.sum", 0.0)
+    ours = {k: a for k, a in agg.items() if k in FWD_KERNELS + BWD_KERNELS}
+    n_fwd = max(agg.get("preprocess_kernel", {}).get("launches", 0), 1)
+    n_bwd = max(agg.get("blend_backward_kernel", {}).get("launches", 0), 1)
+    tot = sum(a["ms"] for a in ours.values())
+    kern = {}
+    print(f"{'kernel':28s} {'launches':>8s} {'total ms':>9s} {'share':>6s} {'ms/launch':>9s} {'DRAM MB/launch':>14s}")
+    for k, a in sorted(ours.items(), key=lambda x: -x[1]["ms"]):
+        calls = n_fwd if k in FWD_KERNELS else n_bwd
+        kern[k] = {"dram_bytes_per_call": (a["rd"] + a["wr"]) / calls, "launches_per_call": a["launches"] / calls,
+                   "ms_per_call_under_ncu": a["ms"] / calls}
+        print(f"{k:28s} {a['launches']:8d} {a['ms']:9.3f} {100 * a['ms'] / tot:5.1f}% {a['ms'] / a['launches']:9.4f} "
+              f"{(a['rd'] + a['wr']) / a['launches'] / 1e6:14.1f}  rd {a['rd'] / a['launches'] / 1e6:.1f} "
+              f"wr {a['wr'] / a['launches'] / 1e6:.1f}")
+    rest = [a for k, a in agg.items() if k not in ours]
+    print(f"(other kernels: {sum(a['launches'] for a in rest)} launches, {sum(a['ms'] for a in rest):.3f} ms; "
+          f"{n_fwd} forward and {n_bwd} backward calls)")
+    out = {"source_hash": source_hash(),
+           "what": "DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of each kernel per gs_render / "
+                   "gs_render_backward call (all its launches in that call), from one ncu run; stale once the "
+                   "kernel sources change (source_hash over csrc/)",
+           "command": command, "kernels": kern}
+    with open(os.path.join(ROOT, "profiles", "dram_traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+
+
 def rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_pix, N, sm_count, sm_mhz):
     """Achieved vs peak per kernel, from live CUDA-event stage times."""
     hbm, peak_kind = peaks()
@@ -267,11 +327,19 @@ def rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_pix, N, sm_count, sm_mh
     alu_peak = sm_count * 128 * mhz * 1e6 / 1e12  # FP32 lanes x clock, T lane-ops/s
     R, nvis, P = stats["n_records"], stats["n_visible"], stats["n_pairs"]
     traffic = dram_traffic()
-    mem = {  # algorithmic bytes per launch (FP16 SH storage)
-        "preprocess": 16 * R + nvis * (12 + 16 + 4 + 96 + 44),
+    # algorithmic bytes per launch (FP16 SH storage; one view per env, so a
+    # visible record is one seen Gaussian)
+    mem = {
+        # means of every Gaussian, the visibility bits; per visible record its
+        # scales + rotation, opacity logit, SH, the 48-byte record and the
+        # 64-byte gradient row it clears
+        "preprocess": 12 * N + R // 8 + nvis * (28 + 4 + 96 + 48 + 64),
         "scatter": nvis * 20 + 12 * P,
         "sort": 16 * P,
-        "preprocess_backward": 12 * N + nvis * (12 + 16 + 4 + 96 + 40) + N * 59 * 4,
+        # the visibility bits; per seen Gaussian its parameters (means, scales +
+        # rotation, opacity logit, SH), its 64-byte gradient row and its
+        # 236-byte parameter gradient
+        "preprocess_backward": R // 8 + nvis * (12 + 28 + 4 + 96 + 64 + 236),
     }
     ops = {"blend": OPS_PER_EVAL_FWD * n_eval_fwd, "blend_backward": OPS_PER_EVAL_BWD * n_eval_bwd}
     ms = dict(stage_ms)
@@ -294,6 +362,10 @@ def rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_pix, N, sm_count, sm_mh
         kern = [KERNEL_OF_STAGE[x] for x in (("sort_chunks", "merge") if k == "sort" else (k,))]
         tb = [traffic.get(x, {}).get("dram_bytes_per_call") for x in kern]
         v["traffic"] = None if any(x is None for x in tb) else float(sum(tb))
+    if "blend_backward" in out:
+        # the persistent backward also writes the zero gradients of the
+        # Gaussians no pixel saw (236 bytes each, between tiles)
+        out["blend_backward"]["also_writes_bytes"] = 236 * (N - nvis)
     dom = max(out, key=lambda k: out[k]["ms"])
     roof = dict(out[dom], kernel=dom)
     return roof, out
@@ -653,7 +725,8 @@ def run_ours(args, ws, rank, local):
         "e2e": {"value": total_envs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "what": "public API calls per step: cameras H2D from pinned memory, "
                                                    "gs_render + gs_render_backward, RGB + depth D2H"},
-        "gpu_launches": (rend.kernels_per_forward() + 2) * args.steps,  # + blend_backward, preprocess_backward
+        # + clear_record_grads, blend_backward, preprocess_backward
+        "gpu_launches": (rend.kernels_per_forward() + 3) * args.steps,
         "clocks": clocks,
         "stage_ms": stage_ms,
         "stats": {"records": stats["n_records"], "visible": stats["n_visible"],
@@ -679,7 +752,12 @@ def main():
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--tile", default="", help="fixed tile_w,tile_h,batch_depth instead of the autotuner")
     ap.add_argument("--envs", type=int, default=N_ENVS, help="envs per GPU (64; fewer only for small profiling cases)")
+    ap.add_argument("--ncu-summary", nargs=2, metavar=("CSV", "COMMAND"),
+                    help="summarise an ncu launch list of this bench into profiles/dram_traffic.json and exit")
     args = ap.parse_args()
+    if args.ncu_summary:
+        ncu_summary(*args.ncu_summary)
+        return
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = dist_init()

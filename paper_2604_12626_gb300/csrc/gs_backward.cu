@@ -169,6 +169,28 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
             }
         }
     }
+    // PX == 2: the two pixels of a row as packed FP32 pairs.  The colour and
+    // depth terms of dL/dalpha enter through one running dot product per
+    // pixel, ndcs = -(dC . S), S the colour and depth accumulated behind the
+    // current pair: S grows by c wgt, so ndcs falls by wgt (dC . c).
+    float2 T2[PY], ndcs[PY], dc0[PY], dc1[PY], dc2[PY], dd[PY];
+    if constexpr (PX == 2) {
+#pragma unroll
+        for (int b = 0; b < PY; ++b) {
+            T2[b] = make_float2(T[2 * b], T[2 * b + 1]);
+            dc0[b] = make_float2(dC0[2 * b], dC0[2 * b + 1]);
+            dc1[b] = make_float2(dC1[2 * b], dC1[2 * b + 1]);
+            dc2[b] = make_float2(dC2[2 * b], dC2[2 * b + 1]);
+            dd[b] = make_float2(dD[2 * b], dD[2 * b + 1]);
+            float x[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int q = 2 * b + e;
+                x[e] = -(dC0[q] * S0[q] + dC1[q] * S1[q] + dC2[q] * S2[q] + dD[q] * SD[q]);
+            }
+            ndcs[b] = make_float2(x[0], x[1]);
+        }
+    }
     const int lane = threadIdx.x & 31;
     const int nb = (int)((n_proc - seg_lo + B - 1) / B);
     // batch b covers [lo_b, hi_b), hi_b = n_proc - b B, lo_b >= seg_lo
@@ -264,8 +286,71 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
                         ok[u][p] = k >= 0 && (uint32_t)(lo + k) < last[p] &&
                                    fmaxf(fabsf(dxs[u][p]), fabsf(dys[u][p])) <= a.w && pw[p] <= 0.0f &&
                                    fminf(kAlphaMax, ar[u][p]) >= kAlphaMin;
+                        if (!ok[u][p]) ex[u][p] = 0.f; // finite where a zero weight multiplies it
                     }
                 }
+                if constexpr (PX == 2) {
+                    // every pixel of the group: a pixel that the pair does not
+                    // reach gets alpha = 0 and adds exact zeros
+                    float2 G[kGroup][10];
+#pragma unroll
+                    for (int u = 0; u < kGroup; ++u)
+#pragma unroll
+                        for (int x = 0; x < 10; ++x) G[u][x] = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int u = 0; u < kGroup; ++u) {
+                        const int k = k1 - u;
+                        const float4 a = s0[k < 0 ? 0 : k];
+                        const float4 q = s1[k < 0 ? 0 : k];
+                        const float4 c = s2[k < 0 ? 0 : k];
+                        const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y),
+                                     cz = make_float2(c.z, c.z), az = make_float2(a.z, a.z);
+                        const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y);
+#pragma unroll
+                        for (int b = 0; b < PY; ++b) {
+                            const int p0 = 2 * b, p1 = 2 * b + 1;
+                            if (!(ok[u][p0] || ok[u][p1])) continue;
+                            contrib = true;
+                            const float2 nal = make_float2(ok[u][p0] ? -fminf(kAlphaMax, ar[u][p0]) : 0.f,
+                                                           ok[u][p1] ? -fminf(kAlphaMax, ar[u][p1]) : 0.f);
+                            const float2 om = __fadd2_rn(make_float2(1.f, 1.f), nal);
+                            const float2 iom = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
+                            const float2 Ti = __fmul2_rn(T2[b], iom);
+                            const float2 nwgt = __fmul2_rn(nal, Ti);
+                            G[u][6] = __ffma2_rn(nwgt, dc0[b], G[u][6]);
+                            G[u][7] = __ffma2_rn(nwgt, dc1[b], G[u][7]);
+                            G[u][8] = __ffma2_rn(nwgt, dc2[b], G[u][8]);
+                            G[u][9] = __ffma2_rn(nwgt, dd[b], G[u][9]);
+                            const float2 dcc = __ffma2_rn(
+                                dd[b], az, __ffma2_rn(dc2[b], cz, __ffma2_rn(dc1[b], cy, __fmul2_rn(dc0[b], cx))));
+                            const float2 dal = __ffma2_rn(ndcs[b], iom, __fmul2_rn(dcc, Ti));
+                            ndcs[b] = __ffma2_rn(nwgt, dcc, ndcs[b]);
+                            T2[b] = Ti;
+                            // the 0.99 clamp passes no gradient to opacity and footprint
+                            const float2 dalm = make_float2(ar[u][p0] < kAlphaMax ? dal.x : 0.f,
+                                                            ar[u][p1] < kAlphaMax ? dal.y : 0.f);
+                            const float2 dx = make_float2(dxs[u][p0], dxs[u][p1]);
+                            const float dy1 = dys[u][p0];
+                            const float2 dy = make_float2(dy1, dy1);
+                            G[u][5] = __ffma2_rn(dalm, make_float2(ex[u][p0], ex[u][p1]), G[u][5]);
+                            const float2 ngp = __fmul2_rn(dalm, nal); // -dL/dalpha * alpha
+                            const float qyd = q.y * dy1, qzd = q.z * dy1;
+                            G[u][0] = __ffma2_rn(ngp, __ffma2_rn(qx, dx, make_float2(qyd, qyd)), G[u][0]);
+                            G[u][1] = __ffma2_rn(ngp, __ffma2_rn(qy, dx, make_float2(qzd, qzd)), G[u][1]);
+                            const float2 hgp = __fmul2_rn(ngp, make_float2(0.5f, 0.5f));
+                            G[u][2] = __ffma2_rn(__fmul2_rn(hgp, dx), dx, G[u][2]);
+                            G[u][3] = __ffma2_rn(__fmul2_rn(ngp, dx), dy, G[u][3]);
+                            G[u][4] = __ffma2_rn(__fmul2_rn(hgp, dy), dy, G[u][4]);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kGroup; ++u) {
+#pragma unroll
+                        for (int x = 0; x < 6; ++x) g[10 * u + x] = G[u][x].x + G[u][x].y;
+#pragma unroll
+                        for (int x = 6; x < 10; ++x) g[10 * u + x] = -(G[u][x].x + G[u][x].y);
+                    }
+                } else {
 #pragma unroll
                 for (int u = 0; u < kGroup; ++u) {
                     const int k = k1 - u;
@@ -305,6 +390,7 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
                             }
                         }
                     }
+                }
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {

@@ -40,8 +40,8 @@ N_ENVS, W, H = 64, 256, 256
 N_MIN, N_MAX = 300_000, 1_500_000
 # (tile_w, tile_h, batch_depth, pixels per thread x, y)
 TILE_CANDIDATES = [(16, 16, 256, 1, 1), (16, 16, 256, 2, 2), (16, 16, 128, 2, 2), (16, 16, 128, 2, 1),
-                   (16, 8, 128, 1, 1), (16, 8, 128, 2, 1), (8, 8, 64, 1, 1), (8, 8, 128, 1, 1), (8, 8, 64, 2, 1),
-                   (32, 16, 256, 2, 2)]
+                   (16, 8, 128, 1, 1), (16, 8, 128, 2, 1), (16, 8, 64, 2, 2), (16, 8, 128, 2, 2), (8, 8, 64, 1, 1),
+                   (8, 8, 128, 1, 1), (8, 8, 64, 2, 1), (32, 16, 256, 2, 2)]
 
 
 def peaks():
@@ -541,7 +541,10 @@ def run_ours(args, ws, rank, local):
     G32 = api.Gaussians(means, ls, quats, ologit, sh32)
 
     # --- autotune the batched renderer (tile, batch depth), cached per GPU + workload
-    rend = api.Renderer(batch, W, H, device=dev, tile=(8, 8), batch_depth=64, persistent=True, grad_overwrite=True)
+    fixed = [int(x) for x in args.tile.split(",")] + [1, 1] if args.tile else None
+    cands = [fixed[:5]] if fixed else TILE_CANDIDATES
+    rend = api.Renderer(batch, W, H, device=dev, tile=(8, 8), batch_depth=64, persistent=True, grad_overwrite=True,
+                        tile_candidates=cands)
     cache_path = os.path.join(ROOT, "paper_2604_12626_gb300", "_build", "autotune.json")
     key = f"{torch.cuda.get_device_name(dev)}|{n_envs}x{W}x{H}|N={N}|f16|fwd+bwd"
     cache = {}
@@ -550,10 +553,9 @@ def run_ours(args, ws, rank, local):
             cache = json.load(f)
     except Exception:
         pass
-    if args.tile:
-        ch = [int(x) for x in args.tile.split(",")] + [1, 1]
-        rend.cfg.tile_w, rend.cfg.tile_h, rend.cfg.batch_depth, rend.cfg.pix_x, rend.cfg.pix_y = ch[:5]
-        tuned = {"choice": ch[:5], "fixed": True}
+    if fixed:
+        rend.cfg.tile_w, rend.cfg.tile_h, rend.cfg.batch_depth, rend.cfg.pix_x, rend.cfg.pix_y = fixed[:5]
+        tuned = {"choice": fixed[:5], "fixed": True}
     elif key in cache and not args.retune:
         ch = cache[key]["choice"]
         rend.cfg.tile_w, rend.cfg.tile_h, rend.cfg.batch_depth, rend.cfg.pix_x, rend.cfg.pix_y = ch

@@ -258,11 +258,16 @@ class Gaussians:
 class Renderer:
     """A configured renderer with its own workspace (one gs_render / gs_render_backward pair)."""
 
-    def __init__(self, batch: Batch, width: int, height: int, device="cuda", **cfg_kw):
+    def __init__(self, batch: Batch, width: int, height: int, device="cuda", tile_candidates=None, **cfg_kw):
+        """``tile_candidates``: (tile_w, tile_h, batch_depth, pix_x, pix_y)
+        rows the workspace must also fit (for autotune over them)."""
         self.batch = batch
         self.cfg = make_config(width, height, **cfg_kw)
         self.device = torch.device(device)
         self.ws_bytes = workspace_size(self.cfg, batch)
+        for c in tile_candidates or ():
+            k = dict(cfg_kw, tile=(c[0], c[1]), batch_depth=c[2], pix=(c[3], c[4]))
+            self.ws_bytes = max(self.ws_bytes, workspace_size(make_config(width, height, **k), batch))
         self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
         self.workspace[:4096].zero_()  # status word and counters
 

@@ -328,7 +328,9 @@ gs_status gs_autotune(const gs_gaussians *g, const gs_batch *batch, const gs_cam
  *              where uc = u - cx, vc = v - cy, z the FP32 depth key, r the radius;
  *              R = n_records, record of (view v, local index k) at view_rec_off[v] + k
  *   vis        [ceil(R/32)] uint32 visibility bits
- *   keys       [pair_capacity] uint64 (depth bits << 32 | record), sorted per bin
+ *   keys       [pair_capacity] uint64 (depth bits << 32 | record), sorted per bin;
+ *              after the blend, bit 31 (the record word's top bit) is set on
+ *              the pairs that some pixel of their tile blended
  *   bin_start  [n_bins + 1] uint32, bin = view * tiles_per_view + ty * tiles_x + tx */
 typedef struct {
     void *records, *vis, *keys, *bin_start;

@@ -354,7 +354,8 @@ class Renderer:
 
     def sections(self) -> dict:
         """Views into the workspace left by the last forward: records [R,12] float32,
-        vis [ceil(R/32)] int32 bits, keys [cap] int64 (depth bits << 32 | record),
+        vis [ceil(R/32)] int32 bits, keys [cap] int64 (depth bits << 32 | record; bit 31 set
+        by the blend on pairs some pixel of the tile blended),
         bin_start [n_bins+1] int32, plus the tile grid."""
         s = GsWsSections()
         _check(_lib.gs_workspace_sections(ctypes.byref(self.cfg), ctypes.byref(self.batch.c), _ptr(self.workspace),

@@ -95,7 +95,7 @@ template <int PX, int PY>
 __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera *cams, const float *d_rgb,
                                                    const float *d_depth, int bin, uint32_t seg_lo, uint32_t seg_hi,
                                                    int64_t ck_slot, float4 *sm, float *acc, uint32_t *sidx,
-                                                   uint32_t *smax_last)
+                                                   uint32_t *clist, uint32_t *smax_last)
 {
     constexpr int NP = PX * PY;
     const Table *tb = w.tb;
@@ -216,13 +216,16 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
         for (int q = 0; q < kMaxPerB; ++q) {
             const int e = threadIdx.x + q * nthr;
             if (e < cnt) {
-                uint32_t rec = (uint32_t)kr[q];
+                const uint32_t word = (uint32_t)kr[q], fl = word & kKeyBlended;
+                uint32_t rec = word & kKeyRecord;
                 if (rec >= R) rec = 0; // only after a capacity overflow
-                const float4 *src = w.rec + 3 * (size_t)rec;
-                cp_async16(buf + e, src);
-                cp_async16(buf + B + e, src + 1);
-                cp_async16(buf + 2 * B + e, src + 2);
-                ib[e] = rec;
+                if (fl) { // pairs that no pixel blended are never read
+                    const float4 *src = w.rec + 3 * (size_t)rec;
+                    cp_async16(buf + e, src);
+                    cp_async16(buf + B + e, src + 1);
+                    cp_async16(buf + 2 * B + e, src + 2);
+                }
+                ib[e] = rec | fl;
             }
         }
     };
@@ -240,23 +243,40 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
         for (int k = threadIdx.x; k < cnt * kAccStride; k += nthr) acc[k] = 0.0f;
         cp_async_wait<1>();
         __syncthreads();
+        const uint32_t *ibc = sidx + (b & 1) * B;
+        if (threadIdx.x < 32) { // the batch's blended entries, in list order
+            uint32_t base = 0;
+            for (int c0 = 0; c0 < cnt; c0 += 32) {
+                const int k = c0 + lane;
+                const bool f = k < cnt && (ibc[k] & kKeyBlended);
+                const unsigned bal = __ballot_sync(0xffffffffu, f);
+                if (f) clist[base + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)k;
+                base += __popc(bal);
+            }
+            if (lane == 0) clist[B] = base;
+        }
+        __syncthreads();
+        const int ncl = (int)clist[B];
         const float4 *s0 = sm + (b & 1) * 3 * B, *s1 = s0 + B, *s2 = s0 + 2 * B;
-        // groups of kGroup Gaussians, back to front: falloff and alpha first
-        // (independent of T), then the sequential transmittance rebuild and
-        // gradients, then one warp reduction of the group's 10 x kGroup sums
-        for (int k1 = cnt - 1; k1 >= 0; k1 -= kGroup) {
+        // groups of kGroup blended Gaussians, back to front: falloff and alpha
+        // first (independent of T), then the sequential transmittance rebuild
+        // and gradients, then one warp reduction of the group's 10 x kGroup sums
+        for (int i1 = ncl - 1; i1 >= 0; i1 -= kGroup) {
+            int kk[kGroup]; // entries of the group (-1: past the list's front)
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u) kk[u] = i1 - u >= 0 ? (int)clist[i1 - u] : -1;
             float g[32];
 #pragma unroll
             for (int x = 0; x < 32; ++x) g[x] = 0.f;
             bool contrib = false;
-            if (__any_sync(0xffffffffu, (uint32_t)(lo + k1 - (kGroup - 1)) < tlast || k1 < kGroup - 1)) {
+            if (__any_sync(0xffffffffu, i1 < kGroup - 1 || (uint32_t)(lo + kk[kGroup - 1]) < tlast)) {
                 float ar[kGroup][NP], ex[kGroup][NP], dxs[kGroup][NP], dys[kGroup][NP];
                 bool ok[kGroup][NP];
 #pragma unroll
                 for (int u = 0; u < kGroup; ++u) {
-                    const int k = k1 - u;
-                    const float4 a = s0[k < 0 ? 0 : k];
-                    const float4 q = s1[k < 0 ? 0 : k];
+                    const int k = kk[u], ks = k < 0 ? kk[0] : k;
+                    const float4 a = s0[ks];
+                    const float4 q = s1[ks];
                     float pw[NP];
                     if constexpr (PX == 2) {
                         // the two pixels of a row as packed FP32 pairs
@@ -299,10 +319,10 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
                         for (int x = 0; x < 10; ++x) G[u][x] = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int u = 0; u < kGroup; ++u) {
-                        const int k = k1 - u;
-                        const float4 a = s0[k < 0 ? 0 : k];
-                        const float4 q = s1[k < 0 ? 0 : k];
-                        const float4 c = s2[k < 0 ? 0 : k];
+                        const int ks = kk[u] < 0 ? kk[0] : kk[u];
+                        const float4 a = s0[ks];
+                        const float4 q = s1[ks];
+                        const float4 c = s2[ks];
                         const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y),
                                      cz = make_float2(c.z, c.z), az = make_float2(a.z, a.z);
                         const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y);
@@ -353,10 +373,10 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
                 } else {
 #pragma unroll
                 for (int u = 0; u < kGroup; ++u) {
-                    const int k = k1 - u;
-                    const float4 a = s0[k < 0 ? 0 : k];
-                    const float4 q = s1[k < 0 ? 0 : k];
-                    const float4 c = s2[k < 0 ? 0 : k];
+                    const int ks = kk[u] < 0 ? kk[0] : kk[u];
+                    const float4 a = s0[ks];
+                    const float4 q = s1[ks];
+                    const float4 c = s2[ks];
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
                         if (ok[u][p]) {
@@ -396,18 +416,17 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
             if (__any_sync(0xffffffffu, contrib)) {
                 const float tot = warp_transpose_sum32(g);
                 const int u = lane / 10, j = lane - 10 * u;
-                const int k = k1 - u;
-                if (lane < 10 * kGroup && k >= 0) atomicAdd(acc + k * kAccStride + j, tot);
+                if (lane < 10 * kGroup && i1 - u >= 0) atomicAdd(acc + clist[i1 - u] * kAccStride + j, tot);
             }
         }
         __syncthreads();
-        const uint32_t *ib = sidx + (b & 1) * B;
-        for (int k = threadIdx.x; k < cnt; k += nthr) {
+        for (int i = threadIdx.x; i < ncl; i += nthr) {
+            const int k = (int)clist[i];
             const float4 *ak = reinterpret_cast<const float4 *>(acc + k * kAccStride);
             const float4 x0 = ak[0], x1 = ak[1], x2 = ak[2];
             if (x0.x != 0.f || x0.y != 0.f || x0.z != 0.f || x0.w != 0.f || x1.x != 0.f || x1.y != 0.f ||
                 x1.z != 0.f || x1.w != 0.f || x2.x != 0.f || x2.y != 0.f) {
-                float4 *dst = reinterpret_cast<float4 *>(w.d_rec + (size_t)ib[k] * kGradStride);
+                float4 *dst = reinterpret_cast<float4 *>(w.d_rec + (size_t)(ibc[k] & kKeyRecord) * kGradStride);
                 atomicAdd(dst + 0, x0);
                 atomicAdd(dst + 1, x1);
                 atomicAdd(dst + 2, x2);
@@ -450,6 +469,7 @@ __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, 
     const int B = w.tb->batch_depth;
     float *acc = reinterpret_cast<float *>(smem_b + 2 * 3 * B); // [B][kAccStride]
     uint32_t *sidx = reinterpret_cast<uint32_t *>(acc + B * kAccStride); // [2][B]
+    uint32_t *clist = sidx + 2 * B;                                        // [B + 1]
     // items: the kSeg-long segments of the heavy bins (largest bins first),
     // then every other bin whole
     const uint32_t nhi = w.hdr->n_heavy_items, nh = w.hdr->n_heavy;
@@ -469,12 +489,12 @@ __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, 
             }
             const uint32_t s = item - w.heavy_seg[lo];
             blend_backward_tile<PX, PY>(w, cams, d_rgb, d_depth, (int)w.heavy[lo], s * kSeg, (s + 1) * kSeg,
-                                        (int64_t)w.heavy_seg[lo] + s, smem_b, acc, sidx, &smax_last);
+                                        (int64_t)w.heavy_seg[lo] + s, smem_b, acc, sidx, clist, &smax_last);
         } else {
             const uint32_t b = item - nhi;
             if (w.bin_count[b] + w.bin_fcount[b] < w.hdr->heavy_min)
                 blend_backward_tile<PX, PY>(w, cams, d_rgb, d_depth, (int)b, 0u, 0xffffffffu, 0, smem_b, acc, sidx,
-                                            &smax_last);
+                                            clist, &smax_last);
         }
         if (zw.total) { // one clearing item between tiles
             __syncthreads();
@@ -850,7 +870,8 @@ void launch_count_visible(const Ws &w, int64_t n_words, cudaStream_t s)
 
 static int blend_bwd_smem(int batch_depth)
 {
-    return 2 * 3 * batch_depth * (int)sizeof(float4) + batch_depth * kAccStride * 4 + 2 * batch_depth * 4;
+    return 2 * 3 * batch_depth * (int)sizeof(float4) + batch_depth * kAccStride * 4 + 2 * batch_depth * 4 +
+           (batch_depth + 1) * 4;
 }
 
 template <int PX, int PY>

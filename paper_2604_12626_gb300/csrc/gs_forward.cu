@@ -666,11 +666,21 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
     const float2 npx2 = make_float2(-pxc[0], -pxc[PX - 1]);
     uint32_t start, n;
     bin_range(w, bin, start, n);
-    const unsigned long long *keys = w.keys + start;
+    unsigned long long *keys = w.keys + start;
     const int B = tb->batch_depth;
     const int nthr = blockDim.x;
     const uint32_t R = (uint32_t)tb->n_records;
     const int nb = (int)((n + B - 1) / B);
+    // bits of the current 32-entry window whose Gaussian some pixel of this
+    // thread blended; OR-ed over the warp and flagged in the key (bit 31 of
+    // the record word) so that the backward walks the blended pairs only
+    uint32_t mk = 0;
+    const int lane = threadIdx.x & 31;
+    auto flag_window = [&](uint32_t base) {
+        const uint32_t wm = __reduce_or_sync(0xffffffffu, mk);
+        mk = 0;
+        if ((wm >> lane) & 1u) atomicOr(reinterpret_cast<unsigned int *>(keys + base + lane), kKeyBlended);
+    };
     unsigned long long kr[kMaxPer];
     auto load_keys = [&](int b) {
 #pragma unroll
@@ -687,7 +697,7 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
             const int e = threadIdx.x + q * nthr;
             const uint32_t idx = (uint32_t)b * B + e;
             if (e < B && idx < n) {
-                uint32_t rec = (uint32_t)kr[q];
+                uint32_t rec = (uint32_t)kr[q] & kKeyRecord;
                 if (rec >= R) rec = 0; // only after a capacity overflow
                 const float4 *src = w.rec + 3 * (size_t)rec;
                 cp_async16(buf + e, src);
@@ -741,7 +751,10 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
         // time: their falloff and alpha (independent of T) first, for ILP, then
         // the front-to-back updates in order.
         for (int k0 = 0; k0 < cnt; k0 += kUnroll) {
-            if (__all_sync(0xffffffffu, tdone)) break;
+            if (__all_sync(0xffffffffu, tdone)) {
+                if (k0 & 31) flag_window((uint32_t)b * B + (uint32_t)(k0 & ~31));
+                break;
+            }
             if (!tdone) {
                 float al[kUnroll][NP];
                 bool ok[kUnroll][NP], cv[kUnroll][NP];
@@ -798,6 +811,7 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
                             const float2 Tn = __fmul2_rn(T2, om);
                             const bool s0b = k0k && Tn.x < kTStop, s1b = k1k && Tn.y < kTStop;
                             const bool bl0 = k0k && !s0b, bl1 = k1k && !s1b;
+                            mk |= (uint32_t)(bl0 || bl1) << ((k0 + u) & 31);
                             dn[p0] = dn[p0] || s0b;
                             dn[p1] = dn[p1] || s1b;
                             const float2 wgt =
@@ -838,6 +852,7 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
                                     T[p] = Tn;
                                     ncon[p] = ncov[p];
                                     last[p] = (uint32_t)b * B + k0 + u + 1;
+                                    mk |= 1u << ((k0 + u) & 31);
                                 }
                             }
                         }
@@ -847,6 +862,8 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
 #pragma unroll
                 for (int p = 0; p < NP; ++p) tdone = tdone && dn[p];
             }
+            if (((k0 + kUnroll) & 31) == 0 || k0 + kUnroll >= cnt)
+                flag_window((uint32_t)b * B + (uint32_t)(k0 & ~31));
             __syncwarp();
         }
         __syncthreads();

@@ -31,6 +31,10 @@ namespace gs {
 
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
+// sorted pair keys: depth bits << 32 | record; the blend sets bit 31 of the
+// record word once some pixel of the tile has blended the pair
+constexpr uint32_t kKeyBlended = 0x80000000u;
+constexpr uint32_t kKeyRecord = 0x7fffffffu;
 constexpr float kTStop = 1e-4f;
 constexpr float kDilation = 0.3f;
 constexpr int kSortChunk = 4096; // keys one CTA sorts; larger bins are merged

@@ -50,12 +50,39 @@ def _check_keys(r, cams, W, H, view_of_rec):
     rec = s["records"].cpu().numpy()
     vis = s["vis"].cpu().numpy()
     bs = s["bin_start"].cpu().numpy().astype(np.int64)
-    keys = s["keys"].cpu().numpy().view(np.uint64)
+    raw = s["keys"].cpu().numpy().view(np.uint64)[:bs[-1]]
+    blended = (raw >> np.uint64(31)) & np.uint64(1)
+    keys = raw & ~np.uint64(1 << 31)  # the blend flags pairs in bit 31 of the record word
     counts, ref = reference_keys(rec, vis, view_of_rec, cams, W, H, r.cfg.tile_w, r.cfg.tile_h)
     n_bins = s["n_bins"]
     assert np.array_equal(np.diff(bs), counts[:n_bins]), "bin counts (tile ranges) differ"
-    assert np.array_equal(keys[:bs[-1]], ref), "sorted keys differ"
+    assert np.array_equal(keys, ref), "sorted keys differ"
+    _check_blended_flags(rec, keys, blended.astype(bool), bs, cams, W, H, r.cfg.tile_w, r.cfg.tile_h)
     return int(bs[-1])
+
+
+def _check_blended_flags(rec, keys, blended, bs, cams, W, H, tw, th, sample=20000):
+    """A pair flagged as blended has, at some pixel of its tile and inside its
+    square footprint, power <= 0 and alpha >= 1/255 (checked in FP64 with a
+    small margin on a sample of the flagged pairs)."""
+    assert blended.any(), "no pair flagged as blended"
+    pos = np.flatnonzero(blended)
+    pos = np.random.default_rng(0).choice(pos, min(sample, pos.size), replace=False)
+    bins = np.searchsorted(bs, pos, side="right") - 1
+    tiles_x, tiles_y = (W + tw - 1) // tw, (H + th - 1) // th
+    v, t = bins // (tiles_x * tiles_y), bins % (tiles_x * tiles_y)
+    ri = (keys[pos] & np.uint64(0x7FFFFFFF)).astype(np.int64)
+    r_ = rec[ri].astype(np.float64)
+    uc, vc, rad, A, B, C, op = r_[:, 0], r_[:, 1], r_[:, 3], r_[:, 4], r_[:, 5], r_[:, 6], r_[:, 7]
+    ii = (t % tiles_x)[:, None] * tw + np.arange(tw)[None, :]
+    jj = (t // tiles_x)[:, None] * th + np.arange(th)[None, :]
+    dx = uc[:, None, None] - (ii[:, None, :] - cams[v, 14][:, None, None])
+    dy = vc[:, None, None] - (jj[:, :, None] - cams[v, 15][:, None, None])
+    inside = (ii[:, None, :] < W) & (jj[:, :, None] < H) & (np.maximum(np.abs(dx), np.abs(dy)) <= rad[:, None, None] + 1e-3)
+    power = -0.5 * (A[:, None, None] * dx * dx + C[:, None, None] * dy * dy) - B[:, None, None] * dx * dy
+    alpha = np.minimum(0.99, op[:, None, None] * np.exp(np.minimum(power, 0.0)))
+    ok = inside & (power <= 1e-5) & (alpha >= (1.0 / 255.0) * (1.0 - 1e-4))
+    assert ok.reshape(ok.shape[0], -1).any(axis=1).all(), "a pair flagged as blended reaches no pixel of its tile"
 
 
 def test_box_scene_keys_bit_exact(gs):

@@ -441,27 +441,47 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
 // backward then writes the rows of the Gaussians some view sees).  The clearing
 // is split into items of kZeroFloats floats that the persistent blend-backward
 // CTAs take one at a time between their tiles, so that the store stream to HBM
-// runs under the issue-bound blend instead of after it.
+// runs under the issue-bound blend instead of after it.  The 16-byte aligned
+// body of an item is written by TMA bulk copies from a zeroed shared-memory
+// buffer (one thread issues them; the load/store pipeline the blend needs for
+// its shared-memory traffic stays free), the unaligned ends by plain stores.
 constexpr int64_t kZeroFloats = 1 << 16;
+constexpr int kZeroBuf = 1024; // bytes of zeros in shared memory (small: the CTAs per SM stay 18)
 
-__device__ void zero_item(const ZeroWork &zw, uint32_t z)
+__device__ __forceinline__ void bulk_zero(char *dst, uint32_t bytes, uint32_t zbuf_saddr, uint64_t policy)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;\n" ::"l"(dst),
+                 "r"(zbuf_saddr), "r"(bytes), "l"(policy)
+                 : "memory");
+}
+
+__device__ __noinline__ void zero_item(const ZeroWork &zw, uint32_t z, uint32_t zbuf_saddr)
 {
     int a = 0;
     while (a + 1 < kZeroArrays && zw.first[a + 1] <= z) ++a;
     float *p = zw.p[a];
     const int64_t lo = (int64_t)(z - zw.first[a]) * kZeroFloats, hi = min(zw.n[a], lo + kZeroFloats);
-    // scalar up to the first 16-byte boundary and after the last, float4 between
+    // plain stores up to the first 16-byte boundary and after the last
     const int64_t a4 = min(hi, lo + (int64_t)((((16 - (reinterpret_cast<uintptr_t>(p + lo) & 15)) & 15)) >> 2));
     const int64_t n4 = (hi - a4) >> 2;
     if (lo + (int64_t)threadIdx.x < a4) p[lo + threadIdx.x] = 0.f;
-    float4 *q = reinterpret_cast<float4 *>(p + a4);
-    for (int64_t i = threadIdx.x; i < n4; i += blockDim.x) q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     const int64_t t0 = a4 + 4 * n4;
     if (t0 + (int64_t)threadIdx.x < hi) p[t0 + threadIdx.x] = 0.f;
+    if (threadIdx.x == 0 && n4 > 0) {
+        // the zeros stream through L2 ahead of the blend's records: evict them first
+        uint64_t policy;
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(policy));
+        char *d = reinterpret_cast<char *>(p + a4);
+        for (int64_t off = 0, nb = n4 * 16; off < nb; off += kZeroBuf)
+            bulk_zero(d + off, (uint32_t)min((int64_t)kZeroBuf, nb - off), zbuf_saddr, policy);
+        asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+    }
 }
 
+// at most 112 registers for one or two pixels per thread: 18 one-warp CTAs
+// per SM
 template <int PX, int PY>
-__global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, const float *__restrict__ d_rgb,
+__global__ void __maxnreg__(PX * PY == 4 ? 168 : 112) blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, const float *__restrict__ d_rgb,
                                       const float *__restrict__ d_depth, ZeroWork zw)
 {
     extern __shared__ float4 smem_b[];
@@ -470,11 +490,30 @@ __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, 
     float *acc = reinterpret_cast<float *>(smem_b + 2 * 3 * B); // [B][kAccStride]
     uint32_t *sidx = reinterpret_cast<uint32_t *>(acc + B * kAccStride); // [2][B]
     uint32_t *clist = sidx + 2 * B;                                        // [B + 1]
+    // zeros for the clearing items' bulk copies (16-byte aligned, after clist)
+    const uint32_t zoff = ((uint32_t)(reinterpret_cast<char *>(clist + B + 1) - reinterpret_cast<char *>(smem_b)) +
+                           15u) & ~15u;
+    float4 *zbuf = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem_b) + zoff);
+    const uint32_t zbuf_saddr = (uint32_t)__cvta_generic_to_shared(zbuf);
+    if (zw.total) {
+        for (int i = threadIdx.x; i < kZeroBuf / 16; i += blockDim.x) zbuf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); // visible to the bulk copies
+    }
     // items: the kSeg-long segments of the heavy bins (largest bins first),
     // then every other bin whole
     const uint32_t nhi = w.hdr->n_heavy_items, nh = w.hdr->n_heavy;
     const uint32_t n_items = nhi + (uint32_t)w.tb->n_bins;
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&w.hdr->n_backward, 1u); // d_rec is dirty from here on
+    // the first clear_ctas CTAs (about one per SM) clear first, so that the
+    // store stream runs from the start beside the heavy tiles; the others take
+    // tiles, then what is left of the clearing
+    for (bool clearing = zw.total && blockIdx.x < zw.clear_ctas; clearing;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item = atomicAdd(&w.hdr->queue_zero, 1u);
+        __syncthreads();
+        if (item >= zw.total) break;
+        zero_item(zw, item, zbuf_saddr);
+    }
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) item = atomicAdd(&w.hdr->queue_bwd, 1u);
@@ -496,20 +535,16 @@ __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, 
                 blend_backward_tile<PX, PY>(w, cams, d_rgb, d_depth, (int)b, 0u, 0xffffffffu, 0, smem_b, acc, sidx,
                                             clist, &smax_last);
         }
-        if (zw.total) { // one clearing item between tiles
-            __syncthreads();
-            if (threadIdx.x == 0) item = atomicAdd(&w.hdr->queue_zero, 1u);
-            __syncthreads();
-            if (item < zw.total) zero_item(zw, item);
-        }
     }
     for (;;) { // clearing items left when the tiles ran out
         __syncthreads();
         if (threadIdx.x == 0) item = zw.total ? atomicAdd(&w.hdr->queue_zero, 1u) : zw.total;
         __syncthreads();
         if (item >= zw.total) break;
-        zero_item(zw, item);
+        zero_item(zw, item, zbuf_saddr);
     }
+    // the bulk copies read the shared buffer until they complete
+    if (zw.total && threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -870,8 +905,9 @@ void launch_count_visible(const Ws &w, int64_t n_words, cudaStream_t s)
 
 static int blend_bwd_smem(int batch_depth)
 {
-    return 2 * 3 * batch_depth * (int)sizeof(float4) + batch_depth * kAccStride * 4 + 2 * batch_depth * 4 +
-           (batch_depth + 1) * 4;
+    const int base = 2 * 3 * batch_depth * (int)sizeof(float4) + batch_depth * kAccStride * 4 + 2 * batch_depth * 4 +
+                     (batch_depth + 1) * 4;
+    return ((base + 15) & ~15) + kZeroBuf;
 }
 
 template <int PX, int PY>
@@ -920,6 +956,7 @@ void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rg
             acc += (uint32_t)((zw.n[a] + kZeroFloats - 1) / kZeroFloats);
         }
         zw.total = acc;
+        zw.clear_ctas = (uint32_t)n_sms;
     }
     if (px == 2 && py == 2) launch_bb<2, 2>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);
     else if (px == 2) launch_bb<2, 1>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);

@@ -38,6 +38,7 @@ struct ZeroWork { // gradient arrays to clear and the first clearing item of eac
     int64_t n[kZeroArrays];
     uint32_t first[kZeroArrays];
     uint32_t total;
+    uint32_t clear_ctas; // CTAs that clear before they take tiles (one per SM)
 };
 void launch_clear_record_grads(const Ws &w, int64_t n_records, int n_sms, cudaStream_t s);
 // clear: in overwrite mode the gradient arrays (n Gaussians) the blend backward

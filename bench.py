@@ -363,9 +363,9 @@ def rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_pix, N, sm_count, sm_mh
         tb = [traffic.get(x, {}).get("dram_bytes_per_call") for x in kern]
         v["traffic"] = None if any(x is None for x in tb) else float(sum(tb))
     if "blend_backward" in out:
-        # the persistent backward also writes the zero gradients of the
-        # Gaussians no pixel saw (236 bytes each, between tiles)
-        out["blend_backward"]["also_writes_bytes"] = 236 * (N - nvis)
+        # the persistent backward also clears the dense parameter gradients
+        # (236 bytes per Gaussian; the preprocess backward then writes the seen rows)
+        out["blend_backward"]["also_writes_bytes"] = 236 * N
     dom = max(out, key=lambda k: out[k]["ms"])
     roof = dict(out[dom], kernel=dom)
     return roof, out

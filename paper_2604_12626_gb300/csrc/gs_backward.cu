@@ -446,7 +446,7 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
 // buffer (one thread issues them; the load/store pipeline the blend needs for
 // its shared-memory traffic stays free), the unaligned ends by plain stores.
 constexpr int64_t kZeroFloats = 1 << 16;
-constexpr int kZeroBuf = 1024; // bytes of zeros in shared memory (small: the CTAs per SM stay 18)
+constexpr int kZeroBuf = 1024; // bytes of zeros in shared memory (small: it costs no resident CTA)
 
 __device__ __forceinline__ void bulk_zero(char *dst, uint32_t bytes, uint32_t zbuf_saddr, uint64_t policy)
 {
@@ -478,10 +478,8 @@ __device__ __noinline__ void zero_item(const ZeroWork &zw, uint32_t z, uint32_t 
     }
 }
 
-// at most 112 registers for one or two pixels per thread: 18 one-warp CTAs
-// per SM
 template <int PX, int PY>
-__global__ void __maxnreg__(PX * PY == 4 ? 168 : 112) blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, const float *__restrict__ d_rgb,
+__global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, const float *__restrict__ d_rgb,
                                       const float *__restrict__ d_depth, ZeroWork zw)
 {
     extern __shared__ float4 smem_b[];
@@ -647,7 +645,7 @@ __device__ __forceinline__ void gaussian_backward(const gs_camera *__restrict__ 
         q = __ldcg(reinterpret_cast<const float4 *>(gin.quats) + g);
         sigma_from_sq(ls, q, S);
     }
-    const float op = 1.0f / (1.0f + expf(-__ldcg(gin.ologits + g)));
+    float op = 0.f; // from the record rows (the forward wrote it there)
     float gS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float gm0 = 0.f, gm1 = 0.f, gm2 = 0.f, go = 0.f;
     bool first_sh = true;
@@ -658,8 +656,9 @@ __device__ __forceinline__ void gaussian_backward(const gs_camera *__restrict__ 
         const uint32_t rec = (uint32_t)(tb->view_rec_off[v] + local);
         if (!((__ldcg(w.vis + (rec >> 5)) >> (rec & 31)) & 1u)) continue;
         const float4 *gr4 = reinterpret_cast<const float4 *>(w.d_rec + (size_t)rec * kGradStride);
-        const float4 r0 = __ldcg(gr4), r1 = __ldcg(gr4 + 1), r2 = __ldcg(gr4 + 2);
-        const uint32_t clamped = __float_as_uint(__ldcg(gr4 + 3).x); // colour channels clamped at 0
+        const float4 r0 = __ldcg(gr4), r1 = __ldcg(gr4 + 1), r2 = __ldcg(gr4 + 2), r3 = __ldcg(gr4 + 3);
+        const uint32_t clamped = __float_as_uint(r3.x); // colour channels clamped at 0
+        op = r2.z;
         // a channel clamped at 0 passes no gradient
         const float gch[3] = {(clamped & 1u) ? 0.f : r1.z, (clamped & 2u) ? 0.f : r1.w, (clamped & 4u) ? 0.f : r2.x};
         // (uc, vc, A, B, C, opacity, r, g, b, z)
@@ -866,7 +865,7 @@ __global__ void __launch_bounds__(256, 2) preprocess_backward_kernel(const gs_ca
 // ---------------------------------------------------------------------------
 // Record gradient rows: the forward leaves the rows of visible records at zero;
 // a second backward of the same forward finds them filled by the first and
-// clears them here (the gradient part only: the clamp bits stay).
+// clears them here (the gradient part only: opacity and clamp bits stay).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) clear_record_grads_kernel(Ws w, int64_t n_words)
 {
@@ -876,7 +875,8 @@ __global__ void __launch_bounds__(256) clear_record_grads_kernel(Ws w, int64_t n
         const uint32_t bits = w.vis[i >> 5];
         if (!((bits >> (i & 31)) & 1u)) continue;
         float4 *row = reinterpret_cast<float4 *>(w.d_rec + (size_t)i * kGradStride);
-        row[0] = row[1] = row[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        row[0] = row[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float2 *>(row + 2) = make_float2(0.f, 0.f); // the opacity stays
     }
 }
 

@@ -146,11 +146,13 @@ __device__ __forceinline__ void finish_entry(const QEntry &en, bool active, uint
         dst[1] = make_float4(en.A, en.B, en.C, op);
         dst[2] = make_float4(col.x, col.y, col.z, __uint_as_float(pack_rect(bx0, by0, bx1 - bx0 + 1, by1 - by0 + 1)));
         // the record's gradient row starts at zero for the backward, which
-        // accumulates into it and zeroes it again once consumed; beside it,
-        // which colour channels were clamped at 0 (they pass no gradient)
+        // accumulates into its first 10 floats; beside them the opacity (the
+        // backward would otherwise gather the logit) and which colour channels
+        // were clamped at 0 (they pass no gradient)
         float4 *dr = reinterpret_cast<float4 *>(w.d_rec + (size_t)en.rec * kGradStride);
         const uint32_t clamped = (col.x > 0.f ? 0u : 1u) | (col.y > 0.f ? 0u : 2u) | (col.z > 0.f ? 0u : 4u);
-        dr[0] = dr[1] = dr[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        dr[0] = dr[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        dr[2] = make_float4(0.f, 0.f, op, 0.f);
         dr[3] = make_float4(__uint_as_float(clamped), 0.f, 0.f, 0.f);
         uint32_t *hk = c.hist ? hist + en.k * tpv : w.bin_fcount + (size_t)en.v * tpv;
         for (int by = by0; by <= by1; ++by)

@@ -38,7 +38,9 @@ constexpr uint32_t kKeyRecord = 0x7fffffffu;
 constexpr float kTStop = 1e-4f;
 constexpr float kDilation = 0.3f;
 constexpr int kSortChunk = 4096; // keys one CTA sorts; larger bins are merged
-constexpr int kGradStride = 16;   // floats per record row of d_rec: 12 gradient + colour-clamp mask + 3 unused
+// floats per record row of d_rec: dL/d(u, v, A, B, C, opacity, r, g, b, z), the
+// opacity, 0, the colour-clamp mask, 0, 0, 0
+constexpr int kGradStride = 16;
 constexpr int kAccStride = 12;    // floats per record in the backward's shared-memory accumulator
 constexpr int kMaxJoints = 64;    // joints of one avatar tree
 

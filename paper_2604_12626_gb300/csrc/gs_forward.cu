@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
         mx = __ldg(gin.means + 3 * g);
         my = __ldg(gin.means + 3 * g + 1);
         mz = __ldg(gin.means + 3 * g + 2);
-        if (!(env_cov && g >= cov_begin)) {
+        if (!((env_cov || FUSED) && g >= cov_begin)) { // posed rows take their covariance elsewhere
             cls = make_float3(__ldg(gin.log_scales + 3 * g), __ldg(gin.log_scales + 3 * g + 1),
                               __ldg(gin.log_scales + 3 * g + 2));
             cq = __ldg(reinterpret_cast<const float4 *>(gin.quats) + g);
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
             nx = __ldg(gin.means + 3 * gn);
             ny = __ldg(gin.means + 3 * gn + 1);
             nz = __ldg(gin.means + 3 * gn + 2);
-            if (!(env_cov && gn >= cov_begin)) {
+            if (!((env_cov || FUSED) && gn >= cov_begin)) {
                 nls = make_float3(__ldg(gin.log_scales + 3 * gn), __ldg(gin.log_scales + 3 * gn + 1),
                                   __ldg(gin.log_scales + 3 * gn + 2));
                 nq = __ldg(reinterpret_cast<const float4 *>(gin.quats) + gn);

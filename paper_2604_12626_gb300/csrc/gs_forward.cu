@@ -154,9 +154,20 @@ __device__ __forceinline__ void finish_entry(const QEntry &en, bool active, uint
         dr[0] = dr[1] = make_float4(0.f, 0.f, 0.f, 0.f);
         dr[2] = make_float4(0.f, 0.f, op, 0.f);
         dr[3] = make_float4(__uint_as_float(clamped), 0.f, 0.f, 0.f);
-        uint32_t *hk = c.hist ? hist + en.k * tpv : w.bin_fcount + (size_t)en.v * tpv;
-        for (int by = by0; by <= by1; ++by)
-            for (int bx = bx0; bx <= bx1; ++bx) atomicAdd(hk + by * tx_n + bx, 1u);
+        if (c.hist) {
+            // the chunk's counts as a 2D difference array: +1 / -1 at the corners
+            // of the tile rectangle (wrapping arithmetic), summed up once per CTA
+            uint32_t *hk = hist + en.k * tpv;
+            const bool xe = bx1 + 1 < tx_n, ye = by1 + 1 < tb->tiles_y;
+            atomicAdd(hk + by0 * tx_n + bx0, 1u);
+            if (xe) atomicAdd(hk + by0 * tx_n + bx1 + 1, 0xffffffffu);
+            if (ye) atomicAdd(hk + (by1 + 1) * tx_n + bx0, 0xffffffffu);
+            if (xe && ye) atomicAdd(hk + (by1 + 1) * tx_n + bx1 + 1, 1u);
+        } else {
+            uint32_t *hk = w.bin_fcount + (size_t)en.v * tpv;
+            for (int by = by0; by <= by1; ++by)
+                for (int bx = bx0; bx <= bx1; ++bx) atomicAdd(hk + by * tx_n + bx, 1u);
+        }
     }
     // visibility bit, aggregated over the lanes that share a word
     const uint32_t word = active ? (en.rec >> 5) : 0xffffffffu;
@@ -325,6 +336,33 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
     }
     __syncthreads();
     if (c.hist) {
+        // 2D inclusive prefix sums of the difference array: rows (one warp per
+        // row, shuffle scan in 32-tile pieces), then columns (one thread each)
+        const int tx_n = tb->tiles_x, ty_n = tb->tiles_y;
+        for (int r = warp; r < c.nv * ty_n; r += nwarps) {
+            uint32_t *row = hist + (r / ty_n) * tpv + (r % ty_n) * tx_n;
+            uint32_t carry = 0;
+            for (int x0 = 0; x0 < tx_n; x0 += 32) {
+                uint32_t v = x0 + lane < tx_n ? row[x0 + lane] : 0u;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += u;
+                }
+                if (x0 + lane < tx_n) row[x0 + lane] = v + carry;
+                carry += __shfl_sync(0xffffffffu, v, 31);
+            }
+        }
+        __syncthreads();
+        for (int col = threadIdx.x; col < c.nv * tx_n; col += blockDim.x) {
+            uint32_t *cp = hist + (col / tx_n) * tpv + (col % tx_n);
+            uint32_t acc = 0;
+            for (int y = 0; y < ty_n; ++y) {
+                acc += cp[y * tx_n];
+                cp[y * tx_n] = acc;
+            }
+        }
+        __syncthreads();
         // the returned old count is this chunk's offset inside the bin
         uint32_t *rel = w.rel + (size_t)blockIdx.x * kHistCap;
         for (int i = threadIdx.x; i < c.nv * tpv; i += blockDim.x) {

@@ -178,8 +178,11 @@ def test_autograd_function_l1_loss(gs):
     r2 = gs.Renderer(gs.Batch(np.array([0, 2000])), W, H)
     r2.forward(G, ct)
     ref = r2.backward(G, ct, d_rgb, d_depth)
+    # two backward runs: the record gradients are summed with float atomics in
+    # whatever order the tiles finish, so they agree to rounding relative to the
+    # largest gradient of the group, not element by element
     for k in params:
-        torch.testing.assert_close(params[k].grad, ref[k], rtol=1e-5, atol=1e-9)
+        torch.testing.assert_close(params[k].grad, ref[k], rtol=1e-5, atol=1e-6 * float(ref[k].abs().max()))
 
 
 def _avatar_scene(seed, n_scene=100, n_av=100, n_avatars=2):

@@ -9,9 +9,11 @@
 //
 //   sort_chunks_kernel  one CTA sorts up to 4096 keys: a bin of <= 4096 pairs,
 //                       or one 4096-long chunk of a larger bin.  LSD radix sort
-//                       over the 32 depth bits (4 passes of 8 bits) in shared
-//                       memory, ranks from warp match masks; keys sharing a
-//                       depth are ordered by record index on the way out.
+//                       in shared memory over the depth bits minus the chunk's
+//                       smallest (3 passes of 9 bits when they span less than
+//                       2^27, else 4 passes of 8 bits over the depth bits),
+//                       ranks from warp match masks; keys sharing a depth are
+//                       ordered by record index on the way out.
 //   merge_pass_kernel   bins of more than 4096 pairs: pass p merges sorted runs
 //                       of 4096 << p; each CTA writes 4096 outputs, located by
 //                       a merge-path search.  Chunk sorts write to keys or to
@@ -23,13 +25,13 @@ namespace gs {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kRadix = 256;
+constexpr int kRadixMax = 512; // digits of up to 9 bits
 
 struct SortSmem {
     unsigned long long keys[kSortChunk];
-    uint32_t cnt[kSortWarps][kRadix];
+    uint32_t cnt[kSortWarps][kRadixMax];
     uint32_t wsum[kSortWarps];
-    uint32_t item;
+    uint32_t item, dmin, dmax;
 };
 
 __device__ __forceinline__ int ceil_log2(uint32_t x)
@@ -43,23 +45,37 @@ __device__ __forceinline__ unsigned long long *sort_buf(const Ws &w, int passes,
     return ((passes - p) & 1) ? w.scratch : w.keys;
 }
 
-// One stable LSD pass over the 8 key bits at `shift`.  Layout: warp w holds
-// positions [w 32K, (w+1) 32K), position w 32K + r 32 + lane in register k[r],
-// so ranking in (warp, round, lane) order is position order.  On return k[]
-// and sm.keys hold the keys in the new order.
-template <int K>
-__device__ __forceinline__ void radix_pass(unsigned long long (&k)[K], int shift, SortSmem &sm)
+// Digit of a key for one LSD pass.  BITS == 8: bits [shift, shift + 8) of the
+// 64-bit key.  BITS == 9: bits [shift, shift + 9) of the depth bits minus the
+// chunk's smallest (`sub`), capped at kDepthCap so that padding keys sort last.
+constexpr uint32_t kDepthCap = (1u << 27) - 1u;
+
+template <int BITS>
+__device__ __forceinline__ uint32_t key_digit(unsigned long long key, int shift, uint32_t sub)
 {
+    if (BITS == 8) return (uint32_t)(key >> shift) & 0xffu;
+    return (min((uint32_t)(key >> 32) - sub, kDepthCap) >> shift) & ((1u << BITS) - 1u);
+}
+
+// One stable LSD pass over one digit.  Layout: warp w holds positions
+// [w 32K, (w+1) 32K), position w 32K + r 32 + lane in register k[r], so
+// ranking in (warp, round, lane) order is position order.  On return k[] and
+// sm.keys hold the keys in the new order.
+template <int K, int BITS>
+__device__ __forceinline__ void radix_pass(unsigned long long (&k)[K], int shift, uint32_t sub, SortSmem &sm)
+{
+    constexpr int R = 1 << BITS, DPT = R / kSortThreads; // digits per thread in the scan
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&sm.cnt[0][0])[i] = 0u;
+#pragma unroll
+    for (int i = threadIdx.x; i < kSortWarps * R; i += kSortThreads) sm.cnt[i / R][i % R] = 0u;
     __syncthreads();
     uint32_t loff[(K + 1) / 2]; // ranks < 4096, two per register
 #pragma unroll
     for (int r = 0; r < (K + 1) / 2; ++r) loff[r] = 0u;
 #pragma unroll
     for (int r = 0; r < K; ++r) {
-        const uint32_t d = (uint32_t)(k[r] >> shift) & 0xffu;
+        const uint32_t d = key_digit<BITS>(k[r], shift, sub);
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const int leader = __ffs(peers) - 1;
         uint32_t base = 0;
@@ -72,15 +88,14 @@ __device__ __forceinline__ void radix_pass(unsigned long long (&k)[K], int shift
     }
     __syncthreads();
     {
-        // exclusive offsets, digit-major then warp: thread t owns digit t
-        const int d = threadIdx.x;
-        uint32_t c[kSortWarps], tot = 0;
+        // exclusive offsets, digit-major then warp: thread t owns digits
+        // t DPT .. t DPT + DPT - 1
+        uint32_t all = 0;
 #pragma unroll
-        for (int q = 0; q < kSortWarps; ++q) {
-            c[q] = sm.cnt[q][d];
-            tot += c[q];
-        }
-        uint32_t incl = tot;
+        for (int j = 0; j < DPT; ++j)
+#pragma unroll
+            for (int q = 0; q < kSortWarps; ++q) all += sm.cnt[q][threadIdx.x * DPT + j];
+        uint32_t incl = all;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
@@ -88,18 +103,22 @@ __device__ __forceinline__ void radix_pass(unsigned long long (&k)[K], int shift
         }
         if (lane == 31) sm.wsum[warp] = incl;
         __syncthreads();
-        uint32_t run = incl - tot;
+        uint32_t run = incl - all;
         for (int q = 0; q < warp; ++q) run += sm.wsum[q];
 #pragma unroll
-        for (int q = 0; q < kSortWarps; ++q) {
-            sm.cnt[q][d] = run;
-            run += c[q];
+        for (int j = 0; j < DPT; ++j) {
+#pragma unroll
+            for (int q = 0; q < kSortWarps; ++q) {
+                const uint32_t cq = sm.cnt[q][threadIdx.x * DPT + j];
+                sm.cnt[q][threadIdx.x * DPT + j] = run;
+                run += cq;
+            }
         }
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < K; ++r) {
-        const uint32_t d = (uint32_t)(k[r] >> shift) & 0xffu;
+        const uint32_t d = key_digit<BITS>(k[r], shift, sub);
         sm.keys[sm.cnt[warp][d] + ((loff[r >> 1] >> (16 * (r & 1))) & 0xffffu)] = k[r];
     }
     __syncthreads();
@@ -128,8 +147,8 @@ __device__ __forceinline__ bool depth_run(const SortSmem &sm, uint32_t pos, uint
     return true;
 }
 
-// Sorts src[0..n) (n <= 256 K) into dst[0..n) (dst may equal src): four passes
-// over the depth bits; keys sharing a depth are then ordered by record index
+// Sorts src[0..n) (n <= 256 K) into dst[0..n) (dst may equal src): three or four
+// passes over the depth bits; keys sharing a depth are then ordered by record index
 // while they are written out, or -- if some run of equal depths is longer than
 // kMaxRun -- the whole 64-bit key is sorted again with eight passes.
 template <int K>
@@ -142,8 +161,40 @@ __device__ void radix_sort_chunk(const unsigned long long *src, unsigned long lo
         const uint32_t pos = (uint32_t)(warp * 32 * K + r * 32 + lane);
         k[r] = pos < n ? src[pos] : ~0ull; // padding sorts last (no real depth has all bits set)
     }
+    // the depths of a chunk usually span less than 2^27 - 1 as FP32 bit patterns
+    // (0.2 m .. 100 m does): then three 9-bit passes over (depth - smallest)
+    // order them, otherwise four 8-bit passes over the depth bits
+    if (threadIdx.x == 0) {
+        sm.dmin = 0xffffffffu;
+        sm.dmax = 0u;
+    }
+    __syncthreads();
+    {
+        uint32_t lo = 0xffffffffu, hi = 0u;
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            const uint32_t pos = (uint32_t)(warp * 32 * K + r * 32 + lane);
+            if (pos < n) {
+                lo = min(lo, (uint32_t)(k[r] >> 32));
+                hi = max(hi, (uint32_t)(k[r] >> 32));
+            }
+        }
+        lo = __reduce_min_sync(0xffffffffu, lo);
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        if (lane == 0) {
+            atomicMin(&sm.dmin, lo);
+            atomicMax(&sm.dmax, hi);
+        }
+    }
+    __syncthreads();
+    const uint32_t dmin = sm.dmin, dmax = sm.dmax;
+    if (dmax - dmin < kDepthCap) {
 #pragma unroll 1
-    for (int pass = 0; pass < 4; ++pass) radix_pass<K>(k, 32 + 8 * pass, sm);
+        for (int pass = 0; pass < 3; ++pass) radix_pass<K, 9>(k, 9 * pass, dmin, sm);
+    } else {
+#pragma unroll 1
+        for (int pass = 0; pass < 4; ++pass) radix_pass<K, 8>(k, 32 + 8 * pass, 0u, sm);
+    }
     bool long_run = false;
 #pragma unroll
     for (int r = 0; r < K; ++r) {
@@ -156,7 +207,7 @@ __device__ void radix_sort_chunk(const unsigned long long *src, unsigned long lo
     }
     if (__syncthreads_or(long_run)) {
 #pragma unroll 1
-        for (int pass = 0; pass < 8; ++pass) radix_pass<K>(k, 8 * pass, sm);
+        for (int pass = 0; pass < 8; ++pass) radix_pass<K, 8>(k, 8 * pass, 0u, sm);
 #pragma unroll
         for (int r = 0; r < K; ++r) {
             const uint32_t pos = (uint32_t)(warp * 32 * K + r * 32 + lane);

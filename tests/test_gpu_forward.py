@@ -277,6 +277,26 @@ def test_large_bins_keys_bit_exact(gs):
     _check_keys(r, cam[None], W, H, np.zeros(g["means"].shape[0], np.int64))
 
 
+@pytest.mark.parametrize("n", [3000, 9000])
+def test_wide_depth_range_keys_bit_exact(gs, n):
+    """Depths from 0.3 m to 100 km inside the same tiles: their FP32 bit patterns
+    span more than 2^27, so the bin sort takes its four 8-bit passes over the
+    depth bits instead of three 9-bit passes over the offset depths."""
+    rng = np.random.default_rng(n)
+    z = np.exp(rng.uniform(np.log(0.3), np.log(1e5), n))
+    xy = rng.uniform(-0.02, 0.02, (n, 2)) * z[:, None]  # within a few pixels of the axis
+    g = synth.box_scene(n, seed=n)
+    g["means"] = np.stack([xy[:, 0], xy[:, 1], z], 1).astype(np.float32)
+    g["log_scales"] = np.log(0.01 * z)[:, None].repeat(3, 1).astype(np.float32)  # about a pixel at any depth
+    W = H = 64
+    cam = synth.identity_camera(W, H)
+    r, out, _, _ = render_gpu(gs, g, cam[None], W, H, tile=(8, 8), batch_depth=64)
+    zk = np.sort(g["means"][:, 2])
+    assert zk.view(np.uint32)[-1] - zk.view(np.uint32)[0] > (1 << 27)
+    assert r.stats()["max_bin"] > 2048
+    _check_keys(r, cam[None], W, H, np.zeros(n, np.int64))
+
+
 @pytest.mark.parametrize("n", [3000, 20_000])
 def test_equal_depths_sorted_by_record_index(gs, oracle, n):
     """Every Gaussian at exactly the same FP32 depth: the order inside a bin is

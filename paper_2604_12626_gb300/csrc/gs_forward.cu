@@ -711,13 +711,14 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
     const int nthr = blockDim.x;
     const uint32_t R = (uint32_t)tb->n_records;
     const int nb = (int)((n + B - 1) / B);
-    // bits of the current 32-entry window whose Gaussian some pixel of this
-    // thread blended; OR-ed over the warp and flagged in the key (bit 31 of
-    // the record word) so that the backward walks the blended pairs only
+    // one bit per entry of the current 32-entry window, set where some pixel of
+    // this thread blended its Gaussian (appended from the right: the window's
+    // first entry ends highest); OR-ed over the warp and flagged in the key (bit
+    // 31 of the record word) so that the backward walks the blended pairs only
     uint32_t mk = 0;
     const int lane = threadIdx.x & 31;
-    auto flag_window = [&](uint32_t base) {
-        const uint32_t wm = __reduce_or_sync(0xffffffffu, mk);
+    auto flag_window = [&](uint32_t base, int n_app) { // n_app in 1..32 entries appended
+        const uint32_t wm = __brev(__reduce_or_sync(0xffffffffu, mk << (32 - n_app)));
         mk = 0;
         if ((wm >> lane) & 1u) atomicOr(reinterpret_cast<unsigned int *>(keys + base + lane), kKeyBlended);
     };
@@ -792,9 +793,10 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
         // the front-to-back updates in order.
         for (int k0 = 0; k0 < cnt; k0 += kUnroll) {
             if (__all_sync(0xffffffffu, tdone)) {
-                if (k0 & 31) flag_window((uint32_t)b * B + (uint32_t)(k0 & ~31));
+                if (k0 & 31) flag_window((uint32_t)b * B + (uint32_t)(k0 & ~31), k0 & 31);
                 break;
             }
+            uint32_t m4 = 0; // this thread's blended bits of the four entries
             if (!tdone) {
                 float al[kUnroll][NP];
                 bool ok[kUnroll][NP], cv[kUnroll][NP];
@@ -834,6 +836,7 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
                 for (int u = 0; u < kUnroll; ++u) {
                     const float4 c = s2[k0 + u];
                     const float z = s0[k0 + u].z;
+                    bool blu = false;
                     if constexpr (PX == 2) {
                         // the two pixels of a row updated as packed pairs, branch-free: a
                         // pixel that does not blend this Gaussian gets weight 0 (C + c 0 = C,
@@ -851,7 +854,7 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
                             const float2 Tn = __fmul2_rn(T2, om);
                             const bool s0b = k0k && Tn.x < kTStop, s1b = k1k && Tn.y < kTStop;
                             const bool bl0 = k0k && !s0b, bl1 = k1k && !s1b;
-                            mk |= (uint32_t)(bl0 || bl1) << ((k0 + u) & 31);
+                            blu = blu || bl0 || bl1;
                             dn[p0] = dn[p0] || s0b;
                             dn[p1] = dn[p1] || s1b;
                             const float2 wgt =
@@ -871,6 +874,7 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
                             last[p0] = bl0 ? pos : last[p0];
                             last[p1] = bl1 ? pos : last[p1];
                         }
+                        m4 = (m4 << 1) | (uint32_t)blu;
                         continue;
                     }
 #pragma unroll
@@ -892,18 +896,20 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
                                     T[p] = Tn;
                                     ncon[p] = ncov[p];
                                     last[p] = (uint32_t)b * B + k0 + u + 1;
-                                    mk |= 1u << ((k0 + u) & 31);
+                                    blu = true;
                                 }
                             }
                         }
                     }
+                    m4 = (m4 << 1) | (uint32_t)blu;
                 }
                 tdone = true;
 #pragma unroll
                 for (int p = 0; p < NP; ++p) tdone = tdone && dn[p];
             }
+            mk = (mk << kUnroll) | m4;
             if (((k0 + kUnroll) & 31) == 0 || k0 + kUnroll >= cnt)
-                flag_window((uint32_t)b * B + (uint32_t)(k0 & ~31));
+                flag_window((uint32_t)b * B + (uint32_t)(k0 & ~31), (k0 & 31) + kUnroll);
             __syncwarp();
         }
         __syncthreads();

@@ -449,7 +449,7 @@ def avatar_and_composite_rows(api, synth, torch, dev, stream, outs, hbm_peak):
 
     return {"lbs_deform": dict(hbm(fwd_bytes, deform_ms), avatars=n_av, gaussians=m),
             "lbs_deform_backward": dict(hbm(bwd_bytes, deform_bwd_ms), avatars=n_av, gaussians=m,
-                                        note="joint-gradient atomics per Gaussian and joint"),
+                                        note="joint gradients summed per warp by joint-owner lanes, one atomic per (CTA, joint, entry)"),
             "keyframe_interpolation": {"ms": interp_ms, "avatars": n_av, "frames": n_frames},
             "forward_kinematics": {"ms": fk_ms, "avatars": n_av, "joints": synth.N_JOINTS},
             "composite": dict(hbm(comp_bytes, comp_ms), views=V, width=W, height=H),

@@ -7,8 +7,10 @@
 //                  cov' = A3 Sigma A3^T with Sigma = R(q) diag(exp(2 s)) R(q)^T;
 //                  the joint matrices of the CTA's avatar are staged in shared
 //                  memory.  100 bytes of HBM traffic per Gaussian.
-// deform_backward  the adjoint; per-joint gradients are reduced in shared memory
-//                  per CTA (for the CTA's first avatar) before global atomics.
+// deform_backward  the adjoint; the joint gradients of the CTA's avatar are summed
+//                  per warp by joint owners (lane l adds w dL/dA of the warp's
+//                  32 Gaussians wherever joint l appears), then over the warps
+//                  in shared memory, then one global atomic per (joint, entry).
 #include "gs_internal.cuh"
 #include "gs_launch.h"
 
@@ -54,19 +56,32 @@ __global__ void __launch_bounds__(256) deform_kernel(AvIn in, const float *__res
 
 constexpr int kDeformWarps = 8; // 256 threads
 
+// One Gaussian's share of the joint gradients, staged for its warp: dL/dA
+// (3x4) and the four (joint, weight) pairs.  80 bytes (16-byte loads).
+struct JointShare {
+    float4 gA[3];
+    float4 w;
+    ushort4 ids;
+    uint32_t pad[2];
+};
+
 __global__ void __launch_bounds__(256) deform_backward_kernel(AvIn in, const float *__restrict__ G,
                                                               const float *__restrict__ d_means,
                                                               const float *__restrict__ d_cov, float *d_cm,
                                                               float *d_cls, float *d_cq, float *d_G)
 {
     __shared__ float sG[kMaxJoints * 12];
-    __shared__ float sdG[kDeformWarps][kMaxJoints * 12]; // one copy per warp: no atomics across warps
+    __shared__ float sdG[kDeformWarps][kMaxJoints * 12]; // per-warp joint-gradient sums
+    __shared__ JointShare sj[kDeformWarps][32];
     const int64_t base = (int64_t)blockIdx.x * blockDim.x;
     const int64_t i = base + threadIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a0 = clamp_avatar(in.avatar_of[base], in.n_avatars);
     const int nj12 = in.n_joints * 12;
     for (int k = threadIdx.x; k < nj12; k += blockDim.x) sG[k] = G[(size_t)a0 * nj12 + k];
-    for (int k = threadIdx.x; k < kDeformWarps * kMaxJoints * 12; k += blockDim.x) (&sdG[0][0])[k] = 0.0f;
+    JointShare mine;
+    mine.gA[0] = mine.gA[1] = mine.gA[2] = mine.w = make_float4(0.f, 0.f, 0.f, 0.f); // no share
+    mine.ids = make_ushort4(0, 0, 0, 0);
     __syncthreads();
     if (i < in.m) {
         const int av = clamp_avatar(in.avatar_of[i], in.n_avatars);
@@ -141,14 +156,46 @@ __global__ void __launch_bounds__(256) deform_backward_kernel(AvIn in, const flo
         d_cq[4 * i + 1] += (gx - qx * dq) * iq;
         d_cq[4 * i + 2] += (gy - qy * dq) * iq;
         d_cq[4 * i + 3] += (gz - qz * dq) * iq;
-        // dL/dG[j_k] += w_k dL/dA
-        const int ids[4] = {id.x, id.y, id.z, id.w};
-        const float ws[4] = {wt.x, wt.y, wt.z, wt.w};
-        float *dst = av == a0 ? sdG[threadIdx.x >> 5] : d_G + (size_t)av * nj12;
+        // dL/dG[j_k] += w_k dL/dA: the CTA's avatar through the warp's owner
+        // sums below, another avatar (a CTA that straddles two) directly
+        if (av == a0) {
+            mine.gA[0] = make_float4(gA[0], gA[1], gA[2], gA[3]);
+            mine.gA[1] = make_float4(gA[4], gA[5], gA[6], gA[7]);
+            mine.gA[2] = make_float4(gA[8], gA[9], gA[10], gA[11]);
+            mine.w = wt;
+            mine.ids = id;
+        } else {
+            const int ids[4] = {id.x, id.y, id.z, id.w};
+            const float ws[4] = {wt.x, wt.y, wt.z, wt.w};
+            float *dst = d_G + (size_t)av * nj12;
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+            for (int k = 0; k < 4; ++k)
 #pragma unroll
-            for (int e = 0; e < 12; ++e) atomicAdd(dst + 12 * ids[k] + e, ws[k] * gA[e]);
+                for (int e = 0; e < 12; ++e) atomicAdd(dst + 12 * ids[k] + e, ws[k] * gA[e]);
+        }
+    }
+    // joint-owner sums over the warp's 32 Gaussians: lane l owns joints l and
+    // l + 32 and adds w dL/dA wherever its joint appears (no atomics)
+    sj[warp][lane] = mine;
+    __syncwarp();
+    for (int j = lane; j < in.n_joints; j += 32) {
+        float acc[12];
+#pragma unroll
+        for (int e = 0; e < 12; ++e) acc[e] = 0.f;
+#pragma unroll 4
+        for (int q = 0; q < 32; ++q) {
+            const JointShare &sh = sj[warp][q];
+            const ushort4 id = sh.ids;
+            const float4 w = sh.w;
+            const float wj = (id.x == j ? w.x : 0.f) + (id.y == j ? w.y : 0.f) + (id.z == j ? w.z : 0.f) +
+                             (id.w == j ? w.w : 0.f);
+            const float4 g0 = sh.gA[0], g1 = sh.gA[1], g2 = sh.gA[2];
+            acc[0] += wj * g0.x; acc[1] += wj * g0.y; acc[2] += wj * g0.z; acc[3] += wj * g0.w;
+            acc[4] += wj * g1.x; acc[5] += wj * g1.y; acc[6] += wj * g1.z; acc[7] += wj * g1.w;
+            acc[8] += wj * g2.x; acc[9] += wj * g2.y; acc[10] += wj * g2.z; acc[11] += wj * g2.w;
+        }
+#pragma unroll
+        for (int e = 0; e < 12; ++e) sdG[warp][12 * j + e] = acc[e];
     }
     __syncthreads();
     for (int k = threadIdx.x; k < nj12; k += blockDim.x) {

@@ -32,19 +32,24 @@ __global__ void __launch_bounds__(256) deform_kernel(AvIn in, const float *__res
     __shared__ float sG[kMaxJoints * 12];
     const int64_t base = (int64_t)blockIdx.x * blockDim.x;
     const int64_t i = base + threadIdx.x;
+    // the Gaussian's inputs are loaded first, so that they are in flight while
+    // the CTA stages its avatar's joint matrices
+    const bool valid = i < in.m;
+    const int64_t ic = valid ? i : base;
+    const int av = clamp_avatar(in.avatar_of[ic], in.n_avatars);
+    const ushort4 id = clamp_ids(reinterpret_cast<const ushort4 *>(in.joint_ids)[ic], in.n_joints);
+    const float4 wt = reinterpret_cast<const float4 *>(in.weights)[ic];
+    const float3 m = make_float3(in.means[3 * ic], in.means[3 * ic + 1], in.means[3 * ic + 2]);
+    const float3 ls = make_float3(in.log_scales[3 * ic], in.log_scales[3 * ic + 1], in.log_scales[3 * ic + 2]);
+    const float4 q = reinterpret_cast<const float4 *>(in.quats)[ic];
     const int a0 = clamp_avatar(in.avatar_of[base], in.n_avatars);
     const int nj12 = in.n_joints * 12;
     for (int k = threadIdx.x; k < nj12; k += blockDim.x) sG[k] = G[(size_t)a0 * nj12 + k];
     __syncthreads();
-    if (i >= in.m) return;
-    const int av = clamp_avatar(in.avatar_of[i], in.n_avatars);
+    if (!valid) return;
     const float *Gs = av == a0 ? sG : G + (size_t)av * nj12;
-    const ushort4 id = clamp_ids(reinterpret_cast<const ushort4 *>(in.joint_ids)[i], in.n_joints);
-    const float4 wt = reinterpret_cast<const float4 *>(in.weights)[i];
     float mu[3], cov[6];
-    lbs_gaussian(Gs, id, wt, make_float3(in.means[3 * i], in.means[3 * i + 1], in.means[3 * i + 2]),
-                 make_float3(in.log_scales[3 * i], in.log_scales[3 * i + 1], in.log_scales[3 * i + 2]),
-                 reinterpret_cast<const float4 *>(in.quats)[i], mu, cov);
+    lbs_gaussian(Gs, id, wt, m, ls, q, mu, cov);
     const int64_t d = in.dest ? in.dest[i] : i;
     out_means[3 * d] = mu[0];
     out_means[3 * d + 1] = mu[1];

@@ -6,11 +6,11 @@
 //                       cull, screen vertices, 1/z, signed area and the pixel
 //                       bounding box -> a 96-byte record
 //   mesh_raster_kernel  one CTA per (view, 16x16 tile), one thread per pixel:
-//                       triangle records staged in shared memory 256 at a
-//                       time, those whose box meets the tile compacted in
-//                       index order; inside test on the edge functions,
-//                       perspective-correct depth and colour, nearest depth
-//                       kept (the lower triangle index on a tie)
+//                       the boxes of 256 triangles at a time tested against
+//                       the tile, the records of those that meet it gathered
+//                       into shared memory in index order; inside test on the
+//                       edge functions, perspective-correct depth and colour,
+//                       nearest depth kept (the lower triangle index on a tie)
 #include <cmath>
 
 #include "gs_internal.cuh"
@@ -82,8 +82,7 @@ __global__ void __launch_bounds__(256) mesh_setup_kernel(MeshIn in, const gs_cam
 __global__ void __launch_bounds__(kMeshTile *kMeshTile) mesh_raster_kernel(MeshTable t, const MeshRec *__restrict__ rec,
                                                                           float *rgb, float *depth)
 {
-    __shared__ MeshRec s[kMeshBatch];
-    __shared__ uint16_t hit[kMeshBatch]; // batch slots whose box meets this tile, in index order
+    __shared__ MeshRec s[kMeshBatch]; // records of the batch whose box meets this tile, in index order
     __shared__ int n_hit, warp_n[kMeshTile * kMeshTile / 32];
     const int v = blockIdx.y;
     const int tiles_x = (t.W + kMeshTile - 1) / kMeshTile;
@@ -96,15 +95,15 @@ __global__ void __launch_bounds__(kMeshTile *kMeshTile) mesh_raster_kernel(MeshT
     for (int64_t b0 = lo; b0 < hi; b0 += kMeshBatch) {
         const int cnt = (int)min((int64_t)kMeshBatch, hi - b0);
         __syncthreads();
-        // each thread tests one triangle's box against the tile; the hits are
-        // compacted in index order (warp ballots, then a scan over the warps)
+        // each thread tests one triangle's box (16 of the record's 96 bytes)
+        // against the tile; the hits are compacted in index order (warp
+        // ballots, then a scan over the warps) and only their records gathered
         bool h = false;
         if ((int)threadIdx.x < cnt) {
-            const MeshRec m = rec[b0 + threadIdx.x];
-            const uint32_t bx = __float_as_uint(m.c.z), by = __float_as_uint(m.c.w);
+            const float4 mc = rec[b0 + threadIdx.x].c;
+            const uint32_t bx = __float_as_uint(mc.z), by = __float_as_uint(mc.w);
             const int x0 = (int)(bx & 0xffffu), x1 = (int)(bx >> 16), y0 = (int)(by & 0xffffu), y1 = (int)(by >> 16);
             h = !(x1 < tx0 || x0 > tx0 + kMeshTile - 1 || y1 < ty0 || y0 > ty0 + kMeshTile - 1);
-            s[threadIdx.x] = m;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, h);
         if (lane == 0) warp_n[warp] = __popc(bal);
@@ -119,11 +118,11 @@ __global__ void __launch_bounds__(kMeshTile *kMeshTile) mesh_raster_kernel(MeshT
             n_hit = acc;
         }
         __syncthreads();
-        if (h) hit[warp_n[warp] + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)threadIdx.x;
+        if (h) s[warp_n[warp] + __popc(bal & ((1u << lane) - 1u))] = rec[b0 + threadIdx.x];
         __syncthreads();
         const int nh = n_hit;
         for (int q = 0; q < nh; ++q) {
-            const int k = hit[q];
+            const int k = q;
             const float4 A = s[k].a, B = s[k].b, C = s[k].c;
             const float X[3] = {A.x, A.z, B.x}, Y[3] = {A.y, A.w, B.y};
             float e[3];

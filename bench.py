@@ -320,7 +320,17 @@ def ncu_summary(csv_path, command):
         json.dump(out, f, indent=1)
 
 
-def rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_pix, N, sm_count, sm_mhz):
+def exp2_rate(api, torch, dev, stream, sm_count):
+    """Measured exp2 throughput of the special-function unit (gs_exp2_rate):
+    8 CTAs of 256 threads per SM, 4096 steps of 8 chains each."""
+    out = torch.empty(sm_count * 8 * 256, device=dev)
+    api.exp2_rate(sm_count * 8, 64, out, stream)  # warm-up
+    ops = sm_count * 8 * 256 * 4096 * 8
+    ms = _event_ms(torch, stream, lambda: api.exp2_rate(sm_count * 8, 4096, out, stream), reps=3)
+    return ops / (ms * 1e-3)
+
+
+def rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_pix, N, sm_count, sm_mhz, exp_rate=None):
     """Achieved vs peak per kernel, from live CUDA-event stage times."""
     hbm, peak_kind = peaks()
     mhz = sm_mhz or 2070.0
@@ -362,6 +372,11 @@ def rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_pix, N, sm_count, sm_mh
         kern = [KERNEL_OF_STAGE[x] for x in (("sort_chunks", "merge") if k == "sort" else (k,))]
         tb = [traffic.get(x, {}).get("dram_bytes_per_call") for x in kern]
         v["traffic"] = None if any(x is None for x in tb) else float(sum(tb))
+    for k, n_ev in (("blend", n_eval_fwd), ("blend_backward", n_eval_bwd)):
+        if exp_rate and k in out:
+            # one exp per evaluation, against the measured exp2 rate
+            a = n_ev / (out[k]["ms"] * 1e-3)
+            out[k]["exp2"] = {"achieved_gops": a / 1e9, "peak_gops": exp_rate / 1e9, "frac": a / exp_rate}
     if "blend_backward" in out:
         # the persistent backward also clears the dense parameter gradients
         # (236 bytes per Gaussian; the preprocess backward then writes the seen rows)
@@ -685,8 +700,9 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     n_eval_bwd = int(outs[3].sum().item())  # sum of n_contrib: what the backward walks
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    e_rate = exp2_rate(api, torch, dev, stream, sm_count)
     roof, per_kernel = rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_envs * W * H, N, sm_count,
-                                 (clocks or {}).get("sm_max_mhz"))
+                                 (clocks or {}).get("sm_max_mhz"), exp_rate=e_rate)
 
     # --- the avatar rows (LBS, its adjoint, keyframes + FK) and the composite,
     # timed on their own: 32 envs x 8 avatars x 50k Gaussians, and the
@@ -728,6 +744,8 @@ def run_ours(args, ws, rank, local):
                 "d2h_bytes_per_step": d2h, "what": "public API calls per step: cameras H2D from pinned memory, "
                                                    "gs_render + gs_render_backward, RGB + depth D2H"},
         # + clear_record_grads, blend_backward, preprocess_backward
+        "exp2_rate": {"gops": e_rate / 1e9,
+                      "per_sm_per_clk": e_rate / (sm_count * ((clocks or {}).get("sm_max_mhz") or 2070.0) * 1e6)},
         "gpu_launches": (rend.kernels_per_forward() + 3) * args.steps,
         "clocks": clocks,
         "stage_ms": stage_ms,

@@ -354,6 +354,16 @@ gs_status gs_workspace_sections(const gs_render_config *cfg, const gs_batch *bat
 gs_status gs_profile_enable(int32_t enable);
 gs_status gs_profile_read(float *stage_ms, int32_t *stage_launches);
 
+/* Measurement of the special-function unit's exp2 throughput, the roofline
+ * of the one transcendental per blend evaluation (alpha = o e^power, Sec. 3.2's
+ * 3DGS blending).  Launches n_blocks CTAs of 256 threads; each thread runs
+ * eight independent chains of `iters` steps x <- 2^(-x) (ex2.approx.ftz), so
+ * one launch performs n_blocks * 256 * iters * 8 exp2 operations; time it with
+ * events on `stream`.  out: device float[n_blocks * 256], written (the chains'
+ * sums, so the work is not elided).  GS_ERR_INVALID_ARG for n_blocks < 1,
+ * iters < 1 or a null out.  Asynchronous. */
+gs_status gs_exp2_rate(int32_t n_blocks, int32_t iters, float *out, void *stream);
+
 /* The CUDA error behind the last GS_ERR_CUDA (a cudaError_t value), 0 if none. */
 int32_t gs_last_cuda_error(void);
 

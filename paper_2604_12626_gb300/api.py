@@ -103,13 +103,15 @@ _lib.gs_profile_read.argtypes = [_P, _P]
 for _f in ("gs_render_static", "gs_profile_enable", "gs_profile_read", "gs_workspace_sections", "gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_deform_avatars",
            "gs_deform_avatars_backward", "gs_get_status", "gs_render_stats", "gs_autotune"):
     getattr(_lib, _f).restype = ctypes.c_int32
+_lib.gs_exp2_rate.argtypes = [ctypes.c_int32, ctypes.c_int32, _P, _P]
+_lib.gs_exp2_rate.restype = ctypes.c_int32
 _lib.gs_last_cuda_error.restype = ctypes.c_int32
 _lib.gs_version.restype = ctypes.c_int32
 
 EXPORTS = ("gs_render_static", "gs_profile_enable", "gs_profile_read", "gs_workspace_sections", "gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_deform_avatars",
            "gs_deform_avatars_backward", "gs_get_status", "gs_render_stats", "gs_autotune", "gs_last_cuda_error",
            "gs_version", "gs_composite_nearest", "gs_forward_kinematics", "gs_interpolate_joints",
-           "gs_render_avatars", "gs_mesh_workspace_size", "gs_render_mesh")
+           "gs_render_avatars", "gs_mesh_workspace_size", "gs_render_mesh", "gs_exp2_rate")
 
 
 class GsError(RuntimeError):
@@ -478,6 +480,15 @@ def render_mesh(mesh: Mesh, batch: Batch, cams: torch.Tensor, width: int, height
                                _ptr(workspace), workspace.numel(), _ptr(out[0]), _ptr(out[1]), _stream(stream)),
            "gs_render_mesh")
     return out
+
+
+def exp2_rate(n_blocks: int, iters: int, out: torch.Tensor, stream=None) -> int:
+    """gs_exp2_rate: launches the exp2 throughput kernel (out: float32 CUDA
+    tensor of n_blocks * 256); returns the exp2 operations it performs."""
+    if out.dtype != torch.float32 or not out.is_cuda or out.numel() < n_blocks * 256:
+        raise GsError("exp2_rate: float32 CUDA tensor of n_blocks * 256 expected")
+    _check(_lib.gs_exp2_rate(n_blocks, iters, _ptr(out), _stream(stream)), "gs_exp2_rate")
+    return n_blocks * 256 * iters * 8
 
 
 def composite_nearest(rgb_a, depth_a, rgb_b, depth_b, out=None, stream=None):

@@ -613,6 +613,13 @@ gs_status gs_deform_avatars_backward(const gs_avatars *av, const float *joint_G,
     return check_launch();
 }
 
+gs_status gs_exp2_rate(int32_t n_blocks, int32_t iters, float *out, void *stream)
+{
+    if (n_blocks < 1 || iters < 1 || !out) return GS_ERR_INVALID_ARG;
+    launch_exp2_rate(n_blocks, iters, out, static_cast<cudaStream_t>(stream));
+    return check_launch();
+}
+
 gs_status gs_get_status(void *workspace, size_t workspace_bytes, void *stream, int32_t *device_status)
 {
     if (!workspace || !device_status || workspace_bytes < sizeof(Header)) return GS_ERR_INVALID_ARG;

@@ -8,6 +8,8 @@
 //                     level by level down the tree
 //   interp_kernel     joint matrices at a fractional frame position, linear
 //                     between the two neighbouring frames (Sec. 3.3.1)
+//   exp2_rate_kernel  throughput of the special-function unit's exp2, the one
+//                     transcendental of every blend evaluation (for its roofline)
 #include <cmath>
 
 #include "gs_internal.cuh"
@@ -168,6 +170,31 @@ void launch_interp(const float *frames, const float *t, int n_avatars, int n_fra
     if (grid > (int64_t)n_sms * 8) grid = (int64_t)n_sms * 8;
     if (grid < 1) return;
     interp_kernel<<<(unsigned)grid, 256, 0, s>>>(frames, t, n_avatars, n_frames, per_frame, out);
+}
+
+// ---------------------------------------------------------------------------
+// exp2 throughput (a measurement, not part of the renderer)
+// ---------------------------------------------------------------------------
+// Eight independent chains per thread, x <- 2^(-x), which stays in (0.5, 1]:
+// one ex2.approx per step and chain, nothing else on the dependent path.
+__global__ void __launch_bounds__(256) exp2_rate_kernel(int iters, float *out)
+{
+    float x[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = 0.5f + 0.01f * (float)((threadIdx.x + c) & 15);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) asm volatile("ex2.approx.ftz.f32 %0, %1;\n" : "=f"(x[c]) : "f"(-x[c]));
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc += x[c];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+void launch_exp2_rate(int n_blocks, int iters, float *out, cudaStream_t s)
+{
+    exp2_rate_kernel<<<n_blocks, 256, 0, s>>>(iters, out);
 }
 
 } // namespace gs

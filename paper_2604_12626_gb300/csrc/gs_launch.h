@@ -16,6 +16,7 @@ void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w
 void launch_scan(const Ws &w, cudaStream_t s);
 void launch_scatter(const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s);
 cudaError_t configure_sort_kernels();
+void launch_exp2_rate(int n_blocks, int iters, float *out, cudaStream_t s);
 int merge_passes_for_capacity(int64_t pair_capacity);
 void launch_sort_chunks(const Ws &w, int n_sms, cudaStream_t s);
 void launch_merge_passes(const Ws &w, int n_passes, int n_sms, cudaStream_t s);

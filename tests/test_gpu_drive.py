@@ -144,3 +144,16 @@ def test_drive_deform_and_composite_chain(gs, oracle):
                                                 out_s[0].cpu().numpy(), out_s[1].cpu().numpy())
     np.testing.assert_array_equal(rgb.cpu().numpy(), sel_rgb.astype(np.float32))
     np.testing.assert_array_equal(dep.cpu().numpy(), sel_dep.astype(np.float32))
+
+
+def test_exp2_rate_kernel(gs):
+    """The exp2 throughput kernel computes what it claims: eight chains of
+    x <- 2^(-x) per thread, which converge to the fixed point 0.6412 (the
+    contraction factor is ln 2 * 2^(-x) < 0.5)."""
+    out = torch.empty(2 * 256, device="cuda")
+    n = gs.exp2_rate(2, 32, out)
+    torch.cuda.synchronize()
+    assert n == 2 * 256 * 32 * 8
+    np.testing.assert_allclose(out.cpu().numpy() / 8.0, 0.641185744, atol=1e-4)
+    with pytest.raises(gs.GsError, match="INVALID_ARG"):
+        gs.exp2_rate(0, 32, out)

@@ -271,3 +271,36 @@ def test_repeated_backward_of_one_forward(gs):
         assert rel_l2(b[k].cpu().numpy(), a[k].cpu().numpy()) < 2e-5, k
         assert rel_l2(c[k].cpu().numpy(), a[k].cpu().numpy()) < 2e-5, k
     assert float(a["opacity_logits"].abs().sum()) > 0
+
+
+def test_overwrite_mode_clears_unseen_rows(gs):
+    """Overwrite mode (GS_FLAG_GRAD_OVERWRITE) on gradient buffers full of
+    garbage: every row ends as the accumulate mode's gradient into zeroed
+    buffers, the rows of Gaussians no view sees exactly zero.  N = 4001 makes
+    every gradient array end off a 16-byte boundary (the clearing's scalar tail)."""
+    n = 4001
+    g = synth.box_scene(n, seed=31)
+    g["means"][1::2, 2] = -g["means"][1::2, 2]  # every other Gaussian behind the camera: unseen
+    W = H = 64
+    cam = synth.identity_camera(W, H)
+    rng = np.random.default_rng(31)
+    d_rgb = torch.from_numpy(rng.standard_normal((1, 3, H, W))).float().cuda()
+    d_dep = torch.from_numpy(0.1 * rng.standard_normal((1, H, W))).float().cuda()
+    G = gs.Gaussians.from_numpy(g)
+    ct = gs.cameras_tensor(cam[None])
+    kw = dict(tile=(8, 8), batch_depth=64, pix=(2, 1), persistent=True)
+    ref_r = gs.Renderer(gs.Batch(np.array([0, n])), W, H, **kw)
+    ref_r.forward(G, ct)
+    ref = ref_r.backward(G, ct, d_rgb, d_dep)  # accumulate into zeros
+    r = gs.Renderer(gs.Batch(np.array([0, n])), W, H, grad_overwrite=True, **kw)
+    r.forward(G, ct)
+    junk = dict(means=torch.full((n, 3), 7.0, device="cuda"), log_scales=torch.full((n, 3), -3.0, device="cuda"),
+                quats=torch.full((n, 4), 5.0, device="cuda"), opacity_logits=torch.full((n,), 9.0, device="cuda"),
+                sh=torch.full((n, 16, 3), 11.0, device="cuda"))
+    out = r.backward(G, ct, d_rgb, d_dep, grads=junk)
+    torch.cuda.synchronize()
+    for k in GROUPS:
+        a, b = out[k].cpu().numpy(), ref[k].cpu().numpy()
+        assert np.all(a[1::2] == 0.0), k  # unseen rows cleared
+        assert rel_l2(a, b) < 2e-5, k
+    assert float(ref["opacity_logits"].abs().sum()) > 0

@@ -683,7 +683,7 @@ struct OutPtrs {
 // batch b+1 is in flight while batch b is blended (keys of batch b+2 are
 // prefetched into registers).
 constexpr int kMaxPer = 4; // records per thread and batch (B <= 4 x threads)
-constexpr int kUnroll = 4; // Gaussians evaluated together in the blend loop
+constexpr int kUnroll = 8; // Gaussians evaluated together in the blend loop
 
 template <int PX, int PY>
 __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, const OutPtrs &o, int bin, int heavy,
@@ -788,7 +788,7 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
         const float4 *s0 = sm + (b & 1) * 3 * B, *s1 = s0 + B, *s2 = s0 + 2 * B;
         const int cnt = (int)min((uint32_t)B, n - (uint32_t)b * B);
         // warp-synchronous: every lane runs the same iterations (predicated),
-        // the warp leaves once all its lanes have stopped.  Four Gaussians at a
+        // the warp leaves once all its lanes have stopped.  kUnroll Gaussians at a
         // time: their falloff and alpha (independent of T) first, for ILP, then
         // the front-to-back updates in order.
         for (int k0 = 0; k0 < cnt; k0 += kUnroll) {
@@ -796,13 +796,13 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
                 if (k0 & 31) flag_window((uint32_t)b * B + (uint32_t)(k0 & ~31), k0 & 31);
                 break;
             }
-            uint32_t m4 = 0; // this thread's blended bits of the four entries
+            uint32_t m4 = 0; // this thread's blended bits of the kUnroll entries
             if (!tdone) {
                 float al[kUnroll][NP];
                 bool ok[kUnroll][NP], cv[kUnroll][NP];
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) {
-                    const float4 a = s0[k0 + u]; // B is a multiple of kUnroll: stays in the buffer
+                    const float4 a = s0[k0 + u]; // < B + kUnroll: inside the buffers and their padding
                     const float4 q = s1[k0 + u];
                     if constexpr (PX == 2) {
                         // the two pixels of a row as packed FP32 pairs
@@ -945,12 +945,14 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
     }
 }
 
-// The batch slots past a batch's end are read by the packed pixel-pair update
-// (with weight 0): they must hold finite values, so the buffers start at zero
-// (later they hold earlier, valid records).
+// The blend loop reads kUnroll slots at a time, up to kUnroll - 1 past a
+// batch's end (batch depths need not be multiples of kUnroll): the two batch
+// buffers are followed by kUnroll padding slots, and all slots must hold finite
+// values (the packed pixel-pair update multiplies them by weight 0), so they
+// start at zero (later they hold earlier, valid records).
 __device__ __forceinline__ void clear_batch_buffers(float4 *sm, int B)
 {
-    for (int k = threadIdx.x; k < 2 * 3 * B; k += blockDim.x) sm[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = threadIdx.x; k < 2 * 3 * B + kUnroll; k += blockDim.x) sm[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
 }
 
@@ -1018,7 +1020,7 @@ void launch_scatter(const gs_camera *cams, const Ws &w, int n_chunks, cudaStream
     if (n_chunks) scatter_kernel<<<n_chunks, 256, kScatterSmem, s>>>(cams, w);
 }
 
-int blend_smem_bytes(int batch_depth) { return 2 * 3 * batch_depth * (int)sizeof(float4); }
+int blend_smem_bytes(int batch_depth) { return (2 * 3 * batch_depth + kUnroll) * (int)sizeof(float4); }
 
 template <int PX, int PY>
 static void launch_blend_t(const gs_camera *cams, const Ws &w, const OutPtrs &o, int n_bins, int threads,

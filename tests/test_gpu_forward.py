@@ -120,8 +120,10 @@ def test_room_1m_keys_bit_exact(gs, room1m):
 
 @pytest.mark.parametrize("tile,depth,pix", [((8, 8), 64, (1, 1)), ((16, 8), 128, (1, 1)), ((32, 8), 256, (1, 1)),
                                             ((32, 16), 32, (1, 1)), ((16, 16), 256, (2, 2)), ((8, 8), 128, (2, 1)),
-                                            ((16, 8), 64, (1, 2)), ((16, 16), 128, (2, 1))])
+                                            ((16, 8), 64, (1, 2)), ((16, 16), 128, (2, 1)),
+                                            ((8, 8), 36, (2, 1)), ((16, 8), 100, (1, 1))])
 def test_tile_size_does_not_change_results(gs, tile, depth, pix):
+    # (batch depths 36 and 100: not multiples of the blend loop's 8 Gaussians)
     g = synth.room_scene(200_000, seed=4)
     W, H = 200, 150  # not a multiple of any tile
     cam = synth.room_camera(4, W, H)

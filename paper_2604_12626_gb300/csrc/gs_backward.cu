@@ -1,17 +1,23 @@
 // gs_backward.cu -- adjoint kernels of libgs (sm_103a).
 //
-// blend_backward   one CTA per (view, tile).  Each pixel walks its tile list
-//                  back to front from the last pair it blended, rebuilding the
-//                  transmittance by division (T_i = T_{i+1} / (1 - alpha_i)), so
-//                  only T_final and the last index per pixel were saved.  The
-//                  per-pair gradients of (uc, vc, conic, opacity, colour, z) are
-//                  reduced across the warp by shuffles, then across the CTA in
-//                  shared memory, and flushed with one set of float4 atomics per
-//                  (tile, Gaussian).
-// preprocess_backward  one thread per Gaussian, looping over the views of its
-//                  env: the chain rule through the conic inverse, the dilation,
-//                  J W Sigma W^T J^T, the quaternion normalisation and scales,
-//                  the SH direction and coefficients, and the opacity sigmoid.
+// blend_backward   persistent CTAs over (view, tile) bins -- heavy bins split
+//                  into 2048-pair segments that start from the forward's
+//                  checkpoints.  Each pixel walks the pairs back to front from
+//                  the last one it blended, rebuilding the transmittance by
+//                  division (T_i = T_{i+1} / (1 - alpha_i)), so only T_final and
+//                  the last index per pixel were saved; only the pairs the
+//                  forward flagged as blended are walked.  The per-pair
+//                  gradients of (uc, vc, conic, opacity, colour, z) are reduced
+//                  across the warp by a shuffle transpose, then across the CTA
+//                  in shared memory, and flushed with float4 atomics per
+//                  (tile, record) into the record's gradient row.  In overwrite
+//                  mode the same kernel clears the dense parameter gradients
+//                  (TMA bulk copies).
+// preprocess_backward  env-aligned chunks; the Gaussians some view sees go
+//                  through per-warp queues: the chain rule through the conic
+//                  inverse, the dilation, J W Sigma W^T J^T, the quaternion
+//                  normalisation and scales, the SH direction and coefficients,
+//                  and the opacity sigmoid.
 // Discrete decisions (cull, radius, footprint, skips, stop) are the forward's,
 // recomputed bit for bit from the same helpers; the 0.99 clamp and the colour
 // clamp at 0 pass zero gradient where active.
@@ -23,45 +29,6 @@
 
 namespace gs {
 
-
-__device__ __forceinline__ float warp_sum(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Sums v[0..15] over the warp with 16 shuffles (butterfly transpose): on
-// return, lane l holds the warp total of v[(l >> 1) & 15] (lanes l and l^1
-// hold the same value).
-__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16])
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const bool up = lane & 16;
-        const float keep = up ? v[i + 8] : v[i], send = up ? v[i] : v[i + 8];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const bool up = lane & 8;
-        const float keep = up ? v[i + 4] : v[i], send = up ? v[i] : v[i + 4];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const bool up = lane & 4;
-        const float keep = up ? v[i + 2] : v[i], send = up ? v[i] : v[i + 2];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    {
-        const bool up = lane & 2;
-        const float keep = up ? v[1] : v[0], send = up ? v[0] : v[1];
-        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-    }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
-}
 
 // Sums v[0..31] over the warp with 31 shuffles (butterfly transpose): on
 // return, lane l holds the warp total of v[l].

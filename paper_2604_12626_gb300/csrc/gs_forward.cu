@@ -2,21 +2,26 @@
 //
 // One gs_render call runs, on one stream and with no host synchronisation:
 //   setup       batch table -> workspace, counters cleared
-//   preprocess  one thread per Gaussian, looping over the views of its env:
-//               FP32 depth key + near cull, covariance, EWA projection with
-//               0.3 px dilation, conic, radius, exact per-pixel footprint
-//               range, SH-3 colour; writes the 48-byte record, the visibility
-//               bit and one bin-count increment per touched tile
-//   scan        exclusive scan of the bin counts -> tile ranges [start, end)
+//   preprocess  one CTA per env-aligned chunk of Gaussians, each warp walking
+//               32-Gaussian rounds over the views of the env: FP32 depth key +
+//               near cull, covariance (or LBS of posed avatar rows, fused),
+//               EWA projection with 0.3 px dilation, conic, radius, exact
+//               per-pixel footprint range; visible entries queued per warp for
+//               SH-3 colour on full warps; writes the 48-byte record, its
+//               64-byte gradient row, the visibility bit, and the chunk's tile
+//               counts (a shared 2D difference array, flushed per CTA)
+//   scan        exclusive scan of the bin counts -> tile ranges [start, end),
+//               heavy-bin list, large-bin chunk list
 //   scatter     one (depth key << 32 | record) key per touched tile, placed in
-//               its bin by an atomic cursor (order inside a bin is arbitrary)
+//               its bin at the chunk's offset (order inside a bin is arbitrary)
 //   sort        each bin sorted by key = (FP32 depth bits, record index), so the
 //               result equals a stable sort of the keys emitted in record order
 //               (gs_sort.cu)
 //   blend       one CTA per (view, tile) -- or a persistent grid pulling tiles
-//               from an atomic queue -- stages batches of records in shared
-//               memory and blends front to back per pixel with block-wide early
-//               exit once every pixel of the tile has stopped.
+//               from an atomic queue, heaviest first -- stages batches of
+//               records in shared memory and blends front to back per pixel
+//               with early exit once every pixel of the warp has stopped;
+//               flags in its key every pair that some pixel blended.
 // The rasterisation follows the 3DGS method the paper builds its renderer on
 // (Sec. 2.2, Sec. 3.2); the exact definition is the one in include/gs.h.
 #include <cuda_bf16.h>
@@ -43,17 +48,6 @@ __global__ void setup_kernel(const Table tb, Ws w)
 // ---------------------------------------------------------------------------
 // preprocess
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int find_env(const Table *tb, int64_t g)
-{
-    int lo = 0, hi = tb->n_envs - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (tb->env_off[mid] <= g) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 struct GaussIn {
     const float *means, *log_scales, *quats, *ologits, *cov3d;
     const void *sh;
@@ -874,29 +868,28 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
                             last[p0] = bl0 ? pos : last[p0];
                             last[p1] = bl1 ? pos : last[p1];
                         }
-                        m4 = (m4 << 1) | (uint32_t)blu;
-                        continue;
-                    }
+                    } else {
 #pragma unroll
-                    for (int p = 0; p < NP; ++p) {
-                        if (!dn[p] && cv[u][p]) {
-                            ++ncov[p];
-                            if (ok[u][p]) {
-                                // explicit roundings: the packed pair path above does the same
-                                const float alpha = al[u][p];
-                                const float Tn = __fmul_rn(T[p], __fsub_rn(1.0f, alpha));
-                                if (Tn < kTStop) {
-                                    dn[p] = true;
-                                } else {
-                                    const float wgt = __fmul_rn(alpha, T[p]);
-                                    C0[p] = __fmaf_rn(c.x, wgt, C0[p]);
-                                    C1[p] = __fmaf_rn(c.y, wgt, C1[p]);
-                                    C2[p] = __fmaf_rn(c.z, wgt, C2[p]);
-                                    D[p] = __fmaf_rn(z, wgt, D[p]);
-                                    T[p] = Tn;
-                                    ncon[p] = ncov[p];
-                                    last[p] = (uint32_t)b * B + k0 + u + 1;
-                                    blu = true;
+                        for (int p = 0; p < NP; ++p) {
+                            if (!dn[p] && cv[u][p]) {
+                                ++ncov[p];
+                                if (ok[u][p]) {
+                                    // explicit roundings: the packed pair path above does the same
+                                    const float alpha = al[u][p];
+                                    const float Tn = __fmul_rn(T[p], __fsub_rn(1.0f, alpha));
+                                    if (Tn < kTStop) {
+                                        dn[p] = true;
+                                    } else {
+                                        const float wgt = __fmul_rn(alpha, T[p]);
+                                        C0[p] = __fmaf_rn(c.x, wgt, C0[p]);
+                                        C1[p] = __fmaf_rn(c.y, wgt, C1[p]);
+                                        C2[p] = __fmaf_rn(c.z, wgt, C2[p]);
+                                        D[p] = __fmaf_rn(z, wgt, D[p]);
+                                        T[p] = Tn;
+                                        ncon[p] = ncov[p];
+                                        last[p] = (uint32_t)b * B + k0 + u + 1;
+                                        blu = true;
+                                    }
                                 }
                             }
                         }

@@ -225,8 +225,8 @@ def tune_fwd_bwd(api, rend, G, cams, candidates, N, dev, reps=2):
     rend.cfg.tile_w, rend.cfg.tile_h, rend.cfg.batch_depth, rend.cfg.pix_x, rend.cfg.pix_y = best
     return best, best_ms
 
-# Algorithmic work per unit (the figures and their derivation are in the design
-# notes): bytes for the memory-bound stages, FP32 lane operations for blending.
+# Algorithmic work per unit: bytes for the memory-bound stages (rooflines()),
+# FP32 lane operations per evaluation for the two blend kernels.
 OPS_PER_EVAL_FWD = 17   # offset, quadratic form, exp, alpha clamp / skip, T update, 3 colours + depth
 OPS_PER_EVAL_BWD = 40   # recomputed alpha, T_prev, dL/dalpha, conic / centre / colour / depth terms
 KERNEL_OF_STAGE = {"preprocess": "preprocess_kernel", "scan": "scan_bins_kernel", "scatter": "scatter_kernel",
@@ -400,7 +400,9 @@ def _event_ms(torch, stream, fn, reps=10):
 
 def avatar_and_composite_rows(api, synth, torch, dev, stream, outs, hbm_peak):
     """CUDA-event times of the kernels outside the headline step: LBS deform
-    and its adjoint (100 B per avatar Gaussian forward), keyframe
+    and its adjoint (100 B per avatar Gaussian forward: 64 B of canonical
+    parameters, weights and joint ids read, 36 B of posed mean and covariance
+    written), keyframe
     interpolation + forward kinematics of 256 avatars, and the composite of two
     64 x 256 x 256 RGB-D layers (48 B per pixel)."""
     n_av, n_per, n_frames = 256, 50_000, 30

@@ -265,12 +265,12 @@ FWD_KERNELS = ("setup_kernel", "preprocess_kernel", "scan_bins_kernel", "scatter
 BWD_KERNELS = ("clear_record_grads_kernel", "blend_backward_kernel", "preprocess_backward_kernel")
 
 
-def ncu_summary(csv_path, command):
+def ncu_summary(csv_path, command, out_path=None):
     """Per-kernel launches, time share and DRAM bytes of an ncu --csv launch
     list of this bench (metrics gpu__time_duration.sum, dram__bytes_read.sum,
-    dram__bytes_write.sum); writes profiles/dram_traffic.json (bytes per
-    gs_render / gs_render_backward call, tagged with the kernel sources' hash)
-    and prints the table."""
+    dram__bytes_write.sum); writes profiles/dram_traffic.json (or out_path:
+    bytes per gs_render / gs_render_backward call, tagged with the kernel
+    sources' hash), prints the table and returns the per-kernel entries."""
     import collections
     import csv
     import re
@@ -316,8 +316,9 @@ def ncu_summary(csv_path, command):
                    "gs_render_backward call (all its launches in that call), from one ncu run; stale once the "
                    "kernel sources change (source_hash over csrc/)",
            "command": command, "kernels": kern}
-    with open(os.path.join(ROOT, "profiles", "dram_traffic.json"), "w") as f:
+    with open(out_path or os.path.join(ROOT, "profiles", "dram_traffic.json"), "w") as f:
         json.dump(out, f, indent=1)
+    return kern
 
 
 def exp2_rate(api, torch, dev, stream, sm_count):

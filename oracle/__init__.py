@@ -45,6 +45,7 @@ _LIB = None
 AMB_VALUE = 1
 AMB_COUNT = 2
 AMB_FOOTPRINT, AMB_ORDER, AMB_ALPHA, AMB_STOP = 4, 8, 16, 32  # which decision was near its threshold
+AMB_CLAMP = 64  # alpha near the 0.99 clamp: the gradient (not the value) may differ
 
 
 def _so_path() -> Path:

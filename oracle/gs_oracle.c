@@ -51,6 +51,8 @@
 #define AMB_ORDER 8u
 #define AMB_ALPHA 16u
 #define AMB_STOP 32u
+#define AMB_CLAMP 64u /* alpha within FP32 error of the 0.99 clamp: the value is continuous there, the
+                         gradient is not (it passes zero where the clamp is active) */
 
 #define ALPHA_MIN (1.0 / 255.0)
 #define ALPHA_MAX 0.99
@@ -492,6 +494,8 @@ static void blend_step(pix_t *s, const cand_t *g, int i, int j, int32_t pos)
             s->amb |= AMB_VALUE;
     }
     if (alpha < ALPHA_MIN) return;
+    /* alpha = min(0.99, .) decision: same error bound as the 1/255 test */
+    if (fabs(power + log(g->o) - log(ALPHA_MAX)) <= dpow + 2e-6) s->amb |= AMB_CLAMP;
     double Tn = s->T * (1.0 - alpha);
     double relTn = s->relT + 4.8e-7 + (a_raw < ALPHA_MAX ? alpha / (1.0 - alpha) * (dpow + 2e-6) : 0.0);
     /* T (1 - alpha) < 1e-4 decision */

@@ -5,6 +5,7 @@ import pytest
 
 import oracle as _oracle
 import test_oracle_adjoint as adj
+import test_oracle_mask_pins as mask
 import test_oracle_pins as pins
 import test_oracle_pins_drive as drive
 
@@ -75,6 +76,15 @@ MUTANTS = [
      "            if (z <= best) {\n                second = best;", drive.test_mesh_occlusion_ties_and_near_cull),
     ("interpolation weights swapped", "o[e] = (1.0 - w) * A0[e] + w * A1[e];", "o[e] = w * A0[e] + (1.0 - w) * A1[e];",
      drive.test_interpolation_between_frames),
+    ("mask: clamp decision not flagged",
+     "if (fabs(power + log(g->o) - log(ALPHA_MAX)) <= dpow + 2e-6) s->amb |= AMB_CLAMP;", "",
+     mask.test_clamp_threshold_is_flagged),
+    ("mask: alpha decision bound dropped", "if (fabs(power + log(g->o) - log(ALPHA_MIN)) <= dpow + 2e-6) {",
+     "if (fabs(power + log(g->o) - log(ALPHA_MIN)) <= 0.0) {", mask.test_alpha_threshold_is_flagged),
+    ("mask: footprint flagged only outside r", "if (m >= g->r_lo - eps && m <= g->r_hi + eps) {",
+     "if (m > g->r_hi && m <= g->r_hi + eps) {", mask.test_footprint_threshold_is_flagged),
+    ("mask: stop decision bound dropped", "if (fabs(Tn - T_STOP) <= T_STOP * relTn + 1e-12) {",
+     "if (fabs(Tn - T_STOP) <= 0.0) {", mask.test_stop_threshold_is_flagged),
     ("adjoint: LBS covariance factor", "gA[4 * r + cc] = gm[r] * mu[cc] + 2.0 * acc;",
      "gA[4 * r + cc] = gm[r] * mu[cc] + acc;", adj.test_lbs_adjoint_matches_finite_differences),
 ]

@@ -7,15 +7,18 @@
 //                  division (T_i = T_{i+1} / (1 - alpha_i)), so only T_final and
 //                  the last index per pixel were saved; only the pairs the
 //                  forward flagged as blended are walked.  The per-pair
-//                  gradients of (uc, vc, conic, opacity, colour, z) are reduced
+//                  gradients of (uc, vc, 2D covariance, opacity, colour, z) --
+//                  the covariance one summed as (Q d)(Q d)^T / 2 per pixel, Q
+//                  the conic and d the offset, so no conic-to-covariance
+//                  conversion follows the sum -- are reduced
 //                  across the warp by a shuffle transpose, then across the CTA
 //                  in shared memory, and flushed with float4 atomics per
 //                  (tile, record) into the record's gradient row.  In overwrite
 //                  mode the same kernel clears the dense parameter gradients
 //                  (TMA bulk copies).
 // preprocess_backward  env-aligned chunks; the Gaussians some view sees go
-//                  through per-warp queues: the chain rule through the conic
-//                  inverse, the dilation, J W Sigma W^T J^T, the quaternion
+//                  through per-warp queues: the chain rule through the
+//                  dilation, J W Sigma W^T J^T, the quaternion
 //                  normalisation and scales, the SH direction and coefficients,
 //                  and the opacity sigmoid.
 // Discrete decisions (cull, radius, footprint, skips, stop) are the forward's,
@@ -321,13 +324,20 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
                             const float2 dy = make_float2(dy1, dy1);
                             G[u][5] = __ffma2_rn(dalm, make_float2(ex[u][p0], ex[u][p1]), G[u][5]);
                             const float2 ngp = __fmul2_rn(dalm, nal); // -dL/dalpha * alpha
+                            // w = Q d (Q the conic): dpower/dd = -w and dpower/dSigma2 =
+                            // w w^T / 2, so the covariance gradient is summed in that
+                            // form directly (no conic-to-covariance conversion, whose
+                            // cancellation on thin ellipses would amplify rounding)
                             const float qyd = q.y * dy1, qzd = q.z * dy1;
-                            G[u][0] = __ffma2_rn(ngp, __ffma2_rn(qx, dx, make_float2(qyd, qyd)), G[u][0]);
-                            G[u][1] = __ffma2_rn(ngp, __ffma2_rn(qy, dx, make_float2(qzd, qzd)), G[u][1]);
-                            const float2 hgp = __fmul2_rn(ngp, make_float2(0.5f, 0.5f));
-                            G[u][2] = __ffma2_rn(__fmul2_rn(hgp, dx), dx, G[u][2]);
-                            G[u][3] = __ffma2_rn(__fmul2_rn(ngp, dx), dy, G[u][3]);
-                            G[u][4] = __ffma2_rn(__fmul2_rn(hgp, dy), dy, G[u][4]);
+                            const float2 wx = __ffma2_rn(qx, dx, make_float2(qyd, qyd));
+                            const float2 wy = __ffma2_rn(qy, dx, make_float2(qzd, qzd));
+                            G[u][0] = __ffma2_rn(ngp, wx, G[u][0]);
+                            G[u][1] = __ffma2_rn(ngp, wy, G[u][1]);
+                            const float2 nhw = __fmul2_rn(__fmul2_rn(ngp, make_float2(-0.5f, -0.5f)), wx);
+                            G[u][2] = __ffma2_rn(nhw, wx, G[u][2]);
+                            G[u][3] = __ffma2_rn(nhw, wy, G[u][3]);
+                            G[u][4] = __ffma2_rn(__fmul2_rn(__fmul2_rn(ngp, make_float2(-0.5f, -0.5f)), wy), wy,
+                                                 G[u][4]);
                         }
                     }
 #pragma unroll
@@ -369,11 +379,14 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
                                 const float dx = dxs[u][p], dy = dys[u][p];
                                 gu[5] += dal * ex[u][p]; // d alpha / d opacity = exp(power)
                                 const float gp = dal * alpha;
-                                gu[0] += -gp * (q.x * dx + q.y * dy);
-                                gu[1] += -gp * (q.z * dy + q.y * dx);
-                                gu[2] += -0.5f * gp * dx * dx;
-                                gu[4] += -0.5f * gp * dy * dy;
-                                gu[3] += -gp * dx * dy;
+                                // w = Q d: dpower/dd = -w, dpower/dSigma2 = w w^T / 2
+                                const float wx = q.x * dx + q.y * dy, wy = q.y * dx + q.z * dy;
+                                gu[0] += -gp * wx;
+                                gu[1] += -gp * wy;
+                                const float hg = 0.5f * gp;
+                                gu[2] += hg * wx * wx;
+                                gu[3] += hg * wx * wy;
+                                gu[4] += hg * wy * wy;
                             }
                         }
                     }
@@ -628,8 +641,9 @@ __device__ __forceinline__ void gaussian_backward(const gs_camera *__restrict__ 
         op = r2.z;
         // a channel clamped at 0 passes no gradient
         const float gch[3] = {(clamped & 1u) ? 0.f : r1.z, (clamped & 2u) ? 0.f : r1.w, (clamped & 4u) ? 0.f : r2.x};
-        // (uc, vc, A, B, C, opacity, r, g, b, z)
-        const float g_u = r0.x, g_v = r0.y, gA = r0.z, gB = r0.w, gC = r1.x, g_op = r1.y;
+        // (uc, vc, Sigma2 xx, Sigma2 xy, Sigma2 yy, opacity, r, g, b, z): the 2D
+        // covariance part as the symmetric matrix dL/dSigma2 (xy = half of dL/db)
+        const float g_u = r0.x, g_v = r0.y, G00 = r0.z, G01 = r0.w, G11 = r1.x, g_op = r1.y;
         const float g_z = r2.y;
         const gs_camera &cam = cams[v];
         const float zk = depth_key(mx, my, mz, cam);
@@ -639,12 +653,6 @@ __device__ __forceinline__ void gaussian_backward(const gs_camera *__restrict__ 
         const float px = pj.px, py = pj.py, ipz = 1.0f / pj.pz, ipz2 = ipz * ipz;
         float gpx = g_u * cam.fx * ipz, gpy = g_v * cam.fy * ipz;
         float gpz = -g_u * cam.fx * px * ipz2 - g_v * cam.fy * py * ipz2 + g_z;
-        // conic = (c, -b, a) / det
-        const float a = pj.a, b = pj.b, c = pj.c, det = pj.det, id2 = 1.0f / (det * det);
-        const float ga = (-gA * c * c + gB * b * c - gC * b * b) * id2;
-        const float gb = (2.f * gA * b * c - gB * (a * c + b * b) + 2.f * gC * a * b) * id2;
-        const float gc = (-gA * b * b + gB * a * b - gC * a * a) * id2;
-        const float G00 = ga, G01 = 0.5f * gb, G11 = gc;
         const float *t = pj.t;
         // dL/dSigma = T^T G2 T (symmetric)
         const float h0 = G00 * t[0] + G01 * t[3], h1 = G00 * t[1] + G01 * t[4], h2 = G00 * t[2] + G01 * t[5];

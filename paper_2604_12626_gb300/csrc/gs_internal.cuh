@@ -15,9 +15,11 @@
 //   scratch     [P_cap] uint64, ping-pong buffer of the large-bin merges
 //   pix_T       [V*H*W] final transmittance (saved for the backward)
 //   pix_last    [V*H*W] 1 + tile-list position of the last blended pair
-//   d_rec       [R] 16 floats (64 B, one DRAM burst): dL/d(uc, vc, A, B, C,
-//               opacity, r, g, b, z), 2 unused, then at [12] the bits of the
-//               colour channels that were clamped at 0 (written by the forward)
+//   d_rec       [R] 16 floats (64 B, one DRAM burst): dL/d(uc, vc), the 2D
+//               covariance gradient dL/dSigma2 (xx, xy, yy; xy = half of the
+//               off-diagonal entry's derivative), dL/d(opacity, r, g, b, z),
+//               the opacity, 1 unused, then at [12] the bits of the colour
+//               channels that were clamped at 0 (written by the forward)
 #pragma once
 
 #include <cuda_bf16.h>
@@ -38,8 +40,8 @@ constexpr uint32_t kKeyRecord = 0x7fffffffu;
 constexpr float kTStop = 1e-4f;
 constexpr float kDilation = 0.3f;
 constexpr int kSortChunk = 4096; // keys one CTA sorts; larger bins are merged
-// floats per record row of d_rec: dL/d(u, v, A, B, C, opacity, r, g, b, z), the
-// opacity, 0, the colour-clamp mask, 0, 0, 0
+// floats per record row of d_rec: dL/d(u, v), dL/dSigma2 (xx, xy, yy),
+// dL/d(opacity, r, g, b, z), the opacity, 0, the colour-clamp mask, 0, 0, 0
 constexpr int kGradStride = 16;
 constexpr int kAccStride = 12;    // floats per record in the backward's shared-memory accumulator
 constexpr int kMaxJoints = 64;    // joints of one avatar tree

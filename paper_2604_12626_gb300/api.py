@@ -98,9 +98,10 @@ _lib.gs_autotune.argtypes = [_R(GsGaussians), _R(GsBatch), _P, _R(GsRenderConfig
                              _P, _P, ctypes.c_int32, ctypes.c_int32, _R(ctypes.c_float), _P]
 _lib.gs_workspace_sections.argtypes = [_R(GsRenderConfig), _R(GsBatch), _P, _R(GsWsSections)]
 _lib.gs_render_static.argtypes = [_R(GsGaussians), _R(GsBatch), _P, _R(GsRenderConfig), _P, _P, _P, _P, _P]
+_lib.gs_render_static_status.argtypes = [_P, _R(ctypes.c_int32)]
 _lib.gs_profile_enable.argtypes = [ctypes.c_int32]
 _lib.gs_profile_read.argtypes = [_P, _P]
-for _f in ("gs_render_static", "gs_profile_enable", "gs_profile_read", "gs_workspace_sections", "gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_deform_avatars",
+for _f in ("gs_render_static", "gs_render_static_status", "gs_profile_enable", "gs_profile_read", "gs_workspace_sections", "gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_deform_avatars",
            "gs_deform_avatars_backward", "gs_get_status", "gs_render_stats", "gs_autotune"):
     getattr(_lib, _f).restype = ctypes.c_int32
 _lib.gs_exp2_rate.argtypes = [ctypes.c_int32, ctypes.c_int32, _P, _P]
@@ -108,7 +109,7 @@ _lib.gs_exp2_rate.restype = ctypes.c_int32
 _lib.gs_last_cuda_error.restype = ctypes.c_int32
 _lib.gs_version.restype = ctypes.c_int32
 
-EXPORTS = ("gs_render_static", "gs_profile_enable", "gs_profile_read", "gs_workspace_sections", "gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_deform_avatars",
+EXPORTS = ("gs_render_static", "gs_render_static_status", "gs_profile_enable", "gs_profile_read", "gs_workspace_sections", "gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_deform_avatars",
            "gs_deform_avatars_backward", "gs_get_status", "gs_render_stats", "gs_autotune", "gs_last_cuda_error",
            "gs_version", "gs_composite_nearest", "gs_forward_kinematics", "gs_interpolate_joints",
            "gs_render_avatars", "gs_mesh_workspace_size", "gs_render_mesh", "gs_exp2_rate")
@@ -433,6 +434,14 @@ def render_static(g: Gaussians, batch: Batch, cams: torch.Tensor, cfg: GsRenderC
     return out
 
 
+def render_static_status(stream=None) -> int:
+    """gs_render_static_status: synchronises; the device status word the last
+    gs_render_static call left (0 or GS_ERR_CAPACITY = -4), then cleared."""
+    v = ctypes.c_int32(0)
+    _check(_lib.gs_render_static_status(_stream(stream), ctypes.byref(v)), "gs_render_static_status")
+    return v.value
+
+
 def deform(av: Avatars, G: torch.Tensor, out_means: torch.Tensor, out_cov3d: torch.Tensor, stream=None):
     _check(_lib.gs_deform_avatars(ctypes.byref(av.c), _ptr(G), _ptr(out_means), _ptr(out_cov3d), _stream(stream)),
            "gs_deform_avatars")
@@ -560,6 +569,86 @@ class RenderFunction(torch.autograd.Function):
 def render(means, log_scales, quats, opacity_logits, sh, renderer: Renderer, cams):
     """Differentiable batched render; see RenderFunction."""
     return RenderFunction.apply(means, log_scales, quats, opacity_logits, sh, renderer, cams)
+
+
+class AvatarScene:
+    """One env of scene Gaussians plus avatars posed by LBS every frame,
+    rendered jointly in one pass into the env's views (Sec. 3.2 last
+    paragraph, Sec. 3.3), with every buffer allocated once so that a forward +
+    backward training step captures into one CUDA graph.
+
+    Rows: the scene's Gaussians, then the avatars' (their mean and covariance
+    written by gs_deform_avatars each forward).  ``scene``: device tensors
+    means, log_scales, quats, opacity_logits, sh of the scene; ``avatars``:
+    canonical means, log_scales, quats, opacity_logits, sh plus joint_ids
+    ([M,4] int16 holding the uint16 ids), weights, avatar_of (int32).  They
+    are copied into this object's own concatenated tensors (``scene_params`` /
+    ``avatar_params`` are views of them, to be updated in place by an
+    optimizer).  Gradients: gs_render_backward in overwrite mode into
+    ``grads`` (all rows), then gs_deform_avatars_backward into ``avatar_grads``
+    (canonical means, log_scales, quats and the joint transforms G)."""
+
+    def __init__(self, scene: dict, avatars: dict, n_avatars: int, n_joints: int, width: int, height: int,
+                 n_views: int, sh_dtype=torch.float32, device="cuda", **cfg_kw):
+        dev = torch.device(device)
+        ns, m = scene["means"].shape[0], avatars["means"].shape[0]
+        n = ns + m
+        self.ns, self.m, self.n_avatars, self.n_joints = ns, m, n_avatars, n_joints
+        f32 = dict(device=dev, dtype=torch.float32)
+        self.means = torch.empty((n, 3), **f32)
+        self.means[:ns] = scene["means"]
+        self.log_scales = torch.zeros((n, 3), **f32)
+        self.log_scales[:ns] = scene["log_scales"]
+        self.quats = torch.zeros((n, 4), **f32)
+        self.quats[:ns] = scene["quats"]
+        self.quats[ns:, 0] = 1.0
+        self.opacity_logits = torch.cat([scene["opacity_logits"], avatars["opacity_logits"]]).to(**f32).contiguous()
+        self.sh = torch.cat([scene["sh"], avatars["sh"]]).to(device=dev, dtype=sh_dtype).contiguous()
+        self.cov3d = torch.zeros((n, 6), **f32)
+        self.av_means = avatars["means"].to(**f32).clone().contiguous()
+        self.av_log_scales = avatars["log_scales"].to(**f32).clone().contiguous()
+        self.av_quats = avatars["quats"].to(**f32).clone().contiguous()
+        self.av = Avatars(self.av_means, self.av_log_scales, self.av_quats, avatars["joint_ids"].contiguous(),
+                          avatars["weights"].to(**f32).contiguous(), avatars["avatar_of"].contiguous(), n_avatars,
+                          n_joints, dest=torch.arange(ns, n, dtype=torch.int64, device=dev))
+        self.g = Gaussians(self.means, self.log_scales, self.quats, self.opacity_logits, self.sh, self.cov3d)
+        batch = Batch(np.array([0, n]), view_env=np.zeros(n_views, np.int32), env_cov3d_begin=[ns])
+        self.renderer = Renderer(batch, width, height, device=device, grad_overwrite=True, **cfg_kw)
+        self.out = self.renderer.alloc_outputs()
+        self.grads = dict(means=torch.empty((n, 3), **f32), log_scales=torch.empty((n, 3), **f32),
+                          quats=torch.empty((n, 4), **f32), opacity_logits=torch.empty((n,), **f32),
+                          sh=torch.empty((n, 16, 3), **f32), cov3d=torch.empty((n, 6), **f32))
+        self.avatar_grads = dict(means=torch.empty((m, 3), **f32), log_scales=torch.empty((m, 3), **f32),
+                                 quats=torch.empty((m, 4), **f32),
+                                 G=torch.empty((n_avatars, n_joints, 3, 4), **f32))
+
+    @property
+    def scene_params(self) -> dict:
+        ns = self.ns
+        return dict(means=self.means[:ns], log_scales=self.log_scales[:ns], quats=self.quats[:ns],
+                    opacity_logits=self.opacity_logits[:ns], sh=self.sh[:ns])
+
+    @property
+    def avatar_params(self) -> dict:
+        return dict(means=self.av_means, log_scales=self.av_log_scales, quats=self.av_quats,
+                    opacity_logits=self.opacity_logits[self.ns:], sh=self.sh[self.ns:])
+
+    def forward(self, G: torch.Tensor, cams: torch.Tensor, stream=None):
+        """Poses the avatars with joint transforms G [A,J,3,4] and renders every
+        view: (rgb, depth, T, n_contrib) in this object's output buffers."""
+        deform(self.av, G, self.means, self.cov3d, stream=stream)
+        return self.renderer.forward(self.g, cams, out=self.out, stream=stream)
+
+    def backward(self, G: torch.Tensor, cams: torch.Tensor, d_rgb: torch.Tensor, d_depth: torch.Tensor, stream=None):
+        """Adjoint of the last forward: (grads of every row, canonical avatar
+        grads with dL/dG).  Scene rows of ``grads`` are the scene's gradients,
+        avatar rows of its opacity_logits / sh the avatars' own."""
+        self.renderer.backward(self.g, cams, d_rgb, d_depth, grads=self.grads, stream=stream)
+        with torch.cuda.stream(stream if stream is not None else torch.cuda.current_stream()):
+            for t in self.avatar_grads.values():
+                t.zero_()
+        deform_backward(self.av, G, self.grads["means"], self.grads["cov3d"], self.avatar_grads, stream=stream)
+        return self.grads, self.avatar_grads
 
 
 class SceneWithAvatarsFunction(torch.autograd.Function):

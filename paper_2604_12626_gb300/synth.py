@@ -315,3 +315,32 @@ def bf16_bits(x: np.ndarray) -> np.ndarray:
 
 def bf16_to_f32(bits: np.ndarray) -> np.ndarray:
     return (np.asarray(bits, np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
+def training_scene(seed: int = 0, n_room: int = 500_000, n_avatars: int = 2, n_per: int = 50_000,
+                   n_views: int = 16, W: int = 512, H: int = 512) -> dict:
+    """The forward + backward training workload: one room of ``n_room``
+    Gaussians, ``n_avatars`` avatars of ``n_per`` Gaussians (24-joint tree,
+    posed per frame with theta ~ N(0, 0.3)), ``n_views`` cameras at random poses
+    (hfov 90 degrees, so f = W / 2 at 512 px: 256), avatar a standing 2 m in
+    front of camera a so that the joint transforms are seen; and the
+    perturbation of the target scene: means + N(0, 1 cm), SH + N(0, 0.02), for
+    the room's and the avatars' canonical Gaussians alike.  Returns a dict:
+    room (Gaussian dict), avatars (canonical dict with joint_ids, weights,
+    avatar_of), G [A,24,3,4], cams [V,16], d_room_means, d_room_sh,
+    d_av_means, d_av_sh (float32)."""
+    rng = np.random.default_rng(80_000 + seed)
+    room = room_scene(n_room, seed=seed)
+    avs = [avatar_canonical(n_per, 100 * seed + a) for a in range(n_avatars)]
+    av = {k: np.concatenate([a[k] for a in avs]) for k in avs[0]}
+    av["avatar_of"] = np.repeat(np.arange(n_avatars), n_per).astype(np.int32)
+    cams = np.stack([room_camera(1000 * seed + v, W, H) for v in range(n_views)])
+    G = np.stack([random_pose(1000 * seed + a) for a in range(n_avatars)]).astype(np.float32)
+    for a in range(n_avatars):
+        fwd, C = cams[a % n_views][6:9].astype(np.float64), cams[a % n_views][9:12].astype(np.float64)
+        root = C + 2.0 * fwd + np.array([0.0, 0.0, -0.3])
+        G[a, :, :, 3] += (root - G[a, 0, :, 3]).astype(np.float32)
+    return dict(room=room, avatars=av, G=G, cams=cams,
+                d_room_means=_normal(rng, (n_room, 3), 0.0, 0.01), d_room_sh=_normal(rng, (n_room, 16, 3), 0.0, 0.02),
+                d_av_means=_normal(rng, (n_avatars * n_per, 3), 0.0, 0.01),
+                d_av_sh=_normal(rng, (n_avatars * n_per, 16, 3), 0.0, 0.02))

@@ -118,3 +118,39 @@ def gpu_outputs(out, v=None):
     if v is None:
         return dict(rgb=rgb, depth=depth, T=T, n_contrib=nc)
     return dict(rgb=rgb[v], depth=depth[v], T=T[v], n_contrib=nc[v])
+
+
+GRAD_ELEM_REL = 1e-3  # per element: |g - g_ref| <= 1e-3 max|g_ref| + 1e-7 (per parameter group)
+GRAD_ELEM_ABS = 1e-7
+
+
+def rel_l2(a, b) -> float:
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def check_grad(a, b, name: str, rel_l2_max: float, elem_rel: float = GRAD_ELEM_REL,
+               elem_abs: float = GRAD_ELEM_ABS) -> dict:
+    """Gradient parity of one parameter group: the relative L2 error over the
+    group is at most ``rel_l2_max``, and every element obeys
+    |a - b| <= elem_rel * max|b| + elem_abs.  ``a`` is the CUDA result, ``b``
+    the reference, both [N, ...] with N the Gaussian index (or any array).  The
+    returned statistics (and the assertion message) name the worst element: its
+    index (row = Gaussian), both values and the bound."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    assert a.shape == b.shape, (name, a.shape, b.shape)
+    diff = np.abs(a - b)
+    scale = float(np.abs(b).max(initial=0.0))
+    bound = elem_rel * scale + elem_abs
+    worst = int(np.argmax(diff)) if diff.size else 0
+    idx = tuple(int(i) for i in np.unravel_index(worst, a.shape)) if diff.size else ()
+    st = dict(group=name, rel_l2=rel_l2(a, b), worst_abs=float(diff.max(initial=0.0)), worst_index=idx,
+              worst_value=float(a[idx]) if diff.size else 0.0, worst_ref=float(b[idx]) if diff.size else 0.0,
+              elem_bound=bound, max_ref=scale, worst_over_bound=float(diff.max(initial=0.0)) / bound)
+    print(f"grad {name}: rel L2 {st['rel_l2']:.2e}, worst |d| {st['worst_abs']:.2e} at {idx} "
+          f"({st['worst_over_bound']:.3f} of the element bound)")
+    assert st["rel_l2"] <= rel_l2_max, st
+    assert st["worst_abs"] <= bound, st
+    return st

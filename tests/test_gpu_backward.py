@@ -1,12 +1,17 @@
 """Adjoint of the CUDA path (gs_render_backward, gs_deform_avatars_backward,
 the autograd Functions) against the FP64 oracle adjoint, which is itself pinned
-to FP64 central finite differences (tests/test_oracle_adjoint.py)."""
+to FP64 central finite differences (tests/test_oracle_adjoint.py).  Every
+parameter group is checked by its relative L2 error and element by element
+(|g - g_oracle| <= 1e-3 max|g_oracle| + 1e-7, the worst element reported).
+Room scenes pass no upstream gradient through the pixels the oracle flags as
+ambiguous: there an FP32 decision may legitimately differ from the FP64 one."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from helpers import check_grad  # noqa: E402
 from paper_2604_12626_gb300 import synth  # noqa: E402
 
 GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
@@ -21,10 +26,19 @@ def gs():
     return api
 
 
-def rel_l2(a, b):
-    a = np.asarray(a, np.float64).ravel()
-    b = np.asarray(b, np.float64).ravel()
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+def mask_ambiguous(oracle, g, cams, W, H, d_rgb, d_depth, offs=None, view_env=None):
+    """Zero the upstream gradient at every pixel the oracle flags (in place)."""
+    n = g["means"].shape[0]
+    offs = np.array([0, n]) if offs is None else offs
+    view_env = np.arange(len(offs) - 1) if view_env is None else np.asarray(view_env)
+    flagged = 0
+    for v, e in enumerate(view_env):
+        sl = slice(offs[e], offs[e + 1])
+        amb = oracle.render({k: x[sl] for k, x in g.items()}, cams[v], W, H)["amb"] != 0
+        d_rgb[v][:, amb] = 0.0
+        d_depth[v][amb] = 0.0
+        flagged += int(amb.sum())
+    return flagged
 
 
 def gpu_forward_backward(api, g, cams, W, H, d_rgb, d_depth, offs=None, view_env=None, sh_dtype=torch.float32, **kw):
@@ -66,9 +80,7 @@ def test_backward_matches_oracle_box_scene(gs, oracle):
     a = gpu_forward_backward(gs, g, cam[None], W, H, d_rgb, d_depth)
     b = oracle_grads(oracle, g, cam[None], W, H, d_rgb, d_depth)
     for k in GROUPS:
-        e = rel_l2(a[k], b[k])
-        print(f"box grad {k}: rel L2 {e:.2e}")
-        assert e < 1e-4, (k, e)
+        check_grad(a[k], b[k], f"box {k}", 1e-4)
 
 
 def test_backward_matches_oracle_room_views(gs, oracle):
@@ -79,12 +91,11 @@ def test_backward_matches_oracle_room_views(gs, oracle):
     d_rgb = rng.standard_normal((3, 3, H, W)).astype(np.float32)
     d_depth = (0.1 * rng.standard_normal((3, H, W))).astype(np.float32)
     offs = np.array([0, 120_000])
+    mask_ambiguous(oracle, g, cams, W, H, d_rgb, d_depth, offs=offs, view_env=[0, 0, 0])
     a = gpu_forward_backward(gs, g, cams, W, H, d_rgb, d_depth, offs=offs, view_env=[0, 0, 0])
     b = oracle_grads(oracle, g, cams, W, H, d_rgb, d_depth, offs=offs, view_env=[0, 0, 0])
     for k in GROUPS:
-        e = rel_l2(a[k], b[k])
-        print(f"room grad {k}: rel L2 {e:.2e}")
-        assert e < 1e-3, (k, e)
+        check_grad(a[k], b[k], f"room {k}", 1e-3)
 
 
 def test_backward_batched_envs_and_persistent(gs, oracle):
@@ -93,10 +104,11 @@ def test_backward_batched_envs_and_persistent(gs, oracle):
     rng = np.random.default_rng(2)
     d_rgb = rng.standard_normal((3, 3, H, W)).astype(np.float32)
     d_depth = (0.1 * rng.standard_normal((3, H, W))).astype(np.float32)
+    mask_ambiguous(oracle, g, cams, W, H, d_rgb, d_depth, offs=offs)
     a = gpu_forward_backward(gs, g, cams, W, H, d_rgb, d_depth, offs=offs, persistent=True)
     b = oracle_grads(oracle, g, cams, W, H, d_rgb, d_depth, offs=offs)
     for k in GROUPS:
-        assert rel_l2(a[k], b[k]) < 1e-3, k
+        check_grad(a[k], b[k], f"batched {k}", 1e-3)
 
 
 @pytest.mark.parametrize("tile,depth,pix", [((8, 8), 64, (1, 1)), ((16, 16), 256, (2, 2)), ((16, 8), 128, (2, 1)),
@@ -108,10 +120,11 @@ def test_backward_tile_and_pixels_per_thread(gs, oracle, tile, depth, pix):
     rng = np.random.default_rng(5)
     d_rgb = rng.standard_normal((1, 3, H, W)).astype(np.float32)
     d_depth = (0.1 * rng.standard_normal((1, H, W))).astype(np.float32)
+    mask_ambiguous(oracle, g, cam[None], W, H, d_rgb, d_depth)
     a = gpu_forward_backward(gs, g, cam[None], W, H, d_rgb, d_depth, tile=tile, batch_depth=depth, pix=pix)
     b = oracle_grads(oracle, g, cam[None], W, H, d_rgb, d_depth)
     for k in GROUPS:
-        assert rel_l2(a[k], b[k]) < 1e-3, k
+        check_grad(a[k], b[k], f"tile {tile} pix {pix} {k}", 1e-3)
 
 
 @pytest.mark.parametrize("persistent", [False, True])
@@ -124,6 +137,7 @@ def test_backward_heavy_tiles_split_into_segments(gs, oracle, persistent):
     rng = np.random.default_rng(6)
     d_rgb = rng.standard_normal((1, 3, H, W)).astype(np.float32)
     d_depth = (0.1 * rng.standard_normal((1, H, W))).astype(np.float32)
+    mask_ambiguous(oracle, g, cam[None], W, H, d_rgb, d_depth)
     r = gs.Renderer(gs.Batch(np.array([0, 400_000])), W, H, persistent=persistent)
     G = gs.Gaussians.from_numpy(g)
     ct = gs.cameras_tensor(cam[None])
@@ -134,9 +148,7 @@ def test_backward_heavy_tiles_split_into_segments(gs, oracle, persistent):
     torch.cuda.synchronize()
     b = oracle_grads(oracle, g, cam[None], W, H, d_rgb, d_depth)
     for k in GROUPS:
-        e = rel_l2(gr[k].cpu().numpy(), b[k])
-        print(f"heavy-tile grad {k}: rel L2 {e:.2e}")
-        assert e < 1e-3, (k, e)
+        check_grad(gr[k].cpu().numpy(), b[k], f"heavy-tile {k}", 1e-3)
 
 
 @pytest.mark.parametrize("dt", ["f16", "bf16"])
@@ -155,7 +167,7 @@ def test_backward_half_sh(gs, oracle, dt):
                 else synth.bf16_to_f32(synth.bf16_bits(g["sh"])))
     b = oracle_grads(oracle, gq, cam[None], W, H, d_rgb, d_depth)
     for k in GROUPS:
-        assert rel_l2(a[k], b[k]) < 1e-4, k
+        check_grad(a[k], b[k], f"{dt} SH {k}", 1e-4)
 
 
 def test_autograd_function_l1_loss(gs):
@@ -240,10 +252,10 @@ def test_scene_with_avatars_forward_backward_vs_oracle(gs, oracle):
              (sp[3].grad, og["opacity_logits"][:ns]), (sp[4].grad, og["sh"][:ns]), (ap[0].grad, oga["means"]),
              (ap[1].grad, oga["log_scales"]), (ap[2].grad, oga["quats"]), (aop.grad, og["opacity_logits"][ns:]),
              (ash.grad, og["sh"][ns:]), (Gt.grad, oga["G"])]
-    for i, (a, b) in enumerate(pairs):
-        e = rel_l2(a.cpu().numpy(), b)
-        print(f"avatar-scene grad {i}: rel L2 {e:.2e}")
-        assert e < 1e-3, (i, e)
+    names = ("scene means", "scene log_scales", "scene quats", "scene opacity_logits", "scene sh", "avatar means",
+             "avatar log_scales", "avatar quats", "avatar opacity_logits", "avatar sh", "joint G")
+    for name, (a, b) in zip(names, pairs):
+        check_grad(a.cpu().numpy(), b, f"avatar-scene {name}", 1e-3)
 
 
 def test_repeated_backward_of_one_forward(gs):
@@ -268,8 +280,8 @@ def test_repeated_backward_of_one_forward(gs):
     c = {k: v.clone() for k, v in r.backward(G, ct, d_rgb, d_dep).items() if v is not None}
     torch.cuda.synchronize()
     for k in a:  # equal up to the order of the float atomics (a stale row would double a gradient)
-        assert rel_l2(b[k].cpu().numpy(), a[k].cpu().numpy()) < 2e-5, k
-        assert rel_l2(c[k].cpu().numpy(), a[k].cpu().numpy()) < 2e-5, k
+        check_grad(b[k].cpu().numpy(), a[k].cpu().numpy(), f"second backward {k}", 2e-5, 1e-5, 1e-9)
+        check_grad(c[k].cpu().numpy(), a[k].cpu().numpy(), f"new forward {k}", 2e-5, 1e-5, 1e-9)
     assert float(a["opacity_logits"].abs().sum()) > 0
 
 
@@ -302,5 +314,5 @@ def test_overwrite_mode_clears_unseen_rows(gs):
     for k in GROUPS:
         a, b = out[k].cpu().numpy(), ref[k].cpu().numpy()
         assert np.all(a[1::2] == 0.0), k  # unseen rows cleared
-        assert rel_l2(a, b) < 2e-5, k
+        check_grad(a, b, f"overwrite {k}", 2e-5, 1e-5, 1e-9)
     assert float(ref["opacity_logits"].abs().sum()) > 0

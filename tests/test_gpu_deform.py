@@ -6,7 +6,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from helpers import compare_view, gpu_outputs  # noqa: E402
+from helpers import check_grad, compare_view, gpu_outputs  # noqa: E402
 from paper_2604_12626_gb300 import synth  # noqa: E402
 
 
@@ -83,9 +83,7 @@ def test_deform_backward_matches_oracle(gs, oracle):
     ref = oracle.lbs_backward(av["means"], av["log_scales"], av["quats"], av["joint_ids"].astype(np.int32),
                               av["weights"], avatar_of, G.astype(np.float64), gm, gc)
     for k in ("means", "log_scales", "quats", "G"):
-        a, b = grads[k].cpu().numpy().ravel(), ref[k].ravel()
-        e = np.linalg.norm(a - b) / np.linalg.norm(b)
-        assert e < 1e-5, (k, e)
+        check_grad(grads[k].cpu().numpy(), ref[k], f"LBS adjoint {k}", 1e-5)
 
 
 def test_rooms_with_avatars_batched_vs_oracle(gs, oracle):

@@ -197,15 +197,27 @@ gs_status gs_render_avatars(const gs_gaussians *g, const gs_batch *batch, const 
  * Allocates nothing: no cudaMalloc/cudaFree, no library allocation, and no
  * profiling events.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  Every call on a device shares the one array and leaves its
- * contents behind (the call clears what must start at zero itself), so calls
- * whose work overlaps on the GPU -- two streams, or two threads -- race;
- * serialise them.  The backward cannot follow this call (its state lives in
- * the shared array). */
+ * capture.  Under CUDA's lazy module loading (the default) that first call is
+ * also when the 64 MiB are reserved on the device, so make it at start-up (or
+ * set CUDA_MODULE_LOADING=EAGER to reserve them when the library loads); a
+ * lookup that fails returns GS_ERR_CUDA and is tried again by the next call.
+ * Every call on a device shares the one array and leaves its contents behind
+ * (the call clears what must start at zero itself), so calls whose work
+ * overlaps on the GPU -- two streams, or two threads -- race; serialise them.
+ * The backward cannot follow this call (its state lives in the shared array).
+ * A device-detected error (pair capacity exceeded) is read with
+ * gs_render_static_status. */
 #define GS_STATIC_SCRATCH_BYTES (64ll << 20)
 gs_status gs_render_static(const gs_gaussians *g, const gs_batch *batch, const gs_camera *cams,
                            const gs_render_config *cfg, float *out_rgb, float *out_depth, float *out_T,
                            int32_t *out_ncontrib, void *stream);
+
+/* gs_get_status for gs_render_static, whose status word lives in the static
+ * array (the caller has no workspace pointer): synchronises `stream`, returns
+ * the device status the last gs_render_static call on the current device left
+ * (GS_OK or GS_ERR_CAPACITY) in *device_status and clears it.  The paper has
+ * no counterpart.  Allocates nothing. */
+gs_status gs_render_static_status(void *stream, int32_t *device_status);
 
 /* Adjoint of gs_render for L with dL/drgb = d_rgb [V,3,H,W] and dL/ddepth =
  * d_depth [V,H,W] (device; raw depth only).  Must follow gs_render with the

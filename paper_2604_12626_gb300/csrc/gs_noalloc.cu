@@ -6,7 +6,9 @@
 // another framework's allocator, or code on a real-time path that is not
 // allowed to allocate after start-up.  They can call gs_render_static, which
 // takes no workspace and allocates nothing; it renders into the caller's
-// output buffers using the static array below.
+// output buffers using the static array below.  gs_render_static_status reads
+// (and clears) the device status word a gs_render_static call leaves in that
+// array, since the caller has no workspace pointer to pass to gs_get_status.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -22,9 +24,32 @@ constexpr size_t kStaticScratchBytes = (size_t)GS_STATIC_SCRATCH_BYTES;
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 constexpr int kMaxDevices = 64;
-std::once_flag g_once[kMaxDevices];
-void *g_scratch_ptr[kMaxDevices];
-cudaError_t g_scratch_err[kMaxDevices];
+std::mutex g_mu;
+void *g_scratch_ptr[kMaxDevices]; // device address of the array, per device; null until looked up
+
+// The array's host-side name is only a stand-in: its device address is looked
+// up with the device current, once per device.  A failed lookup is not kept
+// (the next call tries again), so a transient failure -- the module's memory
+// could not be reserved yet -- does not disable the entry point for good.
+gs_status static_scratch(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return gs::record_cuda_error(e);
+    if (dev < 0 || dev >= kMaxDevices) return GS_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError(); // not sticky: leave no error behind for later launch checks
+            return gs::record_cuda_error(e);
+        }
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return GS_OK;
+}
 
 } // namespace
 
@@ -36,17 +61,19 @@ extern "C" gs_status gs_render_static(const gs_gaussians *g, const gs_batch *bat
     gs_status st = gs_render_workspace_size(cfg, batch, &need);
     if (st != GS_OK) return st;
     if (need > kStaticScratchBytes) return GS_ERR_WORKSPACE_TOO_SMALL; // problem larger than the static scratch
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return gs::record_cuda_error(e);
-    if (dev < 0 || dev >= kMaxDevices) return GS_ERR_UNSUPPORTED;
-    // The array's host-side name is only a stand-in: its device address is
-    // looked up once per device, with that device current.
-    std::call_once(g_once[dev], [dev]() {
-        g_scratch_err[dev] = cudaGetSymbolAddress(&g_scratch_ptr[dev], g_static_scratch);
-    });
-    if (g_scratch_err[dev] != cudaSuccess) return gs::record_cuda_error(g_scratch_err[dev]);
+    void *scratch = nullptr;
+    st = static_scratch(&scratch);
+    if (st != GS_OK) return st;
     gs::ProfileSuppress no_events; // stage profiling would create CUDA events
-    return gs_render(g, batch, cams, cfg, g_scratch_ptr[dev], kStaticScratchBytes, out_rgb, out_depth, out_T,
-                     out_ncontrib, stream);
+    return gs_render(g, batch, cams, cfg, scratch, kStaticScratchBytes, out_rgb, out_depth, out_T, out_ncontrib,
+                     stream);
+}
+
+extern "C" gs_status gs_render_static_status(void *stream, int32_t *device_status)
+{
+    if (!device_status) return GS_ERR_INVALID_ARG;
+    void *scratch = nullptr;
+    gs_status st = static_scratch(&scratch);
+    if (st != GS_OK) return st;
+    return gs_get_status(scratch, kStaticScratchBytes, stream, device_status);
 }

@@ -118,9 +118,11 @@ def smi_index(local: int) -> int:
 
 
 def dist_init():
+    import torch
+
     from paper_2604_12626_gb300 import shard
 
-    return shard.init("nccl")
+    return shard.init("nccl" if torch.cuda.is_available() else "gloo")
 
 
 def barrier(ws):
@@ -162,17 +164,72 @@ def oracle_step(env_ids, seed0, budget_s=None, scale=1.0):
     return done, t_total
 
 
+def oracle_configs(seed0=0):
+    """The FP64 oracle on the other configurations, on the host cores, at 1
+    thread and at all cores (OpenMP over image row bands): forward of the
+    5k-Gaussian box at 128x128, of a 1M-Gaussian room at 640x480 and of env 0
+    of the 64-env batch at 256x256; the adjoint (1 thread) of that env; and one
+    of the 16 views of the training step (500k room + 2 posed avatars, 512x512)
+    forward + adjoint, scaled to the 16-view step."""
+    import oracle
+    from paper_2604_12626_gb300 import synth
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    out = {"cores": cores}
+
+    def t_of(fn):
+        t0 = time.perf_counter()
+        fn()
+        return time.perf_counter() - t0
+
+    def both(name, g, cam, Wc, Hc):
+        t1 = t_of(lambda: oracle.render(g, cam, Wc, Hc, nthreads=1))
+        tn = t_of(lambda: oracle.render(g, cam, Wc, Hc, nthreads=0))
+        out[name] = {"fwd_frames_per_s_1_thread": 1.0 / t1, f"fwd_frames_per_s_{cores}_cores": 1.0 / tn,
+                     "gaussians": int(g["means"].shape[0]), "width": Wc, "height": Hc}
+
+    both("box_5k_128px", synth.box_scene(5000, seed=0), synth.identity_camera(128, 128), 128, 128)
+    both("room_1M_640x480", synth.room_scene(1_000_000, seed=1), synth.room_camera(1, 640, 480), 640, 480)
+    n0 = synth.batch_sizes(1, N_MIN, N_MAX, seed0)[0]
+    g0, cam0 = synth.room_scene(n0, seed=seed0), synth.room_camera(seed0, W, H)
+    both("batch_env0_256px", g0, cam0, W, H)
+    rng = np.random.default_rng(0)
+    tb = t_of(lambda: oracle.render_backward(g0, cam0, W, H, rng.standard_normal((3, H, W)),
+                                              rng.standard_normal((H, W))))
+    out["batch_env0_256px"]["bwd_frames_per_s_1_thread"] = 1.0 / tb
+    wl = synth.training_scene(seed=0)
+    av = wl["avatars"]
+    pm, pc = oracle.lbs(av["means"], av["log_scales"], av["quats"], av["joint_ids"].astype(np.int32), av["weights"],
+                        av["avatar_of"], wl["G"].astype(np.float64))
+    room, ns, m = wl["room"], wl["room"]["means"].shape[0], av["means"].shape[0]
+    g = dict(means=np.concatenate([room["means"].astype(np.float64), pm]),
+             log_scales=np.concatenate([room["log_scales"], np.zeros((m, 3), np.float32)]),
+             quats=np.concatenate([room["quats"], np.tile(np.float32([1, 0, 0, 0]), (m, 1))]),
+             opacity_logits=np.concatenate([room["opacity_logits"], av["opacity_logits"]]),
+             sh=np.concatenate([room["sh"], av["sh"]]), cov3d=np.concatenate([np.zeros((ns, 6)), pc]),
+             use_cov=np.concatenate([np.zeros(ns, np.uint8), np.ones(m, np.uint8)]))
+    cam = wl["cams"][0]
+    tf = t_of(lambda: oracle.render(g, cam, 512, 512, nthreads=0))
+    tb = t_of(lambda: oracle.render_backward(g, cam, 512, 512, np.ones((3, 512, 512)), np.zeros((512, 512))))
+    nv = wl["cams"].shape[0]
+    out["training_16x512px"] = {"step_s_estimate": nv * (tf + tb), "view_frames_per_s": 1.0 / (tf + tb),
+                                "sample": f"view 0 of {nv}: forward on {cores} cores {tf:.2f} s + adjoint on 1 "
+                                          f"thread {tb:.2f} s, scaled to {nv} views"}
+    return out
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
     cores = os.cpu_count() or 1
     envs_per_step = 1
     for _ in range(args.warmup):
-        oracle_step([0], 0)
+        oracle_step([0], 0, scale=args.scale)
     t = 0.0
     n = 0
     for k in range(args.steps):
-        d, s = oracle_step([(k * envs_per_step + i) % N_ENVS for i in range(envs_per_step)], 0)
+        d, s = oracle_step([(k * envs_per_step + i) % N_ENVS for i in range(envs_per_step)], 0, scale=args.scale)
         n += d
         t += s
     value = n / t
@@ -366,7 +423,7 @@ def rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_pix, N, sm_count, sm_mh
     for k, f in ops.items():
         if k in ms and ms[k] > 0:
             a = f / (ms[k] * 1e-3) / 1e12
-            out[k] = {"bound": "alu", "achieved": a, "peak": alu_peak, "unit": "TFLOP/s", "frac": a / alu_peak,
+            out[k] = {"bound": "alu", "achieved": a, "peak": alu_peak, "unit": "T lane-ops/s", "frac": a / alu_peak,
                       "algorithmic": f, "ms": ms[k],
                       "peak_kind": f"derived: {sm_count} SMs x 128 FP32 lanes x {mhz:.0f} MHz"}
     for k, v in out.items():
@@ -473,6 +530,104 @@ def avatar_and_composite_rows(api, synth, torch, dev, stream, outs, hbm_peak):
             "composite": dict(hbm(comp_bytes, comp_ms), views=V, width=W, height=H),
             "mesh_layer": {"ms": mesh_ms, "views": V, "triangles_per_view": int(tri_off[-1]) // V, "width": W,
                            "height": H}}
+
+
+def _graph_ms(torch, stream, fn, k=20, warm=3):
+    """fn captured in a CUDA graph on ``stream``; mean CUDA-event time of k replays."""
+    with torch.cuda.stream(stream):
+        fn()
+    torch.cuda.synchronize()
+    gr = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gr, stream=stream):
+        fn()
+    return _event_ms(torch, stream, gr.replay, k)
+
+
+def single_view_rows(api, synth, torch, dev, stream):
+    """The single-view configurations: a 5k-Gaussian box scene at 128x128 and
+    a 1M-Gaussian room at 640x480, each forward and forward + backward in a
+    CUDA graph (FP32 SH, 16x16 tiles, batch depth 256)."""
+    rows = {}
+    for name, g, cam, Wc, Hc in (
+            ("box_5k_128px", synth.box_scene(5000, seed=0), synth.identity_camera(128, 128), 128, 128),
+            ("room_1M_640x480", synth.room_scene(1_000_000, seed=1), synth.room_camera(1, 640, 480), 640, 480)):
+        n = g["means"].shape[0]
+        G = api.Gaussians.from_numpy(g, device=dev)
+        r = api.Renderer(api.Batch(np.array([0, n])), Wc, Hc, device=dev, grad_overwrite=True)
+        ct = api.cameras_tensor(cam[None], dev)
+        out = r.alloc_outputs()
+        grads = dict(means=torch.empty((n, 3), device=dev), log_scales=torch.empty((n, 3), device=dev),
+                     quats=torch.empty((n, 4), device=dev), opacity_logits=torch.empty((n,), device=dev),
+                     sh=torch.empty((n, 16, 3), device=dev))
+        d_rgb = torch.ones((1, 3, Hc, Wc), device=dev)
+        d_dep = torch.zeros((1, Hc, Wc), device=dev)
+        fwd = _graph_ms(torch, stream, lambda: r.forward(G, ct, out=out, stream=stream))
+
+        def fb():
+            r.forward(G, ct, out=out, stream=stream)
+            r.backward(G, ct, d_rgb, d_dep, grads=grads, stream=stream)
+
+        fbm = _graph_ms(torch, stream, fb)
+        rows[name] = {"gaussians": n, "width": Wc, "height": Hc, "fwd_ms": fwd, "fwd_frames_per_s": 1e3 / fwd,
+                      "fwd_bwd_ms": fbm, "fwd_bwd_frames_per_s": 1e3 / fbm}
+    return rows
+
+
+def training_row(api, synth, torch, dev, stream):
+    """The training step: one 500k-Gaussian room + 2 avatars of 50k Gaussians
+    (24 joints), 16 views at 512x512, L1 loss (RGB and depth, mean) against a
+    target rendered from perturbed parameters, gradients of every parameter and
+    of the joint transforms (api.AvatarScene: deform, render, loss gradient,
+    backward in overwrite mode, deform backward) in one CUDA graph; FP32 and
+    FP16 SH storage."""
+    wl = synth.training_scene(seed=0)
+    T = lambda x, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(x)).to(dev, dt)  # noqa: E731
+    room, av = wl["room"], wl["avatars"]
+    n_views, Hc, Wc = wl["cams"].shape[0], 512, 512
+    cams = api.cameras_tensor(wl["cams"], dev)
+    Gj = T(wl["G"])
+    kw = dict(tile=(16, 16), batch_depth=128, pix=(2, 1), persistent=True)
+    out = {"workload": f"1 room x {room['means'].shape[0]} + {wl['G'].shape[0]} avatars x 50k Gaussians, "
+                       f"{n_views} views {Wc}x{Hc}, L1 loss vs perturbed target, fwd+bwd incl. joint gradients",
+           "tile": [16, 16], "batch_depth": 128, "pixels_per_thread": [2, 1]}
+    for shd, name in ((torch.float32, "f32_sh"), (torch.float16, "f16_sh")):
+        def scene(perturbed):
+            rm, rsh, am, ash = room["means"], room["sh"], av["means"], av["sh"]
+            if perturbed:
+                rm, rsh = rm + wl["d_room_means"], rsh + wl["d_room_sh"]
+                am, ash = am + wl["d_av_means"], ash + wl["d_av_sh"]
+            sc = dict(means=T(rm), log_scales=T(room["log_scales"]), quats=T(room["quats"]),
+                      opacity_logits=T(room["opacity_logits"]), sh=T(rsh))
+            avs = dict(means=T(am), log_scales=T(av["log_scales"]), quats=T(av["quats"]),
+                       opacity_logits=T(av["opacity_logits"]), sh=T(ash),
+                       joint_ids=T(av["joint_ids"].view(np.int16), torch.int16), weights=T(av["weights"]),
+                       avatar_of=T(av["avatar_of"], torch.int32))
+            return api.AvatarScene(sc, avs, wl["G"].shape[0], synth.N_JOINTS, Wc, Hc, n_views, sh_dtype=shd,
+                                   device=dev, **kw)
+        tgt = scene(True)
+        with torch.cuda.stream(stream):
+            t_rgb, t_dep = (x.clone() for x in tgt.forward(Gj, cams, stream=stream)[:2])
+        torch.cuda.synchronize()
+        del tgt
+        sc = scene(False)
+        d_rgb, d_dep = torch.empty_like(t_rgb), torch.empty_like(t_dep)
+        loss = torch.zeros((), device=dev)
+
+        def step():
+            rgb, dep = sc.forward(Gj, cams, stream=stream)[:2]
+            torch.sub(rgb, t_rgb, out=d_rgb)
+            torch.sub(dep, t_dep, out=d_dep)
+            torch.add(d_rgb.abs().mean(), d_dep.abs().mean(), out=loss)
+            d_rgb.sign_().mul_(1.0 / d_rgb.numel())
+            d_dep.sign_().mul_(1.0 / d_dep.numel())
+            sc.backward(Gj, cams, d_rgb, d_dep, stream=stream)
+
+        ms = _graph_ms(torch, stream, step, k=10)
+        torch.cuda.synchronize()
+        assert sc.renderer.status() == 0
+        out[name] = {"ms_per_step": ms, "view_frames_per_s": n_views / (ms * 1e-3), "loss": float(loss)}
+        del sc
+    return out
 
 
 def fused_avatar_row(api, synth, torch, dev, stream):
@@ -648,8 +803,9 @@ def run_ours(args, ws, rank, local):
     ms_fwd, _ = timed(g_fwd.replay, args.steps, args.warmup)
     assert rend.status(stream) == 0
 
-    # --- plain per-env path: one gs_render per env, FP32 SH, 16x16 tiles, B=256, no graph
-    plain_ms = None
+    # --- plain per-env path: one gs_render (+ gs_render_backward) per env, FP32
+    # SH, 16x16 tiles, B=256, no graph; gradients of each env written in place
+    plain_ms = plain_fb_ms = None
     if not args.no_plain:
         envs = []
         for e in range(n_envs):
@@ -658,16 +814,44 @@ def run_ours(args, ws, rank, local):
             envs.append(ge)
         sizes = np.diff(offs)
         big = int(np.argmax(sizes))
-        r1 = api.Renderer(api.Batch(np.array([0, sizes[big]])), W, H, device=dev)
+        r1 = api.Renderer(api.Batch(np.array([0, sizes[big]])), W, H, device=dev, grad_overwrite=True)
         outs1 = r1.alloc_outputs()
         cam_e = [cams_d[e:e + 1] for e in range(n_envs)]
+        batches = [api.Batch(np.array([0, sizes[e]])) for e in range(n_envs)]
+        nb = int(sizes[big])  # one set of gradient buffers, reused by every env (like the outputs)
+        grads1 = dict(means=torch.empty((nb, 3), device=dev), log_scales=torch.empty((nb, 3), device=dev),
+                      quats=torch.empty((nb, 4), device=dev), opacity_logits=torch.empty((nb,), device=dev),
+                      sh=torch.empty((nb, 16, 3), device=dev))
+        env_grads = [{k: v[:int(sizes[e])] for k, v in grads1.items()} for e in range(n_envs)]
 
         def plain_step():
             for e in range(n_envs):
-                r1.batch = api.Batch(np.array([0, sizes[e]]))
+                r1.batch = batches[e]
                 r1.forward(envs[e], cam_e[e], out=outs1, stream=stream)
 
+        def plain_fb_step():
+            for e in range(n_envs):
+                r1.batch = batches[e]
+                r1.forward(envs[e], cam_e[e], out=outs1, stream=stream)
+                r1.backward(envs[e], cam_e[e], d_rgb[e:e + 1], d_depth[e:e + 1], grads=env_grads[e],
+                            stream=stream)
+
         plain_ms, _ = timed(plain_step, max(2, args.steps // 2), 1)
+        plain_fb_ms, _ = timed(plain_fb_step, max(2, args.steps // 2), 1)
+        del r1, outs1, envs, grads1, env_grads
+
+    # --- the batched path with FP32 SH storage (same graph, same tile)
+    def step_fwd32():
+        rend.forward(G32, cams_d, out=outs, stream=stream)
+
+    def step_fb32():
+        rend.forward(G32, cams_d, out=outs, stream=stream)
+        rend.backward(G32, cams_d, d_rgb, d_depth, grads=grads, stream=stream)
+
+    g32_fb, g32_fwd = capture(step_fb32), capture(step_fwd32)
+    ms32_fb, _ = timed(g32_fb.replay, args.steps, args.warmup)
+    ms32_fwd, _ = timed(g32_fwd.replay, args.steps, args.warmup)
+    del g32_fb, g32_fwd
 
     # --- live per-stage timing (same workload, launched without the graph)
     api.profile_enable(True)
@@ -713,6 +897,9 @@ def run_ours(args, ws, rank, local):
     extra = avatar_and_composite_rows(api, synth, torch, dev, stream, outs, hbm_peak=peaks()[0])
     if not args.no_avatar_scene:
         extra["scene_with_avatars"] = fused_avatar_row(api, synth, torch, dev, stream)
+    if not args.no_configs:
+        extra["single_view"] = single_view_rows(api, synth, torch, dev, stream)
+        extra["training_16x512px"] = training_row(api, synth, torch, dev, stream)
 
     # --- CPU oracle on a bounded sample (rank 0, N = 1)
     cpu = None
@@ -721,6 +908,8 @@ def run_ours(args, ws, rank, local):
         cpu = {"value": n / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{n} env(s) of this batch (env 0..{n - 1}), FP64 forward (OpenMP, all cores) + "
                          f"backward (1 thread), {t:.1f} s"}
+        if not args.no_configs:
+            cpu["configs"] = oracle_configs(seed0)
 
     total_envs = n_envs * ws
     line = {
@@ -736,9 +925,16 @@ def run_ours(args, ws, rank, local):
                    "l2_policy": "inputs larger than L2 (no flush)", "parallelism": f"env-sharded x{ws}"},
         "fwd": {"value": total_envs / (ms_fwd * 1e-3), "ms_per_step": ms_fwd},
         "plain_per_env": (None if plain_ms is None else
-                          {"value": total_envs / (plain_ms * 1e-3), "ms_per_step": plain_ms,
-                           "what": "forward only: 64 gs_render calls, FP32 SH, 16x16 tiles, B=256, no graph",
-                           "batched_fwd_speedup": plain_ms / ms_fwd}),
+                          {"fwd": {"value": total_envs / (plain_ms * 1e-3), "ms_per_step": plain_ms},
+                           "fwd_bwd": {"value": total_envs / (plain_fb_ms * 1e-3), "ms_per_step": plain_fb_ms},
+                           "what": "64 single-env gs_render (+ gs_render_backward) calls, FP32 SH, 16x16 tiles, "
+                                   "B=256, no graph",
+                           "batched_fwd_speedup": plain_ms / ms_fwd, "batched_fwd_bwd_speedup": plain_fb_ms / ms_fb,
+                           "batched_f32_fwd_speedup": plain_ms / ms32_fwd,
+                           "batched_f32_fwd_bwd_speedup": plain_fb_ms / ms32_fb}),
+        "batched_f32_sh": {"fwd": {"value": total_envs / (ms32_fwd * 1e-3), "ms_per_step": ms32_fwd},
+                           "fwd_bwd": {"value": total_envs / (ms32_fb * 1e-3), "ms_per_step": ms32_fb},
+                           "what": "the headline step with SH stored FP32 (same graph, tile and launch shape)"},
         "roofline": roof,
         "roofline_per_kernel": per_kernel,
         "other_rows": extra,
@@ -771,6 +967,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-avatar-scene", action="store_true", help="skip the 32-env rooms-with-avatars forward")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the single-view and training-step rows (and their oracle timings)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--tile", default="", help="fixed tile_w,tile_h,batch_depth instead of the autotuner")
@@ -783,6 +981,15 @@ def main():
         return
     if args.warmup < 3:
         args.warmup = 3
+    from paper_2604_12626_gb300 import shard
+
+    try:
+        plan = shard.launch_plan(args.gpus)
+    except ValueError as e:
+        print(f"bench.py: {e}", file=sys.stderr)
+        sys.exit(2)
+    if plan == "spawn":  # started without a launcher: start the N ranks here
+        sys.exit(subprocess.call(shard.spawn_command(args.gpus, os.path.abspath(__file__), sys.argv[1:])))
     ws, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, ws, rank)

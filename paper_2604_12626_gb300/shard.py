@@ -10,6 +10,8 @@ on whatever backend the process group uses (NCCL between GPUs, gloo on CPU).
 from __future__ import annotations
 
 import os
+import socket
+import sys
 
 
 def world() -> tuple[int, int, int]:
@@ -28,6 +30,34 @@ def init(backend: str) -> tuple[int, int, int]:
         if not dist.is_initialized():
             dist.init_process_group(backend, rank=rank, world_size=ws)
     return ws, rank, local
+
+
+def launch_plan(n_gpus: int, environ=None) -> str:
+    """How a run asked for n_gpus ranks proceeds: "run" when this process is
+    already one of n_gpus ranks (or n_gpus is 1 and no launcher is involved),
+    "spawn" when it was started without a launcher for n_gpus > 1 (it then
+    starts the n_gpus ranks itself).  A launcher whose WORLD_SIZE differs from
+    n_gpus is an error (ValueError), so that a multi-GPU run can never
+    silently measure another number of GPUs."""
+    env = os.environ if environ is None else environ
+    if n_gpus < 1:
+        raise ValueError(f"--gpus must be >= 1, got {n_gpus}")
+    ws = env.get("WORLD_SIZE")
+    if ws is None:
+        return "run" if n_gpus == 1 else "spawn"
+    if int(ws) != n_gpus:
+        raise ValueError(f"--gpus {n_gpus} but the launcher started WORLD_SIZE={ws} ranks")
+    return "run"
+
+
+def spawn_command(n_gpus: int, script: str, argv: list) -> list:
+    """The torch.distributed.run command that starts n_gpus ranks of script
+    (one per GPU, rendezvous on 127.0.0.1 at a free port)."""
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n_gpus}",
+            "--master-addr", "127.0.0.1", "--master-port", str(port), script, *argv]
 
 
 def env_block(rank: int, envs_per_rank: int) -> range:

@@ -82,6 +82,8 @@ def test_rooflines_arithmetic(monkeypatch):
     assert per["preprocess_backward"]["algorithmic"] == R // 8 + nvis * (12 + 28 + 4 + 96 + 64 + 236)
     alu = 100 * 128 * 2000e6 / 1e12  # T lane-ops/s
     assert per["blend"]["peak"] == pytest.approx(alu)
+    assert per["blend"]["unit"] == per["blend_backward"]["unit"] == "T lane-ops/s"  # an FMA counts once
+    assert per["preprocess"]["unit"] == "GB/s"
     assert per["blend"]["achieved"] == pytest.approx(bench.OPS_PER_EVAL_FWD * 1e9 / 2e-3 / 1e12)
     assert per["blend_backward"]["achieved"] == pytest.approx(bench.OPS_PER_EVAL_BWD * 5e8 / 4e-3 / 1e12)
     assert per["blend"]["exp2"]["frac"] == pytest.approx(1e9 / 2e-3 / 1e12)

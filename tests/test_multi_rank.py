@@ -84,3 +84,49 @@ def test_shard_helpers_single_process():
     b = synth.batch_sizes(2, 100, 1000, 4)
     assert a[4:] == b
     assert np.array_equal(synth.room_scene(500, seed=5)["means"], synth.room_scene(500, seed=5)["means"])
+
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_launch_plan():
+    assert shard.launch_plan(1, {}) == "run"
+    assert shard.launch_plan(2, {}) == "spawn"
+    assert shard.launch_plan(4, {"WORLD_SIZE": "4"}) == "run"
+    with pytest.raises(ValueError, match="WORLD_SIZE=2"):
+        shard.launch_plan(8, {"WORLD_SIZE": "2"})
+    with pytest.raises(ValueError):
+        shard.launch_plan(0, {})
+    cmd = shard.spawn_command(2, "bench.py", ["--gpus", "2"])
+    assert cmd[1:3] == ["-m", "torch.distributed.run"] and "--nproc-per-node=2" in cmd
+    assert cmd[-3:] == ["bench.py", "--gpus", "2"] and "127.0.0.1" in cmd
+
+
+def _bench(args, extra_env=None):
+    import subprocess
+    import sys
+
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="", PYTHONPATH=ROOT)
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
+        env.pop(k, None)
+    env.update(extra_env or {})
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], cwd=ROOT, env=env,
+                          capture_output=True, text=True, timeout=600)
+
+
+def test_bench_gpus_2_starts_two_ranks_itself(oracle):
+    """bench.py --gpus 2 run without a launcher starts its two ranks (gloo here,
+    with no GPU); the reference arm runs on rank 0 alone and reports n_gpus 2."""
+    r = _bench(["--gpus", "2", "--impl", "reference", "--steps", "1", "--warmup", "3", "--scale", "0.002"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout  # rank 0 alone prints
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+
+
+def test_bench_refuses_a_launcher_with_another_world_size():
+    r = _bench(["--gpus", "4", "--impl", "reference", "--steps", "1"],
+               {"WORLD_SIZE": "2", "RANK": "0", "LOCAL_RANK": "0"})
+    assert r.returncode == 2
+    assert "WORLD_SIZE=2" in r.stderr

@@ -105,7 +105,7 @@ def _bind(L):
     L.or_project.restype = i64
     L.or_project.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, i32, i32, f64] + [P] * 12
     L.or_render.restype = i64
-    L.or_render.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, i32, i32, f64, P, i32, i32, i32] + [P] * 6
+    L.or_render.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, i32, i32, f64, P, i32, i32, i32] + [P] * 7
     L.or_lbs_matrices.restype = None
     L.or_lbs_matrices.argtypes = [i64, P, P, P, P, i32, P]
     L.or_render_backward.restype = i32
@@ -198,9 +198,11 @@ def project(g: dict, cam, W: int, H: int, near: float = 0.2) -> dict:
 
 def render(g: dict, cam, W: int, H: int, near: float = 0.2, bg=(0.0, 0.0, 0.0), mode: str = "gaussian",
            normalize_depth: bool = False, nthreads: int = 0) -> dict:
-    """Render one view.  Returns rgb [3,H,W], depth [H,W], T [H,W], n_contrib [H,W],
-    amb [H,W] (uint8 bit mask), last [H,W] (sorted position + 1 of the last
-    blended Gaussian) and evals (covered Gaussians examined)."""
+    """Render one view.  Returns rgb [3,H,W], depth [H,W], T [H,W], n_contrib [H,W]
+    (Gaussians blended into each pixel), n_covered [H,W] (covered Gaussians
+    examined up to and including the last blended one), amb [H,W] (uint8 bit
+    mask), last [H,W] (sorted position + 1 of the last blended Gaussian) and
+    evals (covered Gaussians examined, the stopping one included)."""
     L = _lib()
     G = _gauss(g)
     cam64 = _f64(np.asarray(cam, np.float32))
@@ -211,12 +213,13 @@ def render(g: dict, cam, W: int, H: int, near: float = 0.2, bg=(0.0, 0.0, 0.0), 
     ncon = np.zeros((H, W), np.int32)
     amb = np.zeros((H, W), np.uint8)
     last = np.zeros((H, W), np.int32)
+    ncov = np.zeros((H, W), np.int32)
     ev = L.or_render(G["n"], _p(G["means"]), _p(G["log_scales"]), _p(G["quats"]), _p(G["ologits"]), _p(G["sh"]),
                      _p(G["cov3d"]), _p(G["use_cov"]), _p(G["inexact"]), _p(G["dirmat"]), _p(cam64), W, H, near,
                      _p(bg64),
                      0 if mode == "pixel" else 1, 1 if normalize_depth else 0, nthreads,
-                     _p(rgb), _p(depth), _p(T), _p(ncon), _p(amb), _p(last))
-    return dict(rgb=rgb, depth=depth, T=T, n_contrib=ncon, amb=amb, last=last, evals=int(ev))
+                     _p(rgb), _p(depth), _p(T), _p(ncon), _p(amb), _p(last), _p(ncov))
+    return dict(rgb=rgb, depth=depth, T=T, n_contrib=ncon, n_covered=ncov, amb=amb, last=last, evals=int(ev))
 
 
 def render_backward(g: dict, cam, W: int, H: int, d_rgb, d_depth, near: float = 0.2, bg=(0.0, 0.0, 0.0),

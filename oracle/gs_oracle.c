@@ -26,7 +26,10 @@
  *   order       per pixel, covered Gaussians by (depth key, index);
  *   blend       alpha = min(0.99, opacity exp(power)), skip alpha < 1/255,
  *               stop before blending when T (1-alpha) < 1e-4;
- *               C += c alpha T, D += z alpha T, T *= (1 - alpha).
+ *               C += c alpha T, D += z alpha T, T *= (1 - alpha);
+ *   counts      n_contrib = the Gaussians blended into the pixel; n_covered =
+ *               the covered Gaussians examined up to and including the last
+ *               blended one (the length of the adjoint's walk).
  * Two decisions are taken in FP32 so that both sides take them in the same
  * precision: the depth key that orders and near-culls the Gaussians is
  *   zkey = fl(fl(fl(W20 d0) + fl(W21 d1)) + fl(W22 d2)),  d_i = fl(mu_i - C_i)
@@ -434,7 +437,7 @@ typedef struct {
 
 typedef struct {
     double T, C[3], D, relT;
-    int32_t ncov, n, last, done;
+    int32_t ncov, n, ncov_last, last, done;
     float prev_zkey;
     int32_t have_prev, prev_inexact;
     uint8_t amb;
@@ -516,7 +519,8 @@ static void blend_step(pix_t *s, const cand_t *g, int i, int j, int32_t pos)
     s->D += g->z * w;
     s->T = Tn;
     s->relT = relTn;
-    s->n = s->ncov;
+    s->n += 1;               /* n_contrib: Gaussians blended into this pixel */
+    s->ncov_last = s->ncov;  /* covered Gaussians up to and including this one */
     s->last = pos + 1;
 }
 
@@ -568,7 +572,7 @@ static int64_t build_candidates(int64_t n, const double *means, const double *ls
 }
 
 static void finish_pixel(const pix_t *s, const double *bg, int flags, int64_t p, int64_t HW, double *rgb, double *depth,
-                         double *Tout, int32_t *nout, uint8_t *amb, int32_t *last)
+                         double *Tout, int32_t *nout, uint8_t *amb, int32_t *last, int32_t *ncov)
 {
     for (int ch = 0; ch < 3; ++ch) rgb[ch * HW + p] = s->C[ch] + s->T * bg[ch];
     double D = s->D;
@@ -578,6 +582,7 @@ static void finish_pixel(const pix_t *s, const double *bg, int flags, int64_t p,
     nout[p] = s->n;
     if (amb) amb[p] = s->amb;
     if (last) last[p] = s->last;
+    if (ncov) ncov[p] = s->ncov_last;
 }
 
 static int num_threads(int32_t req)
@@ -626,7 +631,8 @@ int64_t or_render(int64_t n, const double *means, const double *log_scales, cons
                   const double *sh, const double *cov3d, const uint8_t *use_cov, const uint8_t *inexact,
                   const double *dirmat, const double *cam,
                   int32_t W, int32_t H, double near_plane, const double *bg, int32_t mode, int32_t flags, int32_t nthreads,
-                  double *out_rgb, double *out_depth, double *out_T, int32_t *out_n, uint8_t *out_amb, int32_t *out_last)
+                  double *out_rgb, double *out_depth, double *out_T, int32_t *out_n, uint8_t *out_amb, int32_t *out_last,
+                  int32_t *out_ncov)
 {
     cam_t k;
     load_cam(cam, &k);
@@ -649,7 +655,7 @@ int64_t or_render(int64_t n, const double *means, const double *log_scales, cons
         evals = walk_gaussian_major(c, m, W, H, st, nt);
     }
     for (int64_t p = 0; p < HW; ++p)
-        finish_pixel(st + p, bg, flags, p, HW, out_rgb, out_depth, out_T, out_n, out_amb, out_last);
+        finish_pixel(st + p, bg, flags, p, HW, out_rgb, out_depth, out_T, out_n, out_amb, out_last, out_ncov);
     free(st);
     free(c);
     return evals;

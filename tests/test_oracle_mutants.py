@@ -23,6 +23,10 @@ MUTANTS = [
      pins.test_elongated_gaussian_square_footprint_closed_form),
     ("stop tested on T before the step", "if (Tn < T_STOP) {", "if (s->T < T_STOP) {",
      pins.test_stop_rule_never_blends_below_threshold),
+    ("n_contrib counts covered instead of blended", "s->n += 1;", "s->n = s->ncov;",
+     pins.test_contributor_counts_closed_form),
+    ("n_covered stops at the first blended", "s->ncov_last = s->ncov;", "if (!s->ncov_last) s->ncov_last = s->ncov;",
+     pins.test_contributor_counts_closed_form),
     ("depth weighted by alpha only", "s->D += g->z * w;", "s->D += g->z * alpha;", pins.test_transmittance_invariant),
     ("Jacobian sign", "J[0] = k->fx / pz; J[1] = 0.0; J[2] = -k->fx * tx / pz;",
      "J[0] = k->fx / pz; J[1] = 0.0; J[2] = k->fx * tx / pz;", pins.test_ewa_covariance_is_linearised_pinhole),

@@ -191,6 +191,47 @@ def test_evaluation_count_closed_form(oracle):
     assert out["evals"] == total
 
 
+def test_contributor_counts_closed_form(oracle):
+    # isotropic splats on the axis, alternating faint-and-wide and opaque-and-small:
+    # per pixel, n_contrib counts the splats blended (covered, alpha >= 1/255,
+    # not stopped) and n_covered the covered splats examined up to and including
+    # the last blended one; a faint splat whose square covers a pixel where its
+    # alpha is below 1/255 is counted by the second only
+    W, f = 21, 10.0
+    spec = [(2.0, -1.2, -3.5), (2.4, -2.4, 2.0), (2.8, -1.0, -4.0), (3.2, -2.2, 1.5), (3.6, -1.6, 3.0)]
+    z = np.array([s[0] for s in spec], np.float32)
+    g = dict(means=np.stack([np.zeros(5), np.zeros(5), z], 1).astype(np.float32),
+             log_scales=np.array([[s[1]] * 3 for s in spec], np.float32),
+             quats=np.tile(np.float32([1, 0, 0, 0]), (5, 1)),
+             opacity_logits=np.array([s[2] for s in spec], np.float32), sh=np.zeros((5, 16, 3), np.float32))
+    out = oracle.render(g, cam_f(W, W, f), W, W, mode="pixel")
+    c = (W - 1) / 2
+    s2 = (f * np.exp(g["log_scales"][:, 0].astype(np.float64)) / z.astype(np.float64)) ** 2 + 0.3
+    r = np.ceil(3.0 * np.sqrt(s2 + math.sqrt(0.1)))
+    o = 1.0 / (1.0 + np.exp(-g["opacity_logits"].astype(np.float64)))
+    n_ref = np.zeros((W, W), np.int32)
+    ncov_ref = np.zeros((W, W), np.int32)
+    for y in range(W):
+        for x in range(W):
+            T, n, ncov, last_cov = 1.0, 0, 0, 0
+            for k in range(5):
+                if max(abs(x - c), abs(y - c)) > r[k]:
+                    continue
+                ncov += 1
+                a = min(0.99, o[k] * math.exp(-0.5 * ((x - c) ** 2 + (y - c) ** 2) / s2[k]))
+                if a < 1.0 / 255.0:
+                    continue
+                if T * (1.0 - a) < 1e-4:
+                    break
+                T *= 1.0 - a
+                n += 1
+                last_cov = ncov
+            n_ref[y, x], ncov_ref[y, x] = n, last_cov
+    assert np.any(ncov_ref > n_ref)  # some covered splat is skipped before a blended one
+    np.testing.assert_array_equal(out["n_contrib"], n_ref)
+    np.testing.assert_array_equal(out["n_covered"], ncov_ref)
+
+
 # ---------------------------------------------------------------------------
 # camera pose: moving the camera and the scene together changes nothing
 # ---------------------------------------------------------------------------

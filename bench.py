@@ -882,10 +882,13 @@ def run_ours(args, ws, rank, local):
     d2h = (rgb_host.numel() + depth_host.numel()) * 4
 
     # --- exact work counts for the blend rooflines (outside the timed region)
+    # (the counting forward lists every Gaussian by its square footprint, so
+    # the counts follow the definition whatever tiles the fast path skips)
     with torch.cuda.stream(stream):
         n_eval_fwd = rend.count_evaluations(G16, cams_d, out=outs, stream=stream)
+        n_eval_bwd = rend.stats(stream)["n_covered"]  # what the adjoint walks by the definition
     torch.cuda.synchronize()
-    n_eval_bwd = int(outs[3].sum().item())  # sum of n_contrib: what the backward walks
+    n_blended = int(outs[3].sum().item())  # sum of n_contrib: Gaussians blended into the pixels
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     e_rate = exp2_rate(api, torch, dev, stream, sm_count)
     roof, per_kernel = rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_envs * W * H, N, sm_count,
@@ -951,7 +954,7 @@ def run_ours(args, ws, rank, local):
         "stats": {"records": stats["n_records"], "visible": stats["n_visible"],
                   "f_v": stats["n_visible"] / max(stats["n_records"], 1), "pairs": stats["n_pairs"],
                   "pairs_per_visible": stats["n_pairs"] / max(stats["n_visible"], 1), "max_bin": stats["max_bin"],
-                  "evaluations_fwd": n_eval_fwd, "evaluations_bwd": n_eval_bwd, "gen_s": t_gen},
+                  "evaluations_fwd": n_eval_fwd, "evaluations_bwd": n_eval_bwd, "blended": n_blended, "gen_s": t_gen},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -64,7 +64,9 @@ typedef int32_t gs_status;
 #define GS_FLAG_GRAD_OVERWRITE 4  /* gs_render_backward writes every gradient row (zeros where a
                                      Gaussian is seen by no view) instead of adding to it */
 #define GS_FLAG_COUNT_EVALS 8     /* the forward also counts blend evaluations into
-                                     gs_stats.n_evaluations (one atomic per warp and tile) */
+                                     gs_stats.n_evaluations and n_covered (one atomic per warp
+                                     and tile) and lists every Gaussian for the tiles its square
+                                     footprint touches (the same images, slower) */
 #define GS_FLAG_AVATAR_CANONICAL_SH 16 /* gs_render_avatars: evaluate an avatar Gaussian's SH at
                                      A3^-1 (mu' - C) normalised, the view direction in its
                                      canonical frame (A3: linear part of its skinning matrix);
@@ -128,7 +130,9 @@ typedef struct {
     int32_t reserved;
     int64_t n_evaluations; /* with GS_FLAG_COUNT_EVALS: sum over pixels of the covered Gaussians
                               examined in depth order up to and including the one that stops the
-                              pixel (Sec. 3.1 blending rule); else 0 */
+                              pixel (Sec. 3.2 blending rule); else 0 */
+    int64_t n_covered;     /* with GS_FLAG_COUNT_EVALS: sum over pixels of the covered Gaussians up
+                              to and including the last one blended (the adjoint's walk); else 0 */
 } gs_stats;
 
 /* Canonical avatar Gaussians for LBS (device). */
@@ -153,13 +157,15 @@ gs_status gs_render_workspace_size(const gs_render_config *cfg, const gs_batch *
  * of (tile, depth key) pairs, per-tile sort by (FP32 view depth, index), tile
  * ranges, front-to-back blending (alpha = min(0.99, o exp(power)), skip alpha <
  * 1/255, stop before T < 1e-4).  A Gaussian covers pixel (i, j) iff
- * |i - u| <= r and |j - v| <= r, r = ceil(3 sqrt(lambda_max)).
+ * |i - u| <= r and |j - v| <= r, r = ceil(3 sqrt(lambda_max)).  A Gaussian is
+ * listed only for the tiles where its alpha can reach 1/255 (a window inside
+ * the square, with margins for FP32 rounding), which changes no output.
  *   cams          device [V] gs_camera
  *   out_rgb       device [V,3,H,W]  C + T bg
  *   out_depth     device [V,H,W]    sum z alpha T (raw), or normalised (flag)
  *   out_T         device [V,H,W]    final transmittance
- *   out_ncontrib  device [V,H,W] int32: 1 + position of the last blended
- *                 Gaussian among the Gaussians covering that pixel
+ *   out_ncontrib  device [V,H,W] int32: the number of Gaussians blended into
+ *                 that pixel
  * The workspace keeps what the backward needs.  A tile whose CTA
  * ((tile_w / pix_x) x (tile_h / pix_y) threads) exceeds what the blend kernels'
  * registers allow is rejected with GS_ERR_UNSUPPORTED (e.g. 32x32 at 1x1). */
@@ -336,8 +342,11 @@ gs_status gs_autotune(const gs_gaussians *g, const gs_batch *batch, const gs_cam
 /* Device addresses of the workspace sections a gs_render call leaves behind,
  * for inspection (tests, statistics).  Host-only arithmetic on `workspace`;
  * nothing is read or written.  Layouts:
- *   records    [R][12] float: (uc, vc, z, r, A, B, C, opacity, red, green, blue, 0)
- *              where uc = u - cx, vc = v - cy, z the FP32 depth key, r the radius;
+ *   records    [R][12] float: (uc, vc, hx, hy, A, B, C, opacity, red, green, blue, z)
+ *              where uc = u - cx, vc = v - cy, (hx, hy) the half widths of the pixel
+ *              window (pixels with |i - cx - uc| <= hx and |j - cy - vc| <= hy: the
+ *              square footprint r, narrowed to where alpha can reach 1/255; r itself
+ *              under GS_FLAG_COUNT_EVALS), z the FP32 depth key;
  *              R = n_records, record of (view v, local index k) at view_rec_off[v] + k
  *   vis        [ceil(R/32)] uint32 visibility bits
  *   keys       [pair_capacity] uint64 (depth bits << 32 | record), sorted per bin;

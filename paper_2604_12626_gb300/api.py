@@ -56,7 +56,7 @@ class GsRenderConfig(ctypes.Structure):
 class GsStats(ctypes.Structure):
     _fields_ = [("n_records", ctypes.c_int64), ("n_visible", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
                 ("max_bin", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("n_evaluations", ctypes.c_int64)]
+                ("n_evaluations", ctypes.c_int64), ("n_covered", ctypes.c_int64)]
 
 
 class GsWsSections(ctypes.Structure):
@@ -335,12 +335,14 @@ class Renderer:
         _check(_lib.gs_render_stats(_ptr(self.workspace), self.ws_bytes, _stream(stream), ctypes.byref(s)),
                "gs_render_stats")
         return dict(n_records=s.n_records, n_visible=s.n_visible, n_pairs=s.n_pairs, max_bin=s.max_bin,
-                    status=s.status, n_evaluations=s.n_evaluations)
+                    status=s.status, n_evaluations=s.n_evaluations, n_covered=s.n_covered)
 
     def count_evaluations(self, g: Gaussians, cams: torch.Tensor, out=None, stream=None) -> int:
         """Runs one forward with GS_FLAG_COUNT_EVALS and returns the blend
         evaluations (per pixel, the covered Gaussians examined up to and
-        including the one that stops it, summed over all views)."""
+        including the one that stops it, summed over all views); the stats
+        then also hold n_covered (per pixel, the covered Gaussians up to and
+        including the last blended one, summed)."""
         prev = self.cfg.flags
         self.cfg.flags = prev | FLAG_COUNT_EVALS
         try:

@@ -348,7 +348,8 @@ gs_status enqueue_forward(const gs_gaussians *g, const gs_batch *b, const gs_cam
     const bool persistent = (p.flags & GS_FLAG_PERSISTENT) != 0;
     {
         Stage st6(6, s);
-        launch_blend(cams, w, rgb, depth, T, ncontrib, p.n_bins, p.px, p.py, p.threads, p.B, persistent, sms, s);
+        launch_blend(cams, w, rgb, depth, T, ncontrib, p.n_bins, p.px, p.py, p.threads, p.B, persistent,
+                     (p.flags & GS_FLAG_COUNT_EVALS) != 0, sms, s);
     }
     return check_launch();
 }
@@ -672,6 +673,7 @@ gs_status gs_render_stats(const void *workspace, size_t workspace_bytes, void *s
     out->status = h.status;
     out->reserved = 0;
     out->n_evaluations = (t.flags & GS_FLAG_COUNT_EVALS) ? (int64_t)h.n_evals : 0;
+    out->n_covered = (t.flags & GS_FLAG_COUNT_EVALS) ? (int64_t)h.n_cov : 0;
     return GS_OK;
 }
 

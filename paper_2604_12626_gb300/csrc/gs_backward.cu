@@ -273,8 +273,8 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
                     for (int p = 0; p < NP; ++p) {
                         ex[u][p] = __expf(pw[p]);
                         ar[u][p] = __fmul_rn(q.w, ex[u][p]); // = raw_alpha(q.w, power)
-                        ok[u][p] = k >= 0 && (uint32_t)(lo + k) < last[p] &&
-                                   fmaxf(fabsf(dxs[u][p]), fabsf(dys[u][p])) <= a.w && pw[p] <= 0.0f &&
+                        ok[u][p] = k >= 0 && (uint32_t)(lo + k) < last[p] && fabsf(dxs[u][p]) <= a.z &&
+                                   fabsf(dys[u][p]) <= a.w && pw[p] <= 0.0f &&
                                    fminf(kAlphaMax, ar[u][p]) >= kAlphaMin;
                         if (!ok[u][p]) ex[u][p] = 0.f; // finite where a zero weight multiplies it
                     }
@@ -290,11 +290,10 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
 #pragma unroll
                     for (int u = 0; u < kGroup; ++u) {
                         const int ks = kk[u] < 0 ? kk[0] : kk[u];
-                        const float4 a = s0[ks];
                         const float4 q = s1[ks];
                         const float4 c = s2[ks];
                         const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y),
-                                     cz = make_float2(c.z, c.z), az = make_float2(a.z, a.z);
+                                     cz = make_float2(c.z, c.z), az = make_float2(c.w, c.w);
                         const float2 qx = make_float2(q.x, q.x), qy = make_float2(q.y, q.y);
 #pragma unroll
                         for (int b = 0; b < PY; ++b) {
@@ -351,7 +350,6 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
 #pragma unroll
                 for (int u = 0; u < kGroup; ++u) {
                     const int ks = kk[u] < 0 ? kk[0] : kk[u];
-                    const float4 a = s0[ks];
                     const float4 q = s1[ks];
                     const float4 c = s2[ks];
 #pragma unroll
@@ -369,11 +367,11 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
                             gu[8] += wgt * dC2[p];
                             gu[9] += wgt * dD[p];
                             const float dal = dC0[p] * (c.x * Ti - S0[p] * iom) + dC1[p] * (c.y * Ti - S1[p] * iom) +
-                                              dC2[p] * (c.z * Ti - S2[p] * iom) + dD[p] * (a.z * Ti - SD[p] * iom);
+                                              dC2[p] * (c.z * Ti - S2[p] * iom) + dD[p] * (c.w * Ti - SD[p] * iom);
                             S0[p] += c.x * wgt;
                             S1[p] += c.y * wgt;
                             S2[p] += c.z * wgt;
-                            SD[p] += a.z * wgt;
+                            SD[p] += c.w * wgt;
                             T[p] = Ti;
                             if (ar[u][p] < kAlphaMax) {
                                 const float dx = dxs[u][p], dy = dys[u][p];

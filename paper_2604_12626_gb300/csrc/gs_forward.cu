@@ -115,11 +115,12 @@ __device__ __forceinline__ void chunk_setup(const Table *tb, int cta, Chunk &c)
 // One visible (view, Gaussian) waiting for its colour, record and bin counts.
 struct QEntry {
     uint32_t rec, g;
-    float uc, vc, zk, r, A, B, C, d0, d1, d2;
+    float uc, vc, zk, hx, hy, A, B, C, op, d0, d1, d2;
     uint16_t x0, x1, y0, y1;
     uint16_t v, k;
-    uint32_t pad;
+    uint32_t pad[3];
 };
+static_assert(sizeof(QEntry) % 16 == 0, "queue entries are copied as 16-byte vectors");
 
 // Phase 2, one entry per lane of a warp: colour, record, visibility bit and
 // bin counts of a queued visible (view, Gaussian).
@@ -133,12 +134,12 @@ __device__ __forceinline__ void finish_entry(const QEntry &en, bool active, uint
         float idn;
         const float3 dir = view_dir(en.d0, en.d1, en.d2, idn);
         const float3 col = sh_colour<SHT>(gin.sh, en.g, dir.x, dir.y, dir.z);
-        const float op = 1.0f / (1.0f + expf(-__ldg(gin.ologits + en.g)));
+        const float op = en.op;
         const int bx0 = en.x0 / tw, bx1 = en.x1 / tw, by0 = en.y0 / th, by1 = en.y1 / th;
         float4 *dst = w.rec + 3 * (size_t)en.rec;
-        dst[0] = make_float4(en.uc, en.vc, en.zk, en.r);
+        dst[0] = make_float4(en.uc, en.vc, en.hx, en.hy);
         dst[1] = make_float4(en.A, en.B, en.C, op);
-        dst[2] = make_float4(col.x, col.y, col.z, __uint_as_float(pack_rect(bx0, by0, bx1 - bx0 + 1, by1 - by0 + 1)));
+        dst[2] = make_float4(col.x, col.y, col.z, en.zk);
         // the record's gradient row starts at zero for the backward, which
         // accumulates into its first 10 floats; beside them the opacity (the
         // backward would otherwise gather the logit) and which colour channels
@@ -208,6 +209,7 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
     __syncthreads();
     const int W = tb->W, H = tb->H;
     const float near_plane = tb->near_plane;
+    const bool count_evals = (tb->flags & GS_FLAG_COUNT_EVALS) != 0;
     const int nwarps = blockDim.x >> 5;
     const int64_t env_base = tb->env_off[c.e0];
     const bool env_cov = gin.cov3d != nullptr;
@@ -286,14 +288,22 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
                     Proj pj;
                     if (project_ewa(mx, my, mz, zk, S, cam, W, H, pj)) {
                         const float r = radius_px(pj);
+                        const float idet = 1.0f / pj.det;
+                        const float cA = pj.c * idet, cB = -pj.b * idet, cC = pj.a * idet;
+                        const float op = 1.0f / (1.0f + expf(-__ldg(gin.ologits + g)));
+                        // the pixel window: the square footprint narrowed to where
+                        // alpha can reach 1/255 (the square alone when evaluations
+                        // are counted, so that the count follows the definition)
+                        float hx = r, hy = r;
+                        if (!count_evals) alpha_window(op, cA, cB, cC, r, hx, hy);
                         int x0, x1, y0, y1;
-                        if (pixel_range(pj.uc, r, cam.cx, W, x0, x1) && pixel_range(pj.vc, r, cam.cy, H, y0, y1)) {
+                        if (hx >= 0.0f && pixel_range(pj.uc, hx, cam.cx, W, x0, x1) &&
+                            pixel_range(pj.vc, hy, cam.cy, H, y0, y1)) {
                             vis = true;
-                            const float idet = 1.0f / pj.det;
                             en.rec = (uint32_t)((cam_smem ? s_roff[k] : tb->view_rec_off[v]) + local);
                             en.g = (uint32_t)g;
-                            en.uc = pj.uc; en.vc = pj.vc; en.zk = zk; en.r = r;
-                            en.A = pj.c * idet; en.B = -pj.b * idet; en.C = pj.a * idet;
+                            en.uc = pj.uc; en.vc = pj.vc; en.zk = zk; en.hx = hx; en.hy = hy; en.op = op;
+                            en.A = cA; en.B = cB; en.C = cC;
                             en.d0 = pj.d0; en.d1 = pj.d1; en.d2 = pj.d2;
                             if (FUSED && (tb->flags & GS_FLAG_AVATAR_CANONICAL_SH) && g >= cov_begin)
                                 canonical_direction(gin, tb->env_av_base[c.e0] + (g - cov_begin), en.d0, en.d1,
@@ -602,22 +612,16 @@ __global__ void __launch_bounds__(256) scatter_kernel(const gs_camera *__restric
             uint32_t rec = 0, zb = 0, tx0 = 0, ty0 = 0, ntx = 0, cnt = 0;
             if (i < n) {
                 rec = list[i];
+                // the tiles of the record's pixel window, from the same FP32 values
+                // the preprocess counted them with
                 const float4 ra = w.rec[3 * (size_t)rec];
-                zb = __float_as_uint(ra.z);
-                const uint32_t pr = __float_as_uint(w.rec[3 * (size_t)rec + 2].w);
-                if (pr != 0xffffffffu) {
-                    tx0 = pr & 2047u;
-                    ty0 = (pr >> 11) & 2047u;
-                    ntx = ((pr >> 22) & 31u) + 1;
-                    cnt = ntx * (((pr >> 27) & 31u) + 1);
-                } else {
-                    int x0, x1, y0, y1;
-                    if (pixel_range(ra.x, ra.w, cam.cx, W, x0, x1) && pixel_range(ra.y, ra.w, cam.cy, H, y0, y1)) {
-                        tx0 = x0 / tw;
-                        ty0 = y0 / th;
-                        ntx = x1 / tw - tx0 + 1;
-                        cnt = ntx * (y1 / th - ty0 + 1);
-                    }
+                zb = __float_as_uint(w.rec[3 * (size_t)rec + 2].w);
+                int x0, x1, y0, y1;
+                if (pixel_range(ra.x, ra.z, cam.cx, W, x0, x1) && pixel_range(ra.y, ra.w, cam.cy, H, y0, y1)) {
+                    tx0 = x0 / tw;
+                    ty0 = y0 / th;
+                    ntx = x1 / tw - tx0 + 1;
+                    cnt = ntx * (y1 / th - ty0 + 1);
                 }
             }
             uint32_t incl = cnt;
@@ -679,7 +683,9 @@ struct OutPtrs {
 constexpr int kMaxPer = 4; // records per thread and batch (B <= 4 x threads)
 constexpr int kUnroll = 8; // Gaussians evaluated together in the blend loop
 
-template <int PX, int PY>
+// COUNT (GS_FLAG_COUNT_EVALS): also count per pixel the covered Gaussians
+// examined (the evaluations) and those up to the last blended one.
+template <int PX, int PY, bool COUNT>
 __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, const OutPtrs &o, int bin, int heavy,
                                           float4 *sm)
 {
@@ -742,13 +748,13 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
         }
     };
     float T[NP], C0[NP], C1[NP], C2[NP], D[NP];
-    int32_t ncov[NP], ncon[NP];
+    int32_t ncov[NP], ncovl[NP], ncon[NP]; // ncov, ncovl: only with COUNT
     uint32_t last[NP];
     bool dn[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         T[p] = 1.0f; C0[p] = C1[p] = C2[p] = D[p] = 0.0f;
-        ncov[p] = ncon[p] = 0;
+        ncov[p] = ncovl[p] = ncon[p] = 0;
         last[p] = 0;
         dn[p] = !(i0 + p % PX < W && j0 + p / PX < H);
     }
@@ -785,6 +791,7 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
         // the warp leaves once all its lanes have stopped.  kUnroll Gaussians at a
         // time: their falloff and alpha (independent of T) first, for ILP, then
         // the front-to-back updates in order.
+#pragma unroll 1
         for (int k0 = 0; k0 < cnt; k0 += kUnroll) {
             if (__all_sync(0xffffffffu, tdone)) {
                 if (k0 & 31) flag_window((uint32_t)b * B + (uint32_t)(k0 & ~31), k0 & 31);
@@ -810,7 +817,7 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
 #pragma unroll
                             for (int h = 0; h < 2; ++h) {
                                 const int p = 2 * b + h;
-                                cv[u][p] = (k0 + u < cnt) && fmaxf(fabsf(dxs[h]), fabsf(dy)) <= a.w;
+                                cv[u][p] = (k0 + u < cnt) && fabsf(dxs[h]) <= a.z && fabsf(dy) <= a.w;
                                 al[u][p] = fminf(kAlphaMax, ars[h]);
                                 ok[u][p] = cv[u][p] && pws[h] <= 0.0f && al[u][p] >= kAlphaMin;
                             }
@@ -819,7 +826,7 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
 #pragma unroll
                         for (int p = 0; p < NP; ++p) {
                             const float dx = __fsub_rn(a.x, pxc[p % PX]), dy = __fsub_rn(a.y, pyc[p / PX]);
-                            cv[u][p] = (k0 + u < cnt) && fmaxf(fabsf(dx), fabsf(dy)) <= a.w;
+                            cv[u][p] = (k0 + u < cnt) && fabsf(dx) <= a.z && fabsf(dy) <= a.w;
                             const float power = gauss_power(q.x, q.y, q.z, dx, dy);
                             al[u][p] = fminf(kAlphaMax, raw_alpha(q.w, power));
                             ok[u][p] = cv[u][p] && power <= 0.0f && al[u][p] >= kAlphaMin;
@@ -829,7 +836,7 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) {
                     const float4 c = s2[k0 + u];
-                    const float z = s0[k0 + u].z;
+                    const float z = c.w;
                     bool blu = false;
                     if constexpr (PX == 2) {
                         // the two pixels of a row updated as packed pairs, branch-free: a
@@ -840,8 +847,10 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
                         for (int r = 0; r < PY; ++r) {
                             const int p0 = 2 * r, p1 = 2 * r + 1;
                             const bool a0 = !dn[p0] && cv[u][p0], a1 = !dn[p1] && cv[u][p1];
-                            ncov[p0] += a0;
-                            ncov[p1] += a1;
+                            if constexpr (COUNT) {
+                                ncov[p0] += a0;
+                                ncov[p1] += a1;
+                            }
                             const bool k0k = a0 && ok[u][p0], k1k = a1 && ok[u][p1];
                             const float2 T2 = make_float2(T[p0], T[p1]);
                             const float2 om = __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-al[u][p0], -al[u][p1]));
@@ -863,8 +872,12 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
                             D[p0] = dd.x; D[p1] = dd.y;
                             T[p0] = bl0 ? Tn.x : T[p0];
                             T[p1] = bl1 ? Tn.y : T[p1];
-                            ncon[p0] = bl0 ? ncov[p0] : ncon[p0];
-                            ncon[p1] = bl1 ? ncov[p1] : ncon[p1];
+                            ncon[p0] += bl0;
+                            ncon[p1] += bl1;
+                            if constexpr (COUNT) {
+                                ncovl[p0] = bl0 ? ncov[p0] : ncovl[p0];
+                                ncovl[p1] = bl1 ? ncov[p1] : ncovl[p1];
+                            }
                             last[p0] = bl0 ? pos : last[p0];
                             last[p1] = bl1 ? pos : last[p1];
                         }
@@ -872,7 +885,7 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
 #pragma unroll
                         for (int p = 0; p < NP; ++p) {
                             if (!dn[p] && cv[u][p]) {
-                                ++ncov[p];
+                                if constexpr (COUNT) ++ncov[p];
                                 if (ok[u][p]) {
                                     // explicit roundings: the packed pair path above does the same
                                     const float alpha = al[u][p];
@@ -886,7 +899,8 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
                                         C2[p] = __fmaf_rn(c.z, wgt, C2[p]);
                                         D[p] = __fmaf_rn(z, wgt, D[p]);
                                         T[p] = Tn;
-                                        ncon[p] = ncov[p];
+                                        ++ncon[p];
+                                        if constexpr (COUNT) ncovl[p] = ncov[p];
                                         last[p] = (uint32_t)b * B + k0 + u + 1;
                                         blu = true;
                                     }
@@ -908,13 +922,22 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
         __syncthreads();
     }
     cp_async_wait<0>();
-    if (tb->flags & GS_FLAG_COUNT_EVALS) {
-        unsigned long long ev = 0;
+    if constexpr (COUNT) {
+        unsigned long long ev = 0, el = 0;
 #pragma unroll
-        for (int p = 0; p < NP; ++p) ev += (uint32_t)ncov[p];
+        for (int p = 0; p < NP; ++p) {
+            ev += (uint32_t)ncov[p];
+            el += (uint32_t)ncovl[p];
+        }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, off);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&w.hdr->n_evals, ev);
+        for (int off = 16; off > 0; off >>= 1) {
+            ev += __shfl_xor_sync(0xffffffffu, ev, off);
+            el += __shfl_xor_sync(0xffffffffu, el, off);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&w.hdr->n_evals, ev);
+            atomicAdd(&w.hdr->n_cov, el);
+        }
     }
     const size_t HW = (size_t)W * H;
 #pragma unroll
@@ -949,16 +972,16 @@ __device__ __forceinline__ void clear_batch_buffers(float4 *sm, int B)
     __syncthreads();
 }
 
-template <int PX, int PY>
-__global__ void blend_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
+template <int PX, int PY, bool COUNT>
+__device__ __forceinline__ void blend_one(const gs_camera *cams, const Ws &w, const OutPtrs &o)
 {
     extern __shared__ float4 smem_f4[];
     clear_batch_buffers(smem_f4, w.tb->batch_depth);
-    blend_tile<PX, PY>(w, cams, o, blockIdx.x, w.heavy_of[blockIdx.x], smem_f4);
+    blend_tile<PX, PY, COUNT>(w, cams, o, blockIdx.x, w.heavy_of[blockIdx.x], smem_f4);
 }
 
-template <int PX, int PY>
-__global__ void blend_persistent_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
+template <int PX, int PY, bool COUNT>
+__device__ __forceinline__ void blend_persistent(const gs_camera *cams, const Ws &w, const OutPtrs &o)
 {
     extern __shared__ float4 smem_f4[];
     __shared__ uint32_t item;
@@ -970,9 +993,47 @@ __global__ void blend_persistent_kernel(const gs_camera *__restrict__ cams, Ws w
         __syncthreads();
         if (item >= n_items) break;
         const int bin = bin_of_item(w, item);
-        if (bin >= 0) blend_tile<PX, PY>(w, cams, o, bin, item < w.hdr->n_heavy ? (int)item : -1, smem_f4);
+        if (bin >= 0) blend_tile<PX, PY, COUNT>(w, cams, o, bin, item < w.hdr->n_heavy ? (int)item : -1, smem_f4);
     }
 }
+
+template <int PX, int PY, bool COUNT>
+__global__ void blend_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
+{
+    blend_one<PX, PY, COUNT>(cams, w, o);
+}
+
+template <int PX, int PY, bool COUNT>
+__global__ void blend_persistent_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
+{
+    blend_persistent<PX, PY, COUNT>(cams, w, o);
+}
+
+// 2 x 1 pixels per thread with a register budget of 88 (23 warps per SM); left
+// to itself the compiler takes 110 for the persistent variant (18 warps).
+constexpr int kBlend21Regs = 88;
+template <bool COUNT>
+__global__ void __maxnreg__(kBlend21Regs) blend21_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
+{
+    blend_one<2, 1, COUNT>(cams, w, o);
+}
+
+template <bool COUNT>
+__global__ void __maxnreg__(kBlend21Regs) blend21_persistent_kernel(const gs_camera *__restrict__ cams, Ws w,
+                                                                    OutPtrs o)
+{
+    blend_persistent<2, 1, COUNT>(cams, w, o);
+}
+
+// the kernels of one (PX, PY, COUNT) variant
+template <int PX, int PY, bool COUNT> struct BlendKernels {
+    static constexpr auto one = blend_kernel<PX, PY, COUNT>;
+    static constexpr auto persistent = blend_persistent_kernel<PX, PY, COUNT>;
+};
+template <bool COUNT> struct BlendKernels<2, 1, COUNT> {
+    static constexpr auto one = blend21_kernel<COUNT>;
+    static constexpr auto persistent = blend21_persistent_kernel<COUNT>;
+};
 
 // ---------------------------------------------------------------------------
 // host-side launchers
@@ -1015,29 +1076,45 @@ void launch_scatter(const gs_camera *cams, const Ws &w, int n_chunks, cudaStream
 
 int blend_smem_bytes(int batch_depth) { return (2 * 3 * batch_depth + kUnroll) * (int)sizeof(float4); }
 
-template <int PX, int PY>
-static void launch_blend_t(const gs_camera *cams, const Ws &w, const OutPtrs &o, int n_bins, int threads,
+template <int PX, int PY, bool COUNT>
+static void launch_blend_c(const gs_camera *cams, const Ws &w, const OutPtrs &o, int n_bins, int threads,
                            int batch_depth, bool persistent, int n_sms, cudaStream_t s)
 {
     const int smem = blend_smem_bytes(batch_depth);
+    using K = BlendKernels<PX, PY, COUNT>;
     if (persistent) {
         int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blend_persistent_kernel<PX, PY>, threads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, K::persistent, threads, smem);
         int grid = n_sms * (nb > 0 ? nb : 1);
         if (grid > n_bins) grid = n_bins;
-        blend_persistent_kernel<PX, PY><<<grid, threads, smem, s>>>(cams, w, o);
+        K::persistent<<<grid, threads, smem, s>>>(cams, w, o);
     } else {
-        blend_kernel<PX, PY><<<n_bins, threads, smem, s>>>(cams, w, o);
+        K::one<<<n_bins, threads, smem, s>>>(cams, w, o);
     }
+}
+
+template <int PX, int PY>
+static void launch_blend_t(const gs_camera *cams, const Ws &w, const OutPtrs &o, int n_bins, int threads,
+                           int batch_depth, bool persistent, bool count, int n_sms, cudaStream_t s)
+{
+    if (count) launch_blend_c<PX, PY, true>(cams, w, o, n_bins, threads, batch_depth, persistent, n_sms, s);
+    else launch_blend_c<PX, PY, false>(cams, w, o, n_bins, threads, batch_depth, persistent, n_sms, s);
 }
 
 template <int PX, int PY>
 static int blend_limit_t()
 {
-    cudaFuncAttributes a, b;
-    if (cudaFuncGetAttributes(&a, blend_kernel<PX, PY>) != cudaSuccess) return 0;
-    if (cudaFuncGetAttributes(&b, blend_persistent_kernel<PX, PY>) != cudaSuccess) return 0;
-    return a.maxThreadsPerBlock < b.maxThreadsPerBlock ? a.maxThreadsPerBlock : b.maxThreadsPerBlock;
+    const void *ks[] = {reinterpret_cast<const void *>(BlendKernels<PX, PY, false>::one),
+                        reinterpret_cast<const void *>(BlendKernels<PX, PY, false>::persistent),
+                        reinterpret_cast<const void *>(BlendKernels<PX, PY, true>::one),
+                        reinterpret_cast<const void *>(BlendKernels<PX, PY, true>::persistent)};
+    int lim = 1 << 30;
+    for (const void *k : ks) {
+        cudaFuncAttributes a;
+        if (cudaFuncGetAttributes(&a, k) != cudaSuccess) return 0;
+        lim = a.maxThreadsPerBlock < lim ? a.maxThreadsPerBlock : lim;
+    }
+    return lim;
 }
 
 int blend_thread_limit(int px, int py)
@@ -1049,14 +1126,14 @@ int blend_thread_limit(int px, int py)
 }
 
 void launch_blend(const gs_camera *cams, const Ws &w, float *rgb, float *depth, float *T, int32_t *ncontrib,
-                  int n_bins, int px, int py, int threads, int batch_depth, bool persistent, int n_sms,
+                  int n_bins, int px, int py, int threads, int batch_depth, bool persistent, bool count, int n_sms,
                   cudaStream_t s)
 {
     OutPtrs o{rgb, depth, T, ncontrib};
-    if (px == 2 && py == 2) launch_blend_t<2, 2>(cams, w, o, n_bins, threads, batch_depth, persistent, n_sms, s);
-    else if (px == 2) launch_blend_t<2, 1>(cams, w, o, n_bins, threads, batch_depth, persistent, n_sms, s);
-    else if (py == 2) launch_blend_t<1, 2>(cams, w, o, n_bins, threads, batch_depth, persistent, n_sms, s);
-    else launch_blend_t<1, 1>(cams, w, o, n_bins, threads, batch_depth, persistent, n_sms, s);
+    if (px == 2 && py == 2) launch_blend_t<2, 2>(cams, w, o, n_bins, threads, batch_depth, persistent, count, n_sms, s);
+    else if (px == 2) launch_blend_t<2, 1>(cams, w, o, n_bins, threads, batch_depth, persistent, count, n_sms, s);
+    else if (py == 2) launch_blend_t<1, 2>(cams, w, o, n_bins, threads, batch_depth, persistent, count, n_sms, s);
+    else launch_blend_t<1, 1>(cams, w, o, n_bins, threads, batch_depth, persistent, count, n_sms, s);
 }
 
 cudaError_t configure_forward_kernels()

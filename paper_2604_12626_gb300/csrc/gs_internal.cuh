@@ -4,8 +4,10 @@
 // Workspace layout (all sections 256-byte aligned, sizes from the batch):
 //   Header      device counters and the sticky status word
 //   Table       the batch structure (env/view offsets), written by setup
-//   rec         [R] Record (48 B): (uc, vc, z, r) (A, B, C, opacity) (r, g, b, 0)
-//               R = sum over views of the Gaussians of the view's env
+//   rec         [R] Record (48 B): (uc, vc, hx, hy) (A, B, C, opacity) (r, g, b, z)
+//               R = sum over views of the Gaussians of the view's env; (hx, hy)
+//               the half widths of the pixel window (alpha_window), z the FP32
+//               depth key
 //   vis         [R/32] visibility bitmask of the records
 //   bin_count   [B] pairs per (view, tile) bin, B = V * tiles
 //   bin_start   [B+1] exclusive scan of bin_count (tile ranges)
@@ -82,9 +84,10 @@ struct Header {
     uint32_t n_heavy_items; // backward work items of the heavy bins (one per kSeg-long segment)
     uint32_t max_pass;  // merge passes the largest bin needs
     unsigned long long n_evals; // blend evaluations, counted under GS_FLAG_COUNT_EVALS
+    unsigned long long n_cov;   // covered Gaussians up to each pixel's last blended one (same flag)
     uint32_t n_backward;  // gs_render_backward calls since the forward (d_rec is clean while 0)
     uint32_t queue_zero;  // gradient-clearing items taken by the blend backward
-    uint32_t pad[48];
+    uint32_t pad[46];
 };
 
 struct Table {
@@ -141,14 +144,6 @@ inline int chunk_of(int64_t n)
     return c;
 }
 
-// Tile rectangle of a visible record packed into 32 bits: tx0 (11 bits),
-// ty0 (11), ntx - 1 (5), nty - 1 (5); all-ones when it does not fit.
-__host__ __device__ __forceinline__ uint32_t pack_rect(int tx0, int ty0, int ntx, int nty)
-{
-    if (tx0 >= 2048 || ty0 >= 2048 || ntx > 32 || nty > 32) return 0xffffffffu;
-    return (uint32_t)tx0 | ((uint32_t)ty0 << 11) | ((uint32_t)(ntx - 1) << 22) | ((uint32_t)(nty - 1) << 27);
-}
-
 // ---------------------------------------------------------------------------
 // Decisions both the forward and the backward take; written with explicit
 // round-to-nearest intrinsics so that every kernel gets the same bits.
@@ -167,8 +162,35 @@ __device__ __forceinline__ float depth_key(float mx, float my, float mz, const g
 // Pixel coordinate relative to the principal point.
 __device__ __forceinline__ float pix_c(int i, float c) { return __fsub_rn((float)i, c); }
 
-// Square footprint: pixel covered iff |uc - pxc| <= r (and the same in y).
+// Pixel window test in one axis: |uc - pxc| <= h.  With h = r this is the
+// square footprint (pixel covered iff |uc - pxc| <= r and the same in y).
 __device__ __forceinline__ bool covers1(float uc, float r, float pxc) { return fabsf(__fsub_rn(uc, pxc)) <= r; }
+
+// Half widths (hx, hy) of the pixel window of a Gaussian: the square footprint
+// r, narrowed to where the skip rule (alpha = o e^power < 1/255, Sec. 3.2) can
+// still let a pixel blend.  With Q the conic, o e^power >= 1/255 needs
+// d^T Q d <= t = 2 ln(255 o), and on that ellipse |dx| <= sqrt(t (Q^-1)_xx),
+// (Q^-1)_xx = C / (A C - B^2).  The margins cover the FP32 rounding of the
+// blend's power (relative 1e-5 per unit of A C / (A C - B^2)), of the fast exp
+// and of the window itself, so every pixel the blend finds with alpha >= 1/255
+// lies inside; a pixel outside has alpha < 1/255 and would be skipped anyway,
+// so the window changes no output.  Where the square is the tighter bound
+// (hx = r exactly) the window test is the footprint test itself.  hx < 0: no
+// pixel can blend (o < 1/255).  Nearly degenerate conics keep the square.
+__device__ __forceinline__ void alpha_window(float o, float A, float B, float C, float r, float &hx, float &hy)
+{
+    hx = hy = r;
+    const float ac = A * C, dq = ac - B * B;
+    const float L = logf(255.0f * o) + 1e-4f;
+    if (!(L > 0.0f)) {
+        hx = hy = -1.0f;
+        return;
+    }
+    if (!(dq > 1e-3f * ac)) return;
+    const float t = 2.0f * L * (1.0f + 1e-5f * (ac / dq)) + 1e-4f;
+    hx = fminf(r, sqrtf(t * C / dq) * 1.001f + 0.01f);
+    hy = fminf(r, sqrtf(t * A / dq) * 1.001f + 0.01f);
+}
 
 // Smallest and largest i in [0, n) covered in one axis; false when none.
 __device__ __forceinline__ bool pixel_range(float uc, float r, float c, int n, int &lo, int &hi)

@@ -77,13 +77,14 @@ def covered_ranges(u_c: np.ndarray, r: np.ndarray, c: float, n: int, chunk: int 
 def reference_keys(records: np.ndarray, vis_bits: np.ndarray, view_of_rec: np.ndarray, cams: np.ndarray,
                    W: int, H: int, tw: int, th: int):
     """Per-bin sorted keys from the GPU's records: for every visible record, one
-    key (FP32 depth bits << 32 | record) per tile its FP32 footprint touches;
-    a stable sort of the keys by (bin, key).  Returns (bin_counts, keys_sorted)."""
+    key (FP32 depth bits << 32 | record) per tile its FP32 pixel window
+    (|i - cx - uc| <= hx, |j - cy - vc| <= hy) touches; a stable sort of the
+    keys by (bin, key).  Returns (bin_counts, keys_sorted)."""
     R = records.shape[0]
     bits = np.unpackbits(vis_bits.view(np.uint8), bitorder="little")[:R].astype(bool)
     rec = np.flatnonzero(bits)
     v = view_of_rec[rec]
-    uc, vc, z, rad = (records[rec, k] for k in range(4))
+    uc, vc, hx, hy, z = (records[rec, k] for k in (0, 1, 2, 3, 11))
     tiles_x, tiles_y = (W + tw - 1) // tw, (H + th - 1) // th
     tpv = tiles_x * tiles_y
     x_lo = np.empty(rec.size, np.int64)
@@ -92,8 +93,8 @@ def reference_keys(records: np.ndarray, vis_bits: np.ndarray, view_of_rec: np.nd
     y_hi = np.empty(rec.size, np.int64)
     for vv in np.unique(v):
         s = v == vv
-        x_lo[s], x_hi[s] = covered_ranges(uc[s], rad[s], cams[vv, 14], W)
-        y_lo[s], y_hi[s] = covered_ranges(vc[s], rad[s], cams[vv, 15], H)
+        x_lo[s], x_hi[s] = covered_ranges(uc[s], hx[s], cams[vv, 14], W)
+        y_lo[s], y_hi[s] = covered_ranges(vc[s], hy[s], cams[vv, 15], H)
     assert np.all(x_lo >= 0) and np.all(y_lo >= 0), "a record marked visible covers no pixel"
     zbits = z.astype(np.float32).view(np.uint32).astype(np.uint64)
     key = (zbits << np.uint64(32)) | rec.astype(np.uint64)

@@ -58,13 +58,51 @@ def _check_keys(r, cams, W, H, view_of_rec):
     assert np.array_equal(np.diff(bs), counts[:n_bins]), "bin counts (tile ranges) differ"
     assert np.array_equal(keys, ref), "sorted keys differ"
     _check_blended_flags(rec, keys, blended.astype(bool), bs, cams, W, H, r.cfg.tile_w, r.cfg.tile_h)
+    _check_window(rec, vis, view_of_rec, cams, W, H)
     return int(bs[-1])
+
+
+def _check_window(rec, vis, view_of_rec, cams, W, H, sample=4000):
+    """The pixel window (hx, hy) of a visible record holds every pixel where its
+    alpha can reach 1/255: in FP64 from the record's own conic and opacity, on a
+    sample of the records, every pixel of the image with power <= 0 and
+    o e^power >= (1/255)(1 + 1e-4) lies inside the window; and the window is
+    never wider than the square footprint r = ceil(3 sqrt(lambda_max)) of the
+    2D covariance (the conic's inverse), up to the rounding of that inverse."""
+    R = rec.shape[0]
+    bits = np.unpackbits(vis.view(np.uint8), bitorder="little")[:R].astype(bool)
+    idx = np.flatnonzero(bits)
+    idx = np.random.default_rng(1).choice(idx, min(sample, idx.size), replace=False)
+    r_ = rec[idx].astype(np.float64)
+    uc, vc, hx, hy, A, B, C, op = (r_[:, k] for k in range(8))
+    det = A * C - B * B
+    a2, b2, c2 = C / det, -B / det, A / det  # the 2D covariance
+    mid = 0.5 * (a2 + c2)
+    lam = mid + np.sqrt(np.maximum(0.1, mid * mid - a2 * c2 + b2 * b2))
+    rad = np.ceil(3.0 * np.sqrt(lam) * (1 + 1e-6))
+    assert np.all(hx <= rad) and np.all(hy <= rad), "window wider than the square footprint"
+    v = view_of_rec[idx]
+    ii = np.arange(W, dtype=np.float64)
+    jj = np.arange(H, dtype=np.float64)
+    for k in range(idx.size):
+        dx = uc[k] - (ii - cams[v[k], 14])
+        dy = vc[k] - (jj - cams[v[k], 15])
+        nx = np.abs(dx) <= rad[k] + 1
+        ny = np.abs(dy) <= rad[k] + 1
+        if not nx.any() or not ny.any():
+            continue
+        DX, DY = np.meshgrid(dx[nx], dy[ny])
+        power = -0.5 * (A[k] * DX * DX + C[k] * DY * DY) - B[k] * DX * DY
+        reach = (power <= 0.0) & (op[k] * np.exp(np.minimum(power, 0.0)) >= (1.0 / 255.0) * (1.0 + 1e-4))
+        reach &= (np.abs(DX) <= rad[k]) & (np.abs(DY) <= rad[k])
+        outside = (np.abs(DX) > hx[k]) | (np.abs(DY) > hy[k])
+        assert not np.any(reach & outside), ("window cuts a pixel that can blend", int(idx[k]))
 
 
 def _check_blended_flags(rec, keys, blended, bs, cams, W, H, tw, th, sample=20000):
     """A pair flagged as blended has, at some pixel of its tile and inside its
-    square footprint, power <= 0 and alpha >= 1/255 (checked in FP64 with a
-    small margin on a sample of the flagged pairs)."""
+    pixel window, power <= 0 and alpha >= 1/255 (checked in FP64 with a small
+    margin on a sample of the flagged pairs)."""
     assert blended.any(), "no pair flagged as blended"
     pos = np.flatnonzero(blended)
     pos = np.random.default_rng(0).choice(pos, min(sample, pos.size), replace=False)
@@ -73,12 +111,13 @@ def _check_blended_flags(rec, keys, blended, bs, cams, W, H, tw, th, sample=2000
     v, t = bins // (tiles_x * tiles_y), bins % (tiles_x * tiles_y)
     ri = (keys[pos] & np.uint64(0x7FFFFFFF)).astype(np.int64)
     r_ = rec[ri].astype(np.float64)
-    uc, vc, rad, A, B, C, op = r_[:, 0], r_[:, 1], r_[:, 3], r_[:, 4], r_[:, 5], r_[:, 6], r_[:, 7]
+    uc, vc, hx, hy, A, B, C, op = (r_[:, k] for k in range(8))
     ii = (t % tiles_x)[:, None] * tw + np.arange(tw)[None, :]
     jj = (t // tiles_x)[:, None] * th + np.arange(th)[None, :]
     dx = uc[:, None, None] - (ii[:, None, :] - cams[v, 14][:, None, None])
     dy = vc[:, None, None] - (jj[:, :, None] - cams[v, 15][:, None, None])
-    inside = (ii[:, None, :] < W) & (jj[:, :, None] < H) & (np.maximum(np.abs(dx), np.abs(dy)) <= rad[:, None, None] + 1e-3)
+    inside = ((ii[:, None, :] < W) & (jj[:, :, None] < H) & (np.abs(dx) <= hx[:, None, None] + 1e-3)
+              & (np.abs(dy) <= hy[:, None, None] + 1e-3))
     power = -0.5 * (A[:, None, None] * dx * dx + C[:, None, None] * dy * dy) - B[:, None, None] * dx * dy
     alpha = np.minimum(0.99, op[:, None, None] * np.exp(np.minimum(power, 0.0)))
     ok = inside & (power <= 1e-5) & (alpha >= (1.0 / 255.0) * (1.0 - 1e-4))
@@ -264,6 +303,9 @@ def test_evaluation_count_matches_oracle(gs, oracle, tile, persistent):
     ev = r.count_evaluations(G, ct)
     assert ev == ora["evals"], (ev, ora["evals"])
     assert ev > int(ora["n_contrib"].sum())  # skipped and stopping Gaussians are counted too
+    # the adjoint's walk: covered Gaussians up to each pixel's last blended one
+    assert r.stats()["n_covered"] == int(ora["n_covered"].sum())
+    assert int(ora["n_covered"].sum()) > int(ora["n_contrib"].sum())
 
 
 def test_large_bins_keys_bit_exact(gs):

@@ -171,14 +171,50 @@ __device__ __forceinline__ void finish_entry(const QEntry &en, bool active, uint
     if (active && (threadIdx.x & 31) == __ffs(grp) - 1) atomicOr(w.vis + word, bits);
 }
 
+// One (view, Gaussian) that passed the near cull and the conservative image
+// test, waiting for its projection.
+struct AEntry {
+    uint32_t g;
+    uint16_t k;    // view slot of the chunk's env
+    uint16_t kind; // covariance source: 0 (log-scales, rotation) in c, 1 posed covariance in c, 2 cov3d
+    float mx, my, mz, zk, lo;
+    float c[7];
+    uint32_t pad[2];
+};
+static_assert(sizeof(AEntry) % 16 == 0, "queue entries are copied as 16-byte vectors");
+
+// Conservative image test before the projection: false only if the Gaussian
+// can touch no pixel.  Its radius is r = ceil(3 sqrt(lambda)) with lambda <=
+// lambda_max(Sigma2) + sqrt(0.1) <= trace(J W Sigma W^T J^T) + 0.6 + 0.32 <=
+// |J|_F^2 lambda_max(Sigma) + 0.92 (W a rotation), and a pixel i is covered
+// only if |u - i| <= r; the bound carries 1% and 2 px of slack for FP32.
+__device__ __forceinline__ bool may_touch_image(float mx, float my, float mz, float zk, float lam3,
+                                                const gs_camera &cam, int W, int H)
+{
+    const float d0 = mx - cam.C[0], d1 = my - cam.C[1], d2 = mz - cam.C[2];
+    const float px = cam.R[0] * d0 + cam.R[1] * d1 + cam.R[2] * d2;
+    const float py = cam.R[3] * d0 + cam.R[4] * d1 + cam.R[5] * d2;
+    const float iz = 1.0f / zk;
+    const float limx = 1.3f * (0.5f * (float)W / cam.fx), limy = 1.3f * (0.5f * (float)H / cam.fy);
+    const float tx = fminf(limx, fmaxf(-limx, px * iz)), ty = fminf(limy, fmaxf(-limy, py * iz));
+    const float jx = cam.fx * iz, jy = cam.fy * iz;
+    const float jf2 = jx * jx * (1.0f + tx * tx) + jy * jy * (1.0f + ty * ty);
+    const float rb = 3.03f * sqrtf(jf2 * lam3 + 0.92f) + 2.0f;
+    const float u = cam.fx * px * iz + cam.cx, v = cam.fy * py * iz + cam.cy;
+    return u + rb >= 0.0f && u - rb <= (float)(W - 1) && v + rb >= 0.0f && v - rb <= (float)(H - 1);
+}
+
 // Each warp walks 32-Gaussian rounds of the chunk on its own (no CTA barrier in
-// the loop): phase 1 on every lane (near cull, covariance, projection, radius,
-// footprint), visible results into the warp's ring queue in shared memory, and
-// phase 2 on full warps of 32 queued entries.  The next round's means, scales
-// and rotations are loaded before the current round is processed (most lanes
-// of a warp need them, so the extra bytes are few; 2 CTAs of 256 per SM leave
-// the registers to hold them without spills).
-constexpr int kWarpQ = 64;
+// the loop), in three stages joined by ring queues in shared memory, so that
+// the costly stages run on full warps:
+//   A  every lane: FP32 depth key and near cull per view, then a conservative
+//      image test from the largest scale (cheap, on all Gaussians);
+//   B  32 queued survivors: covariance, EWA projection, conic, radius, pixel
+//      window, exact pixel ranges;
+//   C  32 queued visible entries: SH colour, record, gradient row, bin counts.
+// The next round's means, logits, scales and rotations are loaded before the
+// current round is processed.
+constexpr int kWarpQ = 64; // each queue grows by at most 32 before it is drained below 32
 constexpr int kMaxViewsPerChunk = 16; // cameras of a chunk's env staged in shared memory
 
 // FUSED: the batch's avatar rows are posed by LBS here (gs_render_avatars); a
@@ -191,8 +227,10 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
     __shared__ gs_camera s_cam[kMaxViewsPerChunk];
     __shared__ int64_t s_roff[kMaxViewsPerChunk];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    QEntry *q = reinterpret_cast<QEntry *>(smem_pre) + warp * kWarpQ;
-    uint32_t *hist = reinterpret_cast<uint32_t *>(smem_pre + (kPreThreads / 32) * kWarpQ * sizeof(QEntry));
+    constexpr int kNW = kPreThreads / 32;
+    AEntry *qa = reinterpret_cast<AEntry *>(smem_pre) + warp * kWarpQ;
+    QEntry *qb = reinterpret_cast<QEntry *>(smem_pre + kNW * kWarpQ * sizeof(AEntry)) + warp * kWarpQ;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem_pre + kNW * kWarpQ * (sizeof(AEntry) + sizeof(QEntry)));
     const Table *tb = w.tb;
     Chunk c;
     chunk_setup(tb, blockIdx.x, c);
@@ -214,15 +252,83 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
     const int64_t env_base = tb->env_off[c.e0];
     const bool env_cov = gin.cov3d != nullptr;
     const int64_t cov_begin = tb->env_cov_begin[c.e0];
-    int head = 0, tail = 0; // ring queue of this warp
+    int ha = 0, ta = 0, hb = 0, tb_ = 0; // ring queues of this warp: A (to project), B (visible)
+
+    // stage C on the 32 oldest visible entries (or the last few)
+    auto stage_c = [&](int n) {
+        const bool act = lane < n;
+        QEntry mine;
+        if (act) mine = qb[(hb + lane) & (kWarpQ - 1)];
+        hb += n;
+        __syncwarp();
+        finish_entry<SHT>(mine, act, hist, c, gin, w);
+    };
+    // stage B on the 32 oldest queued survivors (or the last few)
+    auto stage_b = [&](int n) {
+        const bool act = lane < n;
+        bool vis = false;
+        QEntry en;
+        if (act) {
+            const AEntry ea = qa[(ha + lane) & (kWarpQ - 1)];
+            const int k = ea.k;
+            const int v = cam_smem ? 0 : tb->env_views[c.vb + k];
+            const gs_camera &cam = cam_smem ? s_cam[k] : cams[v];
+            float S[6];
+            if (ea.kind == 0) {
+                sigma_from_sq(make_float3(ea.c[0], ea.c[1], ea.c[2]), make_float4(ea.c[3], ea.c[4], ea.c[5], ea.c[6]),
+                              S);
+            } else if (ea.kind == 1) {
+#pragma unroll
+                for (int i = 0; i < 6; ++i) S[i] = ea.c[i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < 6; ++i) S[i] = __ldg(gin.cov3d + 6 * (int64_t)ea.g + i);
+            }
+            Proj pj;
+            if (project_ewa(ea.mx, ea.my, ea.mz, ea.zk, S, cam, W, H, pj)) {
+                const float r = radius_px(pj);
+                const float idet = 1.0f / pj.det;
+                const float cA = pj.c * idet, cB = -pj.b * idet, cC = pj.a * idet;
+                const float op = 1.0f / (1.0f + expf(-ea.lo));
+                // the pixel window: the square footprint narrowed to where
+                // alpha can reach 1/255 (the square alone when evaluations are
+                // counted, so that the count follows the definition)
+                float hx = r, hy = r;
+                if (!count_evals) alpha_window(op, cA, cB, cC, r, hx, hy);
+                int x0, x1, y0, y1;
+                if (hx >= 0.0f && pixel_range(pj.uc, hx, cam.cx, W, x0, x1) &&
+                    pixel_range(pj.vc, hy, cam.cy, H, y0, y1)) {
+                    vis = true;
+                    const int64_t g = ea.g;
+                    en.rec = (uint32_t)((cam_smem ? s_roff[k] : tb->view_rec_off[v]) + (g - env_base));
+                    en.g = ea.g;
+                    en.uc = pj.uc; en.vc = pj.vc; en.zk = ea.zk; en.hx = hx; en.hy = hy; en.op = op;
+                    en.A = cA; en.B = cB; en.C = cC;
+                    en.d0 = pj.d0; en.d1 = pj.d1; en.d2 = pj.d2;
+                    if (FUSED && (tb->flags & GS_FLAG_AVATAR_CANONICAL_SH) && g >= cov_begin)
+                        canonical_direction(gin, tb->env_av_base[c.e0] + (g - cov_begin), en.d0, en.d1, en.d2);
+                    en.x0 = (uint16_t)x0; en.x1 = (uint16_t)x1; en.y0 = (uint16_t)y0; en.y1 = (uint16_t)y1;
+                    en.v = (uint16_t)(cam_smem ? tb->env_views[c.vb + k] : v); en.k = (uint16_t)k;
+                }
+            }
+        }
+        ha += n;
+        const unsigned bal = __ballot_sync(0xffffffffu, vis);
+        if (vis) qb[(tb_ + __popc(bal & ((1u << lane) - 1u))) & (kWarpQ - 1)] = en;
+        tb_ += __popc(bal);
+        __syncwarp();
+        if (tb_ - hb >= 32) stage_c(32);
+    };
+
     int64_t g = c.g0 + warp * 32 + lane;
-    float mx = 0.f, my = 0.f, mz = 0.f;
+    float mx = 0.f, my = 0.f, mz = 0.f, lo = 0.f;
     float3 cls = make_float3(0.f, 0.f, 0.f);
     float4 cq = make_float4(1.f, 0.f, 0.f, 0.f);
     if (g < c.g1) {
         mx = __ldg(gin.means + 3 * g);
         my = __ldg(gin.means + 3 * g + 1);
         mz = __ldg(gin.means + 3 * g + 2);
+        lo = __ldg(gin.ologits + g);
         if (!((env_cov || FUSED) && g >= cov_begin)) { // posed rows take their covariance elsewhere
             cls = make_float3(__ldg(gin.log_scales + 3 * g), __ldg(gin.log_scales + 3 * g + 1),
                               __ldg(gin.log_scales + 3 * g + 2));
@@ -231,15 +337,16 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
     }
     for (int64_t base = c.g0 + warp * 32; base < c.g1; base += 32 * nwarps) {
         const bool valid = g < c.g1;
-        // prefetch the next round's means
+        // prefetch the next round's means, logits, scales and rotations
         const int64_t gn = g + 32 * nwarps;
-        float nx = 0.f, ny = 0.f, nz = 0.f;
+        float nx = 0.f, ny = 0.f, nz = 0.f, nlo = 0.f;
         float3 nls = make_float3(0.f, 0.f, 0.f);
         float4 nq = make_float4(1.f, 0.f, 0.f, 0.f);
         if (gn < c.g1) {
             nx = __ldg(gin.means + 3 * gn);
             ny = __ldg(gin.means + 3 * gn + 1);
             nz = __ldg(gin.means + 3 * gn + 2);
+            nlo = __ldg(gin.ologits + gn);
             if (!((env_cov || FUSED) && gn >= cov_begin)) {
                 nls = make_float3(__ldg(gin.log_scales + 3 * gn), __ldg(gin.log_scales + 3 * gn + 1),
                                   __ldg(gin.log_scales + 3 * gn + 2));
@@ -247,16 +354,18 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
             }
         }
         const int nv = valid ? c.nv : 0;
-        const int64_t local = g - env_base;
-        bool have_sigma = false;
-        float S[6];
+        // covariance source of this lane's Gaussian and the largest variance
+        // of its 3D covariance for the image test
+        uint16_t kind = 0;
+        float cc[7] = {cls.x, cls.y, cls.z, cq.x, cq.y, cq.z, cq.w};
+        float lam3 = __expf(2.0f * fmaxf(cls.x, fmaxf(cls.y, cls.z))) * 1.001f;
         if (FUSED && valid && g >= cov_begin) {
             // posed mean and covariance by LBS, never written to memory
             const int64_t i = tb->env_av_base[c.e0] + (g - cov_begin);
             const int a = clamp_avatar(__ldg(gin.av_of + i), gin.n_avatars);
             const ushort4 id = clamp_ids(__ldg(reinterpret_cast<const ushort4 *>(gin.av_ids) + i), gin.n_joints);
             const float4 wt = __ldg(reinterpret_cast<const float4 *>(gin.av_weights) + i);
-            float mu[3];
+            float mu[3], S[6];
             lbs_gaussian(gin.av_G + (size_t)a * gin.n_joints * 12, id, wt,
                          make_float3(__ldg(gin.av_means + 3 * i), __ldg(gin.av_means + 3 * i + 1),
                                      __ldg(gin.av_means + 3 * i + 2)),
@@ -266,78 +375,48 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
             mx = mu[0];
             my = mu[1];
             mz = mu[2];
-            have_sigma = true;
+            kind = 1;
+#pragma unroll
+            for (int j = 0; j < 6; ++j) cc[j] = S[j];
+            lam3 = fmaxf(S[0] + S[3] + S[5], 0.0f) * 1.001f; // >= lambda_max of a PSD matrix
+        } else if (env_cov && valid && g >= cov_begin) {
+            kind = 2;
+            lam3 = INFINITY; // read in stage B; no image test
         }
         for (int k = 0; k < c.kmax; ++k) {
-            bool vis = false;
-            QEntry en;
+            bool push = false;
+            float zk = 0.0f;
             if (k < nv) {
                 const int v = cam_smem ? 0 : tb->env_views[c.vb + k];
                 const gs_camera &cam = cam_smem ? s_cam[k] : cams[v];
-                const float zk = depth_key(mx, my, mz, cam);
-                if (zk > near_plane) {
-                    if (!have_sigma) {
-                        if (env_cov && g >= cov_begin) {
+                zk = depth_key(mx, my, mz, cam);
+                push = zk > near_plane && (kind == 2 || may_touch_image(mx, my, mz, zk, lam3, cam, W, H));
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, push);
+            if (push) {
+                AEntry ea;
+                ea.g = (uint32_t)g;
+                ea.k = (uint16_t)k;
+                ea.kind = kind;
+                ea.mx = mx; ea.my = my; ea.mz = mz; ea.zk = zk; ea.lo = lo;
 #pragma unroll
-                            for (int i = 0; i < 6; ++i) S[i] = __ldg(gin.cov3d + 6 * g + i);
-                        } else {
-                            sigma_from_sq(cls, cq, S);
-                        }
-                        have_sigma = true;
-                    }
-                    Proj pj;
-                    if (project_ewa(mx, my, mz, zk, S, cam, W, H, pj)) {
-                        const float r = radius_px(pj);
-                        const float idet = 1.0f / pj.det;
-                        const float cA = pj.c * idet, cB = -pj.b * idet, cC = pj.a * idet;
-                        const float op = 1.0f / (1.0f + expf(-__ldg(gin.ologits + g)));
-                        // the pixel window: the square footprint narrowed to where
-                        // alpha can reach 1/255 (the square alone when evaluations
-                        // are counted, so that the count follows the definition)
-                        float hx = r, hy = r;
-                        if (!count_evals) alpha_window(op, cA, cB, cC, r, hx, hy);
-                        int x0, x1, y0, y1;
-                        if (hx >= 0.0f && pixel_range(pj.uc, hx, cam.cx, W, x0, x1) &&
-                            pixel_range(pj.vc, hy, cam.cy, H, y0, y1)) {
-                            vis = true;
-                            en.rec = (uint32_t)((cam_smem ? s_roff[k] : tb->view_rec_off[v]) + local);
-                            en.g = (uint32_t)g;
-                            en.uc = pj.uc; en.vc = pj.vc; en.zk = zk; en.hx = hx; en.hy = hy; en.op = op;
-                            en.A = cA; en.B = cB; en.C = cC;
-                            en.d0 = pj.d0; en.d1 = pj.d1; en.d2 = pj.d2;
-                            if (FUSED && (tb->flags & GS_FLAG_AVATAR_CANONICAL_SH) && g >= cov_begin)
-                                canonical_direction(gin, tb->env_av_base[c.e0] + (g - cov_begin), en.d0, en.d1,
-                                                    en.d2);
-                            en.x0 = (uint16_t)x0; en.x1 = (uint16_t)x1; en.y0 = (uint16_t)y0; en.y1 = (uint16_t)y1;
-                            en.v = (uint16_t)(cam_smem ? tb->env_views[c.vb + k] : v); en.k = (uint16_t)k;
-                        }
-                    }
-                }
+                for (int j = 0; j < 7; ++j) ea.c[j] = cc[j];
+                qa[(ta + __popc(bal & ((1u << lane) - 1u))) & (kWarpQ - 1)] = ea;
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, vis);
-            if (vis) q[(tail + __popc(bal & ((1u << lane) - 1u))) & (kWarpQ - 1)] = en;
-            tail += __popc(bal);
+            ta += __popc(bal);
             __syncwarp();
-            if (tail - head >= 32) {
-                const QEntry mine = q[(head + lane) & (kWarpQ - 1)];
-                head += 32;
-                __syncwarp();
-                finish_entry<SHT>(mine, true, hist, c, gin, w);
-            }
+            if (ta - ha >= 32) stage_b(32);
         }
         g = gn;
         mx = nx;
         my = ny;
         mz = nz;
+        lo = nlo;
         cls = nls;
         cq = nq;
     }
-    if (tail > head) {
-        const bool act = lane < tail - head;
-        QEntry mine;
-        if (act) mine = q[(head + lane) & (kWarpQ - 1)];
-        finish_entry<SHT>(mine, act, hist, c, gin, w);
-    }
+    if (ta > ha) stage_b(ta - ha);
+    if (tb_ > hb) stage_c(tb_ - hb);
     __syncthreads();
     if (c.hist) {
         // 2D inclusive prefix sums of the difference array: rows (one warp per
@@ -1040,7 +1119,7 @@ template <bool COUNT> struct BlendKernels<2, 1, COUNT> {
 // ---------------------------------------------------------------------------
 void launch_setup(const Table &tb, const Ws &w, cudaStream_t s) { setup_kernel<<<1, 256, 0, s>>>(tb, w); }
 
-constexpr int kPreSmem = (kPreThreads / 32) * kWarpQ * (int)sizeof(QEntry) + kHistCap * 4;
+constexpr int kPreSmem = (kPreThreads / 32) * kWarpQ * (int)(sizeof(AEntry) + sizeof(QEntry)) + kHistCap * 4;
 
 void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s,
                        const gs_avatars *av, const float *joint_G)

@@ -181,7 +181,7 @@ __device__ __forceinline__ void alpha_window(float o, float A, float B, float C,
 {
     hx = hy = r;
     const float ac = A * C, dq = ac - B * B;
-    const float L = logf(255.0f * o) + 1e-4f;
+    const float L = __logf(255.0f * o) + 1e-4f; // fast log: absolute error far below the margin
     if (!(L > 0.0f)) {
         hx = hy = -1.0f;
         return;

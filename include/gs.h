@@ -117,7 +117,10 @@ typedef struct {
     float near_plane;          /* Gaussians with FP32 view depth <= near are culled; 0 -> 0.2 */
     int64_t pair_capacity;     /* max (tile, Gaussian) pairs; 0 -> 4 x records + 65536 */
     int32_t pix_x, pix_y;      /* pixels per blend thread, each 1 or 2 (0 -> 1); the CTA has
-                                  (tile_w / pix_x) x (tile_h / pix_y) threads, a multiple of 32 */
+                                  (tile_w / pix_x) x (tile_h / pix_y) threads, a multiple of 32.
+                                  2 x 1: a warp per 8 x 8 block with a Gaussian list per 4 x 4
+                                  quarter; tile_w, tile_h multiples of 8 and at most 4 warps
+                                  (GS_ERR_UNSUPPORTED otherwise) */
 } gs_render_config;
 
 /* Per-call counters, read back by gs_render_stats (synchronises). */
@@ -352,9 +355,14 @@ gs_status gs_autotune(const gs_gaussians *g, const gs_batch *batch, const gs_cam
  *   keys       [pair_capacity] uint64 (depth bits << 32 | record), sorted per bin;
  *              after the blend, bit 31 (the record word's top bit) is set on
  *              the pairs that some pixel of their tile blended
- *   bin_start  [n_bins + 1] uint32, bin = view * tiles_per_view + ty * tiles_x + tx */
+ *   bin_start  [n_bins + 1] uint32, bin = view * tiles_per_view + ty * tiles_x + tx
+ *   quarters   at 2 x 1 pixels per thread (else NULL): [pair_capacity] uint32 beside
+ *              the keys; on a pair whose key has bit 31 set, byte w holds (bits 0-3)
+ *              the 4 x 4 quarters of warp w's 8 x 8 block that blended it (warps in
+ *              row-major order over the tile's blocks, quarter q at (4 (q & 1),
+ *              4 (q >> 1)) in the block); stale elsewhere */
 typedef struct {
-    void *records, *vis, *keys, *bin_start;
+    void *records, *vis, *keys, *bin_start, *quarters;
     int64_t n_records, pair_capacity;
     int32_t n_bins, tiles_x, tiles_y, tiles_per_view;
 } gs_ws_sections;

@@ -60,7 +60,8 @@ class GsStats(ctypes.Structure):
 
 
 class GsWsSections(ctypes.Structure):
-    _fields_ = [("records", _P), ("vis", _P), ("keys", _P), ("bin_start", _P), ("n_records", ctypes.c_int64),
+    _fields_ = [("records", _P), ("vis", _P), ("keys", _P), ("bin_start", _P), ("quarters", _P),
+                ("n_records", ctypes.c_int64),
                 ("pair_capacity", ctypes.c_int64), ("n_bins", ctypes.c_int32), ("tiles_x", ctypes.c_int32),
                 ("tiles_y", ctypes.c_int32), ("tiles_per_view", ctypes.c_int32)]
 
@@ -361,7 +362,9 @@ class Renderer:
         """Views into the workspace left by the last forward: records [R,12] float32,
         vis [ceil(R/32)] int32 bits, keys [cap] int64 (depth bits << 32 | record; bit 31 set
         by the blend on pairs some pixel of the tile blended),
-        bin_start [n_bins+1] int32, plus the tile grid."""
+        bin_start [n_bins+1] int32, quarters [cap] int32 at 2 x 1 pixels per thread
+        (else None: per flagged pair, byte w = the quarters of warp w that blended
+        it), plus the tile grid."""
         s = GsWsSections()
         _check(_lib.gs_workspace_sections(ctypes.byref(self.cfg), ctypes.byref(self.batch.c), _ptr(self.workspace),
                                           ctypes.byref(s)), "gs_workspace_sections")
@@ -376,6 +379,7 @@ class Renderer:
                     vis=view(s.vis, ((R + 31) // 32) * 4, torch.int32),
                     keys=view(s.keys, s.pair_capacity * 8, torch.int64),
                     bin_start=view(s.bin_start, (s.n_bins + 1) * 4, torch.int32),
+                    quarters=view(s.quarters, s.pair_capacity * 4, torch.int32) if s.quarters else None,
                     n_bins=s.n_bins, tiles_x=s.tiles_x, tiles_y=s.tiles_y, tiles_per_view=s.tiles_per_view,
                     pair_capacity=s.pair_capacity)
 

@@ -120,7 +120,7 @@ struct Plan {
     float near_plane;
     // byte offsets
     size_t o_hdr, o_tb, o_rec, o_vis, o_cnt, o_fcnt, o_start, o_cur, o_big, o_heavy, o_rel, o_keys, o_scr, o_pT, o_pL,
-        o_drec, o_hseg, o_hof, o_pC, o_ckC, o_ckD, total;
+        o_drec, o_hseg, o_hof, o_pC, o_ckC, o_ckD, o_pq, total;
     int chunk, n_chunks;
 };
 
@@ -140,6 +140,9 @@ gs_status make_plan(const gs_render_config *cfg, const gs_batch *b, Plan &p)
     if (p.px > 2 || p.py > 2 || p.tw % p.px || p.th % p.py) return GS_ERR_INVALID_ARG;
     p.threads = (p.tw / p.px) * (p.th / p.py);
     if (p.threads > 1024 || p.threads % 32 != 0) return GS_ERR_INVALID_ARG;
+    // 2 x 1 pixels per lane: 8 x 8 blocks per warp, at most 4 warps (the
+    // per-pair quarter bits of a tile fill one 32-bit word)
+    if (p.px == 2 && p.py == 1 && (p.tw % 8 || p.th % 8 || p.threads > 128)) return GS_ERR_UNSUPPORTED;
     p.B = cfg->batch_depth > 0 ? cfg->batch_depth : 256;
     if (p.B < 32 || p.B > 256 || p.B > 4 * p.threads) return GS_ERR_INVALID_ARG;
     p.flags = cfg->flags;
@@ -195,6 +198,7 @@ gs_status make_plan(const gs_render_config *cfg, const gs_batch *b, Plan &p)
     const size_t tpx = (size_t)p.tw * p.th;
     p.o_ckC = o; o = align256(o + slots * tpx * 16);
     p.o_ckD = o; o = align256(o + slots * tpx * 4);
+    p.o_pq = o; o = align256(o + (p.px == 2 && p.py == 1 ? (size_t)p.cap * 4 : 0));
     p.total = o;
     return GS_OK;
 }
@@ -224,6 +228,7 @@ Ws ws_ptrs(void *base, const Plan &p)
     w.pix_C = reinterpret_cast<float4 *>(b + p.o_pC);
     w.ck_C = reinterpret_cast<float4 *>(b + p.o_ckC);
     w.ck_D = reinterpret_cast<float *>(b + p.o_ckD);
+    w.pq = reinterpret_cast<uint32_t *>(b + p.o_pq);
     return w;
 }
 
@@ -753,6 +758,7 @@ gs_status gs_workspace_sections(const gs_render_config *cfg, const gs_batch *bat
     out->vis = b + p.o_vis;
     out->keys = b + p.o_keys;
     out->bin_start = b + p.o_start;
+    out->quarters = (p.px == 2 && p.py == 1) ? b + p.o_pq : nullptr;
     out->n_records = p.R;
     out->pair_capacity = p.cap;
     out->n_bins = p.n_bins;

@@ -415,6 +415,330 @@ __device__ __forceinline__ void blend_backward_tile(const Ws &w, const gs_camera
     cp_async_wait<0>();
 }
 
+// Sums v[0..31] over each 8-lane quarter of the warp with 28 shuffles
+// (butterfly transpose over lane bits 4, 2, 1): on return, lane 8q + m holds
+// in v[0..3] the quarter's totals of v[4m .. 4m + 3].
+__device__ __forceinline__ void quarter_transpose_sum32(float (&v)[32])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 4, m = 32; o > 0; o >>= 1, m >>= 1) {
+        const bool up = lane & o;
+#pragma unroll
+        for (int i = 0; i < m / 2; ++i) {
+            const float keep = up ? v[i + m / 2] : v[i], send = up ? v[i] : v[i + m / 2];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+}
+
+// 2 x 1 pixels per lane with a Gaussian list per 4 x 4 quarter (the layout of
+// the forward's blendq_tile): per batch, back to front, the entries some pixel
+// of the tile blended are gathered; every warp lists, per quarter, those its
+// quarter blended (the forward's quarter bits), and the quarters walk their own
+// lists in lockstep, kGroup entries at a time; the gradient sums of a group are
+// reduced per quarter (8 lanes) and added to the batch's shared accumulator.
+__device__ __forceinline__ void blendq_backward_tile(const Ws &w, const gs_camera *cams, const float *d_rgb,
+                                                    const float *d_depth, int bin, uint32_t seg_lo, uint32_t seg_hi,
+                                                    int64_t ck_slot, float4 *sm, float *acc, uint32_t *sidx,
+                                                    uint32_t *clist, uint32_t *spq, uint8_t *qls,
+                                                    uint32_t *smax_last)
+{
+    const Table *tb = w.tb;
+    const int B = tb->batch_depth;
+    const int nthr = blockDim.x;
+    const int v = bin / tb->tiles_per_view;
+    const int t = bin - v * tb->tiles_per_view;
+    const int tyi = t / tb->tiles_x, txi = t - tyi * tb->tiles_x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = lane >> 3, mq = lane & 7;
+    const int wx = tb->tile_w >> 3;
+    const int tx0 = txi * tb->tile_w, ty0 = tyi * tb->tile_h;
+    const int i0 = tx0 + (warp % wx) * 8 + (q & 1) * 4 + (mq & 1) * 2;
+    const int j0 = ty0 + (warp / wx) * 8 + (q >> 1) * 4 + (mq >> 1);
+    const int W = tb->W, H = tb->H;
+    const gs_camera &cam = cams[v];
+    const float pyc = pix_c(j0, cam.cy);
+    const float2 npx2 = make_float2(-pix_c(i0, cam.cx), -pix_c(i0 + 1, cam.cx));
+    const size_t HW = (size_t)W * H;
+    uint32_t start, n;
+    bin_range(w, bin, start, n);
+    const unsigned long long *keys = w.keys + start;
+    const uint32_t *pqb = w.pq + start;
+    const uint32_t R = (uint32_t)tb->n_records;
+    const int qs = qlist_stride(B);
+    uint8_t *ql = qls + warp * 4 * qs;
+
+    float T[2], dC0[2], dC1[2], dC2[2], dD[2], S0[2], S1[2], S2[2], SD[2];
+    uint32_t last[2];
+    uint32_t tlast = 0;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int i = i0 + p, j = j0;
+        T[p] = 1.0f; dC0[p] = dC1[p] = dC2[p] = dD[p] = 0.f; S0[p] = S1[p] = S2[p] = SD[p] = 0.f;
+        last[p] = 0;
+        if (i < W && j < H) {
+            const size_t px = (size_t)j * W + i;
+            T[p] = w.pix_T[(size_t)v * HW + px];
+            last[p] = w.pix_last[(size_t)v * HW + px];
+            dC0[p] = d_rgb[(3 * (size_t)v + 0) * HW + px];
+            dC1[p] = d_rgb[(3 * (size_t)v + 1) * HW + px];
+            dC2[p] = d_rgb[(3 * (size_t)v + 2) * HW + px];
+            dD[p] = d_depth[(size_t)v * HW + px];
+            S0[p] = T[p] * tb->bg[0];
+            S1[p] = T[p] * tb->bg[1];
+            S2[p] = T[p] * tb->bg[2];
+        }
+        tlast = max(tlast, last[p]);
+    }
+    if (threadIdx.x == 0) *smax_last = 0;
+    __syncthreads();
+    const uint32_t wl = __reduce_max_sync(0xffffffffu, tlast);
+    if (lane == 0) atomicMax(smax_last, wl);
+    __syncthreads();
+    const uint32_t tile_last = min(*smax_last, n);
+    if (seg_lo >= tile_last) return; // nothing blended in this segment
+    const uint32_t n_proc = min(tile_last, seg_hi);
+    if (n_proc < tile_last) {
+        // start from the checkpoint before position seg_hi
+        const int tpx = tb->tile_w * tb->tile_h;
+        const int lpx = (j0 - ty0) * tb->tile_w + (i0 - tx0);
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const int i = i0 + p, j = j0;
+            if (i < W && j < H) {
+                const float4 ck = w.ck_C[(size_t)ck_slot * tpx + lpx + p];
+                const float ckd = w.ck_D[(size_t)ck_slot * tpx + lpx + p];
+                const float4 fin = w.pix_C[(size_t)v * HW + (size_t)j * W + i];
+                T[p] = ck.x;
+                S0[p] = fin.x - ck.y;
+                S1[p] = fin.y - ck.z;
+                S2[p] = fin.z - ck.w;
+                SD[p] = fin.w - ckd;
+            }
+        }
+    }
+    // both pixels as packed FP32 pairs; the colour and depth terms of dL/dalpha
+    // enter through one running dot product per pixel, ndcs = -(dC . S), S the
+    // colour and depth behind the current pair (S grows by c wgt, so ndcs falls
+    // by wgt (dC . c))
+    float2 T2 = make_float2(T[0], T[1]);
+    const float2 dc0 = make_float2(dC0[0], dC0[1]), dc1 = make_float2(dC1[0], dC1[1]),
+                 dc2 = make_float2(dC2[0], dC2[1]), dd = make_float2(dD[0], dD[1]);
+    float2 ndcs;
+    {
+        float x[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) x[e] = -(dC0[e] * S0[e] + dC1[e] * S1[e] + dC2[e] * S2[e] + dD[e] * SD[e]);
+        ndcs = make_float2(x[0], x[1]);
+    }
+    const int nb = (int)((n_proc - seg_lo + B - 1) / B);
+    // batch b covers [lo_b, hi_b), hi_b = n_proc - b B, lo_b >= seg_lo
+    auto lo_of = [&](int b) {
+        const int32_t x = (int32_t)n_proc - (b + 1) * B;
+        return x < (int32_t)seg_lo ? (int32_t)seg_lo : x;
+    };
+    auto hi_of = [&](int b) { return (int32_t)n_proc - b * B; };
+    unsigned long long kr[kMaxPerB];
+    auto load_keys = [&](int b) {
+        const int32_t lo = lo_of(b), cnt = hi_of(b) - lo;
+#pragma unroll
+        for (int qq = 0; qq < kMaxPerB; ++qq) {
+            const int e = threadIdx.x + qq * nthr;
+            kr[qq] = (b < nb && e < cnt) ? keys[lo + e] : 0ull;
+        }
+    };
+    auto issue = [&](int b) {
+        float4 *buf = sm + (b & 1) * 3 * B;
+        uint32_t *ib = sidx + (b & 1) * B;
+        uint32_t *pb = spq + (b & 1) * B;
+        const int32_t lo = lo_of(b), cnt = hi_of(b) - lo;
+#pragma unroll
+        for (int qq = 0; qq < kMaxPerB; ++qq) {
+            const int e = threadIdx.x + qq * nthr;
+            if (e < cnt) {
+                const uint32_t word = (uint32_t)kr[qq], fl = word & kKeyBlended;
+                uint32_t rec = word & kKeyRecord;
+                if (rec >= R) rec = 0; // only after a capacity overflow
+                if (fl) { // pairs that no pixel blended are never read
+                    const float4 *src = w.rec + 3 * (size_t)rec;
+                    cp_async16(buf + e, src);
+                    cp_async16(buf + B + e, src + 1);
+                    cp_async16(buf + 2 * B + e, src + 2);
+                    pb[e] = pqb[lo + e];
+                }
+                ib[e] = rec | fl;
+            }
+        }
+    };
+    if (nb > 0) {
+        load_keys(0);
+        issue(0);
+        cp_async_commit();
+        load_keys(1);
+    }
+    const unsigned lt = (1u << lane) - 1u;
+    for (int b = 0; b < nb; ++b) {
+        if (b + 1 < nb) issue(b + 1);
+        cp_async_commit();
+        if (b + 2 < nb) load_keys(b + 2);
+        const int32_t lo = lo_of(b), cnt = hi_of(b) - lo;
+        for (int k = threadIdx.x; k < cnt * kAccStride; k += nthr) acc[k] = 0.0f;
+        cp_async_wait<1>();
+        __syncthreads();
+        const uint32_t *ibc = sidx + (b & 1) * B;
+        const uint32_t *pbc = spq + (b & 1) * B;
+        if (threadIdx.x < 32) { // the batch's blended entries, in list order
+            uint32_t base = 0;
+            for (int c0 = 0; c0 < cnt; c0 += 32) {
+                const int k = c0 + lane;
+                const bool f = k < cnt && (ibc[k] & kKeyBlended);
+                const unsigned bal = __ballot_sync(0xffffffffu, f);
+                if (f) clist[base + __popc(bal & lt)] = (uint32_t)k;
+                base += __popc(bal);
+            }
+            if (lane == 0) clist[B] = base;
+        }
+        __syncthreads();
+        const int ncl = (int)clist[B];
+        // this warp's quarter lists: the blended entries each quarter blended
+        int len[4] = {0, 0, 0, 0};
+        for (int c0 = 0; c0 < ncl; c0 += 32) {
+            const int i = c0 + lane;
+            const uint32_t k = i < ncl ? clist[i] : 0u;
+            const uint32_t qb = i < ncl ? (pbc[k] >> (8 * warp)) & 15u : 0u;
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                const bool hit = (qb >> qq) & 1u;
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                if (hit) ql[qq * qs + len[qq] + __popc(bal & lt)] = (uint8_t)k;
+                len[qq] += __popc(bal);
+            }
+        }
+        __syncwarp();
+        const int mylen = q == 0 ? len[0] : q == 1 ? len[1] : q == 2 ? len[2] : len[3];
+        const int maxlen = max(max(len[0], len[1]), max(len[2], len[3]));
+        const uint8_t *myl = ql + q * qs;
+        const float4 *s0 = sm + (b & 1) * 3 * B, *s1 = s0 + B, *s2 = s0 + 2 * B;
+        // groups of kGroup entries per quarter, back to front: falloff and
+        // alpha first (independent of T), then the sequential transmittance
+        // rebuild and gradients, then one quarter reduction of the group's
+        // 10 x kGroup sums
+        for (int s = 0; s < maxlen; s += kGroup) {
+            int kk[kGroup]; // batch entries of the group (-1: past this quarter's list)
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u) kk[u] = s + u < mylen ? (int)myl[mylen - 1 - s - u] : -1;
+            float g[32];
+#pragma unroll
+            for (int x = 0; x < 32; ++x) g[x] = 0.f;
+            bool contrib = false;
+            float ar[kGroup][2], ex[kGroup][2], dxs[kGroup][2], dys[kGroup];
+            bool ok[kGroup][2];
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u) {
+                const int k = kk[u], ks = k < 0 ? 0 : k;
+                const float4 a = s0[ks];
+                const float4 qv = s1[ks];
+                const float dy = __fsub_rn(a.y, pyc);
+                const float2 dx2 = __fadd2_rn(make_float2(a.x, a.x), npx2); // = a.x - pxc
+                const float2 p2 = gauss_power2(qv.x, qv.y, qv.z, dx2, dy);
+                dxs[u][0] = dx2.x;
+                dxs[u][1] = dx2.y;
+                dys[u] = dy;
+                const float pw[2] = {p2.x, p2.y};
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    ex[u][p] = __expf(pw[p]);
+                    ar[u][p] = __fmul_rn(qv.w, ex[u][p]); // = raw_alpha(qv.w, power)
+                    ok[u][p] = k >= 0 && (uint32_t)(lo + k) < last[p] && fabsf(dxs[u][p]) <= a.z &&
+                               fabsf(dy) <= a.w && pw[p] <= 0.0f && fminf(kAlphaMax, ar[u][p]) >= kAlphaMin;
+                    if (!ok[u][p]) ex[u][p] = 0.f; // finite where a zero weight multiplies it
+                }
+            }
+            // every pixel of the group: a pixel that the pair does not reach
+            // gets alpha = 0 and adds exact zeros
+            float2 G[kGroup][10];
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u)
+#pragma unroll
+                for (int x = 0; x < 10; ++x) G[u][x] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u) {
+                const int ks = kk[u] < 0 ? 0 : kk[u];
+                const float4 qv = s1[ks];
+                const float4 c = s2[ks];
+                if (!(ok[u][0] || ok[u][1])) continue;
+                contrib = true;
+                const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y), cz = make_float2(c.z, c.z),
+                             az = make_float2(c.w, c.w);
+                const float2 qx = make_float2(qv.x, qv.x), qy = make_float2(qv.y, qv.y);
+                const float2 nal = make_float2(ok[u][0] ? -fminf(kAlphaMax, ar[u][0]) : 0.f,
+                                               ok[u][1] ? -fminf(kAlphaMax, ar[u][1]) : 0.f);
+                const float2 om = __fadd2_rn(make_float2(1.f, 1.f), nal);
+                const float2 iom = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
+                const float2 Ti = __fmul2_rn(T2, iom);
+                const float2 nwgt = __fmul2_rn(nal, Ti);
+                G[u][6] = __ffma2_rn(nwgt, dc0, G[u][6]);
+                G[u][7] = __ffma2_rn(nwgt, dc1, G[u][7]);
+                G[u][8] = __ffma2_rn(nwgt, dc2, G[u][8]);
+                G[u][9] = __ffma2_rn(nwgt, dd, G[u][9]);
+                const float2 dcc = __ffma2_rn(dd, az, __ffma2_rn(dc2, cz, __ffma2_rn(dc1, cy, __fmul2_rn(dc0, cx))));
+                const float2 dal = __ffma2_rn(ndcs, iom, __fmul2_rn(dcc, Ti));
+                ndcs = __ffma2_rn(nwgt, dcc, ndcs);
+                T2 = Ti;
+                // the 0.99 clamp passes no gradient to opacity and footprint
+                const float2 dalm = make_float2(ar[u][0] < kAlphaMax ? dal.x : 0.f, ar[u][1] < kAlphaMax ? dal.y : 0.f);
+                const float2 dx = make_float2(dxs[u][0], dxs[u][1]);
+                const float dy1 = dys[u];
+                G[u][5] = __ffma2_rn(dalm, make_float2(ex[u][0], ex[u][1]), G[u][5]);
+                const float2 ngp = __fmul2_rn(dalm, nal); // -dL/dalpha * alpha
+                // w = Q d (Q the conic): dpower/dd = -w and dpower/dSigma2 = w w^T / 2
+                const float qyd = qv.y * dy1, qzd = qv.z * dy1;
+                const float2 wxv = __ffma2_rn(qx, dx, make_float2(qyd, qyd));
+                const float2 wyv = __ffma2_rn(qy, dx, make_float2(qzd, qzd));
+                G[u][0] = __ffma2_rn(ngp, wxv, G[u][0]);
+                G[u][1] = __ffma2_rn(ngp, wyv, G[u][1]);
+                const float2 nhw = __fmul2_rn(__fmul2_rn(ngp, make_float2(-0.5f, -0.5f)), wxv);
+                G[u][2] = __ffma2_rn(nhw, wxv, G[u][2]);
+                G[u][3] = __ffma2_rn(nhw, wyv, G[u][3]);
+                G[u][4] = __ffma2_rn(__fmul2_rn(__fmul2_rn(ngp, make_float2(-0.5f, -0.5f)), wyv), wyv, G[u][4]);
+            }
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u) {
+#pragma unroll
+                for (int x = 0; x < 6; ++x) g[10 * u + x] = G[u][x].x + G[u][x].y;
+#pragma unroll
+                for (int x = 6; x < 10; ++x) g[10 * u + x] = -(G[u][x].x + G[u][x].y);
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+                quarter_transpose_sum32(g);
+                // lane 8q + mq holds the quarter's sums of g[4 mq .. 4 mq + 3]
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int x = 4 * mq + j, u = x / 10, comp = x - 10 * u;
+                    const int k = u == 0 ? kk[0] : u == 1 ? kk[1] : u == 2 ? kk[2] : -1;
+                    if (x < 10 * kGroup && k >= 0 && g[j] != 0.0f) atomicAdd(acc + k * kAccStride + comp, g[j]);
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < ncl; i += nthr) {
+            const int k = (int)clist[i];
+            const float4 *ak = reinterpret_cast<const float4 *>(acc + k * kAccStride);
+            const float4 x0 = ak[0], x1 = ak[1], x2 = ak[2];
+            if (x0.x != 0.f || x0.y != 0.f || x0.z != 0.f || x0.w != 0.f || x1.x != 0.f || x1.y != 0.f ||
+                x1.z != 0.f || x1.w != 0.f || x2.x != 0.f || x2.y != 0.f) {
+                float4 *dst = reinterpret_cast<float4 *>(w.d_rec + (size_t)(ibc[k] & kKeyRecord) * kGradStride);
+                atomicAdd(dst + 0, x0);
+                atomicAdd(dst + 1, x1);
+                atomicAdd(dst + 2, x2);
+            }
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+}
+
 // Overwrite mode: every gradient row is first set to zero (the preprocess
 // backward then writes the rows of the Gaussians some view sees).  The clearing
 // is split into items of kZeroFloats floats that the persistent blend-backward
@@ -462,12 +786,16 @@ __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, 
 {
     extern __shared__ float4 smem_b[];
     __shared__ uint32_t smax_last, item;
+    constexpr bool Q = PX == 2 && PY == 1; // quarter lists (blendq_backward_tile)
     const int B = w.tb->batch_depth;
     float *acc = reinterpret_cast<float *>(smem_b + 2 * 3 * B); // [B][kAccStride]
     uint32_t *sidx = reinterpret_cast<uint32_t *>(acc + B * kAccStride); // [2][B]
     uint32_t *clist = sidx + 2 * B;                                        // [B + 1]
-    // zeros for the clearing items' bulk copies (16-byte aligned, after clist)
-    const uint32_t zoff = ((uint32_t)(reinterpret_cast<char *>(clist + B + 1) - reinterpret_cast<char *>(smem_b)) +
+    uint32_t *spq = clist + B + 1;                                         // Q: [2][B] quarter bits
+    uint8_t *qls = reinterpret_cast<uint8_t *>(spq + (Q ? 2 * B : 0));     // Q: per warp 4 quarter lists
+    const int qbytes = Q ? (int)(blockDim.x >> 5) * 4 * qlist_stride(B) : 0;
+    // zeros for the clearing items' bulk copies (16-byte aligned, after the lists)
+    const uint32_t zoff = ((uint32_t)(reinterpret_cast<char *>(qls + qbytes) - reinterpret_cast<char *>(smem_b)) +
                            15u) & ~15u;
     float4 *zbuf = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem_b) + zoff);
     const uint32_t zbuf_saddr = (uint32_t)__cvta_generic_to_shared(zbuf);
@@ -503,13 +831,22 @@ __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, 
                 else hi = mid - 1;
             }
             const uint32_t s = item - w.heavy_seg[lo];
-            blend_backward_tile<PX, PY>(w, cams, d_rgb, d_depth, (int)w.heavy[lo], s * kSeg, (s + 1) * kSeg,
-                                        (int64_t)w.heavy_seg[lo] + s, smem_b, acc, sidx, clist, &smax_last);
+            if constexpr (Q)
+                blendq_backward_tile(w, cams, d_rgb, d_depth, (int)w.heavy[lo], s * kSeg, (s + 1) * kSeg,
+                                     (int64_t)w.heavy_seg[lo] + s, smem_b, acc, sidx, clist, spq, qls, &smax_last);
+            else
+                blend_backward_tile<PX, PY>(w, cams, d_rgb, d_depth, (int)w.heavy[lo], s * kSeg, (s + 1) * kSeg,
+                                            (int64_t)w.heavy_seg[lo] + s, smem_b, acc, sidx, clist, &smax_last);
         } else {
             const uint32_t b = item - nhi;
-            if (w.bin_count[b] + w.bin_fcount[b] < w.hdr->heavy_min)
-                blend_backward_tile<PX, PY>(w, cams, d_rgb, d_depth, (int)b, 0u, 0xffffffffu, 0, smem_b, acc, sidx,
-                                            clist, &smax_last);
+            if (w.bin_count[b] + w.bin_fcount[b] < w.hdr->heavy_min) {
+                if constexpr (Q)
+                    blendq_backward_tile(w, cams, d_rgb, d_depth, (int)b, 0u, 0xffffffffu, 0, smem_b, acc, sidx,
+                                         clist, spq, qls, &smax_last);
+                else
+                    blend_backward_tile<PX, PY>(w, cams, d_rgb, d_depth, (int)b, 0u, 0xffffffffu, 0, smem_b, acc,
+                                                sidx, clist, &smax_last);
+            }
         }
     }
     for (;;) { // clearing items left when the tiles ran out
@@ -876,10 +1213,12 @@ void launch_count_visible(const Ws &w, int64_t n_words, cudaStream_t s)
     count_visible_kernel<<<256, 256, 0, s>>>(w, n_words);
 }
 
-static int blend_bwd_smem(int batch_depth)
+// q_warps: warps of a quarter-list CTA (2 x 1 pixels per lane), else 0
+static int blend_bwd_smem(int batch_depth, int q_warps)
 {
-    const int base = 2 * 3 * batch_depth * (int)sizeof(float4) + batch_depth * kAccStride * 4 + 2 * batch_depth * 4 +
-                     (batch_depth + 1) * 4;
+    int base = 2 * 3 * batch_depth * (int)sizeof(float4) + batch_depth * kAccStride * 4 + 2 * batch_depth * 4 +
+               (batch_depth + 1) * 4;
+    if (q_warps) base += 2 * batch_depth * 4 + q_warps * 4 * qlist_stride(batch_depth);
     return ((base + 15) & ~15) + kZeroBuf;
 }
 
@@ -887,7 +1226,7 @@ template <int PX, int PY>
 static void launch_bb(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,
                       int threads, int batch_depth, int n_sms, const ZeroWork &zw, cudaStream_t s)
 {
-    const int smem = blend_bwd_smem(batch_depth);
+    const int smem = blend_bwd_smem(batch_depth, PX == 2 && PY == 1 ? threads / 32 : 0);
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blend_backward_kernel<PX, PY>, threads, smem);
     int grid = n_sms * (nb > 0 ? nb : 1);
@@ -960,7 +1299,7 @@ void launch_preprocess_backward(const gs_gaussians *g, const gs_camera *cams, co
 
 cudaError_t configure_backward_kernels()
 {
-    const int smem = blend_bwd_smem(256);
+    const int smem = blend_bwd_smem(256, 8);
     cudaError_t e = cudaFuncSetAttribute(blend_backward_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(blend_backward_kernel<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

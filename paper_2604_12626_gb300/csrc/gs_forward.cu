@@ -1040,6 +1040,287 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
     }
 }
 
+// ---------------------------------------------------------------------------
+// blend at 2 x 1 pixels per lane, with a Gaussian list per 4 x 4 quarter
+// ---------------------------------------------------------------------------
+// The tile is cut into 8 x 8 blocks, one per warp (tile_w and tile_h are
+// multiples of 8), and every block into four 4 x 4 quarters of 8 lanes: lane
+// 8q + m owns the pixel pair at (2 (m & 1), m >> 1) of quarter q, whose origin
+// in the block is (4 (q & 1), 4 (q >> 1)).  The CTA stages each batch of the
+// tile's list in shared memory as before; then every warp lists, for each of
+// its quarters and in list order, the batch entries whose pixel window meets
+// the quarter, and the four quarters walk their own lists in lockstep -- a
+// Gaussian costs a quarter's lanes a step only where it can reach them, and
+// each pixel still sees every Gaussian that covers it, in depth order.  Per
+// pair, the quarters that blended it are kept (4 bits per warp) for the
+// backward, and bit 31 of the key marks a pair some pixel of the tile blended.
+constexpr int kQuarterSlack = 0; // (documentation only: window tests carry 0.01 px + 1e-6 |uc| of slack)
+
+// Lists, per quarter of this warp's block, the entries [0, cnt) of the staged
+// batch whose pixel window [uc - hx, uc + hx] x [vc - hy, vc + hy] meets the
+// quarter's pixel centres; returns the four lengths.
+__device__ __forceinline__ void build_quarter_lists(const float4 *s0, int cnt, const float (&qx0)[4],
+                                                    const float (&qy0)[4], uint8_t *ql, int qs, int (&len)[4])
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) len[q] = 0;
+    for (int e0 = 0; e0 < cnt; e0 += 32) {
+        const int e = e0 + lane;
+        const float4 a = s0[e < cnt ? e : 0];
+        const float sx = 0.01f + 1e-6f * fabsf(a.x), sy = 0.01f + 1e-6f * fabsf(a.y);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            // quarter q covers pixel centres [qx0, qx0 + 3] x [qy0, qy0 + 3]
+            const bool hit = e < cnt && a.x - a.z <= qx0[q] + 3.0f + sx && a.x + a.z >= qx0[q] - sx &&
+                             a.y - a.w <= qy0[q] + 3.0f + sy && a.y + a.w >= qy0[q] - sy;
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            if (hit) ql[q * qs + len[q] + __popc(bal & lt)] = (uint8_t)e;
+            len[q] += __popc(bal);
+        }
+    }
+    __syncwarp();
+}
+
+template <bool COUNT>
+__device__ __forceinline__ void blendq_tile(const Ws &w, const gs_camera *cams, const OutPtrs &o, int bin, int heavy,
+                                           float4 *sm, uint8_t *qls, uint32_t *wbs)
+{
+    const Table *tb = w.tb;
+    const int v = bin / tb->tiles_per_view;
+    const int t = bin - v * tb->tiles_per_view;
+    const int tyi = t / tb->tiles_x, txi = t - tyi * tb->tiles_x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int q = lane >> 3, m = lane & 7;
+    const int wx = tb->tile_w >> 3;
+    const int tx0 = txi * tb->tile_w, ty0 = tyi * tb->tile_h;
+    const int bx = tx0 + (warp % wx) * 8, by = ty0 + (warp / wx) * 8; // this warp's block
+    const int i0 = bx + (q & 1) * 4 + (m & 1) * 2, j0 = by + (q >> 1) * 4 + (m >> 1);
+    const int W = tb->W, H = tb->H;
+    const gs_camera &cam = cams[v];
+    const float pyc = pix_c(j0, cam.cy);
+    const float2 npx2 = make_float2(-pix_c(i0, cam.cx), -pix_c(i0 + 1, cam.cx));
+    float qx0[4], qy0[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        qx0[k] = pix_c(bx + (k & 1) * 4, cam.cx);
+        qy0[k] = pix_c(by + (k >> 1) * 4, cam.cy);
+    }
+    const int B = tb->batch_depth;
+    const int qs = qlist_stride(B);
+    uint8_t *ql = qls + warp * 4 * qs;
+    uint32_t *wb = wbs + warp * B; // quarters of this warp that blended each batch entry
+    uint32_t start, n;
+    bin_range(w, bin, start, n);
+    unsigned long long *keys = w.keys + start;
+    const int nthr = blockDim.x;
+    const uint32_t R = (uint32_t)tb->n_records;
+    const int nb = (int)((n + B - 1) / B);
+    unsigned long long kr[kMaxPer];
+    auto load_keys = [&](int b) {
+#pragma unroll
+        for (int qq = 0; qq < kMaxPer; ++qq) {
+            const int e = threadIdx.x + qq * nthr;
+            const uint32_t idx = (uint32_t)b * B + e;
+            kr[qq] = (b < nb && e < B && idx < n) ? keys[idx] : 0ull;
+        }
+    };
+    auto issue = [&](int b) {
+        float4 *buf = sm + (b & 1) * 3 * B;
+#pragma unroll
+        for (int qq = 0; qq < kMaxPer; ++qq) {
+            const int e = threadIdx.x + qq * nthr;
+            const uint32_t idx = (uint32_t)b * B + e;
+            if (e < B && idx < n) {
+                uint32_t rec = (uint32_t)kr[qq] & kKeyRecord;
+                if (rec >= R) rec = 0; // only after a capacity overflow
+                const float4 *src = w.rec + 3 * (size_t)rec;
+                cp_async16(buf + e, src);
+                cp_async16(buf + B + e, src + 1);
+                cp_async16(buf + 2 * B + e, src + 2);
+            }
+        }
+    };
+    float T[2], C0[2], C1[2], C2[2], D[2];
+    int32_t ncov[2], ncovl[2], ncon[2]; // ncov, ncovl: only with COUNT
+    uint32_t last[2];
+    bool dn[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        T[p] = 1.0f; C0[p] = C1[p] = C2[p] = D[p] = 0.0f;
+        ncov[p] = ncovl[p] = ncon[p] = 0;
+        last[p] = 0;
+        dn[p] = !(i0 + p < W && j0 < H);
+    }
+    bool tdone = dn[0] && dn[1];
+    for (int e = lane; e < B; e += 32) wb[e] = 0u;
+    if (nb > 0) {
+        load_keys(0);
+        issue(0);
+        cp_async_commit();
+        load_keys(1);
+    }
+    const int tpx = tb->tile_w * tb->tile_h;
+    const int lpx = (j0 - ty0) * tb->tile_w + (i0 - tx0); // tile-local index of the first pixel
+    const uint32_t ck_base = heavy >= 0 ? w.heavy_seg[heavy] : 0u;
+    for (int b = 0; b < nb; ++b) {
+        if (heavy >= 0 && b > 0 && ((uint32_t)b * B) % kSeg == 0) {
+            // checkpoint before list position b B, for the backward's segments
+            const size_t slot = (size_t)(ck_base + ((uint32_t)b * B) / kSeg - 1) * tpx;
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                w.ck_C[slot + lpx + p] = make_float4(T[p], C0[p], C1[p], C2[p]);
+                w.ck_D[slot + lpx + p] = D[p];
+            }
+        }
+        if (b + 1 < nb) issue(b + 1);
+        cp_async_commit();
+        if (b + 2 < nb) load_keys(b + 2);
+        cp_async_wait<1>();
+        if (__syncthreads_count(tdone) == nthr) break;
+        const float4 *s0 = sm + (b & 1) * 3 * B, *s1 = s0 + B, *s2 = s0 + 2 * B;
+        const int cnt = (int)min((uint32_t)B, n - (uint32_t)b * B);
+        int len[4];
+        build_quarter_lists(s0, cnt, qx0, qy0, ql, qs, len);
+        const int mylen = q == 0 ? len[0] : q == 1 ? len[1] : q == 2 ? len[2] : len[3];
+        const int maxlen = max(max(len[0], len[1]), max(len[2], len[3]));
+        const uint8_t *myl = ql + q * qs;
+#pragma unroll 1
+        for (int k0 = 0; k0 < maxlen; k0 += kUnroll) {
+            if (__all_sync(0xffffffffu, tdone || k0 >= mylen)) break;
+            // this quarter's next kUnroll entries (past its list's end: entry 0, not covered)
+            const uint2 id8 = *reinterpret_cast<const uint2 *>(myl + k0);
+            int idx[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const uint32_t word = u < 4 ? id8.x : id8.y;
+                idx[u] = k0 + u < mylen ? (int)((word >> (8 * (u & 3))) & 0xffu) : 0;
+            }
+            uint32_t m8 = 0; // bit u: this lane blended its quarter's entry k0 + u
+            if (!tdone && k0 < mylen) {
+                float al[kUnroll][2];
+                bool ok[kUnroll][2], cv[kUnroll][2];
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    const float4 a = s0[idx[u]];
+                    const float4 qv = s1[idx[u]];
+                    const float dy = __fsub_rn(a.y, pyc);
+                    const float2 dx2 = __fadd2_rn(make_float2(a.x, a.x), npx2); // = a.x - pxc
+                    const float2 pw = gauss_power2(qv.x, qv.y, qv.z, dx2, dy);
+                    const float2 ar = __fmul2_rn(make_float2(qv.w, qv.w), make_float2(__expf(pw.x), __expf(pw.y)));
+                    const bool inl = k0 + u < mylen && fabsf(dy) <= a.w;
+                    cv[u][0] = inl && fabsf(dx2.x) <= a.z;
+                    cv[u][1] = inl && fabsf(dx2.y) <= a.z;
+                    al[u][0] = fminf(kAlphaMax, ar.x);
+                    al[u][1] = fminf(kAlphaMax, ar.y);
+                    ok[u][0] = cv[u][0] && pw.x <= 0.0f && al[u][0] >= kAlphaMin;
+                    ok[u][1] = cv[u][1] && pw.y <= 0.0f && al[u][1] >= kAlphaMin;
+                }
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    const float4 c = s2[idx[u]];
+                    const float z = c.w;
+                    // both pixels as packed pairs, branch-free: a pixel that does not
+                    // blend this Gaussian gets weight 0 (C + c 0 = C, T (1 - 0) = T)
+                    const uint32_t pos = (uint32_t)b * B + idx[u] + 1;
+                    const bool a0 = !dn[0] && cv[u][0], a1 = !dn[1] && cv[u][1];
+                    if constexpr (COUNT) {
+                        ncov[0] += a0;
+                        ncov[1] += a1;
+                    }
+                    const bool k0k = a0 && ok[u][0], k1k = a1 && ok[u][1];
+                    const float2 T2 = make_float2(T[0], T[1]);
+                    const float2 om = __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-al[u][0], -al[u][1]));
+                    const float2 Tn = __fmul2_rn(T2, om);
+                    const bool s0b = k0k && Tn.x < kTStop, s1b = k1k && Tn.y < kTStop;
+                    const bool bl0 = k0k && !s0b, bl1 = k1k && !s1b;
+                    m8 |= (uint32_t)(bl0 || bl1) << u;
+                    dn[0] = dn[0] || s0b;
+                    dn[1] = dn[1] || s1b;
+                    const float2 wgt = __fmul2_rn(make_float2(bl0 ? al[u][0] : 0.0f, bl1 ? al[u][1] : 0.0f), T2);
+                    const float2 c0 = __ffma2_rn(make_float2(c.x, c.x), wgt, make_float2(C0[0], C0[1]));
+                    const float2 c1 = __ffma2_rn(make_float2(c.y, c.y), wgt, make_float2(C1[0], C1[1]));
+                    const float2 c2 = __ffma2_rn(make_float2(c.z, c.z), wgt, make_float2(C2[0], C2[1]));
+                    const float2 dd = __ffma2_rn(make_float2(z, z), wgt, make_float2(D[0], D[1]));
+                    C0[0] = c0.x; C0[1] = c0.y;
+                    C1[0] = c1.x; C1[1] = c1.y;
+                    C2[0] = c2.x; C2[1] = c2.y;
+                    D[0] = dd.x; D[1] = dd.y;
+                    T[0] = bl0 ? Tn.x : T[0];
+                    T[1] = bl1 ? Tn.y : T[1];
+                    ncon[0] += bl0;
+                    ncon[1] += bl1;
+                    if constexpr (COUNT) {
+                        ncovl[0] = bl0 ? ncov[0] : ncovl[0];
+                        ncovl[1] = bl1 ? ncov[1] : ncovl[1];
+                    }
+                    last[0] = bl0 ? pos : last[0];
+                    last[1] = bl1 ? pos : last[1];
+                }
+                tdone = dn[0] && dn[1];
+            }
+            // the quarter's blended entries (OR over its 8 lanes): its first lane records them
+            uint32_t qm = m8;
+            qm |= __shfl_xor_sync(0xffffffffu, qm, 1);
+            qm |= __shfl_xor_sync(0xffffffffu, qm, 2);
+            qm |= __shfl_xor_sync(0xffffffffu, qm, 4);
+            if (m == 0 && qm) {
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u)
+                    if ((qm >> u) & 1u) atomicOr(wb + idx[u], 1u << q);
+            }
+        }
+        __syncthreads();
+        // per batch entry: the quarters of every warp that blended it, and the
+        // key's blended bit when any did (this CTA alone touches the bin)
+        uint32_t *pq = w.pq + start + (uint32_t)b * B;
+        for (int e = threadIdx.x; e < cnt; e += nthr) {
+            uint32_t word = 0;
+            for (int ww = 0; ww < nwarps; ++ww) word |= wbs[ww * B + e] << (8 * ww);
+            if (word) {
+                pq[e] = word;
+                reinterpret_cast<uint32_t *>(keys + (uint32_t)b * B + e)[0] |= kKeyBlended;
+            }
+        }
+        __syncthreads();
+        for (int e = lane; e < cnt; e += 32) wb[e] = 0u;
+    }
+    cp_async_wait<0>();
+    if constexpr (COUNT) {
+        unsigned long long ev = (uint32_t)ncov[0] + (uint32_t)ncov[1], el = (uint32_t)ncovl[0] + (uint32_t)ncovl[1];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            ev += __shfl_xor_sync(0xffffffffu, ev, off);
+            el += __shfl_xor_sync(0xffffffffu, el, off);
+        }
+        if (lane == 0) {
+            atomicAdd(&w.hdr->n_evals, ev);
+            atomicAdd(&w.hdr->n_cov, el);
+        }
+    }
+    const size_t HW = (size_t)W * H;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int i = i0 + p, j = j0;
+        if (i < W && j < H) {
+            const size_t px = (size_t)j * W + i;
+            o.rgb[(3 * (size_t)v + 0) * HW + px] = C0[p] + T[p] * tb->bg[0];
+            o.rgb[(3 * (size_t)v + 1) * HW + px] = C1[p] + T[p] * tb->bg[1];
+            o.rgb[(3 * (size_t)v + 2) * HW + px] = C2[p] + T[p] * tb->bg[2];
+            float dd = D[p];
+            if (tb->flags & GS_FLAG_NORMALIZE_DEPTH) dd = (1.0f - T[p]) < 1e-4f ? 0.0f : D[p] / (1.0f - T[p]);
+            o.depth[(size_t)v * HW + px] = dd;
+            o.T[(size_t)v * HW + px] = T[p];
+            o.ncontrib[(size_t)v * HW + px] = ncon[p];
+            w.pix_T[(size_t)v * HW + px] = T[p];
+            w.pix_last[(size_t)v * HW + px] = last[p];
+            w.pix_C[(size_t)v * HW + px] = make_float4(C0[p] + T[p] * tb->bg[0], C1[p] + T[p] * tb->bg[1],
+                                                       C2[p] + T[p] * tb->bg[2], D[p]);
+        }
+    }
+}
+
 // The blend loop reads kUnroll slots at a time, up to kUnroll - 1 past a
 // batch's end (batch depths need not be multiples of kUnroll): the two batch
 // buffers are followed by kUnroll padding slots, and all slots must hold finite
@@ -1088,20 +1369,46 @@ __global__ void blend_persistent_kernel(const gs_camera *__restrict__ cams, Ws w
     blend_persistent<PX, PY, COUNT>(cams, w, o);
 }
 
-// 2 x 1 pixels per thread with a register budget of 88 (23 warps per SM); left
-// to itself the compiler takes 110 for the persistent variant (18 warps).
-constexpr int kBlend21Regs = 88;
-template <bool COUNT>
-__global__ void __maxnreg__(kBlend21Regs) blend21_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
+// 2 x 1 pixels per lane: the quarter-list kernels.  Shared memory: the two
+// batch buffers, then per warp four quarter lists (qlist_stride(B) bytes each)
+// and B words of blended-quarter bits.
+__device__ __forceinline__ void blendq_smem(float4 *smem, int B, int nwarps, uint8_t *&qls, uint32_t *&wbs)
 {
-    blend_one<2, 1, COUNT>(cams, w, o);
+    qls = reinterpret_cast<uint8_t *>(smem + 2 * 3 * B + kUnroll);
+    wbs = reinterpret_cast<uint32_t *>(qls + nwarps * 4 * qlist_stride(B));
 }
 
 template <bool COUNT>
-__global__ void __maxnreg__(kBlend21Regs) blend21_persistent_kernel(const gs_camera *__restrict__ cams, Ws w,
-                                                                    OutPtrs o)
+__global__ void __launch_bounds__(256) blendq_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
 {
-    blend_persistent<2, 1, COUNT>(cams, w, o);
+    extern __shared__ float4 smem_f4[];
+    const int B = w.tb->batch_depth;
+    uint8_t *qls;
+    uint32_t *wbs;
+    blendq_smem(smem_f4, B, blockDim.x >> 5, qls, wbs);
+    clear_batch_buffers(smem_f4, B);
+    blendq_tile<COUNT>(w, cams, o, blockIdx.x, w.heavy_of[blockIdx.x], smem_f4, qls, wbs);
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(256) blendq_persistent_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
+{
+    extern __shared__ float4 smem_f4[];
+    __shared__ uint32_t item;
+    const int B = w.tb->batch_depth;
+    uint8_t *qls;
+    uint32_t *wbs;
+    blendq_smem(smem_f4, B, blockDim.x >> 5, qls, wbs);
+    clear_batch_buffers(smem_f4, B);
+    const uint32_t n_items = (uint32_t)w.tb->n_bins + w.hdr->n_heavy;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item = atomicAdd(&w.hdr->queue, 1u);
+        __syncthreads();
+        if (item >= n_items) break;
+        const int bin = bin_of_item(w, item);
+        if (bin >= 0) blendq_tile<COUNT>(w, cams, o, bin, item < w.hdr->n_heavy ? (int)item : -1, smem_f4, qls, wbs);
+    }
 }
 
 // the kernels of one (PX, PY, COUNT) variant
@@ -1110,8 +1417,8 @@ template <int PX, int PY, bool COUNT> struct BlendKernels {
     static constexpr auto persistent = blend_persistent_kernel<PX, PY, COUNT>;
 };
 template <bool COUNT> struct BlendKernels<2, 1, COUNT> {
-    static constexpr auto one = blend21_kernel<COUNT>;
-    static constexpr auto persistent = blend21_persistent_kernel<COUNT>;
+    static constexpr auto one = blendq_kernel<COUNT>;
+    static constexpr auto persistent = blendq_persistent_kernel<COUNT>;
 };
 
 // ---------------------------------------------------------------------------
@@ -1153,13 +1460,18 @@ void launch_scatter(const gs_camera *cams, const Ws &w, int n_chunks, cudaStream
     if (n_chunks) scatter_kernel<<<n_chunks, 256, kScatterSmem, s>>>(cams, w);
 }
 
-int blend_smem_bytes(int batch_depth) { return (2 * 3 * batch_depth + kUnroll) * (int)sizeof(float4); }
+// q_warps: warps of a quarter-list CTA (2 x 1 pixels per lane), else 0
+int blend_smem_bytes(int batch_depth, int q_warps)
+{
+    return (2 * 3 * batch_depth + kUnroll) * (int)sizeof(float4) +
+           q_warps * (4 * qlist_stride(batch_depth) + 4 * batch_depth);
+}
 
 template <int PX, int PY, bool COUNT>
 static void launch_blend_c(const gs_camera *cams, const Ws &w, const OutPtrs &o, int n_bins, int threads,
                            int batch_depth, bool persistent, int n_sms, cudaStream_t s)
 {
-    const int smem = blend_smem_bytes(batch_depth);
+    const int smem = blend_smem_bytes(batch_depth, PX == 2 && PY == 1 ? threads / 32 : 0);
     using K = BlendKernels<PX, PY, COUNT>;
     if (persistent) {
         int nb = 0;

@@ -17,6 +17,8 @@
 //   scratch     [P_cap] uint64, ping-pong buffer of the large-bin merges
 //   pix_T       [V*H*W] final transmittance (saved for the backward)
 //   pix_last    [V*H*W] 1 + tile-list position of the last blended pair
+//   pq          [P_cap] uint32 (2 x 1 pixels per lane only): per sorted pair,
+//               byte w holds the 4 x 4 quarters of warp w that blended it
 //   d_rec       [R] 16 floats (64 B, one DRAM burst): dL/d(uc, vc), the 2D
 //               covariance gradient dL/dSigma2 (xx, xy, yy; xy = half of the
 //               off-diagonal entry's derivative), dL/d(opacity, r, g, b, z),
@@ -127,7 +129,12 @@ struct Ws {
     float *pix_T;
     uint32_t *pix_last;
     float *d_rec; // kGradStride floats per record
+    uint32_t *pq; // [P_cap] at 2 x 1 pixels per lane: per pair, byte w = the quarters of warp w that blended it
 };
+
+// Bytes of one quarter list in shared memory (2 x 1 pixels per lane): batch
+// entries as uint8, read 8 at a time.
+__host__ __device__ __forceinline__ int qlist_stride(int B) { return (B + 15) & ~15; }
 
 constexpr int kSeg = 2048;       // backward segment of a heavy bin (a multiple of every batch depth)
 constexpr int kHeavyMin = 1024;  // pairs from which a bin may be scheduled first

@@ -57,7 +57,8 @@ def _check_keys(r, cams, W, H, view_of_rec):
     n_bins = s["n_bins"]
     assert np.array_equal(np.diff(bs), counts[:n_bins]), "bin counts (tile ranges) differ"
     assert np.array_equal(keys, ref), "sorted keys differ"
-    _check_blended_flags(rec, keys, blended.astype(bool), bs, cams, W, H, r.cfg.tile_w, r.cfg.tile_h)
+    quarters = s["quarters"].cpu().numpy().view(np.uint32)[:bs[-1]] if s["quarters"] is not None else None
+    _check_blended_flags(rec, keys, blended.astype(bool), bs, cams, W, H, r.cfg.tile_w, r.cfg.tile_h, quarters)
     _check_window(rec, vis, view_of_rec, cams, W, H)
     return int(bs[-1])
 
@@ -99,10 +100,12 @@ def _check_window(rec, vis, view_of_rec, cams, W, H, sample=4000):
         assert not np.any(reach & outside), ("window cuts a pixel that can blend", int(idx[k]))
 
 
-def _check_blended_flags(rec, keys, blended, bs, cams, W, H, tw, th, sample=20000):
+def _check_blended_flags(rec, keys, blended, bs, cams, W, H, tw, th, quarters=None, sample=20000):
     """A pair flagged as blended has, at some pixel of its tile and inside its
     pixel window, power <= 0 and alpha >= 1/255 (checked in FP64 with a small
-    margin on a sample of the flagged pairs)."""
+    margin on a sample of the flagged pairs).  With quarter bits (2 x 1 pixels
+    per thread), a flagged pair names at least one quarter, and every 4 x 4
+    quarter it names holds such a pixel."""
     assert blended.any(), "no pair flagged as blended"
     pos = np.flatnonzero(blended)
     pos = np.random.default_rng(0).choice(pos, min(sample, pos.size), replace=False)
@@ -122,6 +125,21 @@ def _check_blended_flags(rec, keys, blended, bs, cams, W, H, tw, th, sample=2000
     alpha = np.minimum(0.99, op[:, None, None] * np.exp(np.minimum(power, 0.0)))
     ok = inside & (power <= 1e-5) & (alpha >= (1.0 / 255.0) * (1.0 - 1e-4))
     assert ok.reshape(ok.shape[0], -1).any(axis=1).all(), "a pair flagged as blended reaches no pixel of its tile"
+    if quarters is None:
+        return
+    qw = quarters[pos]
+    assert np.all(qw != 0), "a pair flagged as blended names no quarter"
+    # ok[k, y, x] over the tile's pixels; quarter (w, q) covers block rows/cols
+    nbx = tw // 8
+    for w_ in range(nbx * (th // 8)):
+        for q in range(4):
+            sel = ((qw >> np.uint32(8 * w_ + q)) & np.uint32(1)).astype(bool)
+            if not sel.any():
+                continue
+            y0 = (w_ // nbx) * 8 + (q >> 1) * 4
+            x0 = (w_ % nbx) * 8 + (q & 1) * 4
+            blk = ok[sel][:, y0:y0 + 4, x0:x0 + 4].reshape(int(sel.sum()), -1)
+            assert blk.any(axis=1).all(), ("a quarter flagged as blended holds no pixel that can blend", w_, q)
 
 
 def test_box_scene_keys_bit_exact(gs):
@@ -155,6 +173,21 @@ def test_room_1m_keys_bit_exact(gs, room1m):
     r, out, _, _ = render_gpu(gs, g, cam[None], W, H)
     P = _check_keys(r, cam[None], W, H, np.zeros(g["means"].shape[0], np.int64))
     assert P > 100_000
+
+
+@pytest.mark.parametrize("tile,depth", [((8, 8), 64), ((16, 16), 128), ((16, 8), 36)])
+def test_quarter_lists_keys_and_flags(gs, tile, depth):
+    """2 x 1 pixels per thread (a Gaussian list per 4 x 4 quarter): keys and
+    tile ranges bit-exact, the blended flags and the quarter bits reach pixels
+    that can blend, and the images equal the one-pixel-per-thread path."""
+    g = synth.room_scene(300_000, seed=8)
+    W = H = 256
+    cam = synth.room_camera(8, W, H)
+    r, b, _, _ = render_gpu(gs, g, cam[None], W, H, tile=tile, batch_depth=depth, pix=(2, 1), persistent=True)
+    _check_keys(r, cam[None], W, H, np.zeros(g["means"].shape[0], np.int64))
+    _, a, _, _ = render_gpu(gs, g, cam[None], W, H, tile=tile, pix=(1, 1))
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
 
 
 @pytest.mark.parametrize("tile,depth,pix", [((8, 8), 64, (1, 1)), ((16, 8), 128, (1, 1)), ((32, 8), 256, (1, 1)),

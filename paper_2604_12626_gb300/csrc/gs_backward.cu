@@ -748,7 +748,10 @@ __device__ __forceinline__ void blendq_backward_tile(const Ws &w, const gs_camer
 // buffer (one thread issues them; the load/store pipeline the blend needs for
 // its shared-memory traffic stays free), the unaligned ends by plain stores.
 constexpr int64_t kZeroFloats = 1 << 16;
-constexpr int kZeroBuf = 1024; // bytes of zeros in shared memory (small: it costs no resident CTA)
+// Bytes of zeros in shared memory, the size of each bulk copy: 4 KB measured
+// fastest on GB300 (1 KB copies left the engine's issue rate on the critical
+// path, 8 KB and more cost resident CTAs).
+constexpr int kZeroBuf = 4096;
 
 __device__ __forceinline__ void bulk_zero(char *dst, uint32_t bytes, uint32_t zbuf_saddr, uint64_t policy)
 {

@@ -286,10 +286,11 @@ def tune_fwd_bwd(api, rend, G, cams, candidates, N, dev, reps=2):
 # FP32 lane operations per evaluation for the two blend kernels.
 OPS_PER_EVAL_FWD = 17   # offset, quadratic form, exp, alpha clamp / skip, T update, 3 colours + depth
 OPS_PER_EVAL_BWD = 40   # recomputed alpha, T_prev, dL/dalpha, conic / centre / colour / depth terms
-KERNEL_OF_STAGE = {"preprocess": "preprocess_kernel", "scan": "scan_bins_kernel", "scatter": "scatter_kernel",
-                   "sort_chunks": "sort_chunks_kernel", "merge": "merge_pass_kernel",
-                   "blend": "blend_persistent_kernel", "blend_backward": "blend_backward_kernel",
-                   "preprocess_backward": "preprocess_backward_kernel"}
+# the kernels of each stage (the blend at 2x1 pixels per thread is the quarter-list kernel)
+KERNELS_OF_STAGE = {"preprocess": ("preprocess_kernel",), "scan": ("scan_bins_kernel",),
+                    "scatter": ("scatter_kernel",), "sort": ("sort_chunks_kernel", "sort_small_kernel", "merge_pass_kernel"),
+                    "blend": ("blend_persistent_kernel", "blendq_persistent_kernel"),
+                    "blend_backward": ("blend_backward_kernel",), "preprocess_backward": ("preprocess_backward_kernel",)}
 CSRC = os.path.join(ROOT, "paper_2604_12626_gb300", "csrc")
 
 
@@ -318,7 +319,7 @@ def dram_traffic():
 
 
 FWD_KERNELS = ("setup_kernel", "preprocess_kernel", "scan_bins_kernel", "scatter_kernel", "sort_chunks_kernel",
-               "merge_pass_kernel", "blend_persistent_kernel")
+               "sort_small_kernel", "merge_pass_kernel", "blend_persistent_kernel", "blendq_persistent_kernel")
 BWD_KERNELS = ("clear_record_grads_kernel", "blend_backward_kernel", "preprocess_backward_kernel")
 
 
@@ -412,7 +413,6 @@ def rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_pix, N, sm_count, sm_mh
     ops = {"blend": OPS_PER_EVAL_FWD * n_eval_fwd, "blend_backward": OPS_PER_EVAL_BWD * n_eval_bwd}
     ms = dict(stage_ms)
     if "sort" in ms:
-        ms["sort_chunks"] = ms["sort"]
         ms["sort"] = ms["sort"] + ms.get("merge", 0.0)
     out = {}
     for k, b in mem.items():
@@ -427,9 +427,8 @@ def rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_pix, N, sm_count, sm_mh
                       "algorithmic": f, "ms": ms[k],
                       "peak_kind": f"derived: {sm_count} SMs x 128 FP32 lanes x {mhz:.0f} MHz"}
     for k, v in out.items():
-        kern = [KERNEL_OF_STAGE[x] for x in (("sort_chunks", "merge") if k == "sort" else (k,))]
-        tb = [traffic.get(x, {}).get("dram_bytes_per_call") for x in kern]
-        v["traffic"] = None if any(x is None for x in tb) else float(sum(tb))
+        tb = [traffic[x]["dram_bytes_per_call"] for x in KERNELS_OF_STAGE[k] if x in traffic]
+        v["traffic"] = float(sum(tb)) if tb else None
     for k, n_ev in (("blend", n_eval_fwd), ("blend_backward", n_eval_bwd)):
         if exp_rate and k in out:
             # one exp per evaluation, against the measured exp2 rate

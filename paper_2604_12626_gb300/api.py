@@ -385,10 +385,13 @@ class Renderer:
 
     def kernels_per_forward(self) -> int:
         """Kernel launches of one forward: setup, preprocess, scan, scatter,
-        sort, one merge pass per doubling of 4096 up to the pair capacity, blend."""
+        the two sorts, one merge pass per doubling of 4096 up to the largest
+        possible bin (the pair capacity or the most records of one view), blend."""
         cap = self.sections()["pair_capacity"]
-        chunks = -(-cap // 4096)
-        return 6 + max(0, (chunks - 1).bit_length())
+        offs = self.batch.env_offsets
+        max_view = max(int(offs[e + 1] - offs[e]) for e in self.batch.view_env)
+        chunks = -(-min(cap, max_view) // 4096)
+        return 7 + max(0, (chunks - 1).bit_length())
 
     def autotune(self, g: Gaussians, cams: torch.Tensor, candidates, reps=3, out=None, stream=None):
         """Time each (tile_w, tile_h, batch_depth, pix_x, pix_y) candidate; keep the fastest in self.cfg."""

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -117,6 +118,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Plan {
     int W, H, tw, th, px, py, threads, tiles_x, tiles_y, tpv, n_bins, B, flags;
     int64_t N, R, cap;
+    int64_t max_view; // most records of one view: no bin holds more pairs
     float near_plane;
     // byte offsets
     size_t o_hdr, o_tb, o_rec, o_vis, o_cnt, o_fcnt, o_start, o_cur, o_big, o_heavy, o_rel, o_keys, o_scr, o_pT, o_pL,
@@ -157,12 +159,14 @@ gs_status make_plan(const gs_render_config *cfg, const gs_batch *b, Plan &p)
     for (int e = 0; e < b->n_envs; ++e)
         if (b->env_offsets[e + 1] < b->env_offsets[e]) return GS_ERR_INVALID_ARG;
     p.N = b->env_offsets[b->n_envs];
-    int64_t R = 0;
+    int64_t R = 0, max_view = 0;
     for (int v = 0; v < b->n_views; ++v) {
         const int e = b->view_env[v];
         if (e < 0 || e >= b->n_envs) return GS_ERR_INVALID_ARG;
         R += b->env_offsets[e + 1] - b->env_offsets[e];
+        max_view = std::max(max_view, b->env_offsets[e + 1] - b->env_offsets[e]);
     }
+    p.max_view = max_view;
     if (R >= ((int64_t)1 << 31)) return GS_ERR_UNSUPPORTED;
     p.R = R;
     p.cap = cfg->pair_capacity > 0 ? cfg->pair_capacity : 4 * R + 65536;
@@ -348,7 +352,8 @@ gs_status enqueue_forward(const gs_gaussians *g, const gs_batch *b, const gs_cam
     }
     {
         Stage st5(5, s);
-        launch_merge_passes(w, merge_passes_for_capacity(p.cap), sms, s);
+        // one pass per doubling of 4096 up to the largest possible bin
+        launch_merge_passes(w, merge_passes_for_capacity(std::min(p.cap, p.max_view)), sms, s);
     }
     const bool persistent = (p.flags & GS_FLAG_PERSISTENT) != 0;
     {

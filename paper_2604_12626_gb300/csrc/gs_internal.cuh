@@ -89,7 +89,8 @@ struct Header {
     unsigned long long n_cov;   // covered Gaussians up to each pixel's last blended one (same flag)
     uint32_t n_backward;  // gs_render_backward calls since the forward (d_rec is clean while 0)
     uint32_t queue_zero;  // gradient-clearing items taken by the blend backward
-    uint32_t pad[46];
+    uint32_t small_queue; // bins taken by the warp-per-bin sort
+    uint32_t pad[45];
 };
 
 struct Table {

@@ -14,6 +14,9 @@
 //                       2^27, else 4 passes of 8 bits over the depth bits),
 //                       ranks from warp match masks; keys sharing a depth are
 //                       ordered by record index on the way out.
+//   sort_small_kernel   bins of 2 .. 512 pairs, one warp each: the same passes
+//                       with the keys in registers, warp-level counters and
+//                       ranks, no CTA barrier.
 //   merge_pass_kernel   bins of more than 4096 pairs: pass p merges sorted runs
 //                       of 4096 << p; each CTA writes 4096 outputs, located by
 //                       a merge-path search.  Chunk sorts write to keys or to
@@ -26,6 +29,7 @@ namespace gs {
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kRadixMax = 512; // digits of up to 9 bits
+constexpr int kSmallSort = 512; // bins up to this many pairs: one warp each (sort_small_kernel)
 
 struct SortSmem {
     unsigned long long keys[kSortChunk];
@@ -131,20 +135,26 @@ __device__ __forceinline__ void radix_pass(unsigned long long (&k)[K], int shift
 // of the depth-sorted sm.keys[0..n); false if it is longer than kMaxRun.
 constexpr uint32_t kMaxRun = 32;
 
-__device__ __forceinline__ bool depth_run(const SortSmem &sm, uint32_t pos, uint32_t n, uint32_t hi, uint32_t &s,
-                                          uint32_t &e)
+__device__ __forceinline__ bool run_bounds(const unsigned long long *keys, uint32_t pos, uint32_t n, uint32_t hi,
+                                           uint32_t &s, uint32_t &e)
 {
     s = pos;
     e = pos;
-    while (s > 0 && (uint32_t)(sm.keys[s - 1] >> 32) == hi) {
+    while (s > 0 && (uint32_t)(keys[s - 1] >> 32) == hi) {
         --s;
         if (pos - s >= kMaxRun) return false;
     }
-    while (e + 1 < n && (uint32_t)(sm.keys[e + 1] >> 32) == hi) {
+    while (e + 1 < n && (uint32_t)(keys[e + 1] >> 32) == hi) {
         ++e;
         if (e - s >= kMaxRun) return false;
     }
     return true;
+}
+
+__device__ __forceinline__ bool depth_run(const SortSmem &sm, uint32_t pos, uint32_t n, uint32_t hi, uint32_t &s,
+                                          uint32_t &e)
+{
+    return run_bounds(sm.keys, pos, n, hi, s, e);
 }
 
 // Sorts src[0..n) (n <= 256 K) into dst[0..n) (dst may equal src): three or four
@@ -270,8 +280,170 @@ __global__ void __launch_bounds__(kSortThreads, 3) sort_chunks_kernel(Ws w)
             sort_dispatch(w.keys + start + c0, sort_buf(w, passes, 0) + start + c0, cn, sm);
         } else {
             bin_range(w, (int)(item - n_big), start, n);
-            if (n <= 1u || n > (uint32_t)kSortChunk) continue;
+            if (n <= (uint32_t)kSmallSort || n > (uint32_t)kSortChunk) continue; // small bins: sort_small_kernel
             sort_dispatch(w.keys + start, w.keys + start, n, sm);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Bins of at most kSmallSort pairs: one warp each.  The warp holds the bin's
+// keys in registers (K per lane, position r 32 + lane in k[r]) and runs the
+// same LSD passes with warp-level counting (shared-memory counters), an
+// exclusive scan and stable ranking from match masks, scattering into its own
+// shared-memory buffer and reading back in position order -- no CTA barrier.
+// Equal depths are ordered by record index on the way out, as in the CTA
+// sort; a run of equal depths longer than kMaxRun sorts the whole 64-bit key.
+// ---------------------------------------------------------------------------
+constexpr int kSmallWarps = 8;
+
+struct SmallSortSmem {
+    unsigned long long keys[kSmallWarps][kSmallSort];
+    uint32_t cnt[kSmallWarps][kRadixMax];
+};
+
+template <int K, int BITS>
+__device__ __forceinline__ void warp_radix_pass(unsigned long long (&k)[K], uint32_t n, int shift, uint32_t sub,
+                                                unsigned long long *buf, uint32_t *cnt)
+{
+    constexpr int R = 1 << BITS, PER = R / 32;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) cnt[j * 32 + lane] = 0u;
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < K; ++r)
+        if ((uint32_t)(r * 32 + lane) < n) atomicAdd(cnt + key_digit<BITS>(k[r], shift, sub), 1u);
+    __syncwarp();
+    {
+        // exclusive scan: lane owns digits lane PER .. lane PER + PER - 1
+        uint32_t v[PER], sum = 0;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            v[j] = cnt[lane * PER + j];
+            sum += v[j];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += u;
+        }
+        uint32_t run = incl - sum;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            cnt[lane * PER + j] = run;
+            run += v[j];
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const bool valid = (uint32_t)(r * 32 + lane) < n;
+        const uint32_t d = valid ? key_digit<BITS>(k[r], shift, sub) : 0xffffffffu;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (valid && lane == leader) {
+            base = cnt[d];
+            cnt[d] = base + (uint32_t)__popc(peers);
+        }
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (valid) buf[base + (uint32_t)__popc(peers & lt)] = k[r];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < K; ++r)
+        if ((uint32_t)(r * 32 + lane) < n) k[r] = buf[r * 32 + lane];
+    __syncwarp();
+}
+
+// Sorts keys[0..n) of one bin in place (n <= 32 K) with one warp.
+template <int K>
+__device__ void warp_sort_bin(unsigned long long *keys, uint32_t n, unsigned long long *buf, uint32_t *cnt)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned long long k[K];
+    uint32_t lo = 0xffffffffu, hi = 0u;
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const uint32_t pos = (uint32_t)(r * 32 + lane);
+        k[r] = pos < n ? keys[pos] : ~0ull;
+        if (pos < n) {
+            lo = min(lo, (uint32_t)(k[r] >> 32));
+            hi = max(hi, (uint32_t)(k[r] >> 32));
+        }
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (hi - lo < kDepthCap) {
+#pragma unroll 1
+        for (int pass = 0; pass < 3; ++pass) warp_radix_pass<K, 9>(k, n, 9 * pass, lo, buf, cnt);
+    } else {
+#pragma unroll 1
+        for (int pass = 0; pass < 4; ++pass) warp_radix_pass<K, 8>(k, n, 32 + 8 * pass, 0u, buf, cnt);
+    }
+    // buf[0..n) now holds the keys in depth order; runs of equal depths are
+    // ordered by record index while they are written out
+    bool long_run = false;
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const uint32_t pos = (uint32_t)(r * 32 + lane);
+        const uint32_t h = (uint32_t)(k[r] >> 32);
+        if (pos > 0 && pos < n && (uint32_t)(buf[pos - 1] >> 32) == h) {
+            uint32_t sp, ep;
+            long_run |= !run_bounds(buf, pos, n, h, sp, ep);
+        }
+    }
+    if (__any_sync(0xffffffffu, long_run)) {
+#pragma unroll 1
+        for (int pass = 0; pass < 8; ++pass) warp_radix_pass<K, 8>(k, n, 8 * pass, 0u, buf, cnt);
+#pragma unroll
+        for (int r = 0; r < K; ++r)
+            if ((uint32_t)(r * 32 + lane) < n) keys[r * 32 + lane] = k[r];
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const uint32_t pos = (uint32_t)(r * 32 + lane);
+        if (pos >= n) continue;
+        const unsigned long long key = k[r];
+        const uint32_t h = (uint32_t)(key >> 32);
+        uint32_t at = pos;
+        if ((pos > 0 && (uint32_t)(buf[pos - 1] >> 32) == h) || (pos + 1 < n && (uint32_t)(buf[pos + 1] >> 32) == h)) {
+            uint32_t sp, ep;
+            run_bounds(buf, pos, n, h, sp, ep); // a run of at most kMaxRun keys (checked above)
+            uint32_t rank = 0;
+            for (uint32_t j = sp; j <= ep; ++j) rank += (uint32_t)buf[j] < (uint32_t)key;
+            at = sp + rank;
+        }
+        keys[at] = key;
+    }
+}
+
+// Every bin of 2 .. kSmallSort pairs, a warp per bin (bins taken four at a time).
+__global__ void __launch_bounds__(kSmallWarps * 32) sort_small_kernel(Ws w)
+{
+    extern __shared__ __align__(16) unsigned char smem_small[];
+    SmallSortSmem &sm = *reinterpret_cast<SmallSortSmem *>(smem_small);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned long long *buf = sm.keys[warp];
+    uint32_t *cnt = sm.cnt[warp];
+    const uint32_t n_bins = (uint32_t)w.tb->n_bins;
+    for (;;) {
+        uint32_t b0 = 0;
+        if (lane == 0) b0 = atomicAdd(&w.hdr->small_queue, 4u);
+        b0 = __shfl_sync(0xffffffffu, b0, 0);
+        if (b0 >= n_bins) break;
+        for (uint32_t bin = b0; bin < min(b0 + 4u, n_bins); ++bin) {
+            uint32_t start, n;
+            bin_range(w, (int)bin, start, n);
+            if (n <= 1u || n > (uint32_t)kSmallSort) continue;
+            unsigned long long *keys = w.keys + start;
+            if (n <= 128u) warp_sort_bin<4>(keys, n, buf, cnt);
+            else if (n <= 256u) warp_sort_bin<8>(keys, n, buf, cnt);
+            else warp_sort_bin<16>(keys, n, buf, cnt);
         }
     }
 }
@@ -367,7 +539,7 @@ __global__ void __launch_bounds__(kSortThreads) merge_pass_kernel(Ws w, int pass
     }
 }
 
-static int g_sort_occ = 1, g_merge_occ = 1; // resident CTAs per SM
+static int g_sort_occ = 1, g_merge_occ = 1, g_small_occ = 1; // resident CTAs per SM
 
 cudaError_t configure_sort_kernels()
 {
@@ -383,6 +555,13 @@ cudaError_t configure_sort_kernels()
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, merge_pass_kernel, kSortThreads, (int)sizeof(MergeSmem));
     if (e == cudaSuccess && nb > 0) g_merge_occ = nb;
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sort_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(SmallSortSmem));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sort_small_kernel, kSmallWarps * 32,
+                                                          (int)sizeof(SmallSortSmem));
+    if (e == cudaSuccess && nb > 0) g_small_occ = nb;
     return e;
 }
 
@@ -397,6 +576,7 @@ int merge_passes_for_capacity(int64_t pair_capacity)
 void launch_sort_chunks(const Ws &w, int n_sms, cudaStream_t s)
 {
     sort_chunks_kernel<<<n_sms * g_sort_occ, kSortThreads, sizeof(SortSmem), s>>>(w);
+    sort_small_kernel<<<n_sms * g_small_occ, kSmallWarps * 32, sizeof(SmallSortSmem), s>>>(w);
 }
 
 void launch_merge_passes(const Ws &w, int n_passes, int n_sms, cudaStream_t s)

@@ -323,12 +323,31 @@ FWD_KERNELS = ("setup_kernel", "preprocess_kernel", "scan_bins_kernel", "scatter
 BWD_KERNELS = ("clear_record_grads_kernel", "blend_backward_kernel", "preprocess_backward_kernel")
 
 
-def ncu_summary(csv_path, command, out_path=None):
+# the unit each kernel's DRAM traffic scales with, for carrying bytes measured
+# on a small capture over to the bench workload: the blend backward's bytes are
+# mostly the dense gradient clear (per Gaussian), the pair stages' per pair
+UNIT_OF_KERNEL = {"setup_kernel": "gaussians", "preprocess_kernel": "gaussians", "scan_bins_kernel": "pairs",
+                  "scatter_kernel": "pairs", "sort_chunks_kernel": "pairs", "sort_small_kernel": "pairs",
+                  "merge_pass_kernel": "pairs", "blend_persistent_kernel": "pairs", "blendq_persistent_kernel": "pairs",
+                  "clear_record_grads_kernel": "visible", "blend_backward_kernel": "gaussians",
+                  "preprocess_backward_kernel": "visible"}
+
+
+def _units(stats_line):
+    st = stats_line.get("stats", {})
+    return {"gaussians": stats_line.get("config", {}).get("gaussians_per_gpu") or st.get("records"),
+            "pairs": st.get("pairs"), "visible": st.get("visible")}
+
+
+def ncu_summary(csv_path, command, out_path=None, stats_json=None):
     """Per-kernel launches, time share and DRAM bytes of an ncu --csv launch
     list of this bench (metrics gpu__time_duration.sum, dram__bytes_read.sum,
     dram__bytes_write.sum); writes profiles/dram_traffic.json (or out_path:
     bytes per gs_render / gs_render_backward call, tagged with the kernel
-    sources' hash), prints the table and returns the per-kernel entries."""
+    sources' hash), prints the table and returns the per-kernel entries.
+    With stats_json (the bench's JSON line of the captured command) every
+    kernel also gets its bytes per unit (UNIT_OF_KERNEL), which the bench
+    multiplies by its own counts."""
     import collections
     import csv
     import re
@@ -359,10 +378,17 @@ def ncu_summary(csv_path, command, out_path=None):
     tot = sum(a["ms"] for a in ours.values())
     kern = {}
     print(f"{'kernel':28s} {'launches':>8s} {'total ms':>9s} {'share':>6s} {'ms/launch':>9s} {'DRAM MB/launch':>14s}")
+    units = None
+    if stats_json:
+        with open(stats_json) as f:
+            units = _units(json.loads(f.read().strip().splitlines()[-1]))
     for k, a in sorted(ours.items(), key=lambda x: -x[1]["ms"]):
         calls = n_fwd if k in FWD_KERNELS else n_bwd
         kern[k] = {"dram_bytes_per_call": (a["rd"] + a["wr"]) / calls, "launches_per_call": a["launches"] / calls,
                    "ms_per_call_under_ncu": a["ms"] / calls}
+        if units and units.get(UNIT_OF_KERNEL.get(k)):
+            kern[k]["unit"] = UNIT_OF_KERNEL[k]
+            kern[k]["bytes_per_unit"] = kern[k]["dram_bytes_per_call"] / units[UNIT_OF_KERNEL[k]]
         print(f"{k:28s} {a['launches']:8d} {a['ms']:9.3f} {100 * a['ms'] / tot:5.1f}% {a['ms'] / a['launches']:9.4f} "
               f"{(a['rd'] + a['wr']) / a['launches'] / 1e6:14.1f}  rd {a['rd'] / a['launches'] / 1e6:.1f} "
               f"wr {a['wr'] / a['launches'] / 1e6:.1f}")
@@ -373,7 +399,7 @@ def ncu_summary(csv_path, command, out_path=None):
            "what": "DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of each kernel per gs_render / "
                    "gs_render_backward call (all its launches in that call), from one ncu run; stale once the "
                    "kernel sources change (source_hash over csrc/)",
-           "command": command, "kernels": kern}
+           "command": command, "units_of_capture": units, "kernels": kern}
     with open(out_path or os.path.join(ROOT, "profiles", "dram_traffic.json"), "w") as f:
         json.dump(out, f, indent=1)
     return kern
@@ -426,8 +452,12 @@ def rooflines(stats, stage_ms, n_eval_fwd, n_eval_bwd, n_pix, N, sm_count, sm_mh
             out[k] = {"bound": "alu", "achieved": a, "peak": alu_peak, "unit": "T lane-ops/s", "frac": a / alu_peak,
                       "algorithmic": f, "ms": ms[k],
                       "peak_kind": f"derived: {sm_count} SMs x 128 FP32 lanes x {mhz:.0f} MHz"}
+    live = {"gaussians": N, "pairs": P, "visible": nvis}
     for k, v in out.items():
-        tb = [traffic[x]["dram_bytes_per_call"] for x in KERNELS_OF_STAGE[k] if x in traffic]
+        # bytes per unit from the capture times this run's units (else the
+        # captured call's bytes, when the capture was of this workload)
+        tb = [traffic[x]["bytes_per_unit"] * live[traffic[x]["unit"]] if "bytes_per_unit" in traffic[x]
+              else traffic[x]["dram_bytes_per_call"] for x in KERNELS_OF_STAGE[k] if x in traffic]
         v["traffic"] = float(sum(tb)) if tb else None
     for k, n_ev in (("blend", n_eval_fwd), ("blend_backward", n_eval_bwd)):
         if exp_rate and k in out:
@@ -975,11 +1005,15 @@ def main():
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--tile", default="", help="fixed tile_w,tile_h,batch_depth instead of the autotuner")
     ap.add_argument("--envs", type=int, default=N_ENVS, help="envs per GPU (64; fewer only for small profiling cases)")
-    ap.add_argument("--ncu-summary", nargs=2, metavar=("CSV", "COMMAND"),
-                    help="summarise an ncu launch list of this bench into profiles/dram_traffic.json and exit")
+    ap.add_argument("--ncu-summary", nargs="+", metavar="ARG",
+                    help="CSV COMMAND [STATS_JSON]: summarise an ncu launch list of this bench into "
+                         "profiles/dram_traffic.json (with the captured run's JSON line: bytes per unit) and exit")
     args = ap.parse_args()
     if args.ncu_summary:
-        ncu_summary(*args.ncu_summary)
+        if len(args.ncu_summary) not in (2, 3):
+            ap.error("--ncu-summary takes CSV COMMAND [STATS_JSON]")
+        csv_path, command = args.ncu_summary[:2]
+        ncu_summary(csv_path, command, stats_json=args.ncu_summary[2] if len(args.ncu_summary) == 3 else None)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -89,3 +89,35 @@ def test_rooflines_arithmetic(monkeypatch):
     assert per["blend"]["exp2"]["frac"] == pytest.approx(1e9 / 2e-3 / 1e12)
     assert per["blend_backward"]["also_writes_bytes"] == 236 * N
     assert roof["kernel"] == "blend_backward"  # the longest stage
+
+
+def test_traffic_scaled_by_units(tmp_path, monkeypatch):
+    """A capture of a small case carries over to the bench workload as bytes
+    per unit: preprocess per Gaussian, the pair stages per pair, the
+    preprocess backward per visible record."""
+    rows = []
+    _launch(rows, 0, "void gs::preprocess_kernel<1, false>(const gs_camera *, GaussIn, Ws)", 2000, 600, 400)
+    _launch(rows, 1, "gs::scatter_kernel(const gs_camera *, Ws)", 500, 100, 200)
+    _launch(rows, 2, "gs::preprocess_backward_kernel<1, true>(const gs_camera *, GaussInB, Ws, GradOut)", 900, 50, 50)
+    _launch(rows, 3, "void gs::blend_backward_kernel<2, 1>(const gs_camera *, Ws, const float *)", 500, 1, 1)
+    p = tmp_path / "launches.csv"
+    with open(p, "w", newline="") as f:
+        w = csv.writer(f)
+        w.writerow(HEADER)
+        w.writerows(rows)
+    line = {"config": {"gaussians_per_gpu": 100}, "stats": {"records": 100, "pairs": 30, "visible": 25}}
+    sj = tmp_path / "small.json"
+    sj.write_text("log line\n" + json.dumps(line) + "\n")
+    out = tmp_path / "traffic.json"
+    kern = bench.ncu_summary(str(p), "cmd", out_path=str(out), stats_json=str(sj))
+    assert kern["preprocess_kernel"]["unit"] == "gaussians" and kern["preprocess_kernel"]["bytes_per_unit"] == 10.0
+    assert kern["scatter_kernel"]["bytes_per_unit"] == 10.0  # 300 bytes over 30 pairs
+    assert kern["preprocess_backward_kernel"]["bytes_per_unit"] == 4.0  # 100 bytes over 25 visible
+    monkeypatch.setattr(bench, "peaks", lambda: (1000.0, "measured"))
+    monkeypatch.setattr(bench, "dram_traffic", lambda: kern)
+    stats = {"n_records": 1000, "n_visible": 200, "n_pairs": 500}
+    _, per = bench.rooflines(stats, {"preprocess": 1.0, "scatter": 1.0, "preprocess_backward": 1.0}, n_eval_fwd=1,
+                             n_eval_bwd=1, n_pix=1, N=1000, sm_count=1, sm_mhz=1000.0)
+    assert per["preprocess"]["traffic"] == pytest.approx(10.0 * 1000)
+    assert per["scatter"]["traffic"] == pytest.approx(10.0 * 500)
+    assert per["preprocess_backward"]["traffic"] == pytest.approx(4.0 * 200)

@@ -104,6 +104,10 @@ def _bind(L):
     i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
     L.or_project.restype = i64
     L.or_project.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, i32, i32, f64] + [P] * 12
+    L.or_avatar_capsules.restype = None
+    L.or_avatar_capsules.argtypes = [i32, i32, P, P, P, P, P]
+    L.or_capsule_query.restype = None
+    L.or_capsule_query.argtypes = [i64, P, P, P, P, P, f64, P, P, P, P]
     L.or_render.restype = i64
     L.or_render.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, i32, i32, f64, P, i32, i32, i32] + [P] * 7
     L.or_lbs_matrices.restype = None
@@ -319,6 +323,39 @@ def forward_kinematics(local_rot, root, rest, parents):
     par = np.ascontiguousarray(np.asarray(parents, np.int32).reshape(J))
     L.or_forward_kinematics(A, J, _p(lr), _p(_f64(root)), _p(_f64(rest)), _p(par), _p(out))
     return out
+
+
+def avatar_capsules(M, rest, parents, radius):
+    """Proxy capsules [A,J,8] (a xyz, rho, b xyz, 0) from skinning matrices
+    M [A,J,3,4]: joint j's capsule spans the posed parent and j (the root: a
+    sphere), posed position = M_j [J_j; 1]."""
+    L = _lib()
+    Mm = _f64(M)
+    A, J = Mm.shape[0], Mm.shape[1]
+    out = np.zeros((A, J, 8))
+    par = np.ascontiguousarray(np.asarray(parents, np.int32).reshape(J))
+    L.or_avatar_capsules(A, J, _p(Mm), _p(_f64(rest)), _p(par), _p(_f64(radius)), _p(out))
+    return out
+
+
+def capsule_query(caps, env_cap_off, query_env, p0, p1=None, agent_radius=0.0):
+    """Per query: signed distance from p0 to the nearest capsule surface of its
+    env, that capsule's index within the env (-1: none), and for the step
+    p0 -> p1 the first-contact fraction tclip and the blocked flag."""
+    L = _lib()
+    c = _f64(caps).reshape(-1, 8)
+    off = np.ascontiguousarray(np.asarray(env_cap_off, np.int64))
+    qe = np.ascontiguousarray(np.asarray(query_env, np.int32))
+    Q = qe.shape[0]
+    P0 = _f64(p0).reshape(Q, 3)
+    P1 = None if p1 is None else _f64(p1).reshape(Q, 3)
+    dist = np.zeros(Q)
+    near = np.zeros(Q, np.int32)
+    tclip = np.zeros(Q)
+    blk = np.zeros(Q, np.uint8)
+    L.or_capsule_query(Q, _p(c), _p(off), _p(qe), _p(P0), _p(P1) if P1 is not None else None, float(agent_radius),
+                       _p(dist), _p(near), _p(tclip), _p(blk))
+    return dict(dist=dist, nearest=near, tclip=tclip, blocked=blk.astype(bool))
 
 
 def interpolate_frames(frames, t):

@@ -1143,4 +1143,122 @@ void or_raster_mesh(int64_t n_verts, const double *verts, const double *colors, 
     free(live);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Proxy capsules and the two avatar queries (Sec. 3.3.2, Sec. 3.4).         */
+/* A capsule is the set of points within radius rho of the segment [a, b];   */
+/* one per joint j: the bone from the posed position of parent(j) to that of */
+/* j (the root: a = b, a sphere).  The posed position of joint j is          */
+/* M_j [J_j; 1], M_j its skinning matrix and J_j its rest position (the      */
+/* skinning matrix maps the rest pose to the posed one).  The agent is a     */
+/* sphere of radius r at p; a step moves it from p0 to p1.                    */
+/* Capsule rows: (ax, ay, az, rho, bx, by, bz, 0).                            */
+/* ------------------------------------------------------------------------ */
+void or_avatar_capsules(int32_t n_avatars, int32_t n_joints, const double *M, const double *rest,
+                        const int32_t *parents, const double *radius, double *out)
+{
+    for (int32_t a = 0; a < n_avatars; ++a) {
+        for (int32_t j = 0; j < n_joints; ++j) {
+            double pj[3], pp[3];
+            const int32_t par = parents[j] < 0 ? j : parents[j];
+            const double *Mj = M + ((size_t)a * n_joints + j) * 12, *Mp = M + ((size_t)a * n_joints + par) * 12;
+            for (int r = 0; r < 3; ++r) {
+                pj[r] = Mj[4 * r] * rest[3 * j] + Mj[4 * r + 1] * rest[3 * j + 1] + Mj[4 * r + 2] * rest[3 * j + 2] +
+                        Mj[4 * r + 3];
+                pp[r] = Mp[4 * r] * rest[3 * par] + Mp[4 * r + 1] * rest[3 * par + 1] +
+                        Mp[4 * r + 2] * rest[3 * par + 2] + Mp[4 * r + 3];
+            }
+            double *o = out + ((size_t)a * n_joints + j) * 8;
+            o[0] = pp[0]; o[1] = pp[1]; o[2] = pp[2]; o[3] = radius[j];
+            o[4] = pj[0]; o[5] = pj[1]; o[6] = pj[2]; o[7] = 0.0;
+        }
+    }
+}
+
+/* Distance from point p to the segment [a, b]. */
+static double point_segment_distance(const double *p, const double *a, const double *b)
+{
+    double ab[3], ap[3], ll = 0.0, t = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        ab[i] = b[i] - a[i];
+        ap[i] = p[i] - a[i];
+        ll += ab[i] * ab[i];
+        t += ap[i] * ab[i];
+    }
+    t = ll > 0.0 ? t / ll : 0.0;
+    if (t < 0.0) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    double d2 = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        const double e = ap[i] - t * ab[i];
+        d2 += e * e;
+    }
+    return sqrt(d2);
+}
+
+/* Per query q (env query_env[q]): dist = min over the env's capsules of
+ * |p0 - segment| - rho, nearest = that capsule's index (the lowest on ties,
+ * -1 without capsules); along the step p0 -> p1 the agent sphere first touches
+ * a capsule at the smallest t in [0, 1] with |p(t) - segment| <= rho + r:
+ * tclip = that t (0 when it starts in contact, 1 when it never touches),
+ * blocked = some contact.  f(t) = |p(t) - segment| is convex, so the contact
+ * set is an interval: its minimum over [0, 1] (golden-section search) decides
+ * contact and bisection on [0, argmin] finds the first t. */
+void or_capsule_query(int64_t n_queries, const double *caps, const int64_t *env_cap_off, const int32_t *query_env,
+                      const double *p0, const double *p1, double agent_radius, double *out_dist, int32_t *out_nearest,
+                      double *out_tclip, uint8_t *out_blocked)
+{
+    for (int64_t q = 0; q < n_queries; ++q) {
+        const int32_t e = query_env[q];
+        const double *P0 = p0 + 3 * q, *P1 = p1 ? p1 + 3 * q : p0 + 3 * q;
+        double best = INFINITY, tmin = 1.0;
+        int32_t arg = -1;
+        int blocked = 0;
+        for (int64_t c = env_cap_off[e]; c < env_cap_off[e + 1]; ++c) {
+            const double *cp = caps + 8 * c;
+            const double d = point_segment_distance(P0, cp, cp + 4) - cp[3];
+            if (d < best) {
+                best = d;
+                arg = (int32_t)(c - env_cap_off[e]);
+            }
+            const double R = cp[3] + agent_radius;
+            double pt[3];
+#define PT(t) (pt[0] = P0[0] + (t) * (P1[0] - P0[0]), pt[1] = P0[1] + (t) * (P1[1] - P0[1]), \
+               pt[2] = P0[2] + (t) * (P1[2] - P0[2]), point_segment_distance(pt, cp, cp + 4))
+            if (PT(0.0) <= R) {
+                blocked = 1;
+                tmin = 0.0;
+                continue;
+            }
+            /* golden-section search for the minimum of the convex f on [0, 1] */
+            double lo = 0.0, hi = 1.0;
+            const double g = 0.5 * (sqrt(5.0) - 1.0);
+            double x1 = hi - g * (hi - lo), x2 = lo + g * (hi - lo), f1 = PT(x1), f2 = PT(x2);
+            for (int it = 0; it < 100; ++it) {
+                if (f1 <= f2) {
+                    hi = x2; x2 = x1; f2 = f1; x1 = hi - g * (hi - lo); f1 = PT(x1);
+                } else {
+                    lo = x1; x1 = x2; f1 = f2; x2 = lo + g * (hi - lo); f2 = PT(x2);
+                }
+            }
+            double ts = 0.5 * (lo + hi);
+            if (PT(1.0) < PT(ts)) ts = 1.0;
+            if (PT(ts) > R) continue;
+            /* first crossing: f(0) > R >= f(ts), f decreasing on [0, ts] */
+            double a = 0.0, b = ts;
+            for (int it = 0; it < 100; ++it) {
+                const double m = 0.5 * (a + b);
+                if (PT(m) <= R) b = m;
+                else a = m;
+            }
+#undef PT
+            blocked = 1;
+            if (b < tmin) tmin = b;
+        }
+        out_dist[q] = arg >= 0 ? best : INFINITY;
+        out_nearest[q] = arg;
+        if (out_tclip) out_tclip[q] = blocked ? tmin : 1.0;
+        if (out_blocked) out_blocked[q] = (uint8_t)blocked;
+    }
+}
+
 int32_t or_abi_version(void) { return 1; }

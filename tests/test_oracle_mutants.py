@@ -7,6 +7,7 @@ import oracle as _oracle
 import test_oracle_adjoint as adj
 import test_oracle_mask_pins as mask
 import test_oracle_pins as pins
+import test_oracle_pins_capsule as capsule
 import test_oracle_pins_drive as drive
 
 MUTANTS = [
@@ -54,6 +55,12 @@ MUTANTS = [
      adj.test_adjoint_matches_finite_differences),
     ("adjoint: clamp passes gradient", "if (a_raw < ALPHA_MAX) {\n                    q->go", "if (1) {\n                    q->go",
      adj.test_adjoint_matches_finite_differences),
+    ("capsule distance to the infinite line", "    if (t < 0.0) t = 0.0;\n    if (t > 1.0) t = 1.0;", "",
+     capsule.test_distance_and_nearest_against_sampling),
+    ("first contact bisects towards the last crossing", "if (PT(m) <= R) b = m;\n                else a = m;",
+     "if (PT(m) <= R) a = m;\n                else b = m;", capsule.test_first_contact_against_sampling),
+    ("capsule joint unposed by its translation", "Mj[4 * r + 3];", "0.0;",
+     capsule.test_capsules_of_rest_pose_and_rigid_motion),
     ("composite keeps the farther fragment",
      "const int take_a = layer_depth(depth_a[i]) < layer_depth(depth_b[i]);",
      "const int take_a = layer_depth(depth_a[i]) > layer_depth(depth_b[i]);", drive.test_composite_picks_the_nearer_fragment),

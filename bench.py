@@ -518,6 +518,23 @@ def avatar_and_composite_rows(api, synth, torch, dev, stream, outs, hbm_peak):
     interp_ms = _event_ms(torch, stream, lambda: api.interpolate_joints(frames, t, out=G, stream=stream))
     fk_ms = _event_ms(torch, stream, lambda: api.forward_kinematics(local, root, rest, synth.PARENTS, out=G,
                                                                    stream=stream))
+    # proxy capsules of the posed avatars (8 per env over 32 envs) and the two
+    # avatar queries for 4096 candidate steps per env
+    radius = T(np.full(synth.N_JOINTS, 0.08, np.float32))
+    caps = torch.empty((n_av, synth.N_JOINTS, 8), device=dev)
+    caps_ms = _event_ms(torch, stream, lambda: api.avatar_capsules(G, rest, synth.PARENTS, radius, out=caps,
+                                                                  stream=stream))
+    n_qenv, n_q = 32, 32 * 4096
+    cap_off = torch.arange(0, n_av * synth.N_JOINTS + 1, (n_av // n_qenv) * synth.N_JOINTS, device=dev,
+                           dtype=torch.int64)
+    q_env = T(np.repeat(np.arange(n_qenv), n_q // n_qenv).astype(np.int32), torch.int32)
+    q0 = T(np.stack([rng.uniform(0, 3, n_q), rng.uniform(0, 4, n_q), rng.uniform(0.1, 1.8, n_q)], 1).astype(np.float32))
+    q1 = q0 + T(rng.normal(0, 0.25, (n_q, 3)).astype(np.float32))
+    q_out = (torch.empty(n_q, device=dev), torch.empty(n_q, dtype=torch.int32, device=dev), torch.empty(n_q, device=dev),
+             torch.empty(n_q, dtype=torch.uint8, device=dev))
+    query_ms = _event_ms(torch, stream, lambda: api.capsule_query(caps.view(-1, 8), cap_off, q_env, q0, q1, 0.1,
+                                                                 out=q_out, stream=stream))
+    q_blocked = float(q_out[3].float().mean().item())
     deform_ms = _event_ms(torch, stream, lambda: api.deform(av, G, om, oc, stream=stream))
     dmean, dcov = torch.ones_like(om), torch.ones_like(oc)
     deform_bwd_ms = _event_ms(torch, stream, lambda: api.deform_backward(av, G, dmean, dcov, gr, stream=stream), 5)
@@ -556,6 +573,11 @@ def avatar_and_composite_rows(api, synth, torch, dev, stream, outs, hbm_peak):
                                         note="joint gradients summed per warp by joint-owner lanes, one atomic per (CTA, joint, entry)"),
             "keyframe_interpolation": {"ms": interp_ms, "avatars": n_av, "frames": n_frames},
             "forward_kinematics": {"ms": fk_ms, "avatars": n_av, "joints": synth.N_JOINTS},
+            "avatar_capsules": {"ms": caps_ms, "avatars": n_av, "capsules": n_av * synth.N_JOINTS},
+            "capsule_query": {"ms": query_ms, "queries": n_q, "envs": n_qenv,
+                              "capsules_per_env": (n_av // n_qenv) * synth.N_JOINTS, "blocked_fraction": q_blocked,
+                              "what": "distance to the nearest capsule, blocked flag and first-contact fraction "
+                                      "of a 0.1 m sphere per candidate step"},
             "composite": dict(hbm(comp_bytes, comp_ms), views=V, width=W, height=H),
             "mesh_layer": {"ms": mesh_ms, "views": V, "triangles_per_view": int(tri_off[-1]) // V, "width": W,
                            "height": H}}

@@ -314,7 +314,45 @@ gs_status gs_forward_kinematics(const float *local_rot, const float *root, const
                                 const int32_t *parents_host, int32_t n_avatars, int32_t n_joints, float *out,
                                 void *stream);
 
-/* Joint matrices at the current simulation time (Sec. 3.3.1: the per-frame
+/* Proxy capsules of posed avatars (Sec. 3.3.2: collision capsules derived from
+ * the skeletal bones, posed per frame, approximate each avatar's body for the
+ * navigation side).  Capsule j of avatar a is the segment from the posed
+ * position of parent(j) to that of j (the root: both ends at the root, a
+ * sphere) with radius radius[j]; the posed position of joint j is
+ * M_j [J_j; 1], M_j its skinning matrix (the matrices gs_deform_avatars takes)
+ * and J_j its rest position.
+ *   joint_M       device [A,J,3,4] skinning matrices
+ *   rest          device [J,3] rest joint positions
+ *   parents_host  host [J] parent of each joint, parents[j] < j for j > 0
+ *   radius        device [J] capsule radius per joint (metres)
+ *   out_caps      device [A,J,8] (ax, ay, az, radius, bx, by, bz, 0), 16-byte aligned
+ * 1 <= J <= 64; GS_ERR_INVALID_ARG for a parent that is not below its child. */
+gs_status gs_avatar_capsules(const float *joint_M, const float *rest, const int32_t *parents_host,
+                             const float *radius, int32_t n_avatars, int32_t n_joints, float *out_caps, void *stream);
+
+/* The two avatar queries of Sec. 3.4: the distance to the nearest avatar
+ * capsule, and whether a candidate step is blocked (the planner clips motion
+ * that would enter a capsule, Sec. 3.3.2).  Query q belongs to env
+ * query_env[q], whose capsules are rows [env_cap_off[e], env_cap_off[e+1]) of
+ * caps; the agent is a sphere of radius agent_radius moved from p0[q] to
+ * p1[q].  Per query:
+ *   out_dist     [Q] float32: min over the env's capsules of |p0 - axis| - radius
+ *                (negative inside; +inf for an env without capsules)
+ *   out_nearest  [Q] int32: that capsule's row within the env (the lowest on
+ *                ties), -1 without capsules
+ *   out_tclip    [Q] float32 or NULL: the smallest t in [0, 1] at which the
+ *                sphere at p0 + t (p1 - p0) touches a capsule (0 when it starts
+ *                in contact), 1 when it touches none
+ *   out_blocked  [Q] uint8 or NULL: 1 when the step touches a capsule
+ *   caps         device [C,8] rows as gs_avatar_capsules writes them, 16-byte aligned
+ *   env_cap_off  device [n_envs+1] int64; query_env device [Q] int32 (entries
+ *                outside [0, n_envs) read as an env without capsules)
+ *   p0, p1       device [Q,3]; p1 NULL: no step (tclip 1 unless p0 is in contact) */
+gs_status gs_capsule_query(const float *caps, const int64_t *env_cap_off, int32_t n_envs, const int32_t *query_env,
+                           const float *p0, const float *p1, float agent_radius, int64_t n_queries, float *out_dist,
+                           int32_t *out_nearest, float *out_tclip, uint8_t *out_blocked, void *stream);
+
+/* Joint matrices at the current simulation time (Sec. 3.3.1: the per-frame/* Joint matrices at the current simulation time (Sec. 3.3.1: the per-frame
  * matrices are interpolated at the simulation time).  For avatar a at the
  * fractional frame position t[a]: f = clamp(floor(t), 0, F-1),
  * w = clamp(t - f, 0, 1), out = (1 - w) M[f] + w M[min(f+1, F-1)] -- linear in

@@ -106,6 +106,11 @@ for _f in ("gs_render_static", "gs_render_static_status", "gs_profile_enable", "
            "gs_deform_avatars_backward", "gs_get_status", "gs_render_stats", "gs_autotune"):
     getattr(_lib, _f).restype = ctypes.c_int32
 _lib.gs_exp2_rate.argtypes = [ctypes.c_int32, ctypes.c_int32, _P, _P]
+_lib.gs_avatar_capsules.argtypes = [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]
+_lib.gs_avatar_capsules.restype = ctypes.c_int32
+_lib.gs_capsule_query.argtypes = [_P, _P, ctypes.c_int32, _P, _P, _P, ctypes.c_float, ctypes.c_int64, _P, _P, _P, _P,
+                                  _P]
+_lib.gs_capsule_query.restype = ctypes.c_int32
 _lib.gs_exp2_rate.restype = ctypes.c_int32
 _lib.gs_last_cuda_error.restype = ctypes.c_int32
 _lib.gs_version.restype = ctypes.c_int32
@@ -113,7 +118,8 @@ _lib.gs_version.restype = ctypes.c_int32
 EXPORTS = ("gs_render_static", "gs_render_static_status", "gs_profile_enable", "gs_profile_read", "gs_workspace_sections", "gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_deform_avatars",
            "gs_deform_avatars_backward", "gs_get_status", "gs_render_stats", "gs_autotune", "gs_last_cuda_error",
            "gs_version", "gs_composite_nearest", "gs_forward_kinematics", "gs_interpolate_joints",
-           "gs_render_avatars", "gs_mesh_workspace_size", "gs_render_mesh", "gs_exp2_rate")
+           "gs_render_avatars", "gs_mesh_workspace_size", "gs_render_mesh", "gs_exp2_rate", "gs_avatar_capsules",
+           "gs_capsule_query")
 
 
 class GsError(RuntimeError):
@@ -533,6 +539,47 @@ def forward_kinematics(local_rot, root, rest, parents, out=None, stream=None):
         out = torch.empty((A, J, 3, 4), dtype=torch.float32, device=local_rot.device)
     _check(_lib.gs_forward_kinematics(_ptr(local_rot), _ptr(root), _ptr(rest), par.ctypes.data_as(_P), A, J,
                                       _ptr(out), _stream(stream)), "gs_forward_kinematics")
+    return out
+
+
+def avatar_capsules(joint_M, rest, parents, radius, out=None, stream=None):
+    """Proxy capsules [A,J,8] (a xyz, radius, b xyz, 0; gs_avatar_capsules) of
+    avatars posed by skinning matrices joint_M [A,J,3,4]: joint j's capsule
+    spans the posed parent and j.  rest [J,3], radius [J] CUDA float32; parents
+    a host sequence."""
+    A, J = joint_M.shape[0], joint_M.shape[1]
+    _need(joint_M, torch.float32, (J, 3, 4), "joint_M")
+    _need(rest, torch.float32, (3,), "rest")
+    _need(radius, torch.float32, (), "radius")
+    par = np.ascontiguousarray(np.asarray(parents, np.int32).reshape(J))
+    if out is None:
+        out = torch.empty((A, J, 8), dtype=torch.float32, device=joint_M.device)
+    _check(_lib.gs_avatar_capsules(_ptr(joint_M), _ptr(rest), par.ctypes.data_as(_P), _ptr(radius), A, J, _ptr(out),
+                                   _stream(stream)), "gs_avatar_capsules")
+    return out
+
+
+def capsule_query(caps, env_cap_off, query_env, p0, p1=None, agent_radius=0.0, out=None, stream=None):
+    """The avatar queries (gs_capsule_query): per query, the signed distance
+    from p0 to the nearest capsule surface of its env, that capsule's row
+    within the env, and for the step p0 -> p1 the first-contact fraction and
+    the blocked flag.  caps [C,8], env_cap_off [E+1] int64, query_env [Q] int32,
+    p0 / p1 [Q,3]: CUDA tensors.  Returns (dist, nearest, tclip, blocked)."""
+    Q = query_env.shape[0]
+    _need(caps, torch.float32, (8,), "caps")
+    _need(env_cap_off, torch.int64, (), "env_cap_off")
+    _need(query_env, torch.int32, (), "query_env")
+    _need(p0, torch.float32, (3,), "p0")
+    if p1 is not None:
+        _need(p1, torch.float32, (3,), "p1")
+    if out is None:
+        dev = p0.device
+        out = (torch.empty(Q, dtype=torch.float32, device=dev), torch.empty(Q, dtype=torch.int32, device=dev),
+               torch.empty(Q, dtype=torch.float32, device=dev), torch.empty(Q, dtype=torch.uint8, device=dev))
+    dist, near, tclip, blk = out
+    _check(_lib.gs_capsule_query(_ptr(caps), _ptr(env_cap_off), env_cap_off.shape[0] - 1, _ptr(query_env), _ptr(p0),
+                                 _ptr(p1) if p1 is not None else None, float(agent_radius), Q, _ptr(dist),
+                                 _ptr(near), _ptr(tclip), _ptr(blk), _stream(stream)), "gs_capsule_query")
     return out
 
 

@@ -590,6 +590,46 @@ gs_status gs_forward_kinematics(const float *local_rot, const float *root, const
     return check_launch();
 }
 
+gs_status gs_avatar_capsules(const float *joint_M, const float *rest, const int32_t *parents_host,
+                             const float *radius, int32_t n_avatars, int32_t n_joints, float *out_caps, void *stream)
+{
+    if (!joint_M || !rest || !parents_host || !radius || !out_caps) return GS_ERR_INVALID_ARG;
+    if (n_avatars < 0 || n_joints < 1 || n_joints > kMaxJoints) return GS_ERR_INVALID_ARG;
+    if (!aligned16(out_caps)) return GS_ERR_ALIGNMENT;
+    JointTree tree;
+    std::memset(&tree, 0, sizeof(tree));
+    tree.n = n_joints;
+    tree.parent[0] = -1;
+    for (int j = 1; j < n_joints; ++j) {
+        const int32_t p = parents_host[j];
+        if (p < 0 || p >= j) return GS_ERR_INVALID_ARG;
+        tree.parent[j] = (int8_t)p;
+    }
+    if (n_avatars == 0) return GS_OK;
+    int sms = 0;
+    gs_status st = device_init(&sms);
+    if (st != GS_OK) return st;
+    launch_capsules(joint_M, rest, radius, tree, n_avatars, out_caps, static_cast<cudaStream_t>(stream));
+    return check_launch();
+}
+
+gs_status gs_capsule_query(const float *caps, const int64_t *env_cap_off, int32_t n_envs, const int32_t *query_env,
+                           const float *p0, const float *p1, float agent_radius, int64_t n_queries, float *out_dist,
+                           int32_t *out_nearest, float *out_tclip, uint8_t *out_blocked, void *stream)
+{
+    if (!env_cap_off || !query_env || !p0 || !out_dist || !out_nearest || n_envs < 1 || n_queries < 0)
+        return GS_ERR_INVALID_ARG;
+    if (!(agent_radius >= 0.0f)) return GS_ERR_INVALID_ARG;
+    if (!caps || !aligned16(caps)) return caps ? GS_ERR_ALIGNMENT : GS_ERR_INVALID_ARG;
+    if (n_queries == 0) return GS_OK;
+    int sms = 0;
+    gs_status st = device_init(&sms);
+    if (st != GS_OK) return st;
+    launch_capsule_query(caps, env_cap_off, n_envs, query_env, p0, p1, agent_radius, n_queries, out_dist, out_nearest,
+                         out_tclip, out_blocked, static_cast<cudaStream_t>(stream));
+    return check_launch();
+}
+
 gs_status gs_interpolate_joints(const float *frames, const float *t, int32_t n_avatars, int32_t n_frames,
                                 int32_t n_joints, float *out, void *stream)
 {

@@ -62,6 +62,12 @@ void launch_fk(const float *local_rot, const float *root, const float *rest, con
 void launch_interp(const float *frames, const float *t, int n_avatars, int n_frames, int n_joints, float *out,
                    int n_sms, cudaStream_t s);
 
+void launch_capsules(const float *M, const float *rest, const float *radius, const JointTree &tree, int n_avatars,
+                     float *out, cudaStream_t s);
+void launch_capsule_query(const float *caps, const int64_t *cap_off, int n_envs, const int32_t *query_env,
+                          const float *p0, const float *p1, float agent_r, int64_t n_q, float *out_dist,
+                          int32_t *out_near, float *out_t, uint8_t *out_blk, cudaStream_t s);
+
 size_t mesh_record_bytes();
 void launch_mesh(const MeshIn &in, const gs_camera *cams, const MeshTable &t, void *rec, float *rgb, float *depth,
                  cudaStream_t s);

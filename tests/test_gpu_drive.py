@@ -157,3 +157,84 @@ def test_exp2_rate_kernel(gs):
     np.testing.assert_allclose(out.cpu().numpy() / 8.0, 0.641185744, atol=1e-4)
     with pytest.raises(gs.GsError, match="INVALID_ARG"):
         gs.exp2_rate(0, 32, out)
+
+
+def _capsule_scene(gs, oracle, seed, avatars_per_env=(3, 0, 8, 1)):
+    """Capsules of avatars posed by FK in several rooms (envs), from the CUDA
+    path and from the oracle, with their env offsets."""
+    A = sum(avatars_per_env)
+    local, root = random_pose(seed, A)
+    rest = synth.REST_JOINTS.astype(np.float32)
+    radius = np.linspace(0.06, 0.12, J).astype(np.float32)
+    M = gs.forward_kinematics(T(local), T(root), T(rest), synth.PARENTS)
+    caps = gs.avatar_capsules(M, T(rest), synth.PARENTS, T(radius))
+    torch.cuda.synchronize()
+    ref = oracle.avatar_capsules(M.cpu().numpy(), rest, synth.PARENTS, radius)
+    off = np.concatenate([[0], np.cumsum(np.asarray(avatars_per_env) * J)]).astype(np.int64)
+    return caps, ref, off
+
+
+def test_avatar_capsules_match_oracle(gs, oracle):
+    caps, ref, _ = _capsule_scene(gs, oracle, 5)
+    np.testing.assert_allclose(caps.cpu().numpy(), ref, rtol=0, atol=2e-6)
+    assert np.all(caps.cpu().numpy()[:, 0, :3] == caps.cpu().numpy()[:, 0, 4:7])  # the root: a sphere
+
+
+@pytest.mark.parametrize("with_step", [False, True])
+def test_capsule_queries_match_oracle(gs, oracle, with_step):
+    """Per query: distance and nearest capsule, and for a step the blocked flag
+    and the first-contact fraction, against the FP64 oracle on the same
+    capsules.  A query whose answer an FP32 rounding could change (a second
+    capsule within 1e-5 m of the nearest, or contact within 1e-4 m of grazing:
+    the oracle's flag differs at agent radius r -/+ 1e-4) is left out of the
+    comparison of that answer; there are few of them."""
+    caps, _, off = _capsule_scene(gs, oracle, 9)
+    capf = caps.reshape(-1, 8)
+    capn = capf.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(11)
+    Q, r = 4000, 0.1
+    qe = rng.integers(0, len(off) - 1, Q).astype(np.int32)
+    p0 = np.stack([rng.uniform(0.0, 10.0, Q), rng.uniform(0.0, 8.0, Q), rng.uniform(0.1, 1.8, Q)], 1)
+    step = rng.normal(0.0, 0.4, (Q, 3))
+    step[:, 2] *= 0.1
+    p1 = p0 + step
+    # queries near the avatars, so that contacts and small distances occur
+    ci = rng.integers(0, capn.shape[0], Q)
+    near = rng.uniform(0, 1, Q) < 0.5
+    base = capn[ci, :3] + rng.normal(0, 0.3, (Q, 3))
+    envs_of_cap = np.searchsorted(off, ci, side="right") - 1
+    p0[near] = base[near]
+    qe[near] = envs_of_cap[near]
+    p1[near] = p0[near] + step[near]
+    p0 = p0.astype(np.float32)
+    p1 = p1.astype(np.float32)
+    d_off = torch.from_numpy(off).cuda()
+    dist, nearest, tclip, blocked = gs.capsule_query(capf, d_off, T(qe, torch.int32), T(p0),
+                                                     T(p1) if with_step else None, agent_radius=r)
+    torch.cuda.synchronize()
+    ref = oracle.capsule_query(capn, off, qe, p0, p1 if with_step else None, agent_radius=r)
+    dist, nearest, tclip, blocked = (x.cpu().numpy() for x in (dist, nearest, tclip, blocked))
+    has = off[qe + 1] > off[qe]
+    assert np.all(np.isinf(dist[~has])) and np.all(nearest[~has] == -1) and not blocked[~has].any()
+    np.testing.assert_allclose(dist[has], ref["dist"][has], rtol=0, atol=2e-5)
+    # nearest capsule, except where a second one is within 1e-5 m
+    second = np.full(Q, np.inf)
+    for q in np.flatnonzero(has):
+        c = capn[off[qe[q]]:off[qe[q] + 1]]
+        ab = c[:, 4:7] - c[:, :3]
+        s = np.clip(((p0[q] - c[:, :3]) * ab).sum(1) / np.maximum((ab * ab).sum(1), 1e-300), 0.0, 1.0)
+        d = np.linalg.norm(p0[q] - (c[:, :3] + s[:, None] * ab), axis=1) - c[:, 3]
+        second[q] = np.sort(d)[1] - np.sort(d)[0] if d.size > 1 else np.inf
+    clear = has & (second > 1e-5)
+    assert np.array_equal(nearest[clear], ref["nearest"][clear])
+    assert clear.mean() > 0.5
+    lo = oracle.capsule_query(capn, off, qe, p0, p1 if with_step else None, agent_radius=r - 1e-4)["blocked"]
+    hi = oracle.capsule_query(capn, off, qe, p0, p1 if with_step else None, agent_radius=r + 1e-4)["blocked"]
+    firm = lo == hi
+    assert firm.mean() > 0.99
+    assert np.array_equal(blocked.astype(bool)[firm], ref["blocked"][firm])
+    if with_step:
+        both = firm & ref["blocked"]
+        assert both.sum() > 100  # contacts are exercised
+        np.testing.assert_allclose(tclip[both], ref["tclip"][both], rtol=0, atol=2e-3)
+        assert np.all(tclip[firm & ~ref["blocked"]] == 1.0)

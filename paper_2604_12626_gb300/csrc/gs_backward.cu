@@ -811,7 +811,7 @@ __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, 
     const uint32_t nhi = w.hdr->n_heavy_items, nh = w.hdr->n_heavy;
     const uint32_t n_items = nhi + (uint32_t)w.tb->n_bins;
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&w.hdr->n_backward, 1u); // d_rec is dirty from here on
-    // the first clear_ctas CTAs (about one per SM) clear first, so that the
+    // the first clear_ctas CTAs (one per two SMs) clear first, so that the
     // store stream runs from the start beside the heavy tiles; the others take
     // tiles, then what is left of the clearing
     for (bool clearing = zw.total && blockIdx.x < zw.clear_ctas; clearing;) {
@@ -1271,7 +1271,7 @@ void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rg
             acc += (uint32_t)((zw.n[a] + kZeroFloats - 1) / kZeroFloats);
         }
         zw.total = acc;
-        zw.clear_ctas = (uint32_t)n_sms;
+        zw.clear_ctas = (uint32_t)((n_sms + 1) / 2); // half the SMs: measured fastest (all SMs, twice that: slower)
     }
     if (px == 2 && py == 2) launch_bb<2, 2>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);
     else if (px == 2) launch_bb<2, 1>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);

@@ -215,6 +215,7 @@ __device__ __forceinline__ bool may_touch_image(float mx, float my, float mz, fl
 // The next round's means, logits, scales and rotations are loaded before the
 // current round is processed.
 constexpr int kWarpQ = 64; // each queue grows by at most 32 before it is drained below 32
+constexpr int kFusedJointSlots = 96; // joint matrices a fused-LBS CTA stages (4 avatars of 24 joints)
 constexpr int kMaxViewsPerChunk = 16; // cameras of a chunk's env staged in shared memory
 
 // FUSED: the batch's avatar rows are posed by LBS here (gs_render_avatars); a
@@ -226,6 +227,8 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
     extern __shared__ __align__(16) unsigned char smem_pre[];
     __shared__ gs_camera s_cam[kMaxViewsPerChunk];
     __shared__ int64_t s_roff[kMaxViewsPerChunk];
+    // fused LBS: the joint matrices of the first avatars of the chunk's avatar rows
+    __shared__ float s_G[FUSED ? kFusedJointSlots * 12 : 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int kNW = kPreThreads / 32;
     AEntry *qa = reinterpret_cast<AEntry *>(smem_pre) + warp * kWarpQ;
@@ -244,6 +247,19 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
             s_cam[k] = cams[v];
             s_roff[k] = tb->view_rec_off[v];
         }
+    const int64_t cov_begin = tb->env_cov_begin[c.e0];
+    // avatars a_lo .. a_lo + n_stage - 1 (from the chunk's first avatar row) are
+    // staged in shared memory; rows of other avatars read their matrices from
+    // global memory
+    int a_lo = 0, n_stage = 0;
+    if (FUSED && gin.n_joints > 0 && max(c.g0, cov_begin) < c.g1) {
+        a_lo = clamp_avatar(__ldg(gin.av_of + tb->env_av_base[c.e0] + (max(c.g0, cov_begin) - cov_begin)),
+                            gin.n_avatars);
+        n_stage = min(kFusedJointSlots / gin.n_joints, gin.n_avatars - a_lo);
+        const int nf = n_stage * gin.n_joints * 12;
+        const float *src = gin.av_G + (size_t)a_lo * gin.n_joints * 12;
+        for (int k = threadIdx.x; k < nf; k += blockDim.x) s_G[k] = __ldg(src + k);
+    }
     __syncthreads();
     const int W = tb->W, H = tb->H;
     const float near_plane = tb->near_plane;
@@ -251,7 +267,6 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
     const int nwarps = blockDim.x >> 5;
     const int64_t env_base = tb->env_off[c.e0];
     const bool env_cov = gin.cov3d != nullptr;
-    const int64_t cov_begin = tb->env_cov_begin[c.e0];
     int ha = 0, ta = 0, hb = 0, tb_ = 0; // ring queues of this warp: A (to project), B (visible)
 
     // stage C on the 32 oldest visible entries (or the last few)
@@ -365,8 +380,10 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
             const int a = clamp_avatar(__ldg(gin.av_of + i), gin.n_avatars);
             const ushort4 id = clamp_ids(__ldg(reinterpret_cast<const ushort4 *>(gin.av_ids) + i), gin.n_joints);
             const float4 wt = __ldg(reinterpret_cast<const float4 *>(gin.av_weights) + i);
+            const float *Gs = a - a_lo >= 0 && a - a_lo < n_stage ? s_G + (a - a_lo) * gin.n_joints * 12
+                                                                 : gin.av_G + (size_t)a * gin.n_joints * 12;
             float mu[3], S[6];
-            lbs_gaussian(gin.av_G + (size_t)a * gin.n_joints * 12, id, wt,
+            lbs_gaussian(Gs, id, wt,
                          make_float3(__ldg(gin.av_means + 3 * i), __ldg(gin.av_means + 3 * i + 1),
                                      __ldg(gin.av_means + 3 * i + 2)),
                          make_float3(__ldg(gin.av_log_scales + 3 * i), __ldg(gin.av_log_scales + 3 * i + 1),

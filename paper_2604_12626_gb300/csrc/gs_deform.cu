@@ -29,7 +29,7 @@ struct AvIn {
 __global__ void __launch_bounds__(256) deform_kernel(AvIn in, const float *__restrict__ G, float *out_means,
                                                      float *out_cov)
 {
-    __shared__ float sG[kMaxJoints * 12];
+    __shared__ __align__(16) float sG[kMaxJoints * 12];
     const int64_t base = (int64_t)blockIdx.x * blockDim.x;
     const int64_t i = base + threadIdx.x;
     // the Gaussian's inputs are loaded first, so that they are in flight while
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256) deform_backward_kernel(AvIn in, const flo
                                                               const float *__restrict__ d_cov, float *d_cm,
                                                               float *d_cls, float *d_cq, float *d_G)
 {
-    __shared__ float sG[kMaxJoints * 12];
+    __shared__ __align__(16) float sG[kMaxJoints * 12];
     __shared__ float sdG[kDeformWarps][kMaxJoints * 12]; // per-warp joint-gradient sums
     __shared__ JointShare sj[kDeformWarps][32];
     const int64_t base = (int64_t)blockIdx.x * blockDim.x;

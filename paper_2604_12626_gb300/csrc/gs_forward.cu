@@ -126,9 +126,8 @@ static_assert(sizeof(QEntry) % 16 == 0, "queue entries are copied as 16-byte vec
 // bin counts of a queued visible (view, Gaussian).
 template <int SHT>
 __device__ __forceinline__ void finish_entry(const QEntry &en, bool active, uint32_t *hist, const Chunk &c,
-                                             const GaussIn &gin, const Ws &w)
+                                             const GaussIn &gin, const Ws &w, const Table *tb)
 {
-    const Table *tb = w.tb;
     if (active) {
         const int tpv = tb->tiles_per_view, tx_n = tb->tiles_x, tw = tb->tile_w, th = tb->tile_h;
         float idn;
@@ -212,29 +211,40 @@ __device__ __forceinline__ bool may_touch_image(float mx, float my, float mz, fl
 //   B  32 queued survivors: covariance, EWA projection, conic, radius, pixel
 //      window, exact pixel ranges;
 //   C  32 queued visible entries: SH colour, record, gradient row, bin counts.
-// The next round's means, logits, scales and rotations are loaded before the
-// current round is processed.
+// Each round's means, logits, scales and rotations are copied into a per-warp
+// shared-memory ring by cp.async two rounds ahead (one on the fused path), so
+// that two rounds of loads are in flight while a round is processed.
 constexpr int kWarpQ = 64; // each queue grows by at most 32 before it is drained below 32
 constexpr int kFusedJointSlots = 96; // joint matrices a fused-LBS CTA stages (4 avatars of 24 joints)
 constexpr int kMaxViewsPerChunk = 16; // cameras of a chunk's env staged in shared memory
+// A round's inputs in shared memory: 32 rotations (float4), then 32 each of
+// mean x, y, z, logit and log-scale x, y, z (floats): 1408 bytes per warp.
+constexpr int kRingF4 = 32 + 7 * 32 / 4;
+// rounds in the ring: three (two rounds of loads in flight) on the plain
+// path; two on the fused path, whose joint matrices take the shared memory
+template <bool FUSED> struct PreRing { static constexpr int n = FUSED ? 2 : 3; };
 
 // FUSED: the batch's avatar rows are posed by LBS here (gs_render_avatars); a
 // separate instantiation so that the plain path carries none of its registers
 template <int SHT, bool FUSED>
 __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_camera *__restrict__ cams, GaussIn gin,
-                                                                    Ws w)
+                                                                    Ws w, const __grid_constant__ Table tbp)
 {
     extern __shared__ __align__(16) unsigned char smem_pre[];
     __shared__ gs_camera s_cam[kMaxViewsPerChunk];
     __shared__ int64_t s_roff[kMaxViewsPerChunk];
     // fused LBS: the joint matrices of the first avatars of the chunk's avatar rows
-    __shared__ float s_G[FUSED ? kFusedJointSlots * 12 : 1];
+    __shared__ __align__(16) float s_G[FUSED ? kFusedJointSlots * 12 : 4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int kNW = kPreThreads / 32;
+    constexpr int kRing = PreRing<FUSED>::n;
     AEntry *qa = reinterpret_cast<AEntry *>(smem_pre) + warp * kWarpQ;
     QEntry *qb = reinterpret_cast<QEntry *>(smem_pre + kNW * kWarpQ * sizeof(AEntry)) + warp * kWarpQ;
-    uint32_t *hist = reinterpret_cast<uint32_t *>(smem_pre + kNW * kWarpQ * (sizeof(AEntry) + sizeof(QEntry)));
-    const Table *tb = w.tb;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem_pre + kNW * kWarpQ * (sizeof(AEntry) + sizeof(QEntry)) +
+                                                  kNW * kRing * kRingF4 * sizeof(float4));
+    // the table as a kernel parameter: its fields are constant-bank operands,
+    // never reloaded after the global stores of the stages
+    const Table *tb = &tbp;
     Chunk c;
     chunk_setup(tb, blockIdx.x, c);
     const int tpv = tb->tiles_per_view;
@@ -276,7 +286,7 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
         if (act) mine = qb[(hb + lane) & (kWarpQ - 1)];
         hb += n;
         __syncwarp();
-        finish_entry<SHT>(mine, act, hist, c, gin, w);
+        finish_entry<SHT>(mine, act, hist, c, gin, w, tb);
     };
     // stage B on the 32 oldest queued survivors (or the last few)
     auto stage_b = [&](int n) {
@@ -335,39 +345,54 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
         if (tb_ - hb >= 32) stage_c(32);
     };
 
-    int64_t g = c.g0 + warp * 32 + lane;
-    float mx = 0.f, my = 0.f, mz = 0.f, lo = 0.f;
-    float3 cls = make_float3(0.f, 0.f, 0.f);
-    float4 cq = make_float4(1.f, 0.f, 0.f, 0.f);
-    if (g < c.g1) {
-        mx = __ldg(gin.means + 3 * g);
-        my = __ldg(gin.means + 3 * g + 1);
-        mz = __ldg(gin.means + 3 * g + 2);
-        lo = __ldg(gin.ologits + g);
-        if (!((env_cov || FUSED) && g >= cov_begin)) { // posed rows take their covariance elsewhere
-            cls = make_float3(__ldg(gin.log_scales + 3 * g), __ldg(gin.log_scales + 3 * g + 1),
-                              __ldg(gin.log_scales + 3 * g + 2));
-            cq = __ldg(reinterpret_cast<const float4 *>(gin.quats) + g);
-        }
-    }
-    for (int64_t base = c.g0 + warp * 32; base < c.g1; base += 32 * nwarps) {
-        const bool valid = g < c.g1;
-        // prefetch the next round's means, logits, scales and rotations
-        const int64_t gn = g + 32 * nwarps;
-        float nx = 0.f, ny = 0.f, nz = 0.f, nlo = 0.f;
-        float3 nls = make_float3(0.f, 0.f, 0.f);
-        float4 nq = make_float4(1.f, 0.f, 0.f, 0.f);
-        if (gn < c.g1) {
-            nx = __ldg(gin.means + 3 * gn);
-            ny = __ldg(gin.means + 3 * gn + 1);
-            nz = __ldg(gin.means + 3 * gn + 2);
-            nlo = __ldg(gin.ologits + gn);
-            if (!((env_cov || FUSED) && gn >= cov_begin)) {
-                nls = make_float3(__ldg(gin.log_scales + 3 * gn), __ldg(gin.log_scales + 3 * gn + 1),
-                                  __ldg(gin.log_scales + 3 * gn + 2));
-                nq = __ldg(reinterpret_cast<const float4 *>(gin.quats) + gn);
+    // the round ring: round r's inputs land in buffer r % kRing, issued
+    // kRing - 1 rounds ahead by cp.async, one commit group per round and lane
+    float4 *ring = reinterpret_cast<float4 *>(smem_pre + kNW * kWarpQ * (sizeof(AEntry) + sizeof(QEntry))) +
+                   warp * kRing * kRingF4;
+    auto issue_round = [&](int64_t gg, int r) {
+        float4 *q4 = ring + (r % kRing) * kRingF4;
+        float *f = reinterpret_cast<float *>(q4 + 32);
+        if (gg < c.g1) {
+            cp_async4(f + lane, gin.means + 3 * gg);
+            cp_async4(f + 32 + lane, gin.means + 3 * gg + 1);
+            cp_async4(f + 64 + lane, gin.means + 3 * gg + 2);
+            cp_async4(f + 96 + lane, gin.ologits + gg);
+            if (!((env_cov || FUSED) && gg >= cov_begin)) { // posed rows take their covariance elsewhere
+                cp_async4(f + 128 + lane, gin.log_scales + 3 * gg);
+                cp_async4(f + 160 + lane, gin.log_scales + 3 * gg + 1);
+                cp_async4(f + 192 + lane, gin.log_scales + 3 * gg + 2);
+                cp_async16(q4 + lane, reinterpret_cast<const float4 *>(gin.quats) + gg);
             }
         }
+        cp_async_commit();
+    };
+    int64_t g = c.g0 + warp * 32 + lane;
+    const int64_t gstep = 32 * nwarps;
+#pragma unroll
+    for (int r = 0; r < kRing - 1; ++r) issue_round(g + r * gstep, r);
+    int round = 0;
+    for (int64_t base = c.g0 + warp * 32; base < c.g1; base += gstep, g += gstep, ++round) {
+        const bool valid = g < c.g1;
+        cp_async_wait<kRing - 2>(); // this round's group has landed
+        float mx = 0.f, my = 0.f, mz = 0.f, lo = 0.f;
+        float3 cls = make_float3(0.f, 0.f, 0.f);
+        float4 cq = make_float4(1.f, 0.f, 0.f, 0.f);
+        {
+            const float4 *q4 = ring + (round % kRing) * kRingF4;
+            const float *f = reinterpret_cast<const float *>(q4 + 32);
+            if (valid) {
+                mx = f[lane];
+                my = f[32 + lane];
+                mz = f[64 + lane];
+                lo = f[96 + lane];
+                if (!((env_cov || FUSED) && g >= cov_begin)) {
+                    cls = make_float3(f[128 + lane], f[160 + lane], f[192 + lane]);
+                    cq = q4[lane];
+                }
+            }
+        }
+        // the buffer of the previous round is free again (its values were used there)
+        issue_round(g + (kRing - 1) * gstep, round + kRing - 1);
         const int nv = valid ? c.nv : 0;
         // covariance source of this lane's Gaussian and the largest variance
         // of its 3D covariance for the image test
@@ -424,14 +449,8 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
             __syncwarp();
             if (ta - ha >= 32) stage_b(32);
         }
-        g = gn;
-        mx = nx;
-        my = ny;
-        mz = nz;
-        lo = nlo;
-        cls = nls;
-        cq = nq;
     }
+    cp_async_wait<0>();
     if (ta > ha) stage_b(ta - ha);
     if (tb_ > hb) stage_c(tb_ - hb);
     __syncthreads();
@@ -652,11 +671,14 @@ __global__ void __launch_bounds__(1024) scan_bins_kernel(Ws w)
 // ---------------------------------------------------------------------------
 // scatter: one key per (visible record, touched tile)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) scatter_kernel(const gs_camera *__restrict__ cams, Ws w)
+// hist_words: the preprocess's (view, tile) counter count; the shared memory
+// holds that many slots and one chunk of record indices (3 CTAs per SM at
+// 16384-Gaussian chunks and 2 KB of counters)
+__global__ void __launch_bounds__(256, 3) scatter_kernel(const gs_camera *__restrict__ cams, Ws w, int hist_words)
 {
     extern __shared__ uint32_t smem_sc[];
-    uint32_t *base = smem_sc;          // [kHistCap] next free slot per (view slot, tile)
-    uint32_t *list = smem_sc + kHistCap; // visible records of one view slot, compacted
+    uint32_t *base = smem_sc;              // [hist_words] next free slot per (view slot, tile)
+    uint32_t *list = smem_sc + hist_words; // visible records of one view slot, compacted
     __shared__ int list_n;
     const Table *tb = w.tb;
     Chunk c;
@@ -703,15 +725,31 @@ __global__ void __launch_bounds__(256) scatter_kernel(const gs_camera *__restric
         const int n = list_n;
         // each warp expands 32 records into their (record, tile) pairs, 32
         // pairs at a time, so that the per-record tile loops do not diverge
+        // the record rows of the next 32 are loaded while these are expanded
+        uint32_t nrec = 0;
+        float4 nra = make_float4(0.f, 0.f, -1.f, -1.f);
+        uint32_t nzb = 0;
+        if (warp * 32 + lane < n) {
+            nrec = list[warp * 32 + lane];
+            nra = w.rec[3 * (size_t)nrec];
+            nzb = __float_as_uint(w.rec[3 * (size_t)nrec + 2].w);
+        }
         for (int i0 = warp * 32; i0 < n; i0 += nwarps * 32) {
             const int i = i0 + lane;
             uint32_t rec = 0, zb = 0, tx0 = 0, ty0 = 0, ntx = 0, cnt = 0;
+            const float4 ra = nra;
             if (i < n) {
-                rec = list[i];
+                rec = nrec;
+                zb = nzb;
+            }
+            if (i + nwarps * 32 < n) {
+                nrec = list[i + nwarps * 32];
+                nra = w.rec[3 * (size_t)nrec];
+                nzb = __float_as_uint(w.rec[3 * (size_t)nrec + 2].w);
+            }
+            if (i < n) {
                 // the tiles of the record's pixel window, from the same FP32 values
                 // the preprocess counted them with
-                const float4 ra = w.rec[3 * (size_t)rec];
-                zb = __float_as_uint(w.rec[3 * (size_t)rec + 2].w);
                 int x0, x1, y0, y1;
                 if (pixel_range(ra.x, ra.z, cam.cx, W, x0, x1) && pixel_range(ra.y, ra.w, cam.cy, H, y0, y1)) {
                     tx0 = x0 / tw;
@@ -1443,10 +1481,19 @@ template <bool COUNT> struct BlendKernels<2, 1, COUNT> {
 // ---------------------------------------------------------------------------
 void launch_setup(const Table &tb, const Ws &w, cudaStream_t s) { setup_kernel<<<1, 256, 0, s>>>(tb, w); }
 
-constexpr int kPreSmem = (kPreThreads / 32) * kWarpQ * (int)(sizeof(AEntry) + sizeof(QEntry)) + kHistCap * 4;
+// dynamic shared memory of the preprocess: the two queues of every warp, its
+// round ring and the chunk's (view, tile) counters
+static int pre_smem(bool fused, int hist_words)
+{
+    const int ring = fused ? PreRing<true>::n : PreRing<false>::n;
+    return (kPreThreads / 32) * (kWarpQ * (int)(sizeof(AEntry) + sizeof(QEntry)) + ring * kRingF4 * 16) +
+           hist_words * 4;
+}
+constexpr int kPreSmemMax = (kPreThreads / 32) * (kWarpQ * (int)(sizeof(AEntry) + sizeof(QEntry)) + 3 * kRingF4 * 16) +
+                            kHistCap * 4;
 
-void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s,
-                       const gs_avatars *av, const float *joint_G)
+void launch_preprocess(const Table &tb, const gs_gaussians *g, const gs_camera *cams, const Ws &w, int n_chunks,
+                       int hist_words, cudaStream_t s, const gs_avatars *av, const float *joint_G)
 {
     GaussIn gin{g->means, g->log_scales, g->quats, g->opacity_logits, g->cov3d, g->sh,
                 nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0};
@@ -1458,13 +1505,14 @@ void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w
     const unsigned grid = (unsigned)n_chunks;
     if (grid == 0) return;
     const bool fused = gin.av_G != nullptr;
+    const int sm = pre_smem(fused, std::min(std::max(hist_words, 0), kHistCap));
     switch (g->sh_dtype * 2 + (fused ? 1 : 0)) {
-    case GS_SH_F16 * 2: preprocess_kernel<GS_SH_F16, false><<<grid, kPreThreads, kPreSmem, s>>>(cams, gin, w); break;
-    case GS_SH_F16 * 2 + 1: preprocess_kernel<GS_SH_F16, true><<<grid, kPreThreads, kPreSmem, s>>>(cams, gin, w); break;
-    case GS_SH_BF16 * 2: preprocess_kernel<GS_SH_BF16, false><<<grid, kPreThreads, kPreSmem, s>>>(cams, gin, w); break;
-    case GS_SH_BF16 * 2 + 1: preprocess_kernel<GS_SH_BF16, true><<<grid, kPreThreads, kPreSmem, s>>>(cams, gin, w); break;
-    case GS_SH_F32 * 2 + 1: preprocess_kernel<GS_SH_F32, true><<<grid, kPreThreads, kPreSmem, s>>>(cams, gin, w); break;
-    default: preprocess_kernel<GS_SH_F32, false><<<grid, kPreThreads, kPreSmem, s>>>(cams, gin, w); break;
+    case GS_SH_F16 * 2: preprocess_kernel<GS_SH_F16, false><<<grid, kPreThreads, sm, s>>>(cams, gin, w, tb); break;
+    case GS_SH_F16 * 2 + 1: preprocess_kernel<GS_SH_F16, true><<<grid, kPreThreads, sm, s>>>(cams, gin, w, tb); break;
+    case GS_SH_BF16 * 2: preprocess_kernel<GS_SH_BF16, false><<<grid, kPreThreads, sm, s>>>(cams, gin, w, tb); break;
+    case GS_SH_BF16 * 2 + 1: preprocess_kernel<GS_SH_BF16, true><<<grid, kPreThreads, sm, s>>>(cams, gin, w, tb); break;
+    case GS_SH_F32 * 2 + 1: preprocess_kernel<GS_SH_F32, true><<<grid, kPreThreads, sm, s>>>(cams, gin, w, tb); break;
+    default: preprocess_kernel<GS_SH_F32, false><<<grid, kPreThreads, sm, s>>>(cams, gin, w, tb); break;
     }
 }
 
@@ -1472,9 +1520,11 @@ void launch_scan(const Ws &w, cudaStream_t s) { scan_bins_kernel<<<1, 1024, 0, s
 
 constexpr int kScatterSmem = kHistCap * 4 + kChunkMax * 4;
 
-void launch_scatter(const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s)
+void launch_scatter(const gs_camera *cams, const Ws &w, int n_chunks, int hist_words, int chunk, cudaStream_t s)
 {
-    if (n_chunks) scatter_kernel<<<n_chunks, 256, kScatterSmem, s>>>(cams, w);
+    hist_words = std::min(std::max(hist_words, 0), kHistCap);
+    chunk = std::min(std::max(chunk, 1), kChunkMax);
+    if (n_chunks) scatter_kernel<<<n_chunks, 256, (hist_words + chunk) * 4, s>>>(cams, w, hist_words);
 }
 
 // q_warps: warps of a quarter-list CTA (2 x 1 pixels per lane), else 0
@@ -1554,7 +1604,7 @@ cudaError_t configure_forward_kernels()
                          reinterpret_cast<const void *>(preprocess_kernel<GS_SH_BF16, false>),
                          reinterpret_cast<const void *>(preprocess_kernel<GS_SH_BF16, true>)};
     for (const void *k : pre)
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kPreSmem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kPreSmemMax);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScatterSmem);
     return e;

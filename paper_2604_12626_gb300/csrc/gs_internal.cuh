@@ -247,6 +247,11 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
@@ -468,6 +473,20 @@ __device__ __forceinline__ int clamp_avatar(int a, int na) { return a < 0 ? 0 : 
 __device__ __forceinline__ void blend_matrix(const float *Gs, const ushort4 id, const float4 wt, float (&A)[12])
 {
     const float *g0 = Gs + 12 * id.x, *g1 = Gs + 12 * id.y, *g2 = Gs + 12 * id.z, *g3 = Gs + 12 * id.w;
+    if ((reinterpret_cast<uintptr_t>(Gs) & 15u) == 0) {
+        // 16-byte rows: three vector loads per joint instead of twelve (the
+        // joints of a warp's lanes differ, so shared-memory wavefronts count)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const float4 a0 = reinterpret_cast<const float4 *>(g0)[r], a1 = reinterpret_cast<const float4 *>(g1)[r],
+                         a2 = reinterpret_cast<const float4 *>(g2)[r], a3 = reinterpret_cast<const float4 *>(g3)[r];
+            A[4 * r + 0] = __fmaf_rn(wt.w, a3.x, __fmaf_rn(wt.z, a2.x, __fmaf_rn(wt.y, a1.x, __fmul_rn(wt.x, a0.x))));
+            A[4 * r + 1] = __fmaf_rn(wt.w, a3.y, __fmaf_rn(wt.z, a2.y, __fmaf_rn(wt.y, a1.y, __fmul_rn(wt.x, a0.y))));
+            A[4 * r + 2] = __fmaf_rn(wt.w, a3.z, __fmaf_rn(wt.z, a2.z, __fmaf_rn(wt.y, a1.z, __fmul_rn(wt.x, a0.z))));
+            A[4 * r + 3] = __fmaf_rn(wt.w, a3.w, __fmaf_rn(wt.z, a2.w, __fmaf_rn(wt.y, a1.w, __fmul_rn(wt.x, a0.w))));
+        }
+        return;
+    }
 #pragma unroll
     for (int e = 0; e < 12; ++e)
         A[e] = __fmaf_rn(wt.w, g3[e], __fmaf_rn(wt.z, g2[e], __fmaf_rn(wt.y, g1[e], __fmul_rn(wt.x, g0[e]))));

@@ -11,10 +11,13 @@ cudaError_t configure_forward_kernels();
 cudaError_t configure_backward_kernels();
 
 void launch_setup(const Table &tb, const Ws &w, cudaStream_t s);
-void launch_preprocess(const gs_gaussians *g, const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s,
-                       const gs_avatars *av = nullptr, const float *joint_G = nullptr);
+// hist_words: (view, tile) counters a chunk keeps in shared memory, at least
+// min(kHistCap, most views of an env x tiles per view)
+void launch_preprocess(const Table &tb, const gs_gaussians *g, const gs_camera *cams, const Ws &w, int n_chunks,
+                       int hist_words, cudaStream_t s, const gs_avatars *av = nullptr, const float *joint_G = nullptr);
 void launch_scan(const Ws &w, cudaStream_t s);
-void launch_scatter(const gs_camera *cams, const Ws &w, int n_chunks, cudaStream_t s);
+// chunk: Gaussians per chunk (the record list it keeps in shared memory)
+void launch_scatter(const gs_camera *cams, const Ws &w, int n_chunks, int hist_words, int chunk, cudaStream_t s);
 cudaError_t configure_sort_kernels();
 void launch_exp2_rate(int n_blocks, int iters, float *out, cudaStream_t s);
 int merge_passes_for_capacity(int64_t pair_capacity);

@@ -189,14 +189,17 @@ def project(g: dict, cam, W: int, H: int, near: float = 0.2) -> dict:
         visible=np.zeros(n, np.int32), u=np.zeros(n), v=np.zeros(n), z=np.zeros(n),
         zkey=np.zeros(n, np.float32), cov2=np.zeros((n, 3)), conic=np.zeros((n, 3)),
         opacity=np.zeros(n), rgb=np.zeros((n, 3)), radius=np.zeros(n, np.int32), r3=np.zeros(n),
-        err_uv=np.zeros((n, 2)),
+        err=np.zeros((n, 6)),
     )
     L.or_project(n, _p(G["means"]), _p(G["log_scales"]), _p(G["quats"]), _p(G["ologits"]), _p(G["sh"]),
                  _p(G["cov3d"]), _p(G["use_cov"]), _p(G["inexact"]), _p(G["dirmat"]), _p(cam64), W, H, near,
                  _p(out["visible"]), _p(out["u"]), _p(out["v"]), _p(out["z"]), _p(out["zkey"]),
                  _p(out["cov2"]), _p(out["conic"]), _p(out["opacity"]), _p(out["rgb"]),
-                 _p(out["radius"]), _p(out["r3"]), _p(out["err_uv"]))
+                 _p(out["radius"]), _p(out["r3"]), _p(out["err"]))
     out["visible"] = out["visible"].astype(bool)
+    # FP32 error bounds the ambiguity mask uses: of u, v (pixels), of 3 sqrt(lambda)
+    # and of the conic entries A, B, C
+    out["err_uv"], out["err_r3"], out["err_conic"] = out["err"][:, :2], out["err"][:, 2], out["err"][:, 3:6]
     return out
 
 

@@ -262,10 +262,14 @@ typedef struct {
     double u, v, J[6], T[6], cov2[3], det, conic[3];
     double tx, ty;
     int clampx, clampy;
-    double r3;
+    double r3, er3; /* 3 sqrt(lambda) and its FP32 error bound */
     int32_t r, r_lo, r_hi;
     double opacity, rgb[3], raw[3], dir[3], dnorm;
-    double du, dv; /* FP32 error model of (u, v) in pixels */
+    double du, dv; /* FP32 error bounds of (u, v) in pixels */
+    double eA, eB, eC; /* FP32 error bounds of the conic entries */
+    double ea, eb, ec; /* FP32 error bounds of the 2D covariance entries a, b, c */
+    double rel_conic;  /* relative error of the conic's own roundings */
+    double ez;         /* FP32 error bound of the depth key (inexact inputs only) */
     int cand;      /* footprint under r_hi touches the image */
     int visible;   /* footprint under r touches the image */
 } proj_t;
@@ -280,6 +284,178 @@ static int footprint_on_image(double u, double v, int32_t r, int W, int H)
     if (jlo < 0) jlo = 0;
     if (jhi > H - 1) jhi = H - 1;
     return ilo <= ihi && jlo <= jhi;
+}
+
+/* ------------------------------------------------------------------------ */
+/* First-order FP32 error bounds.  The CUDA path computes the projection in   */
+/* single precision; the ambiguity mask needs, for each decision it takes,    */
+/* a bound on how far its FP32 input can lie from the FP64 value here.  Each  */
+/* bound follows the CUDA path's evaluation order: an expression evaluated    */
+/* with n roundings of terms of magnitudes m_i is off by at most              */
+/* gamma(n) sum m_i (unit roundoff U = 2^-24, gamma(n) = nU / (1 - nU)), and  */
+/* input errors propagate through absolute first-order sensitivities.         */
+/* Library functions enter with their documented accuracy: expf within 2 ulp, */
+/* sqrtf and division correctly rounded.  One ulp is at most 2U relative.     */
+/* Posed (inexact) inputs were produced by an FP32 LBS of rigid joint         */
+/* transforms applied to canonical Gaussians within 2 m (L1) of the canonical */
+/* origin; their mean and covariance errors are bounded under that premise.   */
+/* ------------------------------------------------------------------------ */
+#define U32 (1.0 / 16777216.0)
+static double gam(int n) { return n * U32 / (1.0 - n * U32); }
+#define E_ALPHA (24.0 * U32)
+
+static void fp32_bounds(proj_t *o, const double *ls, const double *q, int use_cov, int inexact, const cam_t *k)
+{
+    const double *d = o->d, *mu = o->mu;
+    /* posed mean: blended 3x4 matrix (4 roundings per entry) applied to the
+     * canonical mean (3 roundings): |dmu_r| <= 7U (|mu_r| + 3 |m|_1), |m|_1 <= 2 */
+    double em[3] = {0.0, 0.0, 0.0};
+    if (inexact)
+        for (int r = 0; r < 3; ++r) em[r] = (gam(4) + gam(3)) * (fabs(mu[r]) + 6.0);
+    /* d = mu - C (one rounding); p_r = sum_j W_rj d_j (three roundings, the
+     * depth key as well); |W_rj| <= 1 */
+    double ed[3], ep[3];
+    for (int j = 0; j < 3; ++j) ed[j] = U32 * fabs(d[j]) + em[j];
+    for (int r = 0; r < 3; ++r) {
+        double a = 0.0, b = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            a += fabs(k->R[3 * r + j]) * ed[j];
+            b += fabs(k->R[3 * r + j] * d[j]);
+        }
+        ep[r] = a + gam(3) * b;
+    }
+    const double px = o->p[0], py = o->p[1], pz = o->p[2];
+    o->ez = inexact ? ep[2] : 0.0; /* exact inputs: the key is the FP32 one here too */
+    /* u - cx = fx (px / pz): a division and a product */
+    const double tx0 = px / pz, ty0 = py / pz;
+    o->du = k->fx / pz * (ep[0] + fabs(tx0) * ep[2]) + gam(2) * fabs(k->fx * tx0);
+    o->dv = k->fy / pz * (ep[1] + fabs(ty0) * ep[2]) + gam(2) * fabs(k->fy * ty0);
+    /* Jacobian: j00 = fx / pz, j02 = -(fx tx) / pz with tx = px / pz, or the
+     * clamp limit 1.3 (W / 2) / fx (three roundings) */
+    const double tx = o->tx, ty = o->ty;
+    const double etx = o->clampx ? gam(3) * fabs(tx) : (ep[0] + fabs(tx0) * ep[2]) / pz + U32 * fabs(tx0);
+    const double ety = o->clampy ? gam(3) * fabs(ty) : (ep[1] + fabs(ty0) * ep[2]) / pz + U32 * fabs(ty0);
+    const double j00 = k->fx / pz, j02 = k->fx * fabs(tx) / pz, j11 = k->fy / pz, j12 = k->fy * fabs(ty) / pz;
+    const double ej00 = j00 * (U32 + ep[2] / pz), ej11 = j11 * (U32 + ep[2] / pz);
+    const double ej02 = k->fx / pz * (fabs(tx) * (gam(2) + ep[2] / pz) + etx);
+    const double ej12 = k->fy / pz * (fabs(ty) * (gam(2) + ep[2] / pz) + ety);
+    /* T = J W: two roundings per entry */
+    double et[6];
+    for (int c = 0; c < 3; ++c) {
+        et[c] = fabs(k->R[c]) * ej00 + fabs(k->R[6 + c]) * ej02 + gam(2) * (j00 * fabs(k->R[c]) + j02 * fabs(k->R[6 + c]));
+        et[3 + c] = fabs(k->R[3 + c]) * ej11 + fabs(k->R[6 + c]) * ej12 +
+                    gam(2) * (j11 * fabs(k->R[3 + c]) + j12 * fabs(k->R[6 + c]));
+    }
+    /* 3D covariance */
+    double eS[9];
+    const double *S = o->Sigma;
+    if (!use_cov) {
+        /* normalised rotation: 1/sqrt(|q|^2) within 4U, components within 5U,
+         * each entry of R(q) within 25U absolute; scales exp(s) within 2 ulp (4U);
+         * M = R diag(scale) (one rounding): |dM_ik| <= scale_k (25U + 5U |R_ik|);
+         * Sigma_ij = sum_k M_ik M_jk (three roundings) */
+        double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        double qn[4] = {q[0] / n, q[1] / n, q[2] / n, q[3] / n};
+        double R[9];
+        quat_rot(qn, R);
+        double sc[3] = {exp(ls[0]), exp(ls[1]), exp(ls[2])};
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double acc = 0.0;
+                for (int kk = 0; kk < 3; ++kk) {
+                    const double ri = fabs(R[3 * i + kk]), rj = fabs(R[3 * j + kk]);
+                    acc += sc[kk] * sc[kk] * ((25.0 * U32 + 5.0 * U32 * rj) * ri + (25.0 * U32 + 5.0 * U32 * ri) * rj +
+                                              gam(3) * ri * rj);
+                }
+                eS[3 * i + j] = acc;
+            }
+    } else {
+        /* a given covariance is exact; a posed one (A3 Sigma A3^T in FP32 from
+         * the FP32 Sigma above, A3 a blend of rotations): within 240U tr(Sigma) */
+        const double tr = S[0] + S[4] + S[8];
+        for (int i = 0; i < 9; ++i) eS[i] = inexact ? 240.0 * U32 * tr : 0.0;
+    }
+    /* Sigma2 = T Sigma T^T + 0.3 I: u = Sigma t (three roundings), a = t . u +
+     * 0.3 (four roundings, 0.3f differs from 0.3 by 1.2e-8) */
+    const double *T = o->T;
+    double uu[2][3], eu[2][3];
+    for (int r = 0; r < 2; ++r)
+        for (int i = 0; i < 3; ++i) {
+            double v = 0.0, m = 0.0, e = 0.0;
+            for (int j = 0; j < 3; ++j) {
+                v += S[3 * i + j] * T[3 * r + j];
+                m += fabs(S[3 * i + j] * T[3 * r + j]);
+                e += eS[3 * i + j] * fabs(T[3 * r + j]) + fabs(S[3 * i + j]) * et[3 * r + j];
+            }
+            uu[r][i] = v;
+            eu[r][i] = gam(3) * m + e;
+        }
+    double e2[3]; /* a, b, c */
+    for (int x = 0; x < 3; ++x) {
+        const int r = x == 2 ? 1 : 0, w = x == 0 ? 0 : 1; /* a = t0 . u0, b = t0 . u1, c = t1 . u1 */
+        double m = 0.0, e = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            m += fabs(T[3 * r + i] * uu[w][i]);
+            e += fabs(T[3 * r + i]) * eu[w][i] + et[3 * r + i] * fabs(uu[w][i]);
+        }
+        e2[x] = x == 1 ? gam(3) * m + e : gam(4) * (m + DILATION) + e + 1.2e-8;
+    }
+    const double a = o->cov2[0], b = o->cov2[1], c = o->cov2[2], det = o->det;
+    o->ea = e2[0]; o->eb = e2[1]; o->ec = e2[2];
+    /* An error dSigma2 of the FP32 2D covariance moves the conic Q = Sigma2^-1
+     * by -Q dSigma2 Q (first order), the power -d^T Q d / 2 by (Qd)^T dSigma2
+     * (Qd) / 2 and the largest eigenvalue by v^T dSigma2 v (v its unit
+     * eigenvector).  On top come the roundings of the conic itself: det = a c -
+     * b b (two roundings, under either contraction within U (ac + b^2) + U det),
+     * the reciprocal and the product: relative rel_conic. */
+    o->rel_conic = det > 0.0 ? U32 * (fabs(a * c) + b * b) / det + 3.0 * U32 : 0.0;
+    const double Q[4] = {o->conic[0], o->conic[1], o->conic[1], o->conic[2]};
+    const double E[4] = {e2[0], e2[1], e2[1], e2[2]};
+    double eq[3] = {0.0, 0.0, 0.0}; /* |Q| |dSigma2| |Q| at (0,0), (0,1), (1,1) */
+    const int ri[3] = {0, 0, 1}, ci[3] = {0, 1, 1};
+    for (int x = 0; x < 3; ++x)
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) eq[x] += fabs(Q[2 * ri[x] + i]) * E[2 * i + j] * fabs(Q[2 * j + ci[x]]);
+    o->eA = eq[0] + fabs(o->conic[0]) * o->rel_conic;
+    o->eB = eq[1] + fabs(o->conic[1]) * o->rel_conic;
+    o->eC = eq[2] + fabs(o->conic[2]) * o->rel_conic;
+    /* radius: lambda = mid + sqrt(max(0.1, x)), mid = (a + c) / 2, x = mid^2 - det.
+     * Input errors: v^T dSigma2 v where the floor is not active, the error of
+     * mid where it is (both near the floor).  Roundings: mid (U mid), x (mid^2
+     * from the rounded mid, the det's own rounding, the fma: 2U mid^2 + U (ac +
+     * b^2 + det) + U |x|), the square root (U), the sum (U), then 3 sqrt(.) */
+    const double mid = 0.5 * (a + c);
+    const double x = mid * mid - det;
+    const double disc = x > 0.0 ? x : 0.0;
+    const double lmax = mid + sqrt(disc);
+    /* unit eigenvector of the largest eigenvalue of [[a, b], [b, c]] */
+    double vx = b, vy = lmax - a;
+    if (fabs(vx) + fabs(vy) < 1e-300 * (fabs(a) + fabs(c))) { vx = a >= c ? 1.0 : 0.0; vy = a >= c ? 0.0 : 1.0; }
+    if (fabs(b) < 1e-12 * (fabs(a) + fabs(c))) { vx = a >= c ? 1.0 : 0.0; vy = a >= c ? 0.0 : 1.0; }
+    const double vn = sqrt(vx * vx + vy * vy);
+    vx /= vn; vy /= vn;
+    const double eig_in = e2[0] * vx * vx + 2.0 * e2[1] * fabs(vx * vy) + e2[2] * vy * vy;
+    const double emid_in = 0.5 * (e2[0] + e2[2]);
+    const double xr = 2.0 * U32 * mid * mid + U32 * (fabs(a * c) + b * b + fabs(det)) + U32 * fabs(x);
+    /* input error of x = mid^2 - det: (lambda_1 - lambda_2)^2 / 4 moves by at most
+     * (lambda_1 - lambda_2)/2 times the eigenvalues' moves, each below |dSigma2|_2 */
+    const double nrm = e2[0] + e2[2] + 2.0 * e2[1];
+    const double xin = sqrt(disc) * nrm;
+    const double ex = xr + xin;
+    const double xm = x > 0.1 ? x : 0.1;
+    double elam;
+    if (x - ex > 0.1) {
+        /* floor inactive: input error through the eigenvalue, rounding through x */
+        elam = eig_in + xr / (2.0 * sqrt(xm)) + U32 * sqrt(xm) + U32 * mid + U32 * (mid + sqrt(xm));
+    } else if (x + ex < 0.1) {
+        /* floor active: lambda = mid + sqrt(0.1f) */
+        elam = emid_in + U32 * mid + U32 * sqrt(0.1) + U32 * (mid + sqrt(0.1)) + 1.5e-9;
+    } else {
+        elam = (eig_in > emid_in ? eig_in : emid_in) + ex / (2.0 * sqrt(0.1)) + U32 * mid +
+               U32 * (mid + sqrt(xm)) + U32 * sqrt(xm) + 1.5e-9;
+    }
+    const double lam = mid + sqrt(xm);
+    o->er3 = 1.5 * elam / sqrt(lam) + gam(2) * o->r3;
 }
 
 /* Returns 0 when the Gaussian is culled by the near plane or a singular conic. */
@@ -339,23 +515,16 @@ static int project_one(const double *mu, const double *ls, const double *q, doub
     double lam = mid + sqrt(disc);
     o->r3 = 3.0 * sqrt(lam);
     o->r = (int32_t)ceil(o->r3);
+    /* FP32 error bounds of what the CUDA path computes in single precision */
+    fp32_bounds(o, ls, q, cov3d != NULL, inexact, k);
     /* FP32 can round 3 sqrt(lambda) to the other side of an integer */
     double k3 = floor(o->r3 + 0.5);
-    if (fabs(o->r3 - k3) <= 4e-6 * o->r3 + 1e-7 && k3 >= 1.0) {
+    if (fabs(o->r3 - k3) <= o->er3 && k3 >= 1.0) {
         o->r_lo = (int32_t)k3;
         o->r_hi = (int32_t)k3 + 1;
     } else {
         o->r_lo = o->r_hi = o->r;
     }
-    /* FP32 error model of u, v: rounding of d, of p and of the projection */
-    double dl1 = fabs(o->d[0]) + fabs(o->d[1]) + fabs(o->d[2]);
-    double pl1 = fabs(px) + fabs(py) + fabs(pz);
-    /* bound on |u_fp32 - u|: a few single-precision roundings of d, p and of
-     * the projection; measured FP32 errors stay below a third of it */
-    double mu_err = inexact ? 3e-7 * (fabs(mu[0]) + fabs(mu[1]) + fabs(mu[2]) + 1.0) : 0.0;
-    double pos_err = 1e-7 * (dl1 + pl1) + mu_err;
-    o->du = k->fx * pos_err / pz * (1.0 + fabs(tx)) + 1e-7 * fabs(o->u - k->cx) + 1e-7;
-    o->dv = k->fy * pos_err / pz * (1.0 + fabs(ty)) + 1e-7 * fabs(o->v - k->cy) + 1e-7;
     o->cand = footprint_on_image(o->u, o->v, o->r_hi, W, H);
     o->visible = footprint_on_image(o->u, o->v, o->r, W, H);
     if (!o->cand) return 0;
@@ -391,7 +560,7 @@ int64_t or_project(int64_t n, const double *means, const double *log_scales, con
                    const double *dirmat, const double *cam,
                    int32_t W, int32_t H, double near_plane, int32_t *visible, double *u, double *v, double *z, float *zkey,
                    double *cov2, double *conic, double *opacity, double *rgb, int32_t *radius, double *r3,
-                   double *err_uv)
+                   double *err)
 {
     cam_t k;
     load_cam(cam, &k);
@@ -414,9 +583,9 @@ int64_t or_project(int64_t n, const double *means, const double *log_scales, con
         opacity[g] = o.opacity;
         radius[g] = o.r;
         r3[g] = o.r3;
-        if (err_uv) {
-            err_uv[2 * g] = o.du;
-            err_uv[2 * g + 1] = o.dv;
+        if (err) { /* FP32 error bounds: u, v, 3 sqrt(lambda), conic A, B, C */
+            const double e6[6] = {o.du, o.dv, o.er3, o.eA, o.eB, o.eC};
+            for (int i = 0; i < 6; ++i) err[6 * g + i] = e6[i];
         }
     }
     return nvis;
@@ -428,7 +597,7 @@ int64_t or_project(int64_t n, const double *means, const double *log_scales, con
 /* order, so their results agree bit for bit.                                 */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-    double u, v, z, A, B, C, o, rgb[3], du, dv;
+    double u, v, z, A, B, C, o, rgb[3], du, dv, ea, eb, ec, rel_conic, ez;
     int32_t r, r_lo, r_hi;
     float zkey;
     uint8_t inexact;
@@ -439,6 +608,7 @@ typedef struct {
     double T, C[3], D, relT;
     int32_t ncov, n, ncov_last, last, done;
     float prev_zkey;
+    double prev_ez;
     int32_t have_prev, prev_inexact;
     uint8_t amb;
     int64_t evals;
@@ -463,12 +633,18 @@ static void blend_step(pix_t *s, const cand_t *g, int i, int j, int32_t pos)
     if (s->done) return;
     double dx = g->u - (double)i, dy = g->v - (double)j;
     double m = fabs(dx) > fabs(dy) ? fabs(dx) : fabs(dy);
-    double eps = (g->du > g->dv ? g->du : g->dv) + 1e-6;
+    /* FP32 offsets: (u - cx) - (i - cx), i - cx exact, one rounding */
+    const double edx = g->du + U32 * fabs(dx), edy = g->dv + U32 * fabs(dy);
+    double eps = edx > edy ? edx : edy;
     if (m > g->r_hi + eps) return;
     double q = g->A * dx * dx + g->C * dy * dy;
     double power = -0.5 * q - g->B * dx * dy;
-    double dpow = fabs(g->A * dx + g->B * dy) * g->du + fabs(g->C * dy + g->B * dx) * g->dv +
-                  2e-6 * (0.5 * q + fabs(g->B * dx * dy)) + 1e-6;
+    /* power in FP32: three roundings on each term and the conic's own
+     * (rel_conic); the offsets' errors through dpower/dd = -Q d = -w, the 2D
+     * covariance's through (w^T dSigma2 w) / 2; 1e-9 for second-order terms */
+    const double wx = g->A * dx + g->B * dy, wy = g->B * dx + g->C * dy;
+    double dpow = fabs(wx) * edx + fabs(wy) * edy + (gam(3) + g->rel_conic) * (0.5 * q + fabs(g->B * dx * dy)) +
+                  0.5 * (g->ea * wx * wx + 2.0 * g->eb * fabs(wx * wy) + g->ec * wy * wy) + 1e-9;
     if (m >= g->r_lo - eps && m <= g->r_hi + eps) {
         /* coverage can flip under FP32 rounding of u, v or of the radius */
         s->amb |= AMB_COUNT | AMB_FOOTPRINT;
@@ -478,31 +654,42 @@ static void blend_step(pix_t *s, const cand_t *g, int i, int j, int32_t pos)
     if (s->have_prev && (g->inexact || s->prev_inexact)) {
         float lo = s->prev_zkey < g->zkey ? s->prev_zkey : g->zkey;
         float hi = s->prev_zkey < g->zkey ? g->zkey : s->prev_zkey;
-        if ((double)hi - (double)lo <= 8.0 * (double)FLT_EPSILON * (double)hi) s->amb |= AMB_VALUE | AMB_COUNT | AMB_ORDER;
+        if ((double)hi - (double)lo <= s->prev_ez + g->ez) s->amb |= AMB_VALUE | AMB_COUNT | AMB_ORDER;
     }
     s->have_prev = 1;
     s->prev_zkey = g->zkey;
     s->prev_inexact = g->inexact;
+    s->prev_ez = g->ez;
     s->ncov += 1;
     s->evals += 1;
+    /* power <= 0 decision (a positive FP32 power skips the pair) */
+    if (fabs(power) <= dpow && g->o >= ALPHA_MIN) s->amb |= AMB_COUNT | AMB_VALUE;
     if (power > 0.0) return;
     double G = exp(power);
     double a_raw = g->o * G;
     double alpha = a_raw < ALPHA_MAX ? a_raw : ALPHA_MAX;
     double cmax = maxabs3(g->rgb) + 1.0;
-    /* alpha >= 1/255 decision */
-    if (fabs(power + log(g->o) - log(ALPHA_MIN)) <= dpow + 2e-6) {
+    /* alpha >= 1/255 decision: ln alpha in FP32 is off by at most dpow plus
+     * E_ALPHA, the relative errors of __expf (2 + floor(1.173 |power|) ulp,
+     * at most 8 ulp = 16U on the range where alpha can reach 1/255), of the
+     * opacity (expf, an add and a division: 6U), of their product (U) and of
+     * the FP32 threshold constants (U) */
+    if (fabs(power + log(g->o) - log(ALPHA_MIN)) <= dpow + E_ALPHA) {
         s->amb |= AMB_COUNT | AMB_ALPHA;
         if (ALPHA_MIN * s->T * cmax > 0.5e-4 || ALPHA_MIN * s->T * g->z > 0.5e-4 * (s->D + ALPHA_MIN * s->T * g->z))
             s->amb |= AMB_VALUE;
     }
     if (alpha < ALPHA_MIN) return;
     /* alpha = min(0.99, .) decision: same error bound as the 1/255 test */
-    if (fabs(power + log(g->o) - log(ALPHA_MAX)) <= dpow + 2e-6) s->amb |= AMB_CLAMP;
+    if (fabs(power + log(g->o) - log(ALPHA_MAX)) <= dpow + E_ALPHA) s->amb |= AMB_CLAMP;
     double Tn = s->T * (1.0 - alpha);
-    double relTn = s->relT + 4.8e-7 + (a_raw < ALPHA_MAX ? alpha / (1.0 - alpha) * (dpow + 2e-6) : 0.0);
-    /* T (1 - alpha) < 1e-4 decision */
-    if (fabs(Tn - T_STOP) <= T_STOP * relTn + 1e-12) {
+    /* relative FP32 error of T: two roundings per step (1 - alpha, the
+     * product), alpha's own error through alpha / (1 - alpha), and at the
+     * clamp the FP32 constant: 1 - 0.99f = 0.0099999905 (16.1U off 0.01) */
+    double relTn = s->relT + gam(2) +
+                   (a_raw < ALPHA_MAX ? alpha / (1.0 - alpha) * (dpow + E_ALPHA) : 16.1 * U32);
+    /* T (1 - alpha) < 1e-4 decision (1e-4f is within U/2 of 1e-4) */
+    if (fabs(Tn - T_STOP) <= T_STOP * (relTn + U32) + 1e-15) {
         s->amb |= AMB_COUNT | AMB_STOP;
         double ec = alpha * s->T * (maxabs3(g->rgb) + 1e-30);
         double ed = alpha * s->T * g->z;
@@ -557,6 +744,7 @@ static int64_t build_candidates(int64_t n, const double *means, const double *ls
         t->o = o.opacity;
         for (int i = 0; i < 3; ++i) t->rgb[i] = o.rgb[i];
         t->du = o.du; t->dv = o.dv;
+        t->ea = o.ea; t->eb = o.eb; t->ec = o.ec; t->rel_conic = o.rel_conic; t->ez = o.ez;
         t->r = o.r; t->r_lo = o.r_lo; t->r_hi = o.r_hi;
         t->zkey = o.zkey;
         t->inexact = (uint8_t)inx;

@@ -441,7 +441,9 @@ gs_status gs_render_backward(const gs_gaussians *g, const gs_batch *batch, const
     }
     {
         Stage st8(8, s);
-        launch_preprocess_backward(g, cams, w, o, p.n_chunks, overwrite, s);
+        Table t;
+        fill_table(p, batch, cfg, sms, t);
+        launch_preprocess_backward(t, g, cams, w, o, p.n_chunks, overwrite, s);
     }
     return check_launch();
 }

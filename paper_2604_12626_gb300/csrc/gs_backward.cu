@@ -944,9 +944,8 @@ __device__ __forceinline__ void sh_weighted(const void *sh, int64_t g, const flo
 // 128-byte lines of mostly unseen neighbours.
 template <int SHT, bool OVERWRITE>
 __device__ __forceinline__ void gaussian_backward(const gs_camera *__restrict__ cams, const GaussInB &gin, const Ws &w,
-                                                  const GradOut &o, int64_t g, int e)
+                                                  const Table *tb, const GradOut &o, int64_t g, int e)
 {
-    const Table *tb = w.tb;
     const int vb = tb->env_view_begin[e], ve = tb->env_view_begin[e + 1];
     const int64_t local = g - tb->env_off[e];
     const bool use_cov = gin.cov3d != nullptr && g >= tb->env_cov_begin[e];
@@ -1133,10 +1132,12 @@ constexpr int kBwdWarpQ = 64;
 
 template <int SHT, bool OVERWRITE>
 __global__ void __launch_bounds__(256, 2) preprocess_backward_kernel(const gs_camera *__restrict__ cams, GaussInB gin,
-                                                                     Ws w, GradOut o)
+                                                                     Ws w, GradOut o, const __grid_constant__ Table tbp)
 {
     __shared__ uint32_t qs[8][kBwdWarpQ];
-    const Table *tb = w.tb;
+    // the table as a kernel parameter: constant-bank operands, never reloaded
+    // after the gradient stores
+    const Table *tb = &tbp;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     uint32_t *q = qs[warp];
     int lo = 0, hi = tb->n_envs - 1; // env of the chunk (chunks never straddle envs)
@@ -1168,11 +1169,11 @@ __global__ void __launch_bounds__(256, 2) preprocess_backward_kernel(const gs_ca
             const int64_t gg = g0 + q[(head + lane) & (kBwdWarpQ - 1)];
             head += 32;
             __syncwarp();
-            gaussian_backward<SHT, OVERWRITE>(cams, gin, w, o, gg, lo);
+            gaussian_backward<SHT, OVERWRITE>(cams, gin, w, tb, o, gg, lo);
         }
     }
     if (lane < tail - head)
-        gaussian_backward<SHT, OVERWRITE>(cams, gin, w, o, g0 + q[(head + lane) & (kBwdWarpQ - 1)], lo);
+        gaussian_backward<SHT, OVERWRITE>(cams, gin, w, tb, o, g0 + q[(head + lane) & (kBwdWarpQ - 1)], lo);
 }
 
 // ---------------------------------------------------------------------------
@@ -1280,24 +1281,24 @@ void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rg
 }
 
 template <bool OW>
-static void launch_pb(const gs_gaussians *g, const gs_camera *cams, const Ws &w, const GradOut &o, unsigned grid,
-                      cudaStream_t s)
+static void launch_pb(const Table &tb, const gs_gaussians *g, const gs_camera *cams, const Ws &w, const GradOut &o,
+                      unsigned grid, cudaStream_t s)
 {
     GaussInB gin{g->means, g->log_scales, g->quats, g->opacity_logits, g->cov3d, g->sh};
     switch (g->sh_dtype) {
-    case GS_SH_F16: preprocess_backward_kernel<GS_SH_F16, OW><<<grid, 256, 0, s>>>(cams, gin, w, o); break;
-    case GS_SH_BF16: preprocess_backward_kernel<GS_SH_BF16, OW><<<grid, 256, 0, s>>>(cams, gin, w, o); break;
-    default: preprocess_backward_kernel<GS_SH_F32, OW><<<grid, 256, 0, s>>>(cams, gin, w, o); break;
+    case GS_SH_F16: preprocess_backward_kernel<GS_SH_F16, OW><<<grid, 256, 0, s>>>(cams, gin, w, o, tb); break;
+    case GS_SH_BF16: preprocess_backward_kernel<GS_SH_BF16, OW><<<grid, 256, 0, s>>>(cams, gin, w, o, tb); break;
+    default: preprocess_backward_kernel<GS_SH_F32, OW><<<grid, 256, 0, s>>>(cams, gin, w, o, tb); break;
     }
 }
 
-void launch_preprocess_backward(const gs_gaussians *g, const gs_camera *cams, const Ws &w, const GradOut &o,
-                                int n_chunks, bool overwrite, cudaStream_t s)
+void launch_preprocess_backward(const Table &tb, const gs_gaussians *g, const gs_camera *cams, const Ws &w,
+                                const GradOut &o, int n_chunks, bool overwrite, cudaStream_t s)
 {
     const unsigned grid = (unsigned)n_chunks;
     if (!grid) return;
-    if (overwrite) launch_pb<true>(g, cams, w, o, grid, s);
-    else launch_pb<false>(g, cams, w, o, grid, s);
+    if (overwrite) launch_pb<true>(tb, g, cams, w, o, grid, s);
+    else launch_pb<false>(tb, g, cams, w, o, grid, s);
 }
 
 cudaError_t configure_backward_kernels()

@@ -51,8 +51,8 @@ void launch_clear_record_grads(const Ws &w, int64_t n_records, int n_sms, cudaSt
 void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,
                            int px, int py, int threads, int batch_depth, int n_sms, const GradOut *clear, int64_t n,
                            cudaStream_t s);
-void launch_preprocess_backward(const gs_gaussians *g, const gs_camera *cams, const Ws &w, const GradOut &o,
-                                int n_chunks, bool overwrite, cudaStream_t s);
+void launch_preprocess_backward(const Table &tb, const gs_gaussians *g, const gs_camera *cams, const Ws &w,
+                                const GradOut &o, int n_chunks, bool overwrite, cudaStream_t s);
 
 void launch_deform(const gs_avatars *av, const float *G, float *out_means, float *out_cov, cudaStream_t s);
 void launch_deform_backward(const gs_avatars *av, const float *G, const float *d_means, const float *d_cov,

@@ -5,6 +5,7 @@ import pytest
 
 import oracle as _oracle
 import test_oracle_adjoint as adj
+import test_oracle_error_bounds as eb
 import test_oracle_mask_pins as mask
 import test_oracle_pins as pins
 import test_oracle_pins_capsule as capsule
@@ -88,14 +89,27 @@ MUTANTS = [
     ("interpolation weights swapped", "o[e] = (1.0 - w) * A0[e] + w * A1[e];", "o[e] = w * A0[e] + (1.0 - w) * A1[e];",
      drive.test_interpolation_between_frames),
     ("mask: clamp decision not flagged",
-     "if (fabs(power + log(g->o) - log(ALPHA_MAX)) <= dpow + 2e-6) s->amb |= AMB_CLAMP;", "",
+     "if (fabs(power + log(g->o) - log(ALPHA_MAX)) <= dpow + E_ALPHA) s->amb |= AMB_CLAMP;", "",
      mask.test_clamp_threshold_is_flagged),
-    ("mask: alpha decision bound dropped", "if (fabs(power + log(g->o) - log(ALPHA_MIN)) <= dpow + 2e-6) {",
+    ("mask: alpha decision bound dropped", "if (fabs(power + log(g->o) - log(ALPHA_MIN)) <= dpow + E_ALPHA) {",
      "if (fabs(power + log(g->o) - log(ALPHA_MIN)) <= 0.0) {", mask.test_alpha_threshold_is_flagged),
     ("mask: footprint flagged only outside r", "if (m >= g->r_lo - eps && m <= g->r_hi + eps) {",
      "if (m > g->r_hi && m <= g->r_hi + eps) {", mask.test_footprint_threshold_is_flagged),
-    ("mask: stop decision bound dropped", "if (fabs(Tn - T_STOP) <= T_STOP * relTn + 1e-12) {",
+    ("mask: stop decision bound dropped", "if (fabs(Tn - T_STOP) <= T_STOP * (relTn + U32) + 1e-15) {",
      "if (fabs(Tn - T_STOP) <= 0.0) {", mask.test_stop_threshold_is_flagged),
+    ("bound: radius ignores the discriminant's cancellation",
+     "elam = eig_in + xr / (2.0 * sqrt(xm)) + U32 * sqrt(xm) + U32 * mid + U32 * (mid + sqrt(xm));",
+     "elam = eig_in + U32 * sqrt(xm) + U32 * mid + U32 * (mid + sqrt(xm));",
+     eb.test_fp32_projection_within_the_oracle_bounds),
+    ("bound: radius ignores the covariance's error",
+     "elam = eig_in + xr / (2.0 * sqrt(xm)) + U32 * sqrt(xm) + U32 * mid + U32 * (mid + sqrt(xm));",
+     "elam = xr / (2.0 * sqrt(xm)) + U32 * sqrt(xm) + U32 * mid + U32 * (mid + sqrt(xm));",
+     eb.test_fp32_projection_within_the_oracle_bounds),
+    ("bound: 3D covariance taken as exact",
+     "e += eS[3 * i + j] * fabs(T[3 * r + j]) + fabs(S[3 * i + j]) * et[3 * r + j];",
+     "e += fabs(S[3 * i + j]) * et[3 * r + j];", eb.test_fp32_projection_within_the_oracle_bounds),
+    ("bound: off-diagonal covariance error dropped", "const double E[4] = {e2[0], e2[1], e2[1], e2[2]};",
+     "const double E[4] = {e2[0], 0.0, 0.0, e2[2]};", eb.test_fp32_projection_within_the_oracle_bounds),
     ("adjoint: LBS covariance factor", "gA[4 * r + cc] = gm[r] * mu[cc] + 2.0 * acc;",
      "gA[4 * r + cc] = gm[r] * mu[cc] + acc;", adj.test_lbs_adjoint_matches_finite_differences),
 ]

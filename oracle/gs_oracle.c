@@ -346,115 +346,138 @@ static void fp32_bounds(proj_t *o, const double *ls, const double *q, int use_co
         et[3 + c] = fabs(k->R[3 + c]) * ej11 + fabs(k->R[6 + c]) * ej12 +
                     gam(2) * (j11 * fabs(k->R[3 + c]) + j12 * fabs(k->R[6 + c]));
     }
-    /* 3D covariance */
-    double eS[9];
-    const double *S = o->Sigma;
+    const double *T = o->T, *S = o->Sigma;
+    const double a = o->cov2[0], b = o->cov2[1], c = o->cov2[2], det = o->det;
+    double e2[3]; /* a, b, c */
+    double edet;
+    o->ea = o->eb = o->ec = o->rel_conic = 0.0;
     if (!use_cov) {
-        /* normalised rotation: 1/sqrt(|q|^2) within 4U, components within 5U,
-         * each entry of R(q) within 25U absolute; scales exp(s) within 2 ulp (4U);
-         * M = R diag(scale) (one rounding): |dM_ik| <= scale_k (25U + 5U |R_ik|);
-         * Sigma_ij = sum_k M_ik M_jk (three roundings) */
+        /* scale-rotation Gaussian, the factor form: M = R(q) diag(exp s) with
+         * 1/|q| within 4U, the entries of R(q) within 25U absolute, exp(s)
+         * within 4U: |dM_kj| <= scale_j (25U + 5U |R_kj|); G = T M (three
+         * roundings); a' = |G_0|^2, b = G_0 . G_1, c' = |G_1|^2 (three each);
+         * a = a' + 0.3 (one, 0.3f - 0.3 = 1.2e-8); det = (sum of the three
+         * squared 2 x 2 minors of G, each minor two roundings, the sum three)
+         * + 0.3 (a' + c') + 0.09 (three more; 0.09f - 0.09 = 3.6e-9) */
         double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
         double qn[4] = {q[0] / n, q[1] / n, q[2] / n, q[3] / n};
         double R[9];
         quat_rot(qn, R);
-        double sc[3] = {exp(ls[0]), exp(ls[1]), exp(ls[2])};
-        for (int i = 0; i < 3; ++i)
+        double M[9], eM[9];
+        for (int kk = 0; kk < 3; ++kk)
             for (int j = 0; j < 3; ++j) {
-                double acc = 0.0;
-                for (int kk = 0; kk < 3; ++kk) {
-                    const double ri = fabs(R[3 * i + kk]), rj = fabs(R[3 * j + kk]);
-                    acc += sc[kk] * sc[kk] * ((25.0 * U32 + 5.0 * U32 * rj) * ri + (25.0 * U32 + 5.0 * U32 * ri) * rj +
-                                              gam(3) * ri * rj);
-                }
-                eS[3 * i + j] = acc;
+                const double sj = exp(ls[j]);
+                M[3 * kk + j] = R[3 * kk + j] * sj;
+                eM[3 * kk + j] = sj * (25.0 * U32 + 5.0 * U32 * fabs(R[3 * kk + j]));
             }
+        double G[2][3], eG[2][3];
+        for (int r = 0; r < 2; ++r)
+            for (int j = 0; j < 3; ++j) {
+                double v = 0.0, m = 0.0, e = 0.0;
+                for (int kk = 0; kk < 3; ++kk) {
+                    v += T[3 * r + kk] * M[3 * kk + j];
+                    m += fabs(T[3 * r + kk] * M[3 * kk + j]);
+                    e += et[3 * r + kk] * fabs(M[3 * kk + j]) + fabs(T[3 * r + kk]) * eM[3 * kk + j];
+                }
+                G[r][j] = v;
+                eG[r][j] = gam(3) * m + e;
+            }
+        double ea1 = 0.0, ec1 = 0.0, eb = 0.0, sa = 0.0, sc1 = 0.0, sb = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            sa += G[0][j] * G[0][j];
+            sc1 += G[1][j] * G[1][j];
+            sb += fabs(G[0][j] * G[1][j]);
+            ea1 += 2.0 * fabs(G[0][j]) * eG[0][j];
+            ec1 += 2.0 * fabs(G[1][j]) * eG[1][j];
+            eb += fabs(G[0][j]) * eG[1][j] + eG[0][j] * fabs(G[1][j]);
+        }
+        ea1 += gam(3) * sa;
+        ec1 += gam(3) * sc1;
+        eb += gam(3) * sb;
+        e2[0] = ea1 + U32 * a + 1.2e-8;
+        e2[1] = eb;
+        e2[2] = ec1 + U32 * c + 1.2e-8;
+        const int mi[3] = {0, 0, 1}, mj[3] = {1, 2, 2};
+        double dg = 0.0, edg = 0.0;
+        for (int x = 0; x < 3; ++x) {
+            const int i = mi[x], j = mj[x];
+            const double m = G[0][i] * G[1][j] - G[0][j] * G[1][i];
+            const double em = gam(2) * (fabs(G[0][i] * G[1][j]) + fabs(G[0][j] * G[1][i])) + fabs(G[1][j]) * eG[0][i] +
+                              fabs(G[0][i]) * eG[1][j] + fabs(G[1][i]) * eG[0][j] + fabs(G[0][j]) * eG[1][i];
+            dg += m * m;
+            edg += 2.0 * fabs(m) * em;
+        }
+        edg += gam(3) * dg;
+        edet = edg + DILATION * (ea1 + ec1) + gam(3) * det + 1.2e-8 * (sa + sc1) + 3.6e-9;
+        /* conic = (c, -b, a) / det: a reciprocal and a product, errors direct */
+        const double rd = edet / det + 2.0 * U32;
+        o->eA = fabs(o->conic[0]) * (e2[2] / c + rd);
+        o->eB = fabs(o->conic[1]) * rd + e2[1] / det;
+        o->eC = fabs(o->conic[2]) * (e2[0] / a + rd);
     } else {
         /* a given covariance is exact; a posed one (A3 Sigma A3^T in FP32 from
-         * the FP32 Sigma above, A3 a blend of rotations): within 240U tr(Sigma) */
+         * the FP32 Sigma of its scales and rotation, A3 a blend of rotations)
+         * within 240U tr(Sigma).  Sigma2 = T Sigma T^T + 0.3 I: u = Sigma t
+         * (three roundings), a = t . u + 0.3 (four) */
+        double eS[9];
         const double tr = S[0] + S[4] + S[8];
         for (int i = 0; i < 9; ++i) eS[i] = inexact ? 240.0 * U32 * tr : 0.0;
-    }
-    /* Sigma2 = T Sigma T^T + 0.3 I: u = Sigma t (three roundings), a = t . u +
-     * 0.3 (four roundings, 0.3f differs from 0.3 by 1.2e-8) */
-    const double *T = o->T;
-    double uu[2][3], eu[2][3];
-    for (int r = 0; r < 2; ++r)
-        for (int i = 0; i < 3; ++i) {
-            double v = 0.0, m = 0.0, e = 0.0;
-            for (int j = 0; j < 3; ++j) {
-                v += S[3 * i + j] * T[3 * r + j];
-                m += fabs(S[3 * i + j] * T[3 * r + j]);
-                e += eS[3 * i + j] * fabs(T[3 * r + j]) + fabs(S[3 * i + j]) * et[3 * r + j];
+        double uu[2][3], eu[2][3];
+        for (int r = 0; r < 2; ++r)
+            for (int i = 0; i < 3; ++i) {
+                double v = 0.0, m = 0.0, e = 0.0;
+                for (int j = 0; j < 3; ++j) {
+                    v += S[3 * i + j] * T[3 * r + j];
+                    m += fabs(S[3 * i + j] * T[3 * r + j]);
+                    e += eS[3 * i + j] * fabs(T[3 * r + j]) + fabs(S[3 * i + j]) * et[3 * r + j];
+                }
+                uu[r][i] = v;
+                eu[r][i] = gam(3) * m + e;
             }
-            uu[r][i] = v;
-            eu[r][i] = gam(3) * m + e;
+        for (int x = 0; x < 3; ++x) {
+            const int r = x == 2 ? 1 : 0, w = x == 0 ? 0 : 1; /* a = t0 . u0, b = t0 . u1, c = t1 . u1 */
+            double m = 0.0, e = 0.0;
+            for (int i = 0; i < 3; ++i) {
+                m += fabs(T[3 * r + i] * uu[w][i]);
+                e += fabs(T[3 * r + i]) * eu[w][i] + et[3 * r + i] * fabs(uu[w][i]);
+            }
+            e2[x] = x == 1 ? gam(3) * m + e : gam(4) * (m + DILATION) + e + 1.2e-8;
         }
-    double e2[3]; /* a, b, c */
-    for (int x = 0; x < 3; ++x) {
-        const int r = x == 2 ? 1 : 0, w = x == 0 ? 0 : 1; /* a = t0 . u0, b = t0 . u1, c = t1 . u1 */
-        double m = 0.0, e = 0.0;
-        for (int i = 0; i < 3; ++i) {
-            m += fabs(T[3 * r + i] * uu[w][i]);
-            e += fabs(T[3 * r + i]) * eu[w][i] + et[3 * r + i] * fabs(uu[w][i]);
-        }
-        e2[x] = x == 1 ? gam(3) * m + e : gam(4) * (m + DILATION) + e + 1.2e-8;
+        edet = fabs(c) * e2[0] + fabs(a) * e2[2] + 2.0 * fabs(b) * e2[1] + gam(2) * (fabs(a * c) + b * b);
+        /* det = a c - b b from the rounded a, b, c: an error dSigma2 moves Q =
+         * Sigma2^-1 by -Q dSigma2 Q (first order) and the power by (Qd)^T
+         * dSigma2 (Qd) / 2; the conic's own roundings (det under either FMA
+         * contraction within U (ac + b^2) + U det, the reciprocal, the
+         * product) add rel_conic relative */
+        o->ea = e2[0]; o->eb = e2[1]; o->ec = e2[2];
+        o->rel_conic = det > 0.0 ? U32 * (fabs(a * c) + b * b) / det + 3.0 * U32 : 0.0;
+        const double Q[4] = {o->conic[0], o->conic[1], o->conic[1], o->conic[2]};
+        const double E[4] = {e2[0], e2[1], e2[1], e2[2]};
+        double eq[3] = {0.0, 0.0, 0.0}; /* |Q| |dSigma2| |Q| at (0,0), (0,1), (1,1) */
+        const int ri[3] = {0, 0, 1}, ci[3] = {0, 1, 1};
+        for (int x = 0; x < 3; ++x)
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j) eq[x] += fabs(Q[2 * ri[x] + i]) * E[2 * i + j] * fabs(Q[2 * j + ci[x]]);
+        o->eA = eq[0] + fabs(o->conic[0]) * o->rel_conic;
+        o->eB = eq[1] + fabs(o->conic[1]) * o->rel_conic;
+        o->eC = eq[2] + fabs(o->conic[2]) * o->rel_conic;
+        (void)edet;
     }
-    const double a = o->cov2[0], b = o->cov2[1], c = o->cov2[2], det = o->det;
-    o->ea = e2[0]; o->eb = e2[1]; o->ec = e2[2];
-    /* An error dSigma2 of the FP32 2D covariance moves the conic Q = Sigma2^-1
-     * by -Q dSigma2 Q (first order), the power -d^T Q d / 2 by (Qd)^T dSigma2
-     * (Qd) / 2 and the largest eigenvalue by v^T dSigma2 v (v its unit
-     * eigenvector).  On top come the roundings of the conic itself: det = a c -
-     * b b (two roundings, under either contraction within U (ac + b^2) + U det),
-     * the reciprocal and the product: relative rel_conic. */
-    o->rel_conic = det > 0.0 ? U32 * (fabs(a * c) + b * b) / det + 3.0 * U32 : 0.0;
-    const double Q[4] = {o->conic[0], o->conic[1], o->conic[1], o->conic[2]};
-    const double E[4] = {e2[0], e2[1], e2[1], e2[2]};
-    double eq[3] = {0.0, 0.0, 0.0}; /* |Q| |dSigma2| |Q| at (0,0), (0,1), (1,1) */
-    const int ri[3] = {0, 0, 1}, ci[3] = {0, 1, 1};
-    for (int x = 0; x < 3; ++x)
-        for (int i = 0; i < 2; ++i)
-            for (int j = 0; j < 2; ++j) eq[x] += fabs(Q[2 * ri[x] + i]) * E[2 * i + j] * fabs(Q[2 * j + ci[x]]);
-    o->eA = eq[0] + fabs(o->conic[0]) * o->rel_conic;
-    o->eB = eq[1] + fabs(o->conic[1]) * o->rel_conic;
-    o->eC = eq[2] + fabs(o->conic[2]) * o->rel_conic;
-    /* radius: lambda = mid + sqrt(max(0.1, x)), mid = (a + c) / 2, x = mid^2 - det.
-     * Input errors: v^T dSigma2 v where the floor is not active, the error of
-     * mid where it is (both near the floor).  Roundings: mid (U mid), x (mid^2
-     * from the rounded mid, the det's own rounding, the fma: 2U mid^2 + U (ac +
-     * b^2 + det) + U |x|), the square root (U), the sum (U), then 3 sqrt(.) */
-    const double mid = 0.5 * (a + c);
-    const double x = mid * mid - det;
-    const double disc = x > 0.0 ? x : 0.0;
-    const double lmax = mid + sqrt(disc);
-    /* unit eigenvector of the largest eigenvalue of [[a, b], [b, c]] */
-    double vx = b, vy = lmax - a;
-    if (fabs(vx) + fabs(vy) < 1e-300 * (fabs(a) + fabs(c))) { vx = a >= c ? 1.0 : 0.0; vy = a >= c ? 0.0 : 1.0; }
-    if (fabs(b) < 1e-12 * (fabs(a) + fabs(c))) { vx = a >= c ? 1.0 : 0.0; vy = a >= c ? 0.0 : 1.0; }
-    const double vn = sqrt(vx * vx + vy * vy);
-    vx /= vn; vy /= vn;
-    const double eig_in = e2[0] * vx * vx + 2.0 * e2[1] * fabs(vx * vy) + e2[2] * vy * vy;
-    const double emid_in = 0.5 * (e2[0] + e2[2]);
-    const double xr = 2.0 * U32 * mid * mid + U32 * (fabs(a * c) + b * b + fabs(det)) + U32 * fabs(x);
-    /* input error of x = mid^2 - det: (lambda_1 - lambda_2)^2 / 4 moves by at most
-     * (lambda_1 - lambda_2)/2 times the eigenvalues' moves, each below |dSigma2|_2 */
-    const double nrm = e2[0] + e2[2] + 2.0 * e2[1];
-    const double xin = sqrt(disc) * nrm;
-    const double ex = xr + xin;
-    const double xm = x > 0.1 ? x : 0.1;
-    double elam;
-    if (x - ex > 0.1) {
-        /* floor inactive: input error through the eigenvalue, rounding through x */
-        elam = eig_in + xr / (2.0 * sqrt(xm)) + U32 * sqrt(xm) + U32 * mid + U32 * (mid + sqrt(xm));
-    } else if (x + ex < 0.1) {
-        /* floor active: lambda = mid + sqrt(0.1f) */
-        elam = emid_in + U32 * mid + U32 * sqrt(0.1) + U32 * (mid + sqrt(0.1)) + 1.5e-9;
-    } else {
-        elam = (eig_in > emid_in ? eig_in : emid_in) + ex / (2.0 * sqrt(0.1)) + U32 * mid +
-               U32 * (mid + sqrt(xm)) + U32 * sqrt(xm) + 1.5e-9;
-    }
+    /* radius: lambda = mid + sqrt(max(0.1, hd^2 + b^2)), mid = (a + c) / 2,
+     * hd = (a - c) / 2 (one rounding each), the discriminant two roundings;
+     * |hd|, |b| <= sqrt(disc), so the input errors pass without amplification */
+    const double mid = 0.5 * (a + c), hd = 0.5 * (a - c);
+    const double emid = 0.5 * (e2[0] + e2[2]) + U32 * mid;
+    const double ehd = 0.5 * (e2[0] + e2[2]) + U32 * fabs(hd);
+    const double disc = hd * hd + b * b;
+    const double edisc = 2.0 * fabs(hd) * ehd + 2.0 * fabs(b) * e2[1] + U32 * hd * hd + U32 * disc;
+    const double xm = disc > 0.1 ? disc : 0.1;
+    double esq;
+    if (disc - edisc > 0.1) esq = edisc / (2.0 * sqrt(xm)) + U32 * sqrt(xm);
+    else if (disc + edisc < 0.1) esq = U32 * sqrt(0.1) + 2.4e-9; /* sqrt(0.1f), 0.1f - 0.1 = 1.5e-9 */
+    else esq = edisc / (2.0 * sqrt(0.1)) + U32 * sqrt(xm) + 2.4e-9;
     const double lam = mid + sqrt(xm);
+    const double elam = emid + esq + U32 * lam;
     o->er3 = 1.5 * elam / sqrt(lam) + gam(2) * o->r3;
 }
 
@@ -597,7 +620,11 @@ int64_t or_project(int64_t n, const double *means, const double *log_scales, con
 /* order, so their results agree bit for bit.                                 */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-    double u, v, z, A, B, C, o, rgb[3], du, dv, ea, eb, ec, rel_conic, ez;
+    double u, v, z, A, B, C, o, rgb[3], du, dv, ez;
+    /* FP32 error model of the conic: direct bounds eA, eB, eC (factor-form
+     * Gaussians), or the 2D covariance's errors ea, eb, ec with the conic's own
+     * relative rounding rel_conic (Gaussians given by a covariance) */
+    double eA, eB, eC, ea, eb, ec, rel_conic;
     int32_t r, r_lo, r_hi;
     float zkey;
     uint8_t inexact;
@@ -639,12 +666,14 @@ static void blend_step(pix_t *s, const cand_t *g, int i, int j, int32_t pos)
     if (m > g->r_hi + eps) return;
     double q = g->A * dx * dx + g->C * dy * dy;
     double power = -0.5 * q - g->B * dx * dy;
-    /* power in FP32: three roundings on each term and the conic's own
-     * (rel_conic); the offsets' errors through dpower/dd = -Q d = -w, the 2D
-     * covariance's through (w^T dSigma2 w) / 2; 1e-9 for second-order terms */
+    /* power in FP32: three roundings on each term; the offsets' errors
+     * through dpower/dd = -Q d = -w; the conic's errors directly (factor form)
+     * or as the 2D covariance's through (w^T dSigma2 w) / 2 plus the conic's
+     * own rounding; 1e-9 for second-order terms */
     const double wx = g->A * dx + g->B * dy, wy = g->B * dx + g->C * dy;
     double dpow = fabs(wx) * edx + fabs(wy) * edy + (gam(3) + g->rel_conic) * (0.5 * q + fabs(g->B * dx * dy)) +
-                  0.5 * (g->ea * wx * wx + 2.0 * g->eb * fabs(wx * wy) + g->ec * wy * wy) + 1e-9;
+                  0.5 * (g->ea * wx * wx + 2.0 * g->eb * fabs(wx * wy) + g->ec * wy * wy) +
+                  0.5 * (g->eA * dx * dx + g->eC * dy * dy) + g->eB * fabs(dx * dy) + 1e-9;
     if (m >= g->r_lo - eps && m <= g->r_hi + eps) {
         /* coverage can flip under FP32 rounding of u, v or of the radius */
         s->amb |= AMB_COUNT | AMB_FOOTPRINT;
@@ -744,7 +773,10 @@ static int64_t build_candidates(int64_t n, const double *means, const double *ls
         t->o = o.opacity;
         for (int i = 0; i < 3; ++i) t->rgb[i] = o.rgb[i];
         t->du = o.du; t->dv = o.dv;
-        t->ea = o.ea; t->eb = o.eb; t->ec = o.ec; t->rel_conic = o.rel_conic; t->ez = o.ez;
+        t->ez = o.ez;
+        const int factor = o.rel_conic == 0.0; /* the factor form sets no covariance-error terms */
+        t->eA = factor ? o.eA : 0.0; t->eB = factor ? o.eB : 0.0; t->eC = factor ? o.eC : 0.0;
+        t->ea = o.ea; t->eb = o.eb; t->ec = o.ec; t->rel_conic = o.rel_conic;
         t->r = o.r; t->r_lo = o.r_lo; t->r_hi = o.r_hi;
         t->zkey = o.zkey;
         t->inexact = (uint8_t)inx;

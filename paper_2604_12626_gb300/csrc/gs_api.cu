@@ -335,12 +335,15 @@ gs_status enqueue_forward(const gs_gaussians *g, const gs_batch *b, const gs_cam
         if (e != cudaSuccess) return cuda_fail(e);
     }
     // (view, tile) counters a preprocess / scatter chunk keeps in shared memory
-    int max_nv = 0;
-    for (int e = 0; e < t.n_envs; ++e) max_nv = std::max(max_nv, t.env_view_begin[e + 1] - t.env_view_begin[e]);
-    const int hist_words = (int)std::min<int64_t>(kHistCap, (int64_t)max_nv * t.tiles_per_view);
+    // (only envs whose views x tiles fit kHistCap keep counters there)
+    int64_t hist_words = 0;
+    for (int e = 0; e < t.n_envs; ++e) {
+        const int64_t h = (int64_t)(t.env_view_begin[e + 1] - t.env_view_begin[e]) * t.tiles_per_view;
+        if (h <= kHistCap) hist_words = std::max(hist_words, h);
+    }
     {
         Stage st1(1, s);
-        launch_preprocess(t, g, cams, w, t.n_chunks, hist_words, s, av, joint_G);
+        launch_preprocess(t, g, cams, w, t.n_chunks, (int)hist_words, s, av, joint_G);
     }
     {
         Stage st2(2, s);
@@ -348,7 +351,7 @@ gs_status enqueue_forward(const gs_gaussians *g, const gs_batch *b, const gs_cam
     }
     {
         Stage st3(3, s);
-        launch_scatter(cams, w, t.n_chunks, hist_words, t.chunk, s);
+        launch_scatter(cams, w, t.n_chunks, (int)hist_words, t.chunk, s);
     }
     {
         Stage st4(4, s);

@@ -220,15 +220,15 @@ constexpr int kMaxViewsPerChunk = 16; // cameras of a chunk's env staged in shar
 // A round's inputs in shared memory: 32 rotations (float4), then 32 each of
 // mean x, y, z, logit and log-scale x, y, z (floats): 1408 bytes per warp.
 constexpr int kRingF4 = 32 + 7 * 32 / 4;
-// rounds in the ring: three (two rounds of loads in flight) on the plain
-// path; two on the fused path, whose joint matrices take the shared memory
-template <bool FUSED> struct PreRing { static constexpr int n = FUSED ? 2 : 3; };
+// rounds in the ring (a launch parameter): three, two rounds of loads in
+// flight, where two CTAs per SM still fit; else two
 
 // FUSED: the batch's avatar rows are posed by LBS here (gs_render_avatars); a
 // separate instantiation so that the plain path carries none of its registers
 template <int SHT, bool FUSED>
 __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_camera *__restrict__ cams, GaussIn gin,
-                                                                    Ws w, const __grid_constant__ Table tbp)
+                                                                    Ws w, const __grid_constant__ Table tbp,
+                                                                    int n_ring)
 {
     extern __shared__ __align__(16) unsigned char smem_pre[];
     __shared__ gs_camera s_cam[kMaxViewsPerChunk];
@@ -237,11 +237,10 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
     __shared__ __align__(16) float s_G[FUSED ? kFusedJointSlots * 12 : 4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int kNW = kPreThreads / 32;
-    constexpr int kRing = PreRing<FUSED>::n;
     AEntry *qa = reinterpret_cast<AEntry *>(smem_pre) + warp * kWarpQ;
     QEntry *qb = reinterpret_cast<QEntry *>(smem_pre + kNW * kWarpQ * sizeof(AEntry)) + warp * kWarpQ;
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem_pre + kNW * kWarpQ * (sizeof(AEntry) + sizeof(QEntry)) +
-                                                  kNW * kRing * kRingF4 * sizeof(float4));
+                                                  kNW * n_ring * kRingF4 * sizeof(float4));
     // the table as a kernel parameter: its fields are constant-bank operands,
     // never reloaded after the global stores of the stages
     const Table *tb = &tbp;
@@ -298,19 +297,27 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
             const int k = ea.k;
             const int v = cam_smem ? 0 : tb->env_views[c.vb + k];
             const gs_camera &cam = cam_smem ? s_cam[k] : cams[v];
-            float S[6];
-            if (ea.kind == 0) {
-                sigma_from_sq(make_float3(ea.c[0], ea.c[1], ea.c[2]), make_float4(ea.c[3], ea.c[4], ea.c[5], ea.c[6]),
-                              S);
-            } else if (ea.kind == 1) {
-#pragma unroll
-                for (int i = 0; i < 6; ++i) S[i] = ea.c[i];
-            } else {
-#pragma unroll
-                for (int i = 0; i < 6; ++i) S[i] = __ldg(gin.cov3d + 6 * (int64_t)ea.g + i);
-            }
             Proj pj;
-            if (project_ewa(ea.mx, ea.my, ea.mz, ea.zk, S, cam, W, H, pj)) {
+            bool proj_ok;
+            if (ea.kind == 0) {
+                // scales and rotation: the factor form (a thin Gaussian's conic
+                // without cancellation)
+                float M[9];
+                factor_from_sq(make_float3(ea.c[0], ea.c[1], ea.c[2]), make_float4(ea.c[3], ea.c[4], ea.c[5], ea.c[6]),
+                               M);
+                proj_ok = project_ewa_factor(ea.mx, ea.my, ea.mz, ea.zk, M, cam, W, H, pj);
+            } else {
+                float S[6];
+                if (ea.kind == 1) {
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) S[i] = ea.c[i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) S[i] = __ldg(gin.cov3d + 6 * (int64_t)ea.g + i);
+                }
+                proj_ok = project_ewa(ea.mx, ea.my, ea.mz, ea.zk, S, cam, W, H, pj);
+            }
+            if (proj_ok) {
                 const float r = radius_px(pj);
                 const float idet = 1.0f / pj.det;
                 const float cA = pj.c * idet, cB = -pj.b * idet, cC = pj.a * idet;
@@ -345,12 +352,12 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
         if (tb_ - hb >= 32) stage_c(32);
     };
 
-    // the round ring: round r's inputs land in buffer r % kRing, issued
-    // kRing - 1 rounds ahead by cp.async, one commit group per round and lane
+    // the round ring: round r's inputs land in buffer r % n_ring, issued
+    // n_ring - 1 rounds ahead by cp.async, one commit group per round and lane
     float4 *ring = reinterpret_cast<float4 *>(smem_pre + kNW * kWarpQ * (sizeof(AEntry) + sizeof(QEntry))) +
-                   warp * kRing * kRingF4;
-    auto issue_round = [&](int64_t gg, int r) {
-        float4 *q4 = ring + (r % kRing) * kRingF4;
+                   warp * n_ring * kRingF4;
+    auto issue_round = [&](int64_t gg, int slot) {
+        float4 *q4 = ring + slot * kRingF4;
         float *f = reinterpret_cast<float *>(q4 + 32);
         if (gg < c.g1) {
             cp_async4(f + lane, gin.means + 3 * gg);
@@ -368,17 +375,17 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
     };
     int64_t g = c.g0 + warp * 32 + lane;
     const int64_t gstep = 32 * nwarps;
-#pragma unroll
-    for (int r = 0; r < kRing - 1; ++r) issue_round(g + r * gstep, r);
-    int round = 0;
-    for (int64_t base = c.g0 + warp * 32; base < c.g1; base += gstep, g += gstep, ++round) {
+    for (int r = 0; r < n_ring - 1; ++r) issue_round(g + r * gstep, r);
+    int slot = 0, slot_next = n_ring - 1; // buffers of this round and of the round issued next
+    for (int64_t base = c.g0 + warp * 32; base < c.g1; base += gstep, g += gstep) {
         const bool valid = g < c.g1;
-        cp_async_wait<kRing - 2>(); // this round's group has landed
+        if (n_ring == 3) cp_async_wait<1>(); // this round's group has landed
+        else cp_async_wait<0>();
         float mx = 0.f, my = 0.f, mz = 0.f, lo = 0.f;
         float3 cls = make_float3(0.f, 0.f, 0.f);
         float4 cq = make_float4(1.f, 0.f, 0.f, 0.f);
         {
-            const float4 *q4 = ring + (round % kRing) * kRingF4;
+            const float4 *q4 = ring + slot * kRingF4;
             const float *f = reinterpret_cast<const float *>(q4 + 32);
             if (valid) {
                 mx = f[lane];
@@ -392,7 +399,9 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
             }
         }
         // the buffer of the previous round is free again (its values were used there)
-        issue_round(g + (kRing - 1) * gstep, round + kRing - 1);
+        issue_round(g + (n_ring - 1) * gstep, slot_next);
+        slot = slot + 1 == n_ring ? 0 : slot + 1;
+        slot_next = slot_next + 1 == n_ring ? 0 : slot_next + 1;
         const int nv = valid ? c.nv : 0;
         // covariance source of this lane's Gaussian and the largest variance
         // of its 3D covariance for the image test
@@ -1483,14 +1492,25 @@ void launch_setup(const Table &tb, const Ws &w, cudaStream_t s) { setup_kernel<<
 
 // dynamic shared memory of the preprocess: the two queues of every warp, its
 // round ring and the chunk's (view, tile) counters
-static int pre_smem(bool fused, int hist_words)
+static int pre_smem(int n_ring, int hist_words)
 {
-    const int ring = fused ? PreRing<true>::n : PreRing<false>::n;
-    return (kPreThreads / 32) * (kWarpQ * (int)(sizeof(AEntry) + sizeof(QEntry)) + ring * kRingF4 * 16) +
+    return (kPreThreads / 32) * (kWarpQ * (int)(sizeof(AEntry) + sizeof(QEntry)) + n_ring * kRingF4 * 16) +
            hist_words * 4;
 }
 constexpr int kPreSmemMax = (kPreThreads / 32) * (kWarpQ * (int)(sizeof(AEntry) + sizeof(QEntry)) + 3 * kRingF4 * 16) +
                             kHistCap * 4;
+
+template <int SHT, bool FUSED>
+static void launch_pre_t(unsigned grid, int hist_words, cudaStream_t s, const gs_camera *cams, const GaussIn &gin,
+                         const Ws &w, const Table &tb)
+{
+    int n_ring = 3, nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, preprocess_kernel<SHT, FUSED>, kPreThreads,
+                                                      pre_smem(3, hist_words)) != cudaSuccess ||
+        nb < 2)
+        n_ring = 2;
+    preprocess_kernel<SHT, FUSED><<<grid, kPreThreads, pre_smem(n_ring, hist_words), s>>>(cams, gin, w, tb, n_ring);
+}
 
 void launch_preprocess(const Table &tb, const gs_gaussians *g, const gs_camera *cams, const Ws &w, int n_chunks,
                        int hist_words, cudaStream_t s, const gs_avatars *av, const float *joint_G)
@@ -1505,14 +1525,14 @@ void launch_preprocess(const Table &tb, const gs_gaussians *g, const gs_camera *
     const unsigned grid = (unsigned)n_chunks;
     if (grid == 0) return;
     const bool fused = gin.av_G != nullptr;
-    const int sm = pre_smem(fused, std::min(std::max(hist_words, 0), kHistCap));
+    const int hw = std::min(std::max(hist_words, 0), kHistCap);
     switch (g->sh_dtype * 2 + (fused ? 1 : 0)) {
-    case GS_SH_F16 * 2: preprocess_kernel<GS_SH_F16, false><<<grid, kPreThreads, sm, s>>>(cams, gin, w, tb); break;
-    case GS_SH_F16 * 2 + 1: preprocess_kernel<GS_SH_F16, true><<<grid, kPreThreads, sm, s>>>(cams, gin, w, tb); break;
-    case GS_SH_BF16 * 2: preprocess_kernel<GS_SH_BF16, false><<<grid, kPreThreads, sm, s>>>(cams, gin, w, tb); break;
-    case GS_SH_BF16 * 2 + 1: preprocess_kernel<GS_SH_BF16, true><<<grid, kPreThreads, sm, s>>>(cams, gin, w, tb); break;
-    case GS_SH_F32 * 2 + 1: preprocess_kernel<GS_SH_F32, true><<<grid, kPreThreads, sm, s>>>(cams, gin, w, tb); break;
-    default: preprocess_kernel<GS_SH_F32, false><<<grid, kPreThreads, sm, s>>>(cams, gin, w, tb); break;
+    case GS_SH_F16 * 2: launch_pre_t<GS_SH_F16, false>(grid, hw, s, cams, gin, w, tb); break;
+    case GS_SH_F16 * 2 + 1: launch_pre_t<GS_SH_F16, true>(grid, hw, s, cams, gin, w, tb); break;
+    case GS_SH_BF16 * 2: launch_pre_t<GS_SH_BF16, false>(grid, hw, s, cams, gin, w, tb); break;
+    case GS_SH_BF16 * 2 + 1: launch_pre_t<GS_SH_BF16, true>(grid, hw, s, cams, gin, w, tb); break;
+    case GS_SH_F32 * 2 + 1: launch_pre_t<GS_SH_F32, true>(grid, hw, s, cams, gin, w, tb); break;
+    default: launch_pre_t<GS_SH_F32, false>(grid, hw, s, cams, gin, w, tb); break;
     }
 }
 

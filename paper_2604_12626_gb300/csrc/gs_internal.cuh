@@ -293,20 +293,26 @@ __device__ __forceinline__ void quat_rot(float w, float x, float y, float z, flo
     R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
 }
 
-// Sigma = R(q) diag(exp(2 s)) R(q)^T as (xx, xy, xz, yy, yz, zz).
-__device__ __forceinline__ void sigma_from_sq(float3 ls, float4 q, float (&S)[6])
+// M = R(q) diag(exp(s)), the factor of Sigma = M M^T (row-major 3 x 3).
+__device__ __forceinline__ void factor_from_sq(float3 ls, float4 q, float (&M)[9])
 {
     const float inv = 1.0f / sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
     float R[9];
     quat_rot(q.x * inv, q.y * inv, q.z * inv, q.w * inv, R);
     const float s0 = expf(ls.x), s1 = expf(ls.y), s2 = expf(ls.z);
-    float M[9];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         M[3 * r] = R[3 * r] * s0;
         M[3 * r + 1] = R[3 * r + 1] * s1;
         M[3 * r + 2] = R[3 * r + 2] * s2;
     }
+}
+
+// Sigma = R(q) diag(exp(2 s)) R(q)^T as (xx, xy, xz, yy, yz, zz).
+__device__ __forceinline__ void sigma_from_sq(float3 ls, float4 q, float (&S)[6])
+{
+    float M[9];
+    factor_from_sq(ls, q, M);
     S[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
     S[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
     S[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
@@ -327,8 +333,10 @@ struct Proj {
 
 // EWA projection with the lateral clamp at 1.3 x the half field and the
 // 0.3 px^2 dilation.  Returns false when the conic is singular.
-__device__ __forceinline__ bool project_ewa(float mx, float my, float mz, float zk, const float (&S)[6],
-                                            const gs_camera &cam, int W, int H, Proj &p)
+// View, screen position and T = J W of the EWA projection (everything but
+// the 2D covariance).
+__device__ __forceinline__ void project_view(float mx, float my, float mz, float zk, const gs_camera &cam, int W, int H,
+                                             Proj &p)
 {
     p.d0 = __fsub_rn(mx, cam.C[0]);
     p.d1 = __fsub_rn(my, cam.C[1]);
@@ -352,6 +360,15 @@ __device__ __forceinline__ bool project_ewa(float mx, float my, float mz, float 
     t[3] = j11 * cam.R[3] + j12 * cam.R[6];
     t[4] = j11 * cam.R[4] + j12 * cam.R[7];
     t[5] = j11 * cam.R[5] + j12 * cam.R[8];
+}
+
+// EWA projection of a Gaussian given by its 3D covariance S (xx, xy, xz, yy,
+// yz, zz): Sigma2 = T S T^T + 0.3 I, det = a c - b^2.
+__device__ __forceinline__ bool project_ewa(float mx, float my, float mz, float zk, const float (&S)[6],
+                                            const gs_camera &cam, int W, int H, Proj &p)
+{
+    project_view(mx, my, mz, zk, cam, W, H, p);
+    const float *t = p.t;
     const float u0 = S[0] * t[0] + S[1] * t[1] + S[2] * t[2], u1 = S[1] * t[0] + S[3] * t[1] + S[4] * t[2],
                 u2 = S[2] * t[0] + S[4] * t[1] + S[5] * t[2];
     const float w0 = S[0] * t[3] + S[1] * t[4] + S[2] * t[5], w1 = S[1] * t[3] + S[3] * t[4] + S[4] * t[5],
@@ -363,11 +380,43 @@ __device__ __forceinline__ bool project_ewa(float mx, float my, float mz, float 
     return p.det > 0.0f;
 }
 
-// 3-sigma radius of the dilated 2D covariance, an integer number of pixels.
+// The same projection from the factor M (S = M M^T) of a scale-rotation
+// Gaussian: with G = T M (2 x 3), Sigma2 = G G^T + 0.3 I and det(Sigma2) =
+// det(G G^T) + 0.3 tr(G G^T) + 0.09, det(G G^T) the sum of the squared 2 x 2
+// minors of G (Cauchy-Binet).  Every term is non-negative, so a thin
+// Gaussian's nearly singular G G^T costs no cancellation: its conic keeps FP32
+// accuracy where a c - b^2 loses digits in proportion to a c / det.
+__device__ __forceinline__ bool project_ewa_factor(float mx, float my, float mz, float zk, const float (&M)[9],
+                                                   const gs_camera &cam, int W, int H, Proj &p)
+{
+    project_view(mx, my, mz, zk, cam, W, H, p);
+    const float *t = p.t;
+    float G0[3], G1[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        G0[j] = t[0] * M[j] + t[1] * M[3 + j] + t[2] * M[6 + j];
+        G1[j] = t[3] * M[j] + t[4] * M[3 + j] + t[5] * M[6 + j];
+    }
+    const float a1 = G0[0] * G0[0] + G0[1] * G0[1] + G0[2] * G0[2];
+    const float c1 = G1[0] * G1[0] + G1[1] * G1[1] + G1[2] * G1[2];
+    p.b = G0[0] * G1[0] + G0[1] * G1[1] + G0[2] * G1[2];
+    const float m01 = G0[0] * G1[1] - G0[1] * G1[0], m02 = G0[0] * G1[2] - G0[2] * G1[0],
+                m12 = G0[1] * G1[2] - G0[2] * G1[1];
+    const float dg = m01 * m01 + m02 * m02 + m12 * m12;
+    p.a = a1 + kDilation;
+    p.c = c1 + kDilation;
+    p.det = __fmaf_rn(kDilation, a1 + c1, dg) + kDilation * kDilation;
+    return p.det > 0.0f;
+}
+
+// 3-sigma radius of the dilated 2D covariance, an integer number of pixels:
+// lambda_max = mid + sqrt(((a - c) / 2)^2 + b^2), the discriminant (mid^2 -
+// det) as a sum of squares, floored at 0.1.
 __device__ __forceinline__ float radius_px(const Proj &p)
 {
     const float mid = 0.5f * (p.a + p.c);
-    const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - p.det));
+    const float hd = 0.5f * (p.a - p.c);
+    const float lam = mid + sqrtf(fmaxf(0.1f, hd * hd + p.b * p.b));
     return ceilf(3.0f * sqrtf(lam));
 }
 

@@ -13,7 +13,9 @@ f32 = np.float32
 
 
 def _fp32_projection(g, cam, W, H):
-    """(u - cx, v - cy, 3 sqrt(lambda), A, B, C) in float32, per Gaussian."""
+    """(u - cx, v - cy, 3 sqrt(lambda), A, B, C) in float32, per Gaussian: the
+    2D covariance of a scale-rotation Gaussian from its factor G = T R diag(e^s),
+    the determinant as 0.3 tr + 0.09 plus the squared minors of G."""
     cam = cam.astype(f32)
     R = cam[:9].reshape(3, 3)
     C = cam[9:12]
@@ -42,16 +44,21 @@ def _fp32_projection(g, cam, W, H):
     # exp correctly rounded to float32 (the bound assumes at most 2 ulp)
     sc = np.exp(g["log_scales"].astype(f32).astype(np.float64)).astype(f32)
     M = Rq * sc[:, None, :]
-    S = np.einsum("nik,njk->nij", M, M).astype(f32)  # 3-term sums in float32
-    def quad(ta, tb):
-        u = np.stack([S[:, i, 0] * tb[:, 0] + S[:, i, 1] * tb[:, 1] + S[:, i, 2] * tb[:, 2] for i in range(3)], 1)
-        return ta[:, 0] * u[:, 0] + ta[:, 1] * u[:, 1] + ta[:, 2] * u[:, 2]
-    a = quad(t0, t0) + f32(0.3)
-    b = quad(t0, t1)
-    c = quad(t1, t1) + f32(0.3)
-    det = a * c - b * b
+    # G = T M; Sigma2 = G G^T + 0.3 I; det by the squared 2 x 2 minors of G
+    G0 = sum(t0[:, k, None] * M[:, k, :] for k in range(3)).astype(f32)
+    G1 = sum(t1[:, k, None] * M[:, k, :] for k in range(3)).astype(f32)
+    a1 = G0[:, 0] * G0[:, 0] + G0[:, 1] * G0[:, 1] + G0[:, 2] * G0[:, 2]
+    c1 = G1[:, 0] * G1[:, 0] + G1[:, 1] * G1[:, 1] + G1[:, 2] * G1[:, 2]
+    b = G0[:, 0] * G1[:, 0] + G0[:, 1] * G1[:, 1] + G0[:, 2] * G1[:, 2]
+    m01 = G0[:, 0] * G1[:, 1] - G0[:, 1] * G1[:, 0]
+    m02 = G0[:, 0] * G1[:, 2] - G0[:, 2] * G1[:, 0]
+    m12 = G0[:, 1] * G1[:, 2] - G0[:, 2] * G1[:, 1]
+    dg = m01 * m01 + m02 * m02 + m12 * m12
+    a, c = a1 + f32(0.3), c1 + f32(0.3)
+    det = f32(0.3) * (a1 + c1) + dg + f32(0.3) * f32(0.3)
     mid = f32(0.5) * (a + c)
-    lam = mid + np.sqrt(np.maximum(f32(0.1), mid * mid - det))
+    hd = f32(0.5) * (a - c)
+    lam = mid + np.sqrt(np.maximum(f32(0.1), hd * hd + b * b))
     r3 = f32(3) * np.sqrt(lam)
     idet = f32(1) / det
     return uc, vc, r3, c * idet, -b * idet, a * idet

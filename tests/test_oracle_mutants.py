@@ -97,19 +97,15 @@ MUTANTS = [
      "if (m > g->r_hi && m <= g->r_hi + eps) {", mask.test_footprint_threshold_is_flagged),
     ("mask: stop decision bound dropped", "if (fabs(Tn - T_STOP) <= T_STOP * (relTn + U32) + 1e-15) {",
      "if (fabs(Tn - T_STOP) <= 0.0) {", mask.test_stop_threshold_is_flagged),
-    ("bound: radius ignores the discriminant's cancellation",
-     "elam = eig_in + xr / (2.0 * sqrt(xm)) + U32 * sqrt(xm) + U32 * mid + U32 * (mid + sqrt(xm));",
-     "elam = eig_in + U32 * sqrt(xm) + U32 * mid + U32 * (mid + sqrt(xm));",
-     eb.test_fp32_projection_within_the_oracle_bounds),
-    ("bound: radius ignores the covariance's error",
-     "elam = eig_in + xr / (2.0 * sqrt(xm)) + U32 * sqrt(xm) + U32 * mid + U32 * (mid + sqrt(xm));",
-     "elam = xr / (2.0 * sqrt(xm)) + U32 * sqrt(xm) + U32 * mid + U32 * (mid + sqrt(xm));",
-     eb.test_fp32_projection_within_the_oracle_bounds),
-    ("bound: 3D covariance taken as exact",
-     "e += eS[3 * i + j] * fabs(T[3 * r + j]) + fabs(S[3 * i + j]) * et[3 * r + j];",
-     "e += fabs(S[3 * i + j]) * et[3 * r + j];", eb.test_fp32_projection_within_the_oracle_bounds),
-    ("bound: off-diagonal covariance error dropped", "const double E[4] = {e2[0], e2[1], e2[1], e2[2]};",
-     "const double E[4] = {e2[0], 0.0, 0.0, e2[2]};", eb.test_fp32_projection_within_the_oracle_bounds),
+    ("bound: radius ignores the covariance's error", "const double emid = 0.5 * (e2[0] + e2[2]) + U32 * mid;",
+     "const double emid = U32 * mid;", eb.test_fp32_projection_within_the_oracle_bounds),
+    ("bound: 3D factor taken as exact",
+     "e += et[3 * r + kk] * fabs(M[3 * kk + j]) + fabs(T[3 * r + kk]) * eM[3 * kk + j];",
+     "e += et[3 * r + kk] * fabs(M[3 * kk + j]);", eb.test_fp32_projection_within_the_oracle_bounds),
+    ("bound: conic ignores the determinant's error", "const double rd = edet / det + 2.0 * U32;",
+     "const double rd = 2.0 * U32;", eb.test_fp32_projection_within_the_oracle_bounds),
+    ("bound: conic B ignores b's error", "o->eB = fabs(o->conic[1]) * rd + e2[1] / det;",
+     "o->eB = fabs(o->conic[1]) * rd;", eb.test_fp32_projection_within_the_oracle_bounds),
     ("adjoint: LBS covariance factor", "gA[4 * r + cc] = gm[r] * mu[cc] + 2.0 * acc;",
      "gA[4 * r + cc] = gm[r] * mu[cc] + acc;", adj.test_lbs_adjoint_matches_finite_differences),
 ]

@@ -630,7 +630,8 @@ def training_row(api, synth, torch, dev, stream):
     target rendered from perturbed parameters, gradients of every parameter and
     of the joint transforms (api.AvatarScene: deform, render, loss gradient,
     backward in overwrite mode, deform backward) in one CUDA graph; FP32 and
-    FP16 SH storage."""
+    FP16 SH storage, and with FP16 SH the fused path (the avatars posed inside
+    gs_render_avatars and gs_render_avatars_backward)."""
     wl = synth.training_scene(seed=0)
     T = lambda x, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(x)).to(dev, dt)  # noqa: E731
     room, av = wl["room"], wl["avatars"]
@@ -641,7 +642,8 @@ def training_row(api, synth, torch, dev, stream):
     out = {"workload": f"1 room x {room['means'].shape[0]} + {wl['G'].shape[0]} avatars x 50k Gaussians, "
                        f"{n_views} views {Wc}x{Hc}, L1 loss vs perturbed target, fwd+bwd incl. joint gradients",
            "tile": [16, 16], "batch_depth": 128, "pixels_per_thread": [2, 1]}
-    for shd, name in ((torch.float32, "f32_sh"), (torch.float16, "f16_sh")):
+    for shd, name, fused in ((torch.float32, "f32_sh", False), (torch.float16, "f16_sh", False),
+                             (torch.float16, "f16_sh_fused", True)):
         def scene(perturbed):
             rm, rsh, am, ash = room["means"], room["sh"], av["means"], av["sh"]
             if perturbed:
@@ -654,7 +656,7 @@ def training_row(api, synth, torch, dev, stream):
                        joint_ids=T(av["joint_ids"].view(np.int16), torch.int16), weights=T(av["weights"]),
                        avatar_of=T(av["avatar_of"], torch.int32))
             return api.AvatarScene(sc, avs, wl["G"].shape[0], synth.N_JOINTS, Wc, Hc, n_views, sh_dtype=shd,
-                                   device=dev, **kw)
+                                   device=dev, fused=fused and not perturbed, **kw)
         tgt = scene(True)
         with torch.cuda.stream(stream):
             t_rgb, t_dep = (x.clone() for x in tgt.forward(Gj, cams, stream=stream)[:2])

@@ -22,8 +22,8 @@
  *  - Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy default
  *    stream).  No call synchronises the stream except gs_get_status and
  *    gs_render_stats, and no call reads device memory from the host, so
- *    gs_render / gs_render_backward / gs_deform_avatars(_backward) can be
- *    captured into a CUDA graph.
+ *    gs_render / gs_render_backward / gs_render_avatars(_backward) /
+ *    gs_deform_avatars(_backward) can be captured into a CUDA graph.
  *  - Returns GS_OK or a negative gs_status.  Errors the device detects (pair
  *    capacity exceeded) set a status word in the workspace, which gs_render
  *    clears when it starts and gs_render_backward leaves as it is; read it with
@@ -185,12 +185,40 @@ gs_status gs_render(const gs_gaussians *g, const gs_batch *batch, const gs_camer
  * total).  For those rows g->means is read but ignored and g->log_scales,
  * g->quats, g->cov3d are not used; opacity and SH are g's rows as for the
  * scene.  joint_G: device [n_avatars, n_joints, 3, 4].  The result equals
- * gs_deform_avatars into those rows followed by gs_render.  Forward only: a
- * gs_render_backward needs the posed rows in memory (the unfused path). */
+ * gs_deform_avatars into those rows followed by gs_render; its adjoint is
+ * gs_render_avatars_backward. */
 gs_status gs_render_avatars(const gs_gaussians *g, const gs_batch *batch, const gs_avatars *av, const float *joint_G,
                             const gs_camera *cams, const gs_render_config *cfg, void *workspace,
                             size_t workspace_bytes, float *out_rgb, float *out_depth, float *out_T,
                             int32_t *out_ncontrib, void *stream);
+
+/* Adjoint of gs_render_avatars (Sec. 3.3's LBS fused into the projection, and
+ * its gradient through the skinning), for L with dL/drgb = d_rgb and dL/ddepth
+ * = d_depth as in gs_render_backward.  Must follow gs_render_avatars with the
+ * same arguments and an untouched workspace.  The preprocess backward poses
+ * the avatar rows again by LBS (the same FP32 values as the forward: nothing
+ * posed is read from memory), and the LBS adjoint then carries their
+ * gradients to the canonical Gaussians and the joint matrices.
+ *   d_means, d_log_scales, d_quats, d_opacity_logits, d_sh: as for
+ *     gs_render_backward (ADDED, or overwritten under GS_FLAG_GRAD_OVERWRITE),
+ *     all rows; an avatar row of d_means receives dL/d(posed mean), its rows
+ *     of d_log_scales and d_quats are left as they are (accumulate) or zero
+ *     (overwrite);
+ *   d_cov3d: device [N,6], required: avatar rows receive dL/d(posed
+ *     covariance) (xx, xy, xz, yy, yz, zz; an off-diagonal entry holds the
+ *     gradient of both of its symmetric entries);
+ *   d_canon_means [M,3], d_canon_log_scales [M,3], d_canon_quats [M,4],
+ *   d_joint_G [n_avatars, n_joints, 3, 4]: device, 16-byte aligned, ADDED to
+ *     (as gs_deform_avatars_backward does).
+ * The result equals gs_render_backward of the posed rows followed by
+ * gs_deform_avatars_backward, up to the order of floating-point atomics. */
+gs_status gs_render_avatars_backward(const gs_gaussians *g, const gs_batch *batch, const gs_avatars *av,
+                                     const float *joint_G, const gs_camera *cams, const gs_render_config *cfg,
+                                     void *workspace, size_t workspace_bytes, const float *d_rgb,
+                                     const float *d_depth, float *d_means, float *d_log_scales, float *d_quats,
+                                     float *d_opacity_logits, float *d_sh, float *d_cov3d, float *d_canon_means,
+                                     float *d_canon_log_scales, float *d_canon_quats, float *d_joint_G,
+                                     void *stream);
 
 /* gs_render without a workspace, for callers that cannot allocate device
  * memory -- for instance a sensor plugin inside a host simulator whose device

@@ -86,6 +86,9 @@ _lib.gs_render_backward.argtypes = [_R(GsGaussians), _R(GsBatch), _P, _R(GsRende
 _lib.gs_deform_avatars.argtypes = [_R(GsAvatars), _P, _P, _P, _P]
 _lib.gs_render_avatars.argtypes = [_R(GsGaussians), _R(GsBatch), _R(GsAvatars), _P, _P, _R(GsRenderConfig), _P,
                                    ctypes.c_size_t, _P, _P, _P, _P, _P]
+_lib.gs_render_avatars_backward.argtypes = [_R(GsGaussians), _R(GsBatch), _R(GsAvatars), _P, _P, _R(GsRenderConfig),
+                                            _P, ctypes.c_size_t] + [_P] * 13
+_lib.gs_render_avatars_backward.restype = ctypes.c_int32
 _lib.gs_mesh_workspace_size.argtypes = [_R(GsBatch), _R(ctypes.c_size_t)]
 _lib.gs_render_mesh.argtypes = [_R(GsMesh), _R(GsBatch), _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_float, _P,
                                 ctypes.c_size_t, _P, _P, _P]
@@ -118,8 +121,8 @@ _lib.gs_version.restype = ctypes.c_int32
 EXPORTS = ("gs_render_static", "gs_render_static_status", "gs_profile_enable", "gs_profile_read", "gs_workspace_sections", "gs_render_workspace_size", "gs_render", "gs_render_backward", "gs_deform_avatars",
            "gs_deform_avatars_backward", "gs_get_status", "gs_render_stats", "gs_autotune", "gs_last_cuda_error",
            "gs_version", "gs_composite_nearest", "gs_forward_kinematics", "gs_interpolate_joints",
-           "gs_render_avatars", "gs_mesh_workspace_size", "gs_render_mesh", "gs_exp2_rate", "gs_avatar_capsules",
-           "gs_capsule_query")
+           "gs_render_avatars", "gs_render_avatars_backward", "gs_mesh_workspace_size", "gs_render_mesh",
+           "gs_exp2_rate", "gs_avatar_capsules", "gs_capsule_query")
 
 
 class GsError(RuntimeError):
@@ -336,6 +339,31 @@ class Renderer:
                                       self.ws_bytes, _ptr(rgb), _ptr(depth), _ptr(T), _ptr(nc), _stream(stream)),
                "gs_render_avatars")
         return out
+
+    def backward_avatars(self, g: Gaussians, av: "Avatars", joint_G: torch.Tensor, cams: torch.Tensor, d_rgb, d_depth,
+                         grads=None, avatar_grads=None, stream=None):
+        """gs_render_avatars_backward after forward_avatars: ``grads`` as for
+        backward (all rows; an avatar row's mean and cov3d entries hold the
+        posed gradients), ``avatar_grads`` (canonical means, log_scales, quats
+        and the joint matrices G) added to.  Both allocated zero if None."""
+        n, m = g.means.shape[0], av.m
+        dev = self.device
+        if grads is None:
+            grads = dict(means=torch.zeros((n, 3), device=dev), log_scales=torch.zeros((n, 3), device=dev),
+                         quats=torch.zeros((n, 4), device=dev), opacity_logits=torch.zeros((n,), device=dev),
+                         sh=torch.zeros((n, 16, 3), device=dev), cov3d=torch.zeros((n, 6), device=dev))
+        if avatar_grads is None:
+            avatar_grads = dict(means=torch.zeros((m, 3), device=dev), log_scales=torch.zeros((m, 3), device=dev),
+                                quats=torch.zeros((m, 4), device=dev), G=torch.zeros_like(joint_G))
+        d_rgb = d_rgb.contiguous()
+        d_depth = d_depth.contiguous()
+        _check(_lib.gs_render_avatars_backward(
+            ctypes.byref(g.c), ctypes.byref(self.batch.c), ctypes.byref(av.c), _ptr(joint_G), _ptr(cams),
+            ctypes.byref(self.cfg), _ptr(self.workspace), self.ws_bytes, _ptr(d_rgb), _ptr(d_depth),
+            _ptr(grads["means"]), _ptr(grads["log_scales"]), _ptr(grads["quats"]), _ptr(grads["opacity_logits"]),
+            _ptr(grads["sh"]), _ptr(grads["cov3d"]), _ptr(avatar_grads["means"]), _ptr(avatar_grads["log_scales"]),
+            _ptr(avatar_grads["quats"]), _ptr(avatar_grads["G"]), _stream(stream)), "gs_render_avatars_backward")
+        return grads, avatar_grads
 
     def stats(self, stream=None) -> dict:
         s = GsStats()
@@ -642,10 +670,13 @@ class AvatarScene:
     ``avatar_params`` are views of them, to be updated in place by an
     optimizer).  Gradients: gs_render_backward in overwrite mode into
     ``grads`` (all rows), then gs_deform_avatars_backward into ``avatar_grads``
-    (canonical means, log_scales, quats and the joint transforms G)."""
+    (canonical means, log_scales, quats and the joint transforms G).  With
+    ``fused`` the avatars are posed inside the render instead
+    (gs_render_avatars / gs_render_avatars_backward): nothing posed is written
+    to memory and the same gradients come out."""
 
     def __init__(self, scene: dict, avatars: dict, n_avatars: int, n_joints: int, width: int, height: int,
-                 n_views: int, sh_dtype=torch.float32, device="cuda", **cfg_kw):
+                 n_views: int, sh_dtype=torch.float32, device="cuda", fused: bool = False, **cfg_kw):
         dev = torch.device(device)
         ns, m = scene["means"].shape[0], avatars["means"].shape[0]
         n = ns + m
@@ -668,6 +699,11 @@ class AvatarScene:
                           avatars["weights"].to(**f32).contiguous(), avatars["avatar_of"].contiguous(), n_avatars,
                           n_joints, dest=torch.arange(ns, n, dtype=torch.int64, device=dev))
         self.g = Gaussians(self.means, self.log_scales, self.quats, self.opacity_logits, self.sh, self.cov3d)
+        self.fused = fused
+        if fused:  # canonical rows in env order (one env), no posed covariance
+            self.av_fused = Avatars(self.av_means, self.av_log_scales, self.av_quats, self.av.t[3], self.av.t[4],
+                                    self.av.t[5], n_avatars, n_joints)
+            self.g_fused = Gaussians(self.means, self.log_scales, self.quats, self.opacity_logits, self.sh)
         batch = Batch(np.array([0, n]), view_env=np.zeros(n_views, np.int32), env_cov3d_begin=[ns])
         self.renderer = Renderer(batch, width, height, device=device, grad_overwrite=True, **cfg_kw)
         self.out = self.renderer.alloc_outputs()
@@ -692,6 +728,8 @@ class AvatarScene:
     def forward(self, G: torch.Tensor, cams: torch.Tensor, stream=None):
         """Poses the avatars with joint transforms G [A,J,3,4] and renders every
         view: (rgb, depth, T, n_contrib) in this object's output buffers."""
+        if self.fused:
+            return self.renderer.forward_avatars(self.g_fused, self.av_fused, G, cams, out=self.out, stream=stream)
         deform(self.av, G, self.means, self.cov3d, stream=stream)
         return self.renderer.forward(self.g, cams, out=self.out, stream=stream)
 
@@ -699,10 +737,14 @@ class AvatarScene:
         """Adjoint of the last forward: (grads of every row, canonical avatar
         grads with dL/dG).  Scene rows of ``grads`` are the scene's gradients,
         avatar rows of its opacity_logits / sh the avatars' own."""
-        self.renderer.backward(self.g, cams, d_rgb, d_depth, grads=self.grads, stream=stream)
         with torch.cuda.stream(stream if stream is not None else torch.cuda.current_stream()):
             for t in self.avatar_grads.values():
                 t.zero_()
+        if self.fused:
+            self.renderer.backward_avatars(self.g_fused, self.av_fused, G, cams, d_rgb, d_depth, grads=self.grads,
+                                           avatar_grads=self.avatar_grads, stream=stream)
+            return self.grads, self.avatar_grads
+        self.renderer.backward(self.g, cams, d_rgb, d_depth, grads=self.grads, stream=stream)
         deform_backward(self.av, G, self.grads["means"], self.grads["cov3d"], self.avatar_grads, stream=stream)
         return self.grads, self.avatar_grads
 

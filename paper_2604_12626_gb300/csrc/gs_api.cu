@@ -278,6 +278,36 @@ void fill_table(const Plan &p, const gs_batch *b, const gs_render_config *cfg, i
     t.env_view_begin[b->n_envs] = cnt;
 }
 
+// Fused LBS: the avatar rows of env e are canonical rows env_av_base[e] + (g -
+// env_cov_begin[e]), env after env; their count must be av->m.
+static gs_status set_avatar_rows(Table &t, const gs_batch *b, const gs_avatars *av)
+{
+    int64_t base = 0;
+    for (int e = 0; e < b->n_envs; ++e) {
+        t.env_av_base[e] = base;
+        base += t.env_off[e + 1] - t.env_cov_begin[e];
+    }
+    return base == av->m ? GS_OK : GS_ERR_INVALID_ARG;
+}
+
+// Arguments of the fused-avatar entry points (gs_render_avatars and its backward).
+static gs_status check_avatars_fused(const gs_batch *batch, const gs_avatars *av, const float *joint_G)
+{
+    if (!batch || !av || !joint_G || !batch->env_cov3d_begin || !batch->env_offsets) return GS_ERR_INVALID_ARG;
+    if (av->dest) return GS_ERR_INVALID_ARG;
+    if (av->m < 0 || av->n_avatars < 1 || av->n_joints < 1 || av->n_joints > kMaxJoints) return GS_ERR_INVALID_ARG;
+    if (av->m > 0 && (!av->means || !av->log_scales || !av->quats || !av->joint_ids || !av->weights || !av->avatar_of))
+        return GS_ERR_INVALID_ARG;
+    const void *ptrs[] = {av->means, av->log_scales, av->quats, av->joint_ids, av->weights, av->avatar_of, joint_G};
+    for (const void *q : ptrs)
+        if (q && !aligned16(q)) return GS_ERR_ALIGNMENT;
+    if (batch->n_envs < 1 || batch->n_envs > GS_MAX_ENVS) return GS_ERR_INVALID_ARG;
+    for (int e = 0; e < batch->n_envs; ++e)
+        if (batch->env_cov3d_begin[e] < batch->env_offsets[e] || batch->env_cov3d_begin[e] > batch->env_offsets[e + 1])
+            return GS_ERR_INVALID_ARG;
+    return GS_OK;
+}
+
 gs_status check_gaussians(const gs_gaussians *g, const Plan &p, bool need_sq)
 {
     if (!g || !g->means || !g->opacity_logits || !g->sh) return GS_ERR_INVALID_ARG;
@@ -315,15 +345,7 @@ gs_status enqueue_forward(const gs_gaussians *g, const gs_batch *b, const gs_cam
     if (ws_bytes < p.total) return GS_ERR_WORKSPACE_TOO_SMALL;
     Table t;
     fill_table(p, b, cfg, sms, t);
-    if (av) {
-        // fused LBS: the avatar rows of env e are canonical rows env_av_base[e] + (g - env_cov_begin[e])
-        int64_t base = 0;
-        for (int e = 0; e < b->n_envs; ++e) {
-            t.env_av_base[e] = base;
-            base += t.env_off[e + 1] - t.env_cov_begin[e];
-        }
-        if (base != av->m) return GS_ERR_INVALID_ARG;
-    }
+    if (av && set_avatar_rows(t, b, av) != GS_OK) return GS_ERR_INVALID_ARG;
     Ws w = ws_ptrs(ws, p);
     {
         Stage st0(0, s);
@@ -402,10 +424,17 @@ gs_status gs_render(const gs_gaussians *g, const gs_batch *batch, const gs_camer
                            static_cast<cudaStream_t>(stream));
 }
 
-gs_status gs_render_backward(const gs_gaussians *g, const gs_batch *batch, const gs_camera *cams,
-                             const gs_render_config *cfg, void *workspace, size_t workspace_bytes,
-                             const float *d_rgb, const float *d_depth, float *d_means, float *d_log_scales,
-                             float *d_quats, float *d_opacity_logits, float *d_sh, float *d_cov3d, void *stream)
+// The adjoint of gs_render (av == NULL) or of gs_render_avatars: blend
+// backward, then the preprocess backward, which for the fused path poses the
+// avatar rows again and writes their posed mean / covariance gradients, then
+// the LBS adjoint of those rows into the canonical and joint gradients.
+static gs_status enqueue_backward(const gs_gaussians *g, const gs_batch *batch, const gs_camera *cams,
+                                  const gs_render_config *cfg, void *workspace, size_t workspace_bytes,
+                                  const float *d_rgb, const float *d_depth, float *d_means, float *d_log_scales,
+                                  float *d_quats, float *d_opacity_logits, float *d_sh, float *d_cov3d,
+                                  cudaStream_t s, const gs_avatars *av = nullptr, const float *joint_G = nullptr,
+                                  float *d_canon_means = nullptr, float *d_canon_log_scales = nullptr,
+                                  float *d_canon_quats = nullptr, float *d_joint_G = nullptr)
 {
     int sms = 0;
     gs_status st = device_init(&sms);
@@ -425,10 +454,12 @@ gs_status gs_render_backward(const gs_gaussians *g, const gs_batch *batch, const
         if (!aligned16(q)) return GS_ERR_ALIGNMENT;
     if (d_cov3d && !aligned16(d_cov3d)) return GS_ERR_ALIGNMENT;
     if (workspace_bytes < p.total) return GS_ERR_WORKSPACE_TOO_SMALL;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     Ws w = ws_ptrs(workspace, p);
     const bool overwrite = (cfg->flags & GS_FLAG_GRAD_OVERWRITE) != 0;
     GradOut o{d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_cov3d};
+    Table t;
+    fill_table(p, batch, cfg, sms, t);
+    if (av && set_avatar_rows(t, batch, av) != GS_OK) return GS_ERR_INVALID_ARG;
     {
         Stage st7(7, s);
         // the record gradient rows were zeroed by the forward (visible records
@@ -444,11 +475,45 @@ gs_status gs_render_backward(const gs_gaussians *g, const gs_batch *batch, const
     }
     {
         Stage st8(8, s);
-        Table t;
-        fill_table(p, batch, cfg, sms, t);
-        launch_preprocess_backward(t, g, cams, w, o, p.n_chunks, overwrite, s);
+        launch_preprocess_backward(t, g, cams, w, o, p.n_chunks, overwrite, s, av, joint_G);
+    }
+    if (av && av->m > 0) {
+        Stage st10(10, s);
+        launch_deform_backward(av, joint_G, d_means, d_cov3d, d_canon_means, d_canon_log_scales, d_canon_quats,
+                               d_joint_G, s, w.tb);
     }
     return check_launch();
+}
+
+gs_status gs_render_backward(const gs_gaussians *g, const gs_batch *batch, const gs_camera *cams,
+                             const gs_render_config *cfg, void *workspace, size_t workspace_bytes,
+                             const float *d_rgb, const float *d_depth, float *d_means, float *d_log_scales,
+                             float *d_quats, float *d_opacity_logits, float *d_sh, float *d_cov3d, void *stream)
+{
+    return enqueue_backward(g, batch, cams, cfg, workspace, workspace_bytes, d_rgb, d_depth, d_means, d_log_scales,
+                            d_quats, d_opacity_logits, d_sh, d_cov3d, static_cast<cudaStream_t>(stream));
+}
+
+gs_status gs_render_avatars_backward(const gs_gaussians *g, const gs_batch *batch, const gs_avatars *av,
+                                     const float *joint_G, const gs_camera *cams, const gs_render_config *cfg,
+                                     void *workspace, size_t workspace_bytes, const float *d_rgb,
+                                     const float *d_depth, float *d_means, float *d_log_scales, float *d_quats,
+                                     float *d_opacity_logits, float *d_sh, float *d_cov3d, float *d_canon_means,
+                                     float *d_canon_log_scales, float *d_canon_quats, float *d_joint_G,
+                                     void *stream)
+{
+    gs_status st = check_avatars_fused(batch, av, joint_G);
+    if (st != GS_OK) return st;
+    if (!d_cov3d || !d_canon_means || !d_canon_log_scales || !d_canon_quats || !d_joint_G) return GS_ERR_INVALID_ARG;
+    const void *ptrs[] = {d_canon_means, d_canon_log_scales, d_canon_quats, d_joint_G};
+    for (const void *q : ptrs)
+        if (!aligned16(q)) return GS_ERR_ALIGNMENT;
+    if (!g) return GS_ERR_INVALID_ARG;
+    gs_gaussians gg = *g;
+    gg.cov3d = nullptr; // the avatar rows are posed inside the preprocess backward
+    return enqueue_backward(&gg, batch, cams, cfg, workspace, workspace_bytes, d_rgb, d_depth, d_means,
+                            d_log_scales, d_quats, d_opacity_logits, d_sh, d_cov3d, static_cast<cudaStream_t>(stream),
+                            av, joint_G, d_canon_means, d_canon_log_scales, d_canon_quats, d_joint_G);
 }
 
 gs_status gs_deform_avatars(const gs_avatars *av, const float *joint_G, float *out_means, float *out_cov3d,
@@ -475,17 +540,9 @@ gs_status gs_render_avatars(const gs_gaussians *g, const gs_batch *batch, const 
                             size_t workspace_bytes, float *out_rgb, float *out_depth, float *out_T,
                             int32_t *out_ncontrib, void *stream)
 {
-    if (!g || !batch || !av || !joint_G || !batch->env_cov3d_begin) return GS_ERR_INVALID_ARG;
-    if (av->dest) return GS_ERR_INVALID_ARG;
-    if (av->m < 0 || av->n_avatars < 1 || av->n_joints < 1 || av->n_joints > kMaxJoints) return GS_ERR_INVALID_ARG;
-    if (av->m > 0 && (!av->means || !av->log_scales || !av->quats || !av->joint_ids || !av->weights || !av->avatar_of))
-        return GS_ERR_INVALID_ARG;
-    const void *ptrs[] = {av->means, av->log_scales, av->quats, av->joint_ids, av->weights, av->avatar_of, joint_G};
-    for (const void *q : ptrs)
-        if (q && !aligned16(q)) return GS_ERR_ALIGNMENT;
-    for (int e = 0; e < batch->n_envs; ++e)
-        if (batch->env_cov3d_begin[e] < batch->env_offsets[e] || batch->env_cov3d_begin[e] > batch->env_offsets[e + 1])
-            return GS_ERR_INVALID_ARG;
+    if (!g) return GS_ERR_INVALID_ARG;
+    gs_status st = check_avatars_fused(batch, av, joint_G);
+    if (st != GS_OK) return st;
     gs_gaussians gg = *g;
     gg.cov3d = nullptr; // the avatar rows are posed inside the preprocess
     return enqueue_forward(&gg, batch, cams, cfg, workspace, workspace_bytes, out_rgb, out_depth, out_T,

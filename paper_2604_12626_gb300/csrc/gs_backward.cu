@@ -895,6 +895,12 @@ __device__ __forceinline__ void sh_dir_vjp(float x, float y, float z, const floa
 struct GaussInB {
     const float *means, *log_scales, *quats, *ologits, *cov3d;
     const void *sh;
+    // fused LBS (gs_render_avatars_backward): the avatar rows are posed again
+    // here, as the forward's preprocess posed them, from their canonical rows
+    const float *av_means, *av_log_scales, *av_quats, *av_weights, *av_G;
+    const uint16_t *av_ids;
+    const int32_t *av_of;
+    int32_t n_avatars, n_joints;
 };
 
 // Streams the 48 SH coefficients of Gaussian g and returns, per basis
@@ -942,25 +948,47 @@ __device__ __forceinline__ void sh_weighted(const void *sh, int64_t g, const flo
 // per-Gaussian rows are scattered (a quarter of the rows are seen), so they
 // are loaded through L2 only (ld.global.cg): an L1 fill would pull whole
 // 128-byte lines of mostly unseen neighbours.
-template <int SHT, bool OVERWRITE>
+template <int SHT, bool OVERWRITE, bool FUSED>
 __device__ __forceinline__ void gaussian_backward(const gs_camera *__restrict__ cams, const GaussInB &gin, const Ws &w,
                                                   const Table *tb, const GradOut &o, int64_t g, int e)
 {
     const int vb = tb->env_view_begin[e], ve = tb->env_view_begin[e + 1];
     const int64_t local = g - tb->env_off[e];
-    const bool use_cov = gin.cov3d != nullptr && g >= tb->env_cov_begin[e];
-    const float mx = __ldcg(gin.means + 3 * g), my = __ldcg(gin.means + 3 * g + 1), mz = __ldcg(gin.means + 3 * g + 2);
+    const bool posed = FUSED && g >= tb->env_cov_begin[e];
+    const bool use_cov = posed || (gin.cov3d != nullptr && g >= tb->env_cov_begin[e]);
+    float mx, my, mz;
     float S[6];
     float3 ls = make_float3(0.f, 0.f, 0.f);
     float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
-    if (use_cov) {
-#pragma unroll
-        for (int i = 0; i < 6; ++i) S[i] = __ldcg(gin.cov3d + 6 * g + i);
+    if (FUSED && posed) {
+        // posed mean and covariance by LBS, bit for bit the forward's
+        const int64_t i = tb->env_av_base[e] + (g - tb->env_cov_begin[e]);
+        const int a = clamp_avatar(__ldg(gin.av_of + i), gin.n_avatars);
+        const ushort4 id = clamp_ids(__ldg(reinterpret_cast<const ushort4 *>(gin.av_ids) + i), gin.n_joints);
+        const float4 wt = __ldg(reinterpret_cast<const float4 *>(gin.av_weights) + i);
+        float mu[3];
+        lbs_gaussian(gin.av_G + (size_t)a * gin.n_joints * 12, id, wt,
+                     make_float3(__ldcg(gin.av_means + 3 * i), __ldcg(gin.av_means + 3 * i + 1),
+                                 __ldcg(gin.av_means + 3 * i + 2)),
+                     make_float3(__ldcg(gin.av_log_scales + 3 * i), __ldcg(gin.av_log_scales + 3 * i + 1),
+                                 __ldcg(gin.av_log_scales + 3 * i + 2)),
+                     __ldcg(reinterpret_cast<const float4 *>(gin.av_quats) + i), mu, S);
+        mx = mu[0];
+        my = mu[1];
+        mz = mu[2];
     } else {
-        ls = make_float3(__ldcg(gin.log_scales + 3 * g), __ldcg(gin.log_scales + 3 * g + 1),
-                         __ldcg(gin.log_scales + 3 * g + 2));
-        q = __ldcg(reinterpret_cast<const float4 *>(gin.quats) + g);
-        sigma_from_sq(ls, q, S);
+        mx = __ldcg(gin.means + 3 * g);
+        my = __ldcg(gin.means + 3 * g + 1);
+        mz = __ldcg(gin.means + 3 * g + 2);
+        if (use_cov) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) S[i] = __ldcg(gin.cov3d + 6 * g + i);
+        } else {
+            ls = make_float3(__ldcg(gin.log_scales + 3 * g), __ldcg(gin.log_scales + 3 * g + 1),
+                             __ldcg(gin.log_scales + 3 * g + 2));
+            q = __ldcg(reinterpret_cast<const float4 *>(gin.quats) + g);
+            sigma_from_sq(ls, q, S);
+        }
     }
     float op = 0.f; // from the record rows (the forward wrote it there)
     float gS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -1130,7 +1158,7 @@ __device__ __forceinline__ void gaussian_backward(const gs_camera *__restrict__ 
 constexpr int kBwdWarpQ = 64;
 
 
-template <int SHT, bool OVERWRITE>
+template <int SHT, bool OVERWRITE, bool FUSED>
 __global__ void __launch_bounds__(256, 2) preprocess_backward_kernel(const gs_camera *__restrict__ cams, GaussInB gin,
                                                                      Ws w, GradOut o, const __grid_constant__ Table tbp)
 {
@@ -1169,11 +1197,11 @@ __global__ void __launch_bounds__(256, 2) preprocess_backward_kernel(const gs_ca
             const int64_t gg = g0 + q[(head + lane) & (kBwdWarpQ - 1)];
             head += 32;
             __syncwarp();
-            gaussian_backward<SHT, OVERWRITE>(cams, gin, w, tb, o, gg, lo);
+            gaussian_backward<SHT, OVERWRITE, FUSED>(cams, gin, w, tb, o, gg, lo);
         }
     }
     if (lane < tail - head)
-        gaussian_backward<SHT, OVERWRITE>(cams, gin, w, tb, o, g0 + q[(head + lane) & (kBwdWarpQ - 1)], lo);
+        gaussian_backward<SHT, OVERWRITE, FUSED>(cams, gin, w, tb, o, g0 + q[(head + lane) & (kBwdWarpQ - 1)], lo);
 }
 
 // ---------------------------------------------------------------------------
@@ -1280,25 +1308,38 @@ void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rg
     else launch_bb<1, 1>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);
 }
 
-template <bool OW>
-static void launch_pb(const Table &tb, const gs_gaussians *g, const gs_camera *cams, const Ws &w, const GradOut &o,
-                      unsigned grid, cudaStream_t s)
+template <bool OW, bool FUSED>
+static void launch_pb(const Table &tb, const GaussInB &gin, int sh_dtype, const gs_camera *cams, const Ws &w,
+                      const GradOut &o, unsigned grid, cudaStream_t s)
 {
-    GaussInB gin{g->means, g->log_scales, g->quats, g->opacity_logits, g->cov3d, g->sh};
-    switch (g->sh_dtype) {
-    case GS_SH_F16: preprocess_backward_kernel<GS_SH_F16, OW><<<grid, 256, 0, s>>>(cams, gin, w, o, tb); break;
-    case GS_SH_BF16: preprocess_backward_kernel<GS_SH_BF16, OW><<<grid, 256, 0, s>>>(cams, gin, w, o, tb); break;
-    default: preprocess_backward_kernel<GS_SH_F32, OW><<<grid, 256, 0, s>>>(cams, gin, w, o, tb); break;
+    switch (sh_dtype) {
+    case GS_SH_F16: preprocess_backward_kernel<GS_SH_F16, OW, FUSED><<<grid, 256, 0, s>>>(cams, gin, w, o, tb); break;
+    case GS_SH_BF16: preprocess_backward_kernel<GS_SH_BF16, OW, FUSED><<<grid, 256, 0, s>>>(cams, gin, w, o, tb); break;
+    default: preprocess_backward_kernel<GS_SH_F32, OW, FUSED><<<grid, 256, 0, s>>>(cams, gin, w, o, tb); break;
     }
 }
 
 void launch_preprocess_backward(const Table &tb, const gs_gaussians *g, const gs_camera *cams, const Ws &w,
-                                const GradOut &o, int n_chunks, bool overwrite, cudaStream_t s)
+                                const GradOut &o, int n_chunks, bool overwrite, cudaStream_t s, const gs_avatars *av,
+                                const float *joint_G)
 {
     const unsigned grid = (unsigned)n_chunks;
     if (!grid) return;
-    if (overwrite) launch_pb<true>(tb, g, cams, w, o, grid, s);
-    else launch_pb<false>(tb, g, cams, w, o, grid, s);
+    GaussInB gin{g->means, g->log_scales, g->quats, g->opacity_logits, g->cov3d, g->sh,
+                 nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0};
+    const bool fused = av && joint_G;
+    if (fused) {
+        gin.av_means = av->means; gin.av_log_scales = av->log_scales; gin.av_quats = av->quats;
+        gin.av_weights = av->weights; gin.av_G = joint_G; gin.av_ids = av->joint_ids; gin.av_of = av->avatar_of;
+        gin.n_avatars = av->n_avatars; gin.n_joints = av->n_joints;
+    }
+    if (overwrite) {
+        if (fused) launch_pb<true, true>(tb, gin, g->sh_dtype, cams, w, o, grid, s);
+        else launch_pb<true, false>(tb, gin, g->sh_dtype, cams, w, o, grid, s);
+    } else {
+        if (fused) launch_pb<false, true>(tb, gin, g->sh_dtype, cams, w, o, grid, s);
+        else launch_pb<false, false>(tb, gin, g->sh_dtype, cams, w, o, grid, s);
+    }
 }
 
 cudaError_t configure_backward_kernels()

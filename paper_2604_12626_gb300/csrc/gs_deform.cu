@@ -24,7 +24,24 @@ struct AvIn {
     const int64_t *dest;
     int64_t m;
     int32_t n_avatars, n_joints;
+    // without dest: the rows of a batch's avatars, canonical row i of env e at
+    // env_cov_begin[e] + (i - env_av_base[e]) (gs_render_avatars_backward)
+    const Table *tb;
 };
+
+// Batch row of canonical avatar row i: e the last env whose first avatar row
+// env_av_base[e] <= i (an env without avatars shares its successor's base and
+// precedes it).
+__device__ __forceinline__ int64_t avatar_row(const Table *tb, int64_t i)
+{
+    int lo = 0, hi = tb->n_envs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tb->env_av_base[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return tb->env_cov_begin[lo] + (i - tb->env_av_base[lo]);
+}
 
 __global__ void __launch_bounds__(256) deform_kernel(AvIn in, const float *__restrict__ G, float *out_means,
                                                      float *out_cov)
@@ -101,7 +118,7 @@ __global__ void __launch_bounds__(256) deform_backward_kernel(AvIn in, const flo
         float S6[6];
         sigma_from_sq(ls, q, S6);
         const float S[9] = {S6[0], S6[1], S6[2], S6[1], S6[3], S6[4], S6[2], S6[4], S6[5]};
-        const int64_t d = in.dest ? in.dest[i] : i;
+        const int64_t d = in.dest ? in.dest[i] : in.tb ? avatar_row(in.tb, i) : i;
         const float gm[3] = {d_means[3 * d], d_means[3 * d + 1], d_means[3 * d + 2]};
         const float *gc = d_cov + 6 * d;
         const float Gm[9] = {gc[0], 0.5f * gc[1], 0.5f * gc[2], 0.5f * gc[1], gc[3], 0.5f * gc[4],
@@ -211,10 +228,10 @@ __global__ void __launch_bounds__(256) deform_backward_kernel(AvIn in, const flo
     }
 }
 
-static AvIn make_in(const gs_avatars *av)
+static AvIn make_in(const gs_avatars *av, const Table *tb = nullptr)
 {
     return AvIn{av->means, av->log_scales, av->quats, av->weights, av->joint_ids, av->avatar_of, av->dest,
-                av->m, av->n_avatars, av->n_joints};
+                av->m, av->n_avatars, av->n_joints, tb};
 }
 
 void launch_deform(const gs_avatars *av, const float *G, float *out_means, float *out_cov, cudaStream_t s)
@@ -224,10 +241,11 @@ void launch_deform(const gs_avatars *av, const float *G, float *out_means, float
 }
 
 void launch_deform_backward(const gs_avatars *av, const float *G, const float *d_means, const float *d_cov,
-                            float *d_cm, float *d_cls, float *d_cq, float *d_G, cudaStream_t s)
+                            float *d_cm, float *d_cls, float *d_cq, float *d_G, cudaStream_t s, const Table *rows)
 {
     const unsigned grid = (unsigned)((av->m + 255) / 256);
-    if (grid) deform_backward_kernel<<<grid, 256, 0, s>>>(make_in(av), G, d_means, d_cov, d_cm, d_cls, d_cq, d_G);
+    if (grid)
+        deform_backward_kernel<<<grid, 256, 0, s>>>(make_in(av, rows), G, d_means, d_cov, d_cm, d_cls, d_cq, d_G);
 }
 
 } // namespace gs

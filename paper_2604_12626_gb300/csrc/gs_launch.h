@@ -51,12 +51,18 @@ void launch_clear_record_grads(const Ws &w, int64_t n_records, int n_sms, cudaSt
 void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,
                            int px, int py, int threads, int batch_depth, int n_sms, const GradOut *clear, int64_t n,
                            cudaStream_t s);
+// av, joint_G: the fused path (gs_render_avatars_backward) poses the avatar
+// rows again by LBS and writes their posed mean / covariance gradients
 void launch_preprocess_backward(const Table &tb, const gs_gaussians *g, const gs_camera *cams, const Ws &w,
-                                const GradOut &o, int n_chunks, bool overwrite, cudaStream_t s);
+                                const GradOut &o, int n_chunks, bool overwrite, cudaStream_t s,
+                                const gs_avatars *av = nullptr, const float *joint_G = nullptr);
 
 void launch_deform(const gs_avatars *av, const float *G, float *out_means, float *out_cov, cudaStream_t s);
+// rows: the batch layout (device table) that maps canonical avatar rows to
+// batch rows when av->dest is NULL (gs_render_avatars_backward), else NULL
 void launch_deform_backward(const gs_avatars *av, const float *G, const float *d_means, const float *d_cov,
-                            float *d_cm, float *d_cls, float *d_cq, float *d_G, cudaStream_t s);
+                            float *d_cm, float *d_cls, float *d_cq, float *d_G, cudaStream_t s,
+                            const Table *rows = nullptr);
 
 void launch_composite(const float *rgb_a, const float *depth_a, const float *rgb_b, const float *depth_b,
                       float *rgb_out, float *depth_out, int64_t n_views, int64_t hw, int n_sms, cudaStream_t s);

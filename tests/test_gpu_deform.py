@@ -136,7 +136,8 @@ def test_rooms_with_avatars_batched_vs_oracle(gs, oracle):
 def test_fused_lbs_in_preprocess_equals_deform_then_render(gs, oracle):
     """gs_render_avatars (LBS inside the preprocess, posed Gaussians never in
     memory) against gs_deform_avatars + gs_render on the same inputs, and
-    against the oracle."""
+    against the oracle; gs_render_avatars_backward against gs_render_backward +
+    gs_deform_avatars_backward."""
     W = H = 96
     n_room, n_av, n_avatars = 40_000, 3000, 2
     envs, cams = [], []
@@ -169,10 +170,37 @@ def test_fused_lbs_in_preprocess_equals_deform_then_render(gs, oracle):
     # fused: the avatar rows of `cat` keep their canonical (unposed) values
     Gf = gs.Gaussians.from_numpy(cat)
     r2 = gs.Renderer(batch, W, H, persistent=True)
-    b = r2.forward_avatars(Gf, gpu_avatars(gs, av_all, avatar_of_all, 2 * n_avatars), G_all, ct)
+    av_f = gpu_avatars(gs, av_all, avatar_of_all, 2 * n_avatars)
+    b = r2.forward_avatars(Gf, av_f, G_all, ct)
     torch.cuda.synchronize()
     for x, y in zip(a, b):
         assert torch.equal(x, y)
+    # the adjoints: gs_render_backward + gs_deform_avatars_backward against
+    # gs_render_avatars_backward, equal up to the order of float atomics
+    rng = np.random.default_rng(5)
+    d_rgb = T(rng.standard_normal((2, 3, H, W)))
+    d_depth = T(0.1 * rng.standard_normal((2, H, W)))
+    g1 = r1.backward(Gg, ct, d_rgb, d_depth)
+    ga1 = dict(means=torch.zeros((2 * n_avatars * n_av, 3), device="cuda"),
+               log_scales=torch.zeros((2 * n_avatars * n_av, 3), device="cuda"),
+               quats=torch.zeros((2 * n_avatars * n_av, 4), device="cuda"), G=torch.zeros_like(G_all))
+    gs.deform_backward(gpu_avatars(gs, av_all, avatar_of_all, 2 * n_avatars, dest), G_all, g1["means"], g1["cov3d"],
+                       ga1)
+    g2, ga2 = r2.backward_avatars(Gf, av_f, G_all, ct, d_rgb, d_depth)
+    torch.cuda.synchronize()
+    assert r2.status() == 0
+    av_rows = torch.from_numpy(dest).cuda()
+    pairs = [(g1[k], g2[k], k) for k in ("means", "opacity_logits", "sh")]
+    pairs += [(g1["cov3d"][av_rows], g2["cov3d"][av_rows], "posed cov3d")]
+    pairs += [(ga1[k], ga2[k], "canonical " + k) for k in ("means", "log_scales", "quats", "G")]
+    scene_rows = torch.ones(2 * m_env, dtype=torch.bool, device="cuda")
+    scene_rows[av_rows] = False
+    pairs += [(g1[k][scene_rows], g2[k][scene_rows], "scene " + k) for k in ("log_scales", "quats")]
+    for x, y, name in pairs:
+        scale = float(x.abs().max())
+        assert scale > 0, name
+        err = float((x - y).abs().max())
+        assert err <= 1e-5 * scale, (name, err, scale)
     for e, (room, av, G, avatar_of) in enumerate(envs):
         pm, pc = oracle.lbs(av["means"], av["log_scales"], av["quats"], av["joint_ids"].astype(np.int32),
                             av["weights"], avatar_of, G.astype(np.float64))

@@ -7,7 +7,9 @@ gs_render_backward in overwrite mode, gs_deform_avatars_backward).  Two views'
 images against the FP64 oracle; the gradients of every scene and avatar
 parameter and of the joint transforms, summed over all 16 views, against the
 oracle's adjoint (LBS in FP64, posed rows flagged inexact), per group by
-relative L2 and element by element.  FP32 and FP16 SH storage.  Paper:
+relative L2 and element by element.  FP32 and FP16 SH storage, and the fused
+path (gs_render_avatars, gs_render_avatars_backward: the avatars posed inside
+the render).  Paper:
 differentiable rasterisation (Sec. 2.2, Sec. 3.2) of scenes with avatars
 (Sec. 3.3)."""
 from concurrent.futures import ThreadPoolExecutor
@@ -40,7 +42,7 @@ def workload():
     return synth.training_scene(seed=0, W=W, H=H, n_views=V)
 
 
-def _scene(gs, wl, sh_dtype, perturbed=False):
+def _scene(gs, wl, sh_dtype, perturbed=False, fused=False):
     T = lambda x, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(x)).to("cuda", dt)  # noqa: E731
     room, av = wl["room"], wl["avatars"]
     rm, rsh, am, ash = room["means"], room["sh"], av["means"], av["sh"]
@@ -52,18 +54,19 @@ def _scene(gs, wl, sh_dtype, perturbed=False):
                    opacity_logits=T(av["opacity_logits"]), sh=T(ash), joint_ids=T(av["joint_ids"].view(np.int16),
                                                                                    torch.int16),
                    weights=T(av["weights"]), avatar_of=T(av["avatar_of"], torch.int32))
-    return gs.AvatarScene(scene, avatars, wl["G"].shape[0], 24, W, H, V, sh_dtype=sh_dtype, **KW)
+    return gs.AvatarScene(scene, avatars, wl["G"].shape[0], 24, W, H, V, sh_dtype=sh_dtype, fused=fused, **KW)
 
 
-@pytest.mark.parametrize("sh_dtype", [torch.float32, torch.float16])
-def test_training_step_matches_oracle(gs, oracle, workload, sh_dtype):
+@pytest.mark.parametrize("sh_dtype,fused", [(torch.float32, False), (torch.float16, False), (torch.float32, True)],
+                         ids=["f32", "f16", "f32-fused"])
+def test_training_step_matches_oracle(gs, oracle, workload, sh_dtype, fused):
     wl = workload
     cams = gs.cameras_tensor(wl["cams"])
     G = torch.from_numpy(wl["G"]).cuda()
     tgt = _scene(gs, wl, sh_dtype, perturbed=True)
     t_rgb, t_depth = (x.clone() for x in tgt.forward(G, cams)[:2])
     del tgt
-    sc = _scene(gs, wl, sh_dtype)
+    sc = _scene(gs, wl, sh_dtype, fused=fused)
     out = sc.forward(G, cams)
     d_rgb = torch.sign(out[0] - t_rgb)
     d_depth = 0.1 * torch.sign(out[1] - t_depth)

@@ -341,6 +341,8 @@ __global__ void __launch_bounds__(kPreThreads, 2) preprocess_kernel(const gs_cam
                         canonical_direction(gin, tb->env_av_base[c.e0] + (g - cov_begin), en.d0, en.d1, en.d2);
                     en.x0 = (uint16_t)x0; en.x1 = (uint16_t)x1; en.y0 = (uint16_t)y0; en.y1 = (uint16_t)y1;
                     en.v = (uint16_t)(cam_smem ? tb->env_views[c.vb + k] : v); en.k = (uint16_t)k;
+                    // its SH row, read by stage C once 32 entries are queued
+                    prefetch_l2(sh_row<SHT>(gin.sh, g), sh_row_bytes<SHT>());
                 }
             }
         }

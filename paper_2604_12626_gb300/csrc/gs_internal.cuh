@@ -241,6 +241,22 @@ __device__ __forceinline__ float2 gauss_power2(float A, float B, float C, float2
     return __ffma2_rn(make_float2(-0.5f, -0.5f), q, nb);
 }
 
+// Prefetch into L2 of the lines holding bytes [p, p + n) (n <= 256): a
+// scattered row that a later stage reads arrives from L2 instead of HBM.
+__device__ __forceinline__ void prefetch_l2(const void *p, int n)
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    for (uintptr_t l = a & ~(uintptr_t)127; l < a + (uintptr_t)n; l += 128)
+        asm volatile("prefetch.global.L2 [%0];\n" ::"l"(l));
+}
+
+// SH row of Gaussian g for the storage type (48 coefficients)
+template <int SHT> __device__ __forceinline__ const void *sh_row(const void *sh, int64_t g)
+{
+    return static_cast<const char *>(sh) + g * 48 * (SHT == GS_SH_F32 ? 4 : 2);
+}
+template <int SHT> __host__ __device__ constexpr int sh_row_bytes() { return 48 * (SHT == GS_SH_F32 ? 4 : 2); }
+
 // cp.async gathers (16 bytes each) into shared memory
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {

@@ -71,6 +71,11 @@ typedef int32_t gs_status;
                                      A3^-1 (mu' - C) normalised, the view direction in its
                                      canonical frame (A3: linear part of its skinning matrix);
                                      without it, at the world view direction */
+#define GS_FLAG_GRAD_PRECLEARED 32 /* gs_render_backward / gs_render_avatars_backward write the rows
+                                      of the Gaussians some view sees and leave every other row as
+                                      it is: on arrays set to zero beforehand (gs_zero_gradients,
+                                      e.g. on a stream beside gs_render) the result of
+                                      GS_FLAG_GRAD_OVERWRITE without its clearing */
 
 #define GS_MAX_ENVS 512
 #define GS_MAX_VIEWS 512
@@ -269,6 +274,18 @@ gs_status gs_render_backward(const gs_gaussians *g, const gs_batch *batch, const
                              const gs_render_config *cfg, void *workspace, size_t workspace_bytes,
                              const float *d_rgb, const float *d_depth, float *d_means, float *d_log_scales,
                              float *d_quats, float *d_opacity_logits, float *d_sh, float *d_cov3d, void *stream);
+
+/* Sets the parameter-gradient arrays of n Gaussians to zero -- d_sh
+ * [n,16,3], d_means [n,3], d_opacity_logits [n], d_log_scales [n,3], d_quats
+ * [n,4], d_cov3d [n,6] or NULL (device, 16-byte aligned) -- with TMA bulk
+ * stores from n_ctas CTAs of 128 threads (n_ctas < 1: one per two SMs).  The
+ * clearing that GS_FLAG_GRAD_OVERWRITE does inside the backward, as a call of
+ * its own: enqueued on a second stream while gs_render runs (the blend leaves
+ * HBM mostly idle), it takes the store stream off the backward, which then
+ * runs with GS_FLAG_GRAD_PRECLEARED after an event joins the streams.  The
+ * paper has no counterpart.  Asynchronous. */
+gs_status gs_zero_gradients(int64_t n, float *d_means, float *d_log_scales, float *d_quats, float *d_opacity_logits,
+                            float *d_sh, float *d_cov3d, int32_t n_ctas, void *stream);
 
 /* Linear blend skinning (Sec. 3.3): A = sum_k w_k G[avatar][j_k] (3x4),
  * mean' = A[:, :3] mean + A[:, 3], cov' = A[:, :3] Sigma A[:, :3]^T with

@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "GS_OK", -1: "GS_ERR_INVALID_ARG", -2: "GS_ERR_ALIGNMENT", -3
                 -4: "GS_ERR_CAPACITY", -5: "GS_ERR_CUDA", -6: "GS_ERR_TIMEOUT", -7: "GS_ERR_UNSUPPORTED"}
 SH_F32, SH_F16, SH_BF16 = 0, 1, 2
 FLAG_PERSISTENT, FLAG_NORMALIZE_DEPTH, FLAG_GRAD_OVERWRITE, FLAG_COUNT_EVALS, FLAG_AVATAR_CANONICAL_SH = 1, 2, 4, 8, 16
+FLAG_GRAD_PRECLEARED = 32
 N_STAGES = 11
 STAGES = ("setup", "preprocess", "scan", "scatter", "sort", "merge", "blend", "blend_backward",
           "preprocess_backward", "deform", "deform_backward")
@@ -89,6 +90,8 @@ _lib.gs_render_avatars.argtypes = [_R(GsGaussians), _R(GsBatch), _R(GsAvatars), 
 _lib.gs_render_avatars_backward.argtypes = [_R(GsGaussians), _R(GsBatch), _R(GsAvatars), _P, _P, _R(GsRenderConfig),
                                             _P, ctypes.c_size_t] + [_P] * 13
 _lib.gs_render_avatars_backward.restype = ctypes.c_int32
+_lib.gs_zero_gradients.argtypes = [ctypes.c_int64, _P, _P, _P, _P, _P, _P, ctypes.c_int32, _P]
+_lib.gs_zero_gradients.restype = ctypes.c_int32
 _lib.gs_mesh_workspace_size.argtypes = [_R(GsBatch), _R(ctypes.c_size_t)]
 _lib.gs_render_mesh.argtypes = [_R(GsMesh), _R(GsBatch), _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_float, _P,
                                 ctypes.c_size_t, _P, _P, _P]
@@ -122,7 +125,7 @@ EXPORTS = ("gs_render_static", "gs_render_static_status", "gs_profile_enable", "
            "gs_deform_avatars_backward", "gs_get_status", "gs_render_stats", "gs_autotune", "gs_last_cuda_error",
            "gs_version", "gs_composite_nearest", "gs_forward_kinematics", "gs_interpolate_joints",
            "gs_render_avatars", "gs_render_avatars_backward", "gs_mesh_workspace_size", "gs_render_mesh",
-           "gs_exp2_rate", "gs_avatar_capsules", "gs_capsule_query")
+           "gs_exp2_rate", "gs_avatar_capsules", "gs_capsule_query", "gs_zero_gradients")
 
 
 class GsError(RuntimeError):
@@ -308,8 +311,12 @@ class Renderer:
                               _stream(stream)), "gs_render")
         return out
 
-    def backward(self, g: Gaussians, cams: torch.Tensor, d_rgb, d_depth, grads=None, stream=None):
-        """Adds dL/d(params) into ``grads`` (allocated zero if None); returns it."""
+    def backward(self, g: Gaussians, cams: torch.Tensor, d_rgb, d_depth, grads=None, stream=None,
+                 precleared: bool = False):
+        """Adds dL/d(params) into ``grads`` (allocated zero if None), or
+        overwrites them in overwrite mode; returns it.  ``precleared``: the
+        arrays were set to zero beforehand (zero_gradients, e.g. on a stream
+        beside the forward), so the backward writes the seen rows only."""
         n = g.means.shape[0]
         dev = self.device
         if grads is None:
@@ -319,8 +326,11 @@ class Renderer:
                          cov3d=torch.zeros((n, 6), device=dev) if g.cov3d is not None else None)
         d_rgb = d_rgb.contiguous()
         d_depth = d_depth.contiguous()
+        cfg = GsRenderConfig.from_buffer_copy(self.cfg)
+        if precleared:
+            cfg.flags |= FLAG_GRAD_PRECLEARED
         _check(_lib.gs_render_backward(ctypes.byref(g.c), ctypes.byref(self.batch.c), _ptr(cams),
-                                       ctypes.byref(self.cfg), _ptr(self.workspace), self.ws_bytes, _ptr(d_rgb),
+                                       ctypes.byref(cfg), _ptr(self.workspace), self.ws_bytes, _ptr(d_rgb),
                                        _ptr(d_depth), _ptr(grads["means"]), _ptr(grads["log_scales"]),
                                        _ptr(grads["quats"]), _ptr(grads["opacity_logits"]), _ptr(grads["sh"]),
                                        _ptr(grads.get("cov3d")), _stream(stream)), "gs_render_backward")
@@ -483,6 +493,17 @@ def render_static_status(stream=None) -> int:
     v = ctypes.c_int32(0)
     _check(_lib.gs_render_static_status(_stream(stream), ctypes.byref(v)), "gs_render_static_status")
     return v.value
+
+
+def zero_gradients(grads: dict, n_ctas: int = 0, stream=None):
+    """gs_zero_gradients: sets the arrays of ``grads`` (means, log_scales, quats,
+    opacity_logits, sh, optional cov3d) to zero with TMA bulk stores from
+    ``n_ctas`` CTAs (0: one per two SMs), asynchronously on ``stream``."""
+    n = grads["means"].shape[0]
+    _check(_lib.gs_zero_gradients(n, _ptr(grads["means"]), _ptr(grads["log_scales"]), _ptr(grads["quats"]),
+                                  _ptr(grads["opacity_logits"]), _ptr(grads["sh"]), _ptr(grads.get("cov3d")),
+                                  int(n_ctas), _stream(stream)), "gs_zero_gradients")
+    return grads
 
 
 def deform(av: Avatars, G: torch.Tensor, out_means: torch.Tensor, out_cov3d: torch.Tensor, stream=None):

@@ -455,7 +455,9 @@ static gs_status enqueue_backward(const gs_gaussians *g, const gs_batch *batch, 
     if (d_cov3d && !aligned16(d_cov3d)) return GS_ERR_ALIGNMENT;
     if (workspace_bytes < p.total) return GS_ERR_WORKSPACE_TOO_SMALL;
     Ws w = ws_ptrs(workspace, p);
-    const bool overwrite = (cfg->flags & GS_FLAG_GRAD_OVERWRITE) != 0;
+    // pre-cleared arrays: the overwrite path without its clearing
+    const bool precleared = (cfg->flags & GS_FLAG_GRAD_PRECLEARED) != 0;
+    const bool overwrite = precleared || (cfg->flags & GS_FLAG_GRAD_OVERWRITE) != 0;
     GradOut o{d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_cov3d};
     Table t;
     fill_table(p, batch, cfg, sms, t);
@@ -471,7 +473,7 @@ static gs_status enqueue_backward(const gs_gaussians *g, const gs_batch *batch, 
         // overwrite mode: the blend backward also sets every gradient row to
         // zero, between its tiles; the preprocess backward writes the seen rows
         launch_blend_backward(cams, w, d_rgb, d_depth, p.n_bins, p.px, p.py, p.threads, p.B, sms,
-                              overwrite ? &o : nullptr, p.N, s);
+                              overwrite && !precleared ? &o : nullptr, p.N, s);
     }
     {
         Stage st8(8, s);
@@ -727,6 +729,23 @@ gs_status gs_deform_avatars_backward(const gs_avatars *av, const float *joint_G,
         launch_deform_backward(av, joint_G, d_means, d_cov3d, d_canon_means, d_canon_log_scales, d_canon_quats,
                                d_joint_G, static_cast<cudaStream_t>(stream));
     }
+    return check_launch();
+}
+
+gs_status gs_zero_gradients(int64_t n, float *d_means, float *d_log_scales, float *d_quats, float *d_opacity_logits,
+                            float *d_sh, float *d_cov3d, int32_t n_ctas, void *stream)
+{
+    if (n < 0 || !d_means || !d_log_scales || !d_quats || !d_opacity_logits || !d_sh) return GS_ERR_INVALID_ARG;
+    const void *ptrs[] = {d_means, d_log_scales, d_quats, d_opacity_logits, d_sh};
+    for (const void *q : ptrs)
+        if (!aligned16(q)) return GS_ERR_ALIGNMENT;
+    if (d_cov3d && !aligned16(d_cov3d)) return GS_ERR_ALIGNMENT;
+    if (n == 0) return GS_OK;
+    int sms = 0;
+    gs_status st = device_init(&sms);
+    if (st != GS_OK) return st;
+    GradOut o{d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, d_cov3d};
+    launch_zero_gradients(o, n, n_ctas > 0 ? n_ctas : (sms + 1) / 2, static_cast<cudaStream_t>(stream));
     return check_launch();
 }
 

@@ -1254,6 +1254,45 @@ static int blend_bwd_smem(int batch_depth, int q_warps)
     return ((base + 15) & ~15) + kZeroBuf;
 }
 
+// The clearing items of the gradient arrays of n Gaussians (none for NULL).
+static ZeroWork zero_work(const GradOut *clear, int64_t n)
+{
+    ZeroWork zw;
+    memset(&zw, 0, sizeof(zw));
+    if (!clear) return zw;
+    float *ps[kZeroArrays] = {clear->sh, clear->means, clear->ologits, clear->log_scales, clear->quats, clear->cov3d};
+    const int64_t ns[kZeroArrays] = {48 * n, 3 * n, n, 3 * n, 4 * n, clear->cov3d ? 6 * n : 0};
+    uint32_t acc = 0;
+    for (int a = 0; a < kZeroArrays; ++a) {
+        zw.p[a] = ps[a];
+        zw.n[a] = ps[a] ? ns[a] : 0;
+        zw.first[a] = acc;
+        acc += (uint32_t)((zw.n[a] + kZeroFloats - 1) / kZeroFloats);
+    }
+    zw.total = acc;
+    return zw;
+}
+
+// gs_zero_gradients: the same clearing items outside the blend backward, for
+// a stream beside the forward.  Each CTA zeroes its 4 KB source and takes the
+// items in turn.
+__global__ void __launch_bounds__(128) zero_gradients_kernel(ZeroWork zw)
+{
+    __shared__ __align__(16) float4 zbuf[kZeroBuf / 16];
+    for (int i = threadIdx.x; i < kZeroBuf / 16; i += blockDim.x) zbuf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); // visible to the bulk copies
+    __syncthreads();
+    const uint32_t saddr = (uint32_t)__cvta_generic_to_shared(zbuf);
+    for (uint32_t z = blockIdx.x; z < zw.total; z += gridDim.x) zero_item(zw, z, saddr);
+    if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+}
+
+void launch_zero_gradients(const GradOut &o, int64_t n, int n_ctas, cudaStream_t s)
+{
+    const ZeroWork zw = zero_work(&o, n);
+    if (zw.total) zero_gradients_kernel<<<(unsigned)std::min<uint32_t>((uint32_t)n_ctas, zw.total), 128, 0, s>>>(zw);
+}
+
 template <int PX, int PY>
 static void launch_bb(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,
                       int threads, int batch_depth, int n_sms, const ZeroWork &zw, cudaStream_t s)
@@ -1286,20 +1325,8 @@ void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rg
                            int px, int py, int threads, int batch_depth, int n_sms, const GradOut *clear, int64_t n,
                            cudaStream_t s)
 {
-    ZeroWork zw;
-    memset(&zw, 0, sizeof(zw));
+    ZeroWork zw = zero_work(clear, n);
     if (clear) {
-        float *ps[kZeroArrays] = {clear->sh, clear->means, clear->ologits, clear->log_scales, clear->quats,
-                                  clear->cov3d};
-        const int64_t ns[kZeroArrays] = {48 * n, 3 * n, n, 3 * n, 4 * n, clear->cov3d ? 6 * n : 0};
-        uint32_t acc = 0;
-        for (int a = 0; a < kZeroArrays; ++a) {
-            zw.p[a] = ps[a];
-            zw.n[a] = ps[a] ? ns[a] : 0;
-            zw.first[a] = acc;
-            acc += (uint32_t)((zw.n[a] + kZeroFloats - 1) / kZeroFloats);
-        }
-        zw.total = acc;
         zw.clear_ctas = (uint32_t)((n_sms + 1) / 2); // half the SMs: measured fastest (all SMs, twice that: slower)
     }
     if (px == 2 && py == 2) launch_bb<2, 2>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);

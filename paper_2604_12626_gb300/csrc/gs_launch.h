@@ -46,6 +46,8 @@ struct ZeroWork { // gradient arrays to clear and the first clearing item of eac
     uint32_t clear_ctas; // CTAs that clear before they take tiles (one per SM)
 };
 void launch_clear_record_grads(const Ws &w, int64_t n_records, int n_sms, cudaStream_t s);
+// gs_zero_gradients: the gradient arrays of n Gaussians set to zero by n_ctas CTAs
+void launch_zero_gradients(const GradOut &o, int64_t n, int n_ctas, cudaStream_t s);
 // clear: in overwrite mode the gradient arrays (n Gaussians) the blend backward
 // sets to zero between its tiles, else nullptr
 void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,

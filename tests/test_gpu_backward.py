@@ -316,3 +316,44 @@ def test_overwrite_mode_clears_unseen_rows(gs):
         assert np.all(a[1::2] == 0.0), k  # unseen rows cleared
         check_grad(a, b, f"overwrite {k}", 2e-5, 1e-5, 1e-9)
     assert float(ref["opacity_logits"].abs().sum()) > 0
+
+
+def test_precleared_mode_after_zero_gradients_on_a_side_stream(gs):
+    """gs_zero_gradients on a second stream beside the forward, joined by an
+    event, then the backward with GS_FLAG_GRAD_PRECLEARED: the overwrite mode's
+    result (buffers full of garbage before, unseen rows exactly zero), with
+    arrays ending off a 16-byte boundary (N = 4001)."""
+    n = 4001
+    g = synth.box_scene(n, seed=32)
+    g["means"][1::2, 2] = -g["means"][1::2, 2]  # every other Gaussian behind the camera: unseen
+    W = H = 64
+    cam = synth.identity_camera(W, H)
+    rng = np.random.default_rng(32)
+    d_rgb = torch.from_numpy(rng.standard_normal((1, 3, H, W))).float().cuda()
+    d_dep = torch.from_numpy(0.1 * rng.standard_normal((1, H, W))).float().cuda()
+    G = gs.Gaussians.from_numpy(g)
+    ct = gs.cameras_tensor(cam[None])
+    kw = dict(tile=(8, 8), batch_depth=64, pix=(2, 1), persistent=True)
+    ref_r = gs.Renderer(gs.Batch(np.array([0, n])), W, H, **kw)
+    ref_r.forward(G, ct)
+    ref = ref_r.backward(G, ct, d_rgb, d_dep)  # accumulate into zeros
+    r = gs.Renderer(gs.Batch(np.array([0, n])), W, H, grad_overwrite=True, **kw)
+    junk = dict(means=torch.full((n, 3), 7.0, device="cuda"), log_scales=torch.full((n, 3), -3.0, device="cuda"),
+                quats=torch.full((n, 4), 5.0, device="cuda"), opacity_logits=torch.full((n,), 9.0, device="cuda"),
+                sh=torch.full((n, 16, 3), 11.0, device="cuda"), cov3d=torch.full((n, 6), 2.0, device="cuda"))
+    main, side = torch.cuda.Stream(), torch.cuda.Stream()
+    main.wait_stream(torch.cuda.current_stream())
+    side.wait_stream(torch.cuda.current_stream())
+    gs.zero_gradients(junk, n_ctas=3, stream=side)
+    cleared = torch.cuda.Event()
+    cleared.record(side)
+    r.forward(G, ct, stream=main)
+    main.wait_event(cleared)
+    out = r.backward(G, ct, d_rgb, d_dep, grads=junk, stream=main, precleared=True)
+    torch.cuda.synchronize()
+    assert float(out["cov3d"].abs().max()) == 0.0  # no Gaussian takes cov3d: cleared, never written
+    for k in GROUPS:
+        a, b = out[k].cpu().numpy(), ref[k].cpu().numpy()
+        assert np.all(a[1::2] == 0.0), k
+        check_grad(a, b, f"precleared {k}", 2e-5, 1e-5, 1e-9)
+    assert float(ref["opacity_logits"].abs().sum()) > 0

@@ -387,7 +387,7 @@ gs_status enqueue_forward(const gs_gaussians *g, const gs_batch *b, const gs_cam
     const bool persistent = (p.flags & GS_FLAG_PERSISTENT) != 0;
     {
         Stage st6(6, s);
-        launch_blend(cams, w, rgb, depth, T, ncontrib, p.n_bins, p.px, p.py, p.threads, p.B, persistent,
+        launch_blend(t, cams, w, rgb, depth, T, ncontrib, p.n_bins, p.px, p.py, p.threads, p.B, persistent,
                      (p.flags & GS_FLAG_COUNT_EVALS) != 0, sms, s);
     }
     return check_launch();

@@ -1424,14 +1424,17 @@ __device__ __forceinline__ void blend_persistent(const gs_camera *cams, const Ws
 }
 
 template <int PX, int PY, bool COUNT>
-__global__ void blend_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
+__global__ void blend_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o, const __grid_constant__ Table tbp)
 {
+    w.tb = const_cast<Table *>(&tbp); // the table from the constant bank (see the preprocess)
     blend_one<PX, PY, COUNT>(cams, w, o);
 }
 
 template <int PX, int PY, bool COUNT>
-__global__ void blend_persistent_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
+__global__ void blend_persistent_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o,
+                                        const __grid_constant__ Table tbp)
 {
+    w.tb = const_cast<Table *>(&tbp); // the table from the constant bank (see the preprocess)
     blend_persistent<PX, PY, COUNT>(cams, w, o);
 }
 
@@ -1445,8 +1448,10 @@ __device__ __forceinline__ void blendq_smem(float4 *smem, int B, int nwarps, uin
 }
 
 template <bool COUNT>
-__global__ void __launch_bounds__(256) blendq_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
+__global__ void __launch_bounds__(256) blendq_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o,
+                                                     const __grid_constant__ Table tbp)
 {
+    w.tb = const_cast<Table *>(&tbp); // the table from the constant bank (see the preprocess)
     extern __shared__ float4 smem_f4[];
     const int B = w.tb->batch_depth;
     uint8_t *qls;
@@ -1457,8 +1462,10 @@ __global__ void __launch_bounds__(256) blendq_kernel(const gs_camera *__restrict
 }
 
 template <bool COUNT>
-__global__ void __launch_bounds__(256) blendq_persistent_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o)
+__global__ void __launch_bounds__(256) blendq_persistent_kernel(const gs_camera *__restrict__ cams, Ws w, OutPtrs o,
+                                                                const __grid_constant__ Table tbp)
 {
+    w.tb = const_cast<Table *>(&tbp); // the table from the constant bank (see the preprocess)
     extern __shared__ float4 smem_f4[];
     __shared__ uint32_t item;
     const int B = w.tb->batch_depth;
@@ -1557,8 +1564,8 @@ int blend_smem_bytes(int batch_depth, int q_warps)
 }
 
 template <int PX, int PY, bool COUNT>
-static void launch_blend_c(const gs_camera *cams, const Ws &w, const OutPtrs &o, int n_bins, int threads,
-                           int batch_depth, bool persistent, int n_sms, cudaStream_t s)
+static void launch_blend_c(const Table &tb, const gs_camera *cams, const Ws &w, const OutPtrs &o, int n_bins,
+                           int threads, int batch_depth, bool persistent, int n_sms, cudaStream_t s)
 {
     const int smem = blend_smem_bytes(batch_depth, PX == 2 && PY == 1 ? threads / 32 : 0);
     using K = BlendKernels<PX, PY, COUNT>;
@@ -1567,18 +1574,18 @@ static void launch_blend_c(const gs_camera *cams, const Ws &w, const OutPtrs &o,
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, K::persistent, threads, smem);
         int grid = n_sms * (nb > 0 ? nb : 1);
         if (grid > n_bins) grid = n_bins;
-        K::persistent<<<grid, threads, smem, s>>>(cams, w, o);
+        K::persistent<<<grid, threads, smem, s>>>(cams, w, o, tb);
     } else {
-        K::one<<<n_bins, threads, smem, s>>>(cams, w, o);
+        K::one<<<n_bins, threads, smem, s>>>(cams, w, o, tb);
     }
 }
 
 template <int PX, int PY>
-static void launch_blend_t(const gs_camera *cams, const Ws &w, const OutPtrs &o, int n_bins, int threads,
-                           int batch_depth, bool persistent, bool count, int n_sms, cudaStream_t s)
+static void launch_blend_t(const Table &tb, const gs_camera *cams, const Ws &w, const OutPtrs &o, int n_bins,
+                           int threads, int batch_depth, bool persistent, bool count, int n_sms, cudaStream_t s)
 {
-    if (count) launch_blend_c<PX, PY, true>(cams, w, o, n_bins, threads, batch_depth, persistent, n_sms, s);
-    else launch_blend_c<PX, PY, false>(cams, w, o, n_bins, threads, batch_depth, persistent, n_sms, s);
+    if (count) launch_blend_c<PX, PY, true>(tb, cams, w, o, n_bins, threads, batch_depth, persistent, n_sms, s);
+    else launch_blend_c<PX, PY, false>(tb, cams, w, o, n_bins, threads, batch_depth, persistent, n_sms, s);
 }
 
 template <int PX, int PY>
@@ -1605,15 +1612,15 @@ int blend_thread_limit(int px, int py)
     return blend_limit_t<1, 1>();
 }
 
-void launch_blend(const gs_camera *cams, const Ws &w, float *rgb, float *depth, float *T, int32_t *ncontrib,
-                  int n_bins, int px, int py, int threads, int batch_depth, bool persistent, bool count, int n_sms,
-                  cudaStream_t s)
+void launch_blend(const Table &tb, const gs_camera *cams, const Ws &w, float *rgb, float *depth, float *T,
+                  int32_t *ncontrib, int n_bins, int px, int py, int threads, int batch_depth, bool persistent,
+                  bool count, int n_sms, cudaStream_t s)
 {
     OutPtrs o{rgb, depth, T, ncontrib};
-    if (px == 2 && py == 2) launch_blend_t<2, 2>(cams, w, o, n_bins, threads, batch_depth, persistent, count, n_sms, s);
-    else if (px == 2) launch_blend_t<2, 1>(cams, w, o, n_bins, threads, batch_depth, persistent, count, n_sms, s);
-    else if (py == 2) launch_blend_t<1, 2>(cams, w, o, n_bins, threads, batch_depth, persistent, count, n_sms, s);
-    else launch_blend_t<1, 1>(cams, w, o, n_bins, threads, batch_depth, persistent, count, n_sms, s);
+    if (px == 2 && py == 2) launch_blend_t<2, 2>(tb, cams, w, o, n_bins, threads, batch_depth, persistent, count, n_sms, s);
+    else if (px == 2) launch_blend_t<2, 1>(tb, cams, w, o, n_bins, threads, batch_depth, persistent, count, n_sms, s);
+    else if (py == 2) launch_blend_t<1, 2>(tb, cams, w, o, n_bins, threads, batch_depth, persistent, count, n_sms, s);
+    else launch_blend_t<1, 1>(tb, cams, w, o, n_bins, threads, batch_depth, persistent, count, n_sms, s);
 }
 
 cudaError_t configure_forward_kernels()

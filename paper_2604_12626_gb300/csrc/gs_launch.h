@@ -24,9 +24,9 @@ int merge_passes_for_capacity(int64_t pair_capacity);
 void launch_sort_chunks(const Ws &w, int n_sms, cudaStream_t s);
 void launch_merge_passes(const Ws &w, int n_passes, int n_sms, cudaStream_t s);
 // count: the GS_FLAG_COUNT_EVALS variant (evaluation counters in the header)
-void launch_blend(const gs_camera *cams, const Ws &w, float *rgb, float *depth, float *T, int32_t *ncontrib,
-                  int n_bins, int px, int py, int threads, int batch_depth, bool persistent, bool count, int n_sms,
-                  cudaStream_t s);
+void launch_blend(const Table &tb, const gs_camera *cams, const Ws &w, float *rgb, float *depth, float *T,
+                  int32_t *ncontrib, int n_bins, int px, int py, int threads, int batch_depth, bool persistent,
+                  bool count, int n_sms, cudaStream_t s);
 // Largest CTA (threads) the blend kernels of this pixels-per-thread variant can
 // launch with (register-limited), forward and backward.
 int blend_thread_limit(int px, int py);

@@ -667,8 +667,7 @@ __device__ __forceinline__ void blendq_backward_tile(const Ws &w, const gs_camer
                 const int ks = kk[u] < 0 ? 0 : kk[u];
                 const float4 qv = s1[ks];
                 const float4 c = s2[ks];
-                if (!(ok[u][0] || ok[u][1])) continue;
-                contrib = true;
+                contrib = contrib || ok[u][0] || ok[u][1]; // branch-free: a lane that blends neither pixel adds zeros
                 const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y), cz = make_float2(c.z, c.z),
                              az = make_float2(c.w, c.w);
                 const float2 qx = make_float2(qv.x, qv.x), qy = make_float2(qv.y, qv.y);

@@ -620,6 +620,10 @@ __device__ __forceinline__ void blendq_backward_tile(const Ws &w, const gs_camer
         const int maxlen = max(max(len[0], len[1]), max(len[2], len[3]));
         const uint8_t *myl = ql + q * qs;
         const float4 *s0 = sm + (b & 1) * 3 * B, *s1 = s0 + B, *s2 = s0 + 2 * B;
+        // the slot a lane past its list's end reads: a gathered record, so that
+        // the branch-free gradient phase multiplies finite values by its zero
+        // weights (the slots of pairs no pixel blended hold stale data)
+        const int ksafe = ncl > 0 ? (int)clist[0] : 0;
         // groups of kGroup entries per quarter, back to front: falloff and
         // alpha first (independent of T), then the sequential transmittance
         // rebuild and gradients, then one quarter reduction of the group's
@@ -636,7 +640,7 @@ __device__ __forceinline__ void blendq_backward_tile(const Ws &w, const gs_camer
             bool ok[kGroup][2];
 #pragma unroll
             for (int u = 0; u < kGroup; ++u) {
-                const int k = kk[u], ks = k < 0 ? 0 : k;
+                const int k = kk[u], ks = k < 0 ? ksafe : k;
                 const float4 a = s0[ks];
                 const float4 qv = s1[ks];
                 const float dy = __fsub_rn(a.y, pyc);
@@ -664,7 +668,7 @@ __device__ __forceinline__ void blendq_backward_tile(const Ws &w, const gs_camer
                 for (int x = 0; x < 10; ++x) G[u][x] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int u = 0; u < kGroup; ++u) {
-                const int ks = kk[u] < 0 ? 0 : kk[u];
+                const int ks = kk[u] < 0 ? ksafe : kk[u];
                 const float4 qv = s1[ks];
                 const float4 c = s2[ks];
                 contrib = contrib || ok[u][0] || ok[u][1]; // branch-free: a lane that blends neither pixel adds zeros

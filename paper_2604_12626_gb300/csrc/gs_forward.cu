@@ -683,8 +683,8 @@ __global__ void __launch_bounds__(1024) scan_bins_kernel(Ws w)
 // scatter: one key per (visible record, touched tile)
 // ---------------------------------------------------------------------------
 // hist_words: the preprocess's (view, tile) counter count; the shared memory
-// holds that many slots and one chunk of record indices (3 CTAs per SM at
-// 16384-Gaussian chunks and 2 KB of counters)
+// holds that many slots and one chunk of record indices (the registers allow
+// 3 CTAs per SM)
 __global__ void __launch_bounds__(256, 3) scatter_kernel(const gs_camera *__restrict__ cams, Ws w, int hist_words)
 {
     extern __shared__ uint32_t smem_sc[];

@@ -140,7 +140,7 @@ __host__ __device__ __forceinline__ int qlist_stride(int B) { return (B + 15) & 
 constexpr int kSeg = 2048;       // backward segment of a heavy bin (a multiple of every batch depth)
 constexpr int kHeavyMin = 1024;  // pairs from which a bin may be scheduled first
 constexpr int kHeavyCap = 4096;  // entries of the heavy-first list
-constexpr int kChunkMax = 16384; // Gaussians per preprocess / scatter CTA, at most
+constexpr int kChunkMax = 8192; // Gaussians per preprocess / scatter CTA, at most
 constexpr int kChunkMin = 1024;
 constexpr int kHistCap = 8192;   // (view, tile) counters a chunk keeps in shared memory
 

@@ -1331,11 +1331,11 @@ __device__ __forceinline__ void blendq_tile(const Ws &w, const gs_camera *cams, 
             qm |= __shfl_xor_sync(0xffffffffu, qm, 1);
             qm |= __shfl_xor_sync(0xffffffffu, qm, 2);
             qm |= __shfl_xor_sync(0xffffffffu, qm, 4);
-            if (m == 0 && qm) {
+            // lane m of the quarter records entry m (the quarter's 8 lanes hold the same idx[])
+            int my_idx = idx[0];
 #pragma unroll
-                for (int u = 0; u < kUnroll; ++u)
-                    if ((qm >> u) & 1u) atomicOr(wb + idx[u], 1u << q);
-            }
+            for (int u = 1; u < kUnroll; ++u) my_idx = m == u ? idx[u] : my_idx;
+            if ((qm >> m) & 1u) atomicOr(wb + my_idx, 1u << q);
         }
         __syncthreads();
         // per batch entry: the quarters of every warp that blended it, and the

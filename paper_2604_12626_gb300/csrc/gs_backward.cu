@@ -742,6 +742,355 @@ __device__ __forceinline__ void blendq_backward_tile(const Ws &w, const gs_camer
     cp_async_wait<0>();
 }
 
+// Sums v[0..19] over each 4-lane group of the warp with 15 shuffles
+// (butterfly transpose over lane bits 2, 1): on return, lane 4g + m holds in
+// v[0..4] the group's totals of v[5m .. 5m + 4].
+__device__ __forceinline__ void quad_transpose_sum20(float (&v)[20])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 2, m = 20; o > 0; o >>= 1, m >>= 1) {
+        const bool up = lane & o;
+#pragma unroll
+        for (int i = 0; i < m / 2; ++i) {
+            const float keep = up ? v[i + m / 2] : v[i], send = up ? v[i] : v[i + m / 2];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+}
+
+constexpr int kGroup4 = 2; // entries per 4-lane reduction (20 sums)
+// Batch depth of the 4-lane walk, whatever the forward's: one-warp CTAs need
+// small batch buffers to keep 16 warps per SM (measured: 64 against 128,
+// 3.72 against 4.54 ms at 64 envs); the backward's batches are its own.
+constexpr int kQ4Batch = 64;
+
+// The quarter walk with 2 x 2 pixels per lane: the tile's 4 x 4 quarters of
+// the forward (four per forward warp) walked by 4 lanes each, eight per warp,
+// so one warp takes the quarters of two forward warps.  Same lists, same
+// per-pixel arithmetic as blendq_backward_tile; the gradient sums of a group
+// are reduced over 4 lanes instead of 8 (a quarter of the shuffles per pixel).
+__device__ __forceinline__ void blendq4_backward_tile(const Ws &w, const gs_camera *cams, const float *d_rgb,
+                                                     const float *d_depth, int bin, uint32_t seg_lo, uint32_t seg_hi,
+                                                     int64_t ck_slot, float4 *sm, float *acc, uint32_t *sidx,
+                                                     uint32_t *clist, uint32_t *spq, uint8_t *qls,
+                                                     uint32_t *smax_last)
+{
+    const Table *tb = w.tb;
+    const int B = min(tb->batch_depth, kQ4Batch);
+    const int nthr = blockDim.x;
+    const int v = bin / tb->tiles_per_view;
+    const int t = bin - v * tb->tiles_per_view;
+    const int tyi = t / tb->tiles_x, txi = t - tyi * tb->tiles_x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int Q = lane >> 2, m = lane & 3;  // quarter of the warp (0..7), lane in it
+    const int fw = 2 * warp + (Q >> 2), qq = Q & 3; // the forward warp and its quarter
+    const int wx = tb->tile_w >> 3;
+    const int tx0 = txi * tb->tile_w, ty0 = tyi * tb->tile_h;
+    const int i0 = tx0 + (fw % wx) * 8 + (qq & 1) * 4 + (m & 1) * 2;
+    const int j0 = ty0 + (fw / wx) * 8 + (qq >> 1) * 4 + (m >> 1) * 2;
+    const int W = tb->W, H = tb->H;
+    const gs_camera &cam = cams[v];
+    const float pyc[2] = {pix_c(j0, cam.cy), pix_c(j0 + 1, cam.cy)};
+    const float2 npx2 = make_float2(-pix_c(i0, cam.cx), -pix_c(i0 + 1, cam.cx));
+    const size_t HW = (size_t)W * H;
+    uint32_t start, n;
+    bin_range(w, bin, start, n);
+    const unsigned long long *keys = w.keys + start;
+    const uint32_t *pqb = w.pq + start;
+    const uint32_t R = (uint32_t)tb->n_records;
+    const int qs = qlist_stride(B);
+    uint8_t *ql = qls + warp * 8 * qs;
+
+    // per pixel (row r, column p): T, dL/dC, dL/dD, the colour and depth behind
+    float T[2][2], dC0[2][2], dC1[2][2], dC2[2][2], dD[2][2], S0[2][2], S1[2][2], S2[2][2], SD[2][2];
+    uint32_t last[2][2];
+    uint32_t tlast = 0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const int i = i0 + p, j = j0 + r;
+            T[r][p] = 1.0f; dC0[r][p] = dC1[r][p] = dC2[r][p] = dD[r][p] = 0.f;
+            S0[r][p] = S1[r][p] = S2[r][p] = SD[r][p] = 0.f;
+            last[r][p] = 0;
+            if (i < W && j < H) {
+                const size_t px = (size_t)j * W + i;
+                T[r][p] = w.pix_T[(size_t)v * HW + px];
+                last[r][p] = w.pix_last[(size_t)v * HW + px];
+                dC0[r][p] = d_rgb[(3 * (size_t)v + 0) * HW + px];
+                dC1[r][p] = d_rgb[(3 * (size_t)v + 1) * HW + px];
+                dC2[r][p] = d_rgb[(3 * (size_t)v + 2) * HW + px];
+                dD[r][p] = d_depth[(size_t)v * HW + px];
+                S0[r][p] = T[r][p] * tb->bg[0];
+                S1[r][p] = T[r][p] * tb->bg[1];
+                S2[r][p] = T[r][p] * tb->bg[2];
+            }
+            tlast = max(tlast, last[r][p]);
+        }
+    if (threadIdx.x == 0) *smax_last = 0;
+    __syncthreads();
+    const uint32_t wl = __reduce_max_sync(0xffffffffu, tlast);
+    if (lane == 0) atomicMax(smax_last, wl);
+    __syncthreads();
+    const uint32_t tile_last = min(*smax_last, n);
+    if (seg_lo >= tile_last) return; // nothing blended in this segment
+    const uint32_t n_proc = min(tile_last, seg_hi);
+    if (n_proc < tile_last) {
+        // start from the checkpoint before position seg_hi
+        const int tpx = tb->tile_w * tb->tile_h;
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const int i = i0 + p, j = j0 + r;
+                if (i < W && j < H) {
+                    const int lpx = (j - ty0) * tb->tile_w + (i - tx0);
+                    const float4 ck = w.ck_C[(size_t)ck_slot * tpx + lpx];
+                    const float ckd = w.ck_D[(size_t)ck_slot * tpx + lpx];
+                    const float4 fin = w.pix_C[(size_t)v * HW + (size_t)j * W + i];
+                    T[r][p] = ck.x;
+                    S0[r][p] = fin.x - ck.y;
+                    S1[r][p] = fin.y - ck.z;
+                    S2[r][p] = fin.z - ck.w;
+                    SD[r][p] = fin.w - ckd;
+                }
+            }
+    }
+    // per row, both pixels as packed FP32 pairs (as blendq_backward_tile)
+    float2 T2[2], dc0[2], dc1[2], dc2[2], dd[2], ndcs[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        T2[r] = make_float2(T[r][0], T[r][1]);
+        dc0[r] = make_float2(dC0[r][0], dC0[r][1]);
+        dc1[r] = make_float2(dC1[r][0], dC1[r][1]);
+        dc2[r] = make_float2(dC2[r][0], dC2[r][1]);
+        dd[r] = make_float2(dD[r][0], dD[r][1]);
+        float x[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+            x[e] = -(dC0[r][e] * S0[r][e] + dC1[r][e] * S1[r][e] + dC2[r][e] * S2[r][e] + dD[r][e] * SD[r][e]);
+        ndcs[r] = make_float2(x[0], x[1]);
+    }
+    const int nb = (int)((n_proc - seg_lo + B - 1) / B);
+    // batch b covers [lo_b, hi_b), hi_b = n_proc - b B, lo_b >= seg_lo
+    auto lo_of = [&](int b) {
+        const int32_t x = (int32_t)n_proc - (b + 1) * B;
+        return x < (int32_t)seg_lo ? (int32_t)seg_lo : x;
+    };
+    auto hi_of = [&](int b) { return (int32_t)n_proc - b * B; };
+    unsigned long long kr[kMaxPerB];
+    auto load_keys = [&](int b) {
+        const int32_t lo = lo_of(b), cnt = hi_of(b) - lo;
+#pragma unroll
+        for (int qq2 = 0; qq2 < kMaxPerB; ++qq2) {
+            const int e = threadIdx.x + qq2 * nthr;
+            kr[qq2] = (b < nb && e < cnt) ? keys[lo + e] : 0ull;
+        }
+    };
+    auto issue = [&](int b) {
+        float4 *buf = sm + (b & 1) * 3 * B;
+        uint32_t *ib = sidx + (b & 1) * B;
+        uint32_t *pb = spq + (b & 1) * B;
+        const int32_t lo = lo_of(b), cnt = hi_of(b) - lo;
+#pragma unroll
+        for (int qq2 = 0; qq2 < kMaxPerB; ++qq2) {
+            const int e = threadIdx.x + qq2 * nthr;
+            if (e < cnt) {
+                const uint32_t word = (uint32_t)kr[qq2], fl = word & kKeyBlended;
+                uint32_t rec = word & kKeyRecord;
+                if (rec >= R) rec = 0; // only after a capacity overflow
+                if (fl) { // pairs that no pixel blended are never read
+                    const float4 *src = w.rec + 3 * (size_t)rec;
+                    cp_async16(buf + e, src);
+                    cp_async16(buf + B + e, src + 1);
+                    cp_async16(buf + 2 * B + e, src + 2);
+                    pb[e] = pqb[lo + e];
+                }
+                ib[e] = rec | fl;
+            }
+        }
+    };
+    if (nb > 0) {
+        load_keys(0);
+        issue(0);
+        cp_async_commit();
+        load_keys(1);
+    }
+    const unsigned lt = (1u << lane) - 1u;
+    for (int b = 0; b < nb; ++b) {
+        if (b + 1 < nb) issue(b + 1);
+        cp_async_commit();
+        if (b + 2 < nb) load_keys(b + 2);
+        const int32_t lo = lo_of(b), cnt = hi_of(b) - lo;
+        for (int k = threadIdx.x; k < cnt * kAccStride; k += nthr) acc[k] = 0.0f;
+        cp_async_wait<1>();
+        __syncthreads();
+        const uint32_t *ibc = sidx + (b & 1) * B;
+        const uint32_t *pbc = spq + (b & 1) * B;
+        if (threadIdx.x < 32) { // the batch's blended entries, in list order
+            uint32_t base = 0;
+            for (int c0 = 0; c0 < cnt; c0 += 32) {
+                const int k = c0 + lane;
+                const bool f = k < cnt && (ibc[k] & kKeyBlended);
+                const unsigned bal = __ballot_sync(0xffffffffu, f);
+                if (f) clist[base + __popc(bal & lt)] = (uint32_t)k;
+                base += __popc(bal);
+            }
+            if (lane == 0) clist[B] = base;
+        }
+        __syncthreads();
+        const int ncl = (int)clist[B];
+        // this warp's eight quarter lists: bytes 2 warp and 2 warp + 1 of the
+        // forward's per-warp quarter bits
+        int len[8];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) len[x] = 0;
+        for (int c0 = 0; c0 < ncl; c0 += 32) {
+            const int i = c0 + lane;
+            const uint32_t k = i < ncl ? clist[i] : 0u;
+            const uint32_t word = i < ncl ? pbc[k] >> (16 * warp) : 0u;
+            const uint32_t qb = (word & 15u) | ((word >> 4) & 0xf0u);
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+                const bool hit = (qb >> x) & 1u;
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                if (hit) ql[x * qs + len[x] + __popc(bal & lt)] = (uint8_t)k;
+                len[x] += __popc(bal);
+            }
+        }
+        __syncwarp();
+        int mylen = len[0], maxlen = len[0];
+#pragma unroll
+        for (int x = 1; x < 8; ++x) {
+            mylen = Q == x ? len[x] : mylen;
+            maxlen = max(maxlen, len[x]);
+        }
+        const uint8_t *myl = ql + Q * qs;
+        const float4 *s0 = sm + (b & 1) * 3 * B, *s1 = s0 + B, *s2 = s0 + 2 * B;
+        // the slot a lane past its list's end reads: a gathered record, so that
+        // the branch-free gradient phase multiplies finite values by its zero
+        // weights (the slots of pairs no pixel blended hold stale data)
+        const int ksafe = ncl > 0 ? (int)clist[0] : 0;
+        // groups of kGroup4 entries per quarter, back to front: falloff and
+        // alpha of the lane's four pixels first, then per row the sequential
+        // transmittance rebuild and gradients (branch-free), then one 4-lane
+        // reduction of the group's 10 x kGroup4 sums
+        for (int s = 0; s < maxlen; s += kGroup4) {
+            int kk[kGroup4]; // batch entries of the group (-1: past this quarter's list)
+#pragma unroll
+            for (int u = 0; u < kGroup4; ++u) kk[u] = s + u < mylen ? (int)myl[mylen - 1 - s - u] : -1;
+            float g[20];
+#pragma unroll
+            for (int x = 0; x < 20; ++x) g[x] = 0.f;
+            bool contrib = false;
+            float ar[kGroup4][2][2], ex[kGroup4][2][2], dxs[kGroup4][2], dys[kGroup4][2];
+            bool ok[kGroup4][2][2];
+#pragma unroll
+            for (int u = 0; u < kGroup4; ++u) {
+                const int k = kk[u], ks = k < 0 ? ksafe : k;
+                const float4 a = s0[ks];
+                const float4 qv = s1[ks];
+                const float2 dx2 = __fadd2_rn(make_float2(a.x, a.x), npx2); // = a.x - pxc
+                dxs[u][0] = dx2.x;
+                dxs[u][1] = dx2.y;
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const float dy = __fsub_rn(a.y, pyc[r]);
+                    dys[u][r] = dy;
+                    const float2 p2 = gauss_power2(qv.x, qv.y, qv.z, dx2, dy);
+                    const float pw[2] = {p2.x, p2.y};
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        ex[u][r][p] = __expf(pw[p]);
+                        ar[u][r][p] = __fmul_rn(qv.w, ex[u][r][p]); // = raw_alpha(qv.w, power)
+                        ok[u][r][p] = k >= 0 && (uint32_t)(lo + k) < last[r][p] && fabsf(dxs[u][p]) <= a.z &&
+                                      fabsf(dy) <= a.w && pw[p] <= 0.0f && fminf(kAlphaMax, ar[u][r][p]) >= kAlphaMin;
+                        if (!ok[u][r][p]) ex[u][r][p] = 0.f; // finite where a zero weight multiplies it
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kGroup4; ++u) {
+                const int ks = kk[u] < 0 ? ksafe : kk[u];
+                const float4 qv = s1[ks];
+                const float4 c = s2[ks];
+                const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y), cz = make_float2(c.z, c.z),
+                             az = make_float2(c.w, c.w);
+                const float2 qx = make_float2(qv.x, qv.x), qy = make_float2(qv.y, qv.y);
+                const float2 dx = make_float2(dxs[u][0], dxs[u][1]);
+                float2 Gs[10];
+#pragma unroll
+                for (int x = 0; x < 10; ++x) Gs[x] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    contrib = contrib || ok[u][r][0] || ok[u][r][1];
+                    const float2 nal = make_float2(ok[u][r][0] ? -fminf(kAlphaMax, ar[u][r][0]) : 0.f,
+                                                   ok[u][r][1] ? -fminf(kAlphaMax, ar[u][r][1]) : 0.f);
+                    const float2 om = __fadd2_rn(make_float2(1.f, 1.f), nal);
+                    const float2 iom = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
+                    const float2 Ti = __fmul2_rn(T2[r], iom);
+                    const float2 nwgt = __fmul2_rn(nal, Ti);
+                    Gs[6] = __ffma2_rn(nwgt, dc0[r], Gs[6]);
+                    Gs[7] = __ffma2_rn(nwgt, dc1[r], Gs[7]);
+                    Gs[8] = __ffma2_rn(nwgt, dc2[r], Gs[8]);
+                    Gs[9] = __ffma2_rn(nwgt, dd[r], Gs[9]);
+                    const float2 dcc =
+                        __ffma2_rn(dd[r], az, __ffma2_rn(dc2[r], cz, __ffma2_rn(dc1[r], cy, __fmul2_rn(dc0[r], cx))));
+                    const float2 dal = __ffma2_rn(ndcs[r], iom, __fmul2_rn(dcc, Ti));
+                    ndcs[r] = __ffma2_rn(nwgt, dcc, ndcs[r]);
+                    T2[r] = Ti;
+                    // the 0.99 clamp passes no gradient to opacity and footprint
+                    const float2 dalm = make_float2(ar[u][r][0] < kAlphaMax ? dal.x : 0.f,
+                                                    ar[u][r][1] < kAlphaMax ? dal.y : 0.f);
+                    const float dy1 = dys[u][r];
+                    Gs[5] = __ffma2_rn(dalm, make_float2(ex[u][r][0], ex[u][r][1]), Gs[5]);
+                    const float2 ngp = __fmul2_rn(dalm, nal); // -dL/dalpha * alpha
+                    // w = Q d (Q the conic): dpower/dd = -w and dpower/dSigma2 = w w^T / 2
+                    const float qyd = qv.y * dy1, qzd = qv.z * dy1;
+                    const float2 wxv = __ffma2_rn(qx, dx, make_float2(qyd, qyd));
+                    const float2 wyv = __ffma2_rn(qy, dx, make_float2(qzd, qzd));
+                    Gs[0] = __ffma2_rn(ngp, wxv, Gs[0]);
+                    Gs[1] = __ffma2_rn(ngp, wyv, Gs[1]);
+                    const float2 nhw = __fmul2_rn(__fmul2_rn(ngp, make_float2(-0.5f, -0.5f)), wxv);
+                    Gs[2] = __ffma2_rn(nhw, wxv, Gs[2]);
+                    Gs[3] = __ffma2_rn(nhw, wyv, Gs[3]);
+                    Gs[4] = __ffma2_rn(__fmul2_rn(__fmul2_rn(ngp, make_float2(-0.5f, -0.5f)), wyv), wyv, Gs[4]);
+                }
+#pragma unroll
+                for (int x = 0; x < 6; ++x) g[10 * u + x] = Gs[x].x + Gs[x].y;
+#pragma unroll
+                for (int x = 6; x < 10; ++x) g[10 * u + x] = -(Gs[x].x + Gs[x].y);
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+                quad_transpose_sum20(g);
+                // lane 4Q + m holds the quarter's sums of g[5 m .. 5 m + 4]
+#pragma unroll
+                for (int j = 0; j < 5; ++j) {
+                    const int x = 5 * m + j, u = x / 10, comp = x - 10 * u;
+                    const int k = u == 0 ? kk[0] : kk[1];
+                    if (k >= 0 && g[j] != 0.0f) atomicAdd(acc + k * kAccStride + comp, g[j]);
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < ncl; i += nthr) {
+            const int k = (int)clist[i];
+            const float4 *ak = reinterpret_cast<const float4 *>(acc + k * kAccStride);
+            const float4 x0 = ak[0], x1 = ak[1], x2 = ak[2];
+            if (x0.x != 0.f || x0.y != 0.f || x0.z != 0.f || x0.w != 0.f || x1.x != 0.f || x1.y != 0.f ||
+                x1.z != 0.f || x1.w != 0.f || x2.x != 0.f || x2.y != 0.f) {
+                float4 *dst = reinterpret_cast<float4 *>(w.d_rec + (size_t)(ibc[k] & kKeyRecord) * kGradStride);
+                atomicAdd(dst + 0, x0);
+                atomicAdd(dst + 1, x1);
+                atomicAdd(dst + 2, x2);
+            }
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+}
+
 // Overwrite mode: every gradient row is first set to zero (the preprocess
 // backward then writes the rows of the Gaussians some view sees).  The clearing
 // is split into items of kZeroFloats floats that the persistent blend-backward
@@ -786,20 +1135,22 @@ __device__ __noinline__ void zero_item(const ZeroWork &zw, uint32_t z, uint32_t 
     }
 }
 
-template <int PX, int PY>
+// Q4: 2 x 1 pixels per lane in the forward, 2 x 2 in the backward
+// (blendq4_backward_tile; the CTA has half the forward's threads)
+template <int PX, int PY, bool Q4>
 __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, const float *__restrict__ d_rgb,
                                       const float *__restrict__ d_depth, ZeroWork zw)
 {
     extern __shared__ float4 smem_b[];
     __shared__ uint32_t smax_last, item;
     constexpr bool Q = PX == 2 && PY == 1; // quarter lists (blendq_backward_tile)
-    const int B = w.tb->batch_depth;
+    const int B = Q4 ? min(w.tb->batch_depth, kQ4Batch) : w.tb->batch_depth;
     float *acc = reinterpret_cast<float *>(smem_b + 2 * 3 * B); // [B][kAccStride]
     uint32_t *sidx = reinterpret_cast<uint32_t *>(acc + B * kAccStride); // [2][B]
     uint32_t *clist = sidx + 2 * B;                                        // [B + 1]
     uint32_t *spq = clist + B + 1;                                         // Q: [2][B] quarter bits
     uint8_t *qls = reinterpret_cast<uint8_t *>(spq + (Q ? 2 * B : 0));     // Q: per warp 4 quarter lists
-    const int qbytes = Q ? (int)(blockDim.x >> 5) * 4 * qlist_stride(B) : 0;
+    const int qbytes = Q ? (int)(blockDim.x >> 5) * (Q4 ? 8 : 4) * qlist_stride(B) : 0;
     // zeros for the clearing items' bulk copies (16-byte aligned, after the lists)
     const uint32_t zoff = ((uint32_t)(reinterpret_cast<char *>(qls + qbytes) - reinterpret_cast<char *>(smem_b)) +
                            15u) & ~15u;
@@ -837,7 +1188,10 @@ __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, 
                 else hi = mid - 1;
             }
             const uint32_t s = item - w.heavy_seg[lo];
-            if constexpr (Q)
+            if constexpr (Q4)
+                blendq4_backward_tile(w, cams, d_rgb, d_depth, (int)w.heavy[lo], s * kSeg, (s + 1) * kSeg,
+                                      (int64_t)w.heavy_seg[lo] + s, smem_b, acc, sidx, clist, spq, qls, &smax_last);
+            else if constexpr (Q)
                 blendq_backward_tile(w, cams, d_rgb, d_depth, (int)w.heavy[lo], s * kSeg, (s + 1) * kSeg,
                                      (int64_t)w.heavy_seg[lo] + s, smem_b, acc, sidx, clist, spq, qls, &smax_last);
             else
@@ -846,7 +1200,10 @@ __global__ void blend_backward_kernel(const gs_camera *__restrict__ cams, Ws w, 
         } else {
             const uint32_t b = item - nhi;
             if (w.bin_count[b] + w.bin_fcount[b] < w.hdr->heavy_min) {
-                if constexpr (Q)
+                if constexpr (Q4)
+                    blendq4_backward_tile(w, cams, d_rgb, d_depth, (int)b, 0u, 0xffffffffu, 0, smem_b, acc, sidx,
+                                          clist, spq, qls, &smax_last);
+                else if constexpr (Q)
                     blendq_backward_tile(w, cams, d_rgb, d_depth, (int)b, 0u, 0xffffffffu, 0, smem_b, acc, sidx,
                                          clist, spq, qls, &smax_last);
                 else
@@ -1296,23 +1653,26 @@ void launch_zero_gradients(const GradOut &o, int64_t n, int n_ctas, cudaStream_t
     if (zw.total) zero_gradients_kernel<<<(unsigned)std::min<uint32_t>((uint32_t)n_ctas, zw.total), 128, 0, s>>>(zw);
 }
 
-template <int PX, int PY>
+// threads: the forward's CTA size; Q4 launches half of them (2 x 2 pixels per lane)
+template <int PX, int PY, bool Q4>
 static void launch_bb(const gs_camera *cams, const Ws &w, const float *d_rgb, const float *d_depth, int n_bins,
                       int threads, int batch_depth, int n_sms, const ZeroWork &zw, cudaStream_t s)
 {
-    const int smem = blend_bwd_smem(batch_depth, PX == 2 && PY == 1 ? threads / 32 : 0);
+    const int bd = Q4 ? std::min(batch_depth, kQ4Batch) : batch_depth;
+    const int smem = blend_bwd_smem(bd, PX == 2 && PY == 1 ? threads / 32 : 0);
+    const int bt = Q4 ? threads / 2 : threads;
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blend_backward_kernel<PX, PY>, threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blend_backward_kernel<PX, PY, Q4>, bt, smem);
     int grid = n_sms * (nb > 0 ? nb : 1);
     if (grid > n_bins) grid = n_bins;
-    blend_backward_kernel<PX, PY><<<grid, threads, smem, s>>>(cams, w, d_rgb, d_depth, zw);
+    blend_backward_kernel<PX, PY, Q4><<<grid, bt, smem, s>>>(cams, w, d_rgb, d_depth, zw);
 }
 
 template <int PX, int PY>
 static int bb_limit_t()
 {
     cudaFuncAttributes a;
-    if (cudaFuncGetAttributes(&a, blend_backward_kernel<PX, PY>) != cudaSuccess) return 0;
+    if (cudaFuncGetAttributes(&a, blend_backward_kernel<PX, PY, false>) != cudaSuccess) return 0;
     return a.maxThreadsPerBlock;
 }
 
@@ -1332,10 +1692,16 @@ void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rg
     if (clear) {
         zw.clear_ctas = (uint32_t)((n_sms + 1) / 2); // half the SMs: measured fastest (all SMs, twice that: slower)
     }
-    if (px == 2 && py == 2) launch_bb<2, 2>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);
-    else if (px == 2) launch_bb<2, 1>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);
-    else if (py == 2) launch_bb<1, 2>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);
-    else launch_bb<1, 1>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);
+    // 2 x 1 pixels per lane with an even number of forward warps: the backward
+    // walks each quarter with 4 lanes of 2 x 2 pixels, in batches of at most
+    // kQ4Batch (its staging needs the depth <= kMaxPerB x its threads)
+    const bool q4 = px == 2 && py == 1 && (threads / 32) % 2 == 0 &&
+                    std::min(batch_depth, kQ4Batch) <= kMaxPerB * (threads / 2);
+    if (px == 2 && py == 2) launch_bb<2, 2, false>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);
+    else if (q4) launch_bb<2, 1, true>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);
+    else if (px == 2) launch_bb<2, 1, false>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);
+    else if (py == 2) launch_bb<1, 2, false>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);
+    else launch_bb<1, 1, false>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);
 }
 
 template <bool OW, bool FUSED>
@@ -1375,13 +1741,14 @@ void launch_preprocess_backward(const Table &tb, const gs_gaussians *g, const gs
 cudaError_t configure_backward_kernels()
 {
     const int smem = blend_bwd_smem(256, 8);
-    cudaError_t e = cudaFuncSetAttribute(blend_backward_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(blend_backward_kernel<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(blend_backward_kernel<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(blend_backward_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const void *ks[] = {reinterpret_cast<const void *>(blend_backward_kernel<1, 1, false>),
+                        reinterpret_cast<const void *>(blend_backward_kernel<2, 1, false>),
+                        reinterpret_cast<const void *>(blend_backward_kernel<2, 1, true>),
+                        reinterpret_cast<const void *>(blend_backward_kernel<1, 2, false>),
+                        reinterpret_cast<const void *>(blend_backward_kernel<2, 2, false>)};
+    cudaError_t e = cudaSuccess;
+    for (const void *k : ks)
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
 }
 

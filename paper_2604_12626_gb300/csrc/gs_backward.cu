@@ -1688,15 +1688,16 @@ void launch_blend_backward(const gs_camera *cams, const Ws &w, const float *d_rg
                            int px, int py, int threads, int batch_depth, int n_sms, const GradOut *clear, int64_t n,
                            cudaStream_t s)
 {
-    ZeroWork zw = zero_work(clear, n);
-    if (clear) {
-        zw.clear_ctas = (uint32_t)((n_sms + 1) / 2); // half the SMs: measured fastest (all SMs, twice that: slower)
-    }
     // 2 x 1 pixels per lane with an even number of forward warps: the backward
     // walks each quarter with 4 lanes of 2 x 2 pixels, in batches of at most
     // kQ4Batch (its staging needs the depth <= kMaxPerB x its threads)
     const bool q4 = px == 2 && py == 1 && (threads / 32) % 2 == 0 &&
                     std::min(batch_depth, kQ4Batch) <= kMaxPerB * (threads / 2);
+    ZeroWork zw = zero_work(clear, n);
+    // CTAs that clear before taking tiles, measured fastest: one per SM with the
+    // one-warp CTAs of the 4-lane walk (a quarter or twice that: slower), one
+    // per two SMs otherwise (all SMs, twice that: slower)
+    if (clear) zw.clear_ctas = (uint32_t)(q4 ? n_sms : (n_sms + 1) / 2);
     if (px == 2 && py == 2) launch_bb<2, 2, false>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);
     else if (q4) launch_bb<2, 1, true>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);
     else if (px == 2) launch_bb<2, 1, false>(cams, w, d_rgb, d_depth, n_bins, threads, batch_depth, n_sms, zw, s);

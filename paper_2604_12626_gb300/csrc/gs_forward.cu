@@ -1120,7 +1120,7 @@ __device__ __forceinline__ void blend_tile(const Ws &w, const gs_camera *cams, c
 // each pixel still sees every Gaussian that covers it, in depth order.  Per
 // pair, the quarters that blended it are kept (4 bits per warp) for the
 // backward, and bit 31 of the key marks a pair some pixel of the tile blended.
-constexpr int kQuarterSlack = 0; // (documentation only: window tests carry 0.01 px + 1e-6 |uc| of slack)
+// The quarter test carries 0.01 px + 1e-6 |uc| of slack for FP32 rounding.
 
 // Lists, per quarter of this warp's block, the entries [0, cnt) of the staged
 // batch whose pixel window [uc - hx, uc + hx] x [vc - hy, vc + hy] meets the

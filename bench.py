@@ -339,18 +339,19 @@ def _units(stats_line):
             "pairs": st.get("pairs"), "visible": st.get("visible")}
 
 
-def ncu_summary(csv_path, command, out_path=None, stats_json=None):
-    """Per-kernel launches, time share and DRAM bytes of an ncu --csv launch
-    list of this bench (metrics gpu__time_duration.sum, dram__bytes_read.sum,
-    dram__bytes_write.sum); writes profiles/dram_traffic.json (or out_path:
-    bytes per gs_render / gs_render_backward call, tagged with the kernel
-    sources' hash), prints the table and returns the per-kernel entries.
-    With stats_json (the bench's JSON line of the captured command) every
-    kernel also gets its bytes per unit (UNIT_OF_KERNEL), which the bench
-    multiplies by its own counts."""
+def _kernel_name(full):
+    import re
+
+    m = re.match(r"(?:void )?(?:gs::)?([A-Za-z_0-9]+)", full)
+    return m.group(1) if m else full[:40]
+
+
+def _launch_list(csv_path):
+    """Per-kernel launches, ms and DRAM bytes (where captured) of an ncu --csv
+    launch list, and the number of forward and backward calls in it (launches
+    of the preprocess and of the blend backward)."""
     import collections
     import csv
-    import re
 
     with open(csv_path) as f:
         rows = [r for r in csv.reader(f) if len(r) > 10]
@@ -363,8 +364,7 @@ def ncu_summary(csv_path, command, out_path=None, stats_json=None):
         if r[iM] == "gpu__time_duration.sum":
             v *= to_ms.get(r[iU], 1e-6)
         per[r[iID]][r[iM]] = v
-        m = re.match(r"(?:void )?(?:gs::)?([A-Za-z_0-9]+)", r[iK])
-        names[r[iID]] = m.group(1) if m else r[iK][:40]
+        names[r[iID]] = _kernel_name(r[iK])
     agg = collections.OrderedDict()
     for i, d in per.items():
         a = agg.setdefault(names[i], dict(launches=0, ms=0.0, rd=0.0, wr=0.0))
@@ -372,33 +372,87 @@ def ncu_summary(csv_path, command, out_path=None, stats_json=None):
         a["ms"] += d.get("gpu__time_duration.sum", 0.0)
         a["rd"] += d.get("dram__bytes_read.sum", 0.0)
         a["wr"] += d.get("dram__bytes_write.sum", 0.0)
-    ours = {k: a for k, a in agg.items() if k in FWD_KERNELS + BWD_KERNELS}
     n_fwd = max(agg.get("preprocess_kernel", {}).get("launches", 0), 1)
     n_bwd = max(agg.get("blend_backward_kernel", {}).get("launches", 0), 1)
+    return agg, n_fwd, n_bwd
+
+
+def ncu_summary(csv_path):
+    """Prints the per-kernel table of an ncu --csv launch list of this bench
+    (launches, time, share of this repository's kernels; DRAM bytes where the
+    list has them) and returns per kernel its launches and ms per call."""
+    agg, n_fwd, n_bwd = _launch_list(csv_path)
+    ours = {k: a for k, a in agg.items() if k in FWD_KERNELS + BWD_KERNELS}
     tot = sum(a["ms"] for a in ours.values())
     kern = {}
     print(f"{'kernel':28s} {'launches':>8s} {'total ms':>9s} {'share':>6s} {'ms/launch':>9s} {'DRAM MB/launch':>14s}")
+    for k, a in sorted(ours.items(), key=lambda x: -x[1]["ms"]):
+        calls = n_fwd if k in FWD_KERNELS else n_bwd
+        kern[k] = {"launches_per_call": a["launches"] / calls, "ms_per_call_under_ncu": a["ms"] / calls}
+        print(f"{k:28s} {a['launches']:8d} {a['ms']:9.3f} {100 * a['ms'] / tot:5.1f}% {a['ms'] / a['launches']:9.4f} "
+              f"{(a['rd'] + a['wr']) / a['launches'] / 1e6:14.1f}")
+    rest = [a for k, a in agg.items() if k not in ours]
+    print(f"(other kernels: {sum(a['launches'] for a in rest)} launches, {sum(a['ms'] for a in rest):.3f} ms; "
+          f"{n_fwd} forward and {n_bwd} backward calls)")
+    return kern
+
+
+def _raw_dram(csv_path):
+    """(kernel, DRAM bytes) of each launch in the raw page of an ncu report
+    (`ncu -i REPORT --page raw --csv`)."""
+    import csv
+
+    with open(csv_path) as f:
+        rows = list(csv.reader(f))
+    h, unit_row, data = rows[0], rows[1], rows[2:]
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
+    iK = h.index("Kernel Name")
+    cols = [h.index("dram__bytes_read.sum"), h.index("dram__bytes_write.sum")]
+    out = []
+    for r in data:
+        if len(r) != len(h):
+            continue
+        b = sum(float(r[i].replace(",", "")) * scale[unit_row[i]] for i in cols)
+        out.append((_kernel_name(r[iK]), b))
+    return out
+
+
+def ncu_traffic(launch_csv, raw_csvs, command, stats_json=None, out_path=None):
+    """profiles/dram_traffic.json (or out_path) from one-kernel captures: each
+    kernel's DRAM bytes per launch from its own report (raw-page CSVs; a kernel
+    launched several times per call is captured over the launches of one whole
+    call), its launches per call from a time-only launch list of the same launch
+    shape whose calls all ran to the end, and -- with stats_json, the captured
+    run's JSON line -- its bytes per unit (UNIT_OF_KERNEL), which the bench
+    multiplies by its own counts.  Tagged with the kernel sources' hash."""
+    import collections
+
+    agg, n_fwd, n_bwd = _launch_list(launch_csv)
     units = None
     if stats_json:
         with open(stats_json) as f:
             units = _units(json.loads(f.read().strip().splitlines()[-1]))
-    for k, a in sorted(ours.items(), key=lambda x: -x[1]["ms"]):
-        calls = n_fwd if k in FWD_KERNELS else n_bwd
-        kern[k] = {"dram_bytes_per_call": (a["rd"] + a["wr"]) / calls, "launches_per_call": a["launches"] / calls,
-                   "ms_per_call_under_ncu": a["ms"] / calls}
+    per = collections.defaultdict(list)
+    for p in raw_csvs:
+        for k, b in _raw_dram(p):
+            per[k].append(b)
+    kern = {}
+    for k in sorted(per):
+        if k not in FWD_KERNELS + BWD_KERNELS or k not in agg:
+            continue
+        lpc = agg[k]["launches"] / (n_fwd if k in FWD_KERNELS else n_bwd)
+        bpl = sum(per[k]) / len(per[k])
+        kern[k] = {"dram_bytes_per_launch": bpl, "captured_launches": len(per[k]), "launches_per_call": lpc,
+                   "dram_bytes_per_call": bpl * lpc}
         if units and units.get(UNIT_OF_KERNEL.get(k)):
             kern[k]["unit"] = UNIT_OF_KERNEL[k]
             kern[k]["bytes_per_unit"] = kern[k]["dram_bytes_per_call"] / units[UNIT_OF_KERNEL[k]]
-        print(f"{k:28s} {a['launches']:8d} {a['ms']:9.3f} {100 * a['ms'] / tot:5.1f}% {a['ms'] / a['launches']:9.4f} "
-              f"{(a['rd'] + a['wr']) / a['launches'] / 1e6:14.1f}  rd {a['rd'] / a['launches'] / 1e6:.1f} "
-              f"wr {a['wr'] / a['launches'] / 1e6:.1f}")
-    rest = [a for k, a in agg.items() if k not in ours]
-    print(f"(other kernels: {sum(a['launches'] for a in rest)} launches, {sum(a['ms'] for a in rest):.3f} ms; "
-          f"{n_fwd} forward and {n_bwd} backward calls)")
+        print(f"{k:28s} {len(per[k]):3d} launches captured  {bpl / 1e6:10.1f} MB/launch  x {lpc:.2f} per call"
+              + (f"  {kern[k]['bytes_per_unit']:8.1f} B per {kern[k]['unit']}" if "unit" in kern[k] else ""))
     out = {"source_hash": source_hash(),
            "what": "DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of each kernel per gs_render / "
-                   "gs_render_backward call (all its launches in that call), from one ncu run; stale once the "
-                   "kernel sources change (source_hash over csrc/)",
+                   "gs_render_backward call: bytes per launch from a capture of that kernel alone, times its "
+                   "launches per call; stale once the kernel sources change (source_hash over csrc/)",
            "command": command, "units_of_capture": units, "kernels": kern}
     with open(out_path or os.path.join(ROOT, "profiles", "dram_traffic.json"), "w") as f:
         json.dump(out, f, indent=1)
@@ -1058,15 +1112,21 @@ def main():
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--tile", default="", help="fixed tile_w,tile_h,batch_depth instead of the autotuner")
     ap.add_argument("--envs", type=int, default=N_ENVS, help="envs per GPU (64; fewer only for small profiling cases)")
-    ap.add_argument("--ncu-summary", nargs="+", metavar="ARG",
-                    help="CSV COMMAND [STATS_JSON]: summarise an ncu launch list of this bench into "
-                         "profiles/dram_traffic.json (with the captured run's JSON line: bytes per unit) and exit")
+    ap.add_argument("--ncu-summary", metavar="CSV",
+                    help="print the per-kernel table of an ncu --csv launch list of this bench and exit")
+    ap.add_argument("--ncu-traffic", nargs="+", metavar="ARG",
+                    help="LAUNCH_CSV STATS_JSON COMMAND RAW_CSV...: write profiles/dram_traffic.json from a "
+                         "complete time-only launch list of the same launch shape (launches per call), the JSON "
+                         "line of COMMAND and the raw-page CSVs of one-kernel captures of COMMAND, and exit")
     args = ap.parse_args()
     if args.ncu_summary:
-        if len(args.ncu_summary) not in (2, 3):
-            ap.error("--ncu-summary takes CSV COMMAND [STATS_JSON]")
-        csv_path, command = args.ncu_summary[:2]
-        ncu_summary(csv_path, command, stats_json=args.ncu_summary[2] if len(args.ncu_summary) == 3 else None)
+        ncu_summary(args.ncu_summary)
+        return
+    if args.ncu_traffic:
+        if len(args.ncu_traffic) < 4:
+            ap.error("--ncu-traffic takes LAUNCH_CSV STATS_JSON COMMAND RAW_CSV...")
+        launch_csv, stats_json, command = args.ncu_traffic[:3]
+        ncu_traffic(launch_csv, args.ncu_traffic[3:], command, stats_json=stats_json)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -11,9 +11,12 @@
 //                  the covariance one summed as (Q d)(Q d)^T / 2 per pixel, Q
 //                  the conic and d the offset, so no conic-to-covariance
 //                  conversion follows the sum -- are reduced
-//                  across the warp by a shuffle transpose, then across the CTA
-//                  in shared memory, and flushed with float4 atomics per
-//                  (tile, record) into the record's gradient row.  In overwrite
+//                  by shuffle transposes (across the warp; or per 4 x 4
+//                  quarter of the tile, over its 8 or 4 lanes, where the
+//                  forward kept per-quarter lists at 2 x 1 pixels per
+//                  thread), then across the CTA in shared memory, and flushed
+//                  with float4 atomics per (tile, record) into the record's
+//                  gradient row.  In overwrite
 //                  mode the same kernel clears the dense parameter gradients
 //                  (TMA bulk copies).
 // preprocess_backward  env-aligned chunks; the Gaussians some view sees go
@@ -1512,8 +1515,9 @@ __device__ __forceinline__ void gaussian_backward(const gs_camera *__restrict__ 
 
 
 // Chunked like the forward preprocess: every lane checks whether any view sees
-// its Gaussian (zero rows otherwise, in overwrite mode); the seen ones go
-// through a per-warp ring queue and are processed 32 at a time, so that the
+// its Gaussian (the rows of an unseen one are not touched: in overwrite mode
+// the blend backward has cleared them); the seen ones go through a per-warp
+// ring queue and are processed 32 at a time, so that the
 // long chain runs on full warps.
 constexpr int kBwdWarpQ = 64;
 

@@ -21,7 +21,11 @@
 //               from an atomic queue, heaviest first -- stages batches of
 //               records in shared memory and blends front to back per pixel
 //               with early exit once every pixel of the warp has stopped;
-//               flags in its key every pair that some pixel blended.
+//               flags in its key every pair that some pixel blended.  At
+//               2 x 1 pixels per thread (blendq_tile) each 4 x 4 quarter of a
+//               warp's 8 x 8 block walks its own list of the batch entries
+//               whose window reaches it, and the quarters that blended each
+//               pair are kept for the backward.
 // The rasterisation follows the 3DGS method the paper builds its renderer on
 // (Sec. 2.2, Sec. 3.2); the exact definition is the one in include/gs.h.
 #include <cuda_bf16.h>

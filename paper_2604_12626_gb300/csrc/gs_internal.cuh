@@ -144,7 +144,7 @@ constexpr int kChunkMax = 8192; // Gaussians per preprocess / scatter CTA, at mo
 constexpr int kChunkMin = 1024;
 constexpr int kHistCap = 8192;   // (view, tile) counters a chunk keeps in shared memory
 
-// Chunk size from the Gaussian count alone: about 2048 chunks, 1024..16384.
+// Chunk size from the Gaussian count alone: about 2048 chunks, 1024..8192.
 inline int chunk_of(int64_t n)
 {
     int c = kChunkMin;

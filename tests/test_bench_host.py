@@ -1,7 +1,8 @@
-"""Host logic of bench.py, no GPU: the ncu launch-list summary (per-call DRAM
-bytes of the forward and backward kernels, unit conversion, foreign kernels left
-out), the stale-hash rule of the traffic file, and the roofline arithmetic
-against hand-computed figures."""
+"""Host logic of bench.py, no GPU: the ncu launch-list summary (launches and
+time per call of the forward and backward kernels, foreign kernels left out),
+the traffic file built from one-kernel captures (bytes per launch with unit
+conversion, per call, per unit), its stale-hash rule, and the roofline
+arithmetic against hand-computed figures."""
 import csv
 import json
 import os
@@ -24,33 +25,82 @@ def _launch(rows, i, name, ns, rd, wr):
     rows.append(base + ["dram__bytes_write.sum", "byte", f"{wr:,}"])
 
 
-def test_ncu_summary_bytes_per_call(tmp_path):
-    rows, i = [], 0
-    for call in range(2):  # two forwards: two merge passes each; one backward
-        for name, ns, rd, wr in (("void gs::preprocess_kernel<1, false>(const gs_camera *, GaussIn, Ws)", 2000, 100, 50),
-                                 ("gs::merge_pass_kernel(Ws, int)", 300, 10, 10),
-                                 ("gs::merge_pass_kernel(Ws, int)", 300, 20, 0),
-                                 ("void gs::blend_persistent_kernel<2, 1>(const gs_camera *, Ws, OutPtrs)", 3000, 40, 4)):
-            _launch(rows, i, name, ns, rd, wr)
-            i += 1
-    _launch(rows, i, "void gs::blend_backward_kernel<2, 1>(const gs_camera *, Ws, const float *)", 5000, 7, 1000)
-    i += 1
-    _launch(rows, i, "void at::native::vectorized_elementwise_kernel<4>(int)", 9000, 1, 1)  # not ours
-    p = tmp_path / "launches.csv"
-    with open(p, "w", newline="") as f:
+def _write_list(path, rows):
+    with open(path, "w", newline="") as f:
         w = csv.writer(f)
         w.writerow(HEADER)
         w.writerows(rows)
-    out = tmp_path / "traffic.json"
-    kern = bench.ncu_summary(str(p), "ncu ... python bench.py", out_path=str(out))
-    assert kern["preprocess_kernel"]["dram_bytes_per_call"] == 150
+
+
+def _write_raw(path, launches):
+    """Raw page of an ncu report: header, units, one row per launch."""
+    h = ["ID", "Kernel Name", "dram__bytes_read.sum", "dram__bytes_write.sum", "gpu__time_duration.sum"]
+    with open(path, "w", newline="") as f:
+        w = csv.writer(f)
+        w.writerow(h)
+        w.writerow(["", "", launches[0][2], launches[0][4], "nsecond"])
+        for i, (name, rd, _, wr, _) in enumerate(launches):
+            w.writerow([str(i), name, f"{rd:,}", f"{wr:,}", "1,000"])
+
+
+PRE = "void gs::preprocess_kernel<1, false>(const gs_camera *, GaussIn, Ws)"
+MERGE = "gs::merge_pass_kernel(Ws, int)"
+BLEND = "void gs::blend_persistent_kernel<2, 1>(const gs_camera *, Ws, OutPtrs)"
+BWD = "void gs::blend_backward_kernel<2, 1>(const gs_camera *, Ws, const float *)"
+
+
+def _two_forwards_one_backward(rows):
+    i = 0
+    for call in range(2):  # two forwards: two merge passes each; one backward
+        for name, ns in ((PRE, 2000), (MERGE, 300), (MERGE, 300), (BLEND, 3000)):
+            _launch(rows, i, name, ns, 0, 0)
+            i += 1
+    _launch(rows, i, BWD, 5000, 0, 0)
+    _launch(rows, i + 1, "void at::native::vectorized_elementwise_kernel<4>(int)", 9000, 1, 1)  # not ours
+
+
+def test_ncu_summary_per_call(tmp_path):
+    rows = []
+    _two_forwards_one_backward(rows)
+    p = tmp_path / "launches.csv"
+    _write_list(p, rows)
+    kern = bench.ncu_summary(str(p))
     assert kern["merge_pass_kernel"]["launches_per_call"] == 2
-    assert kern["merge_pass_kernel"]["dram_bytes_per_call"] == 40
+    assert kern["preprocess_kernel"]["launches_per_call"] == 1
     assert kern["blend_persistent_kernel"]["ms_per_call_under_ncu"] == pytest.approx(0.003)
-    assert kern["blend_backward_kernel"]["dram_bytes_per_call"] == 1007  # one backward call
+    assert kern["blend_backward_kernel"]["ms_per_call_under_ncu"] == pytest.approx(0.005)  # one backward call
     assert "vectorized_elementwise_kernel" not in kern
+
+
+def test_ncu_traffic_from_one_kernel_captures(tmp_path):
+    """Bytes per launch from each kernel's own capture (units converted),
+    launches per call from the time-only list, bytes per unit from the
+    captured run's counts; the file carries the sources' hash."""
+    rows = []
+    _two_forwards_one_backward(rows)
+    lst = tmp_path / "launches.csv"
+    _write_list(lst, rows)
+    _write_raw(tmp_path / "pre.csv", [(PRE, 1.5, "Kbyte", 500, "byte")])  # 1500 + 500 bytes
+    _write_raw(tmp_path / "merge.csv", [(MERGE, 10, "byte", 10, "byte"), (MERGE, 20, "byte", 0, "byte"),
+                                        (MERGE, 30, "byte", 20, "byte")])  # 30 bytes per launch
+    _write_raw(tmp_path / "bwd.csv", [(BWD, 2, "Mbyte", 1, "Mbyte")])
+    line = {"config": {"gaussians_per_gpu": 100}, "stats": {"records": 100, "pairs": 30, "visible": 25}}
+    sj = tmp_path / "small.json"
+    sj.write_text("log line\n" + json.dumps(line) + "\n")
+    out = tmp_path / "traffic.json"
+    kern = bench.ncu_traffic(str(lst), [str(tmp_path / x) for x in ("pre.csv", "merge.csv", "bwd.csv")], "cmd",
+                             stats_json=str(sj), out_path=str(out))
+    assert kern["preprocess_kernel"]["dram_bytes_per_call"] == pytest.approx(2000.0)
+    assert kern["preprocess_kernel"]["unit"] == "gaussians"
+    assert kern["preprocess_kernel"]["bytes_per_unit"] == pytest.approx(20.0)
+    assert kern["merge_pass_kernel"]["captured_launches"] == 3
+    assert kern["merge_pass_kernel"]["dram_bytes_per_launch"] == pytest.approx(30.0)
+    assert kern["merge_pass_kernel"]["dram_bytes_per_call"] == pytest.approx(60.0)  # two passes per call
+    assert kern["merge_pass_kernel"]["bytes_per_unit"] == pytest.approx(2.0)  # over 30 pairs
+    assert kern["blend_backward_kernel"]["dram_bytes_per_call"] == pytest.approx(3e6)
+    assert "blend_persistent_kernel" not in kern  # not captured
     t = json.loads(out.read_text())
-    assert t["source_hash"] == bench.source_hash() and t["kernels"] == kern
+    assert t["source_hash"] == bench.source_hash() and t["kernels"] == kern and t["command"] == "cmd"
 
 
 def test_traffic_file_is_ignored_once_sources_change(monkeypatch, tmp_path):
@@ -96,20 +146,20 @@ def test_traffic_scaled_by_units(tmp_path, monkeypatch):
     per unit: preprocess per Gaussian, the pair stages per pair, the
     preprocess backward per visible record."""
     rows = []
-    _launch(rows, 0, "void gs::preprocess_kernel<1, false>(const gs_camera *, GaussIn, Ws)", 2000, 600, 400)
-    _launch(rows, 1, "gs::scatter_kernel(const gs_camera *, Ws)", 500, 100, 200)
-    _launch(rows, 2, "gs::preprocess_backward_kernel<1, true>(const gs_camera *, GaussInB, Ws, GradOut)", 900, 50, 50)
-    _launch(rows, 3, "void gs::blend_backward_kernel<2, 1>(const gs_camera *, Ws, const float *)", 500, 1, 1)
-    p = tmp_path / "launches.csv"
-    with open(p, "w", newline="") as f:
-        w = csv.writer(f)
-        w.writerow(HEADER)
-        w.writerows(rows)
+    SC = "gs::scatter_kernel(const gs_camera *, Ws)"
+    PB = "gs::preprocess_backward_kernel<1, true>(const gs_camera *, GaussInB, Ws, GradOut)"
+    for i, name in enumerate((PRE, SC, PB, BWD)):
+        _launch(rows, i, name, 1000, 0, 0)
+    lst = tmp_path / "launches.csv"
+    _write_list(lst, rows)
+    for f, name, b in (("a.csv", PRE, 1000), ("b.csv", SC, 300), ("c.csv", PB, 100)):
+        _write_raw(tmp_path / f, [(name, b, "byte", 0, "byte")])
     line = {"config": {"gaussians_per_gpu": 100}, "stats": {"records": 100, "pairs": 30, "visible": 25}}
     sj = tmp_path / "small.json"
     sj.write_text("log line\n" + json.dumps(line) + "\n")
     out = tmp_path / "traffic.json"
-    kern = bench.ncu_summary(str(p), "cmd", out_path=str(out), stats_json=str(sj))
+    kern = bench.ncu_traffic(str(lst), [str(tmp_path / f) for f in ("a.csv", "b.csv", "c.csv")], "cmd",
+                             stats_json=str(sj), out_path=str(out))
     assert kern["preprocess_kernel"]["unit"] == "gaussians" and kern["preprocess_kernel"]["bytes_per_unit"] == 10.0
     assert kern["scatter_kernel"]["bytes_per_unit"] == 10.0  # 300 bytes over 30 pairs
     assert kern["preprocess_backward_kernel"]["bytes_per_unit"] == 4.0  # 100 bytes over 25 visible

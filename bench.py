@@ -417,6 +417,71 @@ def _raw_dram(csv_path):
     return out
 
 
+# rows of the full-capture table: (label, metric, scale); None = SM active / elapsed
+NCU_TABLE = (
+    ("duration (us, serialised)", "gpu__time_duration.sum", 1e-3),
+    ("warp instructions (M)", "smsp__inst_executed.sum", 1e-6),
+    ("issue slots busy (% of active)", "smsp__issue_active.avg.pct_of_peak_sustained_active", 1.0),
+    ("warps active (% of peak)", "sm__warps_active.avg.pct_of_peak_sustained_active", 1.0),
+    ("registers per thread", "launch__registers_per_thread", 1.0),
+    ("ALU pipe (% active)", "sm__inst_executed_pipe_alu.avg.pct_of_peak_sustained_active", 1.0),
+    ("FMA pipe (% active)", "sm__inst_executed_pipe_fma.avg.pct_of_peak_sustained_active", 1.0),
+    ("XU pipe (% active)", "sm__inst_executed_pipe_xu.avg.pct_of_peak_sustained_active", 1.0),
+    ("LSU pipe (% active)", "sm__inst_executed_pipe_lsu.avg.pct_of_peak_sustained_active", 1.0),
+    ("DRAM read (MB)", "dram__bytes_read.sum", 1e-6),
+    ("DRAM write (MB)", "dram__bytes_write.sum", 1e-6),
+    ("DRAM throughput (% of peak)", "gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed", 1.0),
+    ("shared bank conflicts (M)", "l1tex__data_bank_conflicts_pipe_lsu_mem_shared.sum", 1e-6),
+    ("SM cycles active / elapsed", None, 1.0),
+)
+NCU_STALLS = ("long_scoreboard", "short_scoreboard", "wait", "barrier", "not_selected", "math_pipe_throttle",
+              "mio_throttle", "lg_throttle")
+
+
+def _raw_first(csv_path):
+    """{metric: value in base units} of the first launch in the raw page of
+    an ncu report (`ncu -i REPORT --page raw --csv`): times in ns, bytes in
+    bytes."""
+    import csv
+
+    with open(csv_path) as f:
+        rows = list(csv.reader(f))
+    h, unit_row, vals = rows[0], rows[1], rows[2]
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1.0, "ns": 1.0, "usecond": 1e3,
+             "us": 1e3, "msecond": 1e6, "ms": 1e6}
+    out = {}
+    for k, u, v in zip(h, unit_row, vals):
+        try:
+            out[k] = float(v.replace(",", "")) * scale.get(u, 1.0)
+        except ValueError:
+            pass
+    return out
+
+
+def ncu_table(raw_csvs):
+    """Markdown table of the figures the kernel summary quotes, one column per
+    report (raw-page CSVs of `ncu --set full` captures, one launch each)."""
+    ds = [_raw_first(p) for p in raw_csvs]
+    names = [os.path.basename(p).replace("raw_", "").replace(".csv", "") for p in raw_csvs]
+    lines = ["| metric | " + " | ".join(names) + " |", "|---" * (len(names) + 1) + "|"]
+
+    def cell(x, fmt):
+        return "" if x is None else format(x, fmt)
+
+    for label, key, sc in NCU_TABLE:
+        if key is None:
+            cells = [cell(d["sm__cycles_active.avg"] / d["sm__cycles_elapsed.avg"]
+                          if d.get("sm__cycles_elapsed.avg") else None, ".2f") for d in ds]
+        else:
+            cells = [cell(d[key] * sc if key in d else None, ".1f") for d in ds]
+        lines.append(f"| {label} | " + " | ".join(cells) + " |")
+    for st in NCU_STALLS:
+        key = f"smsp__average_warps_issue_stalled_{st}_per_issue_active.ratio"
+        lines.append(f"| stall {st} (per issue) | " + " | ".join(cell(d.get(key), ".2f") for d in ds) + " |")
+    print("\n".join(lines))
+    return lines
+
+
 def ncu_traffic(launch_csv, raw_csvs, command, stats_json=None, out_path=None):
     """profiles/dram_traffic.json (or out_path) from one-kernel captures: each
     kernel's DRAM bytes per launch from its own report (raw-page CSVs; a kernel
@@ -1114,6 +1179,8 @@ def main():
     ap.add_argument("--envs", type=int, default=N_ENVS, help="envs per GPU (64; fewer only for small profiling cases)")
     ap.add_argument("--ncu-summary", metavar="CSV",
                     help="print the per-kernel table of an ncu --csv launch list of this bench and exit")
+    ap.add_argument("--ncu-table", nargs="+", metavar="RAW_CSV",
+                    help="print the full-capture table of the kernel summary from raw-page CSVs and exit")
     ap.add_argument("--ncu-traffic", nargs="+", metavar="ARG",
                     help="LAUNCH_CSV STATS_JSON COMMAND RAW_CSV...: write profiles/dram_traffic.json from a "
                          "complete time-only launch list of the same launch shape (launches per call), the JSON "
@@ -1121,6 +1188,9 @@ def main():
     args = ap.parse_args()
     if args.ncu_summary:
         ncu_summary(args.ncu_summary)
+        return
+    if args.ncu_table:
+        ncu_table(args.ncu_table)
         return
     if args.ncu_traffic:
         if len(args.ncu_traffic) < 4:

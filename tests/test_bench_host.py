@@ -171,3 +171,24 @@ def test_traffic_scaled_by_units(tmp_path, monkeypatch):
     assert per["preprocess"]["traffic"] == pytest.approx(10.0 * 1000)
     assert per["scatter"]["traffic"] == pytest.approx(10.0 * 500)
     assert per["preprocess_backward"]["traffic"] == pytest.approx(4.0 * 200)
+
+
+def test_ncu_table_from_raw_pages(tmp_path, capsys):
+    """The kernel summary's table: units converted (us -> us, Gbyte -> MB),
+    SM active over elapsed, stall ratios, blank cells for missing metrics."""
+    h = ["ID", "Kernel Name", "gpu__time_duration.sum", "dram__bytes_read.sum", "sm__cycles_active.avg",
+         "sm__cycles_elapsed.avg", "smsp__average_warps_issue_stalled_wait_per_issue_active.ratio"]
+    p = tmp_path / "raw_k.csv"
+    with open(p, "w", newline="") as f:
+        w = csv.writer(f)
+        w.writerow(h)
+        w.writerow(["", "", "us", "Gbyte", "cycle", "cycle", ""])
+        w.writerow(["0", "void k(int)", "545.7", "1.25", "50", "200", "1.5"])
+    lines = bench.ncu_table([str(p)])
+    assert lines[0] == "| metric | k |"
+    rows = {ln.split(" | ")[0].lstrip("| "): ln.split(" | ")[1].rstrip(" |") for ln in lines[2:]}
+    assert rows["duration (us, serialised)"] == "545.7"
+    assert rows["DRAM read (MB)"] == "1250.0"
+    assert rows["SM cycles active / elapsed"] == "0.25"
+    assert rows["stall wait (per issue)"] == "1.50"
+    assert rows["DRAM write (MB)"] == ""  # not in the report

@@ -285,6 +285,52 @@ def test_repeated_backward_of_one_forward(gs):
     assert float(a["opacity_logits"].abs().sum()) > 0
 
 
+@pytest.mark.parametrize("overwrite", [False, True])
+def test_backward_edge_cases(gs, oracle, overwrite):
+    """Degenerate inputs of the adjoint, in both gradient modes: a scene the
+    near plane culls entirely (every gradient exactly zero), an empty env next
+    to a non-empty one at 1x1 pixels (hundreds of Gaussians through one pixel
+    that stops), and one Gaussian covering a ragged 37x23 image, the last two
+    against the oracle adjoint."""
+    W, H = 37, 23
+    cam = synth.identity_camera(W, H)
+    rng = np.random.default_rng(40)
+    kw = dict(grad_overwrite=overwrite)
+    # everything behind the camera
+    g = synth.box_scene(500, seed=10)
+    g["means"][:, 2] = np.float32(-1.0)
+    d_rgb = rng.standard_normal((1, 3, H, W)).astype(np.float32)
+    d_depth = rng.standard_normal((1, H, W)).astype(np.float32)
+    a = gpu_forward_backward(gs, g, cam[None], W, H, d_rgb, d_depth, **kw)
+    for k in GROUPS:
+        assert np.all(a[k] == 0.0), k
+    # an empty env next to a non-empty one; 1x1 image
+    g = synth.box_scene(400, seed=11)
+    g["log_scales"] += np.float32(2.0)
+    offs = np.array([0, 0, 400])
+    c1 = synth.identity_camera(1, 1)
+    cams = np.stack([c1, c1])
+    d_rgb = rng.standard_normal((2, 3, 1, 1)).astype(np.float32)
+    d_depth = rng.standard_normal((2, 1, 1)).astype(np.float32)
+    mask_ambiguous(oracle, g, cams, 1, 1, d_rgb, d_depth, offs=offs)
+    a = gpu_forward_backward(gs, g, cams, 1, 1, d_rgb, d_depth, offs=offs, **kw)
+    b = oracle_grads(oracle, g, cams, 1, 1, d_rgb, d_depth, offs=offs)
+    assert np.abs(b["opacity_logits"]).max() > 0  # the pixel passes gradient
+    for k in GROUPS:
+        check_grad(a[k], b[k], f"1x1 {k}", 1e-3)
+    # one Gaussian covering the whole image
+    g = dict(means=np.float32([[0.1, -0.05, 3.0]]), log_scales=np.float32([[1.0, 0.8, 1.2]]),
+             quats=np.float32([[0.9, 0.1, -0.2, 0.3]]), opacity_logits=np.float32([1.5]),
+             sh=(0.3 * rng.standard_normal((1, 16, 3))).astype(np.float32))
+    d_rgb = rng.standard_normal((1, 3, H, W)).astype(np.float32)
+    d_depth = rng.standard_normal((1, H, W)).astype(np.float32)
+    mask_ambiguous(oracle, g, cam[None], W, H, d_rgb, d_depth)
+    a = gpu_forward_backward(gs, g, cam[None], W, H, d_rgb, d_depth, **kw)
+    b = oracle_grads(oracle, g, cam[None], W, H, d_rgb, d_depth)
+    for k in GROUPS:
+        check_grad(a[k], b[k], f"one Gaussian {k}", 1e-4)
+
+
 def test_overwrite_mode_clears_unseen_rows(gs):
     """Overwrite mode (GS_FLAG_GRAD_OVERWRITE) on gradient buffers full of
     garbage: every row ends as the accumulate mode's gradient into zeroed
